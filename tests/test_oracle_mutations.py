@@ -1,0 +1,90 @@
+"""Plant plausible mistakes in the oracle and check that its pins reject them (CPU only).
+
+Each mutation is applied with monkeypatch to the oracle module, then the pin
+that should notice it is re-run and must fail.
+"""
+import numpy as np
+import pytest
+
+import tests.test_oracle_pins as pins
+from oracle import philox, rsvd64, single_pass, srft
+
+
+def _fails(fn, *args):
+    with pytest.raises((AssertionError, ValueError)):
+        fn(*args)
+
+
+def test_philox_swapped_halves_is_caught(monkeypatch):
+    orig = philox.philox4x32_10
+
+    def bad(counter, key):
+        out = orig(counter, key)
+        return out[:, [1, 0, 2, 3]]
+
+    monkeypatch.setattr(philox, "philox4x32_10", bad)
+    _fails(pins.test_philox_known_answers)
+
+
+def test_box_muller_wrong_branch_is_caught(monkeypatch):
+    def bad(seed, stream, rows, cols):
+        groups = (cols + 3) // 4
+        u = philox.bits_to_uniform(philox.raw_words(seed, stream, rows, groups))
+        r = np.sqrt(-2.0 * np.log(u[..., 0]))
+        z = np.stack([r * np.cos(2 * np.pi * u[..., 1])] * 4, axis=-1)   # cos for every output
+        return z.reshape(rows, groups * 4)[:, :cols]
+
+    monkeypatch.setattr(philox, "gaussian", bad)
+    _fails(pins.test_gaussian_layout_and_moments)
+
+
+def test_dropped_power_step_is_caught(monkeypatch):
+    orig = rsvd64.range_finder
+
+    def bad(a, omega, q=0, keep_steps=False):
+        return orig(a, omega, 0, keep_steps) if not keep_steps else orig(a, omega, 0, True)
+
+    monkeypatch.setattr(rsvd64, "range_finder", bad)
+    _fails(pins.test_power_spectrum_and_algorithm_4_3_equivalence)
+
+
+def test_missing_qr_sign_fix_is_caught(monkeypatch):
+    def bad(y):
+        q, r = np.linalg.qr(y)
+        return -q, -r
+
+    monkeypatch.setattr(rsvd64, "qr_pos", bad)
+    _fails(pins.test_qr_pos)
+
+
+def test_wrong_truncation_is_caught(monkeypatch):
+    monkeypatch.setattr(rsvd64, "truncate", lambda u, s, v, k: (u[:, -k:], s[-k:], v[:, -k:]))
+    _fails(pins.test_truncation_theorem_9_3_and_no_degradation)
+
+
+def test_transposed_stage_b_is_caught(monkeypatch):
+    def bad(a, qmat):
+        b = qmat.T @ a
+        ut, s, vt = np.linalg.svd(b, full_matrices=False)
+        return qmat @ ut, s, vt          # V returned untransposed
+    monkeypatch.setattr(rsvd64, "direct_svd", bad)
+    _fails(pins.test_truncation_theorem_9_3_and_no_degradation)
+
+
+def test_srft_missing_scale_is_caught(monkeypatch):
+    orig = srft.omega_complex
+    monkeypatch.setattr(srft, "omega_complex", lambda d, f: orig(d, f) / np.sqrt(d.shape[0] / f.shape[0]))
+    _fails(pins.test_srft_structure)
+
+
+def test_sylvester_sign_error_is_caught(monkeypatch):
+    def bad(x1, c1, x2, c2):
+        p = x2 @ x2.T
+        s = x1 @ x1.T
+        rhs = c1 @ x1.T - x2 @ c2.T
+        lp, up = np.linalg.eigh(p)
+        ls, us = np.linalg.eigh(s)
+        return up @ ((up.T @ rhs @ us) / (lp[:, None] + ls[None, :])) @ us.T
+
+    monkeypatch.setattr(single_pass, "min_residual", bad)
+    _fails(pins.test_single_pass_solver_matches_bruteforce)
