@@ -1,0 +1,172 @@
+/*
+ * rsvd.h -- C ABI of the GB300 (sm_103a) randomized range finder and
+ * randomized SVD library.
+ *
+ * The computation follows Halko, Martinsson and Tropp, "Finding structure with
+ * randomness" (SIAM Review 53(2), 2011):
+ *   Stage A: draw a test matrix Omega (Algorithm 4.1 step 1; the SRFT of
+ *            Section 4.6), form Y = A Omega, and run q steps of randomized
+ *            subspace iteration (Algorithm 4.4), orthonormalising after every
+ *            application of A or A^T (the round-off remark of Section 4.5);
+ *   Stage B: form B = Q^T A, take the SVD of the small matrix and lift
+ *            U = Q Ut (Algorithm 5.1), truncated to rank k (Remark 5.1).
+ * The problem solved is the fixed-rank problem of Section 1.3: a target rank
+ * k and an oversampling p give a basis of l = k + p columns.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  A is m x n with leading dimension lda >= n
+ *     (elements), float32 or bfloat16 as chosen in rsvd_options_t.
+ *   - Pointers named *_host are host memory; every other matrix pointer is
+ *     device memory on the current CUDA device.  The caller owns all of them.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Work is enqueued asynchronously on the plan's
+ *     stream; argument errors are returned at once, errors found on the
+ *     device (breakdown, non-finite data, a bounded wait that expired) are
+ *     recorded in the plan's device status word and returned by rsvd_sync()
+ *     and by the next call on the plan.
+ *   - A plan is not thread safe; distinct plans may be used concurrently.
+ *   - Singular values are returned in descending order.  The sign of each
+ *     singular-vector pair (u_j, v_j) is not specified.
+ */
+#ifndef PAPER_0909_4061_RSVD_H
+#define PAPER_0909_4061_RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RSVD_API __attribute__((visibility("default")))
+#else
+#define RSVD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsvd_plan_s* rsvd_plan_t;
+
+typedef enum {
+  RSVD_OK = 0,
+  RSVD_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, misaligned lda, unsupported combination */
+  RSVD_ERR_ALLOC = 2,         /* device or pinned-host allocation failed */
+  RSVD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  RSVD_ERR_NUMERICAL = 4,     /* Cholesky or Jacobi breakdown that the safeguards could not absorb */
+  RSVD_ERR_NONFINITE = 5,     /* NaN or Inf met in A or in an intermediate */
+  RSVD_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+  RSVD_ERR_UNSUPPORTED = 7    /* valid request the library does not implement (yet) */
+} rsvd_status_t;
+
+enum { RSVD_F32 = 0, RSVD_BF16 = 1 };                 /* element type of A */
+enum { RSVD_GAUSSIAN = 0, RSVD_SRFT = 1 };            /* test matrix (Section 4.1 / 4.6) */
+enum { RSVD_PLAIN_FP32 = 0, RSVD_BF16_TC = 1 };       /* how the passes over A are computed */
+
+typedef struct {
+  int32_t dtype_A;      /* RSVD_F32 or RSVD_BF16 */
+  int32_t test_matrix;  /* RSVD_GAUSSIAN (default) or RSVD_SRFT */
+  int32_t precision;    /* RSVD_PLAIN_FP32: float32 A, float32 FMA on CUDA cores.
+                           RSVD_BF16_TC: bfloat16 A, tcgen05 tensor-core products with
+                           float32 accumulation, float32 re-orthonormalisation, and a
+                           split (hi + lo) basis in the final pass B^T = A^T Q. */
+  int32_t single_pass;  /* 1: two-sided one-pass sketch of Section 5.5 (q ignored) */
+  int32_t recompute;    /* backward: recompute the sample matrices instead of storing them */
+  int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation: 2 or 3 (default 3:
+                           one shifted round for ill-conditioned samples, then two plain) */
+  int64_t lda;          /* leading dimension of A in elements; 0 means n */
+} rsvd_options_t;
+
+/* Fill *opt with the defaults: float32 A, Gaussian test matrix, plain FP32,
+ * two-pass Stage B, three orthonormalisation rounds, lda = n. */
+RSVD_API void rsvd_options_default(rsvd_options_t* opt);
+
+/* Create a plan for the fixed-rank problem (Section 1.3): A is m x n, target
+ * rank k >= 1, oversampling p >= 0, q >= 0 power steps (Algorithm 4.4), and
+ * the test-matrix seed.  Requires l = k + p <= min(m, n) and l <= 256.  All
+ * device workspace is allocated here (rsvd_workspace_bytes reports it); the
+ * plan's work runs on `stream`.  On failure *plan is set to NULL. */
+RSVD_API rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t k,
+                               int32_t p, int32_t q, uint64_t seed,
+                               const rsvd_options_t* opt, void* stream);
+
+/* Release the plan and its workspace (waits for its stream first).  NULL is a no-op. */
+RSVD_API rsvd_status_t rsvd_plan_destroy(rsvd_plan_t plan);
+
+/* Device workspace held by the plan, in bytes. */
+RSVD_API rsvd_status_t rsvd_workspace_bytes(rsvd_plan_t plan, size_t* bytes);
+
+/* Stage A only (Algorithm 4.4; Algorithm 4.1 when q = 0; Algorithm 4.5 for the
+ * SRFT).  A: device, m x n.  Q: device, m x l float32 with leading dimension
+ * ldq >= l; on return its columns are an orthonormal basis approximating the
+ * range of A, in the order the orthonormaliser produces them (diag(R) > 0). */
+RSVD_API rsvd_status_t rsvd_range_finder(rsvd_plan_t plan, const void* A, float* Q, int64_t ldq);
+
+/* Stage A + Stage B (Algorithm 4.4 then Algorithm 5.1 with the Remark 5.1
+ * truncation).  A: device, m x n.  U: device m x k, S: device k, V: device
+ * n x k, all float32 row-major with leading dimension k.  A ~= U diag(S) V^T. */
+RSVD_API rsvd_status_t rsvd_svd(rsvd_plan_t plan, const void* A, float* U, float* S, float* V);
+
+/* rsvd_svd for host-resident data: copies A (host, m x n with the plan's lda)
+ * to a device buffer owned by the plan, runs rsvd_svd, copies U, S, V back to
+ * host memory, and waits for completion.  Page-locked host buffers give the
+ * full copy bandwidth; pageable buffers work but are staged by the driver. */
+RSVD_API rsvd_status_t rsvd_svd_host(rsvd_plan_t plan, const void* A_host, float* U_host,
+                            float* S_host, float* V_host);
+
+/* Gradient of L = ||A - U diag(S) V^T||_F^2 + sum(S) composed with the
+ * caller's loss, Omega held fixed: given the cotangents gU (m x k), gS (k),
+ * gV (n x k) of the caller's loss (any may be NULL = zero) plus the built-in
+ * reconstruction term when add_recon != 0, writes gA (device, m x n float32,
+ * leading dimension n).  Must follow an rsvd_svd call on the same A. */
+RSVD_API rsvd_status_t rsvd_svd_backward(rsvd_plan_t plan, const void* A, const float* gU,
+                                const float* gS, const float* gV, int32_t add_recon,
+                                float* gA);
+
+/* Parity hooks for the test matrix.  get: copy the plan's n x l Omega (device
+ * float32, leading dimension l) as drawn for its seed or as last set.  set:
+ * use the caller's n x l Omega (device float32, leading dimension l) instead
+ * of the seeded draw; NULL returns to the seeded draw. */
+RSVD_API rsvd_status_t rsvd_get_omega(rsvd_plan_t plan, float* Omega);
+RSVD_API rsvd_status_t rsvd_set_omega(rsvd_plan_t plan, const float* Omega);
+
+/* Wait for the plan's stream and return the first device-detected error
+ * since the previous rsvd_sync (RSVD_OK if none); clears it. */
+RSVD_API rsvd_status_t rsvd_sync(rsvd_plan_t plan);
+
+/* Static English description of a status code. */
+RSVD_API const char* rsvd_status_string(rsvd_status_t status);
+
+/* ---- step-level entry points (each runs one step of the method with the
+ * ---- plan's kernels; the tests check each against the oracle) ---------- */
+
+/* Algorithm 4.1 step 1: rows x cols standard Gaussian matrix into `out`
+ * (device float32, leading dimension ld >= cols).  Element (i, j): with
+ * g = j / 4, t = j % 4, the Philox4x32-10 block for counter (g, i, stream_id, 0)
+ * and key (seed mod 2^32, seed / 2^32) gives words x0..x3; u_a =
+ * (2 (x_a >> 9) + 1) 2^-24; z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1) and
+ * z2, z3 likewise from (u2, u3); the element is z_t. */
+RSVD_API rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows,
+                                 int64_t cols, float* out, int64_t ld, void* stream);
+
+/* One pass over A with the plan's precision: transpose = 0 gives Y = A X
+ * (X: n x l, Y: m x l); transpose = 1 gives Y = A^T X (X: m x l, Y: n x l).
+ * X and Y are device float32 with leading dimension l. */
+RSVD_API rsvd_status_t rsvd_sketch(rsvd_plan_t plan, const void* A, int32_t transpose,
+                          const float* X, float* Y);
+
+/* Orthonormalise the columns of Y (device float32, rows x l, leading
+ * dimension l, rows <= max(m, n)) in place with the plan's Cholesky-QR
+ * rounds; R (device float32, l x l, may be NULL) receives the upper
+ * triangular factor with Y_in = Y_out R. */
+RSVD_API rsvd_status_t rsvd_orthonormalize(rsvd_plan_t plan, int64_t rows, float* Y, float* R);
+
+/* SVD of a small l x l matrix X (device float32, leading dimension l):
+ * X = Ut diag(S) W^T with Ut, W (device, l x l, leading dimension l) and S
+ * (device, l) descending, by one-sided Jacobi rotations. */
+RSVD_API rsvd_status_t rsvd_small_svd(rsvd_plan_t plan, const float* X, float* Ut, float* S,
+                             float* W);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_0909_4061_RSVD_H */

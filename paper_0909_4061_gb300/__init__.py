@@ -1,0 +1,293 @@
+"""Python binding of the GB300 randomized range finder / randomized SVD library.
+
+Argument marshalling only: every function below forwards to the C ABI of
+include/rsvd.h (libpaper_rsvd.so, built in-tree by ``paper_0909_4061_gb300.build``)
+and every step of the computation runs in the library's CUDA kernels.  The
+functions carry the C names; ``Plan`` and ``svd`` are thin conveniences that
+take torch CUDA tensors (device memory and the current stream come from torch).
+
+There is no CPU fallback: if the shared library is missing or cannot be
+loaded, every call raises ``RsvdUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpaper_rsvd.so")
+
+RSVD_OK = 0
+RSVD_ERR_INVALID_ARG = 1
+RSVD_ERR_ALLOC = 2
+RSVD_ERR_CUDA = 3
+RSVD_ERR_NUMERICAL = 4
+RSVD_ERR_NONFINITE = 5
+RSVD_ERR_TIMEOUT = 6
+RSVD_ERR_UNSUPPORTED = 7
+
+RSVD_F32, RSVD_BF16 = 0, 1
+RSVD_GAUSSIAN, RSVD_SRFT = 0, 1
+RSVD_PLAIN_FP32, RSVD_BF16_TC = 0, 1
+
+# every symbol include/rsvd.h declares (checked by the CPU tests)
+EXPORTS = (
+    "rsvd_options_default", "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_workspace_bytes",
+    "rsvd_range_finder", "rsvd_svd", "rsvd_svd_host", "rsvd_svd_backward", "rsvd_get_omega",
+    "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
+    "rsvd_orthonormalize", "rsvd_small_svd",
+)
+
+
+class RsvdUnavailable(ImportError):
+    pass
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("dtype_A", ctypes.c_int32),
+        ("test_matrix", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("single_pass", ctypes.c_int32),
+        ("recompute", ctypes.c_int32),
+        ("orth_rounds", ctypes.c_int32),
+        ("lda", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+_c = ctypes
+_P = ctypes.c_void_p
+_SIGS = {
+    "rsvd_options_default": (None, [_P]),
+    "rsvd_plan_create": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int32, _c.c_int32, _c.c_int32,
+                                    _c.c_uint64, _P, _P]),
+    "rsvd_plan_destroy": (_c.c_int, [_P]),
+    "rsvd_workspace_bytes": (_c.c_int, [_P, _P]),
+    "rsvd_range_finder": (_c.c_int, [_P, _P, _P, _c.c_int64]),
+    "rsvd_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "rsvd_svd_host": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "rsvd_svd_backward": (_c.c_int, [_P, _P, _P, _P, _P, _c.c_int32, _P]),
+    "rsvd_get_omega": (_c.c_int, [_P, _P]),
+    "rsvd_set_omega": (_c.c_int, [_P, _P]),
+    "rsvd_sync": (_c.c_int, [_P]),
+    "rsvd_status_string": (_c.c_char_p, [_c.c_int]),
+    "rsvd_draw_gaussian": (_c.c_int, [_c.c_uint64, _c.c_uint32, _c.c_int64, _c.c_int64, _P,
+                                      _c.c_int64, _P]),
+    "rsvd_sketch": (_c.c_int, [_P, _P, _c.c_int32, _P, _P]),
+    "rsvd_orthonormalize": (_c.c_int, [_P, _c.c_int64, _P, _P]),
+    "rsvd_small_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
+}
+
+
+def lib():
+    """The loaded shared library (raises RsvdUnavailable when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RsvdUnavailable(
+                f"{LIB_PATH} is missing: build it with `python -m paper_0909_4061_gb300.build` "
+                "(or __graft_entry__.build()); there is no CPU fallback")
+        try:
+            handle = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise RsvdUnavailable(f"cannot load {LIB_PATH}: {e}") from e
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().rsvd_status_string(int(status)).decode()
+    except RsvdUnavailable:
+        return f"status {status}"
+
+
+def _check(status: int, where: str):
+    if status != RSVD_OK:
+        raise RsvdError(status, where)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C ABI, one wrapper per entry point -----------------------------------------
+
+
+def rsvd_options_default() -> Options:
+    o = Options()
+    lib().rsvd_options_default(ctypes.byref(o))
+    return o
+
+
+def rsvd_plan_create(m, n, k, p, q, seed, opt: Options | None = None, stream=None):
+    h = ctypes.c_void_p()
+    st = lib().rsvd_plan_create(ctypes.byref(h), int(m), int(n), int(k), int(p), int(q),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                ctypes.byref(opt) if opt is not None else None, _stream(stream))
+    _check(st, "rsvd_plan_create")
+    return h
+
+
+def rsvd_plan_destroy(plan):
+    _check(lib().rsvd_plan_destroy(plan), "rsvd_plan_destroy")
+
+
+def rsvd_workspace_bytes(plan) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().rsvd_workspace_bytes(plan, ctypes.byref(v)), "rsvd_workspace_bytes")
+    return v.value
+
+
+def rsvd_range_finder(plan, A, Q, ldq):
+    _check(lib().rsvd_range_finder(plan, _ptr(A), _ptr(Q), int(ldq)), "rsvd_range_finder")
+
+
+def rsvd_svd(plan, A, U, S, V):
+    _check(lib().rsvd_svd(plan, _ptr(A), _ptr(U), _ptr(S), _ptr(V)), "rsvd_svd")
+
+
+def rsvd_svd_host(plan, A_host, U_host, S_host, V_host):
+    _check(lib().rsvd_svd_host(plan, _ptr(A_host), _ptr(U_host), _ptr(S_host), _ptr(V_host)),
+           "rsvd_svd_host")
+
+
+def rsvd_svd_backward(plan, A, gU, gS, gV, add_recon, gA):
+    _check(lib().rsvd_svd_backward(plan, _ptr(A), _ptr(gU), _ptr(gS), _ptr(gV), int(add_recon),
+                                   _ptr(gA)), "rsvd_svd_backward")
+
+
+def rsvd_get_omega(plan, Omega):
+    _check(lib().rsvd_get_omega(plan, _ptr(Omega)), "rsvd_get_omega")
+
+
+def rsvd_set_omega(plan, Omega):
+    _check(lib().rsvd_set_omega(plan, _ptr(Omega)), "rsvd_set_omega")
+
+
+def rsvd_sync(plan) -> int:
+    """Returns the status code (does not raise) so callers can test device-side errors."""
+    return lib().rsvd_sync(plan)
+
+
+def rsvd_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def rsvd_draw_gaussian(seed, stream_id, rows, cols, out, ld, stream=None):
+    _check(lib().rsvd_draw_gaussian(int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id), int(rows),
+                                    int(cols), _ptr(out), int(ld), _stream(stream)),
+           "rsvd_draw_gaussian")
+
+
+def rsvd_sketch(plan, A, transpose, X, Y):
+    _check(lib().rsvd_sketch(plan, _ptr(A), int(transpose), _ptr(X), _ptr(Y)), "rsvd_sketch")
+
+
+def rsvd_orthonormalize(plan, rows, Y, R=None):
+    _check(lib().rsvd_orthonormalize(plan, int(rows), _ptr(Y), _ptr(R)), "rsvd_orthonormalize")
+
+
+def rsvd_small_svd(plan, X, Ut, S, W):
+    _check(lib().rsvd_small_svd(plan, _ptr(X), _ptr(Ut), _ptr(S), _ptr(W)), "rsvd_small_svd")
+
+
+# ---- torch conveniences -------------------------------------------------------------
+
+
+class Plan:
+    """Owns one rsvd plan; tensors are torch CUDA tensors (row-major, contiguous)."""
+
+    def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
+                 lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0):
+        o = rsvd_options_default()
+        o.precision = precision
+        o.dtype_A = RSVD_BF16 if precision == RSVD_BF16_TC else RSVD_F32
+        o.orth_rounds = orth_rounds
+        o.lda = lda
+        o.test_matrix = test_matrix
+        o.single_pass = single_pass
+        self.m, self.n, self.k, self.p, self.q = int(m), int(n), int(k), int(p), int(q)
+        self.l = self.k + self.p
+        self.options = o
+        self.handle = rsvd_plan_create(m, n, k, p, q, seed, o, stream)
+
+    def close(self):
+        if self.handle is not None:
+            rsvd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def svd(self, A, U=None, S=None, V=None, sync=True):
+        import torch
+
+        dev = A.device
+        U = U if U is not None else torch.empty(self.m, self.k, device=dev, dtype=torch.float32)
+        S = S if S is not None else torch.empty(self.k, device=dev, dtype=torch.float32)
+        V = V if V is not None else torch.empty(self.n, self.k, device=dev, dtype=torch.float32)
+        rsvd_svd(self.handle, A, U, S, V)
+        if sync:
+            _check(rsvd_sync(self.handle), "rsvd_svd (device)")
+        return U, S, V
+
+    def range_finder(self, A, Q=None, sync=True):
+        import torch
+
+        Q = Q if Q is not None else torch.empty(self.m, self.l, device=A.device, dtype=torch.float32)
+        rsvd_range_finder(self.handle, A, Q, Q.stride(0))
+        if sync:
+            _check(rsvd_sync(self.handle), "rsvd_range_finder (device)")
+        return Q
+
+    def sync(self):
+        _check(rsvd_sync(self.handle), "rsvd_sync")
+
+
+def svd(A, k, p=10, q=1, seed=0, precision=None, orth_rounds=3):
+    """Rank-k randomized SVD of a CUDA tensor A (float32 -> plain FP32 path,
+    bfloat16 -> tensor-core path).  Returns float32 (U, S, V)."""
+    import torch
+
+    if precision is None:
+        precision = RSVD_BF16_TC if A.dtype == torch.bfloat16 else RSVD_PLAIN_FP32
+    m, n = A.shape
+    with Plan(m, n, k, p, q, seed, precision, orth_rounds, lda=A.stride(0)) as pl:
+        return pl.svd(A)

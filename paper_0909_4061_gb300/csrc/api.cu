@@ -1,0 +1,458 @@
+// C ABI of the library: plan creation, argument checks, workspace, and the
+// sequence of kernel launches for each entry point of include/rsvd.h.
+//
+// rsvd_svd (Algorithm 4.4 as Stage A, Algorithm 5.1 + Remark 5.1 as Stage B):
+//   Omega            draw (Philox + Box-Muller) or the caller's matrix
+//   Y0 = A Omega     pass over A, split-K partials
+//   Q0               Cholesky-QR rounds (the first round sums the partials)
+//   for j = 1..q:    Yt_j = A^T Q_{j-1} -> Qt_j ;  Y_j = A Qt_j -> Q_j
+//   B^T = A^T Q_q    pass over A, then Cholesky-QR rounds B^T = Q_B R_B
+//   R_B^T = Ut S W^T one-sided Jacobi in one CTA
+//   U = Q_q Ut_k, V = Q_B W_k, S = S_k
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "sketch_tc.cuh"
+
+using namespace rsvd;
+
+struct rsvd_plan_s {
+  int64_t m = 0, n = 0, lda = 0, maxmn = 0;
+  int k = 0, p = 0, q = 0, l = 0, lp = 0;
+  uint64_t seed = 0;
+  rsvd_options_t opt{};
+  cudaStream_t st = nullptr;
+  int device = 0, num_sms = kNumSMs;
+  int splits_n = 1, splits_t = 1;  // split-K of the passes Y = A X and Y = A^T X (FP32 path)
+  int nblk = 1;
+  bool omega_user = false;
+  // workspace (device)
+  float* omega = nullptr;    // n x lp
+  float* qbuf = nullptr;     // m x lp   basis Q_j
+  float* qtbuf = nullptr;    // n x lp   basis Qt_j, later Q_B
+  float* tmp1 = nullptr;     // maxmn x lp
+  float* tmp2 = nullptr;     // maxmn x lp
+  float* partial = nullptr;  // split-K partial results
+  int64_t partial_elems = 0;
+  float* gpart = nullptr;    // nblk x lp x lp
+  float* small = nullptr;    // 8 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch
+  float* sig = nullptr;      // lp
+  uint32_t* status = nullptr;
+  __nv_bfloat16* xbf = nullptr;  // 2 lp x maxmn: transposed bfloat16 operand of the tensor-core passes
+  TcPlan tc{};
+  // rsvd_svd_host staging
+  void* a_dev = nullptr;
+  float *u_dev = nullptr, *s_dev = nullptr, *v_dev = nullptr;
+  size_t ws_bytes = 0;
+
+  float* g() { return small; }
+  float* lbuf() { return small + 1 * (size_t)lp * lp; }
+  float* rtmp() { return small + 2 * (size_t)lp * lp; }
+  float* rinv() { return small + 3 * (size_t)lp * lp; }
+  float* racc() { return small + 4 * (size_t)lp * lp; }
+  float* ut() { return small + 5 * (size_t)lp * lp; }
+  float* w() { return small + 6 * (size_t)lp * lp; }
+  float* sq() { return small + 7 * (size_t)lp * lp; }
+};
+
+namespace {
+
+#define TRY(expr)                                 \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return RSVD_ERR_CUDA;  \
+  } while (0)
+
+#define TRYS(expr)                          \
+  do {                                      \
+    rsvd_status_t _s = (expr);              \
+    if (_s != RSVD_OK) return _s;           \
+  } while (0)
+
+template <class T>
+rsvd_status_t dalloc(rsvd_plan_t P, T** ptr, size_t elems) {
+  *ptr = nullptr;
+  if (elems == 0) elems = 1;
+  const size_t bytes = elems * sizeof(T);
+  if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RSVD_ERR_ALLOC;
+  }
+  P->ws_bytes += bytes;
+  return RSVD_OK;
+}
+
+void free_plan(rsvd_plan_t P) {
+  if (!P) return;
+  void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
+                  P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
+                  P->v_dev};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  tc_plan_destroy(&P->tc);
+  delete P;
+}
+
+int choose_splits(int64_t M, int64_t N, int64_t K, int sms) {
+  const int64_t tiles = cdiv(M, 128) * cdiv(N, 64);
+  const int64_t target = 4LL * sms;
+  int64_t s = cdiv(target, tiles);
+  const int64_t kmax = std::max<int64_t>(1, cdiv(K, 16) / 8);
+  s = std::min<int64_t>(s, kmax);
+  s = std::min<int64_t>(s, 32);
+  return (int)std::max<int64_t>(s, 1);
+}
+
+rsvd_status_t take_status(rsvd_plan_t P) {
+  uint32_t st = 0;
+  TRY(cudaMemcpyAsync(&st, P->status, sizeof(st), cudaMemcpyDeviceToHost, P->st));
+  TRY(cudaStreamSynchronize(P->st));
+  if (st) TRY(cudaMemsetAsync(P->status, 0, sizeof(uint32_t), P->st));
+  if (st & ST_NONFINITE) return RSVD_ERR_NONFINITE;
+  if (st & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
+  if (st & ST_NUMERICAL) return RSVD_ERR_NUMERICAL;
+  return RSVD_OK;
+}
+
+// ---- the steps --------------------------------------------------------------
+
+// Test matrix (Algorithm 4.1 step 1) into P->omega (n x lp, float32) and, for
+// the tensor-core path, its bfloat16 transpose into P->xbf.
+rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
+  if (!P->omega_user) {
+    TRY(launch_draw_gaussian(P->seed, 0u, P->n, P->l, P->lp, P->omega, P->lp,
+                             want_bf16 ? P->xbf : nullptr, P->n, P->st));
+  } else if (want_bf16) {
+    TRY(launch_to_bf16_t(P->omega, P->n, P->lp, P->xbf, P->n, 0, P->st));
+  }
+  return RSVD_OK;
+}
+
+// One pass over A (Algorithm 4.4 steps 2, 4, 5; Algorithm 5.1 step 1).
+// FP32 path: X is float32 (K x lp); tensor-core path: the operand is P->xbf.
+// The result is left as `*splits` partial slabs in P->partial (stride rows x lp).
+rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X, bool split_x,
+                        int* splits, int64_t* stride) {
+  const int64_t M = trans ? P->n : P->m;
+  const int64_t K = trans ? P->m : P->n;
+  *stride = M * P->lp;
+  if (P->opt.precision == RSVD_PLAIN_FP32) {
+    const int s = trans ? P->splits_t : P->splits_n;
+    TRY(launch_gemm_f32(trans, M, P->lp, K, static_cast<const float*>(A), P->lda, X, P->lp,
+                        P->partial, P->lp, s, *stride, P->st));
+    *splits = s;
+  } else {
+    int s = 1;
+    if (tc_pass(&P->tc, trans, split_x ? 1 : 0, P->partial, &s, P->st) != 0) return RSVD_ERR_CUDA;
+    *splits = s;
+  }
+  return RSVD_OK;
+}
+
+// Cholesky-QR rounds on the (summed) partial slabs; the basis ends in `dst`
+// (rows x lp).  With `racc`, the triangular factors are multiplied into it.
+rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t stride, int64_t rows,
+                        float* dst, float* racc) {
+  const int rounds = P->opt.orth_rounds;
+  const int lp = P->lp;
+  const int nblk = gram_blocks(rows);
+  const float* cur = src;
+  int cur_splits = splits;
+  for (int r = 0; r < rounds; ++r) {
+    float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
+    TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
+    if (cur_splits > 1) cur = P->tmp1;
+    TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
+    const int shifted = (rounds >= 3 && r == 0) ? 1 : 0;
+    TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+                        r == 0 ? 1 : 0, P->status, P->st));
+    float* next = (r == rounds - 1) ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
+    TRY(launch_gemm_f32(0, rows, lp, lp, cur, lp, P->rinv(), lp, next, lp, 1, 0, P->st));
+    cur = next;
+    cur_splits = 1;
+  }
+  return RSVD_OK;
+}
+
+rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  if (tc) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  TRYS(step_draw(P, tc));
+  int s;
+  int64_t stride;
+  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
+  for (int j = 1; j <= P->q; ++j) {
+    if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, P->m, 0, P->st));
+    TRYS(step_pass(P, A, 1, P->qbuf, false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr));
+    if (tc) TRY(launch_to_bf16_t(P->qtbuf, P->n, P->lp, P->xbf, P->n, 0, P->st));
+    TRYS(step_pass(P, A, 0, P->qtbuf, false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
+  }
+  return RSVD_OK;
+}
+
+rsvd_status_t stage_b(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  int s;
+  int64_t stride;
+  if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, P->m, 1, P->st));
+  TRYS(step_pass(P, A, 1, P->qbuf, true, &s, &stride));      // B^T = A^T Q
+  TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));  // B^T = Q_B R_B
+  TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
+                        P->st));
+  TRY(launch_gemm_f32(0, P->m, P->k, P->lp, P->qbuf, P->lp, P->ut(), P->lp, U, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->n, P->k, P->lp, P->qtbuf, P->lp, P->w(), P->lp, V, P->k, 1, 0, P->st));
+  TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t check_plan(rsvd_plan_t P) {
+  if (!P) return RSVD_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RSVD_ERR_CUDA;
+  if (dev != P->device) return RSVD_ERR_INVALID_ARG;
+  return RSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rsvd_options_default(rsvd_options_t* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->dtype_A = RSVD_F32;
+  opt->test_matrix = RSVD_GAUSSIAN;
+  opt->precision = RSVD_PLAIN_FP32;
+  opt->single_pass = 0;
+  opt->recompute = 0;
+  opt->orth_rounds = 3;
+  opt->lda = 0;
+}
+
+const char* rsvd_status_string(rsvd_status_t s) {
+  switch (s) {
+    case RSVD_OK: return "success";
+    case RSVD_ERR_INVALID_ARG: return "invalid argument";
+    case RSVD_ERR_ALLOC: return "allocation failed";
+    case RSVD_ERR_CUDA: return "CUDA runtime error";
+    case RSVD_ERR_NUMERICAL: return "numerical breakdown";
+    case RSVD_ERR_NONFINITE: return "non-finite value in input or intermediate";
+    case RSVD_ERR_TIMEOUT: return "bounded device wait expired";
+    case RSVD_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t p,
+                               int32_t q, uint64_t seed, const rsvd_options_t* opt,
+                               void* stream) {
+  if (!plan) return RSVD_ERR_INVALID_ARG;
+  *plan = nullptr;
+  rsvd_options_t o;
+  if (opt) o = *opt; else rsvd_options_default(&o);
+  if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0) return RSVD_ERR_INVALID_ARG;
+  const int64_t l = (int64_t)k + p;
+  if (l > std::min(m, n) || l > kMaxL) return RSVD_ERR_INVALID_ARG;
+  if (o.lda == 0) o.lda = n;
+  if (o.lda < n) return RSVD_ERR_INVALID_ARG;
+  if (o.orth_rounds != 2 && o.orth_rounds != 3) return RSVD_ERR_INVALID_ARG;
+  if (o.dtype_A != RSVD_F32 && o.dtype_A != RSVD_BF16) return RSVD_ERR_INVALID_ARG;
+  if (o.precision == RSVD_PLAIN_FP32 && o.dtype_A != RSVD_F32) return RSVD_ERR_INVALID_ARG;
+  if (o.precision == RSVD_BF16_TC && o.dtype_A != RSVD_BF16) return RSVD_ERR_INVALID_ARG;
+  if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
+  if (o.test_matrix != RSVD_GAUSSIAN || o.single_pass) return RSVD_ERR_UNSUPPORTED;
+  if (l > 160) return RSVD_ERR_UNSUPPORTED;  // one-CTA Jacobi limit
+  if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
+
+  rsvd_plan_t P = new (std::nothrow) rsvd_plan_s();
+  if (!P) return RSVD_ERR_ALLOC;
+  P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l;
+  P->lp = (int)round_up(l, 16);
+  P->seed = seed; P->opt = o; P->lda = o.lda;
+  P->maxmn = std::max(m, n);
+  P->st = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return RSVD_ERR_CUDA;
+  }
+  const int lp = P->lp;
+  P->splits_n = choose_splits(m, lp, n, P->num_sms);
+  P->splits_t = choose_splits(n, lp, m, P->num_sms);
+  int64_t part = std::max((int64_t)P->splits_n * m, (int64_t)P->splits_t * n) * lp;
+  if (o.precision == RSVD_BF16_TC) part = std::max(part, tc_partial_elems(m, n, lp, P->num_sms));
+  P->partial_elems = part;
+  rsvd_status_t s = RSVD_OK;
+  const int nblk = std::max(gram_blocks(m), gram_blocks(n));
+  if ((s = dalloc(P, &P->omega, (size_t)n * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->qbuf, (size_t)m * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->qtbuf, (size_t)n * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->tmp1, (size_t)P->maxmn * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->tmp2, (size_t)P->maxmn * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->partial, (size_t)part)) != RSVD_OK ||
+      (s = dalloc(P, &P->gpart, (size_t)nblk * lp * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->small, (size_t)8 * lp * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->status, 4))) {
+    free_plan(P);
+    return s;
+  }
+  if (o.precision == RSVD_BF16_TC) {
+    if ((s = dalloc(P, &P->xbf, (size_t)2 * lp * P->maxmn)) != RSVD_OK) {
+      free_plan(P);
+      return s;
+    }
+    if (tc_plan_init(&P->tc, m, n, o.lda, lp, P->xbf, P->num_sms) != 0) {
+      free_plan(P);
+      return RSVD_ERR_CUDA;
+    }
+  }
+  if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
+      cudaMemsetAsync(P->small, 0, sizeof(float) * 8 * lp * lp, P->st) != cudaSuccess) {
+    free_plan(P);
+    return RSVD_ERR_CUDA;
+  }
+  *plan = P;
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_plan_destroy(rsvd_plan_t P) {
+  if (!P) return RSVD_OK;
+  cudaStreamSynchronize(P->st);
+  free_plan(P);
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_workspace_bytes(rsvd_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return RSVD_ERR_INVALID_ARG;
+  *bytes = P->ws_bytes;
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t ldq) {
+  TRYS(check_plan(P));
+  if (!A || !Q || ldq < P->l) return RSVD_ERR_INVALID_ARG;
+  TRYS(stage_a(P, A));
+  TRY(launch_gather(P->qbuf, 1, 0, P->lp, Q, ldq, P->m, P->l, P->l, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_svd(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  TRYS(check_plan(P));
+  if (!A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
+  TRYS(stage_a(P, A));
+  TRYS(stage_b(P, A, U, S, V));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, float* S_host,
+                            float* V_host) {
+  TRYS(check_plan(P));
+  if (!A_host || !U_host || !S_host || !V_host) return RSVD_ERR_INVALID_ARG;
+  const size_t esz = P->opt.dtype_A == RSVD_BF16 ? 2 : 4;
+  const size_t abytes = ((size_t)(P->m - 1) * P->lda + P->n) * esz;
+  if (!P->a_dev) {
+    TRYS(dalloc(P, reinterpret_cast<char**>(&P->a_dev), abytes));
+    TRYS(dalloc(P, &P->u_dev, (size_t)P->m * P->k));
+    TRYS(dalloc(P, &P->s_dev, (size_t)P->k));
+    TRYS(dalloc(P, &P->v_dev, (size_t)P->n * P->k));
+  }
+  TRY(cudaMemcpyAsync(P->a_dev, A_host, abytes, cudaMemcpyHostToDevice, P->st));
+  TRYS(rsvd_svd(P, P->a_dev, P->u_dev, P->s_dev, P->v_dev));
+  TRY(cudaMemcpyAsync(U_host, P->u_dev, sizeof(float) * P->m * P->k, cudaMemcpyDeviceToHost, P->st));
+  TRY(cudaMemcpyAsync(S_host, P->s_dev, sizeof(float) * P->k, cudaMemcpyDeviceToHost, P->st));
+  TRY(cudaMemcpyAsync(V_host, P->v_dev, sizeof(float) * P->n * P->k, cudaMemcpyDeviceToHost, P->st));
+  return take_status(P);
+}
+
+rsvd_status_t rsvd_svd_backward(rsvd_plan_t P, const void* A, const float* gU, const float* gS,
+                                const float* gV, int32_t add_recon, float* gA) {
+  (void)A; (void)gU; (void)gS; (void)gV; (void)add_recon; (void)gA;
+  TRYS(check_plan(P));
+  return RSVD_ERR_UNSUPPORTED;
+}
+
+rsvd_status_t rsvd_get_omega(rsvd_plan_t P, float* Omega) {
+  TRYS(check_plan(P));
+  if (!Omega) return RSVD_ERR_INVALID_ARG;
+  TRYS(step_draw(P, false));
+  TRY(launch_gather(P->omega, 1, 0, P->lp, Omega, P->l, P->n, P->l, P->l, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_set_omega(rsvd_plan_t P, const float* Omega) {
+  TRYS(check_plan(P));
+  if (!Omega) {
+    P->omega_user = false;
+    return RSVD_OK;
+  }
+  TRY(launch_gather(Omega, 1, 0, P->l, P->omega, P->lp, P->n, P->l, P->lp, P->st));
+  P->omega_user = true;
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_sync(rsvd_plan_t P) {
+  TRYS(check_plan(P));
+  return take_status(P);
+}
+
+rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                                 float* out, int64_t ld, void* stream) {
+  if (rows < 0 || cols < 0 || cols > (1 << 30) || (rows > 0 && cols > 0 && !out) || ld < cols)
+    return RSVD_ERR_INVALID_ARG;
+  TRY(launch_draw_gaussian(seed, stream_id, rows, (int)cols, (int)cols, out, ld, nullptr, 0,
+                           static_cast<cudaStream_t>(stream)));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const float* X,
+                          float* Y) {
+  TRYS(check_plan(P));
+  if (!A || !X || !Y) return RSVD_ERR_INVALID_ARG;
+  const int64_t kx = transpose ? P->m : P->n;
+  const int64_t my = transpose ? P->n : P->m;
+  if (P->opt.precision == RSVD_BF16_TC) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  float* xin = transpose ? P->qbuf : P->omega;  // padded K x lp copy of X
+  TRY(launch_gather(X, 1, 0, P->l, xin, P->lp, kx, P->l, P->lp, P->st));
+  if (P->opt.precision == RSVD_BF16_TC) TRY(launch_to_bf16_t(xin, kx, P->lp, P->xbf, kx, 0, P->st));
+  int s;
+  int64_t stride;
+  TRYS(step_pass(P, A, transpose, xin, false, &s, &stride));
+  TRY(launch_gather(P->partial, s, stride, P->lp, Y, P->l, my, P->l, P->l, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_orthonormalize(rsvd_plan_t P, int64_t rows, float* Y, float* R) {
+  TRYS(check_plan(P));
+  if (!Y || rows < P->l || rows > P->maxmn) return RSVD_ERR_INVALID_ARG;
+  // the rounds ping-pong through tmp1/tmp2, so the result goes to a basis buffer of `rows` rows
+  float* dst = rows <= P->m ? P->qbuf : P->qtbuf;
+  TRY(launch_gather(Y, 1, 0, P->l, P->partial, P->lp, rows, P->l, P->lp, P->st));
+  TRYS(step_orth(P, P->partial, 1, rows * P->lp, rows, dst, P->racc()));
+  TRY(launch_gather(dst, 1, 0, P->lp, Y, P->l, rows, P->l, P->l, P->st));
+  if (R) TRY(launch_gather(P->racc(), 1, 0, P->lp, R, P->l, P->l, P->l, P->l, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_small_svd(rsvd_plan_t P, const float* X, float* Ut, float* S, float* W) {
+  TRYS(check_plan(P));
+  if (!X || !Ut || !S || !W) return RSVD_ERR_INVALID_ARG;
+  TRY(launch_gather(X, 1, 0, P->l, P->sq(), P->lp, P->l, P->l, P->lp, P->st));
+  TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->status, P->st));
+  TRY(launch_gather(P->ut(), 1, 0, P->lp, Ut, P->l, P->l, P->l, P->l, P->st));
+  TRY(launch_gather(P->w(), 1, 0, P->lp, W, P->l, P->l, P->l, P->l, P->st));
+  TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->l, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+}  // extern "C"

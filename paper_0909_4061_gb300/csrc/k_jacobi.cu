@@ -1,0 +1,144 @@
+// SVD of the small l x l matrix of Stage B (Algorithm 5.1 step 2), taken as
+// in Section 3.3.3: B^T = Q_B R_B, then R_B^T = Ut diag(s) W^T, so that
+// B = Ut diag(s) (Q_B W)^T.
+//
+// One-sided (Hestenes) Jacobi in one CTA: the columns of X live in shared
+// memory; each sweep visits every column pair once in the round-robin
+// ("circle") order, l/2 disjoint pairs per round, one warp per pair.  A pair
+// (p, q) is rotated when |x_p . x_q| > tol ||x_p|| ||x_q||, with the angle
+// from zeta = (||x_q||^2 - ||x_p||^2) / (2 x_p . x_q), t = sign(zeta) /
+// (|zeta| + sqrt(1 + zeta^2)).  The same rotations accumulate in J, so that
+// X J = U diag(s) and X = U diag(s) J^T.  Sweeps stop when no pair rotates.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+namespace {
+
+constexpr int kMaxJacobiL = 160;  // X and J both fit in 227 KB of shared memory
+constexpr int kMaxSweeps = 40;
+
+__device__ __forceinline__ int rr_player(int pos, int round, int n) {
+  return pos == 0 ? 0 : ((pos - 1 + round) % (n - 1)) + 1;
+}
+
+__global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ x, int64_t ldx,
+                                                      int transposed, int l, int lp,
+                                                      float* __restrict__ ut, float* __restrict__ s,
+                                                      float* __restrict__ w, uint32_t* status,
+                                                      float tol) {
+  extern __shared__ __align__(16) float sm[];
+  const int le = l + (l & 1);
+  float* Xc = sm;                   // [l][l]: Xc[c][e] = X(e, c)
+  float* Jc = sm + l * l;           // [l][l]
+  float* sig = Jc + l * l;          // [le]
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+
+  for (int e = tid; e < l * l; e += nt) {
+    const int c = e / l, r = e % l;
+    Xc[e] = transposed ? x[(int64_t)c * ldx + r] : x[(int64_t)r * ldx + c];
+    Jc[e] = (c == r) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < le - 1; ++round) {
+      for (int slot = warp; slot < le / 2; slot += nw) {
+        const int p = rr_player(slot, round, le);
+        const int q = rr_player(le - 1 - slot, round, le);
+        if (p >= l || q >= l) continue;
+        float* xp = Xc + p * l;
+        float* xq = Xc + q * l;
+        float a = 0.f, b = 0.f, g = 0.f;
+        for (int e = lane; e < l; e += 32) {
+          const float u = xp[e], v = xq[e];
+          a = fmaf(u, u, a);
+          b = fmaf(v, v, b);
+          g = fmaf(u, v, g);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g == 0.0f || !(fabsf(g) > tol * sqrtf(a) * sqrtf(b))) continue;
+        const float zeta = (b - a) / (2.0f * g);
+        const float az = fabsf(zeta);
+        float t = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(az, az, 1.0f)));
+        t = copysignf(t, zeta);
+        if (zeta == 0.0f) t = 1.0f;
+        const float c = rsqrtf(fmaf(t, t, 1.0f));
+        const float sn = c * t;
+        if (lane == 0) s_rot = 1;
+        float* jp = Jc + p * l;
+        float* jq = Jc + q * l;
+        for (int e = lane; e < l; e += 32) {
+          const float u = xp[e], v = xq[e];
+          xp[e] = c * u - sn * v;
+          xq[e] = fmaf(sn, u, c * v);
+          const float uj = jp[e], vj = jq[e];
+          jp[e] = c * uj - sn * vj;
+          jq[e] = fmaf(sn, uj, c * vj);
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (sweep == kMaxSweeps && tid == 0) set_status(status, ST_JACOBI_NOCONV);
+
+  // singular values = column norms
+  for (int c = warp; c < l; c += nw) {
+    float a = 0.f;
+    for (int e = lane; e < l; e += 32) a = fmaf(Xc[c * l + e], Xc[c * l + e], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[c] = sqrtf(a);
+  }
+  __syncthreads();
+  // zero the padded frame, then scatter each column to its descending rank
+  for (int e = tid; e < lp * lp; e += nt) {
+    const int r = e / lp, c = e % lp;
+    if (r >= l || c >= l) { ut[e] = 0.0f; w[e] = 0.0f; }
+  }
+  for (int c = warp; c < l; c += nw) {
+    const float sc = sig[c];
+    int rank = 0;
+    for (int c2 = lane; c2 < l; c2 += 32) {
+      const float s2 = sig[c2];
+      rank += (s2 > sc || (s2 == sc && c2 < c)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const float inv = sc > 0.0f ? 1.0f / sc : 0.0f;
+    for (int e = lane; e < l; e += 32) {
+      ut[(int64_t)e * lp + rank] = Xc[c * l + e] * inv;
+      w[(int64_t)e * lp + rank] = Jc[c * l + e];
+    }
+    if (lane == 0) s[rank] = sc;
+  }
+}
+
+}  // namespace
+
+size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + l + 2) * sizeof(float); }
+
+cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp, float* ut,
+                              float* s, float* w, uint32_t* status, cudaStream_t st) {
+  if (l > kMaxJacobiL) return cudaErrorInvalidValue;
+  const size_t smem = jacobi_smem_bytes(l);
+  cudaError_t e =
+      cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const float tol = 2.0f * sqrtf((float)l) * kEpsF32;
+  jacobi_kernel<<<1, 1024, smem, st>>>(x, ldx, transposed, l, lp, ut, s, w, status, tol);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

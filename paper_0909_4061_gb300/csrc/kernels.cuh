@@ -1,0 +1,61 @@
+// Launchers of the library's kernels (host side).  Every step of the path
+// runs in one of these kernels; the C ABI in api.cu only sequences them.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsvd {
+
+// Algorithm 4.1 step 1: rows x cols Gaussian, columns [cols, cols_pad) zero.
+// out (float32, ld) and/or out_t (bfloat16 transposed, cols_pad x rows, ld_t) may be null.
+cudaError_t launch_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
+                                 int cols_pad, float* out, int64_t ld, __nv_bfloat16* out_t,
+                                 int64_t ld_t, cudaStream_t st);
+
+// C[s] = op(A)[:, Ks] * X[Ks, :] over split s of the K range, float32 FMA.
+// trans = 0: op(A) = A (M x K, lda); trans = 1: op(A) = A^T with A stored K x M (lda).
+// X is K x N (ldx), C is M x N (ldc); split s writes C + s * split_stride.
+cudaError_t launch_gemm_f32(int trans, int64_t M, int64_t N, int64_t K, const float* A,
+                            int64_t lda, const float* X, int64_t ldx, float* C, int64_t ldc,
+                            int splits, int64_t split_stride, cudaStream_t st);
+
+// Partial Gram matrices of the rows of Y (rows x lp, ld lp) over nblk row blocks;
+// when splits > 1, Y is first formed as the sum of `splits` partial slabs
+// (src + s * split_stride) and written to y_out.
+cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stride, float* y_out,
+                                int64_t rows, int lp, float* gpart, int nblk, cudaStream_t st);
+int gram_blocks(int64_t rows);
+
+// G = sum of the nblk partial Grams (lp x lp).
+cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st);
+
+// Cholesky G (+ shift) = R^T R, R^-1 into rinv (lp x lp upper, zero padded), R into r_out,
+// and racc <- R * racc (or racc <- R when racc_init != 0) when racc is non-null.
+cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,
+                            float* rinv, float* racc, int racc_init, uint32_t* status,
+                            cudaStream_t st);
+
+// float32 rows x lp (ld lp) -> bfloat16 transposed (lp x rows, ld_t); with `split`,
+// also writes the residual x - bf16(x) as rows [lp, 2 lp) of the output.
+cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16* out,
+                             int64_t ld_t, int split, cudaStream_t st);
+
+// float32 <-> bfloat16 conversion of a whole matrix (rows x cols, ld) for A.
+cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
+                               __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
+
+// One-sided Jacobi SVD of X = R^T (transposed = 1, R row-major l x l, ld) or X (transposed = 0).
+// Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
+cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp,
+                              float* ut, float* s, float* w, uint32_t* status, cudaStream_t st);
+size_t jacobi_smem_bytes(int l);
+
+// dst[r][c] = sum_{s < splits} src[s][r][c] for c < cols, 0 for cols <= c < cols_pad
+// (layout change between the caller's leading dimension and the padded width).
+cudaError_t launch_gather(const float* src, int splits, int64_t split_stride, int64_t lds,
+                          float* dst, int64_t ldd, int64_t rows, int cols, int cols_pad,
+                          cudaStream_t st);
+
+}  // namespace rsvd

@@ -1,0 +1,36 @@
+// Tensor-core (tcgen05, bfloat16 in / float32 accumulate) passes over A:
+// Y = A X and Y = A^T X with A row-major bfloat16 and the operand X stored
+// transposed in bfloat16 (lp x K, K contiguous).  Implemented in k_sketch_tc.cu.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsvd {
+
+struct TcPlan {
+  int64_t m = 0, n = 0, lda = 0;
+  int lp = 0, num_sms = 0;
+  __nv_bfloat16* xbf = nullptr;   // operand buffer, 2 lp x max(m, n)
+  const void* a_bound = nullptr;  // A described by the tensor maps below
+  alignas(64) unsigned char map_a_n[128];  // A tiles for Y = A X   (K-major operand)
+  alignas(64) unsigned char map_a_t[128];  // A tiles for Y = A^T X (MN-major operand)
+  alignas(64) unsigned char map_x_n[128];  // X^T tiles, K = n
+  alignas(64) unsigned char map_x_t[128];  // X^T tiles, K = m (lp rows)
+  alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (2 lp rows: hi and lo)
+  bool ready = false;
+};
+
+// 0 on success.
+int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfloat16* xbf,
+                 int num_sms);
+int tc_bind_a(TcPlan* tc, const void* A);
+// One pass.  trans = 0: Y = A X (X^T is lp x n in xbf); trans = 1: Y = A^T X (X^T is lp x m,
+// or 2 lp x m with split_x = 1, the hi and lo halves summed).  Writes *splits slabs of
+// (rows x lp) float32 into `partial`.
+int tc_pass(TcPlan* tc, int trans, int split_x, float* partial, int* splits, cudaStream_t st);
+int64_t tc_partial_elems(int64_t m, int64_t n, int lp, int num_sms);
+void tc_plan_destroy(TcPlan* tc);
+
+}  // namespace rsvd
