@@ -126,9 +126,9 @@ rsvd_status_t take_status(rsvd_plan_t P) {
 rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
   if (!P->omega_user) {
     TRY(launch_draw_gaussian(P->seed, 0u, P->n, P->l, P->lp, P->omega, P->lp,
-                             want_bf16 ? P->xbf : nullptr, P->n, P->st));
+                             want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
   } else if (want_bf16) {
-    TRY(launch_to_bf16_t(P->omega, P->n, P->lp, P->xbf, P->n, 0, P->st));
+    TRY(launch_to_bf16_t(P->omega, P->n, P->lp, P->xbf, tc_ld(P->n), 0, 0, P->st));
   }
   return RSVD_OK;
 }
@@ -188,10 +188,10 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
   for (int j = 1; j <= P->q; ++j) {
-    if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, P->m, 0, P->st));
+    if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, tc_ld(P->m), 0, 0, P->st));
     TRYS(step_pass(P, A, 1, P->qbuf, false, &s, &stride));
     TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr));
-    if (tc) TRY(launch_to_bf16_t(P->qtbuf, P->n, P->lp, P->xbf, P->n, 0, P->st));
+    if (tc) TRY(launch_to_bf16_t(P->qtbuf, P->n, P->lp, P->xbf, tc_ld(P->n), 0, 0, P->st));
     TRYS(step_pass(P, A, 0, P->qtbuf, false, &s, &stride));
     TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
   }
@@ -202,7 +202,8 @@ rsvd_status_t stage_b(rsvd_plan_t P, const void* A, float* U, float* S, float* V
   const bool tc = P->opt.precision == RSVD_BF16_TC;
   int s;
   int64_t stride;
-  if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, P->m, 1, P->st));
+  if (tc)
+    TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, tc_ld(P->m), 1, tc_lo_offset(P->lp), P->st));
   TRYS(step_pass(P, A, 1, P->qbuf, true, &s, &stride));      // B^T = A^T Q
   TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));  // B^T = Q_B R_B
   TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
@@ -308,7 +309,9 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return s;
   }
   if (o.precision == RSVD_BF16_TC) {
-    if ((s = dalloc(P, &P->xbf, (size_t)2 * lp * P->maxmn)) != RSVD_OK) {
+    const size_t xrows = (size_t)tc_lo_offset(lp) + lp;
+    if ((s = dalloc(P, &P->xbf, xrows * (size_t)tc_ld(P->maxmn))) != RSVD_OK ||
+        cudaMemsetAsync(P->xbf, 0, xrows * (size_t)tc_ld(P->maxmn) * 2, P->st) != cudaSuccess) {
       free_plan(P);
       return s;
     }
@@ -316,6 +319,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       free_plan(P);
       return RSVD_ERR_CUDA;
     }
+    P->tc.status = P->status;
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
       cudaMemsetAsync(P->small, 0, sizeof(float) * 8 * lp * lp, P->st) != cudaSuccess) {
@@ -424,7 +428,8 @@ rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const
   if (P->opt.precision == RSVD_BF16_TC) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
   float* xin = transpose ? P->qbuf : P->omega;  // padded K x lp copy of X
   TRY(launch_gather(X, 1, 0, P->l, xin, P->lp, kx, P->l, P->lp, P->st));
-  if (P->opt.precision == RSVD_BF16_TC) TRY(launch_to_bf16_t(xin, kx, P->lp, P->xbf, kx, 0, P->st));
+  if (P->opt.precision == RSVD_BF16_TC)
+    TRY(launch_to_bf16_t(xin, kx, P->lp, P->xbf, tc_ld(kx), 0, 0, P->st));
   int s;
   int64_t stride;
   TRYS(step_pass(P, A, transpose, xin, false, &s, &stride));

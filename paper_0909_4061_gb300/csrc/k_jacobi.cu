@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
         float t = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(az, az, 1.0f)));
         t = copysignf(t, zeta);
         if (zeta == 0.0f) t = 1.0f;
-        const float c = rsqrtf(fmaf(t, t, 1.0f));
+        // correctly rounded 1/sqrt: an approximate reciprocal square root biases every
+        // rotation the same way and the column norms drift over hundreds of rotations
+        const float c = 1.0f / sqrtf(fmaf(t, t, 1.0f));
         const float sn = c * t;
         if (lane == 0) s_rot = 1;
         float* jp = Jc + p * l;

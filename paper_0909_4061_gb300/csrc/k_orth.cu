@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 }
 
 __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int lp,
-                                 __nv_bfloat16* __restrict__ out, int64_t ld_t, int split) {
+                                 __nv_bfloat16* __restrict__ out, int64_t ld_t, int split,
+                                 int lo_off) {
   __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -267,7 +268,7 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int 
       const float v = tile[tx][i];
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
       out[(int64_t)c * ld_t + r] = hi;
-      if (split) out[(int64_t)(lp + c) * ld_t + r] = __float2bfloat16_rn(v - __bfloat162float(hi));
+      if (split) out[(int64_t)(lo_off + c) * ld_t + r] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
   }
 }
@@ -336,9 +337,9 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
 }
 
 cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16* out, int64_t ld_t,
-                             int split, cudaStream_t st) {
+                             int split, int lo_off, cudaStream_t st) {
   const dim3 grid((unsigned)cdiv(rows, 32), (unsigned)cdiv(lp, 32));
-  to_bf16_t_kernel<<<grid, dim3(32, 8), 0, st>>>(x, rows, lp, out, ld_t, split);
+  to_bf16_t_kernel<<<grid, dim3(32, 8), 0, st>>>(x, rows, lp, out, ld_t, split, lo_off);
   return cudaGetLastError();
 }
 

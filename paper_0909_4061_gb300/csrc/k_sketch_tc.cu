@@ -1,11 +1,558 @@
-// Placeholder until the tcgen05 kernels land: the tensor-core path reports
-// itself unavailable so that plan creation fails with an error.
+// Tensor-core passes over A (Algorithm 4.4 steps 2, 4, 5 and Algorithm 5.1
+// step 1) for a bfloat16 A: Y = A X or Y = A^T X, bfloat16 products with
+// float32 accumulation in tensor memory.
+//
+// Shapes: every MMA is M = 128 rows of the output by N = the basis width
+// (lp, or 2 lp when the operand carries a hi and a lo half that the epilogue
+// sums) by K = 16.  The M side is always A:
+//   Y = A X   : A tile = 128 rows x 64 columns of A, K-major (row-major A),
+//   Y = A^T X : A tile = 64 rows x 128 columns of A, read as the transposed
+//               operand (MN-major), two 64-column TMA boxes.
+// The operand X is stored transposed (lp x K, K contiguous, bfloat16) so that
+// it is a K-major B operand in both passes.  All tiles are TMA loads with the
+// 128-byte swizzle; no multicast.
+//
+// Work split ("stream-K"): the iterations (row tile t, k tile kk) are laid out
+// t-major and cut into gridDim.x equal ranges, one per CTA (one CTA per SM).
+// A row tile covered by one CTA is written straight to Y.  A tile split
+// between CTAs is finished by the CTA that holds its first k tile (it reaches
+// the tile last): the other contributors write their partial sums to a slot
+// and raise a flag, and the finishing CTA adds them in CTA order
+// (deterministic) and clears the flags.
+//
+// Warp roles (192 threads): warp 0 issues TMA, warp 1 owns tensor memory and
+// issues the MMAs from one thread, warps 2-5 drain the accumulator (each
+// warp reads the 32 TMEM lanes its index allows).  Every wait is bounded; on
+// expiry the kernel records a timeout in the status word and winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
 #include "sketch_tc.cuh"
 
 namespace rsvd {
-int tc_plan_init(TcPlan*, int64_t, int64_t, int64_t, int, __nv_bfloat16*, int) { return -1; }
-int tc_bind_a(TcPlan*, const void*) { return -1; }
-int tc_pass(TcPlan*, int, int, float*, int*, cudaStream_t) { return -1; }
-int64_t tc_partial_elems(int64_t, int64_t, int, int) { return 0; }
-void tc_plan_destroy(TcPlan*) {}
+namespace {
+
+constexpr int BM = 128;            // MMA M / output rows per tile
+constexpr int BK = 64;             // k extent of one pipeline stage (one 128-byte swizzle row)
+constexpr int kThreads = 192;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and the abort flag) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint32_t* status) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (i > 32) __nanosleep(64);
+  }
+  *abort_flag = 1;
+  set_status(status, ST_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
+// leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
+// >> 4 in 32-45, the fixed version value 1 in bits 46-47, swizzle mode in
+// 61-63 (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor for kind::f16: f32 accumulate (bits 4-5 = 1), bf16 A
+// and B (bits 7-9 and 10-12 = 1), A major-ness in bit 15 (1 = MN-major), B
+// K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t instr_desc(int n, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 (or, for a 16-wide tail, 16) accumulator columns of this thread's row.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int ncol, float* v) {
+  if (ncol == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+    tmem_ld16(taddr, v);
+#pragma unroll
+    for (int i = 16; i < 32; ++i) v[i] = 0.0f;
+  }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void epi_bar() {  // the 4 epilogue warps only
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+struct Range {
+  int64_t total;
+  int grid;
+  __device__ __forceinline__ int64_t start(int c) const { return (int64_t)c * total / grid; }
+  __device__ __forceinline__ int cta_of(int64_t it) const {
+    int c = (int)(it * grid / total);
+    while (c + 1 < grid && start(c + 1) <= it) ++c;
+    while (c > 0 && start(c) > it) --c;
+    return c;
+  }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
+                     const __grid_constant__ CUtensorMap map_x, float* __restrict__ y, int lp,
+                     int64_t M, int kt, int64_t total, int n_total, int fold, int lo_off, int stages,
+                     float* __restrict__ slots, uint32_t* __restrict__ flags, uint32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_full[16], bar_empty[16], bar_acc_full, bar_acc_empty;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Range rg{total, (int)gridDim.x};
+  const int cta = blockIdx.x;
+  const int64_t it0 = rg.start(cta), it1 = rg.start(cta + 1);
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  constexpr uint32_t a_bytes = BM * BK * 2;  // 16 KB
+  const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
+  const uint32_t stage_bytes = a_bytes + x_bytes;
+  uint32_t tmem_cols = 32;
+  while ((int)tmem_cols < n_total) tmem_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc_full, 1);
+    mbar_init(&bar_acc_empty, 4);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int64_t i = 0;
+      for (int64_t it = it0; it < it1; ++it, ++i) {
+        const int s = (int)(i % stages);
+        const uint32_t ph = (uint32_t)((i / stages) & 1);
+        if (!mbar_wait(&bar_empty[s], ph ^ 1u, abort_flag, status)) break;
+        uint8_t* sa = smem + (size_t)s * stage_bytes;
+        uint8_t* sx = sa + a_bytes;
+        mbar_expect_tx(&bar_full[s], stage_bytes);
+        const int t = (int)(it / kt), kk = (int)(it % kt);
+        if (MODE == 0) {
+          tma_load_2d(sa, &map_a, &bar_full[s], kk * BK, t * BM);
+        } else {
+          tma_load_2d(sa, &map_a, &bar_full[s], t * BM, kk * BK);
+          tma_load_2d(sa + 8192, &map_a, &bar_full[s], t * BM + 64, kk * BK);
+        }
+        for (int c = 0; c * 256 < n_total; ++c)
+          tma_load_2d(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256);
+      }
+      // let the copies still in flight land before the CTA can exit
+      const int64_t issued = i;
+      for (int64_t j = (issued > stages ? issued - stages : 0); j < issued; ++j) {
+        const int s = (int)(j % stages);
+        const uint32_t ph = (uint32_t)((j / stages) & 1);
+        for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(&bar_full[s], ph); ++w) __nanosleep(64);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc_full = instr_desc(n_total < 256 ? n_total : 256, MODE);
+      const uint32_t idesc_tail = instr_desc(n_total > 256 ? n_total - 256 : 16, MODE);
+      int64_t i = 0;
+      int seg = 0;
+      bool ok = true;
+      for (int64_t it = it0; it < it1 && ok; ++seg) {
+        const int t = (int)(it / kt);
+        const int64_t seg_end = min(it1, (int64_t)(t + 1) * kt);
+        if (!mbar_wait(&bar_acc_empty, ((uint32_t)seg & 1u) ^ 1u, abort_flag, status)) break;
+        tc_fence_after();
+        for (; it < seg_end; ++it, ++i) {
+          const int s = (int)(i % stages);
+          const uint32_t ph = (uint32_t)((i / stages) & 1);
+          if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sx = sa + a_bytes;
+          const bool first = (it == (int64_t)t * kt) || (it == it0);
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            uint64_t adesc;
+            if (MODE == 0)
+              adesc = smem_desc(sa + j * 32, 16, 1024);           // K-major: +32 B per k16
+            else
+              adesc = smem_desc(sa + j * 2048, 8192, 1024);       // MN-major: +16 rows of 128 B
+            for (int c = 0; c * 256 < n_total; ++c) {
+              const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
+              const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
+              mma_bf16(tmem + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(&bar_empty[s]);
+        }
+        if (ok) mma_commit(&bar_acc_full);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+    int seg = 0;
+    for (int64_t it = it0; it < it1; ++seg) {
+      const int t = (int)(it / kt);
+      const int64_t tile_b = (int64_t)t * kt, tile_e = tile_b + kt;
+      const int64_t seg_end = min(it1, tile_e);
+      const int c_first = rg.cta_of(tile_b), c_last = rg.cta_of(tile_e - 1);
+      const bool ok = __all_sync(0xffffffffu,
+                                 mbar_wait(&bar_acc_full, (uint32_t)seg & 1u, abort_flag, status));
+      tc_fence_after();
+      const int64_t grow = (int64_t)t * BM + row;
+      const bool valid_row = grow < M;
+      const bool direct = (c_first == c_last);
+      const bool finisher = !direct && (cta == c_first);
+      if (finisher) {
+        // wait until every later contributor has published its partial sum
+        for (int c = c_first + 1; c <= c_last; ++c) {
+          uint32_t w = 0;
+          while (ld_acquire(flags + c) == 0u) {
+            if (++w > kSpinLimit || *abort_flag) {
+              set_status(status, ST_TIMEOUT);
+              *abort_flag = 1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+      for (int c0 = 0; c0 < lp; c0 += 32) {
+        const int ncol = min(32, lp - c0);  // lp is a multiple of 16: 32 or 16
+        float v[32];
+        tmem_ld_cols(tbase + c0, ncol, v);
+        if (fold) {
+          float w2[32];
+          tmem_ld_cols(tbase + lo_off + c0, ncol, w2);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] += w2[q];
+        }
+        if (!ok || !valid_row) continue;
+        if (direct || finisher) {
+          if (finisher) {
+            for (int c = c_first + 1; c <= c_last; ++c) {
+              const float* src = slots + ((size_t)c * BM + row) * lp + c0;
+              for (int q = 0; q < ncol; ++q) v[q] += src[q];
+            }
+          }
+          float* dst = y + grow * lp + c0;
+          if (ncol == 32) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+              *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          } else {
+            for (int q = 0; q < ncol; ++q) dst[q] = v[q];
+          }
+        } else {
+          float* dst = slots + ((size_t)cta * BM + row) * lp + c0;
+          for (int q = 0; q < ncol; ++q) dst[q] = v[q];
+        }
+      }
+      tc_fence_before();
+      if (!direct && !finisher) {
+        // publish this CTA's partial of tile t (its first segment)
+        __threadfence();
+        epi_bar();
+        if (warp == 2 && lane == 0) st_release(flags + cta, 1u);
+      } else if (finisher) {
+        epi_bar();  // all rows have read the partials
+        if (warp == 2 && lane == 0)
+          for (int c = c_first + 1; c <= c_last; ++c) flags[c] = 0u;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_acc_empty);
+      it = seg_end;
+      if (!ok) break;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encoder() {
+  if (g_encode) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return -1;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return 0;
+}
+
+// 2-D bfloat16 tensor map: inner dimension `inner` (contiguous), `outer` rows
+// of `ld` elements, box {box_inner, box_outer}, 128-byte swizzle.
+int encode_2d(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+              uint32_t box_inner, uint32_t box_outer) {
+  if (get_encoder()) return -1;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+struct TcBuffers {
+  float* slots = nullptr;
+  uint32_t* flags = nullptr;
+  int grid = 0;
+};
+
+size_t smem_bytes(int n_total, int stages) {
+  return (size_t)stages * (BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
+}
+
+int pick_stages(int n_total) {
+  const size_t budget = 200 * 1024;
+  int s = (int)(budget / ((size_t)BM * BK * 2 + (size_t)n_total * BK * 2));
+  if (s > 8) s = 8;
+  return s < 2 ? 2 : s;
+}
+
+}  // namespace
+
+int64_t tc_ld(int64_t k) { return round_up(k, 8); }
+int tc_lo_offset(int lp) { return 2 * lp <= 256 ? lp : 256; }
+static int fold_ntotal(int lp) { return 2 * lp <= 256 ? 2 * lp : 512; }
+
+int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfloat16* xbf,
+                 int num_sms) {
+  tc->m = m;
+  tc->n = n;
+  tc->lda = lda;
+  tc->lp = lp;
+  tc->num_sms = num_sms;
+  tc->xbf = xbf;
+  tc->a_bound = nullptr;
+  if (lp > 256 || lp % 16) return -1;
+  const int64_t ldn = tc_ld(n), ldm = tc_ld(m);
+  if (encode_2d(tc->map_x_n, xbf, n, lp, ldn, BK, lp)) return -1;
+  if (encode_2d(tc->map_x_t, xbf, m, lp, ldm, BK, lp)) return -1;
+  const int nf = fold_ntotal(lp);
+  if (encode_2d(tc->map_x_t2, xbf, m, tc_lo_offset(lp) + lp, ldm, BK, nf > 256 ? 256 : nf)) return -1;
+  TcBuffers* b = new TcBuffers();
+  b->grid = num_sms;
+  if (cudaMalloc(&b->slots, sizeof(float) * (size_t)num_sms * BM * lp) != cudaSuccess ||
+      cudaMalloc(&b->flags, sizeof(uint32_t) * (size_t)num_sms) != cudaSuccess ||
+      cudaMemset(b->flags, 0, sizeof(uint32_t) * (size_t)num_sms) != cudaSuccess) {
+    cudaGetLastError();
+    if (b->slots) cudaFree(b->slots);
+    if (b->flags) cudaFree(b->flags);
+    delete b;
+    return -1;
+  }
+  tc->priv = b;
+  for (int n_total : {lp, fold_ntotal(lp)}) {
+    const size_t sm = smem_bytes(n_total, pick_stages(n_total));
+    if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess ||
+        cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess)
+      return -1;
+  }
+  tc->ready = true;
+  return 0;
+}
+
+int tc_bind_a(TcPlan* tc, const void* A) {
+  if (!tc->ready) return -1;
+  if (A == tc->a_bound) return 0;
+  if (reinterpret_cast<uintptr_t>(A) & 15) return -1;
+  if (encode_2d(tc->map_a_n, A, tc->n, tc->m, tc->lda, BK, BM)) return -1;
+  if (encode_2d(tc->map_a_t, A, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+  tc->a_bound = A;
+  return 0;
+}
+
+int tc_pass(TcPlan* tc, int trans, int split_x, float* out, int* splits, cudaStream_t st) {
+  if (!tc->ready || !tc->a_bound) return -1;
+  TcBuffers* b = static_cast<TcBuffers*>(tc->priv);
+  const int lp = tc->lp;
+  const int n_total = split_x ? fold_ntotal(lp) : lp;
+  const int lo_off = split_x ? tc_lo_offset(lp) : 0;
+  const int64_t M = trans ? tc->n : tc->m;
+  const int64_t K = trans ? tc->m : tc->n;
+  const int kt = (int)cdiv(K, BK);
+  const int64_t total = cdiv(M, BM) * kt;
+  const int grid = (int)(total < b->grid ? total : b->grid);
+  const int stages = pick_stages(n_total);
+  const size_t sm = smem_bytes(n_total, stages);
+  const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(trans ? tc->map_a_t : tc->map_a_n);
+  const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
+      trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
+  if (split_x && !trans) return -1;
+  if (trans)
+    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *mx, out, lp, M, kt, total, n_total,
+                                                    split_x, lo_off, stages, b->slots, b->flags,
+                                                    tc->status);
+  else
+    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *mx, out, lp, M, kt, total, n_total,
+                                                    split_x, lo_off, stages, b->slots, b->flags,
+                                                    tc->status);
+  *splits = 1;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int64_t tc_partial_elems(int64_t m, int64_t n, int lp, int num_sms) {
+  (void)num_sms;
+  return (m > n ? m : n) * (int64_t)lp;
+}
+
+void tc_plan_destroy(TcPlan* tc) {
+  if (tc->priv) {
+    TcBuffers* b = static_cast<TcBuffers*>(tc->priv);
+    if (b->slots) cudaFree(b->slots);
+    if (b->flags) cudaFree(b->flags);
+    delete b;
+    tc->priv = nullptr;
+  }
+  tc->ready = false;
+}
+
 }  // namespace rsvd

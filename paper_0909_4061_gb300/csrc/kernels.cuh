@@ -38,9 +38,9 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
                             cudaStream_t st);
 
 // float32 rows x lp (ld lp) -> bfloat16 transposed (lp x rows, ld_t); with `split`,
-// also writes the residual x - bf16(x) as rows [lp, 2 lp) of the output.
+// also writes the residual x - bf16(x) as rows [lo_off, lo_off + lp) of the output.
 cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16* out,
-                             int64_t ld_t, int split, cudaStream_t st);
+                             int64_t ld_t, int split, int lo_off, cudaStream_t st);
 
 // float32 <-> bfloat16 conversion of a whole matrix (rows x cols, ld) for A.
 cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,

@@ -18,9 +18,18 @@ struct TcPlan {
   alignas(64) unsigned char map_a_t[128];  // A tiles for Y = A^T X (MN-major operand)
   alignas(64) unsigned char map_x_n[128];  // X^T tiles, K = n
   alignas(64) unsigned char map_x_t[128];  // X^T tiles, K = m (lp rows)
-  alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (2 lp rows: hi and lo)
+  alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (hi rows, then lo rows at tc_lo_offset)
   bool ready = false;
+  uint32_t* status = nullptr;     // device status word of the owning plan
+  void* priv = nullptr;           // stream-K slots and flags
 };
+
+// Leading dimension (elements) of the transposed bfloat16 operand for a K extent:
+// TMA wants row strides that are multiples of 16 bytes.
+int64_t tc_ld(int64_t k);
+// Row at which the lo half of a split operand starts (lp when 2 lp <= 256, else 256),
+// and the rows the operand buffer needs (lo offset + lp).
+int tc_lo_offset(int lp);
 
 // 0 on success.
 int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfloat16* xbf,
