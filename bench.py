@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark of the randomized SVD hot path on GB300 (one JSON line on rank 0).
+
+Workload (default): the 16384 x 16384 matrix A = U diag(j^-1.5) V^T with Haar
+U, V, rank k = 100, oversampling p = 10, q = 1 power step (four passes over
+A), bfloat16-stored A on the tensor-core path, compared with the plain FP32
+CUDA-core path on the float32 A, at matched reconstruction error.
+
+One step = one full rank-k randomized SVD (test-matrix draw, the four passes,
+every orthonormalisation, the small SVD and the lift) through the C ABI with
+A resident in HBM.  `value` is milliseconds per rank-k SVD (lower is better);
+with N GPUs each rank runs its own replica and value = elapsed / (N * steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the float64 CPU oracle on the host cores instead (the
+reference arm); under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rank-k rSVD ms & HBM roofline frac, BF16-TC vs FP32 GPU at matched error"
+WORKLOAD = ("c2: A = U diag(j^-1.5) V^T, 16384 x 16384, Haar U,V (float32 QR of seeded "
+            "Gaussians), bf16-stored A; k=100, p=10, q=1 (4 passes over A)")
+PASS_KERNEL_SRC = os.path.join(ROOT, "paper_0909_4061_gb300", "csrc", "k_sketch_tc.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sketch_tc_pass_c2.md")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas: no collective on the data path)
+# ----------------------------------------------------------------------------
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(backend: str, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and not dist.is_initialized():
+        kw = {}
+        if backend == "nccl":
+            kw["device_id"] = torch.device("cuda", local_rank)
+        dist.init_process_group(backend=backend, **kw)
+    return dist.is_initialized()
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float) -> float:
+    """Largest value of x over all ranks (the slowest replica sets the job time)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_initialized():
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_unit(max_elapsed_ms: float, steps: int, world: int) -> float:
+    """Whole-job time per rank-k SVD: `world` replicas each ran `steps` SVDs in the max elapsed time."""
+    return max_elapsed_ms / (steps * world)
+
+
+# ----------------------------------------------------------------------------
+# clocks, peaks, ncu traffic
+# ----------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, power = [], [], []
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+                power.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "last ~0.5 s of warm-up load + the timed region"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return dict(FALLBACK_PEAKS)
+
+
+def file_sha(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the pass kernel from the committed ncu summary, or None
+    when the summary is missing or was taken on a different version of the kernel."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            key, _, v = line.strip()[2:].partition(":")
+            vals[key.strip()] = v.strip().strip("`")
+    try:
+        if vals.get("kernel_source_sha") != file_sha(PASS_KERNEL_SRC):
+            return None
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+# the workload
+# ----------------------------------------------------------------------------
+
+
+def make_inputs(rank: int):
+    import torch
+
+    import synth
+
+    w = synth.C2
+    A = synth.device_lowrank(w.m, w.n, w.sigma(), w.matrix_seed + 7919 * rank)
+    Ab = A.to(torch.bfloat16)
+    torch.cuda.synchronize()
+    return w, A, Ab
+
+
+def recon_error(A, U, S, V) -> float:
+    """||A - U diag(S) V^T||_F in float64 (on the device)."""
+    import torch
+
+    R = A.double()
+    R.addmm_(U.double() * S.double(), V.double().T, alpha=-1.0)
+    return float(torch.linalg.norm(R).item())
+
+
+def time_steps(pkg, plan, A, U, S, V, steps: int, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        pkg.rsvd_svd(plan.handle, A, U, S, V)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def cpu_baseline(A, w, budget_s: float = 12.0):
+    """The float64 oracle on the host cores (bounded number of full rank-k SVDs)."""
+    import numpy as np
+
+    from oracle import philox, rsvd64
+
+    a64 = A.cpu().numpy().astype(np.float64)
+    om = philox.gaussian(w.omega_seed, philox.STREAM_OMEGA, w.n, w.l)
+    times = []
+    t_start = time.perf_counter()
+    while not times or (time.perf_counter() - t_start < budget_s and len(times) < 5):
+        t0 = time.perf_counter()
+        rsvd64.rsvd(a64, w.k, w.p, w.q, om)
+        times.append((time.perf_counter() - t0) * 1e3)
+    return {"value": statistics.median(times), "unit": "ms", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{len(times)} full rank-{w.k} SVDs of the same 16384x16384 A in float64 "
+                      "(numpy/LAPACK, default BLAS threads), median"}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist_init("nccl", local_rank)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0909_4061_gb300 as pkg
+
+    w, A, Ab = make_inputs(rank)
+    stream = torch.cuda.current_stream()
+    dev = A.device
+    U = torch.empty(w.m, w.k, device=dev)
+    S = torch.empty(w.k, device=dev)
+    V = torch.empty(w.n, w.k, device=dev)
+    out = {}
+
+    with pkg.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_BF16_TC) as pl:
+        for _ in range(max(args.warmup, 3)):
+            pkg.rsvd_svd(pl.handle, Ab, U, S, V)
+        if pkg.rsvd_sync(pl.handle) != pkg.RSVD_OK:
+            raise RuntimeError("device error during warm-up")
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        t_end = time.perf_counter() + (0.0 if args.profile_run else 0.5)
+        while time.perf_counter() < t_end:       # keep the GPU loaded while sampling starts
+            pkg.rsvd_svd(pl.handle, Ab, U, S, V)
+            torch.cuda.synchronize()
+        pkg.rsvd_profile(pl.handle, 1 << pkg.RSVD_STEP_PASS)
+        elapsed = time_steps(pkg, pl, Ab, U, S, V, args.steps, stream)
+        clk = clocks.stop()
+        pass_ms, launches = pkg.rsvd_profile_read(pl.handle)
+        status = pkg.rsvd_sync(pl.handle)
+        if status != pkg.RSVD_OK:
+            raise RuntimeError(f"device status {pkg.status_string(status)}")
+        e_bf16 = recon_error(A, U, S, V)
+        s_bf16 = S.double().cpu()
+        # per-step breakdown (diagnostic, separate short loop, every step kind timed)
+        pkg.rsvd_profile(pl.handle, (1 << pkg.RSVD_NUM_STEPS) - 1)
+        for _ in range(5):
+            pkg.rsvd_svd(pl.handle, Ab, U, S, V)
+        stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
+        pkg.rsvd_profile(pl.handle, 0)
+        out["stages_ms_per_svd"] = {k: round(v / 5, 4) for k, v in stage_ms.items()}
+        # end to end through the host-buffer entry point
+        e2e = None
+        if not args.no_e2e:
+            a_host = Ab.cpu().pin_memory()
+            uh = torch.empty(w.m, w.k).pin_memory()
+            sh = torch.empty(w.k).pin_memory()
+            vh = torch.empty(w.n, w.k).pin_memory()
+            pkg.rsvd_svd_host(pl.handle, a_host, uh, sh, vh)
+            k_e2e = max(3, min(args.steps, 10))
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                pkg.rsvd_svd_host(pl.handle, a_host, uh, sh, vh)
+            t_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3)
+            e2e = {"value": job_ms_per_unit(t_e2e, k_e2e, world), "unit": "ms",
+                   "h2d_bytes_per_step": int(w.m * w.n * 2),
+                   "d2h_bytes_per_step": int((w.m * w.k + w.k + w.n * w.k) * 4),
+                   "steps": k_e2e, "api": "rsvd_svd_host (pinned host buffers)"}
+
+    # the plain FP32 CUDA-core path on the float32 A, same Omega seed
+    k32 = 0
+    el32, e_f32, s_f32 = float("nan"), float("nan"), s_bf16
+    if not args.profile_run:
+        with pkg.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_PLAIN_FP32) as pl32:
+            pkg.rsvd_svd(pl32.handle, A, U, S, V)
+            k32 = max(3, min(args.steps, 10))
+            el32 = time_steps(pkg, pl32, A, U, S, V, k32, stream)
+            if pkg.rsvd_sync(pl32.handle) != pkg.RSVD_OK:
+                raise RuntimeError("device error on the FP32 path")
+            e_f32 = recon_error(A, U, S, V)
+            s_f32 = S.double().cpu()
+
+    elapsed_max = max_over_ranks(elapsed)
+    ms_step = elapsed_max / args.steps
+    value = job_ms_per_unit(elapsed_max, args.steps, world)
+    peaks = measured_peaks()
+    n_pass = launches["pass"]
+    avg_pass_ms = pass_ms["pass"] / max(n_pass, 1)
+    bytes_per_pass = w.m * w.n * 2 + w.n * 112 * 2 + w.m * 112 * 4   # A + bf16 operand + f32 output
+    achieved = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Haar factors on the device; the paper's datasets are not used)",
+        "config": {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
+                   "precision": "bf16 tensor cores, f32 accumulate, f32 re-orthonormalisation",
+                   "l2": "A is 537 MB bf16 (> 129 MB L2); no flush needed between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": ncu_traffic(), "kernel": "sketch_tc_kernel (one pass over A)",
+                     "bytes_per_launch": bytes_per_pass, "avg_launch_ms": round(avg_pass_ms, 5),
+                     "peak_source": peaks["source"]},
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clk,
+        "fp32_path": {"ms": round(el32 / max(k32, 1), 4), "steps": k32,
+                      "speedup_bf16_tc": round((el32 / max(k32, 1)) / ms_step, 3)},
+        "accuracy": {"recon_err_bf16": e_bf16, "recon_err_fp32": e_f32,
+                     "rel_excess": (e_bf16 - e_f32) / e_f32,
+                     "max_sigma_diff_vs_fp32_over_sigma1":
+                         float(((s_bf16 - s_f32).abs().max() / s_f32[0]).item())},
+    }
+    line.update(out)
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(A, w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_pass_probe(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0909_4061_gb300 as pkg
+    import synth
+
+    m, n, k, p = 8192, 16384, 100, 10
+    A = synth.device_lowrank(m, n, synth.spectrum_power(min(m, n), 1.5), 5).to(torch.bfloat16)
+    X = torch.randn(n, k + p, device="cuda")
+    Y = torch.empty(m, k + p, device="cuda")
+    with pkg.Plan(m, n, k, p, 1, 1, pkg.RSVD_BF16_TC) as pl:
+        for trans in (0, 1):
+            for _ in range(3):
+                if trans:
+                    pkg.rsvd_sketch(pl.handle, A, 1, Y, X)
+                else:
+                    pkg.rsvd_sketch(pl.handle, A, 0, X, Y)
+        if pkg.rsvd_sync(pl.handle) != pkg.RSVD_OK:
+            raise RuntimeError("device error in the pass probe")
+    print(json.dumps({"pass_probe": "ok", "m": m, "n": n, "l": k + p}))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+    from oracle import philox, rsvd64
+
+    w = synth.C2
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            a64 = synth.device_lowrank(w.m, w.n, w.sigma(), w.matrix_seed).cpu().numpy().astype(np.float64)
+        else:
+            raise RuntimeError
+    except Exception:
+        a64, *_ = synth.lowrank(w.m, w.n, w.sigma(), w.matrix_seed)
+    om = philox.gaussian(w.omega_seed, philox.STREAM_OMEGA, w.n, w.l)
+    for _ in range(args.warmup):
+        rsvd64.rsvd(a64, w.k, w.p, w.q, om)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rsvd64.rsvd(a64, w.k, w.p, w.q, om)
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    sample = f"{args.steps} full rank-{w.k} SVDs of the 16384x16384 A in float64 (numpy/LAPACK)"
+    line = {"impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q},
+            "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="timed pipeline only (no clock-load loop, e2e, FP32 leg or CPU baseline): "
+                         "the command the ncu launch list is taken on")
+    ap.add_argument("--pass-probe", action="store_true",
+                    help="three launches of the tensor-core pass kernel on an 8192 x 16384 bf16 A "
+                         "(268 MB, larger than L2): the small case for full ncu captures")
+    args = ap.parse_args()
+    if args.pass_probe:
+        run_pass_probe(args)
+        return
+    if args.profile_run:
+        args.no_e2e = args.no_cpu = True
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -135,6 +135,33 @@ RSVD_API rsvd_status_t rsvd_sync(rsvd_plan_t plan);
 /* Static English description of a status code. */
 RSVD_API const char* rsvd_status_string(rsvd_status_t status);
 
+/* ---- tracing ----------------------------------------------------------- */
+
+/* Step kinds for per-step timing and launch counts. */
+enum {
+  RSVD_STEP_DRAW = 0,       /* test matrix (Algorithm 4.1 step 1) */
+  RSVD_STEP_PASS = 1,       /* one pass over A: Y = A X or A^T X */
+  RSVD_STEP_ORTH = 2,       /* Cholesky-QR rounds (Gram, factor, apply) */
+  RSVD_STEP_SMALL_SVD = 3,  /* Jacobi SVD of the l x l factor */
+  RSVD_STEP_LIFT = 4,       /* U = Q Ut_k, V = Q_B W_k */
+  RSVD_STEP_CONVERT = 5,    /* float32 -> transposed bfloat16 operands */
+  RSVD_NUM_STEPS = 6
+};
+
+/* Start per-step timing: for every step kind whose bit is set in `mask`,
+ * each later step of that kind on this plan is bracketed by a pair of CUDA
+ * events recorded on the plan's stream.  Resets the time totals and the
+ * kernel launch counters (which are kept for every kind, whatever the mask).
+ * mask = 0 stops timing. */
+RSVD_API rsvd_status_t rsvd_profile(rsvd_plan_t plan, uint32_t mask);
+
+/* Waits for the plan's stream, then for each step kind s < nkinds writes the
+ * summed device time of the timed steps (ms[s], milliseconds; may be NULL)
+ * and the number of kernels launched (launches[s]; may be NULL) since the
+ * last rsvd_profile call. */
+RSVD_API rsvd_status_t rsvd_profile_read(rsvd_plan_t plan, float* ms, int64_t* launches,
+                                         int32_t nkinds);
+
 /* ---- step-level entry points (each runs one step of the method with the
  * ---- plan's kernels; the tests check each against the oracle) ---------- */
 

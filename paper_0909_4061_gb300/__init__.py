@@ -35,8 +35,12 @@ EXPORTS = (
     "rsvd_options_default", "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_workspace_bytes",
     "rsvd_range_finder", "rsvd_svd", "rsvd_svd_host", "rsvd_svd_backward", "rsvd_get_omega",
     "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
-    "rsvd_orthonormalize", "rsvd_small_svd",
+    "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
 )
+
+RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
+RSVD_STEP_SMALL_SVD, RSVD_STEP_LIFT, RSVD_STEP_CONVERT, RSVD_NUM_STEPS = 3, 4, 5, 6
+STEP_NAMES = ("draw", "pass", "orth", "small_svd", "lift", "convert")
 
 
 class RsvdUnavailable(ImportError):
@@ -84,6 +88,8 @@ _SIGS = {
     "rsvd_sketch": (_c.c_int, [_P, _P, _c.c_int32, _P, _P]),
     "rsvd_orthonormalize": (_c.c_int, [_P, _c.c_int64, _P, _P]),
     "rsvd_small_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "rsvd_profile": (_c.c_int, [_P, _c.c_uint32]),
+    "rsvd_profile_read": (_c.c_int, [_P, _P, _P, _c.c_int32]),
 }
 
 
@@ -217,6 +223,19 @@ def rsvd_orthonormalize(plan, rows, Y, R=None):
 
 def rsvd_small_svd(plan, X, Ut, S, W):
     _check(lib().rsvd_small_svd(plan, _ptr(X), _ptr(Ut), _ptr(S), _ptr(W)), "rsvd_small_svd")
+
+
+def rsvd_profile(plan, mask):
+    _check(lib().rsvd_profile(plan, int(mask)), "rsvd_profile")
+
+
+def rsvd_profile_read(plan):
+    """Returns ({step name: ms}, {step name: kernel launches})."""
+    ms = (ctypes.c_float * RSVD_NUM_STEPS)()
+    cnt = (ctypes.c_int64 * RSVD_NUM_STEPS)()
+    _check(lib().rsvd_profile_read(plan, ms, cnt, RSVD_NUM_STEPS), "rsvd_profile_read")
+    return ({STEP_NAMES[i]: ms[i] for i in range(RSVD_NUM_STEPS)},
+            {STEP_NAMES[i]: cnt[i] for i in range(RSVD_NUM_STEPS)})
 
 
 # ---- torch conveniences -------------------------------------------------------------

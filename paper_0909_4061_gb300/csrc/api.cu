@@ -14,6 +14,8 @@
 
 #include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -49,6 +51,11 @@ struct rsvd_plan_s {
   void* a_dev = nullptr;
   float *u_dev = nullptr, *s_dev = nullptr, *v_dev = nullptr;
   size_t ws_bytes = 0;
+  // tracing
+  uint32_t prof_mask = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[RSVD_NUM_STEPS];
+  int ev_used[RSVD_NUM_STEPS] = {};
+  int64_t launches[RSVD_NUM_STEPS] = {};
 
   float* g() { return small; }
   float* lbuf() { return small + 1 * (size_t)lp * lp; }
@@ -89,6 +96,11 @@ rsvd_status_t dalloc(rsvd_plan_t P, T** ptr, size_t elems) {
 
 void free_plan(rsvd_plan_t P) {
   if (!P) return;
+  for (auto& v : P->ev)
+    for (auto& e : v) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
                   P->v_dev};
@@ -119,11 +131,43 @@ rsvd_status_t take_status(rsvd_plan_t P) {
   return RSVD_OK;
 }
 
+// Brackets one step: counts its kernel launches and, when the step kind is
+// being timed, records a CUDA event pair around it on the plan's stream.
+class Step {
+ public:
+  Step(rsvd_plan_t P, int kind) : P_(P), kind_(kind) {
+    if (!(P->prof_mask & (1u << kind))) return;
+    auto& v = P->ev[kind];
+    int& used = P->ev_used[kind];
+    if (used == (int)v.size()) {
+      if (used >= 1 << 14) return;  // cap: stop timing rather than grow without bound
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      v.emplace_back(a, b);
+    }
+    end_ = v[used].second;
+    cudaEventRecord(v[used].first, P->st);
+    ++used;
+  }
+  ~Step() {
+    if (end_) cudaEventRecord(end_, P_->st);
+  }
+  void launched(int n = 1) { P_->launches[kind_] += n; }
+
+ private:
+  rsvd_plan_t P_;
+  int kind_;
+  cudaEvent_t end_ = nullptr;
+};
+
 // ---- the steps --------------------------------------------------------------
 
 // Test matrix (Algorithm 4.1 step 1) into P->omega (n x lp, float32) and, for
 // the tensor-core path, its bfloat16 transpose into P->xbf.
 rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
+  Step sp(P, RSVD_STEP_DRAW);
+  sp.launched();
   if (!P->omega_user) {
     TRY(launch_draw_gaussian(P->seed, 0u, P->n, P->l, P->lp, P->omega, P->lp,
                              want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
@@ -141,6 +185,8 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
   const int64_t M = trans ? P->n : P->m;
   const int64_t K = trans ? P->m : P->n;
   *stride = M * P->lp;
+  Step sp(P, RSVD_STEP_PASS);
+  sp.launched();
   if (P->opt.precision == RSVD_PLAIN_FP32) {
     const int s = trans ? P->splits_t : P->splits_n;
     TRY(launch_gemm_f32(trans, M, P->lp, K, static_cast<const float*>(A), P->lda, X, P->lp,
@@ -161,6 +207,8 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
   const int rounds = P->opt.orth_rounds;
   const int lp = P->lp;
   const int nblk = gram_blocks(rows);
+  Step sp(P, RSVD_STEP_ORTH);
+  sp.launched(4 * rounds);
   const float* cur = src;
   int cur_splits = splits;
   for (int r = 0; r < rounds; ++r) {
@@ -179,6 +227,16 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
   return RSVD_OK;
 }
 
+// float32 basis (rows x lp) -> transposed bfloat16 operand of the next pass
+// (with the lo half when `split`).
+rsvd_status_t step_convert(rsvd_plan_t P, const float* x, int64_t rows, int split) {
+  Step sp(P, RSVD_STEP_CONVERT);
+  sp.launched();
+  TRY(launch_to_bf16_t(x, rows, P->lp, P->xbf, tc_ld(rows), split,
+                       split ? tc_lo_offset(P->lp) : 0, P->st));
+  return RSVD_OK;
+}
+
 rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   const bool tc = P->opt.precision == RSVD_BF16_TC;
   if (tc) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
@@ -188,10 +246,10 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
   for (int j = 1; j <= P->q; ++j) {
-    if (tc) TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, tc_ld(P->m), 0, 0, P->st));
+    if (tc) TRYS(step_convert(P, P->qbuf, P->m, 0));
     TRYS(step_pass(P, A, 1, P->qbuf, false, &s, &stride));
     TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr));
-    if (tc) TRY(launch_to_bf16_t(P->qtbuf, P->n, P->lp, P->xbf, tc_ld(P->n), 0, 0, P->st));
+    if (tc) TRYS(step_convert(P, P->qtbuf, P->n, 0));
     TRYS(step_pass(P, A, 0, P->qtbuf, false, &s, &stride));
     TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
   }
@@ -202,12 +260,17 @@ rsvd_status_t stage_b(rsvd_plan_t P, const void* A, float* U, float* S, float* V
   const bool tc = P->opt.precision == RSVD_BF16_TC;
   int s;
   int64_t stride;
-  if (tc)
-    TRY(launch_to_bf16_t(P->qbuf, P->m, P->lp, P->xbf, tc_ld(P->m), 1, tc_lo_offset(P->lp), P->st));
+  if (tc) TRYS(step_convert(P, P->qbuf, P->m, 1));
   TRYS(step_pass(P, A, 1, P->qbuf, true, &s, &stride));      // B^T = A^T Q
   TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));  // B^T = Q_B R_B
-  TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
-                        P->st));
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched();
+    TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
+                          P->st));
+  }
+  Step sp(P, RSVD_STEP_LIFT);
+  sp.launched(2);
   TRY(launch_gemm_f32(0, P->m, P->k, P->lp, P->qbuf, P->lp, P->ut(), P->lp, U, P->k, 1, 0, P->st));
   TRY(launch_gemm_f32(0, P->n, P->k, P->lp, P->qtbuf, P->lp, P->w(), P->lp, V, P->k, 1, 0, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
@@ -408,6 +471,40 @@ rsvd_status_t rsvd_set_omega(rsvd_plan_t P, const float* Omega) {
 rsvd_status_t rsvd_sync(rsvd_plan_t P) {
   TRYS(check_plan(P));
   return take_status(P);
+}
+
+rsvd_status_t rsvd_profile(rsvd_plan_t P, uint32_t mask) {
+  TRYS(check_plan(P));
+  P->prof_mask = mask;
+  for (int k = 0; k < RSVD_NUM_STEPS; ++k) {
+    P->ev_used[k] = 0;
+    P->launches[k] = 0;
+  }
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_profile_read(rsvd_plan_t P, float* ms, int64_t* launches, int32_t nkinds) {
+  TRYS(check_plan(P));
+  if (nkinds < 0) return RSVD_ERR_INVALID_ARG;
+  TRY(cudaStreamSynchronize(P->st));
+  for (int k = 0; k < nkinds; ++k) {
+    if (k >= RSVD_NUM_STEPS) {
+      if (ms) ms[k] = 0.0f;
+      if (launches) launches[k] = 0;
+      continue;
+    }
+    if (ms) {
+      float tot = 0.0f;
+      for (int i = 0; i < P->ev_used[k]; ++i) {
+        float t = 0.0f;
+        TRY(cudaEventElapsedTime(&t, P->ev[k][i].first, P->ev[k][i].second));
+        tot += t;
+      }
+      ms[k] = tot;
+    }
+    if (launches) launches[k] = P->launches[k];
+  }
+  return RSVD_OK;
 }
 
 rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,

@@ -9,6 +9,9 @@
 // from zeta = (||x_q||^2 - ||x_p||^2) / (2 x_p . x_q), t = sign(zeta) /
 // (|zeta| + sqrt(1 + zeta^2)).  The same rotations accumulate in J, so that
 // X J = U diag(s) and X = U diag(s) J^T.  Sweeps stop when no pair rotates.
+// The accumulated J drifts from orthogonality by rounding (about 1e-5 after
+// the ~10 l rotations each column receives at l ~ 100); one Newton-Schulz
+// step W = J (3 I - J^T J) / 2 at the end brings it back to float32 level.
 #include <math.h>
 
 #include "common.cuh"
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
     const int r = e / lp, c = e % lp;
     if (r >= l || c >= l) { ut[e] = 0.0f; w[e] = 0.0f; }
   }
+  int* rank_of = reinterpret_cast<int*>(sig + le);  // [l]
   for (int c = warp; c < l; c += nw) {
     const float sc = sig[c];
     int rank = 0;
@@ -119,17 +123,35 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
     const float inv = sc > 0.0f ? 1.0f / sc : 0.0f;
-    for (int e = lane; e < l; e += 32) {
-      ut[(int64_t)e * lp + rank] = Xc[c * l + e] * inv;
-      w[(int64_t)e * lp + rank] = Jc[c * l + e];
+    for (int e = lane; e < l; e += 32) ut[(int64_t)e * lp + rank] = Xc[c * l + e] * inv;
+    if (lane == 0) {
+      s[rank] = sc;
+      rank_of[c] = rank;
     }
-    if (lane == 0) s[rank] = sc;
+  }
+  __syncthreads();
+  // Newton-Schulz: G = J^T J (into X's space), W = J (3 I - G) / 2
+  float* G = Xc;
+  for (int e = tid; e < l * l; e += nt) {
+    const int c1 = e / l, c2 = e % l;
+    const float* j1 = Jc + c1 * l;
+    const float* j2 = Jc + c2 * l;
+    float a = 0.f;
+    for (int r = 0; r < l; ++r) a = fmaf(j1[r], j2[r], a);
+    G[e] = a;
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += nt) {
+    const int c = e / l, r = e % l;  // entry r of column c of W
+    float a = 0.f;
+    for (int c2 = 0; c2 < l; ++c2) a = fmaf(Jc[c2 * l + r], G[c2 * l + c], a);
+    w[(int64_t)r * lp + rank_of[c]] = 1.5f * Jc[c * l + r] - 0.5f * a;
   }
 }
 
 }  // namespace
 
-size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + l + 2) * sizeof(float); }
+size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + 2 * l + 4) * sizeof(float); }
 
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp, float* ut,
                               float* s, float* w, uint32_t* status, cudaStream_t st) {

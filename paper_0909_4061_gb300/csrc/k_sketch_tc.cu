@@ -488,14 +488,17 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
     return -1;
   }
   tc->priv = b;
+  // the attribute must cover the largest of the launch configurations used
+  size_t sm = 0;
   for (int n_total : {lp, fold_ntotal(lp)}) {
-    const size_t sm = smem_bytes(n_total, pick_stages(n_total));
-    if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm) != cudaSuccess ||
-        cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm) != cudaSuccess)
-      return -1;
+    const size_t need = smem_bytes(n_total, pick_stages(n_total));
+    if (need > sm) sm = need;
   }
+  if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess ||
+      cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess)
+    return -1;
   tc->ready = true;
   return 0;
 }
