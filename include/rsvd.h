@@ -137,6 +137,14 @@ RSVD_API const char* rsvd_status_string(rsvd_status_t status);
 
 /* ---- tracing ----------------------------------------------------------- */
 
+/* Diagnostics of the device-side work since the previous call (waits for the
+ * plan's stream): out[0] = status bits seen, including the informational ones
+ * (4: a Cholesky pivot was replaced by the floor because the sample is
+ * numerically rank deficient; 16: the Jacobi sweeps hit their limit); out[1] =
+ * the largest number of Jacobi sweeps taken by one small SVD.  n is the length
+ * of out (<= 2 entries are written); out[1] is reset. */
+RSVD_API rsvd_status_t rsvd_diagnostics(rsvd_plan_t plan, uint32_t* out, int32_t n);
+
 /* Step kinds for per-step timing and launch counts. */
 enum {
   RSVD_STEP_DRAW = 0,       /* test matrix (Algorithm 4.1 step 1) */

@@ -36,6 +36,7 @@ EXPORTS = (
     "rsvd_range_finder", "rsvd_svd", "rsvd_svd_host", "rsvd_svd_backward", "rsvd_get_omega",
     "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
+    "rsvd_diagnostics",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -90,6 +91,7 @@ _SIGS = {
     "rsvd_small_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
     "rsvd_profile": (_c.c_int, [_P, _c.c_uint32]),
     "rsvd_profile_read": (_c.c_int, [_P, _P, _P, _c.c_int32]),
+    "rsvd_diagnostics": (_c.c_int, [_P, _P, _c.c_int32]),
 }
 
 
@@ -236,6 +238,13 @@ def rsvd_profile_read(plan):
     _check(lib().rsvd_profile_read(plan, ms, cnt, RSVD_NUM_STEPS), "rsvd_profile_read")
     return ({STEP_NAMES[i]: ms[i] for i in range(RSVD_NUM_STEPS)},
             {STEP_NAMES[i]: cnt[i] for i in range(RSVD_NUM_STEPS)})
+
+
+def rsvd_diagnostics(plan):
+    """Returns (status bits seen, largest Jacobi sweep count) since the last call."""
+    out = (ctypes.c_uint32 * 2)()
+    _check(lib().rsvd_diagnostics(plan, out, 2), "rsvd_diagnostics")
+    return int(out[0]), int(out[1])
 
 
 # ---- torch conveniences -------------------------------------------------------------

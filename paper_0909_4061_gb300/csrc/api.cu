@@ -267,7 +267,7 @@ rsvd_status_t stage_b(rsvd_plan_t P, const void* A, float* U, float* S, float* V
     Step sp(P, RSVD_STEP_SMALL_SVD);
     sp.launched();
     TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
-                          P->st));
+                          P->status + 1, P->st));
   }
   Step sp(P, RSVD_STEP_LIFT);
   sp.launched(2);
@@ -473,6 +473,17 @@ rsvd_status_t rsvd_sync(rsvd_plan_t P) {
   return take_status(P);
 }
 
+rsvd_status_t rsvd_diagnostics(rsvd_plan_t P, uint32_t* out, int32_t n) {
+  TRYS(check_plan(P));
+  if (!out || n < 0) return RSVD_ERR_INVALID_ARG;
+  uint32_t w[2] = {0, 0};
+  TRY(cudaMemcpyAsync(w, P->status, sizeof(w), cudaMemcpyDeviceToHost, P->st));
+  TRY(cudaStreamSynchronize(P->st));
+  TRY(cudaMemsetAsync(P->status + 1, 0, sizeof(uint32_t), P->st));
+  for (int i = 0; i < n && i < 2; ++i) out[i] = w[i];
+  return RSVD_OK;
+}
+
 rsvd_status_t rsvd_profile(rsvd_plan_t P, uint32_t mask) {
   TRYS(check_plan(P));
   P->prof_mask = mask;
@@ -550,7 +561,8 @@ rsvd_status_t rsvd_small_svd(rsvd_plan_t P, const float* X, float* Ut, float* S,
   TRYS(check_plan(P));
   if (!X || !Ut || !S || !W) return RSVD_ERR_INVALID_ARG;
   TRY(launch_gather(X, 1, 0, P->l, P->sq(), P->lp, P->l, P->l, P->lp, P->st));
-  TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->status, P->st));
+  TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
+                        P->status + 1, P->st));
   TRY(launch_gather(P->ut(), 1, 0, P->lp, Ut, P->l, P->l, P->l, P->l, P->st));
   TRY(launch_gather(P->w(), 1, 0, P->lp, W, P->l, P->l, P->l, P->l, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->l, cudaMemcpyDeviceToDevice, P->st));

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
                                                       int transposed, int l, int lp,
                                                       float* __restrict__ ut, float* __restrict__ s,
                                                       float* __restrict__ w, uint32_t* status,
-                                                      float tol) {
+                                                      uint32_t* info, float tol) {
   extern __shared__ __align__(16) float sm[];
   const int le = l + (l & 1);
   float* Xc = sm;                   // [l][l]: Xc[c][e] = X(e, c)
@@ -75,20 +75,24 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
         float t = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(az, az, 1.0f)));
         t = copysignf(t, zeta);
         if (zeta == 0.0f) t = 1.0f;
-        // correctly rounded 1/sqrt: an approximate reciprocal square root biases every
-        // rotation the same way and the column norms drift over hundreds of rotations
+        // c = cos, sn = sin, tau = tan(angle/2) = sn / (1 + c).  The update is written
+        // x_p - sn (x_q + tau x_p), x_q + sn (x_p - tau x_q) (Rutishauser): for a tiny
+        // angle c rounds to 1 and the plain (c, sn) form would grow both norms by t^2
+        // at every rotation, a bias that accumulates over a sweep; this form keeps the
+        // rotation orthogonal to O(t^4).  c itself is correctly rounded (1 / sqrtf).
         const float c = 1.0f / sqrtf(fmaf(t, t, 1.0f));
         const float sn = c * t;
+        const float tau = sn / (1.0f + c);
         if (lane == 0) s_rot = 1;
         float* jp = Jc + p * l;
         float* jq = Jc + q * l;
         for (int e = lane; e < l; e += 32) {
           const float u = xp[e], v = xq[e];
-          xp[e] = c * u - sn * v;
-          xq[e] = fmaf(sn, u, c * v);
+          xp[e] = u - sn * fmaf(tau, u, v);
+          xq[e] = v + sn * fmaf(-tau, v, u);
           const float uj = jp[e], vj = jq[e];
-          jp[e] = c * uj - sn * vj;
-          jq[e] = fmaf(sn, uj, c * vj);
+          jp[e] = uj - sn * fmaf(tau, uj, vj);
+          jq[e] = vj + sn * fmaf(-tau, vj, uj);
         }
       }
       __syncthreads();
@@ -97,7 +101,10 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
     __syncthreads();
     if (!rot) break;
   }
-  if (sweep == kMaxSweeps && tid == 0) set_status(status, ST_JACOBI_NOCONV);
+  if (tid == 0) {
+    if (sweep == kMaxSweeps) set_status(status, ST_JACOBI_NOCONV);
+    if (info) atomicMax(info, (uint32_t)(sweep + 1));
+  }
 
   // singular values = column norms
   for (int c = warp; c < l; c += nw) {
@@ -154,14 +161,18 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
 size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + 2 * l + 4) * sizeof(float); }
 
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp, float* ut,
-                              float* s, float* w, uint32_t* status, cudaStream_t st) {
+                              float* s, float* w, uint32_t* status, uint32_t* info,
+                              cudaStream_t st) {
   if (l > kMaxJacobiL) return cudaErrorInvalidValue;
   const size_t smem = jacobi_smem_bytes(l);
   cudaError_t e =
       cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const float tol = 2.0f * sqrtf((float)l) * kEpsF32;
-  jacobi_kernel<<<1, 1024, smem, st>>>(x, ldx, transposed, l, lp, ut, s, w, status, tol);
+  // a pair counts as orthogonal below 8 sqrt(l) u: above the float32 rounding floor of
+  // a computed dot product (a few u sqrt(l)), so the sweeps terminate, and small enough
+  // that U is orthonormal to ~5e-6 at l ~ 100
+  const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
+  jacobi_kernel<<<1, 1024, smem, st>>>(x, ldx, transposed, l, lp, ut, s, w, status, info, tol);
   return cudaGetLastError();
 }
 

@@ -248,6 +248,177 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
   }
 }
 
+// Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA, both held in shared
+// memory as full squares (row stride lp + 1), for lp <= 160.  Block columns of
+// NB = 32: the diagonal block is factored by warp 0, the panel below it by one
+// thread per row (forward substitution), the trailing lower triangle by all
+// threads; the inverse takes the diagonal blocks' inverses (one warp each, in
+// parallel) and then the block rows below them in order.  Outputs as in
+// cholesky_kernel: R = L^T, R^-1 = X^T, the optional product racc <- R racc.
+constexpr int CB = 32;
+
+__global__ void __launch_bounds__(1024) cholesky_blocked_kernel(
+    const float* __restrict__ g, int l, int lp, int shifted, float* __restrict__ r_out,
+    float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status) {
+  extern __shared__ __align__(16) float sm[];
+  const int ld = lp + 1;
+  float* A = sm;               // lower: L
+  float* X = sm + lp * ld;     // lower: L^-1
+  __shared__ float s_red[2][32];
+  __shared__ float s_shift, s_floor;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e / l, j = e % l;
+    if (j <= i) A[i * ld + j] = g[(int64_t)i * lp + j];
+    X[i * ld + j] = 0.0f;
+  }
+  float tr = 0.0f, mx = 0.0f;
+  bool bad = false;
+  for (int i = tid; i < l; i += nt) {
+    const float d = g[(int64_t)i * lp + i];
+    if (!isfinite(d)) bad = true;
+    tr += d;
+    mx = fmaxf(mx, d);
+  }
+  if (bad) set_status(status, ST_NONFINITE);
+  tr = warp_sum(tr);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) { s_red[0][warp] = tr; s_red[1][warp] = mx; }
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f, m = 0.0f;
+    for (int w = 0; w < nw; ++w) { t += s_red[0][w]; m = fmaxf(m, s_red[1][w]); }
+    s_shift = shifted ? (float)l * kEpsF32 * t : 0.0f;
+    s_floor = fmaxf((float)l * kEpsF32 * m, 1e-30f);
+  }
+  __syncthreads();
+  const float pfloor = s_floor;
+  for (int i = tid; i < l; i += nt) A[i * ld + i] += s_shift;
+  __syncthreads();
+
+  for (int J = 0; J < l; J += CB) {
+    const int nb = min(CB, l - J);
+    // (1) diagonal block, one warp, lane i owns row J + i
+    if (warp == 0) {
+      for (int j = 0; j < nb; ++j) {
+        float d = A[(J + j) * ld + J + j];
+        if (!(d > pfloor)) {
+          if (lane == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
+          d = pfloor;
+        }
+        const float piv = sqrtf(d);
+        const float rp = 1.0f / piv;
+        __syncwarp();
+        if (lane > j && lane < nb) A[(J + lane) * ld + J + j] *= rp;
+        if (lane == j) A[(J + j) * ld + J + j] = piv;
+        __syncwarp();
+        if (lane > j && lane < nb) {
+          const float lij = A[(J + lane) * ld + J + j];
+          for (int k = j + 1; k <= lane; ++k)
+            A[(J + lane) * ld + J + k] -= lij * A[(J + k) * ld + J + j];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (2) panel rows below: x L_JJ^T = a  (forward substitution, one thread per row)
+    for (int i = J + nb + tid; i < l; i += nt) {
+      float* ai = A + i * ld + J;
+      for (int j = 0; j < nb; ++j) {
+        const float* lj = A + (J + j) * ld + J;
+        float v = ai[j];
+        for (int k = 0; k < j; ++k) v -= ai[k] * lj[k];
+        ai[j] = v / lj[j];
+      }
+    }
+    __syncthreads();
+    // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ
+    const int s0 = J + nb, sz = l - s0;
+    for (int e = tid; e < sz * sz; e += nt) {
+      const int i = s0 + e / sz, k = s0 + e % sz;
+      if (k > i) continue;
+      const float* li = A + i * ld + J;
+      const float* lk = A + k * ld + J;
+      float acc = 0.0f;
+      for (int j = 0; j < nb; ++j) acc = fmaf(li[j], lk[j], acc);
+      A[i * ld + k] -= acc;
+    }
+    __syncthreads();
+  }
+
+  // inverse: diagonal blocks first (one warp per block, lane c owns column c)
+  const int nblk = (l + CB - 1) / CB;
+  for (int b = warp; b < nblk; b += nw) {
+    const int J = b * CB, nb = min(CB, l - J);
+    if (lane < nb) {
+      const int c = lane;
+      X[(J + c) * ld + J + c] = 1.0f / A[(J + c) * ld + J + c];
+      for (int i = c + 1; i < nb; ++i) {
+        float v = 0.0f;
+        for (int k = c; k < i; ++k) v = fmaf(A[(J + i) * ld + J + k], X[(J + k) * ld + J + c], v);
+        X[(J + i) * ld + J + c] = -v / A[(J + i) * ld + J + i];
+      }
+    }
+  }
+  __syncthreads();
+  // block rows below the diagonal, in order: X_IJ = -X_II sum_{J<=K<I} L_IK X_KJ
+  float* T = X;  // the strictly-lower blocks of row I are written after their inputs are read
+  for (int Ib = 1; Ib < nblk; ++Ib) {
+    const int I = Ib * CB, ni = min(CB, l - I);
+    // stage 1: S = sum_{K} L_IK X_KJ for every column c < I, rows I..I+ni, into A's upper part
+    // (A's strictly upper triangle is free scratch): S(r, c) stored at A[c * ld + I + r]
+    for (int e = tid; e < ni * I; e += nt) {
+      const int r = e / I, c = e % I;
+      const int Jc = (c / CB) * CB;
+      float v = 0.0f;
+      for (int k = Jc + (c - Jc); k < I; ++k) v = fmaf(A[(I + r) * ld + k], X[k * ld + c], v);
+      A[c * ld + I + r] = v;
+    }
+    __syncthreads();
+    // stage 2: X(I + r, c) = -sum_t X_II(r, t) S(t, c)
+    for (int e = tid; e < ni * I; e += nt) {
+      const int r = e / I, c = e % I;
+      float v = 0.0f;
+      for (int t2 = 0; t2 <= r; ++t2) v = fmaf(X[(I + r) * ld + I + t2], A[c * ld + I + t2], v);
+      T[(I + r) * ld + c] = -v;
+    }
+    __syncthreads();
+  }
+
+  // outputs: R = L^T, R^-1 = X^T, zero padding
+  for (int e = tid; e < lp * lp; e += nt) {
+    const int a = e / lp, b = e % lp;
+    const bool up = (a < l && b < l && b >= a);
+    r_out[e] = up ? A[b * ld + a] : 0.0f;
+    rinv[e] = up ? X[b * ld + a] : 0.0f;
+  }
+  if (racc) {
+    __syncthreads();
+    // racc <- R racc (upper triangular product), computed into the free X space
+    float* Pm = X;
+    for (int e = tid; e < l * l; e += nt) {
+      const int a = e / l, b = e % l;
+      float v = 0.0f;
+      if (b >= a) {
+        if (racc_init) {
+          v = A[b * ld + a];
+        } else {
+          for (int c = a; c <= b; ++c) v = fmaf(A[c * ld + a], racc[(int64_t)c * lp + b], v);
+        }
+      }
+      Pm[a * ld + b] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < lp * lp; e += nt) {
+      const int a = e / lp, b = e % lp;
+      racc[e] = (a < l && b < l && b >= a) ? Pm[a * ld + b] : 0.0f;
+    }
+  }
+}
+
 __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int lp,
                                  __nv_bfloat16* __restrict__ out, int64_t ld_t, int split,
                                  int lo_off) {
@@ -301,8 +472,8 @@ __global__ void gather_kernel(const float* __restrict__ src, int splits, int64_t
 }  // namespace
 
 int gram_blocks(int64_t rows) {
-  const int64_t b = cdiv(rows, 64);
-  return (int)(b < 2 * kNumSMs ? (b < 1 ? 1 : b) : 2 * kNumSMs);
+  const int64_t b = cdiv(rows, 128);
+  return (int)(b < kNumSMs ? (b < 1 ? 1 : b) : kNumSMs);
 }
 
 cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stride, float* y_out,
@@ -327,6 +498,15 @@ cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, c
 cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,
                             float* rinv, float* racc, int racc_init, uint32_t* status,
                             cudaStream_t st) {
+  if (lp <= 160) {
+    const size_t sm = (size_t)2 * lp * (lp + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cholesky_blocked_kernel<<<1, 1024, sm, st>>>(g, l, lp, shifted, r_out, rinv, racc, racc_init,
+                                                 status);
+    return cudaGetLastError();
+  }
   const size_t smem = ((size_t)l * (l + 1) / 2 + l + 4 + kMaxL) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

@@ -48,8 +48,10 @@ cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64
 
 // One-sided Jacobi SVD of X = R^T (transposed = 1, R row-major l x l, ld) or X (transposed = 0).
 // Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
+// info (may be null): atomicMax of the number of sweeps taken.
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp,
-                              float* ut, float* s, float* w, uint32_t* status, cudaStream_t st);
+                              float* ut, float* s, float* w, uint32_t* status, uint32_t* info,
+                              cudaStream_t st);
 size_t jacobi_smem_bytes(int l);
 
 // dst[r][c] = sum_{s < splits} src[s][r][c] for c < cols, 0 for cols <= c < cols_pad

@@ -159,6 +159,8 @@ def test_small_svd_matches_lapack(rsvd_lib, l):
         S = torch.zeros(l, device="cuda")
         rsvd_lib.rsvd_small_svd(pl.handle, _dev(x), Ut, S, W)
         torch.cuda.synchronize()
+        bits, sweeps = rsvd_lib.rsvd_diagnostics(pl.handle)
+    assert sweeps < 40 and not bits & 16, (bits, sweeps)      # converged before the sweep limit
     ut, s, w = _np(Ut), _np(S), _np(W)
     x64 = x.astype(np.float64)
     uu, ss, vt = np.linalg.svd(x64)
