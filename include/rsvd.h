@@ -200,6 +200,41 @@ RSVD_API rsvd_status_t rsvd_orthonormalize(rsvd_plan_t plan, int64_t rows, float
 RSVD_API rsvd_status_t rsvd_small_svd(rsvd_plan_t plan, const float* X, float* Ut, float* S,
                              float* W);
 
+/* ---- allocation-free pass ------------------------------------------------ */
+
+/* One tensor-core pass over a bfloat16 A without allocating any memory:
+ * Y = A X (transpose = 0) or Y = A^T X (transpose = 1).  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a service whose device memory is carved up once at start-up by
+ * its own allocator, code that runs while a stream is being captured into a
+ * CUDA graph, or a latency-critical loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  It needs no plan.
+ *
+ *   A:  device bfloat16, m x n row-major, leading dimension lda (multiple of 8,
+ *       16-byte-aligned base).
+ *   Xt: device bfloat16, the operand stored transposed: l rows of K elements
+ *       (K = n when transpose = 0, m when transpose = 1), leading dimension
+ *       ldxt >= K, a multiple of 8, 16-byte-aligned base.
+ *   l:  a multiple of 16, 16 <= l <= 128.
+ *   Y:  device float32, (transpose ? n : m) x l row-major, leading dimension l.
+ *   status: device word that receives a timeout bit (8) if a bounded wait
+ *       expires; may be NULL.
+ * Sizes outside these limits return RSVD_ERR_INVALID_ARG before any work.
+ *
+ * The scratch it needs (partial sums of output row tiles shared by two CTAs
+ * and their hand-over flags) is a fixed static device array of 152 x 128 x
+ * 128 floats (9.5 MiB) plus 152 words, held by every GPU that loads the
+ * library until the process exits.  The first call on a device sets it up
+ * (looks up the array's device address and the kernel's shared-memory limit),
+ * so make that first call before any stream capture.  Every call shares the
+ * array: calls whose kernels overlap on the GPU (other streams, other threads)
+ * race on it and give wrong results; order them on one stream.  The call is
+ * asynchronous on `stream`. */
+RSVD_API rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int64_t n,
+                                                int64_t lda, int32_t transpose, const void* Xt,
+                                                int64_t ldxt, int32_t l, float* Y,
+                                                uint32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

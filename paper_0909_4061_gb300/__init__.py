@@ -36,7 +36,7 @@ EXPORTS = (
     "rsvd_range_finder", "rsvd_svd", "rsvd_svd_host", "rsvd_svd_backward", "rsvd_get_omega",
     "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
-    "rsvd_diagnostics",
+    "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -92,6 +92,8 @@ _SIGS = {
     "rsvd_profile": (_c.c_int, [_P, _c.c_uint32]),
     "rsvd_profile_read": (_c.c_int, [_P, _P, _P, _c.c_int32]),
     "rsvd_diagnostics": (_c.c_int, [_P, _P, _c.c_int32]),
+    "rsvd_sketch_bf16_noalloc": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32, _P,
+                                            _c.c_int64, _c.c_int32, _P, _P, _P]),
 }
 
 
@@ -245,6 +247,13 @@ def rsvd_diagnostics(plan):
     out = (ctypes.c_uint32 * 2)()
     _check(lib().rsvd_diagnostics(plan, out, 2), "rsvd_diagnostics")
     return int(out[0]), int(out[1])
+
+
+def rsvd_sketch_bf16_noalloc(A, m, n, lda, transpose, Xt, ldxt, l, Y, status=None, stream=None):
+    """One tensor-core pass that allocates nothing (see include/rsvd.h)."""
+    _check(lib().rsvd_sketch_bf16_noalloc(_ptr(A), int(m), int(n), int(lda), int(transpose),
+                                          _ptr(Xt), int(ldxt), int(l), _ptr(Y), _ptr(status),
+                                          _stream(stream)), "rsvd_sketch_bf16_noalloc")
 
 
 # ---- torch conveniences -------------------------------------------------------------

@@ -559,3 +559,113 @@ void tc_plan_destroy(TcPlan* tc) {
 }
 
 }  // namespace rsvd
+
+// ---------------------------------------------------------------------------
+// Allocation-free pass (rsvd_sketch_bf16_noalloc)
+//
+// The same kernel as tc_pass, for callers that cannot allocate device memory.
+// Its stream-K scratch -- the partial sums of row tiles that two CTAs share
+// and the flags that hand them over -- lives in file-scope device arrays of a
+// fixed size (g_noalloc_slots: 152 CTAs x 128 rows x 128 columns of float32,
+// 9.5 MiB; g_noalloc_flags: 152 words), which every GPU that loads the library
+// keeps until the process exits.  Host code must not hand these symbols to a
+// kernel (on the host they are stand-ins, not device addresses): the set-up
+// below asks the runtime for their device addresses, once per device.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace rsvd {
+namespace {
+
+constexpr int kNoAllocMaxCtas = 152;
+constexpr int kNoAllocMaxL = 128;
+
+__device__ __align__(256) float g_noalloc_slots[(size_t)kNoAllocMaxCtas * BM * kNoAllocMaxL];
+__device__ __align__(256) uint32_t g_noalloc_flags[kNoAllocMaxCtas];
+
+struct NoAllocDevice {
+  bool ready = false;
+  float* slots = nullptr;
+  uint32_t* flags = nullptr;
+  int num_sms = 0;
+};
+
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: device addresses of the scratch
+// arrays, the SM count, and the shared-memory limit of both kernel variants.
+int noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return -1;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_slots) != cudaSuccess) return -1;
+    d.slots = static_cast<float*>(p);
+    if (cudaGetSymbolAddress(&p, g_noalloc_flags) != cudaSuccess) return -1;
+    d.flags = static_cast<uint32_t*>(p);
+    if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return -1;
+    size_t need = 0;
+    for (int l = 16; l <= kNoAllocMaxL; l += 16) {
+      const size_t s = smem_bytes(l, pick_stages(l));
+      if (s > need) need = s;
+    }
+    if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)need) != cudaSuccess ||
+        cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)need) != cudaSuccess)
+      return -1;
+    d.ready = true;
+  }
+  *out = &d;
+  return 0;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int64_t n,
+                                                  int64_t lda, int32_t transpose, const void* Xt,
+                                                  int64_t ldxt, int32_t l, float* Y,
+                                                  uint32_t* status, void* stream) {
+  using namespace rsvd;
+  if (!A || !Xt || !Y || m < 1 || n < 1) return RSVD_ERR_INVALID_ARG;
+  if (l < 16 || l > kNoAllocMaxL || l % 16 != 0) return RSVD_ERR_INVALID_ARG;
+  const int64_t K = transpose ? m : n;
+  if (lda < n || lda % 8 != 0 || ldxt < K || ldxt % 8 != 0) return RSVD_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(Xt) & 15))
+    return RSVD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RSVD_ERR_CUDA;
+  NoAllocDevice* d = nullptr;
+  if (noalloc_setup(dev, &d) != 0) return RSVD_ERR_CUDA;
+  alignas(64) unsigned char map_a[128];
+  alignas(64) unsigned char map_x[128];
+  if (encode_2d(map_a, A, n, m, lda, BK, transpose ? 64 : BM)) return RSVD_ERR_CUDA;
+  if (encode_2d(map_x, Xt, K, l, ldxt, BK, l)) return RSVD_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t M = transpose ? n : m;
+  const int kt = (int)cdiv(K, BK);
+  const int64_t total = cdiv(M, BM) * kt;
+  int grid = d->num_sms < kNoAllocMaxCtas ? d->num_sms : kNoAllocMaxCtas;
+  if (total < grid) grid = (int)total;
+  // the flags must start at zero (the kernel clears the ones it consumes, but a
+  // call that gave up on a wait can leave some set)
+  if (cudaMemsetAsync(d->flags, 0, sizeof(uint32_t) * kNoAllocMaxCtas, st) != cudaSuccess)
+    return RSVD_ERR_CUDA;
+  const int stages = pick_stages(l);
+  const size_t sm = smem_bytes(l, stages);
+  const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(map_a);
+  const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(map_x);
+  if (transpose)
+    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
+                                                    d->slots, d->flags, status);
+  else
+    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
+                                                    d->slots, d->flags, status);
+  return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
