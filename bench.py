@@ -402,6 +402,27 @@ def run_pass_probe(args):
     print(json.dumps({"pass_probe": "ok", "m": m, "n": n, "l": k + p}))
 
 
+def run_small_probe(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0909_4061_gb300 as pkg
+
+    m = n = 8192
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    # decaying spectrum without a QR: Gaussian times a graded diagonal
+    A = (torch.randn(m, n, generator=gen, device="cuda")
+         * torch.arange(1, n + 1, device="cuda").pow(-1.5)).to(torch.bfloat16)
+    with pkg.Plan(m, n, 100, 10, 1, 3, pkg.RSVD_BF16_TC) as pl:
+        for _ in range(2):
+            pl.svd(A)
+        bits, sweeps = pkg.rsvd_diagnostics(pl.handle)
+    print(json.dumps({"small_probe": "ok", "m": m, "n": n, "l": 110, "jacobi_sweeps": sweeps}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -452,12 +473,18 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="timed pipeline only (no clock-load loop, e2e, FP32 leg or CPU baseline): "
                          "the command the ncu launch list is taken on")
+    ap.add_argument("--small-probe", action="store_true",
+                    help="two rank-100 SVDs (l = 110) of an 8192 x 8192 bf16 matrix: the small case "
+                         "for full ncu captures of the orthonormalisation and small-SVD kernels")
     ap.add_argument("--pass-probe", action="store_true",
                     help="three launches of the tensor-core pass kernel on an 8192 x 16384 bf16 A "
                          "(268 MB, larger than L2): the small case for full ncu captures")
     args = ap.parse_args()
     if args.pass_probe:
         run_pass_probe(args)
+        return
+    if args.small_probe:
+        run_small_probe(args)
         return
     if args.profile_run:
         args.no_e2e = args.no_cpu = True

@@ -4,7 +4,7 @@
 //
 // One-sided (Hestenes) Jacobi in one CTA: the columns of X live in shared
 // memory; each sweep visits every column pair once in the round-robin
-// ("circle") order, l/2 disjoint pairs per round, one warp per pair.  A pair
+// ("circle") order, l/2 disjoint pairs per round, one half-warp per pair.  A pair
 // (p, q) is rotated when |x_p . x_q| > tol ||x_p|| ||x_q||, with the angle
 // from zeta = (||x_q||^2 - ||x_p||^2) / (2 x_p . x_q), t = sign(zeta) /
 // (|zeta| + sqrt(1 + zeta^2)).  The same rotations accumulate in J, so that
@@ -48,45 +48,51 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
   }
   __syncthreads();
 
+  // one half-warp (16 lanes) per column pair: 64 pairs in flight per round
+  const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;
+  const unsigned hmask = 0xFFFFu << (lane & 16);
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < le - 1; ++round) {
-      for (int slot = warp; slot < le / 2; slot += nw) {
+      for (int slot = hw; slot < le / 2; slot += nhw) {
         const int p = rr_player(slot, round, le);
         const int q = rr_player(le - 1 - slot, round, le);
-        if (p >= l || q >= l) continue;
+        if (p >= l || q >= l) continue;           // the whole half-warp skips together
         float* xp = Xc + p * l;
         float* xq = Xc + q * l;
         float a = 0.f, b = 0.f, g = 0.f;
-        for (int e = lane; e < l; e += 32) {
+        for (int e = hl; e < l; e += 16) {
           const float u = xp[e], v = xq[e];
           a = fmaf(u, u, a);
           b = fmaf(v, v, b);
           g = fmaf(u, v, g);
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g == 0.0f || !(fabsf(g) > tol * sqrtf(a) * sqrtf(b))) continue;
-        const float zeta = (b - a) / (2.0f * g);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(hmask, a, o);
+          b += __shfl_xor_sync(hmask, b, o);
+          g += __shfl_xor_sync(hmask, g, o);
+        }
+        if (g == 0.0f || !(fabsf(g) > tol * sqrtf(a * b))) continue;
+        // the angle only needs to be close (any angle gives an orthogonal update):
+        // fast divisions; cos and tan(angle/2) must be accurate so that the update stays
+        // orthogonal (rsqrt refined by one Newton step, an IEEE division for tau)
+        const float zeta = __fdividef(b - a, 2.0f * g);
         const float az = fabsf(zeta);
-        float t = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(az, az, 1.0f)));
+        float t = (az > 1e18f) ? __fdividef(0.5f, az) : __fdividef(1.0f, az + sqrtf(fmaf(az, az, 1.0f)));
         t = copysignf(t, zeta);
         if (zeta == 0.0f) t = 1.0f;
-        // c = cos, sn = sin, tau = tan(angle/2) = sn / (1 + c).  The update is written
-        // x_p - sn (x_q + tau x_p), x_q + sn (x_p - tau x_q) (Rutishauser): for a tiny
-        // angle c rounds to 1 and the plain (c, sn) form would grow both norms by t^2
-        // at every rotation, a bias that accumulates over a sweep; this form keeps the
-        // rotation orthogonal to O(t^4).  c itself is correctly rounded (1 / sqrtf).
-        const float c = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+        const float w2 = fmaf(t, t, 1.0f);
+        float c = rsqrtf(w2);
+        c = c * fmaf(-0.5f * w2, c * c, 1.5f);
         const float sn = c * t;
         const float tau = sn / (1.0f + c);
-        if (lane == 0) s_rot = 1;
+        if (hl == 0) s_rot = 1;
         float* jp = Jc + p * l;
         float* jq = Jc + q * l;
-        for (int e = lane; e < l; e += 32) {
+        for (int e = hl; e < l; e += 16) {
           const float u = xp[e], v = xq[e];
           xp[e] = u - sn * fmaf(tau, u, v);
           xq[e] = v + sn * fmaf(-tau, v, u);

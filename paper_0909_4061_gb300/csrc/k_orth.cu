@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 // cholesky_kernel: R = L^T, R^-1 = X^T, the optional product racc <- R racc.
 constexpr int CB = 32;
 
-__global__ void __launch_bounds__(1024) cholesky_blocked_kernel(
+__global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     const float* __restrict__ g, int l, int lp, int shifted, float* __restrict__ r_out,
     float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status) {
   extern __shared__ __align__(16) float sm[];
@@ -301,38 +301,69 @@ __global__ void __launch_bounds__(1024) cholesky_blocked_kernel(
 
   for (int J = 0; J < l; J += CB) {
     const int nb = min(CB, l - J);
-    // (1) diagonal block, one warp, lane i owns row J + i
+    // (1) diagonal block by warp 0, in registers: lane i holds row i (identity padding
+    // beyond nb); then the block's inverse, lane c holding column c.
     if (warp == 0) {
-      for (int j = 0; j < nb; ++j) {
-        float d = A[(J + j) * ld + J + j];
-        if (!(d > pfloor)) {
+      float a[CB];
+#pragma unroll
+      for (int j = 0; j < CB; ++j)
+        a[j] = (lane < nb && j < nb) ? (j <= lane ? A[(J + lane) * ld + J + j] : 0.0f)
+                                     : (j == lane ? 1.0f : 0.0f);
+#pragma unroll
+      for (int j = 0; j < CB; ++j) {
+        float d = __shfl_sync(0xffffffffu, a[j], j);
+        if (j < nb && !(d > pfloor)) {
           if (lane == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
           d = pfloor;
         }
         const float piv = sqrtf(d);
         const float rp = 1.0f / piv;
-        __syncwarp();
-        if (lane > j && lane < nb) A[(J + lane) * ld + J + j] *= rp;
-        if (lane == j) A[(J + j) * ld + J + j] = piv;
-        __syncwarp();
-        if (lane > j && lane < nb) {
-          const float lij = A[(J + lane) * ld + J + j];
-          for (int k = j + 1; k <= lane; ++k)
-            A[(J + lane) * ld + J + k] -= lij * A[(J + k) * ld + J + j];
+        const float lij = (lane == j) ? piv : (lane > j ? a[j] * rp : 0.0f);
+        a[j] = lij;
+#pragma unroll
+        for (int k = j + 1; k < CB; ++k) {
+          const float lkj = __shfl_sync(0xffffffffu, lij, k);
+          if (lane >= k) a[k] = fmaf(-lij, lkj, a[k]);
         }
-        __syncwarp();
+      }
+      // inverse, column c = lane: x_cc = 1 / l_cc, x_ic = -(sum_{c<=k<i} l_ik x_kc) / l_ii
+      float x[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        float v = 0.0f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) {
+          const float lik = __shfl_sync(0xffffffffu, a[k], i);
+          if (k >= lane) v = fmaf(lik, x[k], v);
+        }
+        const float lii = __shfl_sync(0xffffffffu, a[i], i);
+        x[i] = (i > lane) ? -v / lii : (i == lane ? 1.0f / lii : 0.0f);
+      }
+      if (lane < nb) {
+#pragma unroll
+        for (int j = 0; j < CB; ++j)
+          if (j < nb && j <= lane) A[(J + lane) * ld + J + j] = a[j];
+#pragma unroll
+        for (int i = 0; i < CB; ++i)
+          if (i < nb && i >= lane) X[(J + i) * ld + J + lane] = x[i];
       }
     }
     __syncthreads();
-    // (2) panel rows below: x L_JJ^T = a  (forward substitution, one thread per row)
-    for (int i = J + nb + tid; i < l; i += nt) {
-      float* ai = A + i * ld + J;
-      for (int j = 0; j < nb; ++j) {
-        const float* lj = A + (J + j) * ld + J;
-        float v = ai[j];
-        for (int k = 0; k < j; ++k) v -= ai[k] * lj[k];
-        ai[j] = v / lj[j];
-      }
+    // (2) panel rows below: L_iJ = A_iJ L_JJ^-T, i.e. l_ij = sum_{k<=j} a_ik X_JJ(j, k)
+    const int prow = l - J - nb;
+    for (int e = tid; e < prow * nb; e += nt) {
+      const int i = J + nb + e / nb, j = e % nb;
+      const float* ai = A + i * ld + J;
+      const float* xj = X + (J + j) * ld + J;
+      float v = 0.0f;
+      for (int k = 0; k <= j; ++k) v = fmaf(ai[k], xj[k], v);
+      X[i * ld + J + j] = v;          // staged in X's strictly-lower part (free until the inverse)
+    }
+    __syncthreads();
+    for (int e = tid; e < prow * nb; e += nt) {
+      const int i = J + nb + e / nb, j = e % nb;
+      A[i * ld + J + j] = X[i * ld + J + j];
+      X[i * ld + J + j] = 0.0f;
     }
     __syncthreads();
     // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ
@@ -348,22 +379,8 @@ __global__ void __launch_bounds__(1024) cholesky_blocked_kernel(
     }
     __syncthreads();
   }
-
-  // inverse: diagonal blocks first (one warp per block, lane c owns column c)
   const int nblk = (l + CB - 1) / CB;
-  for (int b = warp; b < nblk; b += nw) {
-    const int J = b * CB, nb = min(CB, l - J);
-    if (lane < nb) {
-      const int c = lane;
-      X[(J + c) * ld + J + c] = 1.0f / A[(J + c) * ld + J + c];
-      for (int i = c + 1; i < nb; ++i) {
-        float v = 0.0f;
-        for (int k = c; k < i; ++k) v = fmaf(A[(J + i) * ld + J + k], X[(J + k) * ld + J + c], v);
-        X[(J + i) * ld + J + c] = -v / A[(J + i) * ld + J + i];
-      }
-    }
-  }
-  __syncthreads();
+
   // block rows below the diagonal, in order: X_IJ = -X_II sum_{J<=K<I} L_IK X_KJ
   float* T = X;  // the strictly-lower blocks of row I are written after their inputs are read
   for (int Ib = 1; Ib < nblk; ++Ib) {
@@ -503,8 +520,8 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
     cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    cholesky_blocked_kernel<<<1, 1024, sm, st>>>(g, l, lp, shifted, r_out, rinv, racc, racc_init,
-                                                 status);
+    cholesky_blocked_kernel<<<1, 512, sm, st>>>(g, l, lp, shifted, r_out, rinv, racc, racc_init,
+                                                status);
     return cudaGetLastError();
   }
   const size_t smem = ((size_t)l * (l + 1) / 2 + l + 4 + kMaxL) * sizeof(float);
