@@ -57,17 +57,22 @@ typedef enum {
   RSVD_ERR_UNSUPPORTED = 7    /* valid request the library does not implement (yet) */
 } rsvd_status_t;
 
-enum { RSVD_F32 = 0, RSVD_BF16 = 1 };                 /* element type of A */
+/* element type of A.  RSVD_BF16X2: A is stored as two bfloat16 m x n blocks with the
+ * same lda, the rounded values hi = bf16(A) followed (m * lda elements further) by the
+ * residual lo = bf16(A - hi), as rsvd_convert_a writes them; the passes of Stage A
+ * read hi only, the final pass B^T = A^T Q reads both (about 16 significant bits). */
+enum { RSVD_F32 = 0, RSVD_BF16 = 1, RSVD_BF16X2 = 2 };
 enum { RSVD_GAUSSIAN = 0, RSVD_SRFT = 1 };            /* test matrix (Section 4.1 / 4.6) */
 enum { RSVD_PLAIN_FP32 = 0, RSVD_BF16_TC = 1 };       /* how the passes over A are computed */
 
 typedef struct {
-  int32_t dtype_A;      /* RSVD_F32 or RSVD_BF16 */
+  int32_t dtype_A;      /* RSVD_F32, RSVD_BF16 or RSVD_BF16X2 */
   int32_t test_matrix;  /* RSVD_GAUSSIAN (default) or RSVD_SRFT */
   int32_t precision;    /* RSVD_PLAIN_FP32: float32 A, float32 FMA on CUDA cores.
-                           RSVD_BF16_TC: bfloat16 A, tcgen05 tensor-core products with
-                           float32 accumulation, float32 re-orthonormalisation, and a
-                           split (hi + lo) basis in the final pass B^T = A^T Q. */
+                           RSVD_BF16_TC: bfloat16 A (RSVD_BF16 or RSVD_BF16X2), tcgen05
+                           tensor-core products with float32 accumulation, float32
+                           re-orthonormalisation, and a split (hi + lo) basis in the final
+                           pass B^T = A^T Q (with RSVD_BF16X2 also a split A there). */
   int32_t single_pass;  /* 1: two-sided one-pass sketch of Section 5.5 (q ignored) */
   int32_t recompute;    /* backward: recompute the sample matrices instead of storing them */
   int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation: 2 or 3 (default 3:
@@ -172,6 +177,13 @@ RSVD_API rsvd_status_t rsvd_profile_read(rsvd_plan_t plan, float* ms, int64_t* l
 
 /* ---- step-level entry points (each runs one step of the method with the
  * ---- plan's kernels; the tests check each against the oracle) ---------- */
+
+/* Input staging for the tensor-core path (not part of a timed SVD): A (device
+ * float32, m x n, lda) -> out (device bfloat16, leading dimension ldo): hi = bf16(A)
+ * in the first m rows and, when with_lo != 0, lo = bf16(A - hi) in the next m rows
+ * (the RSVD_BF16X2 layout; out must hold 2 m rows then). */
+RSVD_API rsvd_status_t rsvd_convert_a(const float* A, int64_t m, int64_t n, int64_t lda,
+                                      void* out, int64_t ldo, int32_t with_lo, void* stream);
 
 /* Algorithm 4.1 step 1: rows x cols standard Gaussian matrix into `out`
  * (device float32, leading dimension ld >= cols).  Element (i, j): with

@@ -26,7 +26,7 @@ RSVD_ERR_NONFINITE = 5
 RSVD_ERR_TIMEOUT = 6
 RSVD_ERR_UNSUPPORTED = 7
 
-RSVD_F32, RSVD_BF16 = 0, 1
+RSVD_F32, RSVD_BF16, RSVD_BF16X2 = 0, 1, 2
 RSVD_GAUSSIAN, RSVD_SRFT = 0, 1
 RSVD_PLAIN_FP32, RSVD_BF16_TC = 0, 1
 
@@ -36,7 +36,7 @@ EXPORTS = (
     "rsvd_range_finder", "rsvd_svd", "rsvd_svd_host", "rsvd_svd_backward", "rsvd_get_omega",
     "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
-    "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc",
+    "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc", "rsvd_convert_a",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -92,6 +92,8 @@ _SIGS = {
     "rsvd_profile": (_c.c_int, [_P, _c.c_uint32]),
     "rsvd_profile_read": (_c.c_int, [_P, _P, _P, _c.c_int32]),
     "rsvd_diagnostics": (_c.c_int, [_P, _P, _c.c_int32]),
+    "rsvd_convert_a": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int64, _P, _c.c_int64,
+                                  _c.c_int32, _P]),
     "rsvd_sketch_bf16_noalloc": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32, _P,
                                             _c.c_int64, _c.c_int32, _P, _P, _P]),
 }
@@ -249,6 +251,11 @@ def rsvd_diagnostics(plan):
     return int(out[0]), int(out[1])
 
 
+def rsvd_convert_a(A, m, n, lda, out, ldo, with_lo, stream=None):
+    _check(lib().rsvd_convert_a(_ptr(A), int(m), int(n), int(lda), _ptr(out), int(ldo),
+                                int(with_lo), _stream(stream)), "rsvd_convert_a")
+
+
 def rsvd_sketch_bf16_noalloc(A, m, n, lda, transpose, Xt, ldxt, l, Y, status=None, stream=None):
     """One tensor-core pass that allocates nothing (see include/rsvd.h)."""
     _check(lib().rsvd_sketch_bf16_noalloc(_ptr(A), int(m), int(n), int(lda), int(transpose),
@@ -263,10 +270,12 @@ class Plan:
     """Owns one rsvd plan; tensors are torch CUDA tensors (row-major, contiguous)."""
 
     def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
-                 lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0):
+                 lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None):
         o = rsvd_options_default()
         o.precision = precision
-        o.dtype_A = RSVD_BF16 if precision == RSVD_BF16_TC else RSVD_F32
+        if dtype is None:
+            dtype = RSVD_BF16 if precision == RSVD_BF16_TC else RSVD_F32
+        o.dtype_A = dtype
         o.orth_rounds = orth_rounds
         o.lda = lda
         o.test_matrix = test_matrix
@@ -316,6 +325,17 @@ class Plan:
 
     def sync(self):
         _check(rsvd_sync(self.handle), "rsvd_sync")
+
+
+def split_bf16(A):
+    """float32 CUDA tensor (m x n) -> bfloat16 (2m x n): hi = bf16(A) over lo = bf16(A - hi),
+    the RSVD_BF16X2 layout (computed by the library's conversion kernel)."""
+    import torch
+
+    m, n = A.shape
+    out = torch.empty(2 * m, n, device=A.device, dtype=torch.bfloat16)
+    rsvd_convert_a(A, m, n, A.stride(0), out, n, 1)
+    return out
 
 
 def svd(A, k, p=10, q=1, seed=0, precision=None, orth_rounds=3):

@@ -51,6 +51,12 @@ struct rsvd_plan_s {
   void* a_dev = nullptr;
   float *u_dev = nullptr, *s_dev = nullptr, *v_dev = nullptr;
   size_t ws_bytes = 0;
+  // CUDA graph of rsvd_svd for one (A, U, S, V) binding
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_a = nullptr;
+  const float *g_u = nullptr, *g_s = nullptr, *g_v = nullptr;
+  int64_t g_launches[RSVD_NUM_STEPS] = {};
+  bool use_graph = true;
   // tracing
   uint32_t prof_mask = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[RSVD_NUM_STEPS];
@@ -96,6 +102,7 @@ rsvd_status_t dalloc(rsvd_plan_t P, T** ptr, size_t elems) {
 
 void free_plan(rsvd_plan_t P) {
   if (!P) return;
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (auto& v : P->ev)
     for (auto& e : v) {
       cudaEventDestroy(e.first);
@@ -194,7 +201,9 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
     *splits = s;
   } else {
     int s = 1;
-    if (tc_pass(&P->tc, trans, split_x ? 1 : 0, P->partial, &s, P->st) != 0) return RSVD_ERR_CUDA;
+    const int hilo = (split_x && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
+    if (tc_pass(&P->tc, trans, split_x ? 1 : 0, hilo, P->partial, &s, P->st) != 0)
+      return RSVD_ERR_CUDA;
     *splits = s;
   }
   return RSVD_OK;
@@ -239,7 +248,8 @@ rsvd_status_t step_convert(rsvd_plan_t P, const float* x, int64_t rows, int spli
 
 rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   const bool tc = P->opt.precision == RSVD_BF16_TC;
-  if (tc) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  if (tc)
+    TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
   TRYS(step_draw(P, tc));
   int s;
   int64_t stride;
@@ -328,9 +338,10 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.lda == 0) o.lda = n;
   if (o.lda < n) return RSVD_ERR_INVALID_ARG;
   if (o.orth_rounds != 2 && o.orth_rounds != 3) return RSVD_ERR_INVALID_ARG;
-  if (o.dtype_A != RSVD_F32 && o.dtype_A != RSVD_BF16) return RSVD_ERR_INVALID_ARG;
+  if (o.dtype_A != RSVD_F32 && o.dtype_A != RSVD_BF16 && o.dtype_A != RSVD_BF16X2)
+    return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_PLAIN_FP32 && o.dtype_A != RSVD_F32) return RSVD_ERR_INVALID_ARG;
-  if (o.precision == RSVD_BF16_TC && o.dtype_A != RSVD_BF16) return RSVD_ERR_INVALID_ARG;
+  if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
   if (o.test_matrix != RSVD_GAUSSIAN || o.single_pass) return RSVD_ERR_UNSUPPORTED;
   if (l > 160) return RSVD_ERR_UNSUPPORTED;  // one-CTA Jacobi limit
@@ -349,6 +360,15 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     cudaGetLastError();
     delete P;
     return RSVD_ERR_CUDA;
+  }
+  if (prepare_orth() != cudaSuccess || prepare_jacobi() != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return RSVD_ERR_CUDA;
+  }
+  {
+    const char* e = getenv("RSVD_NO_GRAPH");
+    P->use_graph = !(e && e[0] && e[0] != '0');
   }
   const int lp = P->lp;
   P->splits_n = choose_splits(m, lp, n, P->num_sms);
@@ -414,11 +434,63 @@ rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t 
   return RSVD_OK;
 }
 
+// The kernels of one rsvd_svd call are captured once into a CUDA graph and
+// replayed while the plan sees the same A, U, S, V pointers (one launch per call
+// instead of about sixty).  Direct launches are used while per-step timing is on,
+// on the legacy default stream (which cannot be captured), if capture fails, or
+// when the environment sets RSVD_NO_GRAPH=1.
+rsvd_status_t run_svd_direct(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  TRYS(stage_a(P, A));
+  TRYS(stage_b(P, A, U, S, V));
+  return RSVD_OK;
+}
+
 rsvd_status_t rsvd_svd(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
   TRYS(check_plan(P));
   if (!A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
-  TRYS(stage_a(P, A));
-  TRYS(stage_b(P, A, U, S, V));
+  const bool graph_ok = P->use_graph && P->prof_mask == 0 && P->st != nullptr &&
+                        P->st != cudaStreamLegacy && P->st != cudaStreamPerThread;
+  if (!graph_ok) return run_svd_direct(P, A, U, S, V);
+  if (!(P->gexec && P->g_a == A && P->g_u == U && P->g_s == S && P->g_v == V)) {
+    if (P->gexec) {
+      cudaGraphExecDestroy(P->gexec);
+      P->gexec = nullptr;
+    }
+    int64_t before[RSVD_NUM_STEPS];
+    for (int k = 0; k < RSVD_NUM_STEPS; ++k) before[k] = P->launches[k];
+    if (cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return run_svd_direct(P, A, U, S, V);
+    }
+    const rsvd_status_t st = run_svd_direct(P, A, U, S, V);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(P->st, &graph);
+    if (st != RSVD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess || !graph) {
+      cudaGetLastError();
+      return run_svd_direct(P, A, U, S, V);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&P->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      P->gexec = nullptr;
+      return run_svd_direct(P, A, U, S, V);
+    }
+    for (int k = 0; k < RSVD_NUM_STEPS; ++k) {
+      P->g_launches[k] = P->launches[k] - before[k];
+      P->launches[k] = before[k];
+    }
+    P->g_a = A;
+    P->g_u = U;
+    P->g_s = S;
+    P->g_v = V;
+  }
+  TRY(cudaGraphLaunch(P->gexec, P->st));
+  for (int k = 0; k < RSVD_NUM_STEPS; ++k) P->launches[k] += P->g_launches[k];
   return RSVD_OK;
 }
 
@@ -426,8 +498,9 @@ rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, fl
                             float* V_host) {
   TRYS(check_plan(P));
   if (!A_host || !U_host || !S_host || !V_host) return RSVD_ERR_INVALID_ARG;
-  const size_t esz = P->opt.dtype_A == RSVD_BF16 ? 2 : 4;
-  const size_t abytes = ((size_t)(P->m - 1) * P->lda + P->n) * esz;
+  const size_t esz = P->opt.dtype_A == RSVD_F32 ? 4 : 2;
+  const size_t arows = P->opt.dtype_A == RSVD_BF16X2 ? 2 * P->m : P->m;
+  const size_t abytes = ((size_t)(arows - 1) * P->lda + P->n) * esz;
   if (!P->a_dev) {
     TRYS(dalloc(P, reinterpret_cast<char**>(&P->a_dev), abytes));
     TRYS(dalloc(P, &P->u_dev, (size_t)P->m * P->k));
@@ -459,6 +532,10 @@ rsvd_status_t rsvd_get_omega(rsvd_plan_t P, float* Omega) {
 
 rsvd_status_t rsvd_set_omega(rsvd_plan_t P, const float* Omega) {
   TRYS(check_plan(P));
+  if (P->gexec) {  // the captured draw no longer matches
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
   if (!Omega) {
     P->omega_user = false;
     return RSVD_OK;
@@ -518,6 +595,14 @@ rsvd_status_t rsvd_profile_read(rsvd_plan_t P, float* ms, int64_t* launches, int
   return RSVD_OK;
 }
 
+rsvd_status_t rsvd_convert_a(const float* A, int64_t m, int64_t n, int64_t lda, void* out,
+                             int64_t ldo, int32_t with_lo, void* stream) {
+  if (!A || !out || m < 1 || n < 1 || lda < n || ldo < n) return RSVD_ERR_INVALID_ARG;
+  TRY(launch_split_bf16(A, m, n, lda, static_cast<__nv_bfloat16*>(out), ldo, with_lo,
+                        static_cast<cudaStream_t>(stream)));
+  return RSVD_OK;
+}
+
 rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
                                  float* out, int64_t ld, void* stream) {
   if (rows < 0 || cols < 0 || cols > (1 << 30) || (rows > 0 && cols > 0 && !out) || ld < cols)
@@ -533,7 +618,8 @@ rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const
   if (!A || !X || !Y) return RSVD_ERR_INVALID_ARG;
   const int64_t kx = transpose ? P->m : P->n;
   const int64_t my = transpose ? P->n : P->m;
-  if (P->opt.precision == RSVD_BF16_TC) TRYS(tc_bind_a(&P->tc, A) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  if (P->opt.precision == RSVD_BF16_TC)
+    TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
   float* xin = transpose ? P->qbuf : P->omega;  // padded K x lp copy of X
   TRY(launch_gather(X, 1, 0, P->l, xin, P->lp, kx, P->l, P->lp, P->st));
   if (P->opt.precision == RSVD_BF16_TC)

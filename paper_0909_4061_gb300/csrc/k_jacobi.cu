@@ -162,7 +162,179 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
   }
 }
 
+
+// Same algorithm for l <= 128 with every column padded to 128 floats (zeros) so a
+// half-warp lane moves its 8 elements of a column with two 16-byte shared-memory
+// accesses (float4 index hl and hl + 16), which halves the instructions per pair.
+constexpr int kVecL = 128;
+
+__device__ __forceinline__ void ld8(const float* col, int hl, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4*>(col)[hl];
+  const float4 b = reinterpret_cast<const float4*>(col)[hl + 16];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void st8(float* col, int hl, const float (&v)[8]) {
+  reinterpret_cast<float4*>(col)[hl] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(col)[hl + 16] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ __forceinline__ void rotate8(float (&u)[8], float (&v)[8], float sn, float tau) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float uu = u[i], vv = v[i];
+    u[i] = uu - sn * fmaf(tau, uu, vv);
+    v[i] = vv + sn * fmaf(-tau, vv, uu);
+  }
+}
+
+__global__ void __launch_bounds__(1024) jacobi_vec_kernel(const float* __restrict__ x, int64_t ldx,
+                                                          int transposed, int l, int lp,
+                                                          float* __restrict__ ut,
+                                                          float* __restrict__ s,
+                                                          float* __restrict__ w, uint32_t* status,
+                                                          uint32_t* info, float tol) {
+  extern __shared__ __align__(16) float sm[];
+  const int le = l + (l & 1);
+  float* Xc = sm;                      // [l][128]
+  float* Jc = sm + l * kVecL;          // [l][128]
+  float* sig = Jc + l * kVecL;         // [le]
+  int* rank_of = reinterpret_cast<int*>(sig + le);
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;
+  const unsigned hmask = 0xFFFFu << (lane & 16);
+
+  for (int e = tid; e < l * kVecL; e += nt) {
+    const int c = e / kVecL, r = e % kVecL;
+    Xc[e] = (r < l) ? (transposed ? x[(int64_t)c * ldx + r] : x[(int64_t)r * ldx + c]) : 0.0f;
+    Jc[e] = (c == r) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < le - 1; ++round) {
+      for (int slot = hw; slot < le / 2; slot += nhw) {
+        const int p = rr_player(slot, round, le);
+        const int q = rr_player(le - 1 - slot, round, le);
+        if (p >= l || q >= l) continue;
+        float* xp = Xc + p * kVecL;
+        float* xq = Xc + q * kVecL;
+        float u[8], v[8];
+        ld8(xp, hl, u);
+        ld8(xq, hl, v);
+        float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          a = fmaf(u[i], u[i], a);
+          b = fmaf(v[i], v[i], b);
+          g = fmaf(u[i], v[i], g);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(hmask, a, o);
+          b += __shfl_xor_sync(hmask, b, o);
+          g += __shfl_xor_sync(hmask, g, o);
+        }
+        if (g == 0.0f || !(fabsf(g) > tol * sqrtf(a * b))) continue;
+        const float zeta = __fdividef(b - a, 2.0f * g);
+        const float az = fabsf(zeta);
+        float t = (az > 1e18f) ? __fdividef(0.5f, az)
+                               : __fdividef(1.0f, az + sqrtf(fmaf(az, az, 1.0f)));
+        t = copysignf(t, zeta);
+        if (zeta == 0.0f) t = 1.0f;
+        const float w2 = fmaf(t, t, 1.0f);
+        float c = rsqrtf(w2);
+        c = c * fmaf(-0.5f * w2, c * c, 1.5f);
+        const float sn = c * t;
+        const float tau = sn / (1.0f + c);
+        if (hl == 0) s_rot = 1;
+        rotate8(u, v, sn, tau);
+        st8(xp, hl, u);
+        st8(xq, hl, v);
+        float* jp = Jc + p * kVecL;
+        float* jq = Jc + q * kVecL;
+        ld8(jp, hl, u);
+        ld8(jq, hl, v);
+        rotate8(u, v, sn, tau);
+        st8(jp, hl, u);
+        st8(jq, hl, v);
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (tid == 0) {
+    if (sweep == kMaxSweeps) set_status(status, ST_JACOBI_NOCONV);
+    if (info) atomicMax(info, (uint32_t)(sweep + 1));
+  }
+
+  for (int c = warp; c < l; c += nw) {
+    float a = 0.f;
+    for (int e = lane; e < l; e += 32) a = fmaf(Xc[c * kVecL + e], Xc[c * kVecL + e], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[c] = sqrtf(a);
+  }
+  __syncthreads();
+  for (int e = tid; e < lp * lp; e += nt) {
+    const int r = e / lp, c = e % lp;
+    if (r >= l || c >= l) { ut[e] = 0.0f; w[e] = 0.0f; }
+  }
+  for (int c = warp; c < l; c += nw) {
+    const float sc = sig[c];
+    int rank = 0;
+    for (int c2 = lane; c2 < l; c2 += 32) {
+      const float s2 = sig[c2];
+      rank += (s2 > sc || (s2 == sc && c2 < c)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const float inv = sc > 0.0f ? 1.0f / sc : 0.0f;
+    for (int e = lane; e < l; e += 32) ut[(int64_t)e * lp + rank] = Xc[c * kVecL + e] * inv;
+    if (lane == 0) {
+      s[rank] = sc;
+      rank_of[c] = rank;
+    }
+  }
+  __syncthreads();
+  // Newton-Schulz polish of the accumulated rotations, G = J^T J in X's space
+  float* G = Xc;
+  for (int e = tid; e < l * l; e += nt) {
+    const int c1 = e / l, c2 = e % l;
+    const float* j1 = Jc + c1 * kVecL;
+    const float* j2 = Jc + c2 * kVecL;
+    float a = 0.f;
+    for (int r = 0; r < l; ++r) a = fmaf(j1[r], j2[r], a);
+    G[e] = a;
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += nt) {
+    const int c = e / l, r = e % l;
+    float a = 0.f;
+    for (int c2 = 0; c2 < l; ++c2) a = fmaf(Jc[c2 * kVecL + r], G[c2 * l + c], a);
+    w[(int64_t)r * lp + rank_of[c]] = 1.5f * Jc[c * kVecL + r] - 0.5f * a;
+  }
+}
+
+size_t jacobi_vec_smem_bytes(int l) {
+  return (size_t)(2 * l * kVecL + 2 * l + 4) * sizeof(float);
+}
+
 }  // namespace
+
+cudaError_t prepare_jacobi() {
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)jacobi_smem_bytes(kMaxJacobiL));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(jacobi_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)jacobi_vec_smem_bytes(kVecL));
+}
 
 size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + 2 * l + 4) * sizeof(float); }
 
@@ -171,13 +343,15 @@ cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l
                               cudaStream_t st) {
   if (l > kMaxJacobiL) return cudaErrorInvalidValue;
   const size_t smem = jacobi_smem_bytes(l);
-  cudaError_t e =
-      cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   // a pair counts as orthogonal below 8 sqrt(l) u: above the float32 rounding floor of
   // a computed dot product (a few u sqrt(l)), so the sweeps terminate, and small enough
   // that U is orthonormal to ~5e-6 at l ~ 100
   const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
+  if (l <= kVecL) {
+    jacobi_vec_kernel<<<1, 1024, jacobi_vec_smem_bytes(l), st>>>(x, ldx, transposed, l, lp, ut, s,
+                                                                 w, status, info, tol);
+    return cudaGetLastError();
+  }
   jacobi_kernel<<<1, 1024, smem, st>>>(x, ldx, transposed, l, lp, ut, s, w, status, info, tol);
   return cudaGetLastError();
 }

@@ -49,19 +49,23 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* __restri
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
 
+  const int lp4 = lp / 4;  // lp is a multiple of 16: whole float4 per row
   for (int64_t rb = r0; rb < r1; rb += GR) {
     const int nr = (int)min((int64_t)GR, r1 - rb);
     __syncthreads();
-    for (int e = threadIdx.x; e < GR * lp; e += blockDim.x) {
-      const int rr = e / lp, c = e % lp;
-      float v = 0.0f;
+    for (int e = threadIdx.x; e < GR * lp4; e += blockDim.x) {
+      const int rr = e / lp4, c4 = e - rr * lp4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (rr < nr) {
-        const int64_t off = (rb + rr) * lp + c;
-        v = src[off];
-        for (int s = 1; s < splits; ++s) v += src[off + (int64_t)s * split_stride];
-        if (write_y) y_out[off] = v;
+        const int64_t off = (rb + rr) * lp + 4 * c4;
+        v = *reinterpret_cast<const float4*>(src + off);
+        for (int s = 1; s < splits; ++s) {
+          const float4 w = *reinterpret_cast<const float4*>(src + off + (int64_t)s * split_stride);
+          v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+        }
+        if (write_y) *reinterpret_cast<float4*>(y_out + off) = v;
       }
-      ys[rr * lp + c] = v;
+      *reinterpret_cast<float4*>(ys + rr * lp + 4 * c4) = v;
     }
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 // threads; the inverse takes the diagonal blocks' inverses (one warp each, in
 // parallel) and then the block rows below them in order.  Outputs as in
 // cholesky_kernel: R = L^T, R^-1 = X^T, the optional product racc <- R racc.
-constexpr int CB = 32;
+constexpr int CB = 16;  // 16 x 16 diagonal blocks stay fully unrolled in registers
 
 __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     const float* __restrict__ g, int l, int lp, int shifted, float* __restrict__ r_out,
@@ -304,6 +308,7 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     // (1) diagonal block by warp 0, in registers: lane i holds row i (identity padding
     // beyond nb); then the block's inverse, lane c holding column c.
     if (warp == 0) {
+      // lanes >= CB carry identity rows that no one reads
       float a[CB];
 #pragma unroll
       for (int j = 0; j < CB; ++j)
@@ -461,6 +466,21 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int 
   }
 }
 
+__global__ void split_bf16_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
+                                  int64_t ld, __nv_bfloat16* __restrict__ out, int64_t ld_out,
+                                  int with_lo) {
+  const int64_t n = rows * cols;
+  const int64_t lo_off = rows * ld_out;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    const float v = x[r * ld + c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    out[r * ld_out + c] = hi;
+    if (with_lo) out[lo_off + r * ld_out + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
 __global__ void f32_to_bf16_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
                                    int64_t ld, __nv_bfloat16* __restrict__ out, int64_t ld_out) {
   const int64_t n = rows * cols;
@@ -488,9 +508,21 @@ __global__ void gather_kernel(const float* __restrict__ src, int splits, int64_t
 
 }  // namespace
 
+// Shared-memory limits of the one-CTA factorisation kernels, for every size they accept;
+// set once per device (at plan creation) so no launch needs a host-side attribute call.
+cudaError_t prepare_orth() {
+  cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)2 * 160 * 161 * sizeof(float)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(((size_t)kMaxL * (kMaxL + 1) / 2 + kMaxL + 4 + kMaxL) *
+                                    sizeof(float)));
+}
+
 int gram_blocks(int64_t rows) {
-  const int64_t b = cdiv(rows, 128);
-  return (int)(b < kNumSMs ? (b < 1 ? 1 : b) : kNumSMs);
+  const int64_t b = cdiv(rows, 64);
+  return (int)(b < 4 * kNumSMs ? (b < 1 ? 1 : b) : 4 * kNumSMs);
 }
 
 cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stride, float* y_out,
@@ -498,9 +530,7 @@ cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stri
   const int T = (lp + GT - 1) / GT;
   const int npair = T * (T + 1) / 2;
   const int64_t rpb = round_up(cdiv(rows, nblk), GR);
-  const size_t smem = (size_t)GR * lp * sizeof(float);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)GR * lp * sizeof(float);  // <= 32 KB for lp <= 256
   gram_partial_kernel<<<dim3(nblk, npair), 256, smem, st>>>(src, splits, split_stride, y_out, rows,
                                                             lp, gpart, rpb);
   return cudaGetLastError();
@@ -517,17 +547,11 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
                             cudaStream_t st) {
   if (lp <= 160) {
     const size_t sm = (size_t)2 * lp * (lp + 1) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     cholesky_blocked_kernel<<<1, 512, sm, st>>>(g, l, lp, shifted, r_out, rinv, racc, racc_init,
                                                 status);
     return cudaGetLastError();
   }
   const size_t smem = ((size_t)l * (l + 1) / 2 + l + 4 + kMaxL) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   cholesky_kernel<<<1, 1024, smem, st>>>(g, l, lp, shifted, lbuf, r_out, rinv, racc, racc_init,
                                          status);
   return cudaGetLastError();
@@ -537,6 +561,15 @@ cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16
                              int split, int lo_off, cudaStream_t st) {
   const dim3 grid((unsigned)cdiv(rows, 32), (unsigned)cdiv(lp, 32));
   to_bf16_t_kernel<<<grid, dim3(32, 8), 0, st>>>(x, rows, lp, out, ld_t, split, lo_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
+                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st) {
+  const int64_t n = rows * cols;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(cdiv(n, 256) < 16 * kNumSMs ? cdiv(n, 256) : 16 * kNumSMs);
+  split_bf16_kernel<<<grid, 256, 0, st>>>(x, rows, cols, ld, out, ld_out, with_lo);
   return cudaGetLastError();
 }
 

@@ -196,9 +196,14 @@ struct Range {
   }
 };
 
-template <int MODE>
+// HILO (with MODE 1): A arrives as a bfloat16 hi part (map_a) and the bfloat16
+// residual lo = A - hi (map_alo); each stage carries both tiles and the MMAs of
+// the lo tile accumulate into the same tensor-memory accumulator, so the pass
+// sees A to about 16 significant bits.
+template <int MODE, int HILO = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
+                     const __grid_constant__ CUtensorMap map_alo,
                      const __grid_constant__ CUtensorMap map_x, float* __restrict__ y, int lp,
                      int64_t M, int kt, int64_t total, int n_total, int fold, int lo_off, int stages,
                      float* __restrict__ slots, uint32_t* __restrict__ flags, uint32_t* status) {
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  constexpr uint32_t a_bytes = BM * BK * 2;  // 16 KB
+  constexpr uint32_t a_bytes = BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
   const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
   const uint32_t stage_bytes = a_bytes + x_bytes;
   uint32_t tmem_cols = 32;
@@ -231,6 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)) : "memory");
+    if (HILO)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_alo)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -262,6 +269,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           tma_load_2d(sa, &map_a, &bar_full[s], t * BM, kk * BK);
           tma_load_2d(sa + 8192, &map_a, &bar_full[s], t * BM + 64, kk * BK);
+          if (HILO) {
+            tma_load_2d(sa + 16384, &map_alo, &bar_full[s], t * BM, kk * BK);
+            tma_load_2d(sa + 16384 + 8192, &map_alo, &bar_full[s], t * BM + 64, kk * BK);
+          }
         }
         for (int c = 0; c * 256 < n_total; ++c)
           tma_load_2d(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256);
@@ -306,6 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
               const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
               mma_bf16(tmem + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
+              if (HILO) {
+                const uint64_t adesc_lo = smem_desc(sa + 16384 + j * 2048, 8192, 1024);
+                mma_bf16(tmem + c * 256, adesc_lo, bdesc, idesc, 1u);
+              }
             }
           }
           mma_commit(&bar_empty[s]);
@@ -444,13 +459,13 @@ struct TcBuffers {
   int grid = 0;
 };
 
-size_t smem_bytes(int n_total, int stages) {
-  return (size_t)stages * (BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
+size_t smem_bytes(int n_total, int stages, int a_tiles = 1) {
+  return (size_t)stages * ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
 }
 
-int pick_stages(int n_total) {
+int pick_stages(int n_total, int a_tiles = 1) {
   const size_t budget = 200 * 1024;
-  int s = (int)(budget / ((size_t)BM * BK * 2 + (size_t)n_total * BK * 2));
+  int s = (int)(budget / ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2));
   if (s > 8) s = 8;
   return s < 2 ? 2 : s;
 }
@@ -499,22 +514,33 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
       cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm) != cudaSuccess)
     return -1;
+  const int nf2 = fold_ntotal(lp);
+  if (cudaFuncSetAttribute(sketch_tc_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes(nf2, pick_stages(nf2, 2), 2)) != cudaSuccess)
+    return -1;
   tc->ready = true;
   return 0;
 }
 
-int tc_bind_a(TcPlan* tc, const void* A) {
+int tc_bind_a(TcPlan* tc, const void* A, int with_lo) {
   if (!tc->ready) return -1;
-  if (A == tc->a_bound) return 0;
+  if (A == tc->a_bound && with_lo == tc->lo_bound) return 0;
   if (reinterpret_cast<uintptr_t>(A) & 15) return -1;
   if (encode_2d(tc->map_a_n, A, tc->n, tc->m, tc->lda, BK, BM)) return -1;
   if (encode_2d(tc->map_a_t, A, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+  if (with_lo) {
+    const __nv_bfloat16* lo = static_cast<const __nv_bfloat16*>(A) + tc->m * tc->lda;
+    if (encode_2d(tc->map_a_lo, lo, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+  }
   tc->a_bound = A;
+  tc->lo_bound = with_lo;
   return 0;
 }
 
-int tc_pass(TcPlan* tc, int trans, int split_x, float* out, int* splits, cudaStream_t st) {
+int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* splits,
+            cudaStream_t st) {
   if (!tc->ready || !tc->a_bound) return -1;
+  if (hilo && (!trans || !split_x || !tc->lo_bound)) return -1;
   TcBuffers* b = static_cast<TcBuffers*>(tc->priv);
   const int lp = tc->lp;
   const int n_total = split_x ? fold_ntotal(lp) : lp;
@@ -524,18 +550,23 @@ int tc_pass(TcPlan* tc, int trans, int split_x, float* out, int* splits, cudaStr
   const int kt = (int)cdiv(K, BK);
   const int64_t total = cdiv(M, BM) * kt;
   const int grid = (int)(total < b->grid ? total : b->grid);
-  const int stages = pick_stages(n_total);
-  const size_t sm = smem_bytes(n_total, stages);
+  const int stages = pick_stages(n_total, hilo ? 2 : 1);
+  const size_t sm = smem_bytes(n_total, stages, hilo ? 2 : 1);
   const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(trans ? tc->map_a_t : tc->map_a_n);
+  const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(hilo ? tc->map_a_lo : tc->map_a_t);
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
       trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
   if (split_x && !trans) return -1;
-  if (trans)
-    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *mx, out, lp, M, kt, total, n_total,
+  if (hilo)
+    sketch_tc_kernel<1, 1><<<grid, kThreads, sm, st>>>(*ma, *malo, *mx, out, lp, M, kt, total,
+                                                       n_total, split_x, lo_off, stages, b->slots,
+                                                       b->flags, tc->status);
+  else if (trans)
+    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, out, lp, M, kt, total, n_total,
                                                     split_x, lo_off, stages, b->slots, b->flags,
                                                     tc->status);
   else
-    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *mx, out, lp, M, kt, total, n_total,
+    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, out, lp, M, kt, total, n_total,
                                                     split_x, lo_off, stages, b->slots, b->flags,
                                                     tc->status);
   *splits = 1;
@@ -662,10 +693,10 @@ extern "C" rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int6
   const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(map_a);
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(map_x);
   if (transpose)
-    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
+    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
                                                     d->slots, d->flags, status);
   else
-    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
+    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, Y, l, M, kt, total, l, 0, 0, stages,
                                                     d->slots, d->flags, status);
   return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
 }

@@ -42,6 +42,12 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
 cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16* out,
                              int64_t ld_t, int split, int lo_off, cudaStream_t st);
 
+// A (float32, rows x cols, ld) -> bfloat16 hi (rows x cols, ld_out) and, with_lo, the
+// bfloat16 residual lo = bf16(A - hi) in the rows x cols block that follows (rows * ld_out
+// elements further).
+cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
+                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st);
+
 // float32 <-> bfloat16 conversion of a whole matrix (rows x cols, ld) for A.
 cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
                                __nv_bfloat16* out, int64_t ld_out, cudaStream_t st);
@@ -59,5 +65,9 @@ size_t jacobi_smem_bytes(int l);
 cudaError_t launch_gather(const float* src, int splits, int64_t split_stride, int64_t lds,
                           float* dst, int64_t ldd, int64_t rows, int cols, int cols_pad,
                           cudaStream_t st);
+
+// One-time (per device) shared-memory attributes of the one-CTA kernels.
+cudaError_t prepare_orth();
+cudaError_t prepare_jacobi();
 
 }  // namespace rsvd

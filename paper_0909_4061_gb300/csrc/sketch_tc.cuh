@@ -19,7 +19,9 @@ struct TcPlan {
   alignas(64) unsigned char map_x_n[128];  // X^T tiles, K = n
   alignas(64) unsigned char map_x_t[128];  // X^T tiles, K = m (lp rows)
   alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (hi rows, then lo rows at tc_lo_offset)
+  alignas(64) unsigned char map_a_lo[128]; // residual lo = A - hi, stacked m rows below A (Y = A^T X)
   bool ready = false;
+  int lo_bound = 0;
   uint32_t* status = nullptr;     // device status word of the owning plan
   void* priv = nullptr;           // stream-K slots and flags
 };
@@ -34,11 +36,13 @@ int tc_lo_offset(int lp);
 // 0 on success.
 int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfloat16* xbf,
                  int num_sms);
-int tc_bind_a(TcPlan* tc, const void* A);
+// with_lo: A is followed (m rows of lda further) by its bfloat16 residual lo = A - hi.
+int tc_bind_a(TcPlan* tc, const void* A, int with_lo);
 // One pass.  trans = 0: Y = A X (X^T is lp x n in xbf); trans = 1: Y = A^T X (X^T is lp x m,
-// or 2 lp x m with split_x = 1, the hi and lo halves summed).  Writes *splits slabs of
-// (rows x lp) float32 into `partial`.
-int tc_pass(TcPlan* tc, int trans, int split_x, float* partial, int* splits, cudaStream_t st);
+// or 2 lp x m with split_x = 1, the hi and lo halves summed; hilo = 1 also reads the
+// residual of A).  Writes *splits slabs of (rows x lp) float32 into `partial`.
+int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* partial, int* splits,
+            cudaStream_t st);
 int64_t tc_partial_elems(int64_t m, int64_t n, int lp, int num_sms);
 void tc_plan_destroy(TcPlan* tc);
 

@@ -118,3 +118,48 @@ def test_tc_matched_error_against_fp32_c1(rsvd_lib):
     u, s, v = _tc_svd(rsvd_lib, _bf16(a32), w.k, w.p, w.q, w.omega_seed)
     etc = metrics.fro_error(a32.astype(np.float64), u, s, v)
     assert (etc - e32) / e32 <= 1e-4, (etc - e32) / e32
+
+
+def test_convert_a_hi_lo_exact(rsvd_lib):
+    rng = np.random.default_rng(2)
+    a = rng.standard_normal((300, 261)).astype(np.float32) * np.float32(3.7)
+    out = torch.zeros(600, 264, dtype=torch.bfloat16, device="cuda")
+    rsvd_lib.rsvd_convert_a(_dev(a), 300, 261, 261, out, 264, 1)
+    torch.cuda.synchronize()
+    o = out.float().cpu().numpy().astype(np.float64)
+    hi = _bf16(a)
+    lo = _bf16(a.astype(np.float64) - hi)
+    assert np.array_equal(o[:300, :261], hi) and np.array_equal(o[300:, :261], lo)
+    # hi + lo carries ~16 significant bits of A
+    assert np.max(np.abs(hi + lo - a) / np.abs(a)) <= 2.0 ** -16
+
+
+def _tc_svd_hilo(pkg, a32, k, p, q, seed):
+    m, n = a32.shape
+    A = _dev(a32)
+    with pkg.Plan(m, n, k, p, q, seed, pkg.RSVD_BF16_TC, dtype=pkg.RSVD_BF16X2) as pl:
+        U, S, V = pl.svd(pkg.split_bf16(A))
+    return _np(U), _np(S), _np(V)
+
+
+def test_tc_hilo_rsvd_c1_full_size(rsvd_lib):
+    """Residual-corrected final pass: B = Q^T A from hi + lo, checked against the oracle
+    on the float32 A (Ritz tolerance as above plus the bfloat16 subspace of Stage A)."""
+    w = synth.C1
+    a, *_ = synth.lowrank(w.m, w.n, w.sigma(), w.matrix_seed)
+    a32 = a.astype(np.float32)
+    u, s, v = _tc_svd_hilo(rsvd_lib, a32, w.k, w.p, w.q, w.omega_seed)
+    om = philox.gaussian(w.omega_seed, 0, w.n, w.l)
+    _check_ritz(a32.astype(np.float64), u, s, v, w.k, w.p, w.q, om)
+
+
+def test_tc_hilo_matched_error_c1(rsvd_lib):
+    w = synth.C1
+    a, *_ = synth.lowrank(w.m, w.n, w.sigma(), w.matrix_seed)
+    a32 = a.astype(np.float32)
+    with rsvd_lib.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed) as pl:
+        U, S, V = pl.svd(_dev(a32))
+    e32 = metrics.fro_error(a32.astype(np.float64), _np(U), _np(S), _np(V))
+    u, s, v = _tc_svd_hilo(rsvd_lib, a32, w.k, w.p, w.q, w.omega_seed)
+    etc = metrics.fro_error(a32.astype(np.float64), u, s, v)
+    assert abs(etc - e32) / e32 <= 1e-4, (etc - e32) / e32
