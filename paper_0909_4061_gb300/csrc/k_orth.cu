@@ -105,7 +105,20 @@ __global__ void gram_reduce_kernel(const float* __restrict__ gpart, int nblk, in
   const int64_t n = (int64_t)lp * lp;
   if (e >= n) return;
   float s = 0.0f, c = 0.0f;  // Kahan-compensated sum in a fixed order
-  for (int b = 0; b < nblk; ++b) {
+  int b = 0;
+  for (; b + 8 <= nblk; b += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = gpart[(int64_t)(b + u) * n + e];   // loads in flight together
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float y = v[u] - c;
+      const float t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+  }
+  for (; b < nblk; ++b) {
     const float y = gpart[(int64_t)b * n + e] - c;
     const float t = s + y;
     c = (t - s) - y;
@@ -253,13 +266,16 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 }
 
 // Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA, both held in shared
-// memory as full squares (row stride lp + 1), for lp <= 160.  Block columns of
-// NB = 32: the diagonal block is factored by warp 0, the panel below it by one
-// thread per row (forward substitution), the trailing lower triangle by all
-// threads; the inverse takes the diagonal blocks' inverses (one warp each, in
-// parallel) and then the block rows below them in order.  Outputs as in
-// cholesky_kernel: R = L^T, R^-1 = X^T, the optional product racc <- R racc.
-constexpr int CB = 16;  // 16 x 16 diagonal blocks stay fully unrolled in registers
+// memory as full squares (row stride lp + 1), for lp <= 160.  The factor works on
+// the padded size lp (a multiple of 16) with identity rows and columns beyond l,
+// so every block is a full 16 x 16 and every inner loop has a compile-time trip
+// count (unrolled, shared-memory loads in flight together).  Per block column:
+// the diagonal block is factored and inverted by warp 0 in registers, the panel
+// below it is L_iJ = A_iJ L_JJ^-T (a small product with the block inverse), and
+// the trailing lower triangle is updated by all threads.  The off-diagonal blocks
+// of the inverse follow block row by block row.  Outputs: R = L^T, R^-1 = X^T and
+// the optional product racc <- R racc, restricted to l x l (zero elsewhere).
+constexpr int CB = 16;
 
 __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     const float* __restrict__ g, int l, int lp, int shifted, float* __restrict__ r_out,
@@ -272,11 +288,18 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   __shared__ float s_shift, s_floor;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  const int nb16 = lp / CB;
 
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e / l, j = e % l;
-    if (j <= i) A[i * ld + j] = g[(int64_t)i * lp + j];
-    X[i * ld + j] = 0.0f;
+  // load the lower triangle of G (identity beyond l), clear X; rows by warps
+  for (int i = warp; i < lp; i += nw) {
+    const float* gi = g + (int64_t)i * lp;
+    for (int j = lane; j < lp; j += 32) {
+      float v = 0.0f;
+      if (i < l && j < l) v = gi[j];
+      else if (i == j) v = 1.0f;
+      A[i * ld + j] = (j <= i) ? v : 0.0f;
+      X[i * ld + j] = 0.0f;
+    }
   }
   float tr = 0.0f, mx = 0.0f;
   bool bad = false;
@@ -303,21 +326,18 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   for (int i = tid; i < l; i += nt) A[i * ld + i] += s_shift;
   __syncthreads();
 
-  for (int J = 0; J < l; J += CB) {
-    const int nb = min(CB, l - J);
-    // (1) diagonal block by warp 0, in registers: lane i holds row i (identity padding
-    // beyond nb); then the block's inverse, lane c holding column c.
+  for (int jb = 0; jb < nb16; ++jb) {
+    const int J = jb * CB;
+    // (1) diagonal block by warp 0 in registers: lane i < 16 holds row i
     if (warp == 0) {
-      // lanes >= CB carry identity rows that no one reads
       float a[CB];
 #pragma unroll
       for (int j = 0; j < CB; ++j)
-        a[j] = (lane < nb && j < nb) ? (j <= lane ? A[(J + lane) * ld + J + j] : 0.0f)
-                                     : (j == lane ? 1.0f : 0.0f);
+        a[j] = (lane < CB) ? (j <= lane ? A[(J + lane) * ld + J + j] : 0.0f) : (j == lane ? 1.0f : 0.0f);
 #pragma unroll
       for (int j = 0; j < CB; ++j) {
         float d = __shfl_sync(0xffffffffu, a[j], j);
-        if (j < nb && !(d > pfloor)) {
+        if (J + j < l && !(d > pfloor)) {
           if (lane == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
           d = pfloor;
         }
@@ -331,7 +351,6 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
           if (lane >= k) a[k] = fmaf(-lij, lkj, a[k]);
         }
       }
-      // inverse, column c = lane: x_cc = 1 / l_cc, x_ic = -(sum_{c<=k<i} l_ik x_kc) / l_ii
       float x[CB];
 #pragma unroll
       for (int i = 0; i < CB; ++i) {
@@ -344,100 +363,107 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
         const float lii = __shfl_sync(0xffffffffu, a[i], i);
         x[i] = (i > lane) ? -v / lii : (i == lane ? 1.0f / lii : 0.0f);
       }
-      if (lane < nb) {
+      if (lane < CB) {
 #pragma unroll
         for (int j = 0; j < CB; ++j)
-          if (j < nb && j <= lane) A[(J + lane) * ld + J + j] = a[j];
+          if (j <= lane) A[(J + lane) * ld + J + j] = a[j];
 #pragma unroll
         for (int i = 0; i < CB; ++i)
-          if (i < nb && i >= lane) X[(J + i) * ld + J + lane] = x[i];
+          if (i >= lane) X[(J + i) * ld + J + lane] = x[i];
       }
     }
     __syncthreads();
-    // (2) panel rows below: L_iJ = A_iJ L_JJ^-T, i.e. l_ij = sum_{k<=j} a_ik X_JJ(j, k)
-    const int prow = l - J - nb;
-    for (int e = tid; e < prow * nb; e += nt) {
-      const int i = J + nb + e / nb, j = e % nb;
+    // (2) panel: l_ij = sum_{k<=j} a_ik X_JJ(j, k), rows below the block; staged in the
+    // strictly lower part of X (free until the inverse), then copied into A
+    const int prow = lp - J - CB;
+    for (int e = tid; e < prow * CB; e += nt) {
+      const int i = J + CB + (e >> 4), j = e & (CB - 1);
       const float* ai = A + i * ld + J;
       const float* xj = X + (J + j) * ld + J;
       float v = 0.0f;
-      for (int k = 0; k <= j; ++k) v = fmaf(ai[k], xj[k], v);
-      X[i * ld + J + j] = v;          // staged in X's strictly-lower part (free until the inverse)
+#pragma unroll
+      for (int k = 0; k < CB; ++k) v = fmaf(ai[k], xj[k], v);   // X_JJ(j, k) = 0 for k > j
+      X[i * ld + J + j] = v;
     }
     __syncthreads();
-    for (int e = tid; e < prow * nb; e += nt) {
-      const int i = J + nb + e / nb, j = e % nb;
+    for (int e = tid; e < prow * CB; e += nt) {
+      const int i = J + CB + (e >> 4), j = e & (CB - 1);
       A[i * ld + J + j] = X[i * ld + J + j];
       X[i * ld + J + j] = 0.0f;
     }
     __syncthreads();
-    // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ
-    const int s0 = J + nb, sz = l - s0;
+    // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ  (16-term dots, unrolled)
+    const int s0 = J + CB, sz = lp - s0;
     for (int e = tid; e < sz * sz; e += nt) {
-      const int i = s0 + e / sz, k = s0 + e % sz;
-      if (k > i) continue;
+      const int ii = e / sz, kk = e - ii * sz;
+      if (kk > ii) continue;
+      const int i = s0 + ii, k = s0 + kk;
       const float* li = A + i * ld + J;
       const float* lk = A + k * ld + J;
       float acc = 0.0f;
-      for (int j = 0; j < nb; ++j) acc = fmaf(li[j], lk[j], acc);
+#pragma unroll
+      for (int j = 0; j < CB; ++j) acc = fmaf(li[j], lk[j], acc);
       A[i * ld + k] -= acc;
     }
     __syncthreads();
   }
-  const int nblk = (l + CB - 1) / CB;
 
-  // block rows below the diagonal, in order: X_IJ = -X_II sum_{J<=K<I} L_IK X_KJ
-  float* T = X;  // the strictly-lower blocks of row I are written after their inputs are read
-  for (int Ib = 1; Ib < nblk; ++Ib) {
-    const int I = Ib * CB, ni = min(CB, l - I);
-    // stage 1: S = sum_{K} L_IK X_KJ for every column c < I, rows I..I+ni, into A's upper part
-    // (A's strictly upper triangle is free scratch): S(r, c) stored at A[c * ld + I + r]
-    for (int e = tid; e < ni * I; e += nt) {
-      const int r = e / I, c = e % I;
-      const int Jc = (c / CB) * CB;
+  // off-diagonal blocks of the inverse, block row Ib after block row Ib-1:
+  // S(r, c) = sum_{c<=k<I} L(I+r, k) X(k, c) into A's free upper triangle, then
+  // X(I+r, c) = -sum_{t<=r} X_II(r, t) S(t, c)
+  for (int Ib = 1; Ib < nb16; ++Ib) {
+    const int I = Ib * CB;
+    for (int e = tid; e < CB * I; e += nt) {
+      const int r = e / I, c = e - r * I;
+      const float* lr = A + (I + r) * ld;
       float v = 0.0f;
-      for (int k = Jc + (c - Jc); k < I; ++k) v = fmaf(A[(I + r) * ld + k], X[k * ld + c], v);
+      for (int kb = c / CB; kb < Ib; ++kb) {
+        const int k0 = kb * CB;
+#pragma unroll
+        for (int kk = 0; kk < CB; ++kk) v = fmaf(lr[k0 + kk], X[(k0 + kk) * ld + c], v);
+      }
       A[c * ld + I + r] = v;
     }
     __syncthreads();
-    // stage 2: X(I + r, c) = -sum_t X_II(r, t) S(t, c)
-    for (int e = tid; e < ni * I; e += nt) {
-      const int r = e / I, c = e % I;
+    for (int e = tid; e < CB * I; e += nt) {
+      const int r = e / I, c = e - r * I;
+      const float* xr = X + (I + r) * ld + I;
       float v = 0.0f;
-      for (int t2 = 0; t2 <= r; ++t2) v = fmaf(X[(I + r) * ld + I + t2], A[c * ld + I + t2], v);
-      T[(I + r) * ld + c] = -v;
+#pragma unroll
+      for (int t2 = 0; t2 < CB; ++t2) v = fmaf(xr[t2], A[c * ld + I + t2], v);   // X_II(r, t) = 0, t > r
+      X[(I + r) * ld + c] = -v;
     }
     __syncthreads();
   }
 
-  // outputs: R = L^T, R^-1 = X^T, zero padding
-  for (int e = tid; e < lp * lp; e += nt) {
-    const int a = e / lp, b = e % lp;
-    const bool up = (a < l && b < l && b >= a);
-    r_out[e] = up ? A[b * ld + a] : 0.0f;
-    rinv[e] = up ? X[b * ld + a] : 0.0f;
+  // outputs: R = L^T, R^-1 = X^T restricted to l x l; rows by warps (no division)
+  for (int a = warp; a < lp; a += nw) {
+    for (int b = lane; b < lp; b += 32) {
+      const bool up = (a < l && b < l && b >= a);
+      r_out[(int64_t)a * lp + b] = up ? A[b * ld + a] : 0.0f;
+      rinv[(int64_t)a * lp + b] = up ? X[b * ld + a] : 0.0f;
+    }
   }
   if (racc) {
     __syncthreads();
-    // racc <- R racc (upper triangular product), computed into the free X space
-    float* Pm = X;
-    for (int e = tid; e < l * l; e += nt) {
-      const int a = e / l, b = e % l;
-      float v = 0.0f;
-      if (b >= a) {
-        if (racc_init) {
-          v = A[b * ld + a];
-        } else {
-          for (int c = a; c <= b; ++c) v = fmaf(A[c * ld + a], racc[(int64_t)c * lp + b], v);
+    float* Pm = X;   // racc <- R racc, into the free X space
+    for (int a = warp; a < l; a += nw) {
+      for (int b = lane; b < l; b += 32) {
+        float v = 0.0f;
+        if (b >= a) {
+          if (racc_init) {
+            v = A[b * ld + a];
+          } else {
+            for (int c = a; c <= b; ++c) v = fmaf(A[c * ld + a], racc[(int64_t)c * lp + b], v);
+          }
         }
+        Pm[a * ld + b] = v;
       }
-      Pm[a * ld + b] = v;
     }
     __syncthreads();
-    for (int e = tid; e < lp * lp; e += nt) {
-      const int a = e / lp, b = e % lp;
-      racc[e] = (a < l && b < l && b >= a) ? Pm[a * ld + b] : 0.0f;
-    }
+    for (int a = warp; a < lp; a += nw)
+      for (int b = lane; b < lp; b += 32)
+        racc[(int64_t)a * lp + b] = (a < l && b < l && b >= a) ? Pm[a * ld + b] : 0.0f;
   }
 }
 
