@@ -78,7 +78,13 @@ typedef struct {
   int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation: 2 or 3 (default 3:
                            one shifted round for ill-conditioned samples, then two plain) */
   int64_t lda;          /* leading dimension of A in elements; 0 means n */
+  int32_t small_svd;    /* kernel of the l x l SVD (Algorithm 5.1 step 2): RSVD_SMALL_AUTO
+                           (default), RSVD_SMALL_ONE_CTA (l <= 160) or RSVD_SMALL_CLUSTER
+                           (a thread-block cluster of 4 or 8 CTAs, l <= 256); AUTO takes the
+                           cluster from l = 48 on */
 } rsvd_options_t;
+
+enum { RSVD_SMALL_AUTO = 0, RSVD_SMALL_ONE_CTA = 1, RSVD_SMALL_CLUSTER = 2 };
 
 /* Fill *opt with the defaults: float32 A, Gaussian test matrix, plain FP32,
  * two-pass Stage B, three orthonormalisation rounds, lda = n. */

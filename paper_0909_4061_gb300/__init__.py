@@ -29,6 +29,7 @@ RSVD_ERR_UNSUPPORTED = 7
 RSVD_F32, RSVD_BF16, RSVD_BF16X2 = 0, 1, 2
 RSVD_GAUSSIAN, RSVD_SRFT = 0, 1
 RSVD_PLAIN_FP32, RSVD_BF16_TC = 0, 1
+RSVD_SMALL_AUTO, RSVD_SMALL_ONE_CTA, RSVD_SMALL_CLUSTER = 0, 1, 2
 
 # every symbol include/rsvd.h declares (checked by the CPU tests)
 EXPORTS = (
@@ -63,6 +64,7 @@ class Options(ctypes.Structure):
         ("recompute", ctypes.c_int32),
         ("orth_rounds", ctypes.c_int32),
         ("lda", ctypes.c_int64),
+        ("small_svd", ctypes.c_int32),
     ]
 
 
@@ -270,8 +272,10 @@ class Plan:
     """Owns one rsvd plan; tensors are torch CUDA tensors (row-major, contiguous)."""
 
     def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
-                 lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None):
+                 lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None,
+                 small_svd=RSVD_SMALL_AUTO):
         o = rsvd_options_default()
+        o.small_svd = small_svd
         o.precision = precision
         if dtype is None:
             dtype = RSVD_BF16 if precision == RSVD_BF16_TC else RSVD_F32

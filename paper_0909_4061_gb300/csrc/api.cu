@@ -276,8 +276,8 @@ rsvd_status_t stage_b(rsvd_plan_t P, const void* A, float* U, float* S, float* V
   {
     Step sp(P, RSVD_STEP_SMALL_SVD);
     sp.launched();
-    TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
-                          P->status + 1, P->st));
+    TRY(launch_jacobi_svd(P->racc(), P->lp, 1, P->l, P->lp, P->ut(), P->sig, P->w(), P->lbuf(),
+                          P->status, P->status + 1, P->st, P->opt.small_svd));
   }
   Step sp(P, RSVD_STEP_LIFT);
   sp.launched(2);
@@ -344,7 +344,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
   if (o.test_matrix != RSVD_GAUSSIAN || o.single_pass) return RSVD_ERR_UNSUPPORTED;
-  if (l > 160) return RSVD_ERR_UNSUPPORTED;  // one-CTA Jacobi limit
+  if (o.small_svd < 0 || o.small_svd > 2) return RSVD_ERR_INVALID_ARG;
+  if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
 
   rsvd_plan_t P = new (std::nothrow) rsvd_plan_s();
@@ -361,7 +362,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     delete P;
     return RSVD_ERR_CUDA;
   }
-  if (prepare_orth() != cudaSuccess || prepare_jacobi() != cudaSuccess) {
+  if (prepare_orth() != cudaSuccess || prepare_jacobi() != cudaSuccess ||
+      prepare_jacobi_cluster() != cudaSuccess) {
     cudaGetLastError();
     delete P;
     return RSVD_ERR_CUDA;
@@ -647,8 +649,8 @@ rsvd_status_t rsvd_small_svd(rsvd_plan_t P, const float* X, float* Ut, float* S,
   TRYS(check_plan(P));
   if (!X || !Ut || !S || !W) return RSVD_ERR_INVALID_ARG;
   TRY(launch_gather(X, 1, 0, P->l, P->sq(), P->lp, P->l, P->l, P->lp, P->st));
-  TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->status,
-                        P->status + 1, P->st));
+  TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->lbuf(),
+                        P->status, P->status + 1, P->st, P->opt.small_svd));
   TRY(launch_gather(P->ut(), 1, 0, P->lp, Ut, P->l, P->l, P->l, P->l, P->st));
   TRY(launch_gather(P->w(), 1, 0, P->lp, W, P->l, P->l, P->l, P->l, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->l, cudaMemcpyDeviceToDevice, P->st));

@@ -339,8 +339,11 @@ cudaError_t prepare_jacobi() {
 size_t jacobi_smem_bytes(int l) { return (size_t)(2 * l * l + 2 * l + 4) * sizeof(float); }
 
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp, float* ut,
-                              float* s, float* w, uint32_t* status, uint32_t* info,
-                              cudaStream_t st) {
+                              float* s, float* w, float* scratch, uint32_t* status,
+                              uint32_t* info, cudaStream_t st, int variant) {
+  // the cluster kernel is faster from a few dozen columns on (about 2x at l = 110)
+  if (variant == 2 || (variant == 0 && l >= 48))
+    return launch_jacobi_cluster(x, ldx, transposed, l, lp, ut, s, w, scratch, status, info, st);
   if (l > kMaxJacobiL) return cudaErrorInvalidValue;
   const size_t smem = jacobi_smem_bytes(l);
   // a pair counts as orthogonal below 8 sqrt(l) u: above the float32 rounding floor of

@@ -86,45 +86,74 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* __restri
         for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(yi[a], yj[b], acc[a][b]);
     }
   }
+  // partial block (row-major lp x lp); rows ib..ib+7 as two float4 per row, so a
+  // warp writes two 512-byte row segments (the mirrored tile of an off-diagonal pair
+  // goes out column by column)
   float* g = gpart + (int64_t)blk * lp * lp;
+  if (ib < lp && jb < lp) {
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 8; ++a) {
+      float4* dst = reinterpret_cast<float4*>(g + (int64_t)(ib + a) * lp + jb);
+      dst[0] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+      dst[1] = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+    }
+    if (I != J) {
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int i = ib + a, j = jb + b;
-      if (i < lp && j < lp) {
-        g[(int64_t)i * lp + j] = acc[a][b];
-        if (I != J) g[(int64_t)j * lp + i] = acc[a][b];
+      for (int b = 0; b < 8; ++b) {
+        float4* dst = reinterpret_cast<float4*>(g + (int64_t)(jb + b) * lp + ib);
+        dst[0] = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+        dst[1] = make_float4(acc[4][b], acc[5][b], acc[6][b], acc[7][b]);
       }
     }
+  }
 }
 
-__global__ void gram_reduce_kernel(const float* __restrict__ gpart, int nblk, int lp,
-                                   float* __restrict__ g) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// G = sum_b G_b for the lower triangle (the factorisation reads no more): a block
+// of 512 threads takes 32 consecutive elements (one per lane) and splits the nblk
+// partials into 16 contiguous ranges (one per warp), each summed with Kahan
+// compensation with all of its loads in flight; the 16 (sum, compensation) pairs
+// are then combined in range order, so the result does not depend on timing.
+constexpr int kRedSplit = 16;
+constexpr int kRedBatch = 24;
+
+__global__ void __launch_bounds__(512) gram_reduce_kernel(const float* __restrict__ gpart, int nblk,
+                                                          int lp, float* __restrict__ g) {
+  __shared__ float s_sum[kRedSplit][32], s_cmp[kRedSplit][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = (int64_t)lp * lp;
-  if (e >= n) return;
-  float s = 0.0f, c = 0.0f;  // Kahan-compensated sum in a fixed order
-  int b = 0;
-  for (; b + 8 <= nblk; b += 8) {
-    float v[8];
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int i = (int)(e / lp), j = (int)(e - (int64_t)i * lp);
+  const bool live = e < n && j <= i;
+  const int per = (nblk + kRedSplit - 1) / kRedSplit;
+  const int b0 = w * per, b1 = min(nblk, b0 + per);
+  float s = 0.0f, c = 0.0f;
+  if (live) {
+    for (int b = b0; b < b1; b += kRedBatch) {
+      float v[kRedBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = gpart[(int64_t)(b + u) * n + e];   // loads in flight together
+      for (int u = 0; u < kRedBatch; ++u) v[u] = (b + u < b1) ? gpart[(int64_t)(b + u) * n + e] : 0.0f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const float y = v[u] - c;
-      const float t = s + y;
-      c = (t - s) - y;
-      s = t;
+      for (int u = 0; u < kRedBatch; ++u) {
+        const float y = v[u] - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+      }
     }
   }
-  for (; b < nblk; ++b) {
-    const float y = gpart[(int64_t)b * n + e] - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
+  s_sum[w][lane] = s;
+  s_cmp[w][lane] = c;
+  __syncthreads();
+  if (w == 0 && e < n) {
+    float S = 0.0f, C = 0.0f;
+    for (int q = 0; q < kRedSplit; ++q) {
+      const float y = s_sum[q][lane] - (s_cmp[q][lane] + C);
+      const float t = S + y;
+      C = (t - S) - y;
+      S = t;
+    }
+    g[e] = live ? S : 0.0f;
   }
-  g[e] = s;
 }
 
 __device__ __forceinline__ int tri_off(int i) { return i * (i + 1) / 2; }            // row i of packed lower
@@ -265,49 +294,87 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
   }
 }
 
-// Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA, both held in shared
-// memory as full squares (row stride lp + 1), for lp <= 160.  The factor works on
-// the padded size lp (a multiple of 16) with identity rows and columns beyond l,
-// so every block is a full 16 x 16 and every inner loop has a compile-time trip
-// count (unrolled, shared-memory loads in flight together).  Per block column:
-// the diagonal block is factored and inverted by warp 0 in registers, the panel
-// below it is L_iJ = A_iJ L_JJ^-T (a small product with the block inverse), and
-// the trailing lower triangle is updated by all threads.  The off-diagonal blocks
-// of the inverse follow block row by block row.  Outputs: R = L^T, R^-1 = X^T and
-// the optional product racc <- R racc, restricted to l x l (zero elsewhere).
+// Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA of 512 threads, both
+// held in shared memory as full squares, for LP = 16 NB <= 160.  The row stride
+// LP + 4 keeps rows 16-byte aligned (float4 loads along a row) with an odd number of
+// float4 per row (a column of float4 loads hits distinct banks).  The factor works
+// on the padded size LP with identity rows and columns beyond l, so every block is
+// a full 16 x 16.  Per block column J: warp 0 factors and inverts the diagonal block
+// in registers (lane = row, shuffles, pivots by a Newton-refined reciprocal square
+// root; branch-free: entries above the diagonal are left as scratch and never read);
+// the panel below is L_iJ = A_iJ X_JJ^T; the trailing lower triangle is updated by
+// all warps, two rows per warp and one column per lane.  The off-diagonal blocks of
+// X follow block row by block row: S = L_I,<I X_<I,<I in 2 x 4 register tiles, then
+// X_I,<I = -X_II S.  Every inner product reads shared memory as float4, so the
+// shared-memory pipe, not the FMA units, sets the pace only where unavoidable.
+// Outputs: R = L^T, R^-1 = X^T and the optional product racc <- R racc, restricted
+// to l x l.  The block loops stay rolled: unrolled, the code outgrows the
+// instruction cache.
 constexpr int CB = 16;
 
-__global__ void __launch_bounds__(512) cholesky_blocked_kernel(
-    const float* __restrict__ g, int l, int lp, int shifted, float* __restrict__ r_out,
-    float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status) {
-  extern __shared__ __align__(16) float sm[];
-  const int ld = lp + 1;
-  float* A = sm;               // lower: L
-  float* X = sm + lp * ld;     // lower: L^-1
-  __shared__ float s_red[2][32];
-  __shared__ float s_shift, s_floor;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  const int nb16 = lp / CB;
+__device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
 
-  // load the lower triangle of G (identity beyond l), clear X; rows by warps
-  for (int i = warp; i < lp; i += nw) {
-    const float* gi = g + (int64_t)i * lp;
-    for (int j = lane; j < lp; j += 32) {
-      float v = 0.0f;
-      if (i < l && j < l) v = gi[j];
-      else if (i == j) v = 1.0f;
-      A[i * ld + j] = (j <= i) ? v : 0.0f;
-      X[i * ld + j] = 0.0f;
-    }
-  }
+__device__ __forceinline__ float4 axpy4(float s, const float4 x, float4 y) {
+  y.x = fmaf(s, x.x, y.x);
+  y.y = fmaf(s, x.y, y.y);
+  y.z = fmaf(s, x.z, y.z);
+  y.w = fmaf(s, x.w, y.w);
+  return y;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(512) cholesky_blocked_kernel(
+    const float* __restrict__ g, int l, int shifted, float* __restrict__ r_out,
+    float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status) {
+  constexpr int LP = CB * NB;
+  constexpr int LD = LP + 4;
+  constexpr int NW = 16;                 // warps
+  constexpr int NCOL = (LP + 31) / 32;   // columns per lane in row-by-warp loops
+  extern __shared__ __align__(16) float sm[];
+  float* A = sm;               // lower: L (above the diagonal: scratch)
+  float* X = sm + LP * LD;     // lower: L^-1 (above the diagonal: zero)
+  __shared__ float s_red[2][NW];
+  __shared__ float s_shift, s_floor;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+
+  // load the lower triangle of G (identity beyond l), all loads in flight together
   float tr = 0.0f, mx = 0.0f;
   bool bad = false;
-  for (int i = tid; i < l; i += nt) {
-    const float d = g[(int64_t)i * lp + i];
-    if (!isfinite(d)) bad = true;
-    tr += d;
-    mx = fmaxf(mx, d);
+  {
+    float v[NB][NCOL];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) {
+        const int i = warp + NW * r, j = lane + 32 * c;
+        v[r][c] = (j <= i && i < l) ? g[i * LP + j] : 0.0f;   // lower triangle only
+      }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) {
+        const int i = warp + NW * r, j = lane + 32 * c;
+        if (j < LP) {
+          float w = v[r][c];
+          if (i == j) {
+            if (i < l) {
+              bad |= !isfinite(w);
+              tr += w;
+              mx = fmaxf(mx, w);
+            } else {
+              w = 1.0f;
+            }
+          }
+          A[i * LD + j] = (j <= i) ? w : 0.0f;
+          X[i * LD + j] = 0.0f;
+        }
+      }
   }
   if (bad) set_status(status, ST_NONFINITE);
   tr = warp_sum(tr);
@@ -317,153 +384,205 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   __syncthreads();
   if (tid == 0) {
     float t = 0.0f, m = 0.0f;
-    for (int w = 0; w < nw; ++w) { t += s_red[0][w]; m = fmaxf(m, s_red[1][w]); }
+    for (int w = 0; w < NW; ++w) { t += s_red[0][w]; m = fmaxf(m, s_red[1][w]); }
     s_shift = shifted ? (float)l * kEpsF32 * t : 0.0f;
     s_floor = fmaxf((float)l * kEpsF32 * m, 1e-30f);
   }
   __syncthreads();
   const float pfloor = s_floor;
-  for (int i = tid; i < l; i += nt) A[i * ld + i] += s_shift;
+  if (tid < l) A[tid * LD + tid] += s_shift;
   __syncthreads();
 
-  for (int jb = 0; jb < nb16; ++jb) {
+#pragma unroll 1
+  for (int jb = 0; jb < NB; ++jb) {
     const int J = jb * CB;
-    // (1) diagonal block by warp 0 in registers: lane i < 16 holds row i
+    // (1) diagonal block by warp 0: lanes r and r + 16 both hold row r (mirrored)
     if (warp == 0) {
-      float a[CB];
+      const int r = lane & 15;
+      float a[CB], rpv[CB];
+      {
+        const float4* src = reinterpret_cast<const float4*>(A + (J + r) * LD + J);
 #pragma unroll
-      for (int j = 0; j < CB; ++j)
-        a[j] = (lane < CB) ? (j <= lane ? A[(J + lane) * ld + J + j] : 0.0f) : (j == lane ? 1.0f : 0.0f);
+        for (int q = 0; q < 4; ++q) {
+          const float4 t = src[q];
+          a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < CB; ++j) {
         float d = __shfl_sync(0xffffffffu, a[j], j);
-        if (J + j < l && !(d > pfloor)) {
+        if (J + j < l && !(d > pfloor)) {   // d is the same in every lane
           if (lane == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
           d = pfloor;
         }
-        const float piv = sqrtf(d);
-        const float rp = 1.0f / piv;
-        const float lij = (lane == j) ? piv : (lane > j ? a[j] * rp : 0.0f);
+        // 1/sqrt(d) by the hardware estimate and one Newton step y <- y (3 - d y^2) / 2
+        float rp = rsqrtf(d);
+        rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);
+        rpv[j] = rp;
+        const float lij = (r == j) ? d * rp : (r > j ? a[j] * rp : 0.0f);
         a[j] = lij;
 #pragma unroll
-        for (int k = j + 1; k < CB; ++k) {
-          const float lkj = __shfl_sync(0xffffffffu, lij, k);
-          if (lane >= k) a[k] = fmaf(-lij, lkj, a[k]);
-        }
+        for (int k = j + 1; k < CB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), a[k]);
       }
+      // X_JJ = L_JJ^-1 by columns: lane r holds column r, x[i] = X(i, r), zero for i < r
       float x[CB];
 #pragma unroll
       for (int i = 0; i < CB; ++i) {
-        float v = 0.0f;
+        float v0 = 0.0f, v1 = 0.0f;
 #pragma unroll
         for (int k = 0; k < i; ++k) {
           const float lik = __shfl_sync(0xffffffffu, a[k], i);
-          if (k >= lane) v = fmaf(lik, x[k], v);
+          if (k & 1) v1 = fmaf(lik, x[k], v1);
+          else v0 = fmaf(lik, x[k], v0);
         }
-        const float lii = __shfl_sync(0xffffffffu, a[i], i);
-        x[i] = (i > lane) ? -v / lii : (i == lane ? 1.0f / lii : 0.0f);
+        x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
       }
       if (lane < CB) {
+        float4* dst = reinterpret_cast<float4*>(A + (J + r) * LD + J);
 #pragma unroll
-        for (int j = 0; j < CB; ++j)
-          if (j <= lane) A[(J + lane) * ld + J + j] = a[j];
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
 #pragma unroll
-        for (int i = 0; i < CB; ++i)
-          if (i >= lane) X[(J + i) * ld + J + lane] = x[i];
+        for (int i = 0; i < CB; ++i) X[(J + i) * LD + J + r] = x[i];
       }
     }
     __syncthreads();
-    // (2) panel: l_ij = sum_{k<=j} a_ik X_JJ(j, k), rows below the block; staged in the
-    // strictly lower part of X (free until the inverse), then copied into A
-    const int prow = lp - J - CB;
-    for (int e = tid; e < prow * CB; e += nt) {
-      const int i = J + CB + (e >> 4), j = e & (CB - 1);
-      const float* ai = A + i * ld + J;
-      const float* xj = X + (J + j) * ld + J;
-      float v = 0.0f;
-#pragma unroll
-      for (int k = 0; k < CB; ++k) v = fmaf(ai[k], xj[k], v);   // X_JJ(j, k) = 0 for k > j
-      X[i * ld + J + j] = v;
+    const int s0 = J + CB;
+    if (s0 < LP) {
+      // (2) panel, in place: L_iJ(c) = sum_k A_iJ(k) X_JJ(c, k); a half-warp per row
+      {
+        const int c = tid & 15;
+        const float4* xc = reinterpret_cast<const float4*>(X + (J + c) * LD + J);
+        const float4 x0 = xc[0], x1 = xc[1], x2 = xc[2], x3 = xc[3];
+        for (int i = s0 + (tid >> 4); i < LP; i += 32) {
+          float* ai = A + i * LD + J;
+          const float4* a4 = reinterpret_cast<const float4*>(ai);
+          const float v = dot4(a4[0], x0, dot4(a4[2], x2, 0.0f)) + dot4(a4[1], x1, dot4(a4[3], x3, 0.0f));
+          __syncwarp();
+          ai[c] = v;
+        }
+      }
+      __syncthreads();
+      // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ; rows i0, i0 + 1 per warp, k per lane
+      for (int ip = warp; 2 * ip < LP - s0; ip += NW) {
+        const int i0 = s0 + 2 * ip, i1 = i0 + 1;
+        const float4* p0 = reinterpret_cast<const float4*>(A + i0 * LD + J);
+        const float4* p1 = reinterpret_cast<const float4*>(A + i1 * LD + J);
+        const float4 u0 = p0[0], u1 = p0[1], u2 = p0[2], u3 = p0[3];
+        const float4 w0 = p1[0], w1 = p1[1], w2 = p1[2], w3 = p1[3];
+        for (int k = s0 + lane; k <= i1; k += 32) {
+          const float4* pk = reinterpret_cast<const float4*>(A + k * LD + J);
+          const float4 k0 = pk[0], k1 = pk[1], k2 = pk[2], k3 = pk[3];
+          const float a0 = dot4(u0, k0, dot4(u1, k1, 0.0f)) + dot4(u2, k2, dot4(u3, k3, 0.0f));
+          const float a1 = dot4(w0, k0, dot4(w1, k1, 0.0f)) + dot4(w2, k2, dot4(w3, k3, 0.0f));
+          if (k <= i0) A[i0 * LD + k] -= a0;
+          A[i1 * LD + k] -= a1;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // off-diagonal blocks of the inverse, block row I after block row I-1:
+  // S(r, c) = sum_{c<=k<I} L(I+r, k) X(k, c) into A's scratch upper triangle
+  // (A[c][I + r], c < I), then X(I+r, c) = -sum_{t<=r} X_II(r, t) S(t, c)
+#pragma unroll 1
+  for (int ib = 1; ib < NB; ++ib) {
+    const int I = ib * CB;
+    for (int t = tid; t < 2 * I; t += 512) {   // tiles of rows 2rp, 2rp+1 x columns 4cq..4cq+3
+      const int rp = t & 7, c0 = 4 * (t >> 3);
+      const float* la = A + (I + 2 * rp) * LD;
+      const float* lb = la + LD;
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+      for (int k = c0; k < I; ++k) {   // X(k, c0 + q) = 0 for k < c0 + q
+        const float4 xk = *reinterpret_cast<const float4*>(X + k * LD + c0);
+        s0 = axpy4(la[k], xk, s0);
+        s1 = axpy4(lb[k], xk, s1);
+      }
+      float* d0 = A + c0 * LD + I + 2 * rp;
+      d0[0] = s0.x; d0[1] = s1.x;
+      d0[LD] = s0.y; d0[LD + 1] = s1.y;
+      d0[2 * LD] = s0.z; d0[2 * LD + 1] = s1.z;
+      d0[3 * LD] = s0.w; d0[3 * LD + 1] = s1.w;
     }
     __syncthreads();
-    for (int e = tid; e < prow * CB; e += nt) {
-      const int i = J + CB + (e >> 4), j = e & (CB - 1);
-      A[i * ld + J + j] = X[i * ld + J + j];
-      X[i * ld + J + j] = 0.0f;
-    }
-    __syncthreads();
-    // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ  (16-term dots, unrolled)
-    const int s0 = J + CB, sz = lp - s0;
-    for (int e = tid; e < sz * sz; e += nt) {
-      const int ii = e / sz, kk = e - ii * sz;
-      if (kk > ii) continue;
-      const int i = s0 + ii, k = s0 + kk;
-      const float* li = A + i * ld + J;
-      const float* lk = A + k * ld + J;
-      float acc = 0.0f;
-#pragma unroll
-      for (int j = 0; j < CB; ++j) acc = fmaf(li[j], lk[j], acc);
-      A[i * ld + k] -= acc;
+    {
+      const int r = tid & 15;
+      const float4* xr = reinterpret_cast<const float4*>(X + (I + r) * LD + I);
+      const float4 x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];   // X_II row r (zero beyond r)
+      for (int c = tid >> 4; c < I; c += 32) {
+        const float4* sc = reinterpret_cast<const float4*>(A + c * LD + I);
+        const float v = dot4(x0, sc[0], dot4(x2, sc[2], 0.0f)) + dot4(x1, sc[1], dot4(x3, sc[3], 0.0f));
+        X[(I + r) * LD + c] = -v;
+      }
     }
     __syncthreads();
   }
 
-  // off-diagonal blocks of the inverse, block row Ib after block row Ib-1:
-  // S(r, c) = sum_{c<=k<I} L(I+r, k) X(k, c) into A's free upper triangle, then
-  // X(I+r, c) = -sum_{t<=r} X_II(r, t) S(t, c)
-  for (int Ib = 1; Ib < nb16; ++Ib) {
-    const int I = Ib * CB;
-    for (int e = tid; e < CB * I; e += nt) {
-      const int r = e / I, c = e - r * I;
-      const float* lr = A + (I + r) * ld;
-      float v = 0.0f;
-      for (int kb = c / CB; kb < Ib; ++kb) {
-        const int k0 = kb * CB;
+  // outputs: R = L^T, R^-1 = X^T restricted to l x l; rows by warps
 #pragma unroll
-        for (int kk = 0; kk < CB; ++kk) v = fmaf(lr[k0 + kk], X[(k0 + kk) * ld + c], v);
+  for (int r = 0; r < NB; ++r) {
+    const int a = warp + NW * r;
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+      const int b = lane + 32 * c;
+      if (b < LP) {
+        const bool up = (a < l && b < l && b >= a);
+        r_out[a * LP + b] = up ? A[b * LD + a] : 0.0f;
+        rinv[a * LP + b] = up ? X[b * LD + a] : 0.0f;
       }
-      A[c * ld + I + r] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < CB * I; e += nt) {
-      const int r = e / I, c = e - r * I;
-      const float* xr = X + (I + r) * ld + I;
-      float v = 0.0f;
-#pragma unroll
-      for (int t2 = 0; t2 < CB; ++t2) v = fmaf(xr[t2], A[c * ld + I + t2], v);   // X_II(r, t) = 0, t > r
-      X[(I + r) * ld + c] = -v;
-    }
-    __syncthreads();
-  }
-
-  // outputs: R = L^T, R^-1 = X^T restricted to l x l; rows by warps (no division)
-  for (int a = warp; a < lp; a += nw) {
-    for (int b = lane; b < lp; b += 32) {
-      const bool up = (a < l && b < l && b >= a);
-      r_out[(int64_t)a * lp + b] = up ? A[b * ld + a] : 0.0f;
-      rinv[(int64_t)a * lp + b] = up ? X[b * ld + a] : 0.0f;
     }
   }
   if (racc) {
-    __syncthreads();
-    float* Pm = X;   // racc <- R racc, into the free X space
-    for (int a = warp; a < l; a += nw) {
-      for (int b = lane; b < l; b += 32) {
-        float v = 0.0f;
-        if (b >= a) {
-          if (racc_init) {
-            v = A[b * ld + a];
-          } else {
-            for (int c = a; c <= b; ++c) v = fmaf(A[c * ld + a], racc[(int64_t)c * lp + b], v);
-          }
+    if (racc_init) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        const int a = warp + NW * r;
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+          const int b = lane + 32 * c;
+          if (b < LP) racc[a * LP + b] = (a < l && b < l && b >= a) ? A[b * LD + a] : 0.0f;
         }
-        Pm[a * ld + b] = v;
       }
+      return;
     }
     __syncthreads();
-    for (int a = warp; a < lp; a += nw)
-      for (int b = lane; b < lp; b += 32)
-        racc[(int64_t)a * lp + b] = (a < l && b < l && b >= a) ? Pm[a * ld + b] : 0.0f;
+    // stage the old racc (upper, l x l) in the free X space, then racc <- R racc in
+    // 1 x 4 strips: P(a, b0..b0+3) = sum_{a<=c<=b0+3} R(a, c) Ro(c, b0..b0+3)
+    float* Ro = X;
+    {
+      float v[NB][NCOL];
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+          const int i = warp + NW * r, j = lane + 32 * c;
+          v[r][c] = (j < LP) ? racc[i * LP + j] : 0.0f;
+        }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+          const int i = warp + NW * r, j = lane + 32 * c;
+          if (j < LP) Ro[i * LD + j] = v[r][c];
+        }
+    }
+    __syncthreads();
+    constexpr int NQ = LP / 4;
+    for (int t = tid; t < LP * NQ; t += 512) {
+      const int a = t / NQ, b0 = 4 * (t - a * NQ);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a < l && b0 + 3 >= a) {
+        const int cend = min(b0 + 3, l - 1);
+        for (int c = a; c <= cend; ++c)
+          acc = axpy4(A[c * LD + a], *reinterpret_cast<const float4*>(Ro + c * LD + b0), acc);
+      }
+      float4 o;
+      o.x = (a < l && b0 < l && b0 >= a) ? acc.x : 0.0f;
+      o.y = (a < l && b0 + 1 < l && b0 + 1 >= a) ? acc.y : 0.0f;
+      o.z = (a < l && b0 + 2 < l && b0 + 2 >= a) ? acc.z : 0.0f;
+      o.w = (a < l && b0 + 3 < l && b0 + 3 >= a) ? acc.w : 0.0f;
+      *reinterpret_cast<float4*>(racc + a * LP + b0) = o;
+    }
   }
 }
 
@@ -536,11 +655,23 @@ __global__ void gather_kernel(const float* __restrict__ src, int splits, int64_t
 
 // Shared-memory limits of the one-CTA factorisation kernels, for every size they accept;
 // set once per device (at plan creation) so no launch needs a host-side attribute call.
+template <int NB>
+size_t chol_smem() { return (size_t)2 * (CB * NB) * (CB * NB + 4) * sizeof(float); }
+
+template <int NB>
+cudaError_t prep_chol() {
+  return cudaFuncSetAttribute(cholesky_blocked_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)chol_smem<NB>());
+}
+
 cudaError_t prepare_orth() {
-  cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((size_t)2 * 160 * 161 * sizeof(float)));
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if ((e = prep_chol<1>()) != cudaSuccess || (e = prep_chol<2>()) != cudaSuccess ||
+      (e = prep_chol<3>()) != cudaSuccess || (e = prep_chol<4>()) != cudaSuccess ||
+      (e = prep_chol<5>()) != cudaSuccess || (e = prep_chol<6>()) != cudaSuccess ||
+      (e = prep_chol<7>()) != cudaSuccess || (e = prep_chol<8>()) != cudaSuccess ||
+      (e = prep_chol<9>()) != cudaSuccess || (e = prep_chol<10>()) != cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(((size_t)kMaxL * (kMaxL + 1) / 2 + kMaxL + 4 + kMaxL) *
                                     sizeof(float)));
@@ -564,18 +695,25 @@ cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stri
 
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st) {
   const int64_t n = (int64_t)lp * lp;
-  gram_reduce_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(gpart, nblk, lp, g);
+  gram_reduce_kernel<<<(unsigned)cdiv(n, 32), 512, 0, st>>>(gpart, nblk, lp, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,
                             float* rinv, float* racc, int racc_init, uint32_t* status,
                             cudaStream_t st) {
-  if (lp <= 160) {
-    const size_t sm = (size_t)2 * lp * (lp + 1) * sizeof(float);
-    cholesky_blocked_kernel<<<1, 512, sm, st>>>(g, l, lp, shifted, r_out, rinv, racc, racc_init,
-                                                status);
+  if (lp <= 160 && lp % CB == 0) {
+#define RSVD_CHOL_CASE(NB)                                                                  \
+  case NB:                                                                                 \
+    cholesky_blocked_kernel<NB><<<1, 512, chol_smem<NB>(), st>>>(g, l, shifted, r_out, rinv, \
+                                                                 racc, racc_init, status);  \
     return cudaGetLastError();
+    switch (lp / CB) {
+      RSVD_CHOL_CASE(1) RSVD_CHOL_CASE(2) RSVD_CHOL_CASE(3) RSVD_CHOL_CASE(4) RSVD_CHOL_CASE(5)
+      RSVD_CHOL_CASE(6) RSVD_CHOL_CASE(7) RSVD_CHOL_CASE(8) RSVD_CHOL_CASE(9) RSVD_CHOL_CASE(10)
+      default: break;
+    }
+#undef RSVD_CHOL_CASE
   }
   const size_t smem = ((size_t)l * (l + 1) / 2 + l + 4 + kMaxL) * sizeof(float);
   cholesky_kernel<<<1, 1024, smem, st>>>(g, l, lp, shifted, lbuf, r_out, rinv, racc, racc_init,

@@ -55,9 +55,11 @@ cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64
 // One-sided Jacobi SVD of X = R^T (transposed = 1, R row-major l x l, ld) or X (transposed = 0).
 // Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
 // info (may be null): atomicMax of the number of sweeps taken.
+// variant: 0 = one CTA up to l = 160, else the cluster; 1 = one CTA; 2 = cluster.
+// scratch: lp x lp floats of workspace (used by the cluster variant).
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp,
-                              float* ut, float* s, float* w, uint32_t* status, uint32_t* info,
-                              cudaStream_t st);
+                              float* ut, float* s, float* w, float* scratch, uint32_t* status,
+                              uint32_t* info, cudaStream_t st, int variant = 0);
 size_t jacobi_smem_bytes(int l);
 
 // dst[r][c] = sum_{s < splits} src[s][r][c] for c < cols, 0 for cols <= c < cols_pad
@@ -65,6 +67,12 @@ size_t jacobi_smem_bytes(int l);
 cudaError_t launch_gather(const float* src, int splits, int64_t split_stride, int64_t lds,
                           float* dst, int64_t ldd, int64_t rows, int cols, int cols_pad,
                           cudaStream_t st);
+
+// The same SVD on a thread-block cluster (block round-robin ordering), l <= 256.
+cudaError_t launch_jacobi_cluster(const float* x, int64_t ldx, int transposed, int l, int lp,
+                                  float* ut, float* s, float* w, float* scratch, uint32_t* status,
+                                  uint32_t* info, cudaStream_t st);
+cudaError_t prepare_jacobi_cluster();
 
 // One-time (per device) shared-memory attributes of the one-CTA kernels.
 cudaError_t prepare_orth();

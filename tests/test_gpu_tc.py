@@ -42,7 +42,8 @@ def _plan(pkg, m, n, k, p, q, seed, lda=0, rounds=3):
 
 
 @pytest.mark.parametrize("m,n,l,lda", [(512, 384, 32, 0), (517, 1000, 16, 0), (1000, 520, 112, 0),
-                                       (300, 389, 48, 392), (2048, 4096, 128, 0), (700, 640, 160, 0)])
+                                       (300, 389, 48, 392), (2048, 4096, 128, 0), (700, 640, 160, 0),
+                                       (1000, 1104, 256, 0)])
 def test_tc_sketch_matches_oracle(rsvd_lib, m, n, l, lda):
     rng = np.random.default_rng(m * 3 + n)
     ld = lda if lda else n
@@ -97,7 +98,8 @@ def test_tc_rsvd_c1_full_size(rsvd_lib):
     _check_ritz(ab, u, s, v, w.k, w.p, w.q, om)
 
 
-@pytest.mark.parametrize("m,n,k,p,q", [(1024, 768, 30, 10, 1), (777, 520, 12, 4, 2), (3000, 256, 100, 12, 1)])
+@pytest.mark.parametrize("m,n,k,p,q", [(1024, 768, 30, 10, 1), (777, 520, 12, 4, 2), (3000, 256, 100, 12, 1),
+                                       (1104, 896, 236, 20, 1)])
 def test_tc_rsvd_shapes(rsvd_lib, m, n, k, p, q):
     a, *_ = synth.lowrank(m, n, synth.spectrum_exp(min(m, n), 9.0), m + n)
     ab = _bf16(a)
