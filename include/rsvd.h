@@ -67,7 +67,11 @@ enum { RSVD_PLAIN_FP32 = 0, RSVD_BF16_TC = 1 };       /* how the passes over A a
 
 typedef struct {
   int32_t dtype_A;      /* RSVD_F32, RSVD_BF16 or RSVD_BF16X2 */
-  int32_t test_matrix;  /* RSVD_GAUSSIAN (default) or RSVD_SRFT */
+  int32_t test_matrix;  /* RSVD_GAUSSIAN (default) or RSVD_SRFT: sqrt(n/l_c) D F R with
+                           random +-1 signs D, the unitary DFT F and l_c = l / 2 frequencies
+                           from {1 .. n/2 - 1} without replacement; for a real A the l real
+                           columns are [Re, Im] of each sampled frequency.  Needs l and n
+                           even and n < 2^24 */
   int32_t precision;    /* RSVD_PLAIN_FP32: float32 A, float32 FMA on CUDA cores.
                            RSVD_BF16_TC: bfloat16 A (RSVD_BF16 or RSVD_BF16X2), tcgen05
                            tensor-core products with float32 accumulation, float32

@@ -44,6 +44,7 @@ struct rsvd_plan_s {
   float* gpart = nullptr;    // nblk x lp x lp
   float* small = nullptr;    // 8 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch
   float* sig = nullptr;      // lp
+  int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
   uint32_t* status = nullptr;
   __nv_bfloat16* xbf = nullptr;  // 2 lp x maxmn: transposed bfloat16 operand of the tensor-core passes
   TcPlan tc{};
@@ -110,7 +111,7 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev};
+                  P->v_dev, P->srft_freq};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
@@ -175,7 +176,10 @@ class Step {
 rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
   Step sp(P, RSVD_STEP_DRAW);
   sp.launched();
-  if (!P->omega_user) {
+  if (!P->omega_user && P->opt.test_matrix == RSVD_SRFT) {
+    TRY(launch_draw_srft(P->seed, P->n, P->l / 2, P->lp, P->srft_freq, P->omega, P->lp,
+                         want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
+  } else if (!P->omega_user) {
     TRY(launch_draw_gaussian(P->seed, 0u, P->n, P->l, P->lp, P->omega, P->lp,
                              want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
   } else if (want_bf16) {
@@ -343,7 +347,12 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.precision == RSVD_PLAIN_FP32 && o.dtype_A != RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
-  if (o.test_matrix != RSVD_GAUSSIAN || o.single_pass) return RSVD_ERR_UNSUPPORTED;
+  if (o.test_matrix != RSVD_GAUSSIAN && o.test_matrix != RSVD_SRFT) return RSVD_ERR_INVALID_ARG;
+  // SRFT: l real columns are l / 2 frequencies from {1 .. n/2 - 1} (Section 4.6 for real A)
+  if (o.test_matrix == RSVD_SRFT &&
+      ((l & 1) || (n & 1) || l / 2 > n / 2 - 1 || n >= ((int64_t)1 << 24)))
+    return RSVD_ERR_INVALID_ARG;
+  if (o.single_pass) return RSVD_ERR_UNSUPPORTED;
   if (o.small_svd < 0 || o.small_svd > 2) return RSVD_ERR_INVALID_ARG;
   if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
@@ -389,6 +398,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (s = dalloc(P, &P->gpart, (size_t)nblk * lp * lp)) != RSVD_OK ||
       (s = dalloc(P, &P->small, (size_t)8 * lp * lp)) != RSVD_OK ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
+      (o.test_matrix == RSVD_SRFT && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
     free_plan(P);
     return s;
@@ -405,6 +415,12 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       return RSVD_ERR_CUDA;
     }
     P->tc.status = P->status;
+  }
+  if (o.test_matrix == RSVD_SRFT &&
+      launch_srft_select(seed, n, (int)(l / 2), P->srft_freq, P->st) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(P);
+    return RSVD_ERR_CUDA;
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
       cudaMemsetAsync(P->small, 0, sizeof(float) * 8 * lp * lp, P->st) != cudaSuccess) {

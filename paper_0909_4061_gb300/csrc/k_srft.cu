@@ -1,0 +1,115 @@
+// Subsampled random Fourier transform test matrix (Section 4.6, Algorithm 4.5
+// step 1), Omega = sqrt(n / l_c) D F R, for a real A.
+//
+// D: random signs d_i = +-1; F: the unitary n-point DFT, f_pq = n^-1/2
+// exp(-2 pi i p q / n) (0-based); R: l_c frequencies drawn without replacement.
+// A is real, so the columns of A D F at b and n - b are complex conjugates: the
+// frequencies come from {1, ..., n/2 - 1} (one per conjugate pair; 0 and n/2 are
+// self-conjugate) and the real test matrix interleaves [Re w_c, Im w_c], n x 2 l_c,
+// which spans the same real space as the complex samples at b_c and n - b_c.
+//
+// The sketch Y = A Omega is then an ordinary pass over A on the tensor cores.
+// Applying F by an FFT would save arithmetic, not memory traffic, and a pass over A
+// is bound by HBM here at l <= 256 (l flop per byte of bf16 A, against a ridge near
+// 300), so the structured matrix is materialised (n x l, a few MB) instead.
+//
+// Draws (Philox4x32-10, stream 2): d_i is the top bit of word i mod 4 of counter
+// (i / 4, 0, 2, 0); candidate b has key word b mod 4 of counter (b / 4, 1, 2, 0);
+// the l_c candidates with the smallest (key, b) are taken in ascending order.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace rsvd {
+namespace {
+
+constexpr uint32_t kStreamSrft = 2u;
+constexpr int kSelThreads = 1024;
+constexpr int kSelN = 2048;   // merge buffer: best (<= 1024 kept) + one chunk of 1024
+
+__device__ __forceinline__ uint32_t srft_word(uint2 key, uint32_t row, uint64_t idx) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)(idx >> 2), row, kStreamSrft, 0u), key);
+  const uint32_t q = (uint32_t)(idx & 3u);
+  return q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+}
+
+// One CTA: keep the lc smallest (key << 32 | b) seen so far; each chunk of 1024
+// candidates is sorted together with them (bitonic network on 2048 entries).
+__global__ void __launch_bounds__(kSelThreads) srft_select_kernel(uint2 key, int64_t n, int lc,
+                                                                  int* __restrict__ freq) {
+  __shared__ unsigned long long buf[kSelN];
+  const int tid = threadIdx.x;
+  const int64_t ncand = n / 2 - 1;   // b = 1 .. n/2 - 1
+  for (int e = tid; e < kSelN; e += kSelThreads) buf[e] = ~0ull;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < ncand; c0 += kSelThreads) {
+    const int64_t b = 1 + c0 + tid;
+    unsigned long long v = ~0ull;
+    if (b <= ncand) v = ((unsigned long long)srft_word(key, 1u, (uint64_t)b) << 32) | (unsigned long long)b;
+    // the kept entries sit in buf[0 .. lc), sorted; the chunk goes to the upper half
+    buf[kSelThreads + tid] = v;
+    for (int e = lc + tid; e < kSelThreads; e += kSelThreads) buf[e] = ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= kSelN; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int e = tid; e < kSelN / 2; e += kSelThreads) {
+          const int lo = 2 * e - (e & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = ((lo & size) == 0);
+          const unsigned long long x = buf[lo], y = buf[hi];
+          if ((x > y) == up) { buf[lo] = y; buf[hi] = x; }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int e = tid; e < lc; e += kSelThreads) freq[e] = (int)(buf[e] & 0xffffffffu);
+}
+
+// Omega (n x cols_pad, ld) and optionally its transposed bf16 copy: column 2c / 2c + 1
+// = d_i cos / sin(-2 pi (i b_c mod n) / n) / sqrt(l_c); columns >= 2 l_c are zero.
+__global__ void srft_omega_kernel(uint2 key, int64_t n, int lc, int cols_pad,
+                                  const int* __restrict__ freq, float* __restrict__ out, int64_t ld,
+                                  __nv_bfloat16* __restrict__ out_t, int64_t ld_t) {
+  const float scale = rsqrtf((float)lc);
+  const int64_t total = n * cols_pad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n;   // consecutive threads take consecutive rows
+    const int j = (int)(e / n);
+    float val = 0.0f;
+    if (j < 2 * lc) {
+      const int64_t b = freq[j >> 1];
+      int64_t r = (int64_t)(((unsigned long long)i * (unsigned long long)b) % (unsigned long long)n);
+      if (2 * r > n) r -= n;   // same angle, reduced to [-pi, pi]
+      const float x = -2.0f * (float)r / (float)n;
+      float sv, cv;
+      sincospif(x, &sv, &cv);
+      const float d = (srft_word(key, 0u, (uint64_t)i) >> 31) ? -scale : scale;
+      val = d * ((j & 1) ? sv : cv);
+    }
+    if (out) out[i * ld + j] = val;
+    if (out_t) out_t[(int64_t)j * ld_t + i] = __float2bfloat16_rn(val);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_srft_select(uint64_t seed, int64_t n, int lc, int* freq, cudaStream_t st) {
+  if (n < 4 || (n & 1) || lc < 1 || lc > n / 2 - 1 || lc > kSelThreads) return cudaErrorInvalidValue;
+  srft_select_kernel<<<1, kSelThreads, 0, st>>>(seed_key(seed), n, lc, freq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_srft(uint64_t seed, int64_t n, int lc, int cols_pad, const int* freq,
+                             float* out, int64_t ld, __nv_bfloat16* out_t, int64_t ld_t,
+                             cudaStream_t st) {
+  if (n <= 0 || cols_pad < 2 * lc || n >= (int64_t)1 << 24) return cudaErrorInvalidValue;
+  const int64_t total = n * cols_pad;
+  const int64_t blocks = cdiv(total, 256);
+  const unsigned grid = (unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs);
+  srft_omega_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, lc, cols_pad, freq, out, ld, out_t, ld_t);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

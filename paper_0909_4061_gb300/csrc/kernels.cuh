@@ -56,6 +56,13 @@ cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64
 // Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
 // info (may be null): atomicMax of the number of sweeps taken.
 // variant: 0 = one CTA up to l = 160, else the cluster; 1 = one CTA; 2 = cluster.
+// SRFT test matrix (Section 4.6): the lc sampled frequencies (one CTA, at plan creation),
+// then Omega n x cols_pad (2 lc real columns [Re, Im] per frequency, zero padding).
+cudaError_t launch_srft_select(uint64_t seed, int64_t n, int lc, int* freq, cudaStream_t st);
+cudaError_t launch_draw_srft(uint64_t seed, int64_t n, int lc, int cols_pad, const int* freq,
+                             float* out, int64_t ld, __nv_bfloat16* out_t, int64_t ld_t,
+                             cudaStream_t st);
+
 // scratch: lp x lp floats of workspace (used by the cluster variant).
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp,
                               float* ut, float* s, float* w, float* scratch, uint32_t* status,

@@ -77,6 +77,18 @@ def test_plan_create_rejects_bad_options_on_host(pkg):
     with pytest.raises(pkg.RsvdError) as e:
         pkg.rsvd_plan_create(100, 80, 5, 5, 1, 0, o, 0)
     assert e.value.status == pkg.RSVD_ERR_INVALID_ARG
+    # SRFT: l real columns are l / 2 frequencies of an even-length DFT
+    for m, n, k, p in [(100, 80, 5, 4), (100, 81, 5, 5), (100, 8, 6, 2)]:
+        o = pkg.rsvd_options_default()
+        o.test_matrix = pkg.RSVD_SRFT
+        with pytest.raises(pkg.RsvdError) as e:
+            pkg.rsvd_plan_create(m, n, k, p, 1, 0, o, 0)
+        assert e.value.status == pkg.RSVD_ERR_INVALID_ARG, (m, n, k, p)
+    o = pkg.rsvd_options_default()
+    o.small_svd = 3
+    with pytest.raises(pkg.RsvdError) as e:
+        pkg.rsvd_plan_create(100, 80, 5, 5, 1, 0, o, 0)
+    assert e.value.status == pkg.RSVD_ERR_INVALID_ARG
 
 
 def test_null_pointer_arguments(pkg):

@@ -1,0 +1,80 @@
+"""GPU parity of the SRFT test matrix (Section 4.6, Algorithm 4.5) against the oracle.
+
+Omega from the library (rsvd_get_omega) is compared element by element with the
+oracle's explicit real SRFT built from the same Philox draws: signs and sampled
+frequencies are integer decisions, so a wrong one shows up as an O(1) error; the
+float32 cos/sin of exactly reduced angles agree to a few ulp (<= 2e-6 / sqrt(l_c)).
+The full randomized SVD with the SRFT is then held to the same tolerances as the
+Gaussian path, against the oracle run with that Omega.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import metrics, srft
+
+sys.path.insert(0, os.path.dirname(__file__))
+from test_gpu_parity import _check_svd, _dev, _np  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _srft_plan(pkg, m, n, k, p, q, seed, precision=0):
+    return pkg.Plan(m, n, k, p, q, seed, precision, test_matrix=pkg.RSVD_SRFT)
+
+
+@pytest.mark.parametrize("m,n,l,seed", [(16, 64, 8, 5), (40, 1000, 30, 2004), (200, 4096, 128, 77),
+                                        (256, 32768, 256, 2004), (300, 514, 256, 1)])
+def test_srft_omega_matches_oracle(rsvd_lib, m, n, l, seed):
+    with _srft_plan(rsvd_lib, m, n, l - 2, 2, 1, seed) as pl:
+        om = torch.zeros(n, l, device="cuda")
+        rsvd_lib.rsvd_get_omega(pl.handle, om)
+        torch.cuda.synchronize()
+    got = _np(om)
+    signs, freqs = srft.draw(seed, n, l // 2)
+    ref = srft.omega_real(signs, freqs)
+    assert np.max(np.abs(got - ref)) <= 2e-6 / np.sqrt(l // 2) + 1e-7
+    # structure: the columns are orthogonal with norm^2 n / (2 l_c) each (Omega^H Omega = (n/l_c) I
+    # for the complex matrix; real and imaginary parts split it evenly for 0 < b < n/2)
+    g = got.T @ got
+    assert np.allclose(g, np.eye(l) * n / l, atol=2e-4 * n / l)
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(700, 512, 20, 12, 1), (1000, 2048, 100, 28, 1), (517, 390, 8, 4, 2)])
+def test_srft_rsvd_fp32_matches_oracle(rsvd_lib, m, n, k, p, q):
+    import synth
+
+    a, *_ = synth.lowrank(m, n, synth.spectrum_power(min(m, n), 0.5), m + 3 * n)
+    a32 = a.astype(np.float32)
+    seed = 31
+    with _srft_plan(rsvd_lib, m, n, k, p, q, seed) as pl:
+        om = torch.zeros(n, k + p, device="cuda")
+        rsvd_lib.rsvd_get_omega(pl.handle, om)
+        U, S, V = pl.svd(_dev(a32))
+        torch.cuda.synchronize()
+    u, s, v = _np(U), _np(S), _np(V)
+    signs, freqs = srft.draw(seed, n, (k + p) // 2)
+    omega = srft.omega_real(signs, freqs)
+    assert np.max(np.abs(_np(om) - omega)) <= 2e-6
+    _check_svd(a32.astype(np.float64), u, s, v, k, p, q, omega)
+    assert metrics.orthonormality(u) <= 1e-5 and metrics.orthonormality(v) <= 1e-5
+
+
+def test_srft_sketch_is_the_fft_sketch(rsvd_lib):
+    """Y = A Omega through the library's pass equals the row-FFT form of Algorithm 4.5."""
+    rng = np.random.default_rng(3)
+    m, n, l = 300, 1024, 64
+    a32 = rng.standard_normal((m, n)).astype(np.float32)
+    with _srft_plan(rsvd_lib, m, n, l - 4, 4, 0, 11) as pl:
+        om = torch.zeros(n, l, device="cuda")
+        rsvd_lib.rsvd_get_omega(pl.handle, om)
+        Y = torch.zeros(m, l, device="cuda")
+        rsvd_lib.rsvd_sketch(pl.handle, _dev(a32), 0, om, Y)
+        torch.cuda.synchronize()
+    signs, freqs = srft.draw(11, n, l // 2)
+    ref = srft.sketch_fft(a32.astype(np.float64), signs, freqs)
+    scale = np.abs(a32).astype(np.float64) @ np.abs(srft.omega_real(signs, freqs))
+    assert np.all(np.abs(_np(Y) - ref) <= 1e-5 * scale + 1e-6)
