@@ -42,7 +42,9 @@ struct rsvd_plan_s {
   float* partial = nullptr;  // split-K partial results
   int64_t partial_elems = 0;
   float* gpart = nullptr;    // nblk x lp x lp
-  float* small = nullptr;    // 8 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch
+  float* small = nullptr;    // 16 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch, single pass
+  float* psi = nullptr;      // m x lp   second test matrix of the single-pass sketch
+  float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
   uint32_t* status = nullptr;
@@ -72,6 +74,8 @@ struct rsvd_plan_s {
   float* ut() { return small + 5 * (size_t)lp * lp; }
   float* w() { return small + 6 * (size_t)lp * lp; }
   float* sq() { return small + 7 * (size_t)lp * lp; }
+  // single pass (Section 5.5): X1, X2, C1 (R of Y), F/G/H/B scratch, U1, U2, W scratch
+  float* sp(int i) { return small + (size_t)(8 + i) * lp * lp; }
 };
 
 namespace {
@@ -111,7 +115,7 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev, P->srft_freq};
+                  P->v_dev, P->srft_freq, P->psi, P->sig2};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
@@ -299,6 +303,80 @@ rsvd_status_t check_plan(rsvd_plan_t P) {
   return RSVD_OK;
 }
 
+// Single-pass randomized SVD (Section 5.5): Y = A Omega and Yt = A^T Psi from the
+// two sketches alone, Y = Q R and Yt = Qt Rt (Cholesky QR), and the reduced matrix
+// B ~ Q^T A Qt as the minimum-residual solution of
+//     B X1 = C1,  B^T X2 = C2,   X1 = Qt^T Omega, C1 = Q^T Y = R, X2 = Q^T Psi, C2 = Qt^T Yt = Rt,
+// i.e. of the Sylvester normal equations (X2 X2^T) B + B (X1 X1^T) = C1 X1^T + X2 C2^T,
+// solved in the singular bases of X1 and X2: X_i = U_i S_i W_i^T gives
+// B = U2 [(U2^T F U1) ./ (s2_i^2 + s1_j^2)] U1^T, F = C1 X1^T + X2 C2^T.  Then B = Ub Sb Vb^T
+// (Jacobi), U = Q Ub_k, V = Qt Vb_k.  q is ignored; A is read by one pass of each kind.
+rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S, float* V,
+                                float* Qout, int64_t ldq) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  const int lp = P->lp, l = P->l;
+  const size_t l2 = (size_t)lp * lp;
+  if (tc)
+    TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  int s;
+  int64_t stride;
+  // Y = A Omega, Y = Q R (R accumulated into racc, then kept as C1)
+  TRYS(step_draw(P, tc));
+  // the cross products below must see the test matrices the bf16 passes multiplied with
+  if (tc) TRY(launch_round_bf16(P->omega, P->n, lp, lp, P->st));
+  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, P->racc()));
+  TRY(cudaMemcpyAsync(P->sp(2), P->racc(), sizeof(float) * l2, cudaMemcpyDeviceToDevice, P->st));
+  if (Qout) TRY(launch_gather(P->qbuf, 1, 0, lp, Qout, ldq, P->m, l, l, P->st));
+  // Yt = A^T Psi (Psi: Gaussian, stream 1), Yt = Qt Rt
+  {
+    Step sp(P, RSVD_STEP_DRAW);
+    sp.launched();
+    TRY(launch_draw_gaussian(P->seed, 1u, P->m, l, lp, P->psi, lp, tc ? P->xbf : nullptr,
+                             tc_ld(P->m), P->st));
+    if (tc) TRY(launch_round_bf16(P->psi, P->m, lp, lp, P->st));
+  }
+  TRYS(step_pass(P, A, 1, P->psi, false, &s, &stride));
+  TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched(14);
+    // X1 = Qt^T Omega (K = n), X2 = Q^T Psi (K = m): split over row blocks, summed by gather
+    const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
+    const int s1 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->n, 512)));
+    TRY(launch_gemm_f32(1, lp, lp, P->n, P->qtbuf, lp, P->omega, lp, P->gpart, lp, s1, l2, P->st));
+    TRY(launch_gather(P->gpart, s1, l2, lp, P->sp(0), lp, lp, lp, lp, P->st));
+    const int s2 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->m, 512)));
+    TRY(launch_gemm_f32(1, lp, lp, P->m, P->qbuf, lp, P->psi, lp, P->gpart, lp, s2, l2, P->st));
+    TRY(launch_gather(P->gpart, s2, l2, lp, P->sp(1), lp, lp, lp, lp, P->st));
+    // singular bases of X1 (U1 = sp(5), s1) and X2 (U2 = sp(6), s2)
+    TRY(launch_jacobi_svd(P->sp(0), lp, 0, l, lp, P->sp(5), P->sig2, P->sp(7), P->lbuf(),
+                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_jacobi_svd(P->sp(1), lp, 0, l, lp, P->sp(6), P->sig2 + lp, P->sp(7), P->lbuf(),
+                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    // F = C1 X1^T + X2 C2^T (C1 = sp(2), C2 = racc); G = U2^T F U1; H = G ./ (s2^2 + s1^2)
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(2), lp, 0, P->sp(0), lp, 1, 0.f, P->sp(3), lp, P->st));
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(1), lp, 0, P->racc(), lp, 1, 1.f, P->sp(3), lp, P->st));
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(6), lp, 1, P->sp(3), lp, 0, 0.f, P->sp(4), lp, P->st));
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(4), lp, 0, P->sp(5), lp, 0, 0.f, P->sp(3), lp, P->st));
+    TRY(launch_sylvester_scale(P->sp(3), l, lp, P->sig2 + lp, P->sig2, P->sp(4), P->st));
+    // B = U2 H U1^T into sq (zero padded)
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(6), lp, 0, P->sp(4), lp, 0, 0.f, P->sp(3), lp, P->st));
+    TRY(cudaMemsetAsync(P->sq(), 0, sizeof(float) * l2, P->st));
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(3), lp, 0, P->sp(5), lp, 1, 0.f, P->sq(), lp, P->st));
+    // B = Ub Sb Vb^T
+    TRY(launch_jacobi_svd(P->sq(), lp, 0, l, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd));
+  }
+  if (!U) return RSVD_OK;
+  Step sp(P, RSVD_STEP_LIFT);
+  sp.launched(2);
+  TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->ut(), lp, U, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->n, P->k, lp, P->qtbuf, lp, P->w(), lp, V, P->k, 1, 0, P->st));
+  TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -352,7 +430,6 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.test_matrix == RSVD_SRFT &&
       ((l & 1) || (n & 1) || l / 2 > n / 2 - 1 || n >= ((int64_t)1 << 24)))
     return RSVD_ERR_INVALID_ARG;
-  if (o.single_pass) return RSVD_ERR_UNSUPPORTED;
   if (o.small_svd < 0 || o.small_svd > 2) return RSVD_ERR_INVALID_ARG;
   if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
@@ -396,7 +473,9 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (s = dalloc(P, &P->tmp2, (size_t)P->maxmn * lp)) != RSVD_OK ||
       (s = dalloc(P, &P->partial, (size_t)part)) != RSVD_OK ||
       (s = dalloc(P, &P->gpart, (size_t)nblk * lp * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->small, (size_t)8 * lp * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->small, (size_t)16 * lp * lp)) != RSVD_OK ||
+      (o.single_pass && (s = dalloc(P, &P->psi, (size_t)m * lp)) != RSVD_OK) ||
+      (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lp)) != RSVD_OK) ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
       (o.test_matrix == RSVD_SRFT && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
@@ -423,7 +502,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_CUDA;
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
-      cudaMemsetAsync(P->small, 0, sizeof(float) * 8 * lp * lp, P->st) != cudaSuccess) {
+      cudaMemsetAsync(P->small, 0, sizeof(float) * 16 * lp * lp, P->st) != cudaSuccess) {
     free_plan(P);
     return RSVD_ERR_CUDA;
   }
@@ -447,6 +526,7 @@ rsvd_status_t rsvd_workspace_bytes(rsvd_plan_t P, size_t* bytes) {
 rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t ldq) {
   TRYS(check_plan(P));
   if (!A || !Q || ldq < P->l) return RSVD_ERR_INVALID_ARG;
+  if (P->opt.single_pass) return stage_single_pass(P, A, nullptr, nullptr, nullptr, Q, ldq);
   TRYS(stage_a(P, A));
   TRY(launch_gather(P->qbuf, 1, 0, P->lp, Q, ldq, P->m, P->l, P->l, P->st));
   return RSVD_OK;
@@ -458,6 +538,7 @@ rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t 
 // on the legacy default stream (which cannot be captured), if capture fails, or
 // when the environment sets RSVD_NO_GRAPH=1.
 rsvd_status_t run_svd_direct(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  if (P->opt.single_pass) return stage_single_pass(P, A, U, S, V, nullptr, 0);
   TRYS(stage_a(P, A));
   TRYS(stage_b(P, A, U, S, V));
   return RSVD_OK;

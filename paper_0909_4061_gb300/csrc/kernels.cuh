@@ -56,6 +56,15 @@ cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64
 // Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
 // info (may be null): atomicMax of the number of sweeps taken.
 // variant: 0 = one CTA up to l = 160, else the cluster; 1 = one CTA; 2 = cluster.
+// C = alpha op(A) op(B) + beta C for small matrices (op: 0 identity, 1 transpose; M, N, K <= a
+// few hundred), and H = G ./ (s2_i^2 + s1_j^2) on the leading l x l (zero elsewhere).
+cudaError_t launch_small_gemm(int M, int N, int K, float alpha, const float* A, int lda, int ta,
+                              const float* B, int ldb, int tb, float beta, float* C, int ldc,
+                              cudaStream_t st);
+cudaError_t launch_round_bf16(float* x, int64_t rows, int cols, int64_t ld, cudaStream_t st);
+cudaError_t launch_sylvester_scale(const float* G, int l, int lp, const float* s2, const float* s1,
+                                   float* H, cudaStream_t st);
+
 // SRFT test matrix (Section 4.6): the lc sampled frequencies (one CTA, at plan creation),
 // then Omega n x cols_pad (2 lc real columns [Re, Im] per frequency, zero padding).
 cudaError_t launch_srft_select(uint64_t seed, int64_t n, int lc, int* freq, cudaStream_t st);

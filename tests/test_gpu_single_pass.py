@@ -1,0 +1,115 @@
+"""GPU parity of the single-pass randomized SVD (Section 5.5) against the oracle.
+
+Both sides take the same Omega (Gaussian, stream 0) and Psi (Gaussian, stream 1):
+the library's own draws, read back through the C ABI, feed the oracle.  B is the
+minimum-residual solution of B X1 = C1, B^T X2 = C2 through the Sylvester normal
+equations; its float32 error grows with the conditioning of that system.  A
+first-order bound: a relative perturbation u of the inputs moves B by about
+u (kappa(X1)^2 + kappa(X2)^2) ||B|| (the normal equations square the conditioning
+of each side), so singular values are compared within
+    tol = 2 u32 (kappa(X1)^2 + kappa(X2)^2) sigma_1,     u32 = 2^-24,
+and the singular subspaces through the Wedin gap bound at that tolerance.  (Measured
+errors sit 10-30x below it: 0.7e-5 to 4.6e-5 sigma_1 at kappa^2 sums near 1e4.)
+Exact-rank inputs (rank r < k) must come back exactly up to the same tolerance, with
+the trailing singular values at that level too.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import metrics, single_pass
+
+sys.path.insert(0, os.path.dirname(__file__))
+from test_gpu_parity import _dev, _np  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+def _draws(pkg, pl, m, n, l, seed, bf16):
+    om = torch.zeros(n, l, device="cuda")
+    pkg.rsvd_get_omega(pl.handle, om)
+    psi = torch.zeros(m, l, device="cuda")
+    pkg.rsvd_draw_gaussian(seed, 1, m, l, psi, l)
+    torch.cuda.synchronize()
+    if bf16:
+        om, psi = om.to(torch.bfloat16).float(), psi.to(torch.bfloat16).float()
+    return _np(om), _np(psi)
+
+
+def _run(pkg, a, k, p, seed, precision):
+    m, n = a.shape
+    l = k + p
+    bf16 = precision == pkg.RSVD_BF16_TC
+    with pkg.Plan(m, n, k, p, 0, seed, precision, single_pass=1) as pl:
+        om, psi = _draws(pkg, pl, m, n, l, seed, bf16)
+        A = _dev(a, torch.bfloat16 if bf16 else torch.float32)
+        U, S, V = pl.svd(A)
+        torch.cuda.synchronize()
+        bits, _ = pkg.rsvd_diagnostics(pl.handle)
+    return _np(U), _np(S), _np(V), om, psi, bits
+
+
+def _oracle(a64, k, om, psi):
+    u, s, v, (qm, qt, b) = single_pass.rsvd_single_pass(a64, k, om, psi)
+    y, yt = single_pass.two_sided_sketch(a64, om, psi)
+    x1, _, x2, _ = single_pass.reduced_system(qm, qt, om, psi, y, yt)
+    kap = np.linalg.cond(x1) ** 2 + np.linalg.cond(x2) ** 2
+    sb = np.linalg.svd(b, compute_uv=False)
+    return u, s, v, sb, kap
+
+
+def _compare(u, s, v, ur, sr, vr, sb_full, k, tol):
+    assert np.max(np.abs(s - sr)) <= tol, (np.max(np.abs(s - sr)), tol)
+    eps = tol / sr[0]
+    bound = metrics.gap_bound(sr, eps, s_next=sb_full[k] if k < len(sb_full) else None)
+    d = np.sign(np.sum(u * ur, axis=0))
+    d[d == 0] = 1
+    assert np.all(np.linalg.norm(u * d - ur, axis=0) <= bound + 1e-5)
+    assert np.all(np.linalg.norm(v * d - vr, axis=0) <= bound + 1e-5)
+    assert metrics.orthonormality(u) <= 1e-5 and metrics.orthonormality(v) <= 1e-5
+
+
+@pytest.mark.parametrize("m,n,k,p", [(4096, 512, 16, 8), (2000, 700, 30, 10), (517, 1031, 12, 6)])
+def test_single_pass_fp32_matches_oracle(rsvd_lib, m, n, k, p):
+    sig = synth.spectrum_exp(min(m, n), 20.0)
+    a, *_ = synth.lowrank(m, n, sig, 7 * m + n)
+    a32 = a.astype(np.float32)
+    u, s, v, om, psi, bits = _run(rsvd_lib, a32, k, p, 41, rsvd_lib.RSVD_PLAIN_FP32)
+    assert not bits & 3
+    ur, sr, vr, sb, kap = _oracle(a32.astype(np.float64), k, om, psi)
+    tol = 2 * U32 * kap * sr[0]
+    print("single pass fp32: max dsigma/sigma1", np.max(np.abs(s - sr)) / sr[0], "tol/sigma1", tol / sr[0])
+    _compare(u, s, v, ur, sr, vr, sb, k, tol)
+
+
+def test_single_pass_bf16_tc_matches_oracle(rsvd_lib):
+    m, n, k, p = 4096, 512, 16, 8
+    sig = synth.spectrum_exp(n, 20.0)
+    a, *_ = synth.lowrank(m, n, sig, 99)
+    ab = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).float().numpy()
+    u, s, v, om, psi, bits = _run(rsvd_lib, ab, k, p, 43, rsvd_lib.RSVD_BF16_TC)
+    ur, sr, vr, sb, kap = _oracle(ab.astype(np.float64), k, om, psi)
+    tol = 2 * U32 * kap * sr[0]
+    print("single pass bf16: max dsigma/sigma1", np.max(np.abs(s - sr)) / sr[0], "tol/sigma1", tol / sr[0])
+    _compare(u, s, v, ur, sr, vr, sb, k, tol)
+
+
+def test_single_pass_exact_rank(rsvd_lib):
+    """rank r < k: the two sketches capture A exactly, so B reproduces its spectrum."""
+    m, n, r, k, p = 3000, 400, 6, 10, 6
+    sig = np.zeros(n)
+    sig[:r] = np.linspace(1.0, 0.3, r)
+    a, *_ = synth.lowrank(m, n, sig, 5)
+    a32 = a.astype(np.float32)
+    u, s, v, om, psi, bits = _run(rsvd_lib, a32, k, p, 3, 0)
+    st = np.linalg.svd(a32.astype(np.float64), compute_uv=False)
+    *_, kap = _oracle(a32.astype(np.float64), k, om, psi)
+    tol = 2 * U32 * kap * st[0]
+    print("single pass exact rank: max dsigma/sigma1", np.max(np.abs(s[:r] - st[:r])) / st[0], "tol/sigma1", tol / st[0])
+    assert np.max(np.abs(s[:r] - st[:r])) <= tol
+    assert np.max(np.abs(s[r:])) <= tol
