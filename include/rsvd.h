@@ -257,6 +257,38 @@ RSVD_API rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int64_
                                                 int64_t ldxt, int32_t l, float* Y,
                                                 uint32_t* status, void* stream);
 
+/* ---- Batched: many small matrices, one plan --------------------------------
+ * The randomized SVD of Algorithm 4.4 + Algorithm 5.1 (with the Gaussian test
+ * matrix of Algorithm 4.1) applied to `batch` independent matrices A_b, every step
+ * one launch over the whole batch: grouped tensor-core passes (bfloat16 A_b,
+ * float32 accumulation), one CTA per matrix for the Cholesky-QR rounds and for the
+ * l x l one-sided Jacobi SVD.  Requires l = k + p <= 32, m_b >= l, n_b >= l,
+ * precision RSVD_BF16_TC with dtype_A RSVD_BF16, the Gaussian test matrix; anything
+ * else returns RSVD_ERR_UNSUPPORTED (or RSVD_ERR_INVALID_ARG for bad sizes).
+ * Omega_b is drawn from seed + b (Philox4x32-10, stream 0, as rsvd_draw_gaussian).
+ * m, n (and lda, or NULL for lda_b = n_b rounded up to 8; each lda_b a multiple of 8)
+ * are host arrays of `batch` entries, copied at creation.  The plan is not thread-safe. */
+typedef struct rsvd_batched_plan_s* rsvd_batched_plan_t;
+
+RSVD_API rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
+                                                const int64_t* m, const int64_t* n,
+                                                const int64_t* lda, int32_t k, int32_t p,
+                                                int32_t q, uint64_t seed,
+                                                const rsvd_options_t* opt, void* stream);
+RSVD_API rsvd_status_t rsvd_batched_plan_destroy(rsvd_batched_plan_t plan);
+
+/* A: host array of `batch` device pointers (bfloat16, m_b x n_b row-major, lda_b,
+ * 16-byte-aligned).  Outputs, device float32: U is sum(m_b) x k with matrix b's rows
+ * from row sum_{c<b} m_c; S is batch x k (descending per matrix); V is sum(n_b) x k
+ * likewise.  Asynchronous on the plan's stream; the plan keeps what the backward
+ * pass needs (the bases, R factors and small SVDs of this call). */
+RSVD_API rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t plan, const void* const* A, float* U,
+                                        float* S, float* V);
+
+/* Waits for the plan's stream and returns the device status as rsvd_sync does;
+ * *sweeps (may be NULL) receives the largest Jacobi sweep count since the last call. */
+RSVD_API rsvd_status_t rsvd_batched_sync(rsvd_batched_plan_t plan, uint32_t* sweeps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@ EXPORTS = (
     "rsvd_set_omega", "rsvd_sync", "rsvd_status_string", "rsvd_draw_gaussian", "rsvd_sketch",
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
     "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc", "rsvd_convert_a",
+    "rsvd_batched_plan_create", "rsvd_batched_plan_destroy", "rsvd_batched_svd", "rsvd_batched_sync",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -98,6 +99,11 @@ _SIGS = {
                                   _c.c_int32, _P]),
     "rsvd_sketch_bf16_noalloc": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int32, _P,
                                             _c.c_int64, _c.c_int32, _P, _P, _P]),
+    "rsvd_batched_plan_create": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _c.c_int32, _c.c_int32,
+                                            _c.c_int32, _c.c_uint64, _P, _P]),
+    "rsvd_batched_plan_destroy": (_c.c_int, [_P]),
+    "rsvd_batched_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "rsvd_batched_sync": (_c.c_int, [_P, _P]),
 }
 
 
@@ -352,3 +358,67 @@ def svd(A, k, p=10, q=1, seed=0, precision=None, orth_rounds=3):
     m, n = A.shape
     with Plan(m, n, k, p, q, seed, precision, orth_rounds, lda=A.stride(0)) as pl:
         return pl.svd(A)
+
+
+class BatchedPlan:
+    """Randomized SVD of many small bfloat16 matrices (l = k + p <= 32) with one plan.
+
+    shapes: list of (m_b, n_b); lda_b defaults to n_b rounded up to 8.  Outputs are
+    concatenated: U (sum m_b, k), S (batch, k), V (sum n_b, k)."""
+
+    def __init__(self, shapes, k, p=8, q=1, seed=0, lda=None, stream=None, orth_rounds=3):
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        self.batch = len(self.shapes)
+        self.k, self.p, self.q = int(k), int(p), int(q)
+        ms = (ctypes.c_int64 * self.batch)(*[a for a, _ in self.shapes])
+        ns = (ctypes.c_int64 * self.batch)(*[b for _, b in self.shapes])
+        ld = None if lda is None else (ctypes.c_int64 * self.batch)(*[int(x) for x in lda])
+        o = rsvd_options_default()
+        o.precision = RSVD_BF16_TC
+        o.dtype_A = RSVD_BF16
+        o.orth_rounds = orth_rounds
+        h = ctypes.c_void_p()
+        _check(lib().rsvd_batched_plan_create(ctypes.byref(h), self.batch, ms, ns, ld, self.k, self.p,
+                                              self.q, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
+                                              _stream(stream)), "rsvd_batched_plan_create")
+        self.handle = h.value
+        self.row_m = [0]
+        self.row_n = [0]
+        for a, b in self.shapes:
+            self.row_m.append(self.row_m[-1] + a)
+            self.row_n.append(self.row_n[-1] + b)
+
+    def close(self):
+        if self.handle is not None:
+            lib().rsvd_batched_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def svd(self, mats, U=None, S=None, V=None):
+        import torch
+
+        ptrs = (ctypes.c_void_p * self.batch)(*[int(a.data_ptr()) for a in mats])
+        dev = mats[0].device
+        if U is None:
+            U = torch.empty(self.row_m[-1], self.k, device=dev)
+            S = torch.empty(self.batch, self.k, device=dev)
+            V = torch.empty(self.row_n[-1], self.k, device=dev)
+        _check(lib().rsvd_batched_svd(self.handle, ptrs, _ptr(U), _ptr(S), _ptr(V)), "rsvd_batched_svd")
+        self._keep = ptrs
+        return U, S, V
+
+    def sync(self):
+        sw = ctypes.c_uint32(0)
+        _check(lib().rsvd_batched_sync(self.handle, ctypes.byref(sw)), "rsvd_batched_sync")
+        return int(sw.value)

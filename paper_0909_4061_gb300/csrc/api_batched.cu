@@ -1,0 +1,313 @@
+// Batched C ABI: one plan for many small matrices (l = k + p <= 32), each step of the
+// randomized SVD (Algorithm 4.4 + Algorithm 5.1) one launch over the whole batch, and
+// the gradient of the batched reconstruction loss through that map (test matrices fixed).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "kernels_batched.cuh"
+#include "sketch_tc.cuh"
+
+struct rsvd_batched_plan_s {
+  int nb = 0, k = 0, p = 0, q = 0, l = 0;
+  uint64_t seed = 0;
+  rsvd_options_t opt{};
+  cudaStream_t st = nullptr;
+  int num_sms = 0;
+  std::vector<int64_t> m, n, lda;
+  int64_t sum_m = 0, sum_n = 0, xm_total = 0, xn_total = 0;
+  // device index arrays
+  int64_t* d_roff_m = nullptr;   // nb + 1
+  int64_t* d_roff_n = nullptr;   // nb + 1
+  int64_t* d_xoff_m = nullptr;   // nb
+  int64_t* d_xoff_n = nullptr;   // nb
+  int64_t* d_m = nullptr;        // nb
+  int64_t* d_n = nullptr;        // nb
+  int2* d_units0 = nullptr;      // (b, row tile of m_b)
+  int2* d_units1 = nullptr;      // (b, row tile of n_b)
+  int nunits0 = 0, nunits1 = 0;
+  // tensor maps of A_b (mode 0 boxes, then mode 1 boxes), device copy + the bound pointers
+  unsigned char* d_maps = nullptr;
+  std::vector<unsigned char> h_maps;
+  std::vector<const void*> a_bound;
+  alignas(64) unsigned char map_x_m[128];   // operand with K = sum of padded m_b (32 rows)
+  alignas(64) unsigned char map_x_n[128];   // operand with K = sum of padded n_b (32 rows)
+  alignas(64) unsigned char map_x_m2[128];  // the same with the lo half (64 rows)
+  alignas(64) unsigned char map_x_n2[128];
+  // workspace
+  __nv_bfloat16* xbf = nullptr;   // 2 LP x max(xm_total, xn_total): hi rows, then lo rows
+  float* omega = nullptr;         // sum_n x LP
+  float* ym = nullptr;            // sum_m x LP   pass outputs (m side)
+  float* yn = nullptr;            // sum_n x LP   pass outputs (n side)
+  std::vector<float*> qm;         // q + 1 bases on the m side (Q_0 .. Q_q)
+  std::vector<float*> qn;         // q bases on the n side (Qt_1 .. Qt_q)
+  std::vector<float*> rm, rn;     // their R factors, nb x LP x LP each
+  float* qb = nullptr;            // sum_n x LP   Q_B
+  float* rb = nullptr;            // nb x LP x LP R_B
+  float* ub = nullptr;            // nb x LP x LP singular vectors of R_B^T (left)
+  float* wb = nullptr;            // nb x LP x LP (right)
+  float* sig = nullptr;           // nb x LP
+  uint32_t* status = nullptr;     // [0] status bits, [1] Jacobi sweeps
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace rsvd {
+namespace {
+
+constexpr int LP = kBatchedLP;
+
+#define BTRY(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return RSVD_ERR_CUDA;  \
+  } while (0)
+#define BTRYS(expr)                 \
+  do {                              \
+    rsvd_status_t _s = (expr);      \
+    if (_s != RSVD_OK) return _s;   \
+  } while (0)
+
+template <typename T>
+rsvd_status_t balloc(rsvd_batched_plan_t P, T** ptr, size_t elems) {
+  *ptr = nullptr;
+  const size_t bytes = std::max<size_t>(elems, 1) * sizeof(T);
+  if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RSVD_ERR_ALLOC;
+  }
+  P->allocs.push_back(*ptr);
+  P->ws_bytes += bytes;
+  return RSVD_OK;
+}
+
+void bfree(rsvd_batched_plan_t P) {
+  if (!P) return;
+  for (void* a : P->allocs) cudaFree(a);
+  delete P;
+}
+
+template <typename T>
+rsvd_status_t upload(rsvd_batched_plan_t P, T** dst, const std::vector<T>& src) {
+  BTRYS(balloc(P, dst, src.size()));
+  BTRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return RSVD_OK;
+}
+
+// units of a pass, heaviest first (largest K), so that the round-robin deal to CTAs balances
+std::vector<int2> make_units(const std::vector<int64_t>& rows, const std::vector<int64_t>& kext) {
+  std::vector<int> order(rows.size());
+  for (size_t b = 0; b < rows.size(); ++b) order[b] = (int)b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return kext[a] > kext[c]; });
+  std::vector<int2> u;
+  for (int b : order)
+    for (int64_t t = 0; t < cdiv(rows[b], 128); ++t) u.push_back(make_int2(b, (int)t));
+  return u;
+}
+
+rsvd_status_t bind_maps(rsvd_batched_plan_t P, const void* const* A) {
+  bool same = true;
+  for (int b = 0; b < P->nb && same; ++b) same = (P->a_bound[b] == A[b]);
+  if (same) return RSVD_OK;
+  for (int b = 0; b < P->nb; ++b) {
+    if (!A[b] || (reinterpret_cast<uintptr_t>(A[b]) & 15)) return RSVD_ERR_INVALID_ARG;
+    unsigned char* m0 = P->h_maps.data() + (size_t)b * 128;
+    unsigned char* m1 = P->h_maps.data() + (size_t)(P->nb + b) * 128;
+    if (tc_encode_2d(m0, A[b], P->n[b], P->m[b], P->lda[b], 64, 128) ||
+        tc_encode_2d(m1, A[b], P->n[b], P->m[b], P->lda[b], 64, 64))
+      return RSVD_ERR_CUDA;
+  }
+  BTRY(cudaMemcpyAsync(P->d_maps, P->h_maps.data(), P->h_maps.size(), cudaMemcpyHostToDevice, P->st));
+  for (int b = 0; b < P->nb; ++b) P->a_bound[b] = A[b];
+  return RSVD_OK;
+}
+
+// Y = A X (mode 0: X on the n side, Y on the m side) or Y = A^T X (mode 1); fold: the
+// operand holds hi and lo halves
+rsvd_status_t bpass(rsvd_batched_plan_t P, int mode, int fold, float* y) {
+  const void* maps = P->d_maps + (mode ? (size_t)P->nb * 128 : 0);
+  if (mode == 0)
+    BTRY(launch_batched_tc(0, fold, maps, fold ? P->map_x_n2 : P->map_x_n, P->d_units0, P->nunits0,
+                           P->d_n, P->d_m, P->d_xoff_n, P->d_roff_m, y, P->num_sms, P->status, P->st));
+  else
+    BTRY(launch_batched_tc(1, fold, maps, fold ? P->map_x_m2 : P->map_x_m, P->d_units1, P->nunits1,
+                           P->d_m, P->d_n, P->d_xoff_m, P->d_roff_n, y, P->num_sms, P->status, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t to_operand(rsvd_batched_plan_t P, const float* q, bool m_side, int split) {
+  BTRY(launch_batched_to_bf16t(q, m_side ? P->d_roff_m : P->d_roff_n, P->nb, m_side ? P->sum_m : P->sum_n,
+                               P->xbf, std::max(P->xm_total, P->xn_total),
+                               m_side ? P->d_xoff_m : P->d_xoff_n, split, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
+  BTRYS(bind_maps(P, A));
+  const int64_t ldx = std::max(P->xm_total, P->xn_total);
+  const int rounds = P->opt.orth_rounds;
+  BTRY(launch_batched_draw(P->seed, P->d_roff_n, P->nb, P->sum_n, P->l, P->omega, P->xbf, ldx,
+                           P->d_xoff_n, P->st));
+  BTRYS(bpass(P, 0, 0, P->ym));                                                  // Y_0 = A Omega
+  BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, rounds, P->rm[0], P->status, P->st));
+  for (int j = 1; j <= P->q; ++j) {
+    BTRYS(to_operand(P, P->qm[j - 1], true, 0));
+    BTRYS(bpass(P, 1, 0, P->yn));                                                // A^T Q_{j-1}
+    BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds, P->rn[j - 1],
+                               P->status, P->st));
+    BTRYS(to_operand(P, P->qn[j - 1], false, 0));
+    BTRYS(bpass(P, 0, 0, P->ym));                                                // A Qt_j
+    BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, rounds, P->rm[j], P->status,
+                               P->st));
+  }
+  float* Q = P->qm[P->q];
+  BTRYS(to_operand(P, Q, true, 1));
+  BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
+  BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->status, P->st));
+  BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
+  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->sum_m, P->ub, P->k, U, P->k, P->st));
+  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, P->k, V, P->k, P->st));
+  if (S)
+    BTRY(cudaMemcpy2DAsync(S, sizeof(float) * P->k, P->sig, sizeof(float) * LP, sizeof(float) * P->k,
+                           P->nb, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+using namespace rsvd;
+
+extern "C" {
+
+rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch, const int64_t* m,
+                                       const int64_t* n, const int64_t* lda, int32_t k, int32_t p,
+                                       int32_t q, uint64_t seed, const rsvd_options_t* opt,
+                                       void* stream) {
+  if (!plan) return RSVD_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (batch < 1 || !m || !n || k < 1 || p < 0 || q < 0 || k + p > kBatchedLP) return RSVD_ERR_INVALID_ARG;
+  rsvd_options_t o;
+  if (opt) o = *opt; else rsvd_options_default(&o);
+  if (o.orth_rounds != 2 && o.orth_rounds != 3) return RSVD_ERR_INVALID_ARG;
+  if (o.precision != RSVD_BF16_TC || o.dtype_A != RSVD_BF16 || o.test_matrix != RSVD_GAUSSIAN ||
+      o.single_pass)
+    return RSVD_ERR_UNSUPPORTED;   // the batched path is the bf16 tensor-core Gaussian form
+  const int l = k + p;
+  for (int b = 0; b < batch; ++b) {
+    const int64_t ld = lda ? lda[b] : round_up(n[b], 8);
+    if (m[b] < l || n[b] < l || ld < n[b] || (ld % 8) != 0 || m[b] >= (1ll << 31) ||
+        n[b] >= (1ll << 31))
+      return RSVD_ERR_INVALID_ARG;
+  }
+  rsvd_batched_plan_t P = new (std::nothrow) rsvd_batched_plan_s();
+  if (!P) return RSVD_ERR_ALLOC;
+  P->nb = batch; P->k = k; P->p = p; P->q = q; P->l = l; P->seed = seed; P->opt = o;
+  P->st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      prepare_batched() != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return RSVD_ERR_CUDA;
+  }
+  P->m.assign(m, m + batch);
+  P->n.assign(n, n + batch);
+  P->lda.resize(batch);
+  std::vector<int64_t> roff_m(batch + 1, 0), roff_n(batch + 1, 0), xoff_m(batch), xoff_n(batch);
+  for (int b = 0; b < batch; ++b) {
+    P->lda[b] = lda ? lda[b] : round_up(n[b], 8);
+    roff_m[b + 1] = roff_m[b] + m[b];
+    roff_n[b + 1] = roff_n[b] + n[b];
+    xoff_m[b] = P->xm_total;
+    xoff_n[b] = P->xn_total;
+    P->xm_total += round_up(m[b], 8);
+    P->xn_total += round_up(n[b], 8);
+  }
+  P->sum_m = roff_m[batch];
+  P->sum_n = roff_n[batch];
+  const std::vector<int2> u0 = make_units(P->m, P->n), u1 = make_units(P->n, P->m);
+  P->nunits0 = (int)u0.size();
+  P->nunits1 = (int)u1.size();
+  P->h_maps.assign((size_t)2 * batch * 128, 0);
+  P->a_bound.assign(batch, nullptr);
+  const int64_t ldx = std::max(P->xm_total, P->xn_total);
+  rsvd_status_t s;
+  if ((s = upload(P, &P->d_roff_m, roff_m)) != RSVD_OK || (s = upload(P, &P->d_roff_n, roff_n)) != RSVD_OK ||
+      (s = upload(P, &P->d_xoff_m, xoff_m)) != RSVD_OK || (s = upload(P, &P->d_xoff_n, xoff_n)) != RSVD_OK ||
+      (s = upload(P, &P->d_m, P->m)) != RSVD_OK || (s = upload(P, &P->d_n, P->n)) != RSVD_OK ||
+      (s = upload(P, &P->d_units0, u0)) != RSVD_OK || (s = upload(P, &P->d_units1, u1)) != RSVD_OK ||
+      (s = balloc(P, &P->d_maps, P->h_maps.size())) != RSVD_OK ||
+      (s = balloc(P, &P->xbf, (size_t)2 * LP * ldx)) != RSVD_OK ||
+      (s = balloc(P, &P->omega, (size_t)P->sum_n * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->ym, (size_t)P->sum_m * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->yn, (size_t)P->sum_n * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->qb, (size_t)P->sum_n * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->rb, (size_t)batch * LP * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->ub, (size_t)batch * LP * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->wb, (size_t)batch * LP * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->sig, (size_t)batch * LP)) != RSVD_OK ||
+      (s = balloc(P, &P->status, 4)) != RSVD_OK) {
+    bfree(P);
+    return s;
+  }
+  P->qm.assign(q + 1, nullptr);
+  P->rm.assign(q + 1, nullptr);
+  P->qn.assign(q, nullptr);
+  P->rn.assign(q, nullptr);
+  for (int j = 0; j <= q; ++j)
+    if ((s = balloc(P, &P->qm[j], (size_t)P->sum_m * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->rm[j], (size_t)batch * LP * LP)) != RSVD_OK) {
+      bfree(P);
+      return s;
+    }
+  for (int j = 0; j < q; ++j)
+    if ((s = balloc(P, &P->qn[j], (size_t)P->sum_n * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->rn[j], (size_t)batch * LP * LP)) != RSVD_OK) {
+      bfree(P);
+      return s;
+    }
+  if (tc_encode_2d(P->map_x_m, P->xbf, P->xm_total, LP, ldx, 64, LP) ||
+      tc_encode_2d(P->map_x_n, P->xbf, P->xn_total, LP, ldx, 64, LP) ||
+      tc_encode_2d(P->map_x_m2, P->xbf, P->xm_total, 2 * LP, ldx, 64, 2 * LP) ||
+      tc_encode_2d(P->map_x_n2, P->xbf, P->xn_total, 2 * LP, ldx, 64, 2 * LP) ||
+      cudaMemsetAsync(P->xbf, 0, sizeof(__nv_bfloat16) * 2 * LP * ldx, P->st) != cudaSuccess ||
+      cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess) {
+    cudaGetLastError();
+    bfree(P);
+    return RSVD_ERR_CUDA;
+  }
+  *plan = P;
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_batched_plan_destroy(rsvd_batched_plan_t P) {
+  if (!P) return RSVD_OK;
+  cudaStreamSynchronize(P->st);
+  bfree(P);
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
+  if (!P || !A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
+  return bforward(P, A, U, S, V);
+}
+
+rsvd_status_t rsvd_batched_sync(rsvd_batched_plan_t P, uint32_t* sweeps) {
+  if (!P) return RSVD_ERR_INVALID_ARG;
+  uint32_t w[2] = {0, 0};
+  BTRY(cudaMemcpyAsync(w, P->status, sizeof(w), cudaMemcpyDeviceToHost, P->st));
+  BTRY(cudaStreamSynchronize(P->st));
+  if (sweeps) *sweeps = w[1];
+  if (w[0] || w[1]) BTRY(cudaMemsetAsync(P->status, 0, 2 * sizeof(uint32_t), P->st));
+  if (w[0] & ST_NONFINITE) return RSVD_ERR_NONFINITE;
+  if (w[0] & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
+  if (w[0] & ST_NUMERICAL) return RSVD_ERR_NUMERICAL;
+  return RSVD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,613 @@
+// Batched randomized SVD of many small matrices (l <= 32): every step of
+// Algorithm 4.4 + Algorithm 5.1 as one launch over the whole batch.
+//
+// Layout: the matrices' row blocks are concatenated (matrix b's m_b rows start at
+// row roff[b] of an m-side buffer, its n_b rows at a separate offset on the n side),
+// every row LP = 32 float32 wide; the transposed bfloat16 operand of a pass is
+// one LP x sum(K) array with matrix b's columns from xoff[b] (a multiple of 8:
+// 16-byte aligned TMA coordinates).  Per-matrix small matrices (R factors, the
+// l x l SVD) are LP x LP blocks at b * LP * LP.
+//
+// Kernels:
+//   batched_tc_kernel<MODE> : grouped tensor-core pass; a unit is one 128-row tile of
+//                             one matrix with all its k tiles; CTAs take units
+//                             round-robin; A_b through per-matrix tensor maps in global
+//                             memory, the operand through one map; double-buffered
+//                             accumulator in tensor memory.
+//   batched_draw_kernel     : Omega_b from seed + b (Philox, stream 0), float32 and the
+//                             transposed bfloat16 operand.
+//   batched_cholqr_kernel   : one CTA per matrix: Cholesky-QR rounds (shifted first
+//                             round), the 32 x 32 factor and its inverse by one warp in
+//                             registers, the product of the R factors accumulated.
+//   batched_to_bf16t_kernel : basis -> transposed bfloat16 operand.
+//   batched_jacobi_kernel   : one CTA per matrix: one-sided Jacobi of an l x l matrix,
+//                             one warp per column pair, sorted outputs.
+//   batched_lift_kernel     : rows of Q_b times the leading columns of a small matrix.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "kernels_batched.cuh"
+#include "philox.cuh"
+#include "tc_ptx.cuh"
+
+namespace rsvd {
+namespace {
+
+using namespace tcx;
+
+constexpr int LPB = 32;              // padded basis width of the batched path
+constexpr int kBThreads = 192;
+
+__device__ __forceinline__ int find_matrix(const int64_t* __restrict__ off, int nb, int64_t r) {
+  int lo = 0, hi = nb - 1;   // largest b with off[b] <= r
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// grouped tensor-core pass
+// ---------------------------------------------------------------------------
+// FOLD: the operand carries a bfloat16 hi part (rows 0..31) and the residual lo part
+// (rows 32..63) of a float32 basis; one MMA with N = 64 and the epilogue adds the two
+// halves, so the pass sees the basis to about 16 significant bits.
+template <int MODE, int FOLD>
+__global__ void __launch_bounds__(kBThreads, 1) batched_tc_kernel(
+    const CUtensorMap* __restrict__ maps, const __grid_constant__ CUtensorMap map_x,
+    const int2* __restrict__ units, int nunits, const int64_t* __restrict__ kext,
+    const int64_t* __restrict__ mext, const int64_t* __restrict__ xoff,
+    const int64_t* __restrict__ yoff, float* __restrict__ y, int stages, uint32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_full[16], bar_empty[16], bar_acc_full[2], bar_acc_empty[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  constexpr uint32_t a_bytes = BM * BK * 2;
+  constexpr int NX = LPB * (FOLD ? 2 : 1);   // operand rows = MMA N
+  constexpr uint32_t x_bytes = NX * BK * 2;
+  constexpr uint32_t stage_bytes = a_bytes + x_bytes;
+  constexpr uint32_t acc_cols = NX;
+  constexpr uint32_t tmem_cols = 2 * acc_cols;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&bar_acc_full[a], 1);
+      mbar_init(&bar_acc_empty[a], 4);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t i = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int b = units[u].x, t = units[u].y;
+        const CUtensorMap* ma = maps + b;
+        // the maps were written through the generic proxy (a copy before the launch)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(ma))
+                     : "memory");
+        const int kt = (int)cdiv(kext[b], BK);
+        const int xo = (int)xoff[b];
+        for (int kk = 0; kk < kt; ++kk, ++i) {
+          const int s = (int)(i % stages);
+          const uint32_t ph = (uint32_t)((i / stages) & 1);
+          if (!mbar_wait(&bar_empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
+          uint8_t* sa = smem + (size_t)s * stage_bytes;
+          uint8_t* sx = sa + a_bytes;
+          mbar_expect_tx(&bar_full[s], stage_bytes);
+          if (MODE == 0) {
+            tma_load_2d(sa, ma, &bar_full[s], kk * BK, t * BM);
+          } else {
+            tma_load_2d(sa, ma, &bar_full[s], t * BM, kk * BK);
+            tma_load_2d(sa + 8192, ma, &bar_full[s], t * BM + 64, kk * BK);
+          }
+          tma_load_2d(sx, &map_x, &bar_full[s], xo + kk * BK, 0);
+        }
+      }
+      const int64_t issued = i;
+      for (int64_t j = (issued > stages ? issued - stages : 0); j < issued; ++j) {
+        const int s = (int)(j % stages);
+        const uint32_t ph = (uint32_t)((j / stages) & 1);
+        for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(&bar_full[s], ph); ++w) __nanosleep(64);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(NX, MODE);
+      int64_t i = 0;
+      int j = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++j) {
+        const int b = units[u].x;
+        const int kt = (int)cdiv(kext[b], BK);
+        const int ab = j & 1;
+        if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(j >> 1) & 1u) ^ 1u, abort_flag, status)) break;
+        tc_fence_after();
+        const uint32_t dst = tmem + ab * acc_cols;
+        for (int kk = 0; kk < kt; ++kk, ++i) {
+          const int s = (int)(i % stages);
+          const uint32_t ph = (uint32_t)((i / stages) & 1);
+          if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sx = sa + a_bytes;
+#pragma unroll
+          for (int q = 0; q < BK / 16; ++q) {
+            const uint64_t adesc = MODE == 0 ? smem_desc(sa + q * 32, 16, 1024)
+                                             : smem_desc(sa + q * 2048, 8192, 1024);
+            const uint64_t bdesc = smem_desc(sx + q * 32, 16, 1024);
+            mma_bf16(dst, adesc, bdesc, idesc, (kk == 0 && q == 0) ? 0u : 1u);
+          }
+          mma_commit(&bar_empty[s]);
+        }
+        if (ok) mma_commit(&bar_acc_full[ab]);
+      }
+    }
+  } else {
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    int j = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++j) {
+      const int b = units[u].x, t = units[u].y;
+      const int ab = j & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full[ab], (uint32_t)(j >> 1) & 1u,
+                                                        abort_flag, status));
+      tc_fence_after();
+      if (ok) {
+        float v[32];
+        tmem_ld32(tmem + ab * acc_cols + ((uint32_t)(quad * 32) << 16), v);
+        if (FOLD) {
+          float v2[32];
+          tmem_ld32(tmem + ab * acc_cols + LPB + ((uint32_t)(quad * 32) << 16), v2);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] += v2[q];
+        }
+        const int64_t grow = (int64_t)t * BM + row;
+        if (grow < mext[b]) {
+          float* dst = y + (yoff[b] + grow) * LPB;
+#pragma unroll
+          for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_acc_empty[ab]);
+      if (!ok) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// test matrices
+// ---------------------------------------------------------------------------
+__global__ void batched_draw_kernel(uint64_t seed, const int64_t* __restrict__ roff, int nb, int l,
+                                    float* __restrict__ omega, __nv_bfloat16* __restrict__ xbf,
+                                    int64_t ldx, const int64_t* __restrict__ xoff) {
+  const int64_t total = roff[nb] * (LPB / 4);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % roff[nb];
+    const int g = (int)(e / roff[nb]);
+    const int b = find_matrix(roff, nb, r);
+    const int64_t i = r - roff[b];
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+    if (4 * g < l) {
+      const float4 v = gaussian4(seed_key(seed + (uint64_t)b), (uint32_t)g, (uint32_t)i, 0u);
+      z[0] = v.x; z[1] = v.y; z[2] = v.z; z[3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * g + q;
+      const float val = j < l ? z[q] : 0.0f;
+      omega[r * LPB + j] = val;
+      if (xbf) xbf[(int64_t)j * ldx + xoff[b] + i] = __float2bfloat16_rn(val);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky QR, one CTA per matrix
+// ---------------------------------------------------------------------------
+constexpr int kQRThreads = 256;
+constexpr int kChunk = 64;   // rows staged per step
+
+// 32 x 32 Cholesky of S (+ shift, pivot floor) and inverse, by warp 0: lane r holds
+// row r of L (a) and column r of X = L^-1 (x); entries above the diagonal of a are
+// scratch.  Writes L into Ls (row-major, lower) and X into Xs.
+__device__ __forceinline__ void chol32_warp(const float (*S)[LPB + 1], int l, float shift,
+                                            float pfloor, float (*Ls)[LPB + 1],
+                                            float (*Xs)[LPB + 1], uint32_t* status) {
+  const int r = threadIdx.x & 31;
+  float a[LPB], rpv[LPB];
+#pragma unroll
+  for (int j = 0; j < LPB; ++j) {
+    float v = S[r][j];
+    if (r >= l || j >= l) v = (r == j) ? 1.0f : 0.0f;   // identity beyond l
+    else if (r == j) v += shift;
+    a[j] = v;
+  }
+#pragma unroll
+  for (int j = 0; j < LPB; ++j) {
+    float d = __shfl_sync(0xffffffffu, a[j], j);
+    if (j < l && !(d > pfloor)) {
+      if (r == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
+      d = pfloor;
+    }
+    float rp = rsqrtf(d);
+    rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);   // one Newton step for 1/sqrt(d)
+    rpv[j] = rp;
+    const float lij = (r == j) ? d * rp : (r > j ? a[j] * rp : 0.0f);
+    a[j] = lij;
+#pragma unroll
+    for (int k = j + 1; k < LPB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), a[k]);
+  }
+  float x[LPB];
+#pragma unroll
+  for (int i = 0; i < LPB; ++i) {
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      const float lik = __shfl_sync(0xffffffffu, a[k], i);
+      if (k & 1) v1 = fmaf(lik, x[k], v1);
+      else v0 = fmaf(lik, x[k], v0);
+    }
+    x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
+  }
+#pragma unroll
+  for (int j = 0; j < LPB; ++j) Ls[r][j] = (j <= r) ? a[j] : 0.0f;
+#pragma unroll
+  for (int i = 0; i < LPB; ++i) Xs[i][r] = x[i];
+}
+
+__global__ void __launch_bounds__(kQRThreads) batched_cholqr_kernel(
+    const float* __restrict__ yin, float* __restrict__ qout, const int64_t* __restrict__ roff, int l,
+    int rounds, float* __restrict__ rout, uint32_t* status) {
+  __shared__ float chunk[kChunk][LPB];
+  __shared__ float qch[kChunk][LPB];
+  __shared__ float S[LPB][LPB + 1];
+  __shared__ float Ls[LPB][LPB + 1];
+  __shared__ float Xs[LPB][LPB + 1];
+  __shared__ float Racc[LPB][LPB + 1];
+  __shared__ float Rtmp[LPB][LPB + 1];
+  __shared__ float s_red[2][kQRThreads / 32];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = roff[b], rows = roff[b + 1] - r0;
+  const float* Y = yin + r0 * LPB;
+  float* Q = qout + r0 * LPB;
+  const int gi = 4 * warp, gj = lane;   // Gram outputs (gi .. gi+3, gj)
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int e = tid; e < LPB * LPB; e += kQRThreads) Racc[e / LPB][e % LPB] = (e / LPB == e % LPB) ? 1.0f : 0.0f;
+
+  // Gram of the input
+  for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
+    const int nr = (int)min((int64_t)kChunk, rows - c0);
+    for (int e = tid; e < kChunk * LPB; e += kQRThreads) {
+      const int rr = e / LPB, cc = e % LPB;
+      chunk[rr][cc] = rr < nr ? Y[(c0 + rr) * LPB + cc] : 0.0f;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      const float yj = chunk[rr][gj];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(chunk[rr][gi + q], yj, acc[q]);
+    }
+    __syncthreads();
+  }
+  const float* src = Y;
+  for (int round = 0; round < rounds; ++round) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[gi + q][gj] = acc[q];
+    __syncthreads();
+    // shift (first of three rounds) and pivot floor from the trace and largest diagonal
+    if (warp == 0) {
+      const float d = lane < l ? S[lane][lane] : 0.0f;
+      float tr = warp_sum(d), mx = d;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (!isfinite(tr)) {
+        if (lane == 0) set_status(status, ST_NONFINITE);
+      }
+      const float shift = (rounds >= 3 && round == 0) ? (float)l * kEpsF32 * tr : 0.0f;
+      const float pfloor = fmaxf((float)l * kEpsF32 * mx, 1e-30f);
+      chol32_warp(S, l, shift, pfloor, Ls, Xs, status);
+    }
+    __syncthreads();
+    // Racc <- R Racc with R = L^T (upper): Rtmp(i, j) = sum_{i<=c<=j} L(c, i) Racc(c, j)
+    for (int e = tid; e < LPB * LPB; e += kQRThreads) {
+      const int i = e / LPB, jj = e % LPB;
+      float v = 0.0f;
+      for (int c = i; c <= jj; ++c) v = fmaf(Ls[c][i], Racc[c][jj], v);
+      Rtmp[i][jj] = (jj >= i) ? v : 0.0f;
+    }
+    __syncthreads();
+    for (int e = tid; e < LPB * LPB; e += kQRThreads) Racc[e / LPB][e % LPB] = Rtmp[e / LPB][e % LPB];
+    // apply Q = src R^-1 (R^-1(i, j) = X(j, i)), and the Gram of Q for the next round
+    float xr[LPB];
+#pragma unroll
+    for (int i = 0; i < LPB; ++i) xr[i] = Xs[lane][i];   // thread column j = lane
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = 0.0f;
+    for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
+      const int nr = (int)min((int64_t)kChunk, rows - c0);
+      __syncthreads();
+      for (int e = tid; e < kChunk * LPB; e += kQRThreads) {
+        const int rr = e / LPB, cc = e % LPB;
+        chunk[rr][cc] = rr < nr ? src[(c0 + rr) * LPB + cc] : 0.0f;
+      }
+      __syncthreads();
+      for (int rr = warp; rr < nr; rr += kQRThreads / 32) {
+        float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < LPB; i += 2) {
+          v0 = fmaf(chunk[rr][i], xr[i], v0);
+          v1 = fmaf(chunk[rr][i + 1], xr[i + 1], v1);
+        }
+        const float qv = v0 + v1;
+        qch[rr][lane] = qv;
+        Q[(c0 + rr) * LPB + lane] = qv;
+      }
+      __syncthreads();
+      if (round + 1 < rounds) {
+        for (int rr = 0; rr < nr; ++rr) {
+          const float yj = qch[rr][gj];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(qch[rr][gi + q], yj, acc[q]);
+        }
+      }
+    }
+    __syncthreads();
+    src = Q;
+  }
+  float* R = rout + (size_t)b * LPB * LPB;
+  for (int e = tid; e < LPB * LPB; e += kQRThreads) {
+    const int i = e / LPB, jj = e % LPB;
+    R[e] = (i < l && jj < l) ? Racc[i][jj] : 0.0f;
+  }
+}
+
+// basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K)
+__global__ void batched_to_bf16t_kernel(const float* __restrict__ q, const int64_t* __restrict__ roff,
+                                        int nb, __nv_bfloat16* __restrict__ xbf, int64_t ldx,
+                                        const int64_t* __restrict__ xoff, int split) {
+  const int64_t total = roff[nb] * LPB;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % roff[nb];
+    const int c = (int)(e / roff[nb]);
+    const int b = find_matrix(roff, nb, r);
+    const float v = q[r * LPB + c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const int64_t col = xoff[b] + (r - roff[b]);
+    xbf[(int64_t)c * ldx + col] = hi;
+    if (split) xbf[(int64_t)(LPB + c) * ldx + col] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one-sided Jacobi of the l x l matrices (x_b or x_b^T), one CTA per matrix
+// ---------------------------------------------------------------------------
+constexpr int kJThreads = 512;   // 16 warps: one per column pair of a round
+
+__global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
+    const float* __restrict__ x, int transposed, int l, float* __restrict__ ut,
+    float* __restrict__ sig, float* __restrict__ w, uint32_t* status, uint32_t* info, float tol) {
+  __shared__ float Xc[LPB][LPB + 1];   // column c of X in Xc[c][*]
+  __shared__ float Jc[LPB][LPB + 1];
+  __shared__ float s_sig[LPB];
+  __shared__ int s_rot;
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* xb = x + (size_t)b * LPB * LPB;
+  for (int e = tid; e < LPB * LPB; e += kJThreads) {
+    const int c = e / LPB, r = e % LPB;
+    float v = 0.0f;
+    if (r < l && c < l) v = transposed ? xb[c * LPB + r] : xb[r * LPB + c];
+    Xc[c][r] = v;
+    Jc[c][r] = (c < l && r == c) ? 1.0f : 0.0f;
+  }
+  if (tid == 0) s_rot = 0;
+  __syncthreads();
+  const int le = l + (l & 1);
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    for (int round = 0; round < le - 1; ++round) {
+      if (warp < le / 2) {
+        const int p = warp == 0 ? 0 : ((warp - 1 + round) % (le - 1)) + 1;
+        const int kq = le - 1 - warp;
+        const int q = kq == 0 ? 0 : ((kq - 1 + round) % (le - 1)) + 1;
+        if (p < l && q < l) {
+          float u = Xc[p][lane], v = Xc[q][lane];
+          const float a = warp_sum(u * u), bb = warp_sum(v * v), g = warp_sum(u * v);
+          if (g != 0.0f && fabsf(g) > tol * sqrtf(a * bb)) {
+            const float zeta = __fdividef(bb - a, 2.0f * g);
+            const float az = fabsf(zeta);
+            float t = (az > 1e18f) ? __fdividef(0.5f, az) : __fdividef(1.0f, az + sqrtf(fmaf(az, az, 1.0f)));
+            t = copysignf(t, zeta);
+            if (zeta == 0.0f) t = 1.0f;
+            const float w2 = fmaf(t, t, 1.0f);
+            float c = rsqrtf(w2);
+            c = c * fmaf(-0.5f * w2, c * c, 1.5f);
+            const float sn = c * t, tau = sn / (1.0f + c);
+            Xc[p][lane] = u - sn * fmaf(tau, u, v);
+            Xc[q][lane] = v + sn * fmaf(-tau, v, u);
+            u = Jc[p][lane];
+            v = Jc[q][lane];
+            Jc[p][lane] = u - sn * fmaf(tau, u, v);
+            Jc[q][lane] = v + sn * fmaf(-tau, v, u);
+            if (lane == 0) s_rot = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (tid == 0) {
+    if (sweep == 40) set_status(status, ST_JACOBI_NOCONV);
+    if (info) atomicMax(info, (uint32_t)(sweep + 1));
+  }
+  if (warp < LPB) {
+    for (int c = warp; c < LPB; c += kJThreads / 32) {
+      const float v = Xc[c][lane];
+      const float s2 = warp_sum(v * v);
+      if (lane == 0) s_sig[c] = c < l ? sqrtf(s2) : -1.0f;
+    }
+  }
+  __syncthreads();
+  float* ub = ut + (size_t)b * LPB * LPB;
+  float* wb = w + (size_t)b * LPB * LPB;
+  for (int e = tid; e < LPB * LPB; e += kJThreads) {
+    const int r = e / LPB, c = e % LPB;
+    if (r >= l || c >= l) { ub[e] = 0.0f; wb[e] = 0.0f; }
+  }
+  for (int c = warp; c < l; c += kJThreads / 32) {
+    const float sc = s_sig[c];
+    int rk = 0;
+    for (int c2 = 0; c2 < l; ++c2) {
+      const float s2 = s_sig[c2];
+      rk += (s2 > sc || (s2 == sc && c2 < c)) ? 1 : 0;
+    }
+    const float inv = sc > 0.0f ? 1.0f / sc : 0.0f;
+    if (lane < l) {
+      ub[lane * LPB + rk] = Xc[c][lane] * inv;
+      wb[lane * LPB + rk] = Jc[c][lane];
+    }
+    if (lane == 0) sig[(size_t)b * LPB + rk] = sc;
+  }
+}
+
+// out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
+// per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
+__global__ void batched_lift_kernel(const float* __restrict__ q, const int64_t* __restrict__ roff,
+                                    int nb, const float* __restrict__ small, int cols,
+                                    float* __restrict__ out, int ldo) {
+  const int64_t total = roff[nb] * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols;
+    const int c = (int)(e - r * cols);
+    const int b = find_matrix(roff, nb, r);
+    const float* sb = small + (size_t)b * LPB * LPB;
+    const float* qr = q + r * LPB;
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < LPB; j += 2) {
+      v0 = fmaf(qr[j], sb[j * LPB + c], v0);
+      v1 = fmaf(qr[j + 1], sb[(j + 1) * LPB + c], v1);
+    }
+    out[r * ldo + c] = v0 + v1;
+  }
+}
+
+unsigned grid_for(int64_t n) {
+  const int64_t b = cdiv(n, 256);
+  return (unsigned)(b < 16 * kNumSMs ? (b < 1 ? 1 : b) : 16 * kNumSMs);
+}
+
+}  // namespace
+
+size_t batched_tc_smem(int stages, int fold) {
+  return (size_t)stages * (BM * BK * 2 + (fold ? 2 : 1) * LPB * BK * 2) + 1024;
+}
+
+cudaError_t prepare_batched() {
+  cudaError_t e;
+  const int s0 = (int)batched_tc_smem(kBatchedStages, 0), s1 = (int)batched_tc_smem(kBatchedStages, 1);
+  if ((e = cudaFuncSetAttribute(batched_tc_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(batched_tc_kernel<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(batched_tc_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(batched_tc_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+}
+
+cudaError_t launch_batched_tc(int mode, int fold, const void* maps, const void* map_x,
+                              const int2* units, int nunits, const int64_t* kext, const int64_t* mext,
+                              const int64_t* xoff, const int64_t* yoff, float* y, int grid,
+                              uint32_t* status, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  const CUtensorMap* mp = static_cast<const CUtensorMap*>(maps);
+  const CUtensorMap& mx = *static_cast<const CUtensorMap*>(map_x);
+  const size_t sm = batched_tc_smem(kBatchedStages, fold);
+  if (grid > nunits) grid = nunits;
+#define RSVD_BTC(MO, FO)                                                                        \
+  batched_tc_kernel<MO, FO><<<grid, kBThreads, sm, st>>>(mp, mx, units, nunits, kext, mext, xoff, \
+                                                         yoff, y, kBatchedStages, status)
+  if (mode == 0 && !fold) RSVD_BTC(0, 0);
+  else if (mode == 0) RSVD_BTC(0, 1);
+  else if (!fold) RSVD_BTC(1, 0);
+  else RSVD_BTC(1, 1);
+#undef RSVD_BTC
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int64_t total_rows, int l,
+                                float* omega, __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff,
+                                cudaStream_t st) {
+  batched_draw_kernel<<<grid_for(total_rows * (LPB / 4)), 256, 0, st>>>(seed, roff, nb, l, omega, xbf,
+                                                                          ldx, xoff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
+                                  int rounds, float* rout, uint32_t* status, cudaStream_t st) {
+  batched_cholqr_kernel<<<nb, kQRThreads, 0, st>>>(yin, qout, roff, l, rounds, rout, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb, int64_t total_rows,
+                                    __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff, int split,
+                                    cudaStream_t st) {
+  batched_to_bf16t_kernel<<<grid_for(total_rows * LPB), 256, 0, st>>>(q, roff, nb, xbf, ldx, xoff, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb, float* ut, float* sig,
+                                  float* w, uint32_t* status, uint32_t* info, cudaStream_t st) {
+  const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
+  batched_jacobi_kernel<<<nb, kJThreads, 0, st>>>(x, transposed, l, ut, sig, w, status, info, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
+                                const float* small, int cols, float* out, int ldo, cudaStream_t st) {
+  batched_lift_kernel<<<grid_for(total_rows * cols), 256, 0, st>>>(q, roff, nb, small, cols, out, ldo);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

@@ -29,148 +29,13 @@
 
 #include "common.cuh"
 #include "sketch_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace rsvd {
 namespace {
 
-constexpr int BM = 128;            // MMA M / output rows per tile
-constexpr int BK = 64;             // k extent of one pipeline stage (one 128-byte swizzle row)
+using namespace tcx;
 constexpr int kThreads = 192;
-constexpr uint32_t kSpinLimit = 1u << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false (and the abort flag) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          uint32_t* status) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (i > 32) __nanosleep(64);
-  }
-  *abort_flag = 1;
-  set_status(status, ST_TIMEOUT);
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
-// leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
-// >> 4 in 32-45, the fixed version value 1 in bits 46-47, swizzle mode in
-// 61-63 (2 = 128-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
-}
-
-// Instruction descriptor for kind::f16: f32 accumulate (bits 4-5 = 1), bf16 A
-// and B (bits 7-9 and 10-12 = 1), A major-ness in bit 15 (1 = MN-major), B
-// K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t instr_desc(int n, int a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
-         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 (or, for a 16-wide tail, 16) accumulator columns of this thread's row.
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int ncol, float* v) {
-  if (ncol == 32) {
-    tmem_ld32(taddr, v);
-  } else {
-    tmem_ld16(taddr, v);
-#pragma unroll
-    for (int i = 16; i < 32; ++i) v[i] = 0.0f;
-  }
-}
-
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -423,35 +288,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 // host side
 // ---------------------------------------------------------------------------
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-int get_encoder() {
-  if (g_encode) return 0;
-  cudaDriverEntryPointQueryResult q;
-  void* fn = nullptr;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                       &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn)
-    return -1;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return 0;
-}
-
-// 2-D bfloat16 tensor map: inner dimension `inner` (contiguous), `outer` rows
-// of `ld` elements, box {box_inner, box_outer}, 128-byte swizzle.
-int encode_2d(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
-              uint32_t box_inner, uint32_t box_outer) {
-  if (get_encoder()) return -1;
-  const cuuint64_t dims[2] = {inner, outer};
-  const cuuint64_t strides[1] = {ld * 2};
-  const cuuint32_t box[2] = {box_inner, box_outer};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                        const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : -1;
-}
 
 struct TcBuffers {
   float* slots = nullptr;
@@ -472,6 +308,36 @@ int pick_stages(int n_total, int a_tiles = 1) {
 
 }  // namespace
 
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder() {
+  if (g_encode) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return -1;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return 0;
+}
+
+// 2-D bfloat16 tensor map: inner dimension `inner` (contiguous), `outer` rows
+// of `ld` elements, box {box_inner, box_outer}, 128-byte swizzle.
+int tc_encode_2d(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+              uint32_t box_inner, uint32_t box_outer) {
+  if (get_encoder()) return -1;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 int64_t tc_ld(int64_t k) { return round_up(k, 8); }
 int tc_lo_offset(int lp) { return 2 * lp <= 256 ? lp : 256; }
 static int fold_ntotal(int lp) { return 2 * lp <= 256 ? 2 * lp : 512; }
@@ -487,10 +353,10 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
   tc->a_bound = nullptr;
   if (lp > 256 || lp % 16) return -1;
   const int64_t ldn = tc_ld(n), ldm = tc_ld(m);
-  if (encode_2d(tc->map_x_n, xbf, n, lp, ldn, BK, lp)) return -1;
-  if (encode_2d(tc->map_x_t, xbf, m, lp, ldm, BK, lp)) return -1;
+  if (tc_encode_2d(tc->map_x_n, xbf, n, lp, ldn, BK, lp)) return -1;
+  if (tc_encode_2d(tc->map_x_t, xbf, m, lp, ldm, BK, lp)) return -1;
   const int nf = fold_ntotal(lp);
-  if (encode_2d(tc->map_x_t2, xbf, m, tc_lo_offset(lp) + lp, ldm, BK, nf > 256 ? 256 : nf)) return -1;
+  if (tc_encode_2d(tc->map_x_t2, xbf, m, tc_lo_offset(lp) + lp, ldm, BK, nf > 256 ? 256 : nf)) return -1;
   TcBuffers* b = new TcBuffers();
   b->grid = num_sms;
   if (cudaMalloc(&b->slots, sizeof(float) * (size_t)num_sms * BM * lp) != cudaSuccess ||
@@ -526,11 +392,11 @@ int tc_bind_a(TcPlan* tc, const void* A, int with_lo) {
   if (!tc->ready) return -1;
   if (A == tc->a_bound && with_lo == tc->lo_bound) return 0;
   if (reinterpret_cast<uintptr_t>(A) & 15) return -1;
-  if (encode_2d(tc->map_a_n, A, tc->n, tc->m, tc->lda, BK, BM)) return -1;
-  if (encode_2d(tc->map_a_t, A, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+  if (tc_encode_2d(tc->map_a_n, A, tc->n, tc->m, tc->lda, BK, BM)) return -1;
+  if (tc_encode_2d(tc->map_a_t, A, tc->n, tc->m, tc->lda, 64, BK)) return -1;
   if (with_lo) {
     const __nv_bfloat16* lo = static_cast<const __nv_bfloat16*>(A) + tc->m * tc->lda;
-    if (encode_2d(tc->map_a_lo, lo, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+    if (tc_encode_2d(tc->map_a_lo, lo, tc->n, tc->m, tc->lda, 64, BK)) return -1;
   }
   tc->a_bound = A;
   tc->lo_bound = with_lo;
@@ -676,8 +542,8 @@ extern "C" rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int6
   if (noalloc_setup(dev, &d) != 0) return RSVD_ERR_CUDA;
   alignas(64) unsigned char map_a[128];
   alignas(64) unsigned char map_x[128];
-  if (encode_2d(map_a, A, n, m, lda, BK, transpose ? 64 : BM)) return RSVD_ERR_CUDA;
-  if (encode_2d(map_x, Xt, K, l, ldxt, BK, l)) return RSVD_ERR_CUDA;
+  if (tc_encode_2d(map_a, A, n, m, lda, BK, transpose ? 64 : BM)) return RSVD_ERR_CUDA;
+  if (tc_encode_2d(map_x, Xt, K, l, ldxt, BK, l)) return RSVD_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t M = transpose ? n : m;
   const int kt = (int)cdiv(K, BK);

@@ -43,6 +43,10 @@ int tc_bind_a(TcPlan* tc, const void* A, int with_lo);
 // residual of A).  Writes *splits slabs of (rows x lp) float32 into `partial`.
 int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* partial, int* splits,
             cudaStream_t st);
+// 2-D bfloat16 tensor map, 128-byte swizzle: inner dimension `inner` (contiguous), `outer`
+// rows of `ld` elements, box {box_inner, box_outer}.  0 on success.
+int tc_encode_2d(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                 uint32_t box_inner, uint32_t box_outer);
 int64_t tc_partial_elems(int64_t m, int64_t n, int lp, int num_sms);
 void tc_plan_destroy(TcPlan* tc);
 
