@@ -285,6 +285,17 @@ RSVD_API rsvd_status_t rsvd_batched_plan_destroy(rsvd_batched_plan_t plan);
 RSVD_API rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t plan, const void* const* A, float* U,
                                         float* S, float* V);
 
+/* Gradient of L = sum_b ||A_b - U_b S_b V_b^T||_F^2 + sum_b sum_{i<=k} sigma_{b,i} with
+ * respect to every A_b, through the map of rsvd_batched_svd with the test matrices
+ * held fixed (reverse mode through the passes, the Cholesky-QR steps and the SVD of
+ * B; no counterpart in the paper, which does not differentiate its algorithms).  A
+ * must be the matrices of the plan's last rsvd_batched_svd call (its bases and
+ * factors are reused).  gA: host array of `batch` device pointers to float32
+ * m_b x n_b row-major (leading dimension n_b) outputs.  It reads A 2q + 2 times
+ * more and writes every gA_b once; asynchronous on the plan's stream. */
+RSVD_API rsvd_status_t rsvd_batched_svd_backward(rsvd_batched_plan_t plan, const void* const* A,
+                                                 float* const* gA);
+
 /* Waits for the plan's stream and returns the device status as rsvd_sync does;
  * *sweeps (may be NULL) receives the largest Jacobi sweep count since the last call. */
 RSVD_API rsvd_status_t rsvd_batched_sync(rsvd_batched_plan_t plan, uint32_t* sweeps);

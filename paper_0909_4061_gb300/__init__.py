@@ -39,6 +39,7 @@ EXPORTS = (
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
     "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc", "rsvd_convert_a",
     "rsvd_batched_plan_create", "rsvd_batched_plan_destroy", "rsvd_batched_svd", "rsvd_batched_sync",
+    "rsvd_batched_svd_backward",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -104,6 +105,7 @@ _SIGS = {
     "rsvd_batched_plan_destroy": (_c.c_int, [_P]),
     "rsvd_batched_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
     "rsvd_batched_sync": (_c.c_int, [_P, _P]),
+    "rsvd_batched_svd_backward": (_c.c_int, [_P, _P, _P]),
 }
 
 
@@ -417,6 +419,18 @@ class BatchedPlan:
         _check(lib().rsvd_batched_svd(self.handle, ptrs, _ptr(U), _ptr(S), _ptr(V)), "rsvd_batched_svd")
         self._keep = ptrs
         return U, S, V
+
+    def backward(self, mats, grads=None):
+        """dL/dA_b for the matrices of the last svd() call; grads: float32 (m_b, n_b) tensors."""
+        import torch
+
+        if grads is None:
+            grads = [torch.empty(a, b, device=mats[0].device) for a, b in self.shapes]
+        ptrs = (ctypes.c_void_p * self.batch)(*[int(a.data_ptr()) for a in mats])
+        gptrs = (ctypes.c_void_p * self.batch)(*[int(g.data_ptr()) for g in grads])
+        _check(lib().rsvd_batched_svd_backward(self.handle, ptrs, gptrs), "rsvd_batched_svd_backward")
+        self._keep_b = (ptrs, gptrs)
+        return grads
 
     def sync(self):
         sw = ctypes.c_uint32(0)

@@ -1,6 +1,10 @@
 // Batched C ABI: one plan for many small matrices (l = k + p <= 32), each step of the
 // randomized SVD (Algorithm 4.4 + Algorithm 5.1) one launch over the whole batch, and
 // the gradient of the batched reconstruction loss through that map (test matrices fixed).
+// Every pass after the first carries its float32 operand as a bfloat16 hi/lo pair (the
+// passes are bound by reading A, so the doubled MMA width costs nothing measurable), and
+// Omega is drawn as bfloat16 values: the map differentiated by the backward pass is the
+// float32 map on the bfloat16 A with a bfloat16 Omega.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -51,6 +55,20 @@ struct rsvd_batched_plan_s {
   float* wb = nullptr;            // nb x LP x LP (right)
   float* sig = nullptr;           // nb x LP
   uint32_t* status = nullptr;     // [0] status bits, [1] Jacobi sweeps
+  // backward workspace
+  int kr = 0;                     // 32 (2q + 2) columns of the low-rank factors of dL/dA
+  float* lbuf = nullptr;          // sum_m x kr
+  float* rbuf = nullptr;          // sum_n x kr
+  float* gm = nullptr;            // sum_m x LP
+  float* pm = nullptr;            // sum_m x LP
+  float* gn = nullptr;            // sum_n x LP
+  float* nmat = nullptr;          // nb x LP x LP
+  float* rinv = nullptr;          // nb x LP x LP
+  int4* d_units_f = nullptr;      // (b, 64-row tile, 64-column tile) of dL/dA
+  int nunits_f = 0;
+  int64_t* d_lda = nullptr;
+  const void** d_aptr = nullptr;
+  float** d_gptr = nullptr;
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
 };
@@ -154,12 +172,12 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRYS(bpass(P, 0, 0, P->ym));                                                  // Y_0 = A Omega
   BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, rounds, P->rm[0], P->status, P->st));
   for (int j = 1; j <= P->q; ++j) {
-    BTRYS(to_operand(P, P->qm[j - 1], true, 0));
-    BTRYS(bpass(P, 1, 0, P->yn));                                                // A^T Q_{j-1}
+    BTRYS(to_operand(P, P->qm[j - 1], true, 1));
+    BTRYS(bpass(P, 1, 1, P->yn));                                                // A^T Q_{j-1}
     BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds, P->rn[j - 1],
                                P->status, P->st));
-    BTRYS(to_operand(P, P->qn[j - 1], false, 0));
-    BTRYS(bpass(P, 0, 0, P->ym));                                                // A Qt_j
+    BTRYS(to_operand(P, P->qn[j - 1], false, 1));
+    BTRYS(bpass(P, 0, 1, P->ym));                                                // A Qt_j
     BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, rounds, P->rm[j], P->status,
                                P->st));
   }
@@ -168,11 +186,56 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
   BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->status, P->st));
   BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
-  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->sum_m, P->ub, P->k, U, P->k, P->st));
-  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, P->k, V, P->k, P->st));
+  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->sum_m, P->ub, P->k, P->k, U, P->k, P->st));
+  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, P->k, P->k, V, P->k, P->st));
   if (S)
     BTRY(cudaMemcpy2DAsync(S, sizeof(float) * P->k, P->sig, sizeof(float) * LP, sizeof(float) * P->k,
                            P->nb, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+// dL/dY from dL/dQ for Y = Q R (rows of one side): N, R^-1 per matrix, then per row
+rsvd_status_t qr_back(rsvd_batched_plan_t P, const float* Q, const float* gQ, const float* R, bool m_side,
+                      float* gY) {
+  const int64_t* roff = m_side ? P->d_roff_m : P->d_roff_n;
+  BTRY(launch_bwd_qr_small(Q, gQ, roff, P->nb, P->l, R, P->nmat, P->rinv, P->st));
+  BTRY(launch_bwd_qr_apply(Q, gQ, roff, P->nb, m_side ? P->sum_m : P->sum_n, P->nmat, P->rinv, gY, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* const* gA) {
+  BTRYS(bind_maps(P, A));
+  for (int b = 0; b < P->nb; ++b)
+    if (!gA[b]) return RSVD_ERR_INVALID_ARG;
+  BTRY(cudaMemcpyAsync(P->d_aptr, A, sizeof(void*) * P->nb, cudaMemcpyHostToDevice, P->st));
+  BTRY(cudaMemcpyAsync(P->d_gptr, gA, sizeof(float*) * P->nb, cudaMemcpyHostToDevice, P->st));
+  const int kr = P->kr;
+  // V = Q_B W_k (n side) is the first right factor and the operand of A V
+  BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, LP, P->k, P->gn, LP, P->st));
+  BTRY(launch_copy_block(P->gn, P->sum_n, P->rbuf, kr, 0, P->st));
+  BTRYS(to_operand(P, P->gn, false, 1));
+  BTRYS(bpass(P, 0, 1, P->pm));                                                  // A V
+  // dL/dQ_q and the first left factor U (I - 2 S)
+  BTRY(launch_bwd_gq(P->pm, P->qm[P->q], P->d_roff_m, P->nb, P->sum_m, P->ub, P->sig, P->k, P->gm,
+                     P->lbuf, kr, P->st));
+  int blk = 1;
+  for (int j = P->q; j >= 1; --j, blk += 2) {
+    BTRYS(qr_back(P, P->qm[j], P->gm, P->rm[j], true, P->pm));                   // dY_j
+    BTRY(launch_copy_block(P->pm, P->sum_m, P->lbuf, kr, blk * LP, P->st));
+    BTRY(launch_copy_block(P->qn[j - 1], P->sum_n, P->rbuf, kr, blk * LP, P->st));
+    BTRYS(to_operand(P, P->pm, true, 1));
+    BTRYS(bpass(P, 1, 1, P->gn));                                                // dQt_j = A^T dY_j
+    BTRYS(qr_back(P, P->qn[j - 1], P->gn, P->rn[j - 1], false, P->yn));          // dZ_j
+    BTRY(launch_copy_block(P->yn, P->sum_n, P->rbuf, kr, (blk + 1) * LP, P->st));
+    BTRY(launch_copy_block(P->qm[j - 1], P->sum_m, P->lbuf, kr, (blk + 1) * LP, P->st));
+    BTRYS(to_operand(P, P->yn, false, 1));
+    BTRYS(bpass(P, 0, 1, P->gm));                                                // dQ_{j-1} = A dZ_j
+  }
+  BTRYS(qr_back(P, P->qm[0], P->gm, P->rm[0], true, P->pm));                     // dY_0
+  BTRY(launch_copy_block(P->pm, P->sum_m, P->lbuf, kr, blk * LP, P->st));
+  BTRY(launch_copy_block(P->omega, P->sum_n, P->rbuf, kr, blk * LP, P->st));
+  BTRY(launch_bwd_final(P->d_units_f, P->nunits_f, P->d_aptr, P->d_lda, P->d_gptr, P->d_m, P->d_n,
+                        P->d_roff_m, P->d_roff_n, P->lbuf, P->rbuf, kr, P->st));
   return RSVD_OK;
 }
 
@@ -255,6 +318,27 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
     bfree(P);
     return s;
   }
+  P->kr = kBatchedLP * (2 * q + 2);
+  {
+    std::vector<int4> uf;
+    for (int b = 0; b < batch; ++b)
+      for (int64_t rt = 0; rt < cdiv(m[b], 64); ++rt)
+        for (int64_t ct = 0; ct < cdiv(n[b], 64); ++ct) uf.push_back(make_int4(b, (int)rt, (int)ct, 0));
+    P->nunits_f = (int)uf.size();
+    if ((s = upload(P, &P->d_units_f, uf)) != RSVD_OK || (s = upload(P, &P->d_lda, P->lda)) != RSVD_OK ||
+        (s = balloc(P, &P->lbuf, (size_t)P->sum_m * P->kr)) != RSVD_OK ||
+        (s = balloc(P, &P->rbuf, (size_t)P->sum_n * P->kr)) != RSVD_OK ||
+        (s = balloc(P, &P->gm, (size_t)P->sum_m * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->pm, (size_t)P->sum_m * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->gn, (size_t)P->sum_n * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->nmat, (size_t)batch * LP * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->rinv, (size_t)batch * LP * LP)) != RSVD_OK ||
+        (s = balloc(P, &P->d_aptr, (size_t)batch)) != RSVD_OK ||
+        (s = balloc(P, &P->d_gptr, (size_t)batch)) != RSVD_OK) {
+      bfree(P);
+      return s;
+    }
+  }
   P->qm.assign(q + 1, nullptr);
   P->rm.assign(q + 1, nullptr);
   P->qn.assign(q, nullptr);
@@ -295,6 +379,11 @@ rsvd_status_t rsvd_batched_plan_destroy(rsvd_batched_plan_t P) {
 rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
   if (!P || !A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
   return bforward(P, A, U, S, V);
+}
+
+rsvd_status_t rsvd_batched_svd_backward(rsvd_batched_plan_t P, const void* const* A, float* const* gA) {
+  if (!P || !A || !gA) return RSVD_ERR_INVALID_ARG;
+  return bbackward(P, A, gA);
 }
 
 rsvd_status_t rsvd_batched_sync(rsvd_batched_plan_t P, uint32_t* sweeps) {

@@ -14,8 +14,8 @@
 //                             round-robin; A_b through per-matrix tensor maps in global
 //                             memory, the operand through one map; double-buffered
 //                             accumulator in tensor memory.
-//   batched_draw_kernel     : Omega_b from seed + b (Philox, stream 0), float32 and the
-//                             transposed bfloat16 operand.
+//   batched_draw_kernel     : Omega_b from seed + b (Philox, stream 0), rounded to
+//                             bfloat16: the transposed operand and its float32 copy.
 //   batched_cholqr_kernel   : one CTA per matrix: Cholesky-QR rounds (shifted first
 //                             round), the 32 x 32 factor and its inverse by one warp in
 //                             registers, the product of the R factors accumulated.
@@ -229,9 +229,10 @@ __global__ void batched_draw_kernel(uint64_t seed, const int64_t* __restrict__ r
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 4 * g + q;
-      const float val = j < l ? z[q] : 0.0f;
-      omega[r * LPB + j] = val;
-      if (xbf) xbf[(int64_t)j * ldx + xoff[b] + i] = __float2bfloat16_rn(val);
+      // the float32 copy holds exactly the bfloat16 values the first pass multiplies with
+      const __nv_bfloat16 h = __float2bfloat16_rn(j < l ? z[q] : 0.0f);
+      omega[r * LPB + j] = __bfloat162float(h);
+      if (xbf) xbf[(int64_t)j * ldx + xoff[b] + i] = h;
     }
   }
 }
@@ -514,8 +515,9 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
 
 // out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
 // per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
+// for c < valid, 0 for valid <= c < cols
 __global__ void batched_lift_kernel(const float* __restrict__ q, const int64_t* __restrict__ roff,
-                                    int nb, const float* __restrict__ small, int cols,
+                                    int nb, const float* __restrict__ small, int cols, int valid,
                                     float* __restrict__ out, int ldo) {
   const int64_t total = roff[nb] * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -526,10 +528,12 @@ __global__ void batched_lift_kernel(const float* __restrict__ q, const int64_t* 
     const float* sb = small + (size_t)b * LPB * LPB;
     const float* qr = q + r * LPB;
     float v0 = 0.0f, v1 = 0.0f;
+    if (c < valid) {
 #pragma unroll
-    for (int j = 0; j < LPB; j += 2) {
-      v0 = fmaf(qr[j], sb[j * LPB + c], v0);
-      v1 = fmaf(qr[j + 1], sb[(j + 1) * LPB + c], v1);
+      for (int j = 0; j < LPB; j += 2) {
+        v0 = fmaf(qr[j], sb[j * LPB + c], v0);
+        v1 = fmaf(qr[j + 1], sb[(j + 1) * LPB + c], v1);
+      }
     }
     out[r * ldo + c] = v0 + v1;
   }
@@ -605,8 +609,10 @@ cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb,
 }
 
 cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
-                                const float* small, int cols, float* out, int ldo, cudaStream_t st) {
-  batched_lift_kernel<<<grid_for(total_rows * cols), 256, 0, st>>>(q, roff, nb, small, cols, out, ldo);
+                                const float* small, int cols, int valid, float* out, int ldo,
+                                cudaStream_t st) {
+  batched_lift_kernel<<<grid_for(total_rows * cols), 256, 0, st>>>(q, roff, nb, small, cols, valid, out,
+                                                                     ldo);
   return cudaGetLastError();
 }
 

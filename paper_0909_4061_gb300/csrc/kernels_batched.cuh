@@ -34,6 +34,29 @@ cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb,
 cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb, float* ut, float* sig,
                                   float* w, uint32_t* status, uint32_t* info, cudaStream_t st);
 cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
-                                const float* small, int cols, float* out, int ldo, cudaStream_t st);
+                                const float* small, int cols, int valid, float* out, int ldo,
+                                cudaStream_t st);
+
+// ---- backward (k_batched_bwd.cu) ----
+// gQ = (P (I - 2 S) + 2 U S^2) Ut_k^T with U = Q Ut_k (per row; P = A V, m side), and
+// ublk = U (I - 2 S) (first k columns, zero beyond), ld ldu.
+cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
+                          const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
+                          cudaStream_t st);
+// per matrix: N = copyltu(-gQ^T Q) and Rinv = R^-1 (R upper, l x l, identity beyond l)
+cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, int nb, int l,
+                                const float* R, float* N, float* Rinv, cudaStream_t st);
+// gY = (gQ + Q N) R^-T, per row
+cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
+                                int64_t total_rows, const float* N, const float* Rinv, float* gY,
+                                cudaStream_t st);
+// dst[r][col0 + c] = src[r][c] (rows x 32 -> ld ldd)
+cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
+                              cudaStream_t st);
+// gA_b = 2 A_b + L_b R_b^T over tiles (b, 64-row tile, 64-column tile)
+cudaError_t launch_bwd_final(const int4* units, int nunits, const void* const* A, const int64_t* lda,
+                             float* const* gA, const int64_t* m, const int64_t* n,
+                             const int64_t* roff_m, const int64_t* roff_n, const float* L,
+                             const float* R, int kr, cudaStream_t st);
 
 }  // namespace rsvd

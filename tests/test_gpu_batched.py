@@ -66,3 +66,41 @@ def test_batched_matches_single_matrix_path(rsvd_lib):
         torch.cuda.synchronize()
     s, s1 = S[0].cpu().double().numpy(), S1.cpu().double().numpy()
     assert np.max(np.abs(s - s1)) <= 1e-4 * s1[0]
+
+
+def _omega_bf16(pkg, seed, n, l):
+    om = torch.zeros(n, l, device="cuda")
+    pkg.rsvd_draw_gaussian(seed, 0, n, l, om, l)
+    torch.cuda.synchronize()
+    return om.to(torch.bfloat16).double().cpu().numpy()
+
+
+@pytest.mark.parametrize("q", [1, 0])
+def test_batched_backward_matches_autograd(rsvd_lib, q):
+    """dL/dA_b from the library against torch autograd through the oracle's float64 steps
+    (Householder QR with the sign fix, SVD of B), on the same bfloat16 A_b and the
+    bfloat16 test matrix the first pass multiplies with.  The terms 2 A + U (I - 2S) V^T
+    are float32-accurate; the chain terms (through the range finder) pass through
+    R_0^-T, so float32 rounding in them is amplified by kappa(Y_0) = kappa(R_0):
+        ||dA - dA_ref||_F / ||dA_ref||_F <= 1e-4 + 20 u32 kappa(Y_0) c,
+    c = the chain terms' share of ||dA_ref||_F (measured against the closed form
+    2 (A - A_k) + U_k V_k^T of the exact truncated SVD)."""
+    from oracle import grad
+
+    shapes = [(300, 200), (128, 64), (517, 389), (700, 512)]
+    k, p, seed = 16, 8, 7
+    mats, a64 = _make_batch(shapes, 1105)
+    with rsvd_lib.BatchedPlan(shapes, k, p, q, seed=seed) as pl:
+        pl.svd(mats)
+        grads = pl.backward(mats)
+        pl.sync()
+    for b, (m, n) in enumerate(shapes):
+        om = _omega_bf16(rsvd_lib, seed + b, n, k + p)
+        g_ref = grad.grad_autograd(a64[b], k, p, q, om)
+        g = grads[b].double().cpu().numpy()
+        rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+        chain = np.linalg.norm(g_ref - grad.grad_exact_svd(a64[b], k)) / np.linalg.norm(g_ref)
+        kap = np.linalg.cond(a64[b] @ om)
+        tol = 1e-4 + 20 * 2.0 ** -24 * kap * chain
+        print(f"backward b={b} q={q}: rel err {rel:.3e}  chain share {chain:.3e}  kappa(Y0) {kap:.3e}  tol {tol:.3e}")
+        assert rel <= tol, (rel, tol)
