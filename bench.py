@@ -454,6 +454,107 @@ def run_small_probe(args):
     print(json.dumps({"small_probe": "ok", "m": m, "n": n, "l": 110, "jacobi_sweeps": sweeps}))
 
 
+def _events_ms(fn, steps, warmup):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _rel_err(A, U, S, V):
+    """||A - U diag(S) V^T||_F / ||A||_F in float64, by 16384-row blocks (on the device)."""
+    import torch
+
+    num, den = 0.0, 0.0
+    for r0 in range(0, A.shape[0], 16384):
+        a = A[r0:r0 + 16384].double()
+        den += float((a * a).sum())
+        a.addmm_(U[r0:r0 + 16384].double() * S.double(), V.double().T, alpha=-1.0)
+        num += float((a * a).sum())
+    return (num / den) ** 0.5
+
+
+def run_workload(args):
+    """Secondary workloads (one JSON line each; not the headline metric):
+    c3 -- 262144 x 4096, single-pass (Section 5.5) vs q = 2 multi-pass, k = 64, p = 16;
+    c4 -- 32768 x 32768, SRFT (Section 4.6) vs Gaussian test matrix, k = 236, p = 20, q = 1;
+    c5 -- 512 matrices m ~ U[128, 2048], n ~ U[64, 1024], batched forward and backward."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0909_4061_gb300 as pkg
+    import synth
+
+    torch.cuda.set_device(0)
+    steps, warmup = max(args.steps, 1), max(args.warmup, 3)
+    out = {"workload": args.workload, "unit": "ms", "steps": steps, "warmup": warmup,
+           "data": "synthetic (seeded Haar factors on the device)", "higher_is_better": False}
+    if args.workload in ("c3", "c4"):
+        w = synth.C3 if args.workload == "c3" else synth.C4
+        noise = 1e-4 if args.workload == "c3" else 0.0
+        A = synth.device_lowrank(w.m, w.n, w.sigma(), w.matrix_seed, noise_std=noise)
+        Ab = A.to(torch.bfloat16)
+        torch.cuda.synchronize()
+        variants = ([("single_pass", dict(single_pass=1, q=0)), ("multi_pass_q2", dict(q=2))]
+                    if args.workload == "c3" else
+                    [("srft", dict(test_matrix=pkg.RSVD_SRFT, q=w.q)), ("gaussian", dict(q=w.q))])
+        res = {}
+        for name, kw in variants:
+            q = kw.pop("q")
+            with pkg.Plan(w.m, w.n, w.k, w.p, q, w.omega_seed, pkg.RSVD_BF16_TC, **kw) as pl:
+                U = torch.empty(w.m, w.k, device="cuda")
+                S = torch.empty(w.k, device="cuda")
+                V = torch.empty(w.n, w.k, device="cuda")
+                ms = _events_ms(lambda: pkg.rsvd_svd(pl.handle, Ab, U, S, V), steps, warmup)
+                pkg.rsvd_sync(pl.handle)
+                pkg.rsvd_profile(pl.handle, (1 << pkg.RSVD_NUM_STEPS) - 1)
+                pkg.rsvd_svd(pl.handle, Ab, U, S, V)
+                torch.cuda.synchronize()
+                stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
+                pkg.rsvd_profile(pl.handle, 0)
+                res[name] = {"ms": round(ms, 4), "rel_err_vs_fp32_A": round(_rel_err(A, U, S, V), 6),
+                             "passes_over_A": (2 if kw.get("single_pass") else 2 * q + 2),
+                             "stages_ms": {k2: round(v, 4) for k2, v in stage_ms.items()}}
+        out.update({"metric": "rank-k rSVD ms per matrix (bf16 tensor cores)",
+                    "config": {"m": w.m, "n": w.n, "k": w.k, "p": w.p}, "results": res})
+    elif args.workload == "c5":
+        shapes = synth.c5_shapes()
+        mats = []
+        for b, (m, n) in enumerate(shapes):
+            a = synth.device_lowrank(m, n, synth.spectrum_exp(min(m, n), 4.0),
+                                     synth.C5_MATRIX_SEED * 100003 + b)
+            lda = -(-n // 8) * 8
+            t = torch.zeros(m, lda, dtype=torch.bfloat16, device="cuda")
+            t[:, :n] = a.to(torch.bfloat16)
+            mats.append(t)
+        torch.cuda.synchronize()
+        with pkg.BatchedPlan(shapes, synth.C5_K, synth.C5_P, synth.C5_Q, seed=synth.C5_OMEGA_SEED) as pl:
+            U, S, V = pl.svd(mats)
+            grads = pl.backward(mats)
+            fwd = _events_ms(lambda: pl.svd(mats, U, S, V), steps, warmup)
+            bwd = _events_ms(lambda: pl.backward(mats, grads), steps, warmup)
+            sweeps = pl.sync()
+        elems = sum(m * n for m, n in shapes)
+        out.update({"metric": "batched rank-16 rSVD forward / backward ms for the whole batch",
+                    "config": {"batch": len(shapes), "k": synth.C5_K, "p": synth.C5_P, "q": synth.C5_Q,
+                               "elements": elems},
+                    "results": {"forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4),
+                                "forward_A_bytes_per_ms": round(elems * 2 * 4 / fwd / 1e6, 1),
+                                "jacobi_sweeps_max": sweeps}})
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -510,7 +611,12 @@ def main():
     ap.add_argument("--pass-probe", action="store_true",
                     help="three launches of the tensor-core pass kernel on an 8192 x 16384 bf16 A "
                          "(268 MB, larger than L2): the small case for full ncu captures")
+    ap.add_argument("--workload", choices=("c2", "c3", "c4", "c5"), default="c2",
+                    help="c2 (default) is the headline line; c3/c4/c5 print one secondary line each")
     args = ap.parse_args()
+    if args.workload != "c2" and args.impl == "ours":
+        run_workload(args)
+        return
     if args.pass_probe:
         run_pass_probe(args)
         return

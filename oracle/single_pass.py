@@ -17,6 +17,13 @@ whose normal equations are the Sylvester equation
 solved exactly through the eigenbases of the two symmetric positive definite
 matrices.  ``min_residual_bruteforce`` solves the same least-squares problem
 through its Kronecker form, for tiny l only.
+
+Bases (the remark on single-pass error in Section 5.5): with Q, Qt the full l-column
+bases the coefficient matrices are square and usually ill-conditioned, and on noisy,
+slowly decaying spectra the result degrades badly; the remark's remedy -- keep only
+the k leading left singular vectors of each sample matrix, so that the systems above
+are k x l, overdetermined -- is taken here (``truncate_bases=True``, the default);
+with p = 0 both forms coincide.
 """
 from __future__ import annotations
 
@@ -73,11 +80,20 @@ def min_residual_bruteforce(x1, c1, x2, c2):
     return sol.reshape(lt, l).T
 
 
-def rsvd_single_pass(a: np.ndarray, k: int, omega: np.ndarray, psi: np.ndarray):
+def leading_left(y: np.ndarray, k: int) -> np.ndarray:
+    """The k leading left singular vectors of y."""
+    return np.linalg.svd(y, full_matrices=False)[0][:, :k]
+
+
+def rsvd_single_pass(a: np.ndarray, k: int, omega: np.ndarray, psi: np.ndarray,
+                     truncate_bases: bool = True):
     """Rank-k factors (U, sigma, V) from one pass over A, plus (Q, Qt, B)."""
     y, yt = two_sided_sketch(a, omega, psi)
-    qmat, _ = qr_pos(y)
-    qt, _ = qr_pos(yt)
+    if truncate_bases:
+        qmat, qt = leading_left(y, k), leading_left(yt, k)
+    else:
+        qmat, _ = qr_pos(y)
+        qt, _ = qr_pos(yt)
     x1, c1, x2, c2 = reduced_system(qmat, qt, omega, psi, y, yt)
     b = min_residual(x1, c1, x2, c2)
     ub, s, vbt = np.linalg.svd(b, full_matrices=False)

@@ -42,7 +42,7 @@ struct rsvd_plan_s {
   float* partial = nullptr;  // split-K partial results
   int64_t partial_elems = 0;
   float* gpart = nullptr;    // nblk x lp x lp
-  float* small = nullptr;    // 16 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch, single pass
+  float* small = nullptr;    // 24 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch, single pass
   float* psi = nullptr;      // m x lp   second test matrix of the single-pass sketch
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
@@ -74,7 +74,7 @@ struct rsvd_plan_s {
   float* ut() { return small + 5 * (size_t)lp * lp; }
   float* w() { return small + 6 * (size_t)lp * lp; }
   float* sq() { return small + 7 * (size_t)lp * lp; }
-  // single pass (Section 5.5): X1, X2, C1 (R of Y), F/G/H/B scratch, U1, U2, W scratch
+  // single pass (Section 5.5): 16 more l x l blocks (see stage_single_pass)
   float* sp(int i) { return small + (size_t)(8 + i) * lp * lp; }
 };
 
@@ -304,13 +304,18 @@ rsvd_status_t check_plan(rsvd_plan_t P) {
 }
 
 // Single-pass randomized SVD (Section 5.5): Y = A Omega and Yt = A^T Psi from the
-// two sketches alone, Y = Q R and Yt = Qt Rt (Cholesky QR), and the reduced matrix
-// B ~ Q^T A Qt as the minimum-residual solution of
-//     B X1 = C1,  B^T X2 = C2,   X1 = Qt^T Omega, C1 = Q^T Y = R, X2 = Q^T Psi, C2 = Qt^T Yt = Rt,
+// two sketches alone, Y = Q R and Yt = Qt Rt (Cholesky QR); the bases are cut to the k
+// leading left singular vectors Q_k = Q U_R[:, :k], Qt_k = Qt U_Rt[:, :k] (the remedy of
+// the section's remark on single-pass error: the systems below become k x l,
+// overdetermined), and the reduced k x k matrix B ~ Q_k^T A Qt_k is the minimum-residual
+// solution of
+//     B X1 = C1,  B^T X2 = C2,   X1 = Qt_k^T Omega, C1 = Q_k^T Y = U_R_k^T R,
+//                                X2 = Q_k^T Psi,    C2 = Qt_k^T Yt = U_Rt_k^T Rt,
 // i.e. of the Sylvester normal equations (X2 X2^T) B + B (X1 X1^T) = C1 X1^T + X2 C2^T,
 // solved in the singular bases of X1 and X2: X_i = U_i S_i W_i^T gives
 // B = U2 [(U2^T F U1) ./ (s2_i^2 + s1_j^2)] U1^T, F = C1 X1^T + X2 C2^T.  Then B = Ub Sb Vb^T
-// (Jacobi), U = Q Ub_k, V = Qt Vb_k.  q is ignored; A is read by one pass of each kind.
+// (Jacobi), U = Q (U_R_k Ub), V = Qt (U_Rt_k Vb).  q is ignored; A is read by one pass of
+// each kind.
 rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S, float* V,
                                 float* Qout, int64_t ldq) {
   const bool tc = P->opt.precision == RSVD_BF16_TC;
@@ -338,9 +343,10 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
   }
   TRYS(step_pass(P, A, 1, P->psi, false, &s, &stride));
   TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));
+  const int k = P->k;
   {
     Step sp(P, RSVD_STEP_SMALL_SVD);
-    sp.launched(14);
+    sp.launched(24);
     // X1 = Qt^T Omega (K = n), X2 = Q^T Psi (K = m): split over row blocks, summed by gather
     const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
     const int s1 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->n, 512)));
@@ -349,30 +355,43 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
     const int s2 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->m, 512)));
     TRY(launch_gemm_f32(1, lp, lp, P->m, P->qbuf, lp, P->psi, lp, P->gpart, lp, s2, l2, P->st));
     TRY(launch_gather(P->gpart, s2, l2, lp, P->sp(1), lp, lp, lp, lp, P->st));
-    // singular bases of X1 (U1 = sp(5), s1) and X2 (U2 = sp(6), s2)
-    TRY(launch_jacobi_svd(P->sp(0), lp, 0, l, lp, P->sp(5), P->sig2, P->sp(7), P->lbuf(),
-                          P->status, P->status + 1, P->st, P->opt.small_svd));
-    TRY(launch_jacobi_svd(P->sp(1), lp, 0, l, lp, P->sp(6), P->sig2 + lp, P->sp(7), P->lbuf(),
-                          P->status, P->status + 1, P->st, P->opt.small_svd));
-    // F = C1 X1^T + X2 C2^T (C1 = sp(2), C2 = racc); G = U2^T F U1; H = G ./ (s2^2 + s1^2)
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(2), lp, 0, P->sp(0), lp, 1, 0.f, P->sp(3), lp, P->st));
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(1), lp, 0, P->racc(), lp, 1, 1.f, P->sp(3), lp, P->st));
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(6), lp, 1, P->sp(3), lp, 0, 0.f, P->sp(4), lp, P->st));
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(4), lp, 0, P->sp(5), lp, 0, 0.f, P->sp(3), lp, P->st));
-    TRY(launch_sylvester_scale(P->sp(3), l, lp, P->sig2 + lp, P->sig2, P->sp(4), P->st));
-    // B = U2 H U1^T into sq (zero padded)
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(6), lp, 0, P->sp(4), lp, 0, 0.f, P->sp(3), lp, P->st));
-    TRY(cudaMemsetAsync(P->sq(), 0, sizeof(float) * l2, P->st));
-    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(3), lp, 0, P->sp(5), lp, 1, 0.f, P->sq(), lp, P->st));
-    // B = Ub Sb Vb^T
-    TRY(launch_jacobi_svd(P->sq(), lp, 0, l, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+    // the k leading left singular vectors of Y = Q R and Yt = Qt Rt: Q U_R[:, :k], Qt U_Rt[:, :k]
+    TRY(launch_jacobi_svd(P->sp(2), lp, 0, l, lp, P->sp(5), P->sig2, P->sp(7), P->lbuf(), P->status,
                           P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_jacobi_svd(P->racc(), lp, 0, l, lp, P->sp(6), P->sig2 + lp, P->sp(7), P->lbuf(),
+                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    // the k x l systems: X1 = U_Rt_k^T (Qt^T Omega), C1 = U_R_k^T R, X2 = U_R_k^T (Q^T Psi),
+    // C2 = U_Rt_k^T Rt (rows k..l-1 of the padded squares stay zero)
+    for (int i : {3, 4, 8, 9}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * l2, P->st));
+    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(6), lp, 1, P->sp(0), lp, 0, 0.f, P->sp(3), lp, P->st));
+    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(2), lp, 0, 0.f, P->sp(8), lp, P->st));
+    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(1), lp, 0, 0.f, P->sp(4), lp, P->st));
+    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(6), lp, 1, P->racc(), lp, 0, 0.f, P->sp(9), lp, P->st));
+    // singular bases of X1 (U1 = sp(10), s1) and X2 (U2 = sp(11), s2): k nonzero values each
+    TRY(launch_jacobi_svd(P->sp(3), lp, 0, l, lp, P->sp(10), P->sig2, P->sp(7), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_jacobi_svd(P->sp(4), lp, 0, l, lp, P->sp(11), P->sig2 + lp, P->sp(7), P->lbuf(),
+                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    // F = C1 X1^T + X2 C2^T; G = U2^T F U1; H = G ./ (s2^2 + s1^2); B = U2 H U1^T (all k x k)
+    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(8), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), lp, P->st));
+    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(4), lp, 0, P->sp(9), lp, 1, 1.f, P->sp(12), lp, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), lp, 1, P->sp(12), lp, 0, 0.f, P->sp(13), lp, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(13), lp, 0, P->sp(10), lp, 0, 0.f, P->sp(12), lp, P->st));
+    TRY(launch_sylvester_scale(P->sp(12), k, lp, P->sig2 + lp, P->sig2, P->sp(13), P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), lp, 0, P->sp(13), lp, 0, 0.f, P->sp(12), lp, P->st));
+    TRY(cudaMemsetAsync(P->sq(), 0, sizeof(float) * l2, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(12), lp, 0, P->sp(10), lp, 1, 0.f, P->sq(), lp, P->st));
+    // B = Ub Sb Vb^T (k x k), then the lifts' small factors U_R_k Ub and U_Rt_k Vb
+    TRY(launch_jacobi_svd(P->sq(), lp, 0, k, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_small_gemm(l, k, k, 1.f, P->sp(5), lp, 0, P->ut(), lp, 0, 0.f, P->sp(14), lp, P->st));
+    TRY(launch_small_gemm(l, k, k, 1.f, P->sp(6), lp, 0, P->w(), lp, 0, 0.f, P->sp(15), lp, P->st));
   }
   if (!U) return RSVD_OK;
   Step sp(P, RSVD_STEP_LIFT);
   sp.launched(2);
-  TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->ut(), lp, U, P->k, 1, 0, P->st));
-  TRY(launch_gemm_f32(0, P->n, P->k, lp, P->qtbuf, lp, P->w(), lp, V, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->sp(14), lp, U, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->n, P->k, lp, P->qtbuf, lp, P->sp(15), lp, V, P->k, 1, 0, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
   return RSVD_OK;
 }
@@ -473,7 +492,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (s = dalloc(P, &P->tmp2, (size_t)P->maxmn * lp)) != RSVD_OK ||
       (s = dalloc(P, &P->partial, (size_t)part)) != RSVD_OK ||
       (s = dalloc(P, &P->gpart, (size_t)nblk * lp * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->small, (size_t)16 * lp * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->small, (size_t)24 * lp * lp)) != RSVD_OK ||
       (o.single_pass && (s = dalloc(P, &P->psi, (size_t)m * lp)) != RSVD_OK) ||
       (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lp)) != RSVD_OK) ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
@@ -502,7 +521,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_CUDA;
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
-      cudaMemsetAsync(P->small, 0, sizeof(float) * 16 * lp * lp, P->st) != cudaSuccess) {
+      cudaMemsetAsync(P->small, 0, sizeof(float) * 24 * lp * lp, P->st) != cudaSuccess) {
     free_plan(P);
     return RSVD_ERR_CUDA;
   }

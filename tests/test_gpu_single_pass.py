@@ -69,8 +69,12 @@ def _compare(u, s, v, ur, sr, vr, sb_full, k, tol):
     bound = metrics.gap_bound(sr, eps, s_next=sb_full[k] if k < len(sb_full) else None)
     d = np.sign(np.sum(u * ur, axis=0))
     d[d == 0] = 1
-    assert np.all(np.linalg.norm(u * d - ur, axis=0) <= bound + 1e-5)
-    assert np.all(np.linalg.norm(v * d - vr, axis=0) <= bound + 1e-5)
+    du = np.linalg.norm(u * d - ur, axis=0)
+    dv = np.linalg.norm(v * d - vr, axis=0)
+    print("  vectors: max du", du.max(), "max dv", dv.max(), "min bound", (bound + 1e-5).min(),
+          "worst ratio", max((du / (bound + 1e-5)).max(), (dv / (bound + 1e-5)).max()))
+    assert np.all(du <= bound + 1e-5)
+    assert np.all(dv <= bound + 1e-5)
     assert metrics.orthonormality(u) <= 1e-5 and metrics.orthonormality(v) <= 1e-5
 
 

@@ -307,6 +307,38 @@ def test_single_pass_exact_rank_and_consistency():
     assert np.allclose(b, qm.T @ a @ qt, atol=1e-12)
 
 
+def test_single_pass_truncated_bases_reduce_to_the_square_form_at_p0():
+    """With p = 0 the k leading left singular vectors span range(Y): same B up to the basis."""
+    m, n, k = 300, 200, 10
+    a, *_ = synth.lowrank(m, n, synth.spectrum_exp(n, 6.0), 13)
+    om = philox.gaussian(2, philox.STREAM_OMEGA, n, k)
+    ps = philox.gaussian(2, philox.STREAM_PSI, m, k)
+    u1, s1, v1, _ = single_pass.rsvd_single_pass(a, k, om, ps, truncate_bases=True)
+    u2, s2, v2, _ = single_pass.rsvd_single_pass(a, k, om, ps, truncate_bases=False)
+    assert np.max(np.abs(s1 - s2)) < 1e-10 * s2[0]
+    assert np.allclose(u1 @ np.diag(s1) @ v1.T, u2 @ np.diag(s2) @ v2.T, atol=1e-10 * s2[0])
+
+
+def test_single_pass_truncated_bases_on_a_noisy_flat_tail():
+    """The remark on single-pass error (Section 5.5): on a noisy, slowly decaying spectrum
+    the square system degrades the approximation; the overdetermined k x l system keeps it
+    within a small factor of the two-pass error."""
+    m, n, k, p = 4096, 512, 32, 8
+    sig = np.maximum(np.exp(-np.arange(n) / 10.0), 1e-6)
+    a, *_ = synth.lowrank(m, n, sig, 21)
+    a = a + 1e-4 * np.random.default_rng(3).standard_normal((m, n))
+    om = philox.gaussian(5, philox.STREAM_OMEGA, n, k + p)
+    ps = philox.gaussian(5, philox.STREAM_PSI, m, k + p)
+    e = {}
+    for t in (True, False):
+        u, s, v, _ = single_pass.rsvd_single_pass(a, k, om, ps, truncate_bases=t)
+        e[t] = metrics.fro_error(a, u, s, v)
+    u2, s2, v2, _ = rsvd64.rsvd(a, k, p, 0, om)
+    e_two = metrics.fro_error(a, u2, s2, v2)
+    assert e[True] < 0.5 * e[False]
+    assert e[True] < 10.0 * e_two
+
+
 # --------------------------------------------------------------------------
 # gradient of the reconstruction loss, Omega fixed
 # --------------------------------------------------------------------------
