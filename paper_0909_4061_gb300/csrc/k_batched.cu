@@ -291,45 +291,90 @@ __device__ __forceinline__ void chol32_warp(const float (*S)[LPB + 1], int l, fl
   for (int i = 0; i < LPB; ++i) Xs[i][r] = x[i];
 }
 
+// Rows are streamed in chunks of 64 (two float4 per thread, the next chunk prefetched into
+// registers while the current one is used).  Gram: the 256 threads form 4 row groups of 64,
+// each thread a 4 x 4 block of G over its group's 16 rows of a chunk (float4 loads), the
+// four groups summed at the end in a fixed order.  Apply: a warp per row, column = lane,
+// the row of Y read as float4 and the column of R^-1 held in registers.
+__device__ __forceinline__ void load_chunk(const float* __restrict__ src, int64_t rows, int64_t c0,
+                                           int tid, float4 (&v)[2]) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * kQRThreads;   // float4 index in the 64 x 32 chunk
+    const int rr = e >> 3;
+    v[u] = (c0 + rr < rows) ? reinterpret_cast<const float4*>(src + (c0 + rr) * LPB)[e & 7]
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 __global__ void __launch_bounds__(kQRThreads) batched_cholqr_kernel(
     const float* __restrict__ yin, float* __restrict__ qout, const int64_t* __restrict__ roff, int l,
     int rounds, float* __restrict__ rout, uint32_t* status) {
-  __shared__ float chunk[kChunk][LPB];
-  __shared__ float qch[kChunk][LPB];
+  __shared__ __align__(16) float buf[2 * kChunk * LPB];   // two row chunks, or the Gram partials
+  float (*chunk)[LPB] = reinterpret_cast<float (*)[LPB]>(buf);
+  float (*qch)[LPB] = reinterpret_cast<float (*)[LPB]>(buf + kChunk * LPB);
+  float (*Gp)[LPB * LPB] = reinterpret_cast<float (*)[LPB * LPB]>(buf);   // 4 row groups
   __shared__ float S[LPB][LPB + 1];
   __shared__ float Ls[LPB][LPB + 1];
   __shared__ float Xs[LPB][LPB + 1];
   __shared__ float Racc[LPB][LPB + 1];
   __shared__ float Rtmp[LPB][LPB + 1];
-  __shared__ float s_red[2][kQRThreads / 32];
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = roff[b], rows = roff[b + 1] - r0;
   const float* Y = yin + r0 * LPB;
   float* Q = qout + r0 * LPB;
-  const int gi = 4 * warp, gj = lane;   // Gram outputs (gi .. gi+3, gj)
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int grp = tid >> 6, gt = tid & 63;           // row group, thread in group
+  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;   // 4 x 4 block of G
+  float acc[4][4];
   for (int e = tid; e < LPB * LPB; e += kQRThreads) Racc[e / LPB][e % LPB] = (e / LPB == e % LPB) ? 1.0f : 0.0f;
 
-  // Gram of the input
-  for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
-    const int nr = (int)min((int64_t)kChunk, rows - c0);
-    for (int e = tid; e < kChunk * LPB; e += kQRThreads) {
-      const int rr = e / LPB, cc = e % LPB;
-      chunk[rr][cc] = rr < nr ? Y[(c0 + rr) * LPB + cc] : 0.0f;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
-      const float yj = chunk[rr][gj];
+  auto gram_chunk = [&](const float (*C)[LPB], int nr) {
+    for (int rr = grp; rr < nr; rr += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(&C[rr][bi]);
+      const float4 c = *reinterpret_cast<const float4*>(&C[rr][bj]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(chunk[rr][gi + q], yj, acc[q]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
     }
+  };
+  auto gram_finish = [&]() {   // callers have synchronised: the chunks are no longer read
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Gp[grp][(bi + i) * LPB + bj + j] = acc[i][j];
     __syncthreads();
+    for (int e = tid; e < LPB * LPB; e += kQRThreads)
+      S[e / LPB][e % LPB] = (Gp[0][e] + Gp[1][e]) + (Gp[2][e] + Gp[3][e]);
+  };
+  auto zero_acc = [&]() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  };
+
+  // Gram of the input
+  zero_acc();
+  {
+    float4 nxt[2];
+    load_chunk(Y, rows, 0, tid, nxt);
+    for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
+      const int nr = (int)min((int64_t)kChunk, rows - c0);
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) reinterpret_cast<float4*>(&chunk[0][0])[tid + u * kQRThreads] = nxt[u];
+      if (c0 + kChunk < rows) load_chunk(Y, rows, c0 + kChunk, tid, nxt);
+      __syncthreads();
+      gram_chunk(chunk, nr);
+    }
   }
+  __syncthreads();
+  gram_finish();
   const float* src = Y;
   for (int round = 0; round < rounds; ++round) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S[gi + q][gj] = acc[q];
     __syncthreads();
     // shift (first of three rounds) and pivot floor from the trace and largest diagonal
     if (warp == 0) {
@@ -358,39 +403,42 @@ __global__ void __launch_bounds__(kQRThreads) batched_cholqr_kernel(
     float xr[LPB];
 #pragma unroll
     for (int i = 0; i < LPB; ++i) xr[i] = Xs[lane][i];   // thread column j = lane
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = 0.0f;
+    zero_acc();
+    const bool more = round + 1 < rounds;
+    float4 nxt[2];
+    load_chunk(src, rows, 0, tid, nxt);
     for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
       const int nr = (int)min((int64_t)kChunk, rows - c0);
       __syncthreads();
-      for (int e = tid; e < kChunk * LPB; e += kQRThreads) {
-        const int rr = e / LPB, cc = e % LPB;
-        chunk[rr][cc] = rr < nr ? src[(c0 + rr) * LPB + cc] : 0.0f;
-      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) reinterpret_cast<float4*>(&chunk[0][0])[tid + u * kQRThreads] = nxt[u];
+      if (c0 + kChunk < rows) load_chunk(src, rows, c0 + kChunk, tid, nxt);
       __syncthreads();
       for (int rr = warp; rr < nr; rr += kQRThreads / 32) {
+        const float4* yr = reinterpret_cast<const float4*>(&chunk[rr][0]);
         float v0 = 0.0f, v1 = 0.0f;
 #pragma unroll
-        for (int i = 0; i < LPB; i += 2) {
-          v0 = fmaf(chunk[rr][i], xr[i], v0);
-          v1 = fmaf(chunk[rr][i + 1], xr[i + 1], v1);
+        for (int i4 = 0; i4 < LPB / 4; ++i4) {
+          const float4 y4 = yr[i4];
+          v0 = fmaf(y4.x, xr[4 * i4], v0);
+          v1 = fmaf(y4.y, xr[4 * i4 + 1], v1);
+          v0 = fmaf(y4.z, xr[4 * i4 + 2], v0);
+          v1 = fmaf(y4.w, xr[4 * i4 + 3], v1);
         }
         const float qv = v0 + v1;
         qch[rr][lane] = qv;
         Q[(c0 + rr) * LPB + lane] = qv;
       }
-      __syncthreads();
-      if (round + 1 < rounds) {
-        for (int rr = 0; rr < nr; ++rr) {
-          const float yj = qch[rr][gj];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = fmaf(qch[rr][gi + q], yj, acc[q]);
-        }
+      if (more) {
+        __syncthreads();
+        gram_chunk(qch, nr);
       }
     }
     __syncthreads();
+    if (more) gram_finish();
     src = Q;
   }
+  __syncthreads();
   float* R = rout + (size_t)b * LPB * LPB;
   for (int e = tid; e < LPB * LPB; e += kQRThreads) {
     const int i = e / LPB, jj = e % LPB;
@@ -398,21 +446,31 @@ __global__ void __launch_bounds__(kQRThreads) batched_cholqr_kernel(
   }
 }
 
-// basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K)
-__global__ void batched_to_bf16t_kernel(const float* __restrict__ q, const int64_t* __restrict__ roff,
-                                        int nb, __nv_bfloat16* __restrict__ xbf, int64_t ldx,
-                                        const int64_t* __restrict__ xoff, int split) {
-  const int64_t total = roff[nb] * LPB;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e % roff[nb];
-    const int c = (int)(e / roff[nb]);
-    const int b = find_matrix(roff, nb, r);
-    const float v = q[r * LPB + c];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const int64_t col = xoff[b] + (r - roff[b]);
-    xbf[(int64_t)c * ldx + col] = hi;
-    if (split) xbf[(int64_t)(LPB + c) * ldx + col] = __float2bfloat16_rn(v - __bfloat162float(hi));
+// basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
+// per matrix, a thread per row (row reads from L1, column writes coalesced across threads)
+__global__ void __launch_bounds__(256) batched_to_bf16t_kernel(const float* __restrict__ q,
+                                                               const int64_t* __restrict__ roff,
+                                                               __nv_bfloat16* __restrict__ xbf,
+                                                               int64_t ldx,
+                                                               const int64_t* __restrict__ xoff,
+                                                               int split) {
+  const int b = blockIdx.x;
+  const int64_t r0 = roff[b], rows = roff[b + 1] - r0;
+  __nv_bfloat16* xb = xbf + xoff[b];
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+    const float4* src = reinterpret_cast<const float4*>(q + (r0 + i) * LPB);
+#pragma unroll
+    for (int c4 = 0; c4 < LPB / 4; ++c4) {
+      const float4 v4 = src[c4];
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = 4 * c4 + t;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v[t]);
+        xb[(int64_t)c * ldx + i] = hi;
+        if (split) xb[(int64_t)(LPB + c) * ldx + i] = __float2bfloat16_rn(v[t] - __bfloat162float(hi));
+      }
+    }
   }
 }
 
@@ -515,27 +573,28 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
 
 // out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
 // per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
-// for c < valid, 0 for valid <= c < cols
-__global__ void batched_lift_kernel(const float* __restrict__ q, const int64_t* __restrict__ roff,
-                                    int nb, const float* __restrict__ small, int cols, int valid,
-                                    float* __restrict__ out, int ldo) {
-  const int64_t total = roff[nb] * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / cols;
-    const int c = (int)(e - r * cols);
-    const int b = find_matrix(roff, nb, r);
-    const float* sb = small + (size_t)b * LPB * LPB;
-    const float* qr = q + r * LPB;
+// for c < valid, 0 for valid <= c < cols; one CTA per matrix, a warp per row
+__global__ void __launch_bounds__(256) batched_lift_kernel(const float* __restrict__ q,
+                                                           const int64_t* __restrict__ roff,
+                                                           const float* __restrict__ small, int cols,
+                                                           int valid, float* __restrict__ out, int ldo) {
+  __shared__ float Ss[LPB][LPB + 1];
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
+    const int j = e / LPB, c = e % LPB;
+    Ss[j][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
+  }
+  __syncthreads();
+  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
+    const float qv = q[r * LPB + lane];
     float v0 = 0.0f, v1 = 0.0f;
-    if (c < valid) {
 #pragma unroll
-      for (int j = 0; j < LPB; j += 2) {
-        v0 = fmaf(qr[j], sb[j * LPB + c], v0);
-        v1 = fmaf(qr[j + 1], sb[(j + 1) * LPB + c], v1);
-      }
+    for (int j = 0; j < LPB; j += 2) {
+      v0 = fmaf(__shfl_sync(0xffffffffu, qv, j), Ss[j][lane], v0);
+      v1 = fmaf(__shfl_sync(0xffffffffu, qv, j + 1), Ss[j + 1][lane], v1);
     }
-    out[r * ldo + c] = v0 + v1;
+    if (lane < cols) out[r * ldo + lane] = v0 + v1;
   }
 }
 
@@ -597,7 +656,8 @@ cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* 
 cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb, int64_t total_rows,
                                     __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff, int split,
                                     cudaStream_t st) {
-  batched_to_bf16t_kernel<<<grid_for(total_rows * LPB), 256, 0, st>>>(q, roff, nb, xbf, ldx, xoff, split);
+  (void)total_rows;
+  batched_to_bf16t_kernel<<<nb, 256, 0, st>>>(q, roff, xbf, ldx, xoff, split);
   return cudaGetLastError();
 }
 
@@ -611,8 +671,9 @@ cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb,
 cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
                                 const float* small, int cols, int valid, float* out, int ldo,
                                 cudaStream_t st) {
-  batched_lift_kernel<<<grid_for(total_rows * cols), 256, 0, st>>>(q, roff, nb, small, cols, valid, out,
-                                                                     ldo);
+  (void)total_rows;
+  if (cols > LPB) return cudaErrorInvalidValue;
+  batched_lift_kernel<<<nb, 256, 0, st>>>(q, roff, small, cols, valid, out, ldo);
   return cudaGetLastError();
 }
 

@@ -26,42 +26,43 @@ namespace {
 
 constexpr int LPB = 32;
 
-__device__ __forceinline__ int find_mat(const int64_t* __restrict__ off, int nb, int64_t r) {
-  int lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= r) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-unsigned rows_grid(int64_t rows) {   // one warp per row, 8 warps per block
-  const int64_t b = cdiv(rows, 8);
-  return (unsigned)(b < 32 * kNumSMs ? (b < 1 ? 1 : b) : 32 * kNumSMs);
-}
-
-// one warp per row: lane c forms t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c (u_c = (Q Ut)[r][c]),
-// lane i then gQ[r][i] = sum_{c<k} t_c Ut[i][c]
-__global__ void bwd_gq_kernel(const float* __restrict__ P, const float* __restrict__ Q,
-                              const int64_t* __restrict__ roff, int nb, int64_t rows,
-                              const float* __restrict__ ut, const float* __restrict__ sig, int k,
-                              float* __restrict__ gq, float* __restrict__ ublk, int ldu) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = w0; r < rows; r += nw) {
-    const int b = find_mat(roff, nb, r);
-    const float* U = ut + (size_t)b * LPB * LPB;
+// one CTA per matrix (Ut, sigma in shared memory), one warp per row: lane c forms
+// t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u_c = (Q Ut)[r][c]; lane i then
+// gQ[r][i] = sum_{c<k} t_c Ut[i][c]
+__global__ void __launch_bounds__(256) bwd_gq_kernel(const float* __restrict__ P,
+                                                     const float* __restrict__ Q,
+                                                     const int64_t* __restrict__ roff,
+                                                     const float* __restrict__ ut,
+                                                     const float* __restrict__ sig, int k,
+                                                     float* __restrict__ gq, float* __restrict__ ublk,
+                                                     int ldu) {
+  __shared__ float Us[LPB][LPB + 1];
+  __shared__ float ss[LPB];
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) Us[e / LPB][e % LPB] = ut[(size_t)b * LPB * LPB + e];
+  if (threadIdx.x < LPB) ss[threadIdx.x] = threadIdx.x < k ? sig[(size_t)b * LPB + threadIdx.x] : 0.0f;
+  __syncthreads();
+  const float s = ss[lane];
+  const float c1 = 1.0f - 2.0f * s, c2 = 2.0f * s * s;
+  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
     const float qv = Q[r * LPB + lane];
-    float u = 0.0f;
+    float u0 = 0.0f, u1 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < LPB; ++j) u = fmaf(__shfl_sync(0xffffffffu, qv, j), U[j * LPB + lane], u);
-    const float s = sig[(size_t)b * LPB + lane];
-    const float t = lane < k ? fmaf(P[r * LPB + lane], 1.0f - 2.0f * s, 2.0f * s * s * u) : 0.0f;
-    ublk[r * ldu + lane] = lane < k ? u * (1.0f - 2.0f * s) : 0.0f;
-    float g = 0.0f;
-    for (int c = 0; c < k; ++c) g = fmaf(__shfl_sync(0xffffffffu, t, c), U[lane * LPB + c], g);
-    gq[r * LPB + lane] = g;
+    for (int j = 0; j < LPB; j += 2) {
+      u0 = fmaf(__shfl_sync(0xffffffffu, qv, j), Us[j][lane], u0);
+      u1 = fmaf(__shfl_sync(0xffffffffu, qv, j + 1), Us[j + 1][lane], u1);
+    }
+    const float u = u0 + u1;
+    const float t = lane < k ? fmaf(P[r * LPB + lane], c1, c2 * u) : 0.0f;
+    ublk[r * ldu + lane] = lane < k ? u * c1 : 0.0f;
+    float g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < LPB; c += 2) {   // t_c = 0 for c >= k
+      g0 = fmaf(__shfl_sync(0xffffffffu, t, c), Us[lane][c], g0);
+      g1 = fmaf(__shfl_sync(0xffffffffu, t, c + 1), Us[lane][c + 1], g1);
+    }
+    gq[r * LPB + lane] = g0 + g1;
   }
 }
 
@@ -134,27 +135,39 @@ __global__ void __launch_bounds__(kSmallThreads) bwd_qr_small_kernel(
   }
 }
 
-// one warp per row: lane j: w_j = gQ[r][j] + sum_t Q[r][t] N[t][j]; lane i: gY[r][i] =
-// sum_j w_j Rinv[i][j]  (gY = w R^-T)
-__global__ void bwd_qr_apply_kernel(const float* __restrict__ Q, const float* __restrict__ gQ,
-                                    const int64_t* __restrict__ roff, int nb, int64_t rows,
-                                    const float* __restrict__ N, const float* __restrict__ Rinv,
-                                    float* __restrict__ gY) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = w0; r < rows; r += nw) {
-    const int b = find_mat(roff, nb, r);
-    const float* Nb = N + (size_t)b * LPB * LPB;
-    const float* Rb = Rinv + (size_t)b * LPB * LPB;
+// one CTA per matrix (N, R^-1 in shared memory), one warp per row: lane j:
+// w_j = gQ[r][j] + sum_t Q[r][t] N[t][j]; lane i: gY[r][i] = sum_j w_j Rinv[i][j] (gY = w R^-T)
+__global__ void __launch_bounds__(256) bwd_qr_apply_kernel(const float* __restrict__ Q,
+                                                           const float* __restrict__ gQ,
+                                                           const int64_t* __restrict__ roff,
+                                                           const float* __restrict__ N,
+                                                           const float* __restrict__ Rinv,
+                                                           float* __restrict__ gY) {
+  __shared__ float Ns[LPB][LPB + 1];
+  __shared__ float Rs[LPB][LPB + 1];
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
+    Ns[e / LPB][e % LPB] = N[(size_t)b * LPB * LPB + e];
+    Rs[e / LPB][e % LPB] = Rinv[(size_t)b * LPB * LPB + e];
+  }
+  __syncthreads();
+  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
     const float qv = Q[r * LPB + lane];
-    float w = gQ[r * LPB + lane];
+    float w0 = gQ[r * LPB + lane], w1 = 0.0f;
 #pragma unroll
-    for (int t = 0; t < LPB; ++t) w = fmaf(__shfl_sync(0xffffffffu, qv, t), Nb[t * LPB + lane], w);
-    float g = 0.0f;
+    for (int t = 0; t < LPB; t += 2) {
+      w0 = fmaf(__shfl_sync(0xffffffffu, qv, t), Ns[t][lane], w0);
+      w1 = fmaf(__shfl_sync(0xffffffffu, qv, t + 1), Ns[t + 1][lane], w1);
+    }
+    const float w = w0 + w1;
+    float g0 = 0.0f, g1 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < LPB; ++j) g = fmaf(__shfl_sync(0xffffffffu, w, j), Rb[lane * LPB + j], g);
-    gY[r * LPB + lane] = g;
+    for (int j = 0; j < LPB; j += 2) {
+      g0 = fmaf(__shfl_sync(0xffffffffu, w, j), Rs[lane][j], g0);
+      g1 = fmaf(__shfl_sync(0xffffffffu, w, j + 1), Rs[lane][j + 1], g1);
+    }
+    gY[r * LPB + lane] = g0 + g1;
   }
 }
 
@@ -228,8 +241,8 @@ __global__ void __launch_bounds__(256) bwd_final_kernel(
 cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
                           const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st) {
-  bwd_gq_kernel<<<rows_grid(total_rows), 256, 0, st>>>(P, Q, roff, nb, total_rows, ut, sig, k, gq, ublk,
-                                                        ldu);
+  (void)total_rows;
+  bwd_gq_kernel<<<nb, 256, 0, st>>>(P, Q, roff, ut, sig, k, gq, ublk, ldu);
   return cudaGetLastError();
 }
 
@@ -242,7 +255,9 @@ cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* 
 cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
                                 int64_t total_rows, const float* N, const float* Rinv, float* gY,
                                 cudaStream_t st) {
-  bwd_qr_apply_kernel<<<rows_grid(total_rows), 256, 0, st>>>(Q, gQ, roff, nb, total_rows, N, Rinv, gY);
+  (void)nb;
+  (void)total_rows;
+  bwd_qr_apply_kernel<<<nb, 256, 0, st>>>(Q, gQ, roff, N, Rinv, gY);
   return cudaGetLastError();
 }
 

@@ -294,8 +294,9 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
   }
 }
 
-// Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA of 512 threads, both
-// held in shared memory as full squares, for LP = 16 NB <= 160.  The row stride
+// Blocked Cholesky G + sI = L L^T and X = L^-1 in one CTA of 512 threads, for
+// LP = 16 NB <= 256: up to LP = 160 both held in shared memory as full squares; above,
+// L in a padded row-packed form (143 KB at LP = 256) and X in global memory (L2).  The row stride
 // LP + 4 keeps rows 16-byte aligned (float4 loads along a row) with an odd number of
 // float4 per row (a column of float4 loads hits distinct banks).  The factor works
 // on the padded size LP with identity rows and columns beyond l, so every block is
@@ -311,6 +312,12 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 // to l x l.  The block loops stay rolled: unrolled, the code outgrows the
 // instruction cache.
 constexpr int CB = 16;
+
+// Offset of row i in the padded row-packed form of a lower-triangular L (16-row block
+// rows; row i holds 16 (i / 16 + 1) columns plus 4 floats of skew).
+__host__ __device__ constexpr int pk_off(int i) {
+  return 128 * (i / CB) * (i / CB + 1) + 64 * (i / CB) + (i % CB) * (16 * (i / CB) + 20);
+}
 
 __device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc) {
   acc = fmaf(a.x, b.x, acc);
@@ -330,14 +337,29 @@ __device__ __forceinline__ float4 axpy4(float s, const float4 x, float4 y) {
 template <int NB>
 __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     const float* __restrict__ g, int l, int shifted, float* __restrict__ r_out,
-    float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status) {
+    float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status,
+    float* __restrict__ xg) {
   constexpr int LP = CB * NB;
   constexpr int LD = LP + 4;
+  constexpr bool PACKED = NB > 10;       // L in padded row-packed form, L^-1 in global memory
   constexpr int NW = 16;                 // warps
   constexpr int NCOL = (LP + 31) / 32;   // columns per lane in row-by-warp loops
+  constexpr int RCH = PACKED ? 4 : NB;   // rows per warp loaded together
   extern __shared__ __align__(16) float sm[];
-  float* A = sm;               // lower: L (above the diagonal: scratch)
-  float* X = sm + LP * LD;     // lower: L^-1 (above the diagonal: zero)
+  // Square form: A (L, scratch above the diagonal) and X = L^-1 as LP x LD squares; the
+  // block-row products S of the inverse live in A's scratch upper triangle.
+  // Packed form: row i of L holds columns 0 .. 16 (i / 16 + 1) - 1 (the diagonal block's
+  // scratch included) plus 4 floats of skew, so float4 rows stay aligned and consecutive
+  // rows fall in different banks; X lives in global memory (xg, LP x LP) and S in a
+  // separate 16 x (LP + 4) block.
+  float* A = sm;
+  float* X = PACKED ? xg : sm + LP * LD;
+  float* Sb = sm + pk_off(LP);   // packed form only
+  auto arow = [&](int i) -> float* {
+    return PACKED ? A + pk_off(i) : A + i * LD;
+  };
+  auto xrow = [&](int i) -> float* { return PACKED ? X + i * LP : X + i * LD; };
+  auto alen = [&](int i) -> int { return PACKED ? CB * (i / CB + 1) : LP; };
   __shared__ float s_red[2][NW];
   __shared__ float s_shift, s_floor;
   const int tid = threadIdx.x;
@@ -346,20 +368,21 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   // load the lower triangle of G (identity beyond l), all loads in flight together
   float tr = 0.0f, mx = 0.0f;
   bool bad = false;
-  {
-    float v[NB][NCOL];
+#pragma unroll 1
+  for (int r0 = 0; r0 < NB; r0 += RCH) {
+    float v[RCH][NCOL];
 #pragma unroll
-    for (int r = 0; r < NB; ++r)
+    for (int r = 0; r < RCH; ++r)
 #pragma unroll
       for (int c = 0; c < NCOL; ++c) {
-        const int i = warp + NW * r, j = lane + 32 * c;
+        const int i = warp + NW * (r0 + r), j = lane + 32 * c;
         v[r][c] = (j <= i && i < l) ? g[i * LP + j] : 0.0f;   // lower triangle only
       }
 #pragma unroll
-    for (int r = 0; r < NB; ++r)
+    for (int r = 0; r < RCH; ++r)
 #pragma unroll
       for (int c = 0; c < NCOL; ++c) {
-        const int i = warp + NW * r, j = lane + 32 * c;
+        const int i = warp + NW * (r0 + r), j = lane + 32 * c;
         if (j < LP) {
           float w = v[r][c];
           if (i == j) {
@@ -371,8 +394,8 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
               w = 1.0f;
             }
           }
-          A[i * LD + j] = (j <= i) ? w : 0.0f;
-          X[i * LD + j] = 0.0f;
+          if (j < alen(i)) arow(i)[j] = (j <= i) ? w : 0.0f;
+          xrow(i)[j] = 0.0f;
         }
       }
   }
@@ -390,7 +413,7 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   }
   __syncthreads();
   const float pfloor = s_floor;
-  if (tid < l) A[tid * LD + tid] += s_shift;
+  if (tid < l) arow(tid)[tid] += s_shift;
   __syncthreads();
 
 #pragma unroll 1
@@ -401,7 +424,7 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
       const int r = lane & 15;
       float a[CB], rpv[CB];
       {
-        const float4* src = reinterpret_cast<const float4*>(A + (J + r) * LD + J);
+        const float4* src = reinterpret_cast<const float4*>(arow(J + r) + J);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float4 t = src[q];
@@ -438,11 +461,11 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
         x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
       }
       if (lane < CB) {
-        float4* dst = reinterpret_cast<float4*>(A + (J + r) * LD + J);
+        float4* dst = reinterpret_cast<float4*>(arow(J + r) + J);
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
 #pragma unroll
-        for (int i = 0; i < CB; ++i) X[(J + i) * LD + J + r] = x[i];
+        for (int i = 0; i < CB; ++i) xrow(J + i)[J + r] = x[i];
       }
     }
     __syncthreads();
@@ -451,10 +474,10 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
       // (2) panel, in place: L_iJ(c) = sum_k A_iJ(k) X_JJ(c, k); a half-warp per row
       {
         const int c = tid & 15;
-        const float4* xc = reinterpret_cast<const float4*>(X + (J + c) * LD + J);
+        const float4* xc = reinterpret_cast<const float4*>(xrow(J + c) + J);
         const float4 x0 = xc[0], x1 = xc[1], x2 = xc[2], x3 = xc[3];
         for (int i = s0 + (tid >> 4); i < LP; i += 32) {
-          float* ai = A + i * LD + J;
+          float* ai = arow(i) + J;
           const float4* a4 = reinterpret_cast<const float4*>(ai);
           const float v = dot4(a4[0], x0, dot4(a4[2], x2, 0.0f)) + dot4(a4[1], x1, dot4(a4[3], x3, 0.0f));
           __syncwarp();
@@ -465,17 +488,17 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
       // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ; rows i0, i0 + 1 per warp, k per lane
       for (int ip = warp; 2 * ip < LP - s0; ip += NW) {
         const int i0 = s0 + 2 * ip, i1 = i0 + 1;
-        const float4* p0 = reinterpret_cast<const float4*>(A + i0 * LD + J);
-        const float4* p1 = reinterpret_cast<const float4*>(A + i1 * LD + J);
+        const float4* p0 = reinterpret_cast<const float4*>(arow(i0) + J);
+        const float4* p1 = reinterpret_cast<const float4*>(arow(i1) + J);
         const float4 u0 = p0[0], u1 = p0[1], u2 = p0[2], u3 = p0[3];
         const float4 w0 = p1[0], w1 = p1[1], w2 = p1[2], w3 = p1[3];
         for (int k = s0 + lane; k <= i1; k += 32) {
-          const float4* pk = reinterpret_cast<const float4*>(A + k * LD + J);
+          const float4* pk = reinterpret_cast<const float4*>(arow(k) + J);
           const float4 k0 = pk[0], k1 = pk[1], k2 = pk[2], k3 = pk[3];
           const float a0 = dot4(u0, k0, dot4(u1, k1, 0.0f)) + dot4(u2, k2, dot4(u3, k3, 0.0f));
           const float a1 = dot4(w0, k0, dot4(w1, k1, 0.0f)) + dot4(w2, k2, dot4(w3, k3, 0.0f));
-          if (k <= i0) A[i0 * LD + k] -= a0;
-          A[i1 * LD + k] -= a1;
+          if (k <= i0) arow(i0)[k] -= a0;
+          arow(i1)[k] -= a1;
         }
       }
       __syncthreads();
@@ -490,29 +513,31 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     const int I = ib * CB;
     for (int t = tid; t < 2 * I; t += 512) {   // tiles of rows 2rp, 2rp+1 x columns 4cq..4cq+3
       const int rp = t & 7, c0 = 4 * (t >> 3);
-      const float* la = A + (I + 2 * rp) * LD;
-      const float* lb = la + LD;
+      const float* la = arow(I + 2 * rp);
+      const float* lb = arow(I + 2 * rp + 1);
       float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
       for (int k = c0; k < I; ++k) {   // X(k, c0 + q) = 0 for k < c0 + q
-        const float4 xk = *reinterpret_cast<const float4*>(X + k * LD + c0);
+        const float4 xk = *reinterpret_cast<const float4*>(xrow(k) + c0);
         s0 = axpy4(la[k], xk, s0);
         s1 = axpy4(lb[k], xk, s1);
       }
-      float* d0 = A + c0 * LD + I + 2 * rp;
+      // S(t, c) for t = 2rp, 2rp + 1 and c = c0 .. c0 + 3, in srow(c)[t]
+      float* d0 = PACKED ? Sb + c0 * 20 + 2 * rp : A + c0 * LD + I + 2 * rp;
+      constexpr int SLD = PACKED ? 20 : LD;
       d0[0] = s0.x; d0[1] = s1.x;
-      d0[LD] = s0.y; d0[LD + 1] = s1.y;
-      d0[2 * LD] = s0.z; d0[2 * LD + 1] = s1.z;
-      d0[3 * LD] = s0.w; d0[3 * LD + 1] = s1.w;
+      d0[SLD] = s0.y; d0[SLD + 1] = s1.y;
+      d0[2 * SLD] = s0.z; d0[2 * SLD + 1] = s1.z;
+      d0[3 * SLD] = s0.w; d0[3 * SLD + 1] = s1.w;
     }
     __syncthreads();
     {
       const int r = tid & 15;
-      const float4* xr = reinterpret_cast<const float4*>(X + (I + r) * LD + I);
+      const float4* xr = reinterpret_cast<const float4*>(xrow(I + r) + I);
       const float4 x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];   // X_II row r (zero beyond r)
       for (int c = tid >> 4; c < I; c += 32) {
-        const float4* sc = reinterpret_cast<const float4*>(A + c * LD + I);
+        const float4* sc = reinterpret_cast<const float4*>(PACKED ? Sb + c * 20 : A + c * LD + I);
         const float v = dot4(x0, sc[0], dot4(x2, sc[2], 0.0f)) + dot4(x1, sc[1], dot4(x3, sc[3], 0.0f));
-        X[(I + r) * LD + c] = -v;
+        xrow(I + r)[c] = -v;
       }
     }
     __syncthreads();
@@ -527,8 +552,8 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
       const int b = lane + 32 * c;
       if (b < LP) {
         const bool up = (a < l && b < l && b >= a);
-        r_out[a * LP + b] = up ? A[b * LD + a] : 0.0f;
-        rinv[a * LP + b] = up ? X[b * LD + a] : 0.0f;
+        r_out[a * LP + b] = up ? arow(b)[a] : 0.0f;
+        rinv[a * LP + b] = up ? xrow(b)[a] : 0.0f;
       }
     }
   }
@@ -540,7 +565,7 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
           const int b = lane + 32 * c;
-          if (b < LP) racc[a * LP + b] = (a < l && b < l && b >= a) ? A[b * LD + a] : 0.0f;
+          if (b < LP) racc[a * LP + b] = (a < l && b < l && b >= a) ? arow(b)[a] : 0.0f;
         }
       }
       return;
@@ -548,22 +573,22 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     __syncthreads();
     // stage the old racc (upper, l x l) in the free X space, then racc <- R racc in
     // 1 x 4 strips: P(a, b0..b0+3) = sum_{a<=c<=b0+3} R(a, c) Ro(c, b0..b0+3)
-    float* Ro = X;
-    {
-      float v[NB][NCOL];
+#pragma unroll 1
+    for (int r0 = 0; r0 < NB; r0 += RCH) {
+      float v[RCH][NCOL];
 #pragma unroll
-      for (int r = 0; r < NB; ++r)
+      for (int r = 0; r < RCH; ++r)
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
-          const int i = warp + NW * r, j = lane + 32 * c;
+          const int i = warp + NW * (r0 + r), j = lane + 32 * c;
           v[r][c] = (j < LP) ? racc[i * LP + j] : 0.0f;
         }
 #pragma unroll
-      for (int r = 0; r < NB; ++r)
+      for (int r = 0; r < RCH; ++r)
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
-          const int i = warp + NW * r, j = lane + 32 * c;
-          if (j < LP) Ro[i * LD + j] = v[r][c];
+          const int i = warp + NW * (r0 + r), j = lane + 32 * c;
+          if (j < LP) xrow(i)[j] = v[r][c];   // the old racc, staged where X was
         }
     }
     __syncthreads();
@@ -574,7 +599,7 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
       if (a < l && b0 + 3 >= a) {
         const int cend = min(b0 + 3, l - 1);
         for (int c = a; c <= cend; ++c)
-          acc = axpy4(A[c * LD + a], *reinterpret_cast<const float4*>(Ro + c * LD + b0), acc);
+          acc = axpy4(arow(c)[a], *reinterpret_cast<const float4*>(xrow(c) + b0), acc);
       }
       float4 o;
       o.x = (a < l && b0 < l && b0 >= a) ? acc.x : 0.0f;
@@ -656,7 +681,10 @@ __global__ void gather_kernel(const float* __restrict__ src, int splits, int64_t
 // Shared-memory limits of the one-CTA factorisation kernels, for every size they accept;
 // set once per device (at plan creation) so no launch needs a host-side attribute call.
 template <int NB>
-size_t chol_smem() { return (size_t)2 * (CB * NB) * (CB * NB + 4) * sizeof(float); }
+size_t chol_smem() {
+  return NB > 10 ? (size_t)(pk_off(CB * NB) + 20 * CB * NB) * sizeof(float)
+                 : (size_t)2 * (CB * NB) * (CB * NB + 4) * sizeof(float);
+}
 
 template <int NB>
 cudaError_t prep_chol() {
@@ -670,7 +698,10 @@ cudaError_t prepare_orth() {
       (e = prep_chol<3>()) != cudaSuccess || (e = prep_chol<4>()) != cudaSuccess ||
       (e = prep_chol<5>()) != cudaSuccess || (e = prep_chol<6>()) != cudaSuccess ||
       (e = prep_chol<7>()) != cudaSuccess || (e = prep_chol<8>()) != cudaSuccess ||
-      (e = prep_chol<9>()) != cudaSuccess || (e = prep_chol<10>()) != cudaSuccess)
+      (e = prep_chol<9>()) != cudaSuccess || (e = prep_chol<10>()) != cudaSuccess ||
+      (e = prep_chol<11>()) != cudaSuccess || (e = prep_chol<12>()) != cudaSuccess ||
+      (e = prep_chol<13>()) != cudaSuccess || (e = prep_chol<14>()) != cudaSuccess ||
+      (e = prep_chol<15>()) != cudaSuccess || (e = prep_chol<16>()) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(((size_t)kMaxL * (kMaxL + 1) / 2 + kMaxL + 4 + kMaxL) *
@@ -702,15 +733,18 @@ cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, c
 cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,
                             float* rinv, float* racc, int racc_init, uint32_t* status,
                             cudaStream_t st) {
-  if (lp <= 160 && lp % CB == 0) {
+  if (lp <= 256 && lp % CB == 0 && lbuf) {
 #define RSVD_CHOL_CASE(NB)                                                                  \
   case NB:                                                                                 \
     cholesky_blocked_kernel<NB><<<1, 512, chol_smem<NB>(), st>>>(g, l, shifted, r_out, rinv, \
-                                                                 racc, racc_init, status);  \
+                                                                 racc, racc_init, status,  \
+                                                                 lbuf);                    \
     return cudaGetLastError();
     switch (lp / CB) {
       RSVD_CHOL_CASE(1) RSVD_CHOL_CASE(2) RSVD_CHOL_CASE(3) RSVD_CHOL_CASE(4) RSVD_CHOL_CASE(5)
       RSVD_CHOL_CASE(6) RSVD_CHOL_CASE(7) RSVD_CHOL_CASE(8) RSVD_CHOL_CASE(9) RSVD_CHOL_CASE(10)
+      RSVD_CHOL_CASE(11) RSVD_CHOL_CASE(12) RSVD_CHOL_CASE(13) RSVD_CHOL_CASE(14)
+      RSVD_CHOL_CASE(15) RSVD_CHOL_CASE(16)
       default: break;
     }
 #undef RSVD_CHOL_CASE

@@ -116,7 +116,8 @@ def _orth(pkg, y, l, rows, rounds=3):
         return _np(Y), _np(R), st
 
 
-@pytest.mark.parametrize("rows,l,cond", [(700, 24, 1e2), (1500, 64, 1e4), (300, 110, 1e3), (5000, 16, 1e5)])
+@pytest.mark.parametrize("rows,l,cond", [(700, 24, 1e2), (1500, 64, 1e4), (300, 110, 1e3), (5000, 16, 1e5),
+                                         (2000, 176, 1e3), (3000, 250, 1e4), (1024, 256, 1e2)])
 def test_orthonormalize_matches_householder(rsvd_lib, rows, l, cond):
     rng = np.random.default_rng(rows)
     y = (synth.haar(rng, rows, l) * np.logspace(0, -np.log10(cond), l)) @ synth.haar(rng, l, l).T
@@ -131,9 +132,9 @@ def test_orthonormalize_matches_householder(rsvd_lib, rows, l, cond):
     assert np.max(np.abs(q @ r - y)) <= 1e-5 * np.abs(y).max()
 
 
-def test_orthonormalize_rank_deficient(rsvd_lib):
+@pytest.mark.parametrize("rows,l,r", [(800, 16, 5), (1500, 240, 100)])
+def test_orthonormalize_rank_deficient(rsvd_lib, rows, l, r):
     rng = np.random.default_rng(1)
-    rows, l, r = 800, 16, 5
     y = (synth.haar(rng, rows, r) @ rng.standard_normal((r, l))).astype(np.float32)
     q, _, st = _orth(rsvd_lib, y, l, rows)
     assert st == rsvd_lib.RSVD_OK and np.all(np.isfinite(q))
