@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      int64_t M, int kt, int64_t total, int n_total, int fold, int lo_off, int stages,
                      float* __restrict__ slots, uint32_t* __restrict__ flags, uint32_t* status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_full[16], bar_empty[16], bar_acc_full, bar_acc_empty;
+  __shared__ uint64_t bar_full[16], bar_empty[16], bar_acc_full[2], bar_acc_empty[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
 
@@ -87,16 +87,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t a_bytes = BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
   const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
   const uint32_t stage_bytes = a_bytes + x_bytes;
+  // two accumulators when they fit tensor memory (512 columns): the MMAs of the next row
+  // tile then run while the epilogue drains the previous one
+  const uint32_t acc_cols = (uint32_t)((n_total + 31) & ~31);
+  const int nacc = (2 * acc_cols <= 512) ? 2 : 1;
   uint32_t tmem_cols = 32;
-  while ((int)tmem_cols < n_total) tmem_cols <<= 1;
+  while (tmem_cols < acc_cols * nacc) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&bar_full[s], 1);
       mbar_init(&bar_empty[s], 1);
     }
-    mbar_init(&bar_acc_full, 1);
-    mbar_init(&bar_acc_empty, 4);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&bar_acc_full[a], 1);
+      mbar_init(&bar_acc_empty[a], 4);
+    }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
@@ -161,7 +167,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t it = it0; it < it1 && ok; ++seg) {
         const int t = (int)(it / kt);
         const int64_t seg_end = min(it1, (int64_t)(t + 1) * kt);
-        if (!mbar_wait(&bar_acc_empty, ((uint32_t)seg & 1u) ^ 1u, abort_flag, status)) break;
+        const int ab = seg % nacc;
+        const uint32_t acc = tmem + (uint32_t)ab * acc_cols;
+        if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(seg / nacc) & 1u) ^ 1u, abort_flag, status)) break;
         tc_fence_after();
         for (; it < seg_end; ++it, ++i) {
           const int s = (int)(i % stages);
@@ -181,16 +189,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c * 256 < n_total; ++c) {
               const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
               const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
-              mma_bf16(tmem + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
+              mma_bf16(acc + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
               if (HILO) {
                 const uint64_t adesc_lo = smem_desc(sa + 16384 + j * 2048, 8192, 1024);
-                mma_bf16(tmem + c * 256, adesc_lo, bdesc, idesc, 1u);
+                mma_bf16(acc + c * 256, adesc_lo, bdesc, idesc, 1u);
               }
             }
           }
           mma_commit(&bar_empty[s]);
         }
-        if (ok) mma_commit(&bar_acc_full);
+        if (ok) mma_commit(&bar_acc_full[ab]);
       }
     }
   } else {
@@ -205,8 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t seg_end = min(it1, tile_e);
       const int c_first = rg.cta_of(tile_b), c_last = rg.cta_of(tile_e - 1);
       const bool ok = __all_sync(0xffffffffu,
-                                 mbar_wait(&bar_acc_full, (uint32_t)seg & 1u, abort_flag, status));
+                                 mbar_wait(&bar_acc_full[seg % nacc], (uint32_t)(seg / nacc) & 1u,
+                                           abort_flag, status));
       tc_fence_after();
+      const uint32_t tb = tbase + (uint32_t)(seg % nacc) * acc_cols;
       const int64_t grow = (int64_t)t * BM + row;
       const bool valid_row = grow < M;
       const bool direct = (c_first == c_last);
@@ -228,10 +238,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c0 = 0; c0 < lp; c0 += 32) {
         const int ncol = min(32, lp - c0);  // lp is a multiple of 16: 32 or 16
         float v[32];
-        tmem_ld_cols(tbase + c0, ncol, v);
+        tmem_ld_cols(tb + c0, ncol, v);
         if (fold) {
           float w2[32];
-          tmem_ld_cols(tbase + lo_off + c0, ncol, w2);
+          tmem_ld_cols(tb + lo_off + c0, ncol, w2);
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] += w2[q];
         }
@@ -239,21 +249,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (direct || finisher) {
           if (finisher) {
             for (int c = c_first + 1; c <= c_last; ++c) {
-              const float* src = slots + ((size_t)c * BM + row) * lp + c0;
-              for (int q = 0; q < ncol; ++q) v[q] += src[q];
+              const float4* src = reinterpret_cast<const float4*>(slots + ((size_t)c * BM + row) * lp + c0);
+#pragma unroll
+              for (int q = 0; q < 32; q += 4) {
+                if (q < ncol) {
+                  const float4 w4 = src[q >> 2];
+                  v[q] += w4.x; v[q + 1] += w4.y; v[q + 2] += w4.z; v[q + 3] += w4.w;
+                }
+              }
             }
           }
           float* dst = y + grow * lp + c0;
-          if (ncol == 32) {
 #pragma unroll
-            for (int q = 0; q < 32; q += 4)
+          for (int q = 0; q < 32; q += 4)   // ncol is 32 or 16
+            if (q < ncol)
               *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-          } else {
-            for (int q = 0; q < ncol; ++q) dst[q] = v[q];
-          }
         } else {
-          float* dst = slots + ((size_t)cta * BM + row) * lp + c0;
-          for (int q = 0; q < ncol; ++q) dst[q] = v[q];
+          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)cta * BM + row) * lp + c0);
+#pragma unroll
+          for (int q = 0; q < 32; q += 4)
+            if (q < ncol) dst[q >> 2] = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
         }
       }
       tc_fence_before();
@@ -268,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int c = c_first + 1; c <= c_last; ++c) flags[c] = 0u;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_acc_empty);
+      if (lane == 0) mbar_arrive(&bar_acc_empty[seg % nacc]);
       it = seg_end;
       if (!ok) break;
     }
