@@ -220,20 +220,42 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
 // Cholesky-QR rounds on the (summed) partial slabs; the basis ends in `dst`
 // (rows x lp).  With `racc`, the triangular factors are multiplied into it.
 rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t stride, int64_t rows,
-                        float* dst, float* racc) {
-  const int rounds = P->opt.orth_rounds;
+                        float* dst, float* racc, bool final_basis = true) {
+  // A basis that only feeds the next power-iteration pass needs to span the sample, not
+  // to be orthonormal to working precision: the shifted round and one plain round leave
+  // ||Q^T Q - I|| ~ u kappa(Q_1)^2 with kappa(Q_1) modest after the shift, and the next
+  // orthonormalisation starts from the product anyway.  Final bases get every round.
+  const int rounds = final_basis ? P->opt.orth_rounds : std::min(P->opt.orth_rounds, 2);
   const int lp = P->lp;
   const int nblk = gram_blocks(rows);
   Step sp(P, RSVD_STEP_ORTH);
-  sp.launched(4 * rounds);
+  sp.launched(lp <= 128 ? 3 * rounds + 1 : 4 * rounds);
   const float* cur = src;
   int cur_splits = splits;
+  if (lp <= 128) {
+    // Gram of the sample, then per round: factor, and Q = Y R^-1 fused with the next Gram
+    float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
+    TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
+    if (cur_splits > 1) cur = P->tmp1;
+    TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
+    for (int r = 0; r < rounds; ++r) {
+      const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
+      TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+                          r == 0 ? 1 : 0, P->status, P->st));
+      const bool last = (r == rounds - 1);
+      float* next = last ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
+      TRY(launch_apply_gram(cur, next, rows, lp, P->rinv(), P->gpart, nblk, last ? 0 : 1, P->st));
+      if (!last) TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
+      cur = next;
+    }
+    return RSVD_OK;
+  }
   for (int r = 0; r < rounds; ++r) {
     float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
     TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
     if (cur_splits > 1) cur = P->tmp1;
     TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
-    const int shifted = (rounds >= 3 && r == 0) ? 1 : 0;
+    const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
     TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
                         r == 0 ? 1 : 0, P->status, P->st));
     float* next = (r == rounds - 1) ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
@@ -262,14 +284,14 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   int s;
   int64_t stride;
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
-  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr, P->q == 0));
   for (int j = 1; j <= P->q; ++j) {
     if (tc) TRYS(step_convert(P, P->qbuf, P->m, 0));
     TRYS(step_pass(P, A, 1, P->qbuf, false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr));
+    TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr, false));
     if (tc) TRYS(step_convert(P, P->qtbuf, P->n, 0));
     TRYS(step_pass(P, A, 0, P->qtbuf, false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr));
+    TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr, j == P->q));
   }
   return RSVD_OK;
 }

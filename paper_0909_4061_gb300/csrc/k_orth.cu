@@ -116,6 +116,111 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* __restri
 constexpr int kRedSplit = 16;
 constexpr int kRedBatch = 24;
 
+// One Cholesky-QR step fused with the Gram matrix of the next (lp <= 128): the rows of a
+// block of Y (64 at a time) go through shared memory, Q = Y R^-1 is written out (a 16 x 16
+// thread grid of 4 x 8 output tiles, R^-1 held in shared memory) and, unless this is the
+// last round, the block's Q rows accumulate the Gram partial Q^T Q (8 x 8 tiles) that the
+// reduce kernel sums for the next factorisation.  Y is then read once per round.
+constexpr int AG_ROWS = 64;
+
+size_t apply_gram_smem(int lp) { return (size_t)(lp + AG_ROWS) * (lp + 4) * sizeof(float); }
+
+__global__ void __launch_bounds__(256, 2) apply_gram_kernel(const float* __restrict__ y,
+                                                         float* __restrict__ q, int64_t rows, int lp,
+                                                         const float* __restrict__ rinv,
+                                                         float* __restrict__ gpart,
+                                                         int64_t rows_per_blk, int do_gram) {
+  extern __shared__ __align__(16) float sm[];
+  const int ldp = lp + 4;
+  float* Rs = sm;                // lp x ldp
+  float* Ys = sm + lp * ldp;     // AG_ROWS x ldp: the Y rows, then the Q rows
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int lp4 = lp / 4;
+  for (int e = tid; e < lp * lp4; e += 256) {
+    const int r = e / lp4, c4 = e - r * lp4;
+    *reinterpret_cast<float4*>(Rs + r * ldp + 4 * c4) = *reinterpret_cast<const float4*>(rinv + r * lp + 4 * c4);
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
+  const int ib = ty * 8, jb = tx * 8;          // Gram tile
+  const int ar = ty * 4, ac = tx * 8;          // apply tile: rows ar..ar+3, columns ac..ac+7
+  const bool cols_in = ac < lp;
+  float g[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) g[a][b] = 0.0f;
+  for (int64_t rb = r0; rb < r1; rb += AG_ROWS) {
+    const int nr = (int)min((int64_t)AG_ROWS, r1 - rb);
+    __syncthreads();
+    for (int e = tid; e < AG_ROWS * lp4; e += 256) {
+      const int rr = e / lp4, c4 = e - rr * lp4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rr < nr) v = *reinterpret_cast<const float4*>(y + (rb + rr) * lp + 4 * c4);
+      *reinterpret_cast<float4*>(Ys + rr * ldp + 4 * c4) = v;
+    }
+    __syncthreads();
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+    if (cols_in) {
+      for (int i = 0; i < lp; ++i) {
+        const float4 rv0 = *reinterpret_cast<const float4*>(Rs + i * ldp + ac);
+        const float4 rv1 = *reinterpret_cast<const float4*>(Rs + i * ldp + ac + 4);
+        const float rv[8] = {rv0.x, rv0.y, rv0.z, rv0.w, rv1.x, rv1.y, rv1.z, rv1.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float yv = Ys[(ar + a) * ldp + i];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(yv, rv[b], acc[a][b]);
+        }
+      }
+    }
+    __syncthreads();   // every thread has read its Y rows before they become Q rows
+    if (cols_in) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int row = ar + a;
+        const float4 w0 = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        const float4 w1 = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+        *reinterpret_cast<float4*>(Ys + row * ldp + ac) = w0;
+        *reinterpret_cast<float4*>(Ys + row * ldp + ac + 4) = w1;
+        if (row < nr) {
+          float4* dst = reinterpret_cast<float4*>(q + (rb + row) * lp + ac);
+          dst[0] = w0;
+          dst[1] = w1;
+        }
+      }
+    }
+    if (!do_gram) continue;
+    __syncthreads();
+    if (ib < lp && jb < lp) {
+      for (int r = 0; r < nr; ++r) {
+        const float4 i0 = *reinterpret_cast<const float4*>(Ys + r * ldp + ib);
+        const float4 i1 = *reinterpret_cast<const float4*>(Ys + r * ldp + ib + 4);
+        const float4 j0 = *reinterpret_cast<const float4*>(Ys + r * ldp + jb);
+        const float4 j1 = *reinterpret_cast<const float4*>(Ys + r * ldp + jb + 4);
+        const float yi[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+        const float yj[8] = {j0.x, j0.y, j0.z, j0.w, j1.x, j1.y, j1.z, j1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) g[a][b] = fmaf(yi[a], yj[b], g[a][b]);
+      }
+    }
+  }
+  if (do_gram && ib < lp && jb < lp) {
+    float* gp = gpart + (int64_t)blockIdx.x * lp * lp;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      float4* dst = reinterpret_cast<float4*>(gp + (int64_t)(ib + a) * lp + jb);
+      dst[0] = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
+      dst[1] = make_float4(g[a][4], g[a][5], g[a][6], g[a][7]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(512) gram_reduce_kernel(const float* __restrict__ gpart, int nblk,
                                                           int lp, float* __restrict__ g) {
   __shared__ float s_sum[kRedSplit][32], s_cmp[kRedSplit][32];
@@ -694,6 +799,9 @@ cudaError_t prep_chol() {
 
 cudaError_t prepare_orth() {
   cudaError_t e;
+  if ((e = cudaFuncSetAttribute(apply_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)apply_gram_smem(128))) != cudaSuccess)
+    return e;
   if ((e = prep_chol<1>()) != cudaSuccess || (e = prep_chol<2>()) != cudaSuccess ||
       (e = prep_chol<3>()) != cudaSuccess || (e = prep_chol<4>()) != cudaSuccess ||
       (e = prep_chol<5>()) != cudaSuccess || (e = prep_chol<6>()) != cudaSuccess ||
@@ -721,6 +829,14 @@ cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stri
   const size_t smem = (size_t)GR * lp * sizeof(float);  // <= 32 KB for lp <= 256
   gram_partial_kernel<<<dim3(nblk, npair), 256, smem, st>>>(src, splits, split_stride, y_out, rows,
                                                             lp, gpart, rpb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_gram(const float* y, float* q, int64_t rows, int lp, const float* rinv,
+                              float* gpart, int nblk, int do_gram, cudaStream_t st) {
+  if (lp > 128 || lp % 16) return cudaErrorInvalidValue;
+  const int64_t rpb = round_up(cdiv(rows, nblk), AG_ROWS);
+  apply_gram_kernel<<<nblk, 256, apply_gram_smem(lp), st>>>(y, q, rows, lp, rinv, gpart, rpb, do_gram);
   return cudaGetLastError();
 }
 
