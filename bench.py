@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 METRIC = "rank-k rSVD ms & HBM roofline frac, BF16-TC vs FP32 GPU at matched error"
 WORKLOAD = ("c2: A = U diag(j^-1.5) V^T, 16384 x 16384, Haar U,V (float32 QR of seeded "
             "Gaussians), bf16-stored A; k=100, p=10, q=1 (4 passes over A)")
-PASS_KERNEL_SRC = os.path.join(ROOT, "paper_0909_4061_gb300", "csrc", "k_sketch_tc.cu")
+PASS_KERNEL_SRC = [os.path.join(ROOT, "paper_0909_4061_gb300", "csrc", f)
+                   for f in ("k_sketch_tc.cu", "tc_ptx.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sketch_tc_pass_c2.md")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
@@ -157,9 +158,12 @@ def measured_peaks():
         return dict(FALLBACK_PEAKS)
 
 
-def file_sha(path: str) -> str:
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def file_sha(paths) -> str:
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic():
