@@ -315,6 +315,7 @@ def run_ours(args):
         stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
         pkg.rsvd_profile(pl.handle, 0)
         out["stages_ms_per_svd"] = {k: round(v / 5, 4) for k, v in stage_ms.items()}
+        out["jacobi_sweeps_max"] = pkg.rsvd_diagnostics(pl.handle)[1]
         # end to end through the host-buffer entry point
         e2e = None
         if not args.no_e2e:
@@ -534,6 +535,7 @@ def run_workload(args):
                 stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
                 pkg.rsvd_profile(pl.handle, 0)
                 res[name] = {"ms": round(ms, 4), "rel_err_vs_fp32_A": round(_rel_err(A, U, S, V), 6),
+                             "jacobi_sweeps_max": pkg.rsvd_diagnostics(pl.handle)[1],
                              "passes_over_A": (2 if kw.get("single_pass") else 2 * q + 2),
                              "stages_ms": {k2: round(v, 4) for k2, v in stage_ms.items()}}
         out.update({"metric": "rank-k rSVD ms per matrix (bf16 tensor cores)",

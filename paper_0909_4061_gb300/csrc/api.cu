@@ -235,7 +235,7 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
   if (lp <= 128) {
     // Gram of the sample, then per round: factor, and Q = Y R^-1 fused with the next Gram
     float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
-    TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
+    TRY(launch_gram_tri(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
     if (cur_splits > 1) cur = P->tmp1;
     TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
     for (int r = 0; r < rounds; ++r) {

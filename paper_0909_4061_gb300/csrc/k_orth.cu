@@ -116,107 +116,226 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const float* __restri
 constexpr int kRedSplit = 16;
 constexpr int kRedBatch = 24;
 
-// One Cholesky-QR step fused with the Gram matrix of the next (lp <= 128): the rows of a
-// block of Y (64 at a time) go through shared memory, Q = Y R^-1 is written out (a 16 x 16
-// thread grid of 4 x 8 output tiles, R^-1 held in shared memory) and, unless this is the
-// last round, the block's Q rows accumulate the Gram partial Q^T Q (8 x 8 tiles) that the
-// reduce kernel sums for the next factorisation.  Y is then read once per round.
-constexpr int AG_ROWS = 64;
+// One Cholesky-QR step fused with the Gram matrix of the next, for l_p <= 128 (APPLY), and
+// the Gram matrix of a sample alone (!APPLY), both on 64-row tiles of Y.
+//
+// Apply: Q = Y R^-1 with R^-1 upper triangular, so column block c (8 columns) of Q needs
+// only rows 0 .. 8c + 7 of R^-1.  Warp w owns the column blocks w and NCB - 1 - w, which
+// makes every warp's share of the triangle the same (NCB + 1 blocks of 8 products), and
+// each lane owns two rows of the tile.  The tile of Y sits transposed in shared memory
+// (one 8-byte load gives a lane its two rows of a column) and R^-1 row-major (the 8
+// columns of a block are one broadcast read per warp).
+// Gram: only the lower triangle is formed (the factorisation reads no more), as 8 x 4
+// (or 8 x 8) tiles of Q^T Q over the tile's rows, one tile per thread, accumulated over
+// the CTA's row tiles and written as this CTA's partial for the reduce kernel.
+// Products are paired into fma.rn.f32x2, which rounds each lane exactly as fmaf does: the
+// sums, and their order over rows and columns, are those of the plain definition.
+constexpr int TR_ROWS = 64;
+constexpr int TR_LDT = TR_ROWS + 2;   // transposed tile stride: conflict-free staging stores
 
-size_t apply_gram_smem(int lp) { return (size_t)(lp + AG_ROWS) * (lp + 4) * sizeof(float); }
+template <int LP, bool APPLY>
+struct TriCfg {
+  static constexpr int NCB = LP / 8;                 // column blocks of 8 (even)
+  static constexpr int NP = NCB / 2;                 // warps: one block pair each
+  static constexpr int T = 32 * NP;
+  static constexpr int LDQ = LP + 4;
+  static constexpr int NB8 = NCB * (NCB + 1) / 2;    // 8 x 8 blocks of the lower triangle
+  static constexpr int TW = (2 * NB8 <= T) ? 4 : 8;  // Gram tile width
+  static constexpr int NTASK = NB8 * (8 / TW);
+  static constexpr int UFL = APPLY ? (LP * TR_LDT > TR_ROWS * LDQ ? LP * TR_LDT : TR_ROWS * LDQ)
+                                   : TR_ROWS * LDQ;
+  static constexpr int SMEM = (APPLY ? LP * LDQ + UFL : UFL) * (int)sizeof(float);
+};
 
-__global__ void __launch_bounds__(256, 2) apply_gram_kernel(const float* __restrict__ y,
-                                                         float* __restrict__ q, int64_t rows, int lp,
-                                                         const float* __restrict__ rinv,
-                                                         float* __restrict__ gpart,
-                                                         int64_t rows_per_blk, int do_gram) {
+typedef unsigned long long f2_t;   // two float32 values, the first in the low half
+__device__ __forceinline__ f2_t pk2(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(f2_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ void fma2(f2_t& acc, f2_t a, f2_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+template <int LP, bool APPLY>
+__global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
+    orth_tri_kernel(const float* __restrict__ y, int splits, int64_t split_stride,
+                    float* __restrict__ q, int64_t rows, const float* __restrict__ rinv,
+                    float* __restrict__ gpart, int64_t rows_per_blk, int do_gram) {
+  using C = TriCfg<LP, APPLY>;
+  constexpr int NCB = C::NCB, NP = C::NP, T = C::T, LDQ = C::LDQ, TW = C::TW;
+  constexpr int NC4 = LP / 4;
   extern __shared__ __align__(16) float sm[];
-  const int ldp = lp + 4;
-  float* Rs = sm;                // lp x ldp
-  float* Ys = sm + lp * ldp;     // AG_ROWS x ldp: the Y rows, then the Q rows
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const int lp4 = lp / 4;
-  for (int e = tid; e < lp * lp4; e += 256) {
-    const int r = e / lp4, c4 = e - r * lp4;
-    *reinterpret_cast<float4*>(Rs + r * ldp + 4 * c4) = *reinterpret_cast<const float4*>(rinv + r * lp + 4 * c4);
-  }
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
-  const int ib = ty * 8, jb = tx * 8;          // Gram tile
-  const int ar = ty * 4, ac = tx * 8;          // apply tile: rows ar..ar+3, columns ac..ac+7
-  const bool cols_in = ac < lp;
-  float g[8][8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) g[a][b] = 0.0f;
-  for (int64_t rb = r0; rb < r1; rb += AG_ROWS) {
-    const int nr = (int)min((int64_t)AG_ROWS, r1 - rb);
-    __syncthreads();
-    for (int e = tid; e < AG_ROWS * lp4; e += 256) {
-      const int rr = e / lp4, c4 = e - rr * lp4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rr < nr) v = *reinterpret_cast<const float4*>(y + (rb + rr) * lp + 4 * c4);
-      *reinterpret_cast<float4*>(Ys + rr * ldp + 4 * c4) = v;
+  float* Rs = sm;                                 // R^-1, LP x LDQ (APPLY)
+  float* Ub = sm + (APPLY ? LP * LDQ : 0);        // Y^T (LP x TR_LDT), then Q (TR_ROWS x LDQ)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (APPLY) {
+    for (int e = tid; e < LP * NC4; e += T) {
+      const int r = e / NC4, c4 = e - r * NC4;
+      *reinterpret_cast<float4*>(Rs + r * LDQ + 4 * c4) =
+          *reinterpret_cast<const float4*>(rinv + r * LP + 4 * c4);
     }
-    __syncthreads();
-    float acc[4][8];
+  }
+  // this thread's Gram tile: rows 8 ga .. 8 ga + 7, columns gc .. gc + TW - 1 (gc <= 8 ga)
+  const bool has_task = tid < C::NTASK;
+  int ga = 0, gc = 0;
+  {
+    int t = has_task ? tid : 0;
+    while (t >= (ga + 1) * (8 / TW)) { t -= (ga + 1) * (8 / TW); ++ga; }
+    gc = TW * t;
+  }
+  f2_t g[4][TW];   // g[p][c] = (G(8 ga + 2p, gc + c), G(8 ga + 2p + 1, gc + c))
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+  for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
-    if (cols_in) {
-      for (int i = 0; i < lp; ++i) {
-        const float4 rv0 = *reinterpret_cast<const float4*>(Rs + i * ldp + ac);
-        const float4 rv1 = *reinterpret_cast<const float4*>(Rs + i * ldp + ac + 4);
-        const float rv[8] = {rv0.x, rv0.y, rv0.z, rv0.w, rv1.x, rv1.y, rv1.z, rv1.w};
+    for (int c = 0; c < TW; ++c) g[p][c] = 0ull;
+  const int cb0 = warp, cb1 = NCB - 1 - warp;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
+  for (int64_t rb = r0; rb < r1; rb += TR_ROWS) {
+    const int nr = (int)min((int64_t)TR_ROWS, r1 - rb);
+    __syncthreads();   // the previous tile is no longer read
+    if (APPLY) {
+      // stage Y^T: per step a warp takes 8 rows x 4 float4 columns (lane = 8 cc + rr), so
+      // the global reads are whole sectors and the transposed stores hit 32 banks
+      {
+        float4 v[8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float yv = Ys[(ar + a) * ldp + i];
+        for (int k = 0; k < 8; ++k) {
+          const int s = warp + NP * k, rg = s & 7, cg = s >> 3;
+          const int r = 8 * rg + (lane & 7), c4 = 4 * cg + (lane >> 3);
+          v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r < nr) v[k] = *reinterpret_cast<const float4*>(y + (rb + r) * LP + 4 * c4);
+        }
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(yv, rv[b], acc[a][b]);
+        for (int k = 0; k < 8; ++k) {
+          const int s = warp + NP * k, rg = s & 7, cg = s >> 3;
+          const int r = 8 * rg + (lane & 7), c4 = 4 * cg + (lane >> 3);
+          float* d = Ub + (4 * c4) * TR_LDT + r;
+          d[0] = v[k].x; d[TR_LDT] = v[k].y; d[2 * TR_LDT] = v[k].z; d[3 * TR_LDT] = v[k].w;
         }
       }
-    }
-    __syncthreads();   // every thread has read its Y rows before they become Q rows
-    if (cols_in) {
+      __syncthreads();
+      f2_t a0[2][4], a1[2][4];   // rows 2 lane + rr; column pairs of blocks cb0, cb1
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int row = ar + a;
-        const float4 w0 = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-        const float4 w1 = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
-        *reinterpret_cast<float4*>(Ys + row * ldp + ac) = w0;
-        *reinterpret_cast<float4*>(Ys + row * ldp + ac + 4) = w1;
+      for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { a0[rr][c] = 0ull; a1[rr][c] = 0ull; }
+      const float* yt = Ub + 2 * lane;
+      const float* p0 = Rs + 8 * cb0;
+      const float* p1 = Rs + 8 * cb1;
+      const int k0 = 8 * (cb0 + 1), k1 = 8 * (cb1 + 1);
+      int i = 0;
+#pragma unroll 2
+      for (; i < k0; ++i) {
+        const float2 yv = *reinterpret_cast<const float2*>(yt + i * TR_LDT);
+        const f2_t y0 = pk2(yv.x, yv.x), y1 = pk2(yv.y, yv.y);
+        const ulonglong2 x0 = *reinterpret_cast<const ulonglong2*>(p0 + i * LDQ);
+        const ulonglong2 x1 = *reinterpret_cast<const ulonglong2*>(p0 + i * LDQ + 4);
+        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2*>(p1 + i * LDQ);
+        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2*>(p1 + i * LDQ + 4);
+        fma2(a0[0][0], y0, x0.x); fma2(a0[0][1], y0, x0.y); fma2(a0[0][2], y0, x1.x); fma2(a0[0][3], y0, x1.y);
+        fma2(a0[1][0], y1, x0.x); fma2(a0[1][1], y1, x0.y); fma2(a0[1][2], y1, x1.x); fma2(a0[1][3], y1, x1.y);
+        fma2(a1[0][0], y0, z0.x); fma2(a1[0][1], y0, z0.y); fma2(a1[0][2], y0, z1.x); fma2(a1[0][3], y0, z1.y);
+        fma2(a1[1][0], y1, z0.x); fma2(a1[1][1], y1, z0.y); fma2(a1[1][2], y1, z1.x); fma2(a1[1][3], y1, z1.y);
+      }
+#pragma unroll 2
+      for (; i < k1; ++i) {
+        const float2 yv = *reinterpret_cast<const float2*>(yt + i * TR_LDT);
+        const f2_t y0 = pk2(yv.x, yv.x), y1 = pk2(yv.y, yv.y);
+        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2*>(p1 + i * LDQ);
+        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2*>(p1 + i * LDQ + 4);
+        fma2(a1[0][0], y0, z0.x); fma2(a1[0][1], y0, z0.y); fma2(a1[0][2], y0, z1.x); fma2(a1[0][3], y0, z1.y);
+        fma2(a1[1][0], y1, z0.x); fma2(a1[1][1], y1, z0.y); fma2(a1[1][2], y1, z1.x); fma2(a1[1][3], y1, z1.y);
+      }
+      __syncthreads();   // every warp has read Y^T before Q overwrites it
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int row = 2 * lane + rr;
+        const float2 u0 = upk2(a0[rr][0]), u1 = upk2(a0[rr][1]), u2 = upk2(a0[rr][2]), u3 = upk2(a0[rr][3]);
+        const float2 w0 = upk2(a1[rr][0]), w1 = upk2(a1[rr][1]), w2 = upk2(a1[rr][2]), w3 = upk2(a1[rr][3]);
+        const float4 qa0 = make_float4(u0.x, u0.y, u1.x, u1.y), qa1 = make_float4(u2.x, u2.y, u3.x, u3.y);
+        const float4 qb0 = make_float4(w0.x, w0.y, w1.x, w1.y), qb1 = make_float4(w2.x, w2.y, w3.x, w3.y);
+        float* srow = Ub + row * LDQ;
+        *reinterpret_cast<float4*>(srow + 8 * cb0) = qa0;
+        *reinterpret_cast<float4*>(srow + 8 * cb0 + 4) = qa1;
+        *reinterpret_cast<float4*>(srow + 8 * cb1) = qb0;
+        *reinterpret_cast<float4*>(srow + 8 * cb1 + 4) = qb1;
         if (row < nr) {
-          float4* dst = reinterpret_cast<float4*>(q + (rb + row) * lp + ac);
-          dst[0] = w0;
-          dst[1] = w1;
+          float* grow = q + (rb + row) * LP;
+          *reinterpret_cast<float4*>(grow + 8 * cb0) = qa0;
+          *reinterpret_cast<float4*>(grow + 8 * cb0 + 4) = qa1;
+          *reinterpret_cast<float4*>(grow + 8 * cb1) = qb0;
+          *reinterpret_cast<float4*>(grow + 8 * cb1 + 4) = qb1;
         }
+      }
+    } else {
+      // stage Y row-major (the sum of the partial slabs), writing the sum out when asked
+      for (int e = tid; e < TR_ROWS * NC4; e += T) {
+        const int r = e / NC4, c4 = e - r * NC4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < nr) {
+          const int64_t off = (rb + r) * LP + 4 * c4;
+          v = *reinterpret_cast<const float4*>(y + off);
+          for (int s = 1; s < splits; ++s) {
+            const float4 w = *reinterpret_cast<const float4*>(y + off + (int64_t)s * split_stride);
+            v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+          }
+          if (q) *reinterpret_cast<float4*>(q + off) = v;
+        }
+        *reinterpret_cast<float4*>(Ub + r * LDQ + 4 * c4) = v;
       }
     }
     if (!do_gram) continue;
     __syncthreads();
-    if (ib < lp && jb < lp) {
+    if (has_task) {
+      const float* qa = Ub + 8 * ga;
+      const float* qb = Ub + gc;
+#pragma unroll 4
       for (int r = 0; r < nr; ++r) {
-        const float4 i0 = *reinterpret_cast<const float4*>(Ys + r * ldp + ib);
-        const float4 i1 = *reinterpret_cast<const float4*>(Ys + r * ldp + ib + 4);
-        const float4 j0 = *reinterpret_cast<const float4*>(Ys + r * ldp + jb);
-        const float4 j1 = *reinterpret_cast<const float4*>(Ys + r * ldp + jb + 4);
-        const float yi[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-        const float yj[8] = {j0.x, j0.y, j0.z, j0.w, j1.x, j1.y, j1.z, j1.w};
+        const ulonglong2 i0 = *reinterpret_cast<const ulonglong2*>(qa + r * LDQ);
+        const ulonglong2 i1 = *reinterpret_cast<const ulonglong2*>(qa + r * LDQ + 4);
+        const f2_t ip[4] = {i0.x, i0.y, i1.x, i1.y};
+        float jv[TW];
+        {
+          const float4 j0 = *reinterpret_cast<const float4*>(qb + r * LDQ);
+          jv[0] = j0.x; jv[1] = j0.y; jv[2] = j0.z; jv[3] = j0.w;
+          if constexpr (TW == 8) {
+            const float4 j1 = *reinterpret_cast<const float4*>(qb + r * LDQ + 4);
+            jv[4] = j1.x; jv[5] = j1.y; jv[6] = j1.z; jv[7] = j1.w;
+          }
+        }
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int c = 0; c < TW; ++c) {
+          const f2_t jj = pk2(jv[c], jv[c]);
 #pragma unroll
-          for (int b = 0; b < 8; ++b) g[a][b] = fmaf(yi[a], yj[b], g[a][b]);
+          for (int p = 0; p < 4; ++p) fma2(g[p][c], ip[p], jj);
+        }
       }
     }
   }
-  if (do_gram && ib < lp && jb < lp) {
-    float* gp = gpart + (int64_t)blockIdx.x * lp * lp;
+  if (do_gram && has_task) {
+    float* gp = gpart + (int64_t)blockIdx.x * LP * LP;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      float4* dst = reinterpret_cast<float4*>(gp + (int64_t)(ib + a) * lp + jb);
-      dst[0] = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
-      dst[1] = make_float4(g[a][4], g[a][5], g[a][6], g[a][7]);
+    for (int p = 0; p < 4; ++p) {
+      float lo[TW], hi[TW];
+#pragma unroll
+      for (int c = 0; c < TW; ++c) {
+        const float2 v = upk2(g[p][c]);
+        lo[c] = v.x;
+        hi[c] = v.y;
+      }
+      float* d0 = gp + (8 * ga + 2 * p) * LP + gc;
+      float* d1 = d0 + LP;
+#pragma unroll
+      for (int c = 0; c < TW; c += 4) {
+        *reinterpret_cast<float4*>(d0 + c) = make_float4(lo[c], lo[c + 1], lo[c + 2], lo[c + 3]);
+        *reinterpret_cast<float4*>(d1 + c) = make_float4(hi[c], hi[c + 1], hi[c + 2], hi[c + 3]);
+      }
     }
   }
 }
@@ -797,10 +916,40 @@ cudaError_t prep_chol() {
                               (int)chol_smem<NB>());
 }
 
+template <int LP>
+cudaError_t prep_tri() {
+  cudaError_t e = cudaFuncSetAttribute(orth_tri_kernel<LP, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TriCfg<LP, true>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(orth_tri_kernel<LP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TriCfg<LP, false>::SMEM);
+}
+
+template <bool APPLY>
+cudaError_t launch_tri(const float* y, int splits, int64_t split_stride, float* q, int64_t rows,
+                       int lp, const float* rinv, float* gpart, int nblk, int do_gram,
+                       cudaStream_t st) {
+  const int64_t rpb = round_up(cdiv(rows, nblk), TR_ROWS);
+#define RSVD_TRI_CASE(LP)                                                                    \
+  case LP:                                                                                  \
+    orth_tri_kernel<LP, APPLY><<<nblk, TriCfg<LP, APPLY>::T, TriCfg<LP, APPLY>::SMEM, st>>>( \
+        y, splits, split_stride, q, rows, rinv, gpart, rpb, do_gram);                       \
+    return cudaGetLastError();
+  switch (lp) {
+    RSVD_TRI_CASE(16) RSVD_TRI_CASE(32) RSVD_TRI_CASE(48) RSVD_TRI_CASE(64)
+    RSVD_TRI_CASE(80) RSVD_TRI_CASE(96) RSVD_TRI_CASE(112) RSVD_TRI_CASE(128)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RSVD_TRI_CASE
+}
+
 cudaError_t prepare_orth() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(apply_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)apply_gram_smem(128))) != cudaSuccess)
+  if ((e = prep_tri<16>()) != cudaSuccess || (e = prep_tri<32>()) != cudaSuccess ||
+      (e = prep_tri<48>()) != cudaSuccess || (e = prep_tri<64>()) != cudaSuccess ||
+      (e = prep_tri<80>()) != cudaSuccess || (e = prep_tri<96>()) != cudaSuccess ||
+      (e = prep_tri<112>()) != cudaSuccess || (e = prep_tri<128>()) != cudaSuccess)
     return e;
   if ((e = prep_chol<1>()) != cudaSuccess || (e = prep_chol<2>()) != cudaSuccess ||
       (e = prep_chol<3>()) != cudaSuccess || (e = prep_chol<4>()) != cudaSuccess ||
@@ -834,10 +983,12 @@ cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stri
 
 cudaError_t launch_apply_gram(const float* y, float* q, int64_t rows, int lp, const float* rinv,
                               float* gpart, int nblk, int do_gram, cudaStream_t st) {
-  if (lp > 128 || lp % 16) return cudaErrorInvalidValue;
-  const int64_t rpb = round_up(cdiv(rows, nblk), AG_ROWS);
-  apply_gram_kernel<<<nblk, 256, apply_gram_smem(lp), st>>>(y, q, rows, lp, rinv, gpart, rpb, do_gram);
-  return cudaGetLastError();
+  return launch_tri<true>(y, 1, 0, q, rows, lp, rinv, gpart, nblk, do_gram, st);
+}
+
+cudaError_t launch_gram_tri(const float* src, int splits, int64_t split_stride, float* y_out,
+                            int64_t rows, int lp, float* gpart, int nblk, cudaStream_t st) {
+  return launch_tri<false>(src, splits, split_stride, y_out, rows, lp, nullptr, gpart, nblk, 1, st);
 }
 
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st) {

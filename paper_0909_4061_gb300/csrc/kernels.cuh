@@ -31,10 +31,15 @@ int gram_blocks(int64_t rows);
 // G = sum of the nblk partial Grams (lp x lp).
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st);
 
-// Q = Y R^-1 (rows x lp, lp <= 128, nblk row blocks) and, with do_gram, the Gram partials
-// Q^T Q of each block into gpart (nblk x lp x lp) for launch_gram_reduce.
+// Q = Y R^-1 (rows x lp, lp a multiple of 16 up to 128, R^-1 upper triangular, nblk row
+// blocks) and, with do_gram, the lower triangle of each block's Gram partial Q^T Q into
+// gpart (nblk x lp x lp) for launch_gram_reduce.
 cudaError_t launch_apply_gram(const float* y, float* q, int64_t rows, int lp, const float* rinv,
                               float* gpart, int nblk, int do_gram, cudaStream_t st);
+// The lower triangle of the Gram partials of Y (the sum of `splits` slabs, written to y_out
+// when y_out is non-null) for the same lp range.
+cudaError_t launch_gram_tri(const float* src, int splits, int64_t split_stride, float* y_out,
+                            int64_t rows, int lp, float* gpart, int nblk, cudaStream_t st);
 
 // Cholesky G (+ shift) = R^T R, R^-1 into rinv (lp x lp upper, zero padded), R into r_out,
 // and racc <- R * racc (or racc <- R when racc_init != 0) when racc is non-null.
