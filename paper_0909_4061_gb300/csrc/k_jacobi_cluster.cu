@@ -13,9 +13,9 @@
 // once per sweep, as in the cyclic sweep of the one-CTA kernel, while 2C pairs'
 // worth of rotation work runs on C SMs at once and no column is read remotely
 // during the rotations.  The rotation is the tan(angle/2) form; a pair counts as
-// orthogonal below tol; sweeps end when none rotates.  Epilogue: sigma_c = ||x_c||,
-// U = X diag(1/sigma), W = J, in descending sigma order; a second kernel polishes W
-// by one Newton-Schulz step W <- W (3 I - W^T W) / 2.
+// orthogonal while |x_p . x_q| <= tol ||x_p|| ||x_q||; sweeps end when none rotates.
+// Epilogue: sigma_c = ||x_c||, U = X diag(1/sigma), W = J, in descending sigma order; a
+// second kernel polishes W by one Newton-Schulz step W <- W (3 I - W^T W) / 2.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -49,6 +49,10 @@ __device__ __forceinline__ void stcol(float* p, int hl, const float (&u)[4 * VPL
         make_float4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
 }
 
+// [u v] <- [u v] [[c, s], [-s, c]] in the tan(theta / 2) form, tau = s / (1 + c):
+// u - s (tau u + v), v + s (u - tau v).  Its scaling error is (c^2 + s^2 - 1) times
+// (1 - c) / (1 + c), about theta^2 / 4 of that of the plain form, which keeps column norms
+// from drifting over the many small rotations of the last sweeps.
 template <int VPL>
 __device__ __forceinline__ void rotcols(float (&u)[4 * VPL], float (&v)[4 * VPL], float sn, float tau) {
 #pragma unroll
@@ -59,47 +63,87 @@ __device__ __forceinline__ void rotcols(float (&u)[4 * VPL], float (&v)[4 * VPL]
   }
 }
 
-// Rotate columns xp, xq (and jp, jq) so that they become orthogonal, by one half-warp
-// (hl = lane within it, hmask = its lanes).  Returns true when a rotation was applied.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// The rotation (s, tau = s / (1 + c)) that makes two columns with squared norms a, b and
+// inner product g orthogonal; false when they already count as orthogonal,
+// g^2 <= tol^2 a b.
+// a, b, g are first scaled by the power of two that puts max(a, b) in [1, 2) (exact), so
+// neither the test nor the angle underflows for tiny columns.  t = tan(theta) is the
+// root of t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 g), with |theta| <= pi/4, taken as
+// t = sign(b - a) 2 g / (|b - a| + sqrt((b - a)^2 + 4 g^2)) from approximate reciprocals
+// and square roots: any angle gives an orthogonal transform, only how far the pair's new
+// inner product is from zero depends on its accuracy.  c = 1 / sqrt(1 + t^2) gets one
+// Newton step, so that c^2 + s^2 = 1 to rounding and column norms do not drift.
+__device__ __forceinline__ bool jacobi_angle(float a, float b, float g, float tol2, float& sn,
+                                             float& tau) {
+  const int e = min((__float_as_int(fmaxf(a, b)) >> 23) & 0xff, 253);
+  const float f = __int_as_float((254 - e) << 23);
+  a *= f;
+  b *= f;
+  g *= f;
+  if (!(g * g > (tol2 * a) * b)) return false;   // also false for g = 0 and NaN
+  const float d = b - a;
+  const float h = fmaf(d, d, 4.0f * g * g);
+  const float r = h * rsqrtf(h);
+  float t = 2.0f * g * rcp_approx(fabsf(d) + r);
+  t = d < 0.0f ? -t : t;
+  const float w = fmaf(t, t, 1.0f);
+  float cc = rsqrtf(w);
+  cc = cc * fmaf(-0.5f * w, cc * cc, 1.5f);
+  sn = cc * t;
+  tau = sn * rcp_approx(1.0f + cc);
+  return true;
+}
+
+// Squared norms and inner product of two columns held by a half-warp, summed over it.
 template <int VPL>
-__device__ __forceinline__ bool pair_rotate(float* xp, float* xq, float* jp, float* jq, int hl,
-                                            unsigned hmask, float tol) {
-  float u[4 * VPL], v[4 * VPL];
-  ldcol<VPL>(xp, hl, u);
-  ldcol<VPL>(xq, hl, v);
-  float a = 0.f, b = 0.f, g = 0.f;
+__device__ __forceinline__ void col_dots(const float (&u)[4 * VPL], const float (&v)[4 * VPL],
+                                         unsigned hmask, float& a, float& b, float& g) {
+  float a0 = 0.f, b0 = 0.f, g0 = 0.f, a1 = 0.f, b1 = 0.f, g1 = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4 * VPL; ++i) {
-    a = fmaf(u[i], u[i], a);
-    b = fmaf(v[i], v[i], b);
-    g = fmaf(u[i], v[i], g);
+  for (int i = 0; i < 4 * VPL; i += 2) {
+    a0 = fmaf(u[i], u[i], a0);
+    b0 = fmaf(v[i], v[i], b0);
+    g0 = fmaf(u[i], v[i], g0);
+    a1 = fmaf(u[i + 1], u[i + 1], a1);
+    b1 = fmaf(v[i + 1], v[i + 1], b1);
+    g1 = fmaf(u[i + 1], v[i + 1], g1);
   }
+  a = a0 + a1;
+  b = b0 + b1;
+  g = g0 + g1;
 #pragma unroll
   for (int o = 8; o > 0; o >>= 1) {
     a += __shfl_xor_sync(hmask, a, o);
     b += __shfl_xor_sync(hmask, b, o);
     g += __shfl_xor_sync(hmask, g, o);
   }
-  if (g == 0.0f || !(fabsf(g) > tol * sqrtf(a * b))) return false;
-  // t = tan(theta) of the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 g)
-  const float zeta = __fdividef(b - a, 2.0f * g);
-  const float az = fabsf(zeta);
-  float t = (az > 1e18f) ? __fdividef(0.5f, az) : __fdividef(1.0f, az + sqrtf(fmaf(az, az, 1.0f)));
-  t = copysignf(t, zeta);
-  if (zeta == 0.0f) t = 1.0f;
-  const float w2 = fmaf(t, t, 1.0f);
-  float c = rsqrtf(w2);
-  c = c * fmaf(-0.5f * w2, c * c, 1.5f);
-  const float sn = c * t;
-  const float tau = sn / (1.0f + c);
+}
+
+// Rotate columns xp, xq (and jp, jq) of shared memory so that they become orthogonal,
+// by one half-warp (hl = lane within it, hmask = its lanes).  True when rotated.
+template <int VPL>
+__device__ __forceinline__ bool pair_rotate(float* xp, float* xq, float* jp, float* jq, int hl,
+                                            unsigned hmask, float tol2) {
+  float u[4 * VPL], v[4 * VPL], ju[4 * VPL], jv[4 * VPL];
+  ldcol<VPL>(xp, hl, u);
+  ldcol<VPL>(xq, hl, v);
+  ldcol<VPL>(jp, hl, ju);
+  ldcol<VPL>(jq, hl, jv);
+  float a, b, g, sn, tau;
+  col_dots<VPL>(u, v, hmask, a, b, g);
+  if (!jacobi_angle(a, b, g, tol2, sn, tau)) return false;
   rotcols<VPL>(u, v, sn, tau);
+  rotcols<VPL>(ju, jv, sn, tau);
   stcol<VPL>(xp, hl, u);
   stcol<VPL>(xq, hl, v);
-  ldcol<VPL>(jp, hl, u);
-  ldcol<VPL>(jq, hl, v);
-  rotcols<VPL>(u, v, sn, tau);
-  stcol<VPL>(jp, hl, u);
-  stcol<VPL>(jq, hl, v);
+  stcol<VPL>(jp, hl, ju);
+  stcol<VPL>(jq, hl, jv);
   return true;
 }
 
@@ -114,7 +158,7 @@ template <int VPL>
 __global__ void __launch_bounds__(kThreadsC) jacobi_block_kernel(
     const float* __restrict__ x, int64_t ldx, int transposed, int l, int lp, int bw,
     float* __restrict__ ut, float* __restrict__ s, float* __restrict__ w, uint32_t* status,
-    uint32_t* info, float tol) {
+    uint32_t* info, float tol2) {
   constexpr int LR = 64 * VPL;   // rows per stored column (zero beyond l)
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -167,21 +211,46 @@ __global__ void __launch_bounds__(kThreadsC) jacobi_block_kernel(
         if (p < bw && q < bw) {
           float* X = buf(cur, sl);
           float* Jm = X + bw * LR;
-          rotated |= pair_rotate<VPL>(X + p * LR, X + q * LR, Jm + p * LR, Jm + q * LR, hl, hmask, tol);
+          rotated |= pair_rotate<VPL>(X + p * LR, X + q * LR, Jm + p * LR, Jm + q * LR, hl, hmask, tol2);
         }
       }
       __syncthreads();
     }
     for (int round = 0; round < nblk - 1; ++round) {
+      // Half-warp h keeps column h of the first block (X and J) in registers for the
+      // round and meets column (h + sub) mod bw of the second block in sub-round sub;
+      // that column comes from half-warp h + 1 of the previous sub-round.
       float* X0 = buf(cur, 0);
       float* X1 = buf(cur, 1);
+      float* J0 = X0 + bw * LR;
+      float* J1 = X1 + bw * LR;
+      const bool act = hw < bw;
+      float xr[4 * VPL], jr[4 * VPL];
+      if (act) {
+        ldcol<VPL>(X0 + hw * LR, hl, xr);
+        ldcol<VPL>(J0 + hw * LR, hl, jr);
+      }
       for (int sub = 0; sub < bw; ++sub) {
-        if (hw < bw) {
-          const int p = hw, q = (hw + sub) % bw;
-          rotated |= pair_rotate<VPL>(X0 + p * LR, X1 + q * LR, X0 + bw * LR + p * LR,
-                                      X1 + bw * LR + q * LR, hl, hmask, tol);
+        if (act) {
+          const int q = hw + sub < bw ? hw + sub : hw + sub - bw;
+          float v[4 * VPL], jv[4 * VPL];
+          ldcol<VPL>(X1 + q * LR, hl, v);
+          ldcol<VPL>(J1 + q * LR, hl, jv);
+          float a, b, g, sn, tau;
+          col_dots<VPL>(xr, v, hmask, a, b, g);
+          if (jacobi_angle(a, b, g, tol2, sn, tau)) {
+            rotated = true;
+            rotcols<VPL>(xr, v, sn, tau);
+            rotcols<VPL>(jr, jv, sn, tau);
+            stcol<VPL>(X1 + q * LR, hl, v);
+            stcol<VPL>(J1 + q * LR, hl, jv);
+          }
         }
         __syncthreads();
+      }
+      if (act) {
+        stcol<VPL>(X0 + hw * LR, hl, xr);
+        stcol<VPL>(J0 + hw * LR, hl, jr);
       }
       if (rotated && hl == 0) s_rot[par] = 1;
       cluster.sync();   // every CTA has finished this round: its blocks may be read
@@ -205,8 +274,11 @@ __global__ void __launch_bounds__(kThreadsC) jacobi_block_kernel(
         for (; e < n4; e += kThreadsC) dst[e] = src[e];
       }
       cur = nxt;
-      // no CTA may overwrite a buffer (next round's pull) before all have read it
-      cluster.sync();
+      // The pulled columns are complete in this CTA before any half-warp rotates them.  No
+      // second cluster barrier: a CTA writes its other buffer again only in the next
+      // round's pull, after the next cluster barrier, which every CTA reaches only once it
+      // has finished this round's pull.
+      __syncthreads();
     }
     // after 2C - 1 moves every block is back in its first place; did any CTA rotate?
     if (tid == 0) {
@@ -362,7 +434,7 @@ size_t block_smem(int bw) { return (size_t)4 * 2 * bw * 64 * VPL * sizeof(float)
 
 template <int VPL>
 cudaError_t launch_vpl(int C, const float* x, int64_t ldx, int transposed, int l, int lp, int bw,
-                       float* ut, float* s, float* w, uint32_t* status, uint32_t* info, float tol,
+                       float* ut, float* s, float* w, uint32_t* status, uint32_t* info, float tol2,
                        cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
@@ -377,7 +449,7 @@ cudaError_t launch_vpl(int C, const float* x, int64_t ldx, int transposed, int l
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, jacobi_block_kernel<VPL>, x, ldx, transposed, l, lp, bw, ut, s,
-                            w, status, info, tol);
+                            w, status, info, tol2);
 }
 
 }  // namespace
@@ -402,13 +474,14 @@ cudaError_t launch_jacobi_cluster(const float* x, int64_t ldx, int transposed, i
   const int C = l <= 128 ? 4 : kMaxCluster;
   const int bw = (l + 2 * C - 1) / (2 * C);   // <= 16
   const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
+  const float tol2 = tol * tol;
   const int vpl = (l + 63) / 64;
   cudaError_t e;
   switch (vpl) {
-    case 1: e = launch_vpl<1>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol, st); break;
-    case 2: e = launch_vpl<2>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol, st); break;
-    case 3: e = launch_vpl<3>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol, st); break;
-    default: e = launch_vpl<4>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol, st); break;
+    case 1: e = launch_vpl<1>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
+    case 2: e = launch_vpl<2>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
+    case 3: e = launch_vpl<3>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
+    default: e = launch_vpl<4>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
   }
   if (e != cudaSuccess) return e;
   // padding of W (rows/columns >= l) is zero in scratch; copy it, then polish the l x l part
