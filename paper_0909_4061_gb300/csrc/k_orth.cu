@@ -147,6 +147,14 @@ struct TriCfg {
   static constexpr int SMEM = (APPLY ? LP * LDQ + UFL : UFL) * (int)sizeof(float);
 };
 
+// 16-byte global -> shared copy that does not pass through registers (L2 only), so a
+// thread can have all of its copies in flight at once.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 typedef unsigned long long f2_t;   // two float32 values, the first in the low half
 __device__ __forceinline__ f2_t pk2(float a, float b) {
   f2_t r;
@@ -174,11 +182,10 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
   float* Rs = sm;                                 // R^-1, LP x LDQ (APPLY)
   float* Ub = sm + (APPLY ? LP * LDQ : 0);        // Y^T (LP x TR_LDT), then Q (TR_ROWS x LDQ)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (APPLY) {
+  if (APPLY) {   // R^-1 into shared memory, waited for with the first tile of Y
     for (int e = tid; e < LP * NC4; e += T) {
       const int r = e / NC4, c4 = e - r * NC4;
-      *reinterpret_cast<float4*>(Rs + r * LDQ + 4 * c4) =
-          *reinterpret_cast<const float4*>(rinv + r * LP + 4 * c4);
+      cp_async16(Rs + r * LDQ + 4 * c4, rinv + r * LP + 4 * c4);
     }
   }
   // this thread's Gram tile: rows 8 ga .. 8 ga + 7, columns gc .. gc + TW - 1 (gc <= 8 ga)
@@ -219,6 +226,7 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
           d[0] = v[k].x; d[TR_LDT] = v[k].y; d[2 * TR_LDT] = v[k].z; d[3 * TR_LDT] = v[k].w;
         }
       }
+      cp_async_wait_all();
       __syncthreads();
       f2_t a0[2][4], a1[2][4];   // rows 2 lane + rr; column pairs of blocks cb0, cb1
 #pragma unroll
@@ -273,6 +281,14 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
           *reinterpret_cast<float4*>(grow + 8 * cb1 + 4) = qb1;
         }
       }
+    } else if (splits == 1 && q == nullptr) {
+      // stage Y row-major, every copy in flight; rows past the end are zero
+      for (int e = tid; e < TR_ROWS * NC4; e += T) {
+        const int r = e / NC4, c4 = e - r * NC4;
+        if (r < nr) cp_async16(Ub + r * LDQ + 4 * c4, y + (rb + r) * LP + 4 * c4);
+        else *reinterpret_cast<float4*>(Ub + r * LDQ + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cp_async_wait_all();
     } else {
       // stage Y row-major (the sum of the partial slabs), writing the sum out when asked
       for (int e = tid; e < TR_ROWS * NC4; e += T) {
@@ -559,7 +575,7 @@ __device__ __forceinline__ float4 axpy4(float s, const float4 x, float4 y) {
 }
 
 template <int NB>
-__global__ void __launch_bounds__(512) cholesky_blocked_kernel(
+__global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
     const float* __restrict__ g, int l, int shifted, float* __restrict__ r_out,
     float* __restrict__ rinv, float* __restrict__ racc, int racc_init, uint32_t* status,
     float* __restrict__ xg) {
@@ -640,160 +656,235 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
   if (tid < l) arow(tid)[tid] += s_shift;
   __syncthreads();
 
-#pragma unroll 1
-  for (int jb = 0; jb < NB; ++jb) {
-    const int J = jb * CB;
-    // (1) diagonal block by warp 0: lanes r and r + 16 both hold row r (mirrored)
-    if (warp == 0) {
-      const int r = lane & 15;
-      float a[CB], rpv[CB];
-      {
-        const float4* src = reinterpret_cast<const float4*>(arow(J + r) + J);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 t = src[q];
-          a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < CB; ++j) {
-        float d = __shfl_sync(0xffffffffu, a[j], j);
-        if (J + j < l && !(d > pfloor)) {   // d is the same in every lane
-          if (lane == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
-          d = pfloor;
-        }
-        // 1/sqrt(d) by the hardware estimate and one Newton step y <- y (3 - d y^2) / 2
-        float rp = rsqrtf(d);
-        rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);
-        rpv[j] = rp;
-        const float lij = (r == j) ? d * rp : (r > j ? a[j] * rp : 0.0f);
-        a[j] = lij;
-#pragma unroll
-        for (int k = j + 1; k < CB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), a[k]);
-      }
-      // X_JJ = L_JJ^-1 by columns: lane r holds column r, x[i] = X(i, r), zero for i < r
-      float x[CB];
-#pragma unroll
-      for (int i = 0; i < CB; ++i) {
-        float v0 = 0.0f, v1 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < i; ++k) {
-          const float lik = __shfl_sync(0xffffffffu, a[k], i);
-          if (k & 1) v1 = fmaf(lik, x[k], v1);
-          else v0 = fmaf(lik, x[k], v0);
-        }
-        x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
-      }
-      if (lane < CB) {
-        float4* dst = reinterpret_cast<float4*>(arow(J + r) + J);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
-#pragma unroll
-        for (int i = 0; i < CB; ++i) xrow(J + i)[J + r] = x[i];
-      }
-    }
-    __syncthreads();
-    const int s0 = J + CB;
-    if (s0 < LP) {
-      // (2) panel, in place: L_iJ(c) = sum_k A_iJ(k) X_JJ(c, k); a half-warp per row
-      {
-        const int c = tid & 15;
-        const float4* xc = reinterpret_cast<const float4*>(xrow(J + c) + J);
-        const float4 x0 = xc[0], x1 = xc[1], x2 = xc[2], x3 = xc[3];
-        for (int i = s0 + (tid >> 4); i < LP; i += 32) {
-          float* ai = arow(i) + J;
-          const float4* a4 = reinterpret_cast<const float4*>(ai);
-          const float v = dot4(a4[0], x0, dot4(a4[2], x2, 0.0f)) + dot4(a4[1], x1, dot4(a4[3], x3, 0.0f));
-          __syncwarp();
-          ai[c] = v;
-        }
-      }
-      __syncthreads();
-      // (3) trailing lower triangle: A_ik -= L_iJ . L_kJ; rows i0, i0 + 1 per warp, k per lane
-      for (int ip = warp; 2 * ip < LP - s0; ip += NW) {
-        const int i0 = s0 + 2 * ip, i1 = i0 + 1;
-        const float4* p0 = reinterpret_cast<const float4*>(arow(i0) + J);
-        const float4* p1 = reinterpret_cast<const float4*>(arow(i1) + J);
-        const float4 u0 = p0[0], u1 = p0[1], u2 = p0[2], u3 = p0[3];
-        const float4 w0 = p1[0], w1 = p1[1], w2 = p1[2], w3 = p1[3];
-        for (int k = s0 + lane; k <= i1; k += 32) {
-          const float4* pk = reinterpret_cast<const float4*>(arow(k) + J);
-          const float4 k0 = pk[0], k1 = pk[1], k2 = pk[2], k3 = pk[3];
-          const float a0 = dot4(u0, k0, dot4(u1, k1, 0.0f)) + dot4(u2, k2, dot4(u3, k3, 0.0f));
-          const float a1 = dot4(w0, k0, dot4(w1, k1, 0.0f)) + dot4(w2, k2, dot4(w3, k3, 0.0f));
-          if (k <= i0) arow(i0)[k] -= a0;
-          arow(i1)[k] -= a1;
-        }
-      }
-      __syncthreads();
-    }
-  }
-
-  // off-diagonal blocks of the inverse, block row I after block row I-1:
-  // S(r, c) = sum_{c<=k<I} L(I+r, k) X(k, c) into A's scratch upper triangle
-  // (A[c][I + r], c < I), then X(I+r, c) = -sum_{t<=r} X_II(r, t) S(t, c)
-#pragma unroll 1
-  for (int ib = 1; ib < NB; ++ib) {
-    const int I = ib * CB;
-    for (int t = tid; t < 2 * I; t += 512) {   // tiles of rows 2rp, 2rp+1 x columns 4cq..4cq+3
-      const int rp = t & 7, c0 = 4 * (t >> 3);
-      const float* la = arow(I + 2 * rp);
-      const float* lb = arow(I + 2 * rp + 1);
-      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
-      for (int k = c0; k < I; ++k) {   // X(k, c0 + q) = 0 for k < c0 + q
-        const float4 xk = *reinterpret_cast<const float4*>(xrow(k) + c0);
-        s0 = axpy4(la[k], xk, s0);
-        s1 = axpy4(lb[k], xk, s1);
-      }
-      // S(t, c) for t = 2rp, 2rp + 1 and c = c0 .. c0 + 3, in srow(c)[t]
-      float* d0 = PACKED ? Sb + c0 * 20 + 2 * rp : A + c0 * LD + I + 2 * rp;
-      constexpr int SLD = PACKED ? 20 : LD;
-      d0[0] = s0.x; d0[1] = s1.x;
-      d0[SLD] = s0.y; d0[SLD + 1] = s1.y;
-      d0[2 * SLD] = s0.z; d0[2 * SLD + 1] = s1.z;
-      d0[3 * SLD] = s0.w; d0[3 * SLD + 1] = s1.w;
-    }
-    __syncthreads();
+  // Diagonal block J (16 x 16) by warp 0: L_JJ by Cholesky in registers (lanes r and
+  // r + 16 both hold row r), then X_JJ = L_JJ^-1 by columns.  The pivot of step j + 1 is
+  // lane (j + 1)'s own A(j + 1, j + 1) - L(j + 1, j)^2, formed from its own L(j + 1, j) and
+  // broadcast first, so one shuffle per step lies on the chain of pivots; a floored pivot
+  // is reported once, after the loop.
+  auto diag_block = [&](int J) {
+    const int r = lane & 15;
+    float a[CB], rpv[CB];
     {
-      const int r = tid & 15;
-      const float4* xr = reinterpret_cast<const float4*>(xrow(I + r) + I);
-      const float4 x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];   // X_II row r (zero beyond r)
-      for (int c = tid >> 4; c < I; c += 32) {
-        const float4* sc = reinterpret_cast<const float4*>(PACKED ? Sb + c * 20 : A + c * LD + I);
-        const float v = dot4(x0, sc[0], dot4(x2, sc[2], 0.0f)) + dot4(x1, sc[1], dot4(x3, sc[3], 0.0f));
-        xrow(I + r)[c] = -v;
+      const float4* src = reinterpret_cast<const float4*>(arow(J + r) + J);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = src[q];
+        a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+      }
+    }
+    float dn = __shfl_sync(0xffffffffu, a[0], 0);
+    bool any_low = false;
+    float dlow = 0.0f;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      float d = dn;
+      const bool low = J + j < l && !(d > pfloor);   // d is the same in every lane
+      if (low && !any_low) dlow = d;
+      any_low |= low;
+      d = low ? pfloor : d;
+      // 1/sqrt(d) by the hardware estimate and one Newton step y <- y (3 - d y^2) / 2
+      float rp = rsqrtf(d);
+      rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);
+      rpv[j] = rp;
+      const float lij = (r == j) ? d * rp : (r > j ? a[j] * rp : 0.0f);
+      a[j] = lij;
+      // the next pivot is broadcast before the row updates queue their shuffles
+      if (j + 1 < CB) dn = __shfl_sync(0xffffffffu, fmaf(-lij, lij, a[j + 1 < CB ? j + 1 : j]), j + 1);
+#pragma unroll
+      for (int k = j + 1; k < CB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), a[k]);
+    }
+    if (any_low && lane == 0) set_status(status, isnan(dlow) ? ST_NONFINITE : ST_RANK_DEFICIENT);
+    // X_JJ = L_JJ^-1 by columns: lane r holds column r, x[i] = X(i, r), zero for i < r
+    float x[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        const float lik = __shfl_sync(0xffffffffu, a[k], i);
+        if (k & 1) v1 = fmaf(lik, x[k], v1);
+        else v0 = fmaf(lik, x[k], v0);
+      }
+      x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
+    }
+    if (lane < CB) {
+      float4* dst = reinterpret_cast<float4*>(arow(J + r) + J);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+#pragma unroll
+      for (int i = 0; i < CB; ++i) xrow(J + i)[J + r] = x[i];
+    }
+  };
+  // A_ik -= L_iJ . L_kJ for rows i0, i0 + 1 and columns k = k0, k0 + kstep, ... <= i
+  auto update_rows = [&](int J, int i0, int k0, int kstep) {
+    const int i1 = i0 + 1;
+    const float4* p0 = reinterpret_cast<const float4*>(arow(i0) + J);
+    const float4* p1 = reinterpret_cast<const float4*>(arow(i1) + J);
+    const float4 u0 = p0[0], u1 = p0[1], u2 = p0[2], u3 = p0[3];
+    const float4 w0 = p1[0], w1 = p1[1], w2 = p1[2], w3 = p1[3];
+    for (int k = k0; k <= i1; k += kstep) {
+      const float4* pk = reinterpret_cast<const float4*>(arow(k) + J);
+      const float4 k0v = pk[0], k1 = pk[1], k2 = pk[2], k3 = pk[3];
+      const float a0 = dot4(u0, k0v, dot4(u1, k1, 0.0f)) + dot4(u2, k2, dot4(u3, k3, 0.0f));
+      const float a1 = dot4(w0, k0v, dot4(w1, k1, 0.0f)) + dot4(w2, k2, dot4(w3, k3, 0.0f));
+      if (k <= i0) arow(i0)[k] -= a0;
+      arow(i1)[k] -= a1;
+    }
+  };
+
+  // Off-diagonal blocks of X = L^-1, block row I (16 rows) from the block rows above it:
+  // S(r, c) = sum_{c<=k<I} L(I+r, k) X(k, c) into A's scratch upper triangle
+  // (A[c][I + r], c < I; a separate 16-row block in the packed form), then
+  // X(I+r, c) = -sum_{t<=r} X_II(r, t) S(t, c).  Run by threads t < nt of the caller.
+  // S in 4 x 4 tiles (rows 4 rg .. 4 rg + 3, columns c0 = 4 cg .. c0 + 3), consecutive
+  // lanes on consecutive column groups (their rows of X fall in distinct banks); the k
+  // range of a tile, [c0, I) (X(k, c) = 0 for k < c), is split into two halves on
+  // neighbouring lanes, summed by one shuffle (2 I is a multiple of 32: whole warps).
+  auto inverse_s = [&](int I, int t, int nt) {
+    const int ncg = I / 4;
+    for (int u = t; u < 2 * I; u += nt) {
+      const int tile = u >> 1, h = u & 1;
+      const int cg = tile % ncg, rg = tile / ncg;
+      const int c0 = 4 * cg;
+      const int half4 = (((I - c0) >> 2) + 1) >> 1;
+      const int kb = h ? c0 + 4 * half4 : c0, ke = h ? I : c0 + 4 * half4;
+      const float* l0 = arow(I + 4 * rg);
+      const float* l1 = arow(I + 4 * rg + 1);
+      const float* l2 = arow(I + 4 * rg + 2);
+      const float* l3 = arow(I + 4 * rg + 3);
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;   // rows of the tile
+      for (int k = kb; k < ke; k += 4) {
+        const float4 a0 = *reinterpret_cast<const float4*>(l0 + k);
+        const float4 a1 = *reinterpret_cast<const float4*>(l1 + k);
+        const float4 a2 = *reinterpret_cast<const float4*>(l2 + k);
+        const float4 a3 = *reinterpret_cast<const float4*>(l3 + k);
+        const float4 x0 = *reinterpret_cast<const float4*>(xrow(k) + c0);
+        const float4 x1 = *reinterpret_cast<const float4*>(xrow(k + 1) + c0);
+        const float4 x2 = *reinterpret_cast<const float4*>(xrow(k + 2) + c0);
+        const float4 x3 = *reinterpret_cast<const float4*>(xrow(k + 3) + c0);
+        s0 = axpy4(a0.x, x0, s0); s1 = axpy4(a1.x, x0, s1); s2 = axpy4(a2.x, x0, s2); s3 = axpy4(a3.x, x0, s3);
+        s0 = axpy4(a0.y, x1, s0); s1 = axpy4(a1.y, x1, s1); s2 = axpy4(a2.y, x1, s2); s3 = axpy4(a3.y, x1, s3);
+        s0 = axpy4(a0.z, x2, s0); s1 = axpy4(a1.z, x2, s1); s2 = axpy4(a2.z, x2, s2); s3 = axpy4(a3.z, x2, s3);
+        s0 = axpy4(a0.w, x3, s0); s1 = axpy4(a1.w, x3, s1); s2 = axpy4(a2.w, x3, s2); s3 = axpy4(a3.w, x3, s3);
+      }
+      auto pair_sum = [](float4 v) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+        v.z += __shfl_xor_sync(0xffffffffu, v.z, 1);
+        v.w += __shfl_xor_sync(0xffffffffu, v.w, 1);
+        return v;
+      };
+      s0 = pair_sum(s0); s1 = pair_sum(s1); s2 = pair_sum(s2); s3 = pair_sum(s3);
+      // S(t, c) goes to srow(c)[t]; lane h writes columns c0 + 2 h and c0 + 2 h + 1
+      constexpr int SLD = PACKED ? 20 : LD;
+      float* d = (PACKED ? Sb + c0 * 20 : A + c0 * LD + I) + 4 * rg;
+      if (h == 0) {
+        *reinterpret_cast<float4*>(d) = make_float4(s0.x, s1.x, s2.x, s3.x);
+        *reinterpret_cast<float4*>(d + SLD) = make_float4(s0.y, s1.y, s2.y, s3.y);
+      } else {
+        *reinterpret_cast<float4*>(d + 2 * SLD) = make_float4(s0.z, s1.z, s2.z, s3.z);
+        *reinterpret_cast<float4*>(d + 3 * SLD) = make_float4(s0.w, s1.w, s2.w, s3.w);
+      }
+    }
+  };
+  auto inverse_x = [&](int I, int t, int nt) {
+    const int r = t & 15;
+    const float4* xr = reinterpret_cast<const float4*>(xrow(I + r) + I);
+    const float4 x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];   // X_II row r (zero beyond r)
+    for (int c = t >> 4; c < I; c += nt >> 4) {
+      const float4* sc = reinterpret_cast<const float4*>(PACKED ? Sb + c * 20 : A + c * LD + I);
+      const float v = dot4(x0, sc[0], dot4(x2, sc[2], 0.0f)) + dot4(x1, sc[1], dot4(x3, sc[3], 0.0f));
+      xrow(I + r)[c] = -v;
+    }
+  };
+
+  // Right-looking blocked factorisation with look-ahead: after the panel of block column
+  // J and the update of the next diagonal block, warp 0 factors that block while the
+  // other warps update the rest of the trailing triangle and form block row J of the
+  // inverse.
+  if (warp == 0) diag_block(0);
+  __syncthreads();
+#pragma unroll 1
+  for (int jb = 0; jb + 1 < NB; ++jb) {
+    const int J = jb * CB, s0 = J + CB;
+    // panel, in place: L_iJ(c) = sum_k A_iJ(k) X_JJ(c, k); a half-warp per row
+    {
+      const int c = tid & 15;
+      const float4* xc = reinterpret_cast<const float4*>(xrow(J + c) + J);
+      const float4 x0 = xc[0], x1 = xc[1], x2 = xc[2], x3 = xc[3];
+      for (int i = s0 + (tid >> 4); i < LP; i += 32) {
+        float* ai = arow(i) + J;
+        const float4* a4 = reinterpret_cast<const float4*>(ai);
+        const float v = dot4(a4[0], x0, dot4(a4[2], x2, 0.0f)) + dot4(a4[1], x1, dot4(a4[3], x3, 0.0f));
+        __syncwarp();
+        ai[c] = v;
+      }
+    }
+    __syncthreads();
+    // the next diagonal block's lower triangle (136 entries), one per thread
+    if (tid < CB * (CB + 1) / 2) {
+      int i = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
+      if ((i + 1) * (i + 2) / 2 <= tid) ++i;
+      if (i * (i + 1) / 2 > tid) --i;
+      const int k = tid - i * (i + 1) / 2;
+      const float4* pi = reinterpret_cast<const float4*>(arow(s0 + i) + J);
+      const float4* pk = reinterpret_cast<const float4*>(arow(s0 + k) + J);
+      const float v = dot4(pi[0], pk[0], dot4(pi[1], pk[1], 0.0f)) + dot4(pi[2], pk[2], dot4(pi[3], pk[3], 0.0f));
+      arow(s0 + i)[s0 + k] -= v;
+    }
+    __syncthreads();
+    // The trailing update runs on the 12 warps that do not share warp 0's scheduler
+    // (warp w issues from sub-partition w mod 4), so the latency-bound factorisation of
+    // the diagonal block is not slowed by their instructions.  They then form block row
+    // J of X = L^-1: it needs X above it, L's rows J .. J + 15 left of J (final since the
+    // previous panel) and X_JJ, and nothing that this step writes.
+    if (warp == 0) {
+      diag_block(s0);
+    } else if (warp & 3) {
+      constexpr int NTW = NW - NW / 4;
+      const int tw = warp - (warp >> 2) - 1;
+      for (int ip = tw; 2 * ip < LP - s0 - CB; ip += NTW) update_rows(J, s0 + CB + 2 * ip, s0 + lane, 32);
+      if (jb >= 1) {
+        const int tt = tw * 32 + lane;
+        inverse_s(J, tt, NTW * 32);
+        asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");   // the trailing warps only
+        inverse_x(J, tt, NTW * 32);
       }
     }
     __syncthreads();
   }
 
-  // outputs: R = L^T, R^-1 = X^T restricted to l x l; rows by warps
+  // the last block row of the inverse
+  inverse_s(CB * (NB - 1), tid, 512);
+  __syncthreads();
+  inverse_x(CB * (NB - 1), tid, 512);
+  __syncthreads();
+
+  // outputs: R = L^T, R^-1 = X^T restricted to l x l (and racc <- R when racc_init).  A
+  // thread reads four consecutive columns a of row b of L and X (lanes on consecutive
+  // rows: distinct banks) and writes them to rows a of the outputs (coalesced over b).
+  {
+    const bool rinit = racc != nullptr && racc_init;
+    for (int t = tid; t < LP * (LP / 4); t += 512) {
+      const int b = t % LP, a4 = 4 * (t / LP);
+      float4 lv = make_float4(0.f, 0.f, 0.f, 0.f), xv = lv;
+      if (a4 <= b && b < l) {
+        lv = *reinterpret_cast<const float4*>(arow(b) + a4);
+        xv = *reinterpret_cast<const float4*>(xrow(b) + a4);
+      }
+      const float lq[4] = {lv.x, lv.y, lv.z, lv.w}, xq[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    const int a = warp + NW * r;
-#pragma unroll
-    for (int c = 0; c < NCOL; ++c) {
-      const int b = lane + 32 * c;
-      if (b < LP) {
+      for (int q = 0; q < 4; ++q) {
+        const int a = a4 + q;
         const bool up = (a < l && b < l && b >= a);
-        r_out[a * LP + b] = up ? arow(b)[a] : 0.0f;
-        rinv[a * LP + b] = up ? xrow(b)[a] : 0.0f;
+        r_out[a * LP + b] = up ? lq[q] : 0.0f;
+        rinv[a * LP + b] = up ? xq[q] : 0.0f;
+        if (rinit) racc[a * LP + b] = up ? lq[q] : 0.0f;
       }
     }
+    if (rinit) return;
   }
   if (racc) {
-    if (racc_init) {
-#pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        const int a = warp + NW * r;
-#pragma unroll
-        for (int c = 0; c < NCOL; ++c) {
-          const int b = lane + 32 * c;
-          if (b < LP) racc[a * LP + b] = (a < l && b < l && b >= a) ? arow(b)[a] : 0.0f;
-        }
-      }
-      return;
-    }
     __syncthreads();
     // stage the old racc (upper, l x l) in the free X space, then racc <- R racc in
     // 1 x 4 strips: P(a, b0..b0+3) = sum_{a<=c<=b0+3} R(a, c) Ro(c, b0..b0+3)
@@ -819,11 +910,24 @@ __global__ void __launch_bounds__(512) cholesky_blocked_kernel(
     constexpr int NQ = LP / 4;
     for (int t = tid; t < LP * NQ; t += 512) {
       const int a = t / NQ, b0 = 4 * (t - a * NQ);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc;
       if (a < l && b0 + 3 >= a) {
         const int cend = min(b0 + 3, l - 1);
-        for (int c = a; c <= cend; ++c)
+        int c = a;
+        for (; c + 3 <= cend; c += 4) {   // four rows per step, all loads in flight
+          const float r0 = arow(c)[a], r1 = arow(c + 1)[a], r2 = arow(c + 2)[a], r3 = arow(c + 3)[a];
+          const float4 o0 = *reinterpret_cast<const float4*>(xrow(c) + b0);
+          const float4 o1 = *reinterpret_cast<const float4*>(xrow(c + 1) + b0);
+          const float4 o2 = *reinterpret_cast<const float4*>(xrow(c + 2) + b0);
+          const float4 o3 = *reinterpret_cast<const float4*>(xrow(c + 3) + b0);
+          acc = axpy4(r0, o0, acc);
+          acc1 = axpy4(r1, o1, acc1);
+          acc = axpy4(r2, o2, acc);
+          acc1 = axpy4(r3, o3, acc1);
+        }
+        for (; c <= cend; ++c)
           acc = axpy4(arow(c)[a], *reinterpret_cast<const float4*>(xrow(c) + b0), acc);
+        acc.x += acc1.x; acc.y += acc1.y; acc.z += acc1.z; acc.w += acc1.w;
       }
       float4 o;
       o.x = (a < l && b0 < l && b0 >= a) ? acc.x : 0.0f;
