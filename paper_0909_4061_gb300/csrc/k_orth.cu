@@ -601,6 +601,8 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   auto xrow = [&](int i) -> float* { return PACKED ? X + i * LP : X + i * LD; };
   auto alen = [&](int i) -> int { return PACKED ? CB * (i / CB + 1) : LP; };
   __shared__ float s_red[2][NW];
+  __shared__ __align__(16) float s_lt[CB][CB];   // L_JJ^T of the latest diagonal block
+  __shared__ __align__(16) float s_rpv[LP];      // 1 / L(j, j)
   __shared__ float s_shift, s_floor;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -657,11 +659,11 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   __syncthreads();
 
   // Diagonal block J (16 x 16) by warp 0: L_JJ by Cholesky in registers (lanes r and
-  // r + 16 both hold row r), then X_JJ = L_JJ^-1 by columns.  The pivot of step j + 1 is
-  // lane (j + 1)'s own A(j + 1, j + 1) - L(j + 1, j)^2, formed from its own L(j + 1, j) and
-  // broadcast first, so one shuffle per step lies on the chain of pivots; a floored pivot
-  // is reported once, after the loop.
-  auto diag_block = [&](int J) {
+  // r + 16 both hold row r), written to A, transposed to s_lt, its reciprocal pivots to
+  // s_rpv.  The pivot of step j + 1 is lane (j + 1)'s own A(j + 1, j + 1) - L(j + 1, j)^2,
+  // formed from its own L(j + 1, j) and broadcast first, so one shuffle per step lies on
+  // the chain of pivots; a floored pivot is reported once, after the loop.
+  auto diag_factor = [&](int J) {
     const int r = lane & 15;
     float a[CB], rpv[CB];
     {
@@ -694,23 +696,43 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       for (int k = j + 1; k < CB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), a[k]);
     }
     if (any_low && lane == 0) set_status(status, isnan(dlow) ? ST_NONFINITE : ST_RANK_DEFICIENT);
-    // X_JJ = L_JJ^-1 by columns: lane r holds column r, x[i] = X(i, r), zero for i < r
-    float x[CB];
-#pragma unroll
-    for (int i = 0; i < CB; ++i) {
-      float v0 = 0.0f, v1 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < i; ++k) {
-        const float lik = __shfl_sync(0xffffffffu, a[k], i);
-        if (k & 1) v1 = fmaf(lik, x[k], v1);
-        else v0 = fmaf(lik, x[k], v0);
-      }
-      x[i] = (i > r) ? -(v0 + v1) * rpv[i] : (i == r ? rpv[i] : 0.0f);
-    }
     if (lane < CB) {
       float4* dst = reinterpret_cast<float4*>(arow(J + r) + J);
 #pragma unroll
       for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+#pragma unroll
+      for (int c = 0; c < CB; ++c) s_lt[c][r] = a[c];
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(s_rpv + J + 4 * q) = make_float4(rpv[4 * q], rpv[4 * q + 1], rpv[4 * q + 2], rpv[4 * q + 3]);
+    }
+  };
+  // X_JJ = L_JJ^-1 by one warp, by columns: lane r holds column r, x[i] = X(i, r), zero for
+  // i < r, from the rows of L_JJ in A and the reciprocal pivots.
+  auto xjj_block = [&](int J) {
+    const int r = lane & 15;
+    float x[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      const float4* li = reinterpret_cast<const float4*>(arow(J + i) + J);
+      float lrow[CB];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = li[q];
+        lrow[4 * q] = t.x; lrow[4 * q + 1] = t.y; lrow[4 * q + 2] = t.z; lrow[4 * q + 3] = t.w;
+      }
+      float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        if (k & 1) v1 = fmaf(lrow[k], x[k], v1);
+        else v0 = fmaf(lrow[k], x[k], v0);
+      }
+      const float rp = s_rpv[J + i];
+      x[i] = (i > r) ? -(v0 + v1) * rp : (i == r ? rp : 0.0f);
+    }
+    if (lane < CB) {
 #pragma unroll
       for (int i = 0; i < CB; ++i) xrow(J + i)[J + r] = x[i];
     }
@@ -802,23 +824,40 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   // J and the update of the next diagonal block, warp 0 factors that block while the
   // other warps update the rest of the trailing triangle and form block row J of the
   // inverse.
-  if (warp == 0) diag_block(0);
+  if (warp == 0) diag_factor(0);
   __syncthreads();
 #pragma unroll 1
   for (int jb = 0; jb + 1 < NB; ++jb) {
     const int J = jb * CB, s0 = J + CB;
-    // panel, in place: L_iJ(c) = sum_k A_iJ(k) X_JJ(c, k); a half-warp per row
-    {
-      const int c = tid & 15;
-      const float4* xc = reinterpret_cast<const float4*>(xrow(J + c) + J);
-      const float4 x0 = xc[0], x1 = xc[1], x2 = xc[2], x3 = xc[3];
-      for (int i = s0 + (tid >> 4); i < LP; i += 32) {
-        float* ai = arow(i) + J;
-        const float4* a4 = reinterpret_cast<const float4*>(ai);
-        const float v = dot4(a4[0], x0, dot4(a4[2], x2, 0.0f)) + dot4(a4[1], x1, dot4(a4[3], x3, 0.0f));
-        __syncwarp();
-        ai[c] = v;
+    // panel, in place: L_iJ = A_iJ L_JJ^-T by forward substitution, one thread per row
+    for (int i = s0 + tid; i < LP; i += 512) {
+      float* ai = arow(i) + J;
+      float a[CB], rp[CB];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = reinterpret_cast<const float4*>(ai)[q];
+        a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+        const float4 u = reinterpret_cast<const float4*>(s_rpv + J)[q];
+        rp[4 * q] = u.x; rp[4 * q + 1] = u.y; rp[4 * q + 2] = u.z; rp[4 * q + 3] = u.w;
       }
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const float lc = a[c] * rp[c];
+        a[c] = lc;
+        if (c + 1 < CB) {
+          float lt[CB];   // column c of L_JJ
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 t = reinterpret_cast<const float4*>(s_lt[c < CB - 1 ? c : 0])[q];
+            lt[4 * q] = t.x; lt[4 * q + 1] = t.y; lt[4 * q + 2] = t.z; lt[4 * q + 3] = t.w;
+          }
+#pragma unroll
+          for (int c2 = c + 1; c2 < CB; ++c2) a[c2] = fmaf(-lc, lt[c2], a[c2]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(ai)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
     }
     __syncthreads();
     // the next diagonal block's lower triangle (136 entries), one per thread
@@ -833,28 +872,37 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       arow(s0 + i)[s0 + k] -= v;
     }
     __syncthreads();
-    // The trailing update runs on the 12 warps that do not share warp 0's scheduler
+    // The trailing update runs on 11 of the 12 warps that do not share warp 0's scheduler
     // (warp w issues from sub-partition w mod 4), so the latency-bound factorisation of
-    // the diagonal block is not slowed by their instructions.  They then form block row
-    // J of X = L^-1: it needs X above it, L's rows J .. J + 15 left of J (final since the
-    // previous panel) and X_JJ, and nothing that this step writes.
+    // the diagonal block is not slowed by their instructions; the twelfth inverts L_JJ.
+    // They then form block row J of X = L^-1: it needs X above it, L's rows J .. J + 15
+    // left of J (final since the previous panel) and X_JJ, and nothing that this step
+    // writes.
     if (warp == 0) {
-      diag_block(s0);
+      diag_factor(s0);
     } else if (warp & 3) {
       constexpr int NTW = NW - NW / 4;
       const int tw = warp - (warp >> 2) - 1;
-      for (int ip = tw; 2 * ip < LP - s0 - CB; ip += NTW) update_rows(J, s0 + CB + 2 * ip, s0 + lane, 32);
+      if (tw == 0) {
+        xjj_block(J);
+      } else {
+        for (int ip = tw - 1; 2 * ip < LP - s0 - CB; ip += NTW - 1)
+          update_rows(J, s0 + CB + 2 * ip, s0 + lane, 32);
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");   // the trailing warps only
       if (jb >= 1) {
         const int tt = tw * 32 + lane;
         inverse_s(J, tt, NTW * 32);
-        asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");   // the trailing warps only
+        asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");
         inverse_x(J, tt, NTW * 32);
       }
     }
     __syncthreads();
   }
 
-  // the last block row of the inverse
+  // the last diagonal block and block row of the inverse
+  if (warp == 0) xjj_block(CB * (NB - 1));
+  __syncthreads();
   inverse_s(CB * (NB - 1), tid, 512);
   __syncthreads();
   inverse_x(CB * (NB - 1), tid, 512);
