@@ -20,10 +20,12 @@
 // and raise a flag, and the finishing CTA adds them in CTA order
 // (deterministic) and clears the flags.
 //
-// Warp roles (192 threads): warp 0 issues TMA, warp 1 owns tensor memory and
-// issues the MMAs from one thread, warps 2-5 drain the accumulator (each
-// warp reads the 32 TMEM lanes its index allows).  Every wait is bounded; on
-// expiry the kernel records a timeout in the status word and winds down.
+// Warp roles (64 + 128 TM threads): warp 0 issues TMA, warp 1 owns tensor memory
+// and issues the MMAs from one thread, the 4 TM warps from 2 on drain the
+// accumulators (each warp reads the 32 TMEM lanes its index allows).  With TM = 2 a
+// work unit is two 128-row tiles that share every X tile (two MMAs per k step into
+// two accumulators), which halves the operand's re-reads from L2.  Every wait is
+// bounded; on expiry the kernel records a timeout in the status word and winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -35,7 +37,9 @@ namespace rsvd {
 namespace {
 
 using namespace tcx;
-constexpr int kThreads = 192;
+constexpr int kThreads = 192;   // TM = 1
+template <int TM>
+constexpr int threads_for() { return 64 + 128 * TM; }
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -45,8 +49,9 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void epi_bar() {  // the 4 epilogue warps only
-  asm volatile("bar.sync 1, 128;" ::: "memory");
+template <int TM>
+__device__ __forceinline__ void epi_bar() {  // the epilogue warps only
+  asm volatile("bar.sync 1, %0;" ::"n"(128 * TM) : "memory");
 }
 
 struct Range {
@@ -65,8 +70,8 @@ struct Range {
 // residual lo = A - hi (map_alo); each stage carries both tiles and the MMAs of
 // the lo tile accumulate into the same tensor-memory accumulator, so the pass
 // sees A to about 16 significant bits.
-template <int MODE, int HILO = 0>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int MODE, int HILO = 0, int TM = 1>
+__global__ void __launch_bounds__(64 + 128 * TM, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
                      const __grid_constant__ CUtensorMap map_alo,
                      const __grid_constant__ CUtensorMap map_x, float* __restrict__ y, int lp,
@@ -84,15 +89,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  constexpr uint32_t a_bytes = BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
+  static_assert(TM == 1 || !HILO, "the residual of A is read with single tiles");
+  constexpr uint32_t a_bytes = TM * BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
   const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
   const uint32_t stage_bytes = a_bytes + x_bytes;
   // two accumulators when they fit tensor memory (512 columns): the MMAs of the next row
   // tile then run while the epilogue drains the previous one
   const uint32_t acc_cols = (uint32_t)((n_total + 31) & ~31);
-  const int nacc = (2 * acc_cols <= 512) ? 2 : 1;
+  const uint32_t unit_cols = (uint32_t)TM * acc_cols;   // the accumulators of one work unit
+  const int nacc = (2 * unit_cols <= 512) ? 2 : 1;
   uint32_t tmem_cols = 32;
-  while (tmem_cols < acc_cols * nacc) tmem_cols <<= 1;
+  while (tmem_cols < unit_cols * nacc) tmem_cols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&bar_acc_full[a], 1);
-      mbar_init(&bar_acc_empty[a], 4);
+      mbar_init(&bar_acc_empty[a], 4 * TM);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -126,6 +133,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
+      // A is streamed once per pass; the operand tiles are read again by every row tile
+      const uint64_t pol_a = l2_evict_first_policy(), pol_x = l2_evict_last_policy();
       int64_t i = 0;
       for (int64_t it = it0; it < it1; ++it, ++i) {
         const int s = (int)(i % stages);
@@ -136,17 +145,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(&bar_full[s], stage_bytes);
         const int t = (int)(it / kt), kk = (int)(it % kt);
         if (MODE == 0) {
-          tma_load_2d(sa, &map_a, &bar_full[s], kk * BK, t * BM);
+#pragma unroll
+          for (int h = 0; h < TM; ++h)
+            tma_load_2d_hint(sa + h * 16384, &map_a, &bar_full[s], kk * BK, (t * TM + h) * BM, pol_a);
         } else {
-          tma_load_2d(sa, &map_a, &bar_full[s], t * BM, kk * BK);
-          tma_load_2d(sa + 8192, &map_a, &bar_full[s], t * BM + 64, kk * BK);
+#pragma unroll
+          for (int h = 0; h < TM; ++h) {
+            tma_load_2d_hint(sa + h * 16384, &map_a, &bar_full[s], (t * TM + h) * BM, kk * BK, pol_a);
+            tma_load_2d_hint(sa + h * 16384 + 8192, &map_a, &bar_full[s], (t * TM + h) * BM + 64,
+                             kk * BK, pol_a);
+          }
           if (HILO) {
-            tma_load_2d(sa + 16384, &map_alo, &bar_full[s], t * BM, kk * BK);
-            tma_load_2d(sa + 16384 + 8192, &map_alo, &bar_full[s], t * BM + 64, kk * BK);
+            tma_load_2d_hint(sa + 16384, &map_alo, &bar_full[s], t * BM, kk * BK, pol_a);
+            tma_load_2d_hint(sa + 16384 + 8192, &map_alo, &bar_full[s], t * BM + 64, kk * BK, pol_a);
           }
         }
         for (int c = 0; c * 256 < n_total; ++c)
-          tma_load_2d(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256);
+          tma_load_2d_hint(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256, pol_x);
       }
       // let the copies still in flight land before the CTA can exit
       const int64_t issued = i;
@@ -168,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int t = (int)(it / kt);
         const int64_t seg_end = min(it1, (int64_t)(t + 1) * kt);
         const int ab = seg % nacc;
-        const uint32_t acc = tmem + (uint32_t)ab * acc_cols;
+        const uint32_t acc = tmem + (uint32_t)ab * unit_cols;
         if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(seg / nacc) & 1u) ^ 1u, abort_flag, status)) break;
         tc_fence_after();
         for (; it < seg_end; ++it, ++i) {
@@ -181,18 +196,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool first = (it == (int64_t)t * kt) || (it == it0);
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
-            uint64_t adesc;
-            if (MODE == 0)
-              adesc = smem_desc(sa + j * 32, 16, 1024);           // K-major: +32 B per k16
-            else
-              adesc = smem_desc(sa + j * 2048, 8192, 1024);       // MN-major: +16 rows of 128 B
-            for (int c = 0; c * 256 < n_total; ++c) {
-              const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
-              const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
-              mma_bf16(acc + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
-              if (HILO) {
-                const uint64_t adesc_lo = smem_desc(sa + 16384 + j * 2048, 8192, 1024);
-                mma_bf16(acc + c * 256, adesc_lo, bdesc, idesc, 1u);
+#pragma unroll
+            for (int h = 0; h < TM; ++h) {
+              uint64_t adesc;
+              if (MODE == 0)
+                adesc = smem_desc(sa + h * 16384 + j * 32, 16, 1024);       // K-major: +32 B per k16
+              else
+                adesc = smem_desc(sa + h * 16384 + j * 2048, 8192, 1024);   // MN-major: +16 rows of 128 B
+              for (int c = 0; c * 256 < n_total; ++c) {
+                const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
+                const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
+                mma_bf16(acc + h * acc_cols + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
+                if (HILO) {
+                  const uint64_t adesc_lo = smem_desc(sa + 16384 + j * 2048, 8192, 1024);
+                  mma_bf16(acc + c * 256, adesc_lo, bdesc, idesc, 1u);
+                }
               }
             }
           }
@@ -202,10 +220,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2 .. 1 + 4 TM) ----------------
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+    const int half = (warp - 2) >> 2;   // which 128-row tile of the unit
+    const int row = half * BM + quad * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)half * acc_cols;
     int seg = 0;
     for (int64_t it = it0; it < it1; ++seg) {
       const int t = (int)(it / kt);
@@ -216,8 +235,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  mbar_wait(&bar_acc_full[seg % nacc], (uint32_t)(seg / nacc) & 1u,
                                            abort_flag, status));
       tc_fence_after();
-      const uint32_t tb = tbase + (uint32_t)(seg % nacc) * acc_cols;
-      const int64_t grow = (int64_t)t * BM + row;
+      const uint32_t tb = tbase + (uint32_t)(seg % nacc) * unit_cols;
+      const int64_t grow = (int64_t)t * (BM * TM) + row;
       const bool valid_row = grow < M;
       const bool direct = (c_first == c_last);
       const bool finisher = !direct && (cta == c_first);
@@ -249,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (direct || finisher) {
           if (finisher) {
             for (int c = c_first + 1; c <= c_last; ++c) {
-              const float4* src = reinterpret_cast<const float4*>(slots + ((size_t)c * BM + row) * lp + c0);
+              const float4* src = reinterpret_cast<const float4*>(slots + ((size_t)c * BM * TM + row) * lp + c0);
 #pragma unroll
               for (int q = 0; q < 32; q += 4) {
                 if (q < ncol) {
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (q < ncol)
               *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
         } else {
-          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)cta * BM + row) * lp + c0);
+          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)cta * BM * TM + row) * lp + c0);
 #pragma unroll
           for (int q = 0; q < 32; q += 4)
             if (q < ncol) dst[q >> 2] = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
@@ -275,10 +294,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!direct && !finisher) {
         // publish this CTA's partial of tile t (its first segment)
         __threadfence();
-        epi_bar();
+        epi_bar<TM>();
         if (warp == 2 && lane == 0) st_release(flags + cta, 1u);
       } else if (finisher) {
-        epi_bar();  // all rows have read the partials
+        epi_bar<TM>();  // all rows have read the partials
         if (warp == 2 && lane == 0)
           for (int c = c_first + 1; c <= c_last; ++c) flags[c] = 0u;
       }
@@ -314,8 +333,15 @@ size_t smem_bytes(int n_total, int stages, int a_tiles = 1) {
   return (size_t)stages * ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
 }
 
+// Widest operand (columns) for which a work unit takes two row tiles: two double-buffered
+// accumulators of 128 columns fill the 512 columns of tensor memory.
+constexpr int kPairMaxN = 128;
+
+constexpr int kStageBudget = 200 * 1024;
+constexpr int kPassSmemCap = kStageBudget + 4096;   // stages plus the 1 KB alignment pad
+
 int pick_stages(int n_total, int a_tiles = 1) {
-  const size_t budget = 200 * 1024;
+  const size_t budget = kStageBudget;
   int s = (int)(budget / ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2));
   if (s > 8) s = 8;
   return s < 2 ? 2 : s;
@@ -374,7 +400,7 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
   if (tc_encode_2d(tc->map_x_t2, xbf, m, tc_lo_offset(lp) + lp, ldm, BK, nf > 256 ? 256 : nf)) return -1;
   TcBuffers* b = new TcBuffers();
   b->grid = num_sms;
-  if (cudaMalloc(&b->slots, sizeof(float) * (size_t)num_sms * BM * lp) != cudaSuccess ||
+  if (cudaMalloc(&b->slots, sizeof(float) * (size_t)num_sms * 2 * BM * lp) != cudaSuccess ||
       cudaMalloc(&b->flags, sizeof(uint32_t) * (size_t)num_sms) != cudaSuccess ||
       cudaMemset(b->flags, 0, sizeof(uint32_t) * (size_t)num_sms) != cudaSuccess) {
     cudaGetLastError();
@@ -384,21 +410,15 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
     return -1;
   }
   tc->priv = b;
-  // the attribute must cover the largest of the launch configurations used
-  size_t sm = 0;
-  for (int n_total : {lp, fold_ntotal(lp)}) {
-    const size_t need = smem_bytes(n_total, pick_stages(n_total));
-    if (need > sm) sm = need;
-  }
-  if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess ||
-      cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm) != cudaSuccess)
-    return -1;
-  const int nf2 = fold_ntotal(lp);
-  if (cudaFuncSetAttribute(sketch_tc_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes(nf2, pick_stages(nf2, 2), 2)) != cudaSuccess)
-    return -1;
+  // One limit for every pass kernel, above the stage budget of pick_stages: the attribute
+  // belongs to the kernel, not to this plan, so a later plan must not lower it under an
+  // earlier one.
+  for (const void* fn : {(const void*)sketch_tc_kernel<0>, (const void*)sketch_tc_kernel<1>,
+                         (const void*)sketch_tc_kernel<1, 1>, (const void*)sketch_tc_kernel<0, 0, 2>,
+                         (const void*)sketch_tc_kernel<1, 0, 2>})
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmemCap) !=
+        cudaSuccess)
+      return -1;
   tc->ready = true;
   return 0;
 }
@@ -429,10 +449,12 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
   const int64_t M = trans ? tc->n : tc->m;
   const int64_t K = trans ? tc->m : tc->n;
   const int kt = (int)cdiv(K, BK);
-  const int64_t total = cdiv(M, BM) * kt;
+  // two row tiles per work unit while both accumulators stay double-buffered
+  const int tm = (!hilo && n_total <= kPairMaxN) ? 2 : 1;
+  const int64_t total = cdiv(M, (int64_t)BM * tm) * kt;
   const int grid = (int)(total < b->grid ? total : b->grid);
-  const int stages = pick_stages(n_total, hilo ? 2 : 1);
-  const size_t sm = smem_bytes(n_total, stages, hilo ? 2 : 1);
+  const int stages = pick_stages(n_total, hilo ? 2 : tm);
+  const size_t sm = smem_bytes(n_total, stages, hilo ? 2 : tm);
   const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(trans ? tc->map_a_t : tc->map_a_n);
   const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(hilo ? tc->map_a_lo : tc->map_a_t);
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
@@ -442,6 +464,14 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
     sketch_tc_kernel<1, 1><<<grid, kThreads, sm, st>>>(*ma, *malo, *mx, out, lp, M, kt, total,
                                                        n_total, split_x, lo_off, stages, b->slots,
                                                        b->flags, tc->status);
+  else if (tm == 2 && trans)
+    sketch_tc_kernel<1, 0, 2><<<grid, threads_for<2>(), sm, st>>>(
+        *ma, *ma, *mx, out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
+        tc->status);
+  else if (tm == 2)
+    sketch_tc_kernel<0, 0, 2><<<grid, threads_for<2>(), sm, st>>>(
+        *ma, *ma, *mx, out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
+        tc->status);
   else if (trans)
     sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, out, lp, M, kt, total, n_total,
                                                     split_x, lo_off, stages, b->slots, b->flags,
@@ -521,15 +551,11 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
     d.flags = static_cast<uint32_t*>(p);
     if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return -1;
-    size_t need = 0;
-    for (int l = 16; l <= kNoAllocMaxL; l += 16) {
-      const size_t s = smem_bytes(l, pick_stages(l));
-      if (s > need) need = s;
-    }
+    // the same limit as the plans set (never lower it under a live plan)
     if (cudaFuncSetAttribute(sketch_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)need) != cudaSuccess ||
+                             kPassSmemCap) != cudaSuccess ||
         cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)need) != cudaSuccess)
+                             kPassSmemCap) != cudaSuccess)
       return -1;
     d.ready = true;
   }
