@@ -389,10 +389,15 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
     TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(2), lp, 0, 0.f, P->sp(8), lp, P->st));
     TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(1), lp, 0, 0.f, P->sp(4), lp, P->st));
     TRY(launch_small_gemm(k, l, l, 1.f, P->sp(6), lp, 1, P->racc(), lp, 0, 0.f, P->sp(9), lp, P->st));
-    // singular bases of X1 (U1 = sp(10), s1) and X2 (U2 = sp(11), s2): k nonzero values each
-    TRY(launch_jacobi_svd(P->sp(3), lp, 0, l, lp, P->sp(10), P->sig2, P->sp(7), P->lbuf(), P->status,
+    // singular bases of X1 (U1 = sp(10), s1) and X2 (U2 = sp(11), s2): k nonzero values each.
+    // The one-sided Jacobi runs on X1^T and X2^T: their columns are the k rows of the k x l
+    // systems plus l - k zero columns that never rotate, where the l columns of X1 itself
+    // would be l vectors in a k-dimensional space, l - k of them rounding noise that no
+    // sweep can make orthogonal to the rest.  X^T = Ut S W^T gives X = W S Ut^T: the left
+    // singular vectors are the accumulated rotations W.
+    TRY(launch_jacobi_svd(P->sp(3), lp, 1, l, lp, P->sp(7), P->sig2, P->sp(10), P->lbuf(), P->status,
                           P->status + 1, P->st, P->opt.small_svd));
-    TRY(launch_jacobi_svd(P->sp(4), lp, 0, l, lp, P->sp(11), P->sig2 + lp, P->sp(7), P->lbuf(),
+    TRY(launch_jacobi_svd(P->sp(4), lp, 1, l, lp, P->sp(7), P->sig2 + lp, P->sp(11), P->lbuf(),
                           P->status, P->status + 1, P->st, P->opt.small_svd));
     // F = C1 X1^T + X2 C2^T; G = U2^T F U1; H = G ./ (s2^2 + s1^2); B = U2 H U1^T (all k x k)
     TRY(launch_small_gemm(k, k, l, 1.f, P->sp(8), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), lp, P->st));
