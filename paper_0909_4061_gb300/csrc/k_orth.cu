@@ -182,6 +182,22 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
   float* Rs = sm;                                 // R^-1, LP x LDQ (APPLY)
   float* Ub = sm + (APPLY ? LP * LDQ : 0);        // Y^T (LP x TR_LDT), then Q (TR_ROWS x LDQ)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
+  // With APPLY, Y comes from the Cholesky-QR round before the factorisation this launch
+  // depends on (two or more launches back): the first tile's loads go out before the wait.
+  float4 vpre[8];
+  if (APPLY) {
+    const int nr0 = (int)min((int64_t)TR_ROWS, r1 - r0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int s = warp + NP * k, rg = s & 7, cg = s >> 3;
+      const int r = 8 * rg + (lane & 7), c4 = 4 * cg + (lane >> 3);
+      vpre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < nr0) vpre[k] = *reinterpret_cast<const float4*>(y + (r0 + r) * LP + 4 * c4);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
   if (APPLY) {   // R^-1 into shared memory, waited for with the first tile of Y
     for (int e = tid; e < LP * NC4; e += T) {
       const int r = e / NC4, c4 = e - r * NC4;
@@ -202,7 +218,6 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
 #pragma unroll
     for (int c = 0; c < TW; ++c) g[p][c] = 0ull;
   const int cb0 = warp, cb1 = NCB - 1 - warp;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
   for (int64_t rb = r0; rb < r1; rb += TR_ROWS) {
     const int nr = (int)min((int64_t)TR_ROWS, r1 - rb);
     __syncthreads();   // the previous tile is no longer read
@@ -215,8 +230,11 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
         for (int k = 0; k < 8; ++k) {
           const int s = warp + NP * k, rg = s & 7, cg = s >> 3;
           const int r = 8 * rg + (lane & 7), c4 = 4 * cg + (lane >> 3);
-          v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r < nr) v[k] = *reinterpret_cast<const float4*>(y + (rb + r) * LP + 4 * c4);
+          v[k] = vpre[k];
+          if (rb != r0) {
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < nr) v[k] = *reinterpret_cast<const float4*>(y + (rb + r) * LP + 4 * c4);
+          }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -359,6 +377,8 @@ __global__ void __launch_bounds__(TriCfg<LP, APPLY>::T, (LP >= 128 ? 1 : 2))
 __global__ void __launch_bounds__(512) gram_reduce_kernel(const float* __restrict__ gpart, int nblk,
                                                           int lp, float* __restrict__ g) {
   __shared__ float s_sum[kRedSplit][32], s_cmp[kRedSplit][32];
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = (int64_t)lp * lp;
   const int64_t e = (int64_t)blockIdx.x * 32 + lane;
@@ -607,6 +627,8 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
+  pdl_wait();
+  pdl_trigger();
   // load the lower triangle of G (identity beyond l), all loads in flight together
   float tr = 0.0f, mx = 0.0f;
   bool bad = false;
@@ -1083,11 +1105,11 @@ cudaError_t launch_tri(const float* y, int splits, int64_t split_stride, float* 
                        int lp, const float* rinv, float* gpart, int nblk, int do_gram,
                        cudaStream_t st) {
   const int64_t rpb = round_up(cdiv(rows, nblk), TR_ROWS);
-#define RSVD_TRI_CASE(LP)                                                                    \
-  case LP:                                                                                  \
-    orth_tri_kernel<LP, APPLY><<<nblk, TriCfg<LP, APPLY>::T, TriCfg<LP, APPLY>::SMEM, st>>>( \
-        y, splits, split_stride, q, rows, rinv, gpart, rpb, do_gram);                       \
-    return cudaGetLastError();
+#define RSVD_TRI_CASE(LP)                                                                     \
+  case LP:                                                                                   \
+    return launch_pdl(orth_tri_kernel<LP, APPLY>, dim3(nblk), dim3(TriCfg<LP, APPLY>::T),    \
+                      (size_t)TriCfg<LP, APPLY>::SMEM, st, y, splits, split_stride, q, rows, rinv, \
+                      gpart, rpb, do_gram);
   switch (lp) {
     RSVD_TRI_CASE(16) RSVD_TRI_CASE(32) RSVD_TRI_CASE(48) RSVD_TRI_CASE(64)
     RSVD_TRI_CASE(80) RSVD_TRI_CASE(96) RSVD_TRI_CASE(112) RSVD_TRI_CASE(128)
@@ -1145,8 +1167,8 @@ cudaError_t launch_gram_tri(const float* src, int splits, int64_t split_stride, 
 
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st) {
   const int64_t n = (int64_t)lp * lp;
-  gram_reduce_kernel<<<(unsigned)cdiv(n, 32), 512, 0, st>>>(gpart, nblk, lp, g);
-  return cudaGetLastError();
+  return launch_pdl(gram_reduce_kernel, dim3((unsigned)cdiv(n, 32)), dim3(512), 0, st, gpart, nblk,
+                    lp, g);
 }
 
 cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,
@@ -1155,10 +1177,8 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
   if (lp <= 256 && lp % CB == 0 && lbuf) {
 #define RSVD_CHOL_CASE(NB)                                                                  \
   case NB:                                                                                 \
-    cholesky_blocked_kernel<NB><<<1, 512, chol_smem<NB>(), st>>>(g, l, shifted, r_out, rinv, \
-                                                                 racc, racc_init, status,  \
-                                                                 lbuf);                    \
-    return cudaGetLastError();
+    return launch_pdl(cholesky_blocked_kernel<NB>, dim3(1), dim3(512), chol_smem<NB>(), st, g, l, \
+                      shifted, r_out, rinv, racc, racc_init, status, lbuf);
     switch (lp / CB) {
       RSVD_CHOL_CASE(1) RSVD_CHOL_CASE(2) RSVD_CHOL_CASE(3) RSVD_CHOL_CASE(4) RSVD_CHOL_CASE(5)
       RSVD_CHOL_CASE(6) RSVD_CHOL_CASE(7) RSVD_CHOL_CASE(8) RSVD_CHOL_CASE(9) RSVD_CHOL_CASE(10)
