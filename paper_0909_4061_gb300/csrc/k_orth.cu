@@ -1013,6 +1013,8 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int 
                                  __nv_bfloat16* __restrict__ out, int64_t ld_t, int split,
                                  int lo_off) {
   __shared__ float tile[32][33];
+  pdl_wait();
+  pdl_trigger();
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -1197,8 +1199,7 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
 cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16* out, int64_t ld_t,
                              int split, int lo_off, cudaStream_t st) {
   const dim3 grid((unsigned)cdiv(rows, 32), (unsigned)cdiv(lp, 32));
-  to_bf16_t_kernel<<<grid, dim3(32, 8), 0, st>>>(x, rows, lp, out, ld_t, split, lo_off);
-  return cudaGetLastError();
+  return launch_pdl(to_bf16_t_kernel, grid, dim3(32, 8), 0, st, x, rows, lp, out, ld_t, split, lo_off);
 }
 
 cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,

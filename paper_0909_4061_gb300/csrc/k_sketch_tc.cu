@@ -135,33 +135,51 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
     if (lane == 0) {
       // A is streamed once per pass; the operand tiles are read again by every row tile
       const uint64_t pol_a = l2_evict_first_policy(), pol_x = l2_evict_last_policy();
-      int64_t i = 0;
-      for (int64_t it = it0; it < it1; ++it, ++i) {
-        const int s = (int)(i % stages);
-        const uint32_t ph = (uint32_t)((i / stages) & 1);
-        if (!mbar_wait(&bar_empty[s], ph ^ 1u, abort_flag, status)) break;
+      // the A tiles (both halves with TM = 2, and the residual with HILO) and the operand
+      // tile of iteration `it` into stage s
+      auto load_a = [&](int64_t it, int s) {
         uint8_t* sa = smem + (size_t)s * stage_bytes;
-        uint8_t* sx = sa + a_bytes;
-        mbar_expect_tx(&bar_full[s], stage_bytes);
+        uint64_t* bar = &bar_full[s];
         const int t = (int)(it / kt), kk = (int)(it % kt);
         if (MODE == 0) {
 #pragma unroll
           for (int h = 0; h < TM; ++h)
-            tma_load_2d_hint(sa + h * 16384, &map_a, &bar_full[s], kk * BK, (t * TM + h) * BM, pol_a);
+            tma_load_2d_hint(sa + h * 16384, &map_a, bar, kk * BK, (t * TM + h) * BM, pol_a);
         } else {
 #pragma unroll
           for (int h = 0; h < TM; ++h) {
-            tma_load_2d_hint(sa + h * 16384, &map_a, &bar_full[s], (t * TM + h) * BM, kk * BK, pol_a);
-            tma_load_2d_hint(sa + h * 16384 + 8192, &map_a, &bar_full[s], (t * TM + h) * BM + 64,
-                             kk * BK, pol_a);
+            tma_load_2d_hint(sa + h * 16384, &map_a, bar, (t * TM + h) * BM, kk * BK, pol_a);
+            tma_load_2d_hint(sa + h * 16384 + 8192, &map_a, bar, (t * TM + h) * BM + 64, kk * BK, pol_a);
           }
           if (HILO) {
-            tma_load_2d_hint(sa + 16384, &map_alo, &bar_full[s], t * BM, kk * BK, pol_a);
-            tma_load_2d_hint(sa + 16384 + 8192, &map_alo, &bar_full[s], t * BM + 64, kk * BK, pol_a);
+            tma_load_2d_hint(sa + 16384, &map_alo, bar, t * BM, kk * BK, pol_a);
+            tma_load_2d_hint(sa + 16384 + 8192, &map_alo, bar, t * BM + 64, kk * BK, pol_a);
           }
         }
+      };
+      auto load_x = [&](int64_t it, int s) {
+        uint8_t* sx = smem + (size_t)s * stage_bytes + a_bytes;
+        const int kk = (int)(it % kt);
         for (int c = 0; c * 256 < n_total; ++c)
           tma_load_2d_hint(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256, pol_x);
+      };
+      // A is an input of the whole call and is never written by it: the A tiles of the
+      // first stages go out before waiting for the launch that wrote the operand.
+      const int64_t npre = (it1 - it0 < stages) ? it1 - it0 : stages;
+      for (int64_t j = 0; j < npre; ++j) {
+        mbar_expect_tx(&bar_full[j], stage_bytes);
+        load_a(it0 + j, (int)j);
+      }
+      pdl_wait();
+      for (int64_t j = 0; j < npre; ++j) load_x(it0 + j, (int)j);
+      int64_t i = npre;
+      for (int64_t it = it0 + npre; it < it1; ++it, ++i) {
+        const int s = (int)(i % stages);
+        const uint32_t ph = (uint32_t)((i / stages) & 1);
+        if (!mbar_wait(&bar_empty[s], ph ^ 1u, abort_flag, status)) break;
+        mbar_expect_tx(&bar_full[s], stage_bytes);
+        load_a(it, s);
+        load_x(it, s);
       }
       // let the copies still in flight land before the CTA can exit
       const int64_t issued = i;
@@ -460,26 +478,27 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
       trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
   if (split_x && !trans) return -1;
+  // launched as a programmatic dependent: the A tiles of the first stages are loaded
+  // while the launch that converts the operand finishes
+  cudaError_t e;
   if (hilo)
-    sketch_tc_kernel<1, 1><<<grid, kThreads, sm, st>>>(*ma, *malo, *mx, out, lp, M, kt, total,
-                                                       n_total, split_x, lo_off, stages, b->slots,
-                                                       b->flags, tc->status);
+    e = launch_pdl(sketch_tc_kernel<1, 1>, dim3(grid), dim3(kThreads), sm, st, *ma, *malo, *mx, out, lp,
+                   M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
   else if (tm == 2 && trans)
-    sketch_tc_kernel<1, 0, 2><<<grid, threads_for<2>(), sm, st>>>(
-        *ma, *ma, *mx, out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
-        tc->status);
+    e = launch_pdl(sketch_tc_kernel<1, 0, 2>, dim3(grid), dim3(threads_for<2>()), sm, st, *ma, *ma, *mx,
+                   out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
+                   tc->status);
   else if (tm == 2)
-    sketch_tc_kernel<0, 0, 2><<<grid, threads_for<2>(), sm, st>>>(
-        *ma, *ma, *mx, out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
-        tc->status);
+    e = launch_pdl(sketch_tc_kernel<0, 0, 2>, dim3(grid), dim3(threads_for<2>()), sm, st, *ma, *ma, *mx,
+                   out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
+                   tc->status);
   else if (trans)
-    sketch_tc_kernel<1><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, out, lp, M, kt, total, n_total,
-                                                    split_x, lo_off, stages, b->slots, b->flags,
-                                                    tc->status);
+    e = launch_pdl(sketch_tc_kernel<1>, dim3(grid), dim3(kThreads), sm, st, *ma, *ma, *mx, out, lp, M,
+                   kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
   else
-    sketch_tc_kernel<0><<<grid, kThreads, sm, st>>>(*ma, *ma, *mx, out, lp, M, kt, total, n_total,
-                                                    split_x, lo_off, stages, b->slots, b->flags,
-                                                    tc->status);
+    e = launch_pdl(sketch_tc_kernel<0>, dim3(grid), dim3(kThreads), sm, st, *ma, *ma, *mx, out, lp, M,
+                   kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
+  if (e != cudaSuccess) return -1;
   *splits = 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
