@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
 #pragma unroll
       for (int c = 0; c < NCOL; ++c) {
         const int i = warp + NW * (r0 + r), j = lane + 32 * c;
-        if (j < LP) {
+        if (i < LP && j < LP) {   // the last group of RCH row blocks may run past LP
           float w = v[r][c];
           if (i == j) {
             if (i < l) {
@@ -972,14 +972,15 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
     } else if (warp & 3) {
       constexpr int NTW = NW - NW / 4;
       const int tw = warp - (warp >> 2) - 1;
-      if (tw == 0) {
+      if (!PACKED && tw == 0) {
         xjj_block(J);
       } else {
-        for (int ip = tw - 1; 2 * ip < LP - s0 - CB; ip += NTW - 1)
-          update_rows(J, s0 + CB + 2 * ip, s0 + lane, 32);
+        // in the packed form L^-1 is formed by trinv_kernel afterwards: all 12 warps update
+        const int t0 = PACKED ? tw : tw - 1, ntr = PACKED ? NTW : NTW - 1;
+        for (int ip = t0; 2 * ip < LP - s0 - CB; ip += ntr) update_rows(J, s0 + CB + 2 * ip, s0 + lane, 32);
       }
       asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");   // the trailing warps only
-      if (jb >= 1) {
+      if (!PACKED && jb >= 1) {
         const int tt = tw * 32 + lane;
         inverse_s(J, tt, NTW * 32);
         asm volatile("bar.sync 1, %0;" ::"n"(NTW * 32) : "memory");
@@ -990,16 +991,19 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   }
 
   // the last diagonal block and block row of the inverse
-  if (warp == 0) xjj_block(CB * (NB - 1));
-  __syncthreads();
-  inverse_s(CB * (NB - 1), tid, 512);
-  __syncthreads();
-  inverse_x(CB * (NB - 1), tid, 512);
-  __syncthreads();
+  if (!PACKED) {
+    if (warp == 0) xjj_block(CB * (NB - 1));
+    __syncthreads();
+    inverse_s(CB * (NB - 1), tid, 512);
+    __syncthreads();
+    inverse_x(CB * (NB - 1), tid, 512);
+    __syncthreads();
+  }
 
   // outputs: R = L^T, R^-1 = X^T restricted to l x l (and racc <- R when racc_init).  A
   // thread reads four consecutive columns a of row b of L and X (lanes on consecutive
   // rows: distinct banks) and writes them to rows a of the outputs (coalesced over b).
+  // In the packed form R^-1 comes from trinv_kernel.
   {
     const bool rinit = racc != nullptr && racc_init;
     for (int t = tid; t < LP * (LP / 4); t += 512) {
@@ -1007,7 +1011,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       float4 lv = make_float4(0.f, 0.f, 0.f, 0.f), xv = lv;
       if (a4 <= b && b < l) {
         lv = *reinterpret_cast<const float4*>(arow(b) + a4);
-        xv = *reinterpret_cast<const float4*>(xrow(b) + a4);
+        if (!PACKED) xv = *reinterpret_cast<const float4*>(xrow(b) + a4);
       }
       const float lq[4] = {lv.x, lv.y, lv.z, lv.w}, xq[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
@@ -1015,7 +1019,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
         const int a = a4 + q;
         const bool up = (a < l && b < l && b >= a);
         r_out[a * LP + b] = up ? lq[q] : 0.0f;
-        rinv[a * LP + b] = up ? xq[q] : 0.0f;
+        if (!PACKED) rinv[a * LP + b] = up ? xq[q] : 0.0f;
         if (rinit) racc[a * LP + b] = up ? lq[q] : 0.0f;
       }
     }
@@ -1033,14 +1037,14 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
           const int i = warp + NW * (r0 + r), j = lane + 32 * c;
-          v[r][c] = (j < LP) ? racc[i * LP + j] : 0.0f;
+          v[r][c] = (i < LP && j < LP) ? racc[i * LP + j] : 0.0f;
         }
 #pragma unroll
       for (int r = 0; r < RCH; ++r)
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
           const int i = warp + NW * (r0 + r), j = lane + 32 * c;
-          if (j < LP) xrow(i)[j] = v[r][c];   // the old racc, staged where X was
+          if (i < LP && j < LP) xrow(i)[j] = v[r][c];   // the old racc, staged where X was
         }
     }
     __syncthreads();
@@ -1073,6 +1077,103 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       o.w = (a < l && b0 + 3 < l && b0 + 3 >= a) ? acc.w : 0.0f;
       *reinterpret_cast<float4*>(racc + a * LP + b0) = o;
     }
+  }
+}
+
+// X = L^-1 for the packed form (l_p > 160), from R = L^T (l_p x l_p, upper, zero beyond
+// l) after the factorisation: CTA c forms column block c of X (16 columns, rows 16 c ..
+// l_p - 1) by block forward substitution, X_cc = L_cc^-1 and
+//   X_Ic = -X_II sum_{c<=K<I} L_IK X_Kc,   I = c + 1 .. NB - 1,
+// and writes rows 16 c .. 16 c + 15 of R^-1 = X^T.  The diagonal inverses X_II come from
+// the rows of L_II by columns (one warp per block), with L treated as the identity beyond
+// l.  The column blocks are independent: NB CTAs run them side by side.
+template <int NB>
+__host__ __device__ constexpr int trinv_ldl() { return CB * (NB - 1) + 4; }
+template <int NB>
+constexpr size_t trinv_smem() {
+  return (size_t)(2 * NB * CB * CB + CB * trinv_ldl<NB>() + CB * CB) * sizeof(float);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256, 1) trinv_kernel(const float* __restrict__ r, int l,
+                                                    float* __restrict__ rinv) {
+  constexpr int LP = CB * NB, LDL = trinv_ldl<NB>();
+  extern __shared__ __align__(16) float tsm[];
+  const int c = blockIdx.x, nbr = NB - c;
+  float* Xs = tsm;                       // X(16 c + i, 16 c + t) at [i][t], i < 16 nbr
+  float* Xd = Xs + NB * CB * CB;         // X_II for I = c + ii at [ii][row][col]
+  float* Ls = Xd + NB * CB * CB;         // L(16 I + row, 16 c + k) at [row][k]
+  float* Ts = Ls + CB * LDL;             // 16 x 16
+  pdl_wait();
+  pdl_trigger();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rr = lane & 15;
+  for (int ii = warp; ii < nbr; ii += 8) {
+    const int I = c + ii;
+    float lrow[CB];   // row rr of L_II
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int gi = CB * I + rr, gj = CB * I + t;
+      float v = (t <= rr) ? r[(int64_t)gj * LP + gi] : 0.0f;
+      if (gi >= l || gj >= l) v = (gi == gj) ? 1.0f : 0.0f;
+      lrow[t] = v;
+    }
+    // lane rr forms column rr of X_II: x[i] = X(i, rr), zero above the diagonal
+    float x[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        const float lik = __shfl_sync(0xffffffffu, lrow[k], i);
+        if (k & 1) v1 = fmaf(lik, x[k], v1);
+        else v0 = fmaf(lik, x[k], v0);
+      }
+      const float lii = __shfl_sync(0xffffffffu, lrow[i], i);
+      x[i] = (i > rr) ? -(v0 + v1) / lii : (i == rr ? 1.0f / lii : 0.0f);
+    }
+    if (lane < CB) {
+#pragma unroll
+      for (int i = 0; i < CB; ++i) Xd[(ii * CB + i) * CB + rr] = x[i];
+    }
+  }
+  __syncthreads();
+  Xs[tid] = Xd[tid];   // X_cc (256 threads, 16 x 16)
+  __syncthreads();
+  for (int ii = 1; ii < nbr; ++ii) {
+    const int I = c + ii, kw = CB * ii;
+    for (int e = tid; e < kw * CB; e += 256) {   // L_{I, c .. I-1}, read along rows of R
+      const int k = e >> 4, q = e & 15;
+      Ls[q * LDL + k] = r[(int64_t)(CB * c + k) * LP + CB * I + q];
+    }
+    __syncthreads();
+    {
+      const int q = tid >> 4, t = tid & 15;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int k = 0; k < kw; k += 4) {
+        s0 = fmaf(Ls[q * LDL + k], Xs[k * CB + t], s0);
+        s1 = fmaf(Ls[q * LDL + k + 1], Xs[(k + 1) * CB + t], s1);
+        s2 = fmaf(Ls[q * LDL + k + 2], Xs[(k + 2) * CB + t], s2);
+        s3 = fmaf(Ls[q * LDL + k + 3], Xs[(k + 3) * CB + t], s3);
+      }
+      Ts[q * CB + t] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    {
+      const int q = tid >> 4, t = tid & 15;
+      float s = 0.0f;
+#pragma unroll
+      for (int u = 0; u < CB; ++u) s = fmaf(Xd[(ii * CB + q) * CB + u], Ts[u * CB + t], s);
+      Xs[(kw + q) * CB + t] = -s;
+    }
+    __syncthreads();
+  }
+  // rows 16 c .. 16 c + 15 of R^-1: R^-1(a, b) = X(b, a) for a <= b < l
+  for (int e = tid; e < CB * LP; e += 256) {
+    const int t = e / LP, b = e - t * LP, a = CB * c + t;
+    float v = 0.0f;
+    if (a < l && b < l && b >= a) v = Xs[(b - CB * c) * CB + t];
+    rinv[(int64_t)a * LP + b] = v;
   }
 }
 
@@ -1155,8 +1256,11 @@ size_t chol_smem() {
 
 template <int NB>
 cudaError_t prep_chol() {
-  return cudaFuncSetAttribute(cholesky_blocked_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)chol_smem<NB>());
+  cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel<NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem<NB>());
+  if (e != cudaSuccess || NB <= 10) return e;
+  return cudaFuncSetAttribute(trinv_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)trinv_smem<NB>());
 }
 
 template <int LP>
@@ -1245,9 +1349,13 @@ cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* l
                             cudaStream_t st) {
   if (lp <= 256 && lp % CB == 0 && lbuf) {
 #define RSVD_CHOL_CASE(NB)                                                                  \
-  case NB:                                                                                 \
-    return launch_pdl(cholesky_blocked_kernel<NB>, dim3(1), dim3(512), chol_smem<NB>(), st, g, l, \
-                      shifted, r_out, rinv, racc, racc_init, status, lbuf);
+  case NB: {                                                                               \
+    cudaError_t e = launch_pdl(cholesky_blocked_kernel<NB>, dim3(1), dim3(512), chol_smem<NB>(), st, \
+                               g, l, shifted, r_out, rinv, racc, racc_init, status, lbuf);  \
+    if (e != cudaSuccess || NB <= 10) return e;                                            \
+    return launch_pdl(trinv_kernel<NB>, dim3(NB), dim3(256), trinv_smem<NB>(), st,          \
+                      (const float*)r_out, l, rinv);                                       \
+  }
     switch (lp / CB) {
       RSVD_CHOL_CASE(1) RSVD_CHOL_CASE(2) RSVD_CHOL_CASE(3) RSVD_CHOL_CASE(4) RSVD_CHOL_CASE(5)
       RSVD_CHOL_CASE(6) RSVD_CHOL_CASE(7) RSVD_CHOL_CASE(8) RSVD_CHOL_CASE(9) RSVD_CHOL_CASE(10)
