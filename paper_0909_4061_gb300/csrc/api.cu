@@ -250,11 +250,21 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     }
     return RSVD_OK;
   }
+  // Wider bases: Q = Y R^-1 by the float32 GEMM; on the tensor-core path the Gram partials
+  // are formed on the tensor cores too.  Their float32 accumulation is not IEEE-exact (about
+  // 1e-6 of |Y|^T |Y| against 1e-7 for float32 FMA), far below the bfloat16 rounding of A
+  // that the path already carries, but not float32-faithful: the plain float32 path keeps
+  // the FMA Gram.
+  const bool tc_gram = P->opt.precision == RSVD_BF16_TC;
+  const int gblk = tc_gram ? gram_tc_grid(rows, nblk) : nblk;
   for (int r = 0; r < rounds; ++r) {
     float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
-    TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
+    if (tc_gram)
+      TRY(launch_gram_tc(cur, cur_splits, stride, yout, rows, lp, P->gpart, gblk, P->status, P->st));
+    else
+      TRY(launch_gram_partial(cur, cur_splits, stride, yout, rows, lp, P->gpart, nblk, P->st));
     if (cur_splits > 1) cur = P->tmp1;
-    TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
+    TRY(launch_gram_reduce(P->gpart, gblk, lp, P->g(), P->st));
     const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
     TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
                         r == 0 ? 1 : 0, P->status, P->st));

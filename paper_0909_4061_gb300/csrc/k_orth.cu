@@ -8,9 +8,11 @@
 //   gram_reduce   : G = sum_b G_b in a fixed order with Kahan compensation
 //   cholesky      : G + s I = R^T R in one CTA (s = l u tr(G) in a shifted
 //                   round, else 0), pivots below l u max(diag G) replaced by
-//                   that floor (rank-deficient samples), then R^-1 by
-//                   column-oriented forward substitution
-//   apply         : Q = Y R^-1 (the float32 GEMM of k_gemm_simt.cu)
+//                   that floor and the column below them set to zero
+//                   (rank-deficient samples), then R^-1 by forward substitution
+//   apply         : Q = Y R^-1 (the float32 GEMM of k_gemm_simt.cu; fused with
+//                   the next Gram for l_p <= 128)
+// Wider samples (l_p > 128) form the Gram partials on the tensor cores (k_gram_tc.cu).
 #include <math.h>
 
 #include "common.cuh"
@@ -469,14 +471,18 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
   // 2. right-looking Cholesky, column by column
   for (int j = 0; j < l; ++j) {
     float d = Lp[tri_off(j) + j];
-    if (!(d > pfloor)) {
+    const bool low = !(d > pfloor);
+    if (low) {
       if (tid == 0) set_status(status, isnan(d) ? ST_NONFINITE : ST_RANK_DEFICIENT);
       d = pfloor;
     }
     const float piv = sqrtf(d);
-    const float rp = 1.0f / piv;
+    // below a floored pivot the column is rounding noise (|a_ij| <= sqrt(a_ii a_jj) for a
+    // semidefinite matrix): it is set to zero rather than scaled by 1 / sqrt(floor), which
+    // would feed that noise, enlarged, into every later pivot
+    const float cs = low ? 0.0f : 1.0f / piv;
     for (int i = j + 1 + tid; i < l; i += nt) {
-      const float v = Lp[tri_off(i) + j] * rp;
+      const float v = Lp[tri_off(i) + j] * cs;
       cvec[i] = v;
       Lp[tri_off(i) + j] = v;
     }
@@ -623,6 +629,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   __shared__ float s_red[2][NW];
   __shared__ __align__(16) float s_lt[CB][CB];   // L_JJ^T of the latest diagonal block
   __shared__ __align__(16) float s_rpv[LP];      // 1 / L(j, j)
+  __shared__ __align__(16) float s_csv[LP];      // scale of column j below the pivot (0 if floored)
   __shared__ float s_shift, s_floor;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -688,7 +695,9 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   bool any_low = false;
   float dlow = 0.0f;
   // Cholesky of the 8 x 8 lower triangle a (in place), pivots base .. base + 7
-  auto chol8 = [&](float (&a)[8][8], float (&rp8)[8], int base) {
+  // (rp8: reciprocal pivots; cs8: the scale of the column below each pivot, zero below a
+  // floored one, whose column is rounding noise)
+  auto chol8 = [&](float (&a)[8][8], float (&rp8)[8], float (&cs8)[8], int base) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       float d = a[j][j];
@@ -699,10 +708,12 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       // 1/sqrt(d) by the hardware estimate and one Newton step y <- y (3 - d y^2) / 2
       float rp = rsqrtf(d);
       rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);
+      const float cs = low ? 0.0f : rp;
       rp8[j] = rp;
+      cs8[j] = cs;
       a[j][j] = d * rp;
 #pragma unroll
-      for (int i = j + 1; i < 8; ++i) a[i][j] *= rp;
+      for (int i = j + 1; i < 8; ++i) a[i][j] *= cs;
 #pragma unroll
       for (int i = j + 1; i < 8; ++i)
 #pragma unroll
@@ -720,9 +731,9 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
     }
   };
   auto diag_factor = [&](int J) {
-    float l11[8][8], l22[8][8], rp1[8], rp2[8];
+    float l11[8][8], l22[8][8], rp1[8], rp2[8], cs1[8], cs2[8];
     load8(l11, J, J);
-    chol8(l11, rp1, J);
+    chol8(l11, rp1, cs1, J);
     // L21: lane i & 7 forms row 8 + (i & 7) by forward substitution with L11
     const int ri = lane & 7;
     float l21[8];
@@ -733,7 +744,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       l21[4] = v.x; l21[5] = v.y; l21[6] = v.z; l21[7] = v.w;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        l21[c] *= rp1[c];
+        l21[c] *= cs1[c];
 #pragma unroll
         for (int c2 = c + 1; c2 < 8; ++c2) l21[c2] = fmaf(-l21[c], l11[c2][c], l21[c2]);
       }
@@ -756,7 +767,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
     }
     __syncwarp();
     load8(l22, J + 8, J + 8);
-    chol8(l22, rp2, J + 8);
+    chol8(l22, rp2, cs2, J + 8);
     if (any_low && lane == 0) set_status(status, isnan(dlow) ? ST_NONFINITE : ST_RANK_DEFICIENT);
     __syncwarp();
     // L_JJ rows: lane i < 8 writes row i (L11) and row 8 + i (L22 part); s_lt and s_rpv
@@ -796,6 +807,10 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       *reinterpret_cast<float4*>(s_rpv + J + 4) = make_float4(rp1[4], rp1[5], rp1[6], rp1[7]);
       *reinterpret_cast<float4*>(s_rpv + J + 8) = make_float4(rp2[0], rp2[1], rp2[2], rp2[3]);
       *reinterpret_cast<float4*>(s_rpv + J + 12) = make_float4(rp2[4], rp2[5], rp2[6], rp2[7]);
+      *reinterpret_cast<float4*>(s_csv + J) = make_float4(cs1[0], cs1[1], cs1[2], cs1[3]);
+      *reinterpret_cast<float4*>(s_csv + J + 4) = make_float4(cs1[4], cs1[5], cs1[6], cs1[7]);
+      *reinterpret_cast<float4*>(s_csv + J + 8) = make_float4(cs2[0], cs2[1], cs2[2], cs2[3]);
+      *reinterpret_cast<float4*>(s_csv + J + 12) = make_float4(cs2[4], cs2[5], cs2[6], cs2[7]);
     }
   };
   // X_JJ = L_JJ^-1 by one warp, by columns: lane r holds column r, x[i] = X(i, r), zero for
@@ -919,6 +934,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   for (int jb = 0; jb + 1 < NB; ++jb) {
     const int J = jb * CB, s0 = J + CB;
     // panel, in place: L_iJ = A_iJ L_JJ^-T by forward substitution, one thread per row
+    // (a floored pivot's column is zero)
     for (int i = s0 + tid; i < LP; i += 512) {
       float* ai = arow(i) + J;
       float a[CB], rp[CB];
@@ -926,7 +942,7 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
       for (int q = 0; q < 4; ++q) {
         const float4 t = reinterpret_cast<const float4*>(ai)[q];
         a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
-        const float4 u = reinterpret_cast<const float4*>(s_rpv + J)[q];
+        const float4 u = reinterpret_cast<const float4*>(s_csv + J)[q];
         rp[4 * q] = u.x; rp[4 * q + 1] = u.y; rp[4 * q + 2] = u.z; rp[4 * q + 3] = u.w;
       }
 #pragma unroll

@@ -28,6 +28,14 @@ cudaError_t launch_gram_partial(const float* src, int splits, int64_t split_stri
                                 int64_t rows, int lp, float* gpart, int nblk, cudaStream_t st);
 int gram_blocks(int64_t rows);
 
+// The same partials on the tensor cores (each entry of Y split exactly into three bfloat16
+// parts, six products, float32 accumulation) over gram_tc_grid(rows, nblk_max) row blocks,
+// lower triangles only; lp a multiple of 16 up to 256.
+int gram_tc_grid(int64_t rows, int nblk_max);
+cudaError_t launch_gram_tc(const float* src, int splits, int64_t split_stride, float* y_out,
+                           int64_t rows, int lp, float* gpart, int nblk, uint32_t* status,
+                           cudaStream_t st);
+
 // G = sum of the nblk partial Grams (lp x lp).
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st);
 
