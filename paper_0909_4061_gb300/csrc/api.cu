@@ -42,6 +42,7 @@ struct rsvd_plan_s {
   float* partial = nullptr;  // split-K partial results
   int64_t partial_elems = 0;
   float* gpart = nullptr;    // nblk x lp x lp
+  uint8_t* rimg = nullptr;   // bfloat16 planes of R^-1 for the tensor-core apply (l_p > 128)
   float* small = nullptr;    // 24 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch, single pass
   float* psi = nullptr;      // m x lp   second test matrix of the single-pass sketch
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
@@ -115,7 +116,7 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev, P->srft_freq, P->psi, P->sig2};
+                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
@@ -250,13 +251,16 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     }
     return RSVD_OK;
   }
-  // Wider bases: Q = Y R^-1 by the float32 GEMM; on the tensor-core path the Gram partials
-  // are formed on the tensor cores too.  Their float32 accumulation is not IEEE-exact (about
+  // Wider bases: on the tensor-core path the Gram partials and Q = Y R^-1 are formed on the
+  // tensor cores too (exact three-way bfloat16 splits, six products), else by float32 FMA.  Their float32 accumulation is not IEEE-exact (about
   // 1e-6 of |Y|^T |Y| against 1e-7 for float32 FMA), far below the bfloat16 rounding of A
   // that the path already carries, but not float32-faithful: the plain float32 path keeps
   // the FMA Gram.
   const bool tc_gram = P->opt.precision == RSVD_BF16_TC;
   const int gblk = tc_gram ? gram_tc_grid(rows, nblk) : nblk;
+  // per round beyond the Gram, reduce and factorisation: R^-1 by a second kernel for the
+  // row-packed factorisation, and the image of R^-1 before the tensor-core apply
+  sp.launched(rounds * ((lp / 16 > 10 ? 1 : 0) + (tc_gram ? 1 : 0)));
   for (int r = 0; r < rounds; ++r) {
     float* yout = (cur_splits > 1) ? P->tmp1 : nullptr;
     if (tc_gram)
@@ -269,7 +273,10 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
                         r == 0 ? 1 : 0, P->status, P->st));
     float* next = (r == rounds - 1) ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
-    TRY(launch_gemm_f32(0, rows, lp, lp, cur, lp, P->rinv(), lp, next, lp, 1, 0, P->st));
+    if (tc_gram)
+      TRY(launch_apply_tc(cur, next, rows, lp, P->rinv(), P->rimg, P->status, P->st));
+    else
+      TRY(launch_gemm_f32(0, rows, lp, lp, cur, lp, P->rinv(), lp, next, lp, 1, 0, P->st));
     cur = next;
     cur_splits = 1;
   }
@@ -535,6 +542,11 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
       (o.test_matrix == RSVD_SRFT && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
+    free_plan(P);
+    return s;
+  }
+  if (o.precision == RSVD_BF16_TC && lp > 128 &&
+      (s = dalloc(P, &P->rimg, apply_tc_image_bytes(lp))) != RSVD_OK) {
     free_plan(P);
     return s;
   }

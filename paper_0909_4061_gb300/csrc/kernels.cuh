@@ -36,6 +36,12 @@ cudaError_t launch_gram_tc(const float* src, int splits, int64_t split_stride, f
                            int64_t rows, int lp, float* gpart, int nblk, uint32_t* status,
                            cudaStream_t st);
 
+// Q = Y R^-1 on the tensor cores (Y and R^-1 split exactly into three bfloat16 parts, six
+// products): img (apply_tc_image_bytes(lp) bytes) receives the planes of R^-1 first.
+size_t apply_tc_image_bytes(int lp);
+cudaError_t launch_apply_tc(const float* y, float* q, int64_t rows, int lp, const float* rinv,
+                            void* img, uint32_t* status, cudaStream_t st);
+
 // G = sum of the nblk partial Grams (lp x lp).
 cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, cudaStream_t st);
 

@@ -99,10 +99,11 @@ __device__ __forceinline__ void tc_fence_after() {
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
 // leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
 // >> 4 in 32-45, the fixed version value 1 in bits 46-47, swizzle mode in
-// 61-63 (2 = 128-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// 61-63 (2 = 128-byte swizzle, 4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t swizzle = 2) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swizzle << 61);
 }
 
 // Instruction descriptor for kind::f16: f32 accumulate (bits 4-5 = 1), bf16 A
