@@ -385,7 +385,9 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
   const int k = P->k;
   {
     Step sp(P, RSVD_STEP_SMALL_SVD);
-    sp.launched(24);
+    // (two pairs of Jacobi SVDs run one launch each on the cluster kernel)
+    const bool paired = P->opt.small_svd == 2 || (P->opt.small_svd == 0 && l >= 48);
+    sp.launched(paired ? 20 : 24);
     // X1 = Qt^T Omega (K = n), X2 = Q^T Psi (K = m): split over row blocks, summed by gather
     const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
     const int s1 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->n, 512)));
@@ -395,10 +397,11 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
     TRY(launch_gemm_f32(1, lp, lp, P->m, P->qbuf, lp, P->psi, lp, P->gpart, lp, s2, l2, P->st));
     TRY(launch_gather(P->gpart, s2, l2, lp, P->sp(1), lp, lp, lp, lp, P->st));
     // the k leading left singular vectors of Y = Q R and Yt = Qt Rt: Q U_R[:, :k], Qt U_Rt[:, :k]
-    TRY(launch_jacobi_svd(P->sp(2), lp, 0, l, lp, P->sp(5), P->sig2, P->sp(7), P->lbuf(), P->status,
-                          P->status + 1, P->st, P->opt.small_svd));
-    TRY(launch_jacobi_svd(P->racc(), lp, 0, l, lp, P->sp(6), P->sig2 + lp, P->sp(7), P->lbuf(),
-                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    // (the two SVDs are independent: one launch, one cluster each; the second's discarded W
+    // and scratch are the factorisation's buffers, free after the orthonormalisations)
+    TRY(launch_jacobi_svd_pair(P->sp(2), P->racc(), lp, 0, l, lp, P->sp(5), P->sp(6), P->sig2,
+                               P->sig2 + lp, P->sp(7), P->rtmp(), P->lbuf(), P->rinv(), P->status,
+                               P->status + 1, P->st, P->opt.small_svd));
     // the k x l systems: X1 = U_Rt_k^T (Qt^T Omega), C1 = U_R_k^T R, X2 = U_R_k^T (Q^T Psi),
     // C2 = U_Rt_k^T Rt (rows k..l-1 of the padded squares stay zero)
     for (int i : {3, 4, 8, 9}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * l2, P->st));
@@ -412,10 +415,9 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
     // would be l vectors in a k-dimensional space, l - k of them rounding noise that no
     // sweep can make orthogonal to the rest.  X^T = Ut S W^T gives X = W S Ut^T: the left
     // singular vectors are the accumulated rotations W.
-    TRY(launch_jacobi_svd(P->sp(3), lp, 1, l, lp, P->sp(7), P->sig2, P->sp(10), P->lbuf(), P->status,
-                          P->status + 1, P->st, P->opt.small_svd));
-    TRY(launch_jacobi_svd(P->sp(4), lp, 1, l, lp, P->sp(7), P->sig2 + lp, P->sp(11), P->lbuf(),
-                          P->status, P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_jacobi_svd_pair(P->sp(3), P->sp(4), lp, 1, l, lp, P->sp(7), P->rtmp(), P->sig2,
+                               P->sig2 + lp, P->sp(10), P->sp(11), P->lbuf(), P->rinv(), P->status,
+                               P->status + 1, P->st, P->opt.small_svd));
     // F = C1 X1^T + X2 C2^T; G = U2^T F U1; H = G ./ (s2^2 + s1^2); B = U2 H U1^T (all k x k)
     TRY(launch_small_gemm(k, k, l, 1.f, P->sp(8), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), lp, P->st));
     TRY(launch_small_gemm(k, k, l, 1.f, P->sp(4), lp, 0, P->sp(9), lp, 1, 1.f, P->sp(12), lp, P->st));

@@ -359,4 +359,16 @@ cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l
   return cudaGetLastError();
 }
 
+cudaError_t launch_jacobi_svd_pair(const float* x, const float* x_b, int64_t ldx, int transposed, int l,
+                                   int lp, float* ut, float* ut_b, float* s, float* s_b, float* w,
+                                   float* w_b, float* scratch, float* scratch_b, uint32_t* status,
+                                   uint32_t* info, cudaStream_t st, int variant) {
+  if (variant == 2 || (variant == 0 && l >= 48))
+    return launch_jacobi_cluster(x, ldx, transposed, l, lp, ut, s, w, scratch, status, info, st, x_b,
+                                 ut_b, s_b, w_b, scratch_b);
+  cudaError_t e = launch_jacobi_svd(x, ldx, transposed, l, lp, ut, s, w, scratch, status, info, st, variant);
+  if (e != cudaSuccess) return e;
+  return launch_jacobi_svd(x_b, ldx, transposed, l, lp, ut_b, s_b, w_b, scratch_b, status, info, st, variant);
+}
+
 }  // namespace rsvd

@@ -154,15 +154,28 @@ __device__ __forceinline__ int src_position(int p, int nblk) {
   return p == 0 ? 0 : (p == 1 ? nblk - 1 : p - 1);
 }
 
+// One matrix per cluster: the grid's first cluster takes job0, a second one job1 (two
+// independent SVDs of the same size in one launch).
+struct JacobiJob {
+  const float* x;
+  float* ut;
+  float* s;
+  float* w;
+};
+
 template <int VPL>
 __global__ void __launch_bounds__(kThreadsC) jacobi_block_kernel(
-    const float* __restrict__ x, int64_t ldx, int transposed, int l, int lp, int bw,
-    float* __restrict__ ut, float* __restrict__ s, float* __restrict__ w, uint32_t* status,
-    uint32_t* info, float tol2) {
+    JacobiJob job0, JacobiJob job1, int64_t ldx, int transposed, int l, int lp, int bw,
+    uint32_t* status, uint32_t* info, float tol2) {
   constexpr int LR = 64 * VPL;   // rows per stored column (zero beyond l)
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
+  const JacobiJob& job = (int)blockIdx.x < C ? job0 : job1;
+  const float* __restrict__ x = job.x;
+  float* __restrict__ ut = job.ut;
+  float* __restrict__ s = job.s;
+  float* __restrict__ w = job.w;
   const int nblk = 2 * C;
   const int slot_floats = 2 * bw * LR;   // X block then J block
   extern __shared__ __align__(16) float sm[];
@@ -347,8 +360,12 @@ __global__ void __launch_bounds__(kThreadsC) jacobi_block_kernel(
 // columns t: G_t = W^T W_t (l x 16; thread c computes row c, reading column c of W
 // coalesced across the CTA), then W_t <- 1.5 W_t - 0.5 W G_t (thread r computes
 // row r, reading row r of W as float4).  W stays in L2 (<= 256 KB); wout != win.
-__global__ void __launch_bounds__(256) ns_polish_kernel(const float* __restrict__ win, int l, int lp,
-                                                        float* __restrict__ wout) {
+__global__ void __launch_bounds__(256) ns_polish_kernel(const float* __restrict__ win0, float* __restrict__ wout0,
+                                                        const float* __restrict__ win1, float* __restrict__ wout1,
+                                                        int l, int lp) {
+  // blockIdx.y picks the matrix
+  const float* __restrict__ win = blockIdx.y ? win1 : win0;
+  float* __restrict__ wout = blockIdx.y ? wout1 : wout0;
   extern __shared__ __align__(16) float psm[];
   float* Wt = psm;              // [l][16]
   float* Gt = psm + 16 * l;     // [l][16]
@@ -433,11 +450,10 @@ template <int VPL>
 size_t block_smem(int bw) { return (size_t)4 * 2 * bw * 64 * VPL * sizeof(float); }
 
 template <int VPL>
-cudaError_t launch_vpl(int C, const float* x, int64_t ldx, int transposed, int l, int lp, int bw,
-                       float* ut, float* s, float* w, uint32_t* status, uint32_t* info, float tol2,
-                       cudaStream_t st) {
+cudaError_t launch_vpl(int C, int njobs, JacobiJob j0, JacobiJob j1, int64_t ldx, int transposed, int l,
+                       int lp, int bw, uint32_t* status, uint32_t* info, float tol2, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C);
+  cfg.gridDim = dim3(C * njobs);
   cfg.blockDim = dim3(kThreadsC);
   cfg.dynamicSmemBytes = block_smem<VPL>(bw);
   cfg.stream = st;
@@ -448,8 +464,8 @@ cudaError_t launch_vpl(int C, const float* x, int64_t ldx, int transposed, int l
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacobi_block_kernel<VPL>, x, ldx, transposed, l, lp, bw, ut, s,
-                            w, status, info, tol2);
+  return cudaLaunchKernelEx(&cfg, jacobi_block_kernel<VPL>, j0, j1, ldx, transposed, l, lp, bw, status,
+                            info, tol2);
 }
 
 }  // namespace
@@ -466,28 +482,38 @@ cudaError_t prepare_jacobi_cluster() {
                               (int)block_smem<4>(16));
 }
 
-// scratch: lp x lp floats (the unpolished W)
+// scratch: lp x lp floats (the unpolished W).  With a second matrix (x_b non-null: the same
+// l, lp, ldx and orientation, its own outputs and scratch), both run in one launch, one
+// cluster each.
 cudaError_t launch_jacobi_cluster(const float* x, int64_t ldx, int transposed, int l, int lp,
                                   float* ut, float* s, float* w, float* scratch, uint32_t* status,
-                                  uint32_t* info, cudaStream_t st) {
+                                  uint32_t* info, cudaStream_t st, const float* x_b, float* ut_b,
+                                  float* s_b, float* w_b, float* scratch_b) {
   if (l < 1 || l > kMaxLC || !scratch) return cudaErrorInvalidValue;
+  const int njobs = x_b ? 2 : 1;
+  if (x_b && !(ut_b && s_b && w_b && scratch_b)) return cudaErrorInvalidValue;
   const int C = l <= 128 ? 4 : kMaxCluster;
   const int bw = (l + 2 * C - 1) / (2 * C);   // <= 16
   const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
   const float tol2 = tol * tol;
   const int vpl = (l + 63) / 64;
+  const JacobiJob j0{x, ut, s, scratch};
+  const JacobiJob j1 = x_b ? JacobiJob{x_b, ut_b, s_b, scratch_b} : j0;
   cudaError_t e;
   switch (vpl) {
-    case 1: e = launch_vpl<1>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
-    case 2: e = launch_vpl<2>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
-    case 3: e = launch_vpl<3>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
-    default: e = launch_vpl<4>(C, x, ldx, transposed, l, lp, bw, ut, s, scratch, status, info, tol2, st); break;
+    case 1: e = launch_vpl<1>(C, njobs, j0, j1, ldx, transposed, l, lp, bw, status, info, tol2, st); break;
+    case 2: e = launch_vpl<2>(C, njobs, j0, j1, ldx, transposed, l, lp, bw, status, info, tol2, st); break;
+    case 3: e = launch_vpl<3>(C, njobs, j0, j1, ldx, transposed, l, lp, bw, status, info, tol2, st); break;
+    default: e = launch_vpl<4>(C, njobs, j0, j1, ldx, transposed, l, lp, bw, status, info, tol2, st); break;
   }
   if (e != cudaSuccess) return e;
   // padding of W (rows/columns >= l) is zero in scratch; copy it, then polish the l x l part
   e = cudaMemcpyAsync(w, scratch, sizeof(float) * lp * lp, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && x_b)
+    e = cudaMemcpyAsync(w_b, scratch_b, sizeof(float) * lp * lp, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  ns_polish_kernel<<<(l + 15) / 16, 256, (size_t)32 * l * sizeof(float), st>>>(scratch, l, lp, w);
+  ns_polish_kernel<<<dim3((l + 15) / 16, njobs), 256, (size_t)32 * l * sizeof(float), st>>>(
+      scratch, w, x_b ? scratch_b : scratch, x_b ? w_b : w, l, lp);
   return cudaGetLastError();
 }
 

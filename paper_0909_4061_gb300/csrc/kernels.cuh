@@ -108,10 +108,20 @@ cudaError_t launch_gather(const float* src, int splits, int64_t split_stride, in
                           float* dst, int64_t ldd, int64_t rows, int cols, int cols_pad,
                           cudaStream_t st);
 
-// The same SVD on a thread-block cluster (block round-robin ordering), l <= 256.
+// The same SVD on a thread-block cluster (block round-robin ordering), l <= 256.  With x_b,
+// a second matrix of the same size and orientation (own outputs and scratch) runs in the
+// same launch on a second cluster.
 cudaError_t launch_jacobi_cluster(const float* x, int64_t ldx, int transposed, int l, int lp,
                                   float* ut, float* s, float* w, float* scratch, uint32_t* status,
-                                  uint32_t* info, cudaStream_t st);
+                                  uint32_t* info, cudaStream_t st, const float* x_b = nullptr,
+                                  float* ut_b = nullptr, float* s_b = nullptr, float* w_b = nullptr,
+                                  float* scratch_b = nullptr);
+// Two independent SVDs of the same size and orientation: one launch of the cluster kernel
+// when it is the one launch_jacobi_svd would pick, else two launches.
+cudaError_t launch_jacobi_svd_pair(const float* x, const float* x_b, int64_t ldx, int transposed, int l,
+                                   int lp, float* ut, float* ut_b, float* s, float* s_b, float* w,
+                                   float* w_b, float* scratch, float* scratch_b, uint32_t* status,
+                                   uint32_t* info, cudaStream_t st, int variant);
 cudaError_t prepare_jacobi_cluster();
 
 // One-time (per device) shared-memory attributes of the one-CTA kernels.
