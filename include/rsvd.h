@@ -59,8 +59,8 @@ typedef enum {
 
 /* element type of A.  RSVD_BF16X2: A is stored as two bfloat16 m x n blocks with the
  * same lda, the rounded values hi = bf16(A) followed (m * lda elements further) by the
- * residual lo = bf16(A - hi), as rsvd_convert_a writes them; the passes of Stage A
- * read hi only, the final pass B^T = A^T Q reads both (about 16 significant bits). */
+ * residual lo = bf16(A - hi), as rsvd_convert_a writes them; the final pass B^T = A^T Q
+ * reads both (about 16 significant bits), and with residual_passes = 1 every pass does. */
 enum { RSVD_F32 = 0, RSVD_BF16 = 1, RSVD_BF16X2 = 2 };
 enum { RSVD_GAUSSIAN = 0, RSVD_SRFT = 1 };            /* test matrix (Section 4.1 / 4.6) */
 enum { RSVD_PLAIN_FP32 = 0, RSVD_BF16_TC = 1 };       /* how the passes over A are computed */
@@ -86,6 +86,11 @@ typedef struct {
                            (default), RSVD_SMALL_ONE_CTA (l <= 160) or RSVD_SMALL_CLUSTER
                            (a thread-block cluster of 4 or 8 CTAs, l <= 256); AUTO takes the
                            cluster from l = 48 on */
+  int32_t residual_passes; /* with dtype_A RSVD_BF16X2: 0 (default) only the final pass
+                           reads hi + lo; 1 every pass over A does (twice the bytes of A per
+                           pass; the reconstruction error then matches the float32 path's to
+                           about 1e-5 relative where a hi-only Stage A leaves 2e-4 to 1e-3).
+                           Must be 0 for other dtypes */
 } rsvd_options_t;
 
 enum { RSVD_SMALL_AUTO = 0, RSVD_SMALL_ONE_CTA = 1, RSVD_SMALL_CLUSTER = 2 };

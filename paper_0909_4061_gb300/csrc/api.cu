@@ -210,7 +210,9 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
     *splits = s;
   } else {
     int s = 1;
-    const int hilo = (split_x && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
+    // the residual of A: in the final pass, or in every pass when asked
+    const int hilo =
+        ((split_x || P->opt.residual_passes) && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
     if (tc_pass(&P->tc, trans, split_x ? 1 : 0, hilo, P->partial, &s, P->st) != 0)
       return RSVD_ERR_CUDA;
     *splits = s;
@@ -456,6 +458,7 @@ void rsvd_options_default(rsvd_options_t* opt) {
   opt->recompute = 0;
   opt->orth_rounds = 3;
   opt->lda = 0;
+  opt->residual_passes = 0;
 }
 
 const char* rsvd_status_string(rsvd_status_t s) {
@@ -488,6 +491,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.dtype_A != RSVD_F32 && o.dtype_A != RSVD_BF16 && o.dtype_A != RSVD_BF16X2)
     return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_PLAIN_FP32 && o.dtype_A != RSVD_F32) return RSVD_ERR_INVALID_ARG;
+  if (o.residual_passes != 0 && (o.residual_passes != 1 || o.dtype_A != RSVD_BF16X2))
+    return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
   if (o.test_matrix != RSVD_GAUSSIAN && o.test_matrix != RSVD_SRFT) return RSVD_ERR_INVALID_ARG;

@@ -66,10 +66,10 @@ struct Range {
   }
 };
 
-// HILO (with MODE 1): A arrives as a bfloat16 hi part (map_a) and the bfloat16
-// residual lo = A - hi (map_alo); each stage carries both tiles and the MMAs of
-// the lo tile accumulate into the same tensor-memory accumulator, so the pass
-// sees A to about 16 significant bits.
+// HILO (one row tile per unit): A arrives as a bfloat16 hi part (map_a) and the bfloat16
+// residual lo = A - hi (map_alo, the same tile shape and major-ness); each stage carries
+// both tiles and the MMAs of the lo tile accumulate into the same tensor-memory
+// accumulator, so the pass sees A to about 16 significant bits.
 template <int MODE, int HILO = 0, int TM = 1>
 __global__ void __launch_bounds__(64 + 128 * TM, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
 #pragma unroll
           for (int h = 0; h < TM; ++h)
             tma_load_2d_hint(sa + h * 16384, &map_a, bar, kk * BK, (t * TM + h) * BM, pol_a);
+          if (HILO) tma_load_2d_hint(sa + 16384, &map_alo, bar, kk * BK, t * BM, pol_a);
         } else {
 #pragma unroll
           for (int h = 0; h < TM; ++h) {
@@ -226,7 +227,8 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
                 const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
                 mma_bf16(acc + h * acc_cols + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
                 if (HILO) {
-                  const uint64_t adesc_lo = smem_desc(sa + 16384 + j * 2048, 8192, 1024);
+                  const uint64_t adesc_lo = MODE == 0 ? smem_desc(sa + 16384 + j * 32, 16, 1024)
+                                                      : smem_desc(sa + 16384 + j * 2048, 8192, 1024);
                   mma_bf16(acc + c * 256, adesc_lo, bdesc, idesc, 1u);
                 }
               }
@@ -432,7 +434,8 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
   // belongs to the kernel, not to this plan, so a later plan must not lower it under an
   // earlier one.
   for (const void* fn : {(const void*)sketch_tc_kernel<0>, (const void*)sketch_tc_kernel<1>,
-                         (const void*)sketch_tc_kernel<1, 1>, (const void*)sketch_tc_kernel<0, 0, 2>,
+                         (const void*)sketch_tc_kernel<1, 1>, (const void*)sketch_tc_kernel<0, 1>,
+                         (const void*)sketch_tc_kernel<0, 0, 2>,
                          (const void*)sketch_tc_kernel<1, 0, 2>})
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmemCap) !=
         cudaSuccess)
@@ -450,6 +453,7 @@ int tc_bind_a(TcPlan* tc, const void* A, int with_lo) {
   if (with_lo) {
     const __nv_bfloat16* lo = static_cast<const __nv_bfloat16*>(A) + tc->m * tc->lda;
     if (tc_encode_2d(tc->map_a_lo, lo, tc->n, tc->m, tc->lda, 64, BK)) return -1;
+    if (tc_encode_2d(tc->map_a_lo_n, lo, tc->n, tc->m, tc->lda, BK, BM)) return -1;
   }
   tc->a_bound = A;
   tc->lo_bound = with_lo;
@@ -459,7 +463,7 @@ int tc_bind_a(TcPlan* tc, const void* A, int with_lo) {
 int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* splits,
             cudaStream_t st) {
   if (!tc->ready || !tc->a_bound) return -1;
-  if (hilo && (!trans || !split_x || !tc->lo_bound)) return -1;
+  if (hilo && !tc->lo_bound) return -1;
   TcBuffers* b = static_cast<TcBuffers*>(tc->priv);
   const int lp = tc->lp;
   const int n_total = split_x ? fold_ntotal(lp) : lp;
@@ -474,15 +478,19 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
   const int stages = pick_stages(n_total, hilo ? 2 : tm);
   const size_t sm = smem_bytes(n_total, stages, hilo ? 2 : tm);
   const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(trans ? tc->map_a_t : tc->map_a_n);
-  const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(hilo ? tc->map_a_lo : tc->map_a_t);
+  const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(
+      hilo ? (trans ? tc->map_a_lo : tc->map_a_lo_n) : (trans ? tc->map_a_t : tc->map_a_n));
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
       trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
   if (split_x && !trans) return -1;
   // launched as a programmatic dependent: the A tiles of the first stages are loaded
   // while the launch that converts the operand finishes
   cudaError_t e;
-  if (hilo)
+  if (hilo && trans)
     e = launch_pdl(sketch_tc_kernel<1, 1>, dim3(grid), dim3(kThreads), sm, st, *ma, *malo, *mx, out, lp,
+                   M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
+  else if (hilo)
+    e = launch_pdl(sketch_tc_kernel<0, 1>, dim3(grid), dim3(kThreads), sm, st, *ma, *malo, *mx, out, lp,
                    M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
   else if (tm == 2 && trans)
     e = launch_pdl(sketch_tc_kernel<1, 0, 2>, dim3(grid), dim3(threads_for<2>()), sm, st, *ma, *ma, *mx,

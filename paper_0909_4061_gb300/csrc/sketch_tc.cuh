@@ -20,6 +20,7 @@ struct TcPlan {
   alignas(64) unsigned char map_x_t[128];  // X^T tiles, K = m (lp rows)
   alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (hi rows, then lo rows at tc_lo_offset)
   alignas(64) unsigned char map_a_lo[128]; // residual lo = A - hi, stacked m rows below A (Y = A^T X)
+  alignas(64) unsigned char map_a_lo_n[128]; // the same residual as K-major tiles (Y = A X)
   bool ready = false;
   int lo_bound = 0;
   uint32_t* status = nullptr;     // device status word of the owning plan

@@ -89,6 +89,16 @@ def test_plan_create_rejects_bad_options_on_host(pkg):
     with pytest.raises(pkg.RsvdError) as e:
         pkg.rsvd_plan_create(100, 80, 5, 5, 1, 0, o, 0)
     assert e.value.status == pkg.RSVD_ERR_INVALID_ARG
+    # the residual of A in every pass needs A stored as hi + lo
+    assert pkg.rsvd_options_default().residual_passes == 0
+    for dtype, rp in [(pkg.RSVD_BF16, 1), (pkg.RSVD_BF16X2, 2), (pkg.RSVD_F32, 1)]:
+        o = pkg.rsvd_options_default()
+        o.precision = pkg.RSVD_PLAIN_FP32 if dtype == pkg.RSVD_F32 else pkg.RSVD_BF16_TC
+        o.dtype_A = dtype
+        o.residual_passes = rp
+        with pytest.raises(pkg.RsvdError) as e:
+            pkg.rsvd_plan_create(100, 80, 5, 5, 1, 0, o, 0)
+        assert e.value.status == pkg.RSVD_ERR_INVALID_ARG, (dtype, rp)
 
 
 def test_null_pointer_arguments(pkg):
