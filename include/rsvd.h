@@ -76,7 +76,8 @@ typedef struct {
                            RSVD_BF16_TC: bfloat16 A (RSVD_BF16 or RSVD_BF16X2), tcgen05
                            tensor-core products with float32 accumulation, float32
                            re-orthonormalisation, and a split (hi + lo) basis in the final
-                           pass B^T = A^T Q (with RSVD_BF16X2 also a split A there). */
+                           pass B^T = A^T Q (with RSVD_BF16X2 also a split A there, or in
+                           every pass with residual_passes = 1). */
   int32_t single_pass;  /* 1: two-sided one-pass sketch of Section 5.5 (q ignored) */
   int32_t recompute;    /* backward: recompute the sample matrices instead of storing them */
   int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation: 2 or 3 (default 3:
