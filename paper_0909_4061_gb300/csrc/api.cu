@@ -519,7 +519,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_CUDA;
   }
   if (prepare_orth() != cudaSuccess || prepare_jacobi() != cudaSuccess ||
-      prepare_jacobi_cluster() != cudaSuccess) {
+      prepare_jacobi_cluster() != cudaSuccess || prepare_gram_tc() != cudaSuccess ||
+      prepare_apply_tc() != cudaSuccess) {
     cudaGetLastError();
     delete P;
     return RSVD_ERR_CUDA;

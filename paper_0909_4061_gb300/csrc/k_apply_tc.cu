@@ -303,16 +303,14 @@ size_t apply_tc_image_bytes(int lp) {
   return (size_t)nkc * 3 * nbox * ABOX;
 }
 
+cudaError_t prepare_apply_tc() {
+  return cudaFuncSetAttribute(apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)apply_tc_smem(256));
+}
+
 cudaError_t launch_apply_tc(const float* y, float* q, int64_t rows, int lp, const float* rinv,
                             void* img, uint32_t* status, cudaStream_t st) {
   if (lp < 16 || lp > 256 || lp % 16 != 0 || rows < 1) return cudaErrorInvalidValue;
-  static int attr_set = 0;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)apply_tc_smem(256));
-    if (e != cudaSuccess) return e;
-    attr_set = 1;
-  }
   const int nbox = (lp + 63) / 64;
   cudaError_t e = launch_pdl(apply_tc_prep_kernel, dim3(64), dim3(256), 0, st, rinv, lp, nbox,
                              static_cast<uint8_t*>(img));

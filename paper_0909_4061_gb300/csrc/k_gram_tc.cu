@@ -247,17 +247,15 @@ int gram_tc_grid(int64_t rows, int nblk_max) {
   return (int)(g < 1 ? 1 : g);
 }
 
+cudaError_t prepare_gram_tc() {
+  return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_tc_smem(256));
+}
+
 cudaError_t launch_gram_tc(const float* src, int splits, int64_t split_stride, float* y_out,
                            int64_t rows, int lp, float* gpart, int nblk, uint32_t* status,
                            cudaStream_t st) {
   if (lp < 16 || lp > 256 || lp % 16 != 0 || nblk < 1) return cudaErrorInvalidValue;
-  static int attr_set = 0;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)gram_tc_smem(256));
-    if (e != cudaSuccess) return e;
-    attr_set = 1;
-  }
   return launch_pdl(gram_tc_kernel, dim3(nblk), dim3(GTHREADS), gram_tc_smem(lp), st, src, splits,
                     split_stride, y_out, rows, lp, gpart, status);
 }

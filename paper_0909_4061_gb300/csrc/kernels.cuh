@@ -124,8 +124,11 @@ cudaError_t launch_jacobi_svd_pair(const float* x, const float* x_b, int64_t ldx
                                    uint32_t* info, cudaStream_t st, int variant);
 cudaError_t prepare_jacobi_cluster();
 
-// One-time (per device) shared-memory attributes of the one-CTA kernels.
+// One-time (per device) shared-memory attributes of the one-CTA kernels and of the
+// tensor-core Gram and apply.
 cudaError_t prepare_orth();
 cudaError_t prepare_jacobi();
+cudaError_t prepare_gram_tc();
+cudaError_t prepare_apply_tc();
 
 }  // namespace rsvd
