@@ -37,7 +37,8 @@ if ROOT not in sys.path:
 
 METRIC = "rank-k rSVD ms & HBM roofline frac, BF16-TC vs FP32 GPU at matched error"
 WORKLOAD = ("c2: A = U diag(j^-1.5) V^T, 16384 x 16384, Haar U,V (float32 QR of seeded "
-            "Gaussians), bf16-stored A; k=100, p=10, q=1 (4 passes over A)")
+            "Gaussians), A stored as bf16 hi + bf16 lo and read in full by every pass; "
+            "k=100, p=10, q=1 (4 passes over A)")
 PASS_KERNEL_SRC = [os.path.join(ROOT, "paper_0909_4061_gb300", "csrc", f)
                    for f in ("k_sketch_tc.cu", "tc_ptx.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sketch_tc_pass_c2.md")
