@@ -3,8 +3,8 @@
 // triangular (l_p x l_p, zero padded), Q float32.
 //
 // Precision: Y and R^-1 are split exactly into three bfloat16 parts each (y = h + m + t,
-// as for the tensor-core Gram) and Q ~= Σ over the six products H Rh + H Rm + M Rh +
-// H Rt + T Rh + M Rm with float32 accumulation in tensor memory.  As for the Gram, the
+// as for the tensor-core Gram) and Q ~= H Rh + H Rm + M Rh + H Rt + T Rh + M Rm, six
+// products with float32 accumulation in tensor memory.  As for the Gram, the
 // accumulation is not IEEE-exact (about 1e-6 relative), which the bfloat16 path, whose A
 // is rounded to 2^-9, absorbs.
 //
@@ -17,7 +17,8 @@
 // box kc / 2 and are l_p - 64 (kc / 2) wide.
 //
 // Work split: 128-row tiles, tile t by CTA t mod G (persistent); two accumulators of l_p
-// columns let the MMAs of a tile run while the previous tile is written out.
+// columns (32-column aligned) let the MMAs of a tile run while the previous tile is
+// written out.
 //
 // Warp roles (320 threads): warp 0 copies the B image chunks (bulk copies), warp 1 owns
 // tensor memory and issues the MMAs from one thread, warps 2..5 load, split and store
