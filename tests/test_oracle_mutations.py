@@ -88,3 +88,30 @@ def test_sylvester_sign_error_is_caught(monkeypatch):
 
     monkeypatch.setattr(single_pass, "min_residual", bad)
     _fails(pins.test_single_pass_solver_matches_bruteforce)
+
+
+def test_dropped_lo_half_is_caught(monkeypatch):
+    import tests.test_oracle_mixed as mpins
+    from oracle import mixed
+
+    monkeypatch.setattr(mixed, "split", lambda x: mixed.bf16(x))
+    _fails(mpins.test_exact_rank_recovery_limited_by_the_split_basis)
+
+
+def test_rounded_basis_in_the_lift_is_caught(monkeypatch):
+    import tests.test_oracle_mixed as mpins
+    from oracle import mixed
+
+    orig = mixed.range_finder
+    monkeypatch.setattr(mixed, "range_finder", lambda *a, **kw: mixed.bf16(orig(*a, **kw)))
+    _fails(mpins.test_lift_uses_the_float64_basis)
+
+
+def test_unrounded_test_matrix_is_caught(monkeypatch):
+    import tests.test_oracle_mixed as mpins
+    from oracle import mixed
+
+    orig = mixed.range_finder
+    monkeypatch.setattr(mixed, "range_finder",
+                        lambda a, om, q, operand=None: orig(a, om, q, operand=lambda x: x))
+    _fails(mpins.test_first_sample_uses_the_rounded_test_matrix)
