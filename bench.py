@@ -223,6 +223,47 @@ def make_inputs(rank: int, pkg, cached: bool = False):
     return w, A, Ab, Ahl
 
 
+def bench_config(w, world: int) -> dict:
+    """The `config` object of both arms (the same workload, so the same dict)."""
+    return {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
+            "precision": "bf16 tensor cores on A stored as bf16 hi + bf16 lo (every pass "
+                         "reads both: about 16 significant bits), f32 accumulate, f32 "
+                         "re-orthonormalisation",
+            "l2": "A is 1.07 GB as hi + lo (> 129 MB L2); no flush needed between steps",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def pass_bytes(m: int, n: int, l: int, a_copies: int = 1) -> int:
+    """Bytes one pass Y = A X over an m x n A moves at minimum: A as bfloat16 (a_copies
+    times: 2 for hi + lo), the bfloat16 operand (n x l_p) and the float32 output (m x l_p),
+    with l_p = l rounded up to 16 (the tile width of the pass)."""
+    lp = -(-l // 16) * 16
+    return a_copies * 2 * m * n + 2 * n * lp + 4 * m * lp
+
+
+def oracle_errors(res, ref, k: int) -> dict:
+    """Error of a rank-k result (U, S, V) against the float64 oracle's (same A, same Omega):
+    singular values relative to sigma_1, and each singular vector's distance (after sign
+    alignment) times its spectral gap over sigma_1 -- the size of the perturbation that
+    Wedin's theorem would need to explain it."""
+    import numpy as np
+
+    u, s, v = (np.asarray(x, dtype=np.float64) for x in res)
+    ur, sr, vr, s_next = ref
+    gaps = np.empty(k)
+    for j in range(k):
+        g = sr[j - 1] - sr[j] if j > 0 else np.inf
+        g = min(g, (sr[j] - sr[j + 1]) if j + 1 < k else (sr[j] - s_next))
+        gaps[j] = g
+    d = np.sign(np.sum(u * ur, axis=0))
+    d[d == 0] = 1.0
+    du = np.linalg.norm(u * d - ur, axis=0)
+    dv = np.linalg.norm(v * d - vr, axis=0)
+    return {"max_abs_sigma_err_over_sigma1": float(np.max(np.abs(s - sr)) / sr[0]),
+            "max_gap_scaled_u_err_over_sigma1": float(np.max(du * gaps) / sr[0]),
+            "max_gap_scaled_v_err_over_sigma1": float(np.max(dv * gaps) / sr[0])}
+
+
 def recon_error(A, U, S, V) -> float:
     """||A - U diag(S) V^T||_F in float64 (on the device)."""
     import torch
@@ -260,12 +301,16 @@ def cpu_baseline(A, w, budget_s: float = 12.0):
     t_start = time.perf_counter()
     while not times or (time.perf_counter() - t_start < budget_s and len(times) < 5):
         t0 = time.perf_counter()
-        rsvd64.rsvd(a64, w.k, w.p, w.q, om)
+        u, s, v, _ = rsvd64.rsvd(a64, w.k + w.p, 0, w.q, om)     # untruncated: sigma_{k+1} too
         times.append((time.perf_counter() - t0) * 1e3)
-    return {"value": statistics.median(times), "unit": "ms", "cores": os.cpu_count(),
+    k = w.k
+    r = a64 - (u[:, :k] * s[:k]) @ v[:, :k].T
+    e_f = float(np.sqrt(np.sum(r * r)))
+    base = {"value": statistics.median(times), "unit": "ms", "cores": os.cpu_count(),
             "kind": "oracle",
             "sample": f"{len(times)} full rank-{w.k} SVDs of the same 16384x16384 A in float64 "
                       "(numpy/LAPACK, default BLAS threads), median"}
+    return base, (u[:, :k], s[:k], v[:, :k], s[k]), e_f
 
 
 def run_ours(args):
@@ -291,7 +336,7 @@ def run_ours(args):
     # and every pass reading both (about 16 significant bits of A); the bf16-only storage
     # and the residual in the final pass alone are timed below as variants.
     with pkg.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_BF16_TC, dtype=pkg.RSVD_BF16X2,
-                  residual_passes=1) as pl:
+                  residual_passes=1, host_f32=1) as pl:
         for _ in range(max(args.warmup, 3)):
             pkg.rsvd_svd(pl.handle, Ahl, U, S, V)
         if pkg.rsvd_sync(pl.handle) != pkg.RSVD_OK:
@@ -318,6 +363,7 @@ def run_ours(args):
         pkg.rsvd_profile(pl.handle, 0)
         e_main = recon_error(A, U, S, V) if A is not None else float("nan")
         s_main = S.double().cpu()
+        res_main = (U.double().cpu().numpy(), S.double().cpu().numpy(), V.double().cpu().numpy())
         # per-step breakdown (diagnostic, separate short loop, every step kind timed)
         pkg.rsvd_profile(pl.handle, (1 << pkg.RSVD_NUM_STEPS) - 1)
         for _ in range(5):
@@ -327,9 +373,11 @@ def run_ours(args):
         out["stages_ms_per_svd"] = {k: round(v / 5, 4) for k, v in stage_ms.items()}
         out["jacobi_sweeps_max"] = pkg.rsvd_diagnostics(pl.handle)[1]
         # end to end through the host-buffer entry point
+        # (the caller's float32 A is copied in and split into hi + lo on the device by the
+        # library -- the host_f32 option -- inside the timed region)
         e2e = None
-        if not args.no_e2e:
-            a_host = Ahl.cpu().pin_memory()
+        if not args.no_e2e and A is not None:
+            a_host = A.cpu().pin_memory()
             uh = torch.empty(w.m, w.k).pin_memory()
             sh = torch.empty(w.k).pin_memory()
             vh = torch.empty(w.n, w.k).pin_memory()
@@ -341,9 +389,11 @@ def run_ours(args):
                 pkg.rsvd_svd_host(pl.handle, a_host, uh, sh, vh)
             t_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3)
             e2e = {"value": job_ms_per_unit(t_e2e, k_e2e, world), "unit": "ms",
-                   "h2d_bytes_per_step": int(2 * w.m * w.n * 2),
+                   "h2d_bytes_per_step": int(w.m * w.n * 4),
                    "d2h_bytes_per_step": int((w.m * w.k + w.k + w.n * w.k) * 4),
-                   "steps": k_e2e, "api": "rsvd_svd_host (pinned host buffers)"}
+                   "steps": k_e2e,
+                   "api": "rsvd_svd_host with host_f32 = 1: float32 A from pinned host memory, "
+                          "split into bf16 hi + lo on the device, U/S/V back to pinned host memory"}
 
     # variants: bf16 storage only (every pass reads bf16(A)); hi + lo storage with only the
     # final pass B^T = A^T Q reading the residual
@@ -365,7 +415,7 @@ def run_ours(args):
 
     # the plain FP32 CUDA-core path on the float32 A, same Omega seed
     k32 = 0
-    el32, e_f32, s_f32 = float("nan"), float("nan"), s_main
+    el32, e_f32, s_f32, res_f32 = float("nan"), float("nan"), s_main, None
     if not args.profile_run:
         with pkg.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_PLAIN_FP32) as pl32:
             pkg.rsvd_svd(pl32.handle, A, U, S, V)
@@ -375,6 +425,7 @@ def run_ours(args):
                 raise RuntimeError("device error on the FP32 path")
             e_f32 = recon_error(A, U, S, V)
             s_f32 = S.double().cpu()
+            res_f32 = (U.double().cpu().numpy(), S.double().cpu().numpy(), V.double().cpu().numpy())
 
     elapsed_max = max_over_ranks(elapsed)
     ms_step = elapsed_max / args.steps
@@ -382,25 +433,30 @@ def run_ours(args):
     peaks = measured_peaks()
     n_pass = pass_launches["pass"]
     avg_pass_ms = pass_ms["pass"] / max(n_pass, 1)
-    # A as hi + lo (2 x 2mn bytes) + bf16 operand + f32 output
-    bytes_per_pass = 2 * w.m * w.n * 2 + w.n * 112 * 2 + w.m * 112 * 4
+    # the pass's algorithmic bytes: A once as bfloat16 + the bf16 operand + the f32 output
+    # (the headline kernel reads A as hi + lo, twice those bytes of A: reported beside)
+    bytes_per_pass = pass_bytes(w.m, w.n, w.l)
+    bytes_moved = pass_bytes(w.m, w.n, w.l, a_copies=2)
     achieved = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic (seeded Haar factors on the device; the paper's datasets are not used)",
-        "config": {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
-                   "precision": "bf16 tensor cores on A stored as bf16 hi + bf16 lo (every pass "
-                                "reads both: about 16 significant bits), f32 accumulate, f32 "
-                                "re-orthonormalisation",
-                   "l2": "A is 1.07 GB as hi + lo (> 129 MB L2); no flush needed between steps",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": bench_config(w, world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": ncu_traffic(),
                      "kernel": "sketch_tc_kernel (one pass over A read as hi + lo)",
-                     "bytes_per_launch": bytes_per_pass, "avg_launch_ms": round(avg_pass_ms, 5),
+                     "bytes_per_launch": bytes_per_pass,
+                     "bytes_definition": "2mn (A as bf16) + 2 n l_p (operand) + 4 m l_p (output)",
+                     "bytes_moved_per_launch": bytes_moved,
+                     "frac_of_bytes_moved": round(bytes_moved / (avg_pass_ms * 1e-3) / 1e9
+                                                  / peaks["hbm_gbs"], 4),
+                     "traffic_note": "DRAM bytes per launch of the hi + lo kernel (ncu): about "
+                                     "bytes_moved_per_launch, twice the algorithmic bytes of A "
+                                     "because every pass also reads the residual lo",
+                     "avg_launch_ms": round(avg_pass_ms, 5),
                      "peak_source": peaks["source"],
                      "timing": f"CUDA events around each of the {n_pass} pass launches of a second "
                                f"{args.steps}-step loop on the plan stream (direct launches, "
@@ -422,7 +478,16 @@ def run_ours(args):
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(A, w)
+        base, ref, e_oracle = cpu_baseline(A, w)
+        line["cpu_baseline"] = base
+        acc = {"oracle": "float64 Algorithm 4.4 + 5.1 on the float32 A with the same Omega",
+               "recon_err_oracle": e_oracle,
+               "headline": oracle_errors(res_main, ref, w.k)}
+        acc["headline"]["rel_recon_excess"] = (e_main - e_oracle) / e_oracle
+        if res_f32 is not None:
+            acc["fp32_path"] = oracle_errors(res_f32, ref, w.k)
+            acc["fp32_path"]["rel_recon_excess"] = (e_f32 - e_oracle) / e_oracle
+        line["error_vs_fp64_oracle"] = acc
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -619,7 +684,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q},
+            "config": bench_config(w, world),
             "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,

@@ -92,6 +92,11 @@ typedef struct {
                            pass; the reconstruction error then matches the float32 path's to
                            about 1e-5 relative where a hi-only Stage A leaves 2e-4 to 1e-3).
                            Must be 0 for other dtypes */
+  int32_t host_f32;     /* 1: rsvd_svd_host takes A as float32 (m x n, leading dimension
+                           lda) and converts it on the device to the plan's bfloat16 storage
+                           (hi, and lo for RSVD_BF16X2) before the SVD, so a caller holding a
+                           float32 matrix needs no conversion of its own.  Only with
+                           RSVD_BF16_TC; 0 (default): A_host is in the plan's dtype */
 } rsvd_options_t;
 
 enum { RSVD_SMALL_AUTO = 0, RSVD_SMALL_ONE_CTA = 1, RSVD_SMALL_CLUSTER = 2 };
@@ -126,9 +131,10 @@ RSVD_API rsvd_status_t rsvd_range_finder(rsvd_plan_t plan, const void* A, float*
  * n x k, all float32 row-major with leading dimension k.  A ~= U diag(S) V^T. */
 RSVD_API rsvd_status_t rsvd_svd(rsvd_plan_t plan, const void* A, float* U, float* S, float* V);
 
-/* rsvd_svd for host-resident data: copies A (host, m x n with the plan's lda)
- * to a device buffer owned by the plan, runs rsvd_svd, copies U, S, V back to
- * host memory, and waits for completion.  Page-locked host buffers give the
+/* rsvd_svd for host-resident data: copies A (host, m x n with the plan's lda,
+ * in the plan's dtype, or float32 with the host_f32 option) to a device buffer
+ * owned by the plan (allocated on the first call), runs rsvd_svd, copies U, S, V
+ * back to host memory, and waits for completion.  Page-locked host buffers give the
  * full copy bandwidth; pageable buffers work but are staged by the driver. */
 RSVD_API rsvd_status_t rsvd_svd_host(rsvd_plan_t plan, const void* A_host, float* U_host,
                             float* S_host, float* V_host);
@@ -244,7 +250,8 @@ RSVD_API rsvd_status_t rsvd_small_svd(rsvd_plan_t plan, const float* X, float* U
  *       (K = n when transpose = 0, m when transpose = 1), leading dimension
  *       ldxt >= K, a multiple of 8, 16-byte-aligned base.
  *   l:  a multiple of 16, 16 <= l <= 128.
- *   Y:  device float32, (transpose ? n : m) x l row-major, leading dimension l.
+ *   Y:  device float32, (transpose ? n : m) x l row-major, leading dimension l,
+ *       16-byte-aligned base (the results are stored four floats at a time).
  *   status: device word that receives a timeout bit (8) if a bounded wait
  *       expires; may be NULL.
  * Sizes outside these limits return RSVD_ERR_INVALID_ARG before any work.

@@ -68,6 +68,7 @@ class Options(ctypes.Structure):
         ("lda", ctypes.c_int64),
         ("small_svd", ctypes.c_int32),
         ("residual_passes", ctypes.c_int32),
+        ("host_f32", ctypes.c_int32),
     ]
 
 
@@ -282,8 +283,9 @@ class Plan:
 
     def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
                  lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None,
-                 small_svd=RSVD_SMALL_AUTO, residual_passes=0):
+                 small_svd=RSVD_SMALL_AUTO, residual_passes=0, host_f32=0):
         o = rsvd_options_default()
+        o.host_f32 = host_f32
         o.small_svd = small_svd
         o.residual_passes = residual_passes
         o.precision = precision

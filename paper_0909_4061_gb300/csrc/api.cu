@@ -53,6 +53,7 @@ struct rsvd_plan_s {
   TcPlan tc{};
   // rsvd_svd_host staging
   void* a_dev = nullptr;
+  float* a_f32 = nullptr;  // float32 staging of A for the host_f32 option
   float *u_dev = nullptr, *s_dev = nullptr, *v_dev = nullptr;
   size_t ws_bytes = 0;
   // CUDA graph of rsvd_svd for one (A, U, S, V) binding
@@ -116,7 +117,7 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg};
+                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
@@ -459,6 +460,7 @@ void rsvd_options_default(rsvd_options_t* opt) {
   opt->orth_rounds = 3;
   opt->lda = 0;
   opt->residual_passes = 0;
+  opt->host_f32 = 0;
 }
 
 const char* rsvd_status_string(rsvd_status_t s) {
@@ -503,6 +505,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.small_svd < 0 || o.small_svd > 2) return RSVD_ERR_INVALID_ARG;
   if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
+  if (o.host_f32 != 0 && (o.host_f32 != 1 || o.precision != RSVD_BF16_TC)) return RSVD_ERR_INVALID_ARG;
+  if (o.recompute != 0) return RSVD_ERR_UNSUPPORTED;  // the single-matrix backward keeps no samples
 
   rsvd_plan_t P = new (std::nothrow) rsvd_plan_s();
   if (!P) return RSVD_ERR_ALLOC;
@@ -674,15 +678,27 @@ rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, fl
   TRYS(check_plan(P));
   if (!A_host || !U_host || !S_host || !V_host) return RSVD_ERR_INVALID_ARG;
   const size_t esz = P->opt.dtype_A == RSVD_F32 ? 4 : 2;
-  const size_t arows = P->opt.dtype_A == RSVD_BF16X2 ? 2 * P->m : P->m;
+  const bool hilo = P->opt.dtype_A == RSVD_BF16X2;
+  const size_t arows = hilo ? 2 * P->m : P->m;
   const size_t abytes = ((size_t)(arows - 1) * P->lda + P->n) * esz;
+  const size_t fbytes = ((size_t)(P->m - 1) * P->lda + P->n) * sizeof(float);
   if (!P->a_dev) {
     TRYS(dalloc(P, reinterpret_cast<char**>(&P->a_dev), abytes));
+    if (P->opt.host_f32) TRYS(dalloc(P, &P->a_f32, fbytes / sizeof(float)));
     TRYS(dalloc(P, &P->u_dev, (size_t)P->m * P->k));
     TRYS(dalloc(P, &P->s_dev, (size_t)P->k));
     TRYS(dalloc(P, &P->v_dev, (size_t)P->n * P->k));
   }
-  TRY(cudaMemcpyAsync(P->a_dev, A_host, abytes, cudaMemcpyHostToDevice, P->st));
+  if (P->opt.host_f32) {
+    // float32 in, the plan's bfloat16 storage (hi, and lo m * lda elements further) out
+    TRY(cudaMemcpyAsync(P->a_f32, A_host, fbytes, cudaMemcpyHostToDevice, P->st));
+    Step sp(P, RSVD_STEP_CONVERT);
+    sp.launched();
+    TRY(launch_split_bf16(P->a_f32, P->m, P->n, P->lda, static_cast<__nv_bfloat16*>(P->a_dev),
+                          P->lda, hilo ? 1 : 0, P->st));
+  } else {
+    TRY(cudaMemcpyAsync(P->a_dev, A_host, abytes, cudaMemcpyHostToDevice, P->st));
+  }
   TRYS(rsvd_svd(P, P->a_dev, P->u_dev, P->s_dev, P->v_dev));
   TRY(cudaMemcpyAsync(U_host, P->u_dev, sizeof(float) * P->m * P->k, cudaMemcpyDeviceToHost, P->st));
   TRY(cudaMemcpyAsync(S_host, P->s_dev, sizeof(float) * P->k, cudaMemcpyDeviceToHost, P->st));

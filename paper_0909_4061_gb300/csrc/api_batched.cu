@@ -257,7 +257,7 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   if (opt) o = *opt; else rsvd_options_default(&o);
   if (o.orth_rounds != 2 && o.orth_rounds != 3) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_BF16_TC || o.dtype_A != RSVD_BF16 || o.test_matrix != RSVD_GAUSSIAN ||
-      o.single_pass || o.residual_passes)
+      o.single_pass || o.residual_passes || o.host_f32 || o.recompute)
     return RSVD_ERR_UNSUPPORTED;   // the batched path is the bf16 tensor-core Gaussian form
   const int l = k + p;
   for (int b = 0; b < batch; ++b) {

@@ -1220,18 +1220,37 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ x, int64_t rows, int 
   }
 }
 
+__device__ __forceinline__ void split_one(float v, __nv_bfloat16* hi_out, __nv_bfloat16* lo_out) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  *hi_out = hi;
+  if (lo_out) *lo_out = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// A (float32) -> hi = bf16(A) and, with with_lo, lo = bf16(A - hi) rows * ld_out elements
+// further.  One row per block iteration; four columns per thread when every row starts
+// on a 16-byte boundary on both sides.
 __global__ void split_bf16_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
                                   int64_t ld, __nv_bfloat16* __restrict__ out, int64_t ld_out,
-                                  int with_lo) {
-  const int64_t n = rows * cols;
+                                  int with_lo, int vec4) {
   const int64_t lo_off = rows * ld_out;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / cols, c = e % cols;
-    const float v = x[r * ld + c];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    out[r * ld_out + c] = hi;
-    if (with_lo) out[lo_off + r * ld_out + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float* xr = x + r * ld;
+    __nv_bfloat16* hr = out + r * ld_out;
+    __nv_bfloat16* lr = hr + lo_off;
+    if (vec4) {
+      for (int64_t c = 4 * (int64_t)threadIdx.x; c < cols; c += 4 * (int64_t)blockDim.x) {
+        const float4 v = *reinterpret_cast<const float4*>(xr + c);
+        __align__(8) __nv_bfloat16 h[4], l[4];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split_one(vv[i], &h[i], &l[i]);
+        *reinterpret_cast<uint2*>(hr + c) = *reinterpret_cast<const uint2*>(h);
+        if (with_lo) *reinterpret_cast<uint2*>(lr + c) = *reinterpret_cast<const uint2*>(l);
+      }
+    } else {
+      for (int64_t c = threadIdx.x; c < cols; c += blockDim.x)
+        split_one(xr[c], hr + c, with_lo ? lr + c : nullptr);
+    }
   }
 }
 
@@ -1395,10 +1414,12 @@ cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16
 
 cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
                               __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st) {
-  const int64_t n = rows * cols;
-  if (n == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(cdiv(n, 256) < 16 * kNumSMs ? cdiv(n, 256) : 16 * kNumSMs);
-  split_bf16_kernel<<<grid, 256, 0, st>>>(x, rows, cols, ld, out, ld_out, with_lo);
+  if (rows * cols == 0) return cudaSuccess;
+  const int vec4 = (cols % 4 == 0 && ld % 4 == 0 && ld_out % 4 == 0 &&
+                    (reinterpret_cast<uintptr_t>(x) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(out) & 7) == 0) ? 1 : 0;
+  const unsigned grid = (unsigned)(rows < 16 * kNumSMs ? rows : 16 * kNumSMs);
+  split_bf16_kernel<<<grid, 256, 0, st>>>(x, rows, cols, ld, out, ld_out, with_lo, vec4);
   return cudaGetLastError();
 }
 

@@ -20,12 +20,21 @@
 // and raise a flag, and the finishing CTA adds them in CTA order
 // (deterministic) and clears the flags.
 //
-// Warp roles (64 + 128 TM threads): warp 0 issues TMA, warp 1 owns tensor memory
-// and issues the MMAs from one thread, the 4 TM warps from 2 on drain the
-// accumulators (each warp reads the 32 TMEM lanes its index allows).  With TM = 2 a
-// work unit is two 128-row tiles that share every X tile (two MMAs per k step into
-// two accumulators), which halves the operand's re-reads from L2.  Every wait is
-// bounded; on expiry the kernel records a timeout in the status word and winds down.
+// Warp roles (64 + 128 TM CH threads): warp 0 issues TMA, warp 1 owns tensor memory
+// and issues the MMAs from one thread, the 4 TM CH warps from 2 on drain the
+// accumulators (each warp reads the 32 TMEM lanes its index allows; with CH = 2 two
+// warps share those lanes and take half of the columns each).  With TM = 2 a work unit
+// is two 128-row tiles that share every X tile (two MMAs per k step into two
+// accumulators), which halves the operand's re-reads from L2.  Every wait is bounded;
+// on expiry the kernel records a timeout in the status word and winds down.
+//
+// Accumulation: the tensor cores add each k16 product into the float32 accumulator
+// with truncation, so a long chain of MMAs into one accumulator drifts towards zero
+// (about -2e-5 relative over K = 16384, i.e. a thousand k16 steps).  The MMAs of a row
+// tile are therefore cut into chunks of kChunk k tiles, each into a fresh accumulator
+// (double-buffered), and the epilogue adds the chunks in registers with IEEE float32
+// additions: the drift then stays that of one chunk (32 or, with the residual of A, 64
+// k16 steps).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -37,9 +46,11 @@ namespace rsvd {
 namespace {
 
 using namespace tcx;
-constexpr int kThreads = 192;   // TM = 1
-template <int TM>
-constexpr int threads_for() { return 64 + 128 * TM; }
+constexpr int kThreads = 192;   // TM = 1, CH = 1
+template <int TM, int CH = 1>
+constexpr int threads_for() { return 64 + 128 * TM * CH; }
+constexpr int kChunk = 8;       // k tiles (of BK = 64) accumulated in tensor memory per chunk
+constexpr int kAccRegs = 128;   // accumulator columns an epilogue thread holds in registers
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -49,9 +60,23 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int TM>
-__device__ __forceinline__ void epi_bar() {  // the epilogue warps only
-  asm volatile("bar.sync 1, %0;" ::"n"(128 * TM) : "memory");
+template <int NT>
+__device__ __forceinline__ void epi_bar() {  // the epilogue warps only (NT threads)
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+// A barrier of the epilogue warps that also ANDs a flag over them, so that after a bounded
+// wait gave up in one warp every epilogue warp takes the same path (no named barrier is
+// then left waiting for warps that have stopped).
+template <int NT>
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(NT)
+      : "memory");
+  return r != 0;
 }
 
 struct Range {
@@ -70,8 +95,8 @@ struct Range {
 // residual lo = A - hi (map_alo, the same tile shape and major-ness); each stage carries
 // both tiles and the MMAs of the lo tile accumulate into the same tensor-memory
 // accumulator, so the pass sees A to about 16 significant bits.
-template <int MODE, int HILO = 0, int TM = 1>
-__global__ void __launch_bounds__(64 + 128 * TM, 1)
+template <int MODE, int HILO = 0, int TM = 1, int CH = 1>
+__global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
                      const __grid_constant__ CUtensorMap map_alo,
                      const __grid_constant__ CUtensorMap map_x, float* __restrict__ y, int lp,
@@ -90,12 +115,18 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   static_assert(TM == 1 || !HILO, "the residual of A is read with single tiles");
+  static_assert(TM * CH <= 2, "at most eight epilogue warps");
+  constexpr int kEpi = 128 * TM * CH;   // epilogue threads
   constexpr uint32_t a_bytes = TM * BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
   const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
   const uint32_t stage_bytes = a_bytes + x_bytes;
-  // two accumulators when they fit tensor memory (512 columns): the MMAs of the next row
-  // tile then run while the epilogue drains the previous one
-  const uint32_t acc_cols = (uint32_t)((n_total + 31) & ~31);
+  // A split operand wider than one MMA (2 lp > 256: hi rows from 0, lo rows from 256) is
+  // summed by the tensor cores: both MMAs accumulate into the same lp columns.  A narrower
+  // one is one MMA of N = 2 lp whose halves the epilogue adds.
+  const bool fold_mma = fold && n_total > 256;
+  // two accumulators when they fit tensor memory (512 columns): the MMAs of the next chunk
+  // then run while the epilogue drains the previous one
+  const uint32_t acc_cols = fold_mma ? 256u : (uint32_t)((n_total + 31) & ~31);
   const uint32_t unit_cols = (uint32_t)TM * acc_cols;   // the accumulators of one work unit
   const int nacc = (2 * unit_cols <= 512) ? 2 : 1;
   uint32_t tmem_cols = 32;
@@ -108,7 +139,7 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&bar_acc_full[a], 1);
-      mbar_init(&bar_acc_empty[a], 4 * TM);
+      mbar_init(&bar_acc_empty[a], 4 * TM * CH);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -196,71 +227,111 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
       const uint32_t idesc_full = instr_desc(n_total < 256 ? n_total : 256, MODE);
       const uint32_t idesc_tail = instr_desc(n_total > 256 ? n_total - 256 : 16, MODE);
       int64_t i = 0;
-      int seg = 0;
+      int ch = 0;   // chunk counter: accumulator buffer ch % nacc, phase (ch / nacc) & 1
       bool ok = true;
-      for (int64_t it = it0; it < it1 && ok; ++seg) {
+      for (int64_t it = it0; it < it1 && ok;) {
         const int t = (int)(it / kt);
         const int64_t seg_end = min(it1, (int64_t)(t + 1) * kt);
-        const int ab = seg % nacc;
-        const uint32_t acc = tmem + (uint32_t)ab * unit_cols;
-        if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(seg / nacc) & 1u) ^ 1u, abort_flag, status)) break;
-        tc_fence_after();
-        for (; it < seg_end; ++it, ++i) {
-          const int s = (int)(i % stages);
-          const uint32_t ph = (uint32_t)((i / stages) & 1);
-          if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
+        for (; it < seg_end && ok; ++ch) {
+          const int64_t ch_begin = it, ch_end = min(seg_end, it + kChunk);
+          const int ab = ch % nacc;
+          const uint32_t acc = tmem + (uint32_t)ab * unit_cols;
+          if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(ch / nacc) & 1u) ^ 1u, abort_flag, status)) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
-          const uint32_t sx = sa + a_bytes;
-          const bool first = (it == (int64_t)t * kt) || (it == it0);
+          for (; it < ch_end; ++it, ++i) {
+            const int s = (int)(i % stages);
+            const uint32_t ph = (uint32_t)((i / stages) & 1);
+            if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+            const uint32_t sx = sa + a_bytes;
+            const bool first = (it == ch_begin);
 #pragma unroll
-          for (int j = 0; j < BK / 16; ++j) {
+            for (int j = 0; j < BK / 16; ++j) {
 #pragma unroll
-            for (int h = 0; h < TM; ++h) {
-              uint64_t adesc;
-              if (MODE == 0)
-                adesc = smem_desc(sa + h * 16384 + j * 32, 16, 1024);       // K-major: +32 B per k16
-              else
-                adesc = smem_desc(sa + h * 16384 + j * 2048, 8192, 1024);   // MN-major: +16 rows of 128 B
-              for (int c = 0; c * 256 < n_total; ++c) {
-                const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
-                const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
-                mma_bf16(acc + h * acc_cols + c * 256, adesc, bdesc, idesc, (first && j == 0) ? 0u : 1u);
-                if (HILO) {
-                  const uint64_t adesc_lo = MODE == 0 ? smem_desc(sa + 16384 + j * 32, 16, 1024)
-                                                      : smem_desc(sa + 16384 + j * 2048, 8192, 1024);
-                  mma_bf16(acc + c * 256, adesc_lo, bdesc, idesc, 1u);
+              for (int h = 0; h < TM; ++h) {
+                uint64_t adesc;
+                if (MODE == 0)
+                  adesc = smem_desc(sa + h * 16384 + j * 32, 16, 1024);       // K-major: +32 B per k16
+                else
+                  adesc = smem_desc(sa + h * 16384 + j * 2048, 8192, 1024);   // MN-major: +16 rows of 128 B
+                for (int c = 0; c * 256 < n_total; ++c) {
+                  const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
+                  const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
+                  const uint32_t dcol = fold_mma ? 0u : (uint32_t)c * 256;
+                  const uint32_t accum = (first && j == 0 && (c == 0 || !fold_mma)) ? 0u : 1u;
+                  mma_bf16(acc + h * acc_cols + dcol, adesc, bdesc, idesc, accum);
+                  if (HILO) {
+                    const uint64_t adesc_lo = MODE == 0 ? smem_desc(sa + 16384 + j * 32, 16, 1024)
+                                                        : smem_desc(sa + 16384 + j * 2048, 8192, 1024);
+                    mma_bf16(acc + dcol, adesc_lo, bdesc, idesc, 1u);
+                  }
                 }
               }
             }
+            mma_commit(&bar_empty[s]);
           }
-          mma_commit(&bar_empty[s]);
+          if (ok) mma_commit(&bar_acc_full[ab]);
         }
-        if (ok) mma_commit(&bar_acc_full[ab]);
       }
     }
   } else {
-    // ---------------- epilogue (warps 2 .. 1 + 4 TM) ----------------
+    // ---------------- epilogue (warps 2 .. 1 + 4 TM CH) ----------------
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;   // which 128-row tile of the unit
+    const int idx = (warp - 2) >> 2;
+    const int half = TM == 2 ? idx : 0;   // which 128-row tile of the unit
+    const int chalf = CH == 2 ? idx : 0;  // which half of the columns
     const int row = half * BM + quad * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)half * acc_cols;
-    int seg = 0;
-    for (int64_t it = it0; it < it1; ++seg) {
+    // this thread's columns: [cb, cb + ncols), multiples of 16 (lp is a multiple of 16)
+    const int cmid = CH == 2 ? (int)(((lp >> 1) + 15) & ~15) : lp;
+    const int cb = chalf ? cmid : 0;
+    const int ncols = chalf ? lp - cmid : cmid;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)half * acc_cols + (uint32_t)cb;
+    const bool fold_epi = fold && !fold_mma;
+    float racc[kAccRegs];
+    int ch = 0;
+    for (int64_t it = it0; it < it1;) {
       const int t = (int)(it / kt);
       const int64_t tile_b = (int64_t)t * kt, tile_e = tile_b + kt;
       const int64_t seg_end = min(it1, tile_e);
       const int c_first = rg.cta_of(tile_b), c_last = rg.cta_of(tile_e - 1);
-      const bool ok = __all_sync(0xffffffffu,
-                                 mbar_wait(&bar_acc_full[seg % nacc], (uint32_t)(seg / nacc) & 1u,
-                                           abort_flag, status));
-      tc_fence_after();
-      const uint32_t tb = tbase + (uint32_t)(seg % nacc) * unit_cols;
+      bool ok = true;
+      // drain the chunks of this segment into registers (IEEE float32 additions)
+      for (int64_t cs = it; cs < seg_end; cs = min(seg_end, cs + kChunk), ++ch) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full[ch % nacc], (uint32_t)(ch / nacc) & 1u,
+                                               abort_flag, status));
+        tc_fence_after();
+        const uint32_t tb = tbase + (uint32_t)(ch % nacc) * unit_cols;
+        const bool first = (cs == it);
+#pragma unroll
+        for (int c0 = 0; c0 < kAccRegs; c0 += 16) {   // 16 columns at a time (ncols % 16 == 0)
+          if (c0 < ncols) {
+            float v[16];
+            tmem_ld16(tb + c0, v);
+            if (fold_epi) {
+              float w2[16];
+              tmem_ld16(tb + lo_off + c0, w2);
+#pragma unroll
+              for (int q = 0; q < 16; ++q) v[q] += w2[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) racc[c0 + q] = first ? v[q] : racc[c0 + q] + v[q];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_acc_empty[ch % nacc]);
+        if (!ok) break;
+      }
+      ok = epi_all<kEpi>(ok);
       const int64_t grow = (int64_t)t * (BM * TM) + row;
       const bool valid_row = grow < M;
       const bool direct = (c_first == c_last);
       const bool finisher = !direct && (cta == c_first);
-      if (finisher) {
+      if (finisher && ok) {
         // wait until every later contributor has published its partial sum
         for (int c = c_first + 1; c <= c_last; ++c) {
           uint32_t w = 0;
@@ -274,55 +345,53 @@ __global__ void __launch_bounds__(64 + 128 * TM, 1)
           }
         }
       }
-      for (int c0 = 0; c0 < lp; c0 += 32) {
-        const int ncol = min(32, lp - c0);  // lp is a multiple of 16: 32 or 16
-        float v[32];
-        tmem_ld_cols(tb + c0, ncol, v);
-        if (fold) {
-          float w2[32];
-          tmem_ld_cols(tb + lo_off + c0, ncol, w2);
+      if (ok && valid_row) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] += w2[q];
-        }
-        if (!ok || !valid_row) continue;
-        if (direct || finisher) {
-          if (finisher) {
-            for (int c = c_first + 1; c <= c_last; ++c) {
-              const float4* src = reinterpret_cast<const float4*>(slots + ((size_t)c * BM * TM + row) * lp + c0);
+        for (int c0 = 0; c0 < kAccRegs; c0 += 32) {
+          if (c0 < ncols) {
+            const int nc = min(32, ncols - c0);
+            const int col = cb + c0;
+            if (direct || finisher) {
+              if (finisher) {
+                for (int c = c_first + 1; c <= c_last; ++c) {
+                  const float4* src =
+                      reinterpret_cast<const float4*>(slots + ((size_t)c * BM * TM + row) * lp + col);
 #pragma unroll
-              for (int q = 0; q < 32; q += 4) {
-                if (q < ncol) {
-                  const float4 w4 = src[q >> 2];
-                  v[q] += w4.x; v[q + 1] += w4.y; v[q + 2] += w4.z; v[q + 3] += w4.w;
+                  for (int q = 0; q < 32; q += 4) {
+                    if (q < nc) {
+                      const float4 w4 = src[q >> 2];
+                      racc[c0 + q] += w4.x; racc[c0 + q + 1] += w4.y;
+                      racc[c0 + q + 2] += w4.z; racc[c0 + q + 3] += w4.w;
+                    }
+                  }
                 }
               }
+              float* dst = y + grow * lp + col;
+#pragma unroll
+              for (int q = 0; q < 32; q += 4)
+                if (q < nc)
+                  *reinterpret_cast<float4*>(dst + q) =
+                      make_float4(racc[c0 + q], racc[c0 + q + 1], racc[c0 + q + 2], racc[c0 + q + 3]);
+            } else {
+              float4* dst = reinterpret_cast<float4*>(slots + ((size_t)cta * BM * TM + row) * lp + col);
+#pragma unroll
+              for (int q = 0; q < 32; q += 4)
+                if (q < nc)
+                  dst[q >> 2] = make_float4(racc[c0 + q], racc[c0 + q + 1], racc[c0 + q + 2], racc[c0 + q + 3]);
             }
           }
-          float* dst = y + grow * lp + c0;
-#pragma unroll
-          for (int q = 0; q < 32; q += 4)   // ncol is 32 or 16
-            if (q < ncol)
-              *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        } else {
-          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)cta * BM * TM + row) * lp + c0);
-#pragma unroll
-          for (int q = 0; q < 32; q += 4)
-            if (q < ncol) dst[q >> 2] = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
         }
       }
-      tc_fence_before();
       if (!direct && !finisher) {
         // publish this CTA's partial of tile t (its first segment)
         __threadfence();
-        epi_bar<TM>();
+        epi_bar<kEpi>();
         if (warp == 2 && lane == 0) st_release(flags + cta, 1u);
       } else if (finisher) {
-        epi_bar<TM>();  // all rows have read the partials
+        epi_bar<kEpi>();  // all rows have read the partials
         if (warp == 2 && lane == 0)
           for (int c = c_first + 1; c <= c_last; ++c) flags[c] = 0u;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_acc_empty[seg % nacc]);
       it = seg_end;
       if (!ok) break;
     }
@@ -436,7 +505,11 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
   for (const void* fn : {(const void*)sketch_tc_kernel<0>, (const void*)sketch_tc_kernel<1>,
                          (const void*)sketch_tc_kernel<1, 1>, (const void*)sketch_tc_kernel<0, 1>,
                          (const void*)sketch_tc_kernel<0, 0, 2>,
-                         (const void*)sketch_tc_kernel<1, 0, 2>})
+                         (const void*)sketch_tc_kernel<1, 0, 2>,
+                         (const void*)sketch_tc_kernel<0, 0, 1, 2>,
+                         (const void*)sketch_tc_kernel<1, 0, 1, 2>,
+                         (const void*)sketch_tc_kernel<0, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<1, 1, 1, 2>})
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmemCap) !=
         cudaSuccess)
       return -1;
@@ -484,28 +557,33 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
       trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
   if (split_x && !trans) return -1;
   // launched as a programmatic dependent: the A tiles of the first stages are loaded
-  // while the launch that converts the operand finishes
+  // while the launch that converts the operand finishes.  Bases wider than kAccRegs
+  // columns take two epilogue warps per TMEM lane quarter (CH = 2), each holding half of
+  // a row's columns in registers.
+  const int ch = lp > kAccRegs ? 2 : 1;
+  auto go = [&](auto kernel, int threads) {
+    return launch_pdl(kernel, dim3(grid), dim3(threads), sm, st, *ma, *malo, *mx, out, lp, M, kt,
+                      total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
+  };
   cudaError_t e;
-  if (hilo && trans)
-    e = launch_pdl(sketch_tc_kernel<1, 1>, dim3(grid), dim3(kThreads), sm, st, *ma, *malo, *mx, out, lp,
-                   M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
-  else if (hilo)
-    e = launch_pdl(sketch_tc_kernel<0, 1>, dim3(grid), dim3(kThreads), sm, st, *ma, *malo, *mx, out, lp,
-                   M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
-  else if (tm == 2 && trans)
-    e = launch_pdl(sketch_tc_kernel<1, 0, 2>, dim3(grid), dim3(threads_for<2>()), sm, st, *ma, *ma, *mx,
-                   out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
-                   tc->status);
-  else if (tm == 2)
-    e = launch_pdl(sketch_tc_kernel<0, 0, 2>, dim3(grid), dim3(threads_for<2>()), sm, st, *ma, *ma, *mx,
-                   out, lp, M, kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags,
-                   tc->status);
-  else if (trans)
-    e = launch_pdl(sketch_tc_kernel<1>, dim3(grid), dim3(kThreads), sm, st, *ma, *ma, *mx, out, lp, M,
-                   kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
-  else
-    e = launch_pdl(sketch_tc_kernel<0>, dim3(grid), dim3(kThreads), sm, st, *ma, *ma, *mx, out, lp, M,
-                   kt, total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
+  if (ch == 2) {
+    if (hilo && trans) e = go(sketch_tc_kernel<1, 1, 1, 2>, threads_for<1, 2>());
+    else if (hilo) e = go(sketch_tc_kernel<0, 1, 1, 2>, threads_for<1, 2>());
+    else if (trans) e = go(sketch_tc_kernel<1, 0, 1, 2>, threads_for<1, 2>());
+    else e = go(sketch_tc_kernel<0, 0, 1, 2>, threads_for<1, 2>());
+  } else if (hilo && trans) {
+    e = go(sketch_tc_kernel<1, 1>, kThreads);
+  } else if (hilo) {
+    e = go(sketch_tc_kernel<0, 1>, kThreads);
+  } else if (tm == 2 && trans) {
+    e = go(sketch_tc_kernel<1, 0, 2>, threads_for<2>());
+  } else if (tm == 2) {
+    e = go(sketch_tc_kernel<0, 0, 2>, threads_for<2>());
+  } else if (trans) {
+    e = go(sketch_tc_kernel<1>, kThreads);
+  } else {
+    e = go(sketch_tc_kernel<0>, kThreads);
+  }
   if (e != cudaSuccess) return -1;
   *splits = 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -602,7 +680,9 @@ extern "C" rsvd_status_t rsvd_sketch_bf16_noalloc(const void* A, int64_t m, int6
   if (l < 16 || l > kNoAllocMaxL || l % 16 != 0) return RSVD_ERR_INVALID_ARG;
   const int64_t K = transpose ? m : n;
   if (lda < n || lda % 8 != 0 || ldxt < K || ldxt % 8 != 0) return RSVD_ERR_INVALID_ARG;
-  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(Xt) & 15))
+  // TMA reads A and Xt from 16-byte boundaries; the epilogue writes Y as float4
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(Xt) & 15) ||
+      (reinterpret_cast<uintptr_t>(Y) & 15))
     return RSVD_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RSVD_ERR_CUDA;
