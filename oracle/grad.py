@@ -16,6 +16,13 @@ independent routes give the gradient here:
     truncated SVD (d sigma_i = u_i^T dA v_i and ||A - A_k||_F^2 =
     ||A||_F^2 - sum_{i<=k} sigma_i^2), which the randomized gradient
     approaches when the basis captures the dominant subspace.
+
+General cotangents (the library's rsvd_svd_backward takes any gU, gS, gV): the
+gradient of <gU, U(A)> + <gS, S(A)> + <gV, V(A)> through the same map,
+``cotangent_autograd`` (torch autograd of the float64 steps) and
+``cotangent_fd`` (central differences, each singular pair's sign held to that
+of the unperturbed A, so that U(A) and V(A) are the smooth branch being
+differentiated).
 """
 from __future__ import annotations
 
@@ -81,3 +88,59 @@ def grad_exact_svd(a: np.ndarray, k: int) -> np.ndarray:
     u, s, vt = np.linalg.svd(a, full_matrices=False)
     ak = (u[:, :k] * s[:k]) @ vt[:k]
     return 2.0 * (a - ak) + u[:, :k] @ vt[:k]
+
+
+def _rsvd_torch(at, omega, k, q):
+    """The float64 steps of ``loss`` (Algorithm 4.4 + 5.1) on a torch tensor."""
+    import torch
+
+    om = torch.tensor(omega, dtype=torch.float64)
+
+    def qr_pos(y):
+        qm, r = torch.linalg.qr(y, mode="reduced")
+        d = torch.sign(torch.diagonal(r)).detach()
+        d[d == 0] = 1.0
+        return qm * d
+
+    qm = qr_pos(at @ om)
+    for _ in range(q):
+        qt = qr_pos(at.T @ qm)
+        qm = qr_pos(at @ qt)
+    ub, s, vbt = torch.linalg.svd(qm.T @ at, full_matrices=False)
+    return qm @ ub[:, :k], s[:k], vbt[:k].T
+
+
+def cotangent_value(a, k, p, q, omega, gu, gs, gv, ref=None):
+    """<gU, U> + <gS, S> + <gV, V> for the rank-k factors of ``rsvd`` on a; with ref =
+    (U0, V0) each pair's sign is aligned to ref's (the branch through A0)."""
+    u, s, v, _ = rsvd(a, k, p, q, omega)
+    if ref is not None:
+        d = np.sign(np.sum(u * ref[0], axis=0))
+        d[d == 0] = 1.0
+        u, v = u * d, v * d
+    return float(np.sum(gu * u) + np.sum(gs * s) + np.sum(gv * v))
+
+
+def cotangent_autograd(a, k, p, q, omega, gu, gs, gv):
+    """Gradient of <gU, U> + <gS, S> + <gV, V> by torch autograd; returns (grad, U, S, V)."""
+    import torch
+
+    at = torch.tensor(a, dtype=torch.float64, requires_grad=True)
+    u, s, v = _rsvd_torch(at, omega, k, q)
+    val = (torch.tensor(gu) * u).sum() + (torch.tensor(gs) * s).sum() + (torch.tensor(gv) * v).sum()
+    val.backward()
+    return at.grad.numpy().copy(), u.detach().numpy(), s.detach().numpy(), v.detach().numpy()
+
+
+def cotangent_fd(a, k, p, q, omega, gu, gs, gv, directions, h=1e-4, ref=None):
+    """Central differences of ``cotangent_value`` along the given directions, on the sign
+    branch of ref = (U0, V0) (default: the factors of ``rsvd`` at a)."""
+    if ref is None:
+        u0, _, v0, _ = rsvd(a, k, p, q, omega)
+        ref = (u0, v0)
+    out = []
+    for e in directions:
+        fp = cotangent_value(a + h * e, k, p, q, omega, gu, gs, gv, ref=ref)
+        fm = cotangent_value(a - h * e, k, p, q, omega, gu, gs, gv, ref=ref)
+        out.append((fp - fm) / (2.0 * h))
+    return np.array(out)

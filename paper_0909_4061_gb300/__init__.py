@@ -68,6 +68,7 @@ class Options(ctypes.Structure):
         ("lda", ctypes.c_int64),
         ("small_svd", ctypes.c_int32),
         ("residual_passes", ctypes.c_int32),
+        ("psi_cols", ctypes.c_int32),
         ("host_f32", ctypes.c_int32),
     ]
 
@@ -283,9 +284,11 @@ class Plan:
 
     def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
                  lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None,
-                 small_svd=RSVD_SMALL_AUTO, residual_passes=0, host_f32=0):
+                 small_svd=RSVD_SMALL_AUTO, residual_passes=0, host_f32=0, recompute=0, psi_cols=0):
         o = rsvd_options_default()
+        o.psi_cols = psi_cols
         o.host_f32 = host_f32
+        o.recompute = recompute
         o.small_svd = small_svd
         o.residual_passes = residual_passes
         o.precision = precision
@@ -341,6 +344,70 @@ class Plan:
 
     def sync(self):
         _check(rsvd_sync(self.handle), "rsvd_sync")
+
+    def backward(self, A, gU=None, gS=None, gV=None, add_recon=0, gA=None, sync=True):
+        """gA (m x n float32) for the cotangents of the last svd() on A (see rsvd.h)."""
+        import torch
+
+        gA = gA if gA is not None else torch.empty(self.m, self.n, device=A.device, dtype=torch.float32)
+        rsvd_svd_backward(self.handle, A, gU, gS, gV, add_recon, gA)
+        if sync:
+            _check(rsvd_sync(self.handle), "rsvd_svd_backward (device)")
+        return gA
+
+    def stored(self, A):
+        """A (float32 CUDA tensor) in the plan's storage: itself for float32 plans, else the
+        library's bfloat16 (or hi + lo) conversion."""
+        import torch
+
+        dt = self.options.dtype_A
+        if dt == RSVD_F32:
+            return A
+        if dt == RSVD_BF16X2:
+            return split_bf16(A)
+        out = torch.empty(self.m, self.n, device=A.device, dtype=torch.bfloat16)
+        rsvd_convert_a(A, self.m, self.n, A.stride(0), out, self.n, 0)
+        return out
+
+
+def _autograd_function():
+    import torch
+
+    class RSVDFunction(torch.autograd.Function):
+        """(U, S, V) = rsvd_svd(A) with rsvd_svd_backward as the adjoint (test matrix fixed).
+
+        A is a float32 CUDA tensor; the plan stores it as its dtype requires (the library's
+        conversion).  The backward hands the cotangents of U, S and V (None where an output
+        is unused) to rsvd_svd_backward; no arithmetic happens here."""
+
+        @staticmethod
+        def forward(ctx, A, plan):
+            As = plan.stored(A.detach().contiguous())
+            U, S, V = plan.svd(As)
+            ctx.plan, ctx.stored = plan, As
+            ctx.set_materialize_grads(False)
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, gU, gS, gV):
+            c = (lambda t: None if t is None else t.contiguous())
+            gA = ctx.plan.backward(ctx.stored, c(gU), c(gS), c(gV))
+            return gA, None
+
+    return RSVDFunction
+
+
+_RSVD_FN = None
+
+
+def svd_autograd(A, plan):
+    """Differentiable rank-k randomized SVD through the library: returns (U, S, V) whose
+    gradients flow to the float32 tensor A through rsvd_svd_backward.  The plan's last
+    rsvd_svd must be this call's when backward runs (one forward per backward)."""
+    global _RSVD_FN
+    if _RSVD_FN is None:
+        _RSVD_FN = _autograd_function()
+    return _RSVD_FN.apply(A, plan)
 
 
 def split_bf16(A):

@@ -115,3 +115,11 @@ def test_unrounded_test_matrix_is_caught(monkeypatch):
     monkeypatch.setattr(mixed, "range_finder",
                         lambda a, om, q, operand=None: orig(a, om, q, operand=lambda x: x))
     _fails(mpins.test_first_sample_uses_the_rounded_test_matrix)
+
+
+def test_dropped_power_step_in_the_gradient_is_caught(monkeypatch):
+    from oracle import grad
+
+    orig = grad._rsvd_torch
+    monkeypatch.setattr(grad, "_rsvd_torch", lambda at, om, k, q: orig(at, om, k, 0))
+    _fails(pins.test_cotangent_gradient_autograd_vs_finite_differences)
