@@ -92,6 +92,10 @@ typedef struct {
                            pass; the reconstruction error then matches the float32 path's to
                            about 1e-5 relative where a hi-only Stage A leaves 2e-4 to 1e-3).
                            Must be 0 for other dtypes */
+  int32_t psi_cols;     /* single pass: columns l' of the second test matrix Psi (m x l'),
+                           k <= l' <= min(n, 256); 0 (default) takes min(3 l, 256, n).  A Psi
+                           wider than l makes the system for B^T overdetermined (Section 5.5,
+                           the remark on single-pass error) */
   int32_t host_f32;     /* 1: rsvd_svd_host takes A as float32 (m x n, leading dimension
                            lda) and converts it on the device to the plan's bfloat16 storage
                            (hi, and lo for RSVD_BF16X2) before the SVD, so a caller holding a
@@ -158,6 +162,24 @@ RSVD_API rsvd_status_t rsvd_set_omega(rsvd_plan_t plan, const float* Omega);
 /* Wait for the plan's stream and return the first device-detected error
  * since the previous rsvd_sync (RSVD_OK if none); clears it. */
 RSVD_API rsvd_status_t rsvd_sync(rsvd_plan_t plan);
+
+/* ---- failure detection, tested without a fault --------------------------
+ * Every device-side wait of the library (mbarrier phases, stream-K hand-over flags) is
+ * bounded: when it runs out the kernel records RSVD_ERR_TIMEOUT in the plan's status word,
+ * lets its own copies in flight land, releases its tensor memory and returns, so the
+ * CUDA context stays usable and rsvd_sync() reports the timeout. */
+
+/* Diagnostic of that path: enqueues on the plan's stream a kernel that waits for a device
+ * word nothing ever sets, with a limit of `spins` polls about 64 ns apart (spins >= 1);
+ * the wait always runs out, the kernel records the timeout and returns, and the next
+ * rsvd_sync() returns RSVD_ERR_TIMEOUT (and clears it).  The paper has no counterpart. */
+RSVD_API rsvd_status_t rsvd_wait_selftest(rsvd_plan_t plan, uint32_t spins);
+
+/* Failure injection for tests of allocation-failure handling: the `after`-th device
+ * allocation the library makes from now on (0 = the next one) fails as a failed
+ * cudaMalloc would, with RSVD_ERR_ALLOC and no workspace leaked; -1 disarms.  The setting
+ * is process wide and is consumed by the failure.  The paper has no counterpart. */
+RSVD_API void rsvd_debug_fail_alloc(int32_t after);
 
 /* Static English description of a status code. */
 RSVD_API const char* rsvd_status_string(rsvd_status_t status);

@@ -39,7 +39,7 @@ EXPORTS = (
     "rsvd_orthonormalize", "rsvd_small_svd", "rsvd_profile", "rsvd_profile_read",
     "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc", "rsvd_convert_a",
     "rsvd_batched_plan_create", "rsvd_batched_plan_destroy", "rsvd_batched_svd", "rsvd_batched_sync",
-    "rsvd_batched_svd_backward",
+    "rsvd_batched_svd_backward", "rsvd_wait_selftest", "rsvd_debug_fail_alloc",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -109,6 +109,8 @@ _SIGS = {
     "rsvd_batched_svd": (_c.c_int, [_P, _P, _P, _P, _P]),
     "rsvd_batched_sync": (_c.c_int, [_P, _P]),
     "rsvd_batched_svd_backward": (_c.c_int, [_P, _P, _P]),
+    "rsvd_wait_selftest": (_c.c_int, [_P, _c.c_uint32]),
+    "rsvd_debug_fail_alloc": (None, [_c.c_int32]),
 }
 
 
@@ -220,6 +222,14 @@ def rsvd_set_omega(plan, Omega):
 def rsvd_sync(plan) -> int:
     """Returns the status code (does not raise) so callers can test device-side errors."""
     return lib().rsvd_sync(plan)
+
+
+def rsvd_wait_selftest(plan, spins):
+    _check(lib().rsvd_wait_selftest(plan, int(spins)), "rsvd_wait_selftest")
+
+
+def rsvd_debug_fail_alloc(after):
+    lib().rsvd_debug_fail_alloc(int(after))
 
 
 def rsvd_status_string(status: int) -> str:

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <utility>
 #include <vector>
@@ -26,11 +27,14 @@ using namespace rsvd;
 struct rsvd_plan_s {
   int64_t m = 0, n = 0, lda = 0, maxmn = 0;
   int k = 0, p = 0, q = 0, l = 0, lp = 0;
+  int lt = 0, lpp = 0;   // single pass: columns of Psi (l') and their padded width
+  int lq = 0;            // the widest padded width, max(lp, lpp): the stride of the small blocks
   uint64_t seed = 0;
   rsvd_options_t opt{};
   cudaStream_t st = nullptr;
   int device = 0, num_sms = kNumSMs;
   int splits_n = 1, splits_t = 1;  // split-K of the passes Y = A X and Y = A^T X (FP32 path)
+  int splits_psi = 1;              // split-K of Yt = A^T Psi (FP32 path, single pass)
   int nblk = 1;
   bool omega_user = false;
   // workspace (device)
@@ -49,8 +53,16 @@ struct rsvd_plan_s {
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
   uint32_t* status = nullptr;
+  // backward tape: the R factors of every orthonormalisation of Stage A (always), and in
+  // store mode (recompute = 0) the intermediate bases Q_0 .. Q_{q-1}, Qt_1 .. Qt_q
+  float* tape_r = nullptr;   // (2q + 1) x lp x lp: R_0 .. R_q, then Rt_1 .. Rt_q
+  float* tape_q = nullptr;   // q x m x lp
+  float* tape_qt = nullptr;  // q x n x lp
+  bool fwd_ok = false;       // the last call on the plan was rsvd_svd (its state is intact)
+  float* bw = nullptr;       // backward workspace (allocated by the first backward call)
   __nv_bfloat16* xbf = nullptr;  // 2 lp x maxmn: transposed bfloat16 operand of the tensor-core passes
   TcPlan tc{};
+  TcPlan tc2{};   // the tensor-core pass at the width of Psi (single pass)
   // rsvd_svd_host staging
   void* a_dev = nullptr;
   float* a_f32 = nullptr;  // float32 staging of A for the host_f32 option
@@ -68,16 +80,23 @@ struct rsvd_plan_s {
   int ev_used[RSVD_NUM_STEPS] = {};
   int64_t launches[RSVD_NUM_STEPS] = {};
 
+  // 24 small blocks of lq x lq floats (each holds one padded square of any width <= lq)
   float* g() { return small; }
-  float* lbuf() { return small + 1 * (size_t)lp * lp; }
-  float* rtmp() { return small + 2 * (size_t)lp * lp; }
-  float* rinv() { return small + 3 * (size_t)lp * lp; }
-  float* racc() { return small + 4 * (size_t)lp * lp; }
-  float* ut() { return small + 5 * (size_t)lp * lp; }
-  float* w() { return small + 6 * (size_t)lp * lp; }
-  float* sq() { return small + 7 * (size_t)lp * lp; }
-  // single pass (Section 5.5): 16 more l x l blocks (see stage_single_pass)
-  float* sp(int i) { return small + (size_t)(8 + i) * lp * lp; }
+  float* lbuf() { return small + 1 * (size_t)lq * lq; }
+  float* rtmp() { return small + 2 * (size_t)lq * lq; }
+  float* rinv() { return small + 3 * (size_t)lq * lq; }
+  float* racc() { return small + 4 * (size_t)lq * lq; }
+  float* ut() { return small + 5 * (size_t)lq * lq; }
+  float* w() { return small + 6 * (size_t)lq * lq; }
+  float* sq() { return small + 7 * (size_t)lq * lq; }
+  // single pass (Section 5.5): 16 more blocks (see stage_single_pass)
+  float* sp(int i) { return small + (size_t)(8 + i) * lq * lq; }
+  // where the forward leaves the bases of Stage A: Q_j (j = 0 .. q; Q_q is always qbuf)
+  // and Qt_j (j = 1 .. q), and their R factors
+  float* basis_q(int j) { return (j < q && tape_q) ? tape_q + (size_t)j * m * lp : qbuf; }
+  float* basis_qt(int j) { return tape_qt ? tape_qt + (size_t)(j - 1) * n * lp : qtbuf; }
+  float* r_q(int j) { return tape_r ? tape_r + (size_t)j * lp * lp : nullptr; }
+  float* r_qt(int j) { return tape_r ? tape_r + (size_t)(q + j) * lp * lp : nullptr; }
 };
 
 namespace {
@@ -94,11 +113,24 @@ namespace {
     if (_s != RSVD_OK) return _s;           \
   } while (0)
 
+// Failure injection for tests (rsvd_debug_fail_alloc): the number of device allocations
+// still to succeed before one fails, or -1.
+std::atomic<int> g_fail_alloc_after{-1};
+
+bool injected_alloc_failure() {
+  int v = g_fail_alloc_after.load();
+  while (v >= 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
 template <class T>
 rsvd_status_t dalloc(rsvd_plan_t P, T** ptr, size_t elems) {
   *ptr = nullptr;
   if (elems == 0) elems = 1;
   const size_t bytes = elems * sizeof(T);
+  if (injected_alloc_failure()) return RSVD_ERR_ALLOC;
   if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) {
     cudaGetLastError();
     return RSVD_ERR_ALLOC;
@@ -117,10 +149,12 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32};
+                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32,
+                  P->tape_r, P->tape_q, P->tape_qt, P->bw};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
+  tc_plan_destroy(&P->tc2);
   delete P;
 }
 
@@ -221,16 +255,38 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
   return RSVD_OK;
 }
 
+// Yt = A^T Psi at the width of Psi (single pass): the second tensor-core plan or the
+// float32 GEMM with lpp columns; the result stays in P->partial as `*splits` slabs.
+rsvd_status_t step_pass_psi(rsvd_plan_t P, const void* A, int* splits, int64_t* stride) {
+  *stride = P->n * P->lpp;
+  Step sp(P, RSVD_STEP_PASS);
+  sp.launched();
+  if (P->opt.precision == RSVD_PLAIN_FP32) {
+    TRY(launch_gemm_f32(1, P->n, P->lpp, P->m, static_cast<const float*>(A), P->lda, P->psi, P->lpp,
+                        P->partial, P->lpp, P->splits_psi, *stride, P->st));
+    *splits = P->splits_psi;
+  } else {
+    int s = 1;
+    const int hilo = (P->opt.residual_passes && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
+    if (tc_pass(&P->tc2, 1, 0, hilo, P->partial, &s, P->st) != 0) return RSVD_ERR_CUDA;
+    *splits = s;
+  }
+  return RSVD_OK;
+}
+
 // Cholesky-QR rounds on the (summed) partial slabs; the basis ends in `dst`
 // (rows x lp).  With `racc`, the triangular factors are multiplied into it.
 rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t stride, int64_t rows,
-                        float* dst, float* racc, bool final_basis = true) {
+                        float* dst, float* racc, bool final_basis = true, int width = 0) {
   // A basis that only feeds the next power-iteration pass needs to span the sample, not
   // to be orthonormal to working precision: the shifted round and one plain round leave
   // ||Q^T Q - I|| ~ u kappa(Q_1)^2 with kappa(Q_1) modest after the shift, and the next
   // orthonormalisation starts from the product anyway.  Final bases get every round.
+  // width: the columns of the sample (0: l; the single pass also orthonormalises the l'
+  // columns of A^T Psi).
   const int rounds = final_basis ? P->opt.orth_rounds : std::min(P->opt.orth_rounds, 2);
-  const int lp = P->lp;
+  const int wl = width ? width : P->l;
+  const int lp = (int)round_up(wl, 16);
   const int nblk = gram_blocks(rows);
   Step sp(P, RSVD_STEP_ORTH);
   sp.launched(lp <= 128 ? 3 * rounds + 1 : 4 * rounds);
@@ -244,7 +300,7 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
     for (int r = 0; r < rounds; ++r) {
       const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
-      TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+      TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
                           r == 0 ? 1 : 0, P->status, P->st));
       const bool last = (r == rounds - 1);
       float* next = last ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
@@ -273,7 +329,7 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     if (cur_splits > 1) cur = P->tmp1;
     TRY(launch_gram_reduce(P->gpart, gblk, lp, P->g(), P->st));
     const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
-    TRY(launch_cholesky(P->g(), P->l, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+    TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
                         r == 0 ? 1 : 0, P->status, P->st));
     float* next = (r == rounds - 1) ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
     if (tc_gram)
@@ -303,15 +359,16 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   TRYS(step_draw(P, tc));
   int s;
   int64_t stride;
+  // the bases go where the backward finds them (the tape in store mode), with their R factors
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
-  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr, P->q == 0));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(0), P->r_q(0), P->q == 0));
   for (int j = 1; j <= P->q; ++j) {
-    if (tc) TRYS(step_convert(P, P->qbuf, P->m, 0));
-    TRYS(step_pass(P, A, 1, P->qbuf, false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, nullptr, false));
-    if (tc) TRYS(step_convert(P, P->qtbuf, P->n, 0));
-    TRYS(step_pass(P, A, 0, P->qtbuf, false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, nullptr, j == P->q));
+    if (tc) TRYS(step_convert(P, P->basis_q(j - 1), P->m, 0));
+    TRYS(step_pass(P, A, 1, P->basis_q(j - 1), false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->n, P->basis_qt(j), P->r_qt(j), false));
+    if (tc) TRYS(step_convert(P, P->basis_qt(j), P->n, 0));
+    TRYS(step_pass(P, A, 0, P->basis_qt(j), false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(j), P->r_q(j), j == P->q));
   }
   return RSVD_OK;
 }
@@ -345,103 +402,326 @@ rsvd_status_t check_plan(rsvd_plan_t P) {
   return RSVD_OK;
 }
 
-// Single-pass randomized SVD (Section 5.5): Y = A Omega and Yt = A^T Psi from the
-// two sketches alone, Y = Q R and Yt = Qt Rt (Cholesky QR); the bases are cut to the k
-// leading left singular vectors Q_k = Q U_R[:, :k], Qt_k = Qt U_Rt[:, :k] (the remedy of
-// the section's remark on single-pass error: the systems below become k x l,
-// overdetermined), and the reduced k x k matrix B ~ Q_k^T A Qt_k is the minimum-residual
-// solution of
-//     B X1 = C1,  B^T X2 = C2,   X1 = Qt_k^T Omega, C1 = Q_k^T Y = U_R_k^T R,
-//                                X2 = Q_k^T Psi,    C2 = Qt_k^T Yt = U_Rt_k^T Rt,
+// Single-pass randomized SVD (Section 5.5): Y = A Omega (n x l) and Yt = A^T Psi (Psi m x l')
+// from the two sketches alone, Y = Q R and Yt = Qt Rt (Cholesky QR); the bases are cut to
+// the k leading left singular vectors Q_k = Q U_R[:, :k], Qt_k = Qt U_Rt[:, :k] (the remedy
+// of the section's remark on single-pass error: the systems below become k x l and
+// k x l', overdetermined), and the reduced k x k matrix B ~ Q_k^T A Qt_k is the
+// minimum-residual solution of
+//     B X1 = C1,  B^T X2 = C2,   X1 = Qt_k^T Omega (k x l),  C1 = Q_k^T Y = U_R_k^T R,
+//                                X2 = Q_k^T Psi (k x l'),    C2 = Qt_k^T Yt = U_Rt_k^T Rt,
 // i.e. of the Sylvester normal equations (X2 X2^T) B + B (X1 X1^T) = C1 X1^T + X2 C2^T,
-// solved in the singular bases of X1 and X2: X_i = U_i S_i W_i^T gives
-// B = U2 [(U2^T F U1) ./ (s2_i^2 + s1_j^2)] U1^T, F = C1 X1^T + X2 C2^T.  Then B = Ub Sb Vb^T
-// (Jacobi), U = Q (U_R_k Ub), V = Qt (U_Rt_k Vb).  q is ignored; A is read by one pass of
-// each kind.
+// solved in the eigenbases of the two k x k Gram matrices: X1 X1^T = U1 L1 U1^T,
+// X2 X2^T = U2 L2 U2^T give B = U2 [(U2^T F U1) ./ (L2_i + L1_j)] U1^T, F = C1 X1^T + X2 C2^T
+// (the eigendecompositions come from the one-sided Jacobi SVD of the symmetric positive
+// semidefinite Grams).  Then B = Ub Sb Vb^T (Jacobi), U = Q (U_R_k Ub), V = Qt (U_Rt_k Vb).
+// q is ignored; A is read by one pass of each kind.
+// Small blocks: R (lp, ld lp), Rt (lpp, ld lpp), the k x k matrices with ld kp = k rounded
+// up to 16.
 rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S, float* V,
                                 float* Qout, int64_t ldq) {
   const bool tc = P->opt.precision == RSVD_BF16_TC;
-  const int lp = P->lp, l = P->l;
-  const size_t l2 = (size_t)lp * lp;
-  if (tc)
-    TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  const int lp = P->lp, l = P->l, lpp = P->lpp, lt = P->lt, lq = P->lq, k = P->k;
+  const int kp = (int)round_up(k, 16);
+  if (tc) {
+    const int lo = P->opt.dtype_A == RSVD_BF16X2;
+    if (tc_bind_a(&P->tc, A, lo) != 0 || tc_bind_a(&P->tc2, A, lo) != 0) return RSVD_ERR_CUDA;
+  }
   int s;
   int64_t stride;
-  // Y = A Omega, Y = Q R (R accumulated into racc, then kept as C1)
+  // Y = A Omega, Y = Q R (R kept in sp(2))
   TRYS(step_draw(P, tc));
   // the cross products below must see the test matrices the bf16 passes multiplied with
   if (tc) TRY(launch_round_bf16(P->omega, P->n, lp, lp, P->st));
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
-  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, P->racc()));
-  TRY(cudaMemcpyAsync(P->sp(2), P->racc(), sizeof(float) * l2, cudaMemcpyDeviceToDevice, P->st));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, P->sp(2)));
   if (Qout) TRY(launch_gather(P->qbuf, 1, 0, lp, Qout, ldq, P->m, l, l, P->st));
-  // Yt = A^T Psi (Psi: Gaussian, stream 1), Yt = Qt Rt
+  // Yt = A^T Psi (Psi: Gaussian, stream 1, l' columns), Yt = Qt Rt (Rt in racc, ld lpp)
   {
     Step sp(P, RSVD_STEP_DRAW);
     sp.launched();
-    TRY(launch_draw_gaussian(P->seed, 1u, P->m, l, lp, P->psi, lp, tc ? P->xbf : nullptr,
+    TRY(launch_draw_gaussian(P->seed, 1u, P->m, lt, lpp, P->psi, lpp, tc ? P->xbf : nullptr,
                              tc_ld(P->m), P->st));
-    if (tc) TRY(launch_round_bf16(P->psi, P->m, lp, lp, P->st));
+    if (tc) TRY(launch_round_bf16(P->psi, P->m, lpp, lpp, P->st));
   }
-  TRYS(step_pass(P, A, 1, P->psi, false, &s, &stride));
-  TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc()));
-  const int k = P->k;
+  TRYS(step_pass_psi(P, A, &s, &stride));
+  TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc(), true, lt));
   {
     Step sp(P, RSVD_STEP_SMALL_SVD);
-    // (two pairs of Jacobi SVDs run one launch each on the cluster kernel)
-    const bool paired = P->opt.small_svd == 2 || (P->opt.small_svd == 0 && l >= 48);
-    sp.launched(paired ? 20 : 24);
-    // X1 = Qt^T Omega (K = n), X2 = Q^T Psi (K = m): split over row blocks, summed by gather
+    sp.launched(23);
+    // X1 = Qt^T Omega (lpp x lp, K = n), X2 = Q^T Psi (lp x lpp, K = m): row blocks, summed
     const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
     const int s1 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->n, 512)));
-    TRY(launch_gemm_f32(1, lp, lp, P->n, P->qtbuf, lp, P->omega, lp, P->gpart, lp, s1, l2, P->st));
-    TRY(launch_gather(P->gpart, s1, l2, lp, P->sp(0), lp, lp, lp, lp, P->st));
+    const int64_t l12 = (int64_t)lpp * lp;
+    TRY(launch_gemm_f32(1, lpp, lp, P->n, P->qtbuf, lpp, P->omega, lp, P->gpart, lp, s1, l12, P->st));
+    TRY(launch_gather(P->gpart, s1, l12, lp, P->sp(0), lp, lpp, lp, lp, P->st));
     const int s2 = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->m, 512)));
-    TRY(launch_gemm_f32(1, lp, lp, P->m, P->qbuf, lp, P->psi, lp, P->gpart, lp, s2, l2, P->st));
-    TRY(launch_gather(P->gpart, s2, l2, lp, P->sp(1), lp, lp, lp, lp, P->st));
-    // the k leading left singular vectors of Y = Q R and Yt = Qt Rt: Q U_R[:, :k], Qt U_Rt[:, :k]
-    // (the two SVDs are independent: one launch, one cluster each; the second's discarded W
-    // and scratch are the factorisation's buffers, free after the orthonormalisations)
-    TRY(launch_jacobi_svd_pair(P->sp(2), P->racc(), lp, 0, l, lp, P->sp(5), P->sp(6), P->sig2,
-                               P->sig2 + lp, P->sp(7), P->rtmp(), P->lbuf(), P->rinv(), P->status,
-                               P->status + 1, P->st, P->opt.small_svd));
-    // the k x l systems: X1 = U_Rt_k^T (Qt^T Omega), C1 = U_R_k^T R, X2 = U_R_k^T (Q^T Psi),
-    // C2 = U_Rt_k^T Rt (rows k..l-1 of the padded squares stay zero)
-    for (int i : {3, 4, 8, 9}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * l2, P->st));
-    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(6), lp, 1, P->sp(0), lp, 0, 0.f, P->sp(3), lp, P->st));
+    TRY(launch_gemm_f32(1, lp, lpp, P->m, P->qbuf, lp, P->psi, lpp, P->gpart, lpp, s2, l12, P->st));
+    TRY(launch_gather(P->gpart, s2, l12, lpp, P->sp(1), lpp, lp, lpp, lpp, P->st));
+    // the left singular vectors of R and of Rt: U_R (sp(5), ld lp), U_Rt (sp(6), ld lpp)
+    TRY(launch_jacobi_svd(P->sp(2), lp, 0, l, lp, P->sp(5), P->sig2, P->sp(7), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd == 1 && l > 160 ? 0 : P->opt.small_svd));
+    TRY(launch_jacobi_svd(P->racc(), lpp, 0, lt, lpp, P->sp(6), P->sig2 + lq, P->rtmp(), P->lbuf(),
+                          P->status, P->status + 1, P->st,
+                          P->opt.small_svd == 1 && lt > 160 ? 0 : P->opt.small_svd));
+    // the k x l and k x l' systems (sp(3) X1_k, sp(8) C1: ld lp; sp(4) X2_k, sp(9) C2: ld lpp)
+    for (int i : {3, 4, 8, 9}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * lq * lq, P->st));
+    TRY(launch_small_gemm(k, l, lt, 1.f, P->sp(6), lpp, 1, P->sp(0), lp, 0, 0.f, P->sp(3), lp, P->st));
     TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(2), lp, 0, 0.f, P->sp(8), lp, P->st));
-    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(5), lp, 1, P->sp(1), lp, 0, 0.f, P->sp(4), lp, P->st));
-    TRY(launch_small_gemm(k, l, l, 1.f, P->sp(6), lp, 1, P->racc(), lp, 0, 0.f, P->sp(9), lp, P->st));
-    // singular bases of X1 (U1 = sp(10), s1) and X2 (U2 = sp(11), s2): k nonzero values each.
-    // The one-sided Jacobi runs on X1^T and X2^T: their columns are the k rows of the k x l
-    // systems plus l - k zero columns that never rotate, where the l columns of X1 itself
-    // would be l vectors in a k-dimensional space, l - k of them rounding noise that no
-    // sweep can make orthogonal to the rest.  X^T = Ut S W^T gives X = W S Ut^T: the left
-    // singular vectors are the accumulated rotations W.
-    TRY(launch_jacobi_svd_pair(P->sp(3), P->sp(4), lp, 1, l, lp, P->sp(7), P->rtmp(), P->sig2,
-                               P->sig2 + lp, P->sp(10), P->sp(11), P->lbuf(), P->rinv(), P->status,
+    TRY(launch_small_gemm(k, lt, l, 1.f, P->sp(5), lp, 1, P->sp(1), lpp, 0, 0.f, P->sp(4), lpp, P->st));
+    TRY(launch_small_gemm(k, lt, lt, 1.f, P->sp(6), lpp, 1, P->racc(), lpp, 0, 0.f, P->sp(9), lpp, P->st));
+    // the normal-equation matrices G1 = X1_k X1_k^T, G2 = X2_k X2_k^T (k x k, ld kp) and their
+    // eigenbases (U1 in sp(10), U2 in sp(11); eigenvalues in sig2 and sig2 + lq)
+    for (int i : {12, 13}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * lq * lq, P->st));
+    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(3), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), kp, P->st));
+    TRY(launch_small_gemm(k, k, lt, 1.f, P->sp(4), lpp, 0, P->sp(4), lpp, 1, 0.f, P->sp(13), kp, P->st));
+    TRY(launch_jacobi_svd_pair(P->sp(12), P->sp(13), kp, 0, k, kp, P->sp(10), P->sp(11), P->sig2,
+                               P->sig2 + lq, P->sp(7), P->rtmp(), P->lbuf(), P->rinv(), P->status,
                                P->status + 1, P->st, P->opt.small_svd));
-    // F = C1 X1^T + X2 C2^T; G = U2^T F U1; H = G ./ (s2^2 + s1^2); B = U2 H U1^T (all k x k)
-    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(8), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), lp, P->st));
-    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(4), lp, 0, P->sp(9), lp, 1, 1.f, P->sp(12), lp, P->st));
-    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), lp, 1, P->sp(12), lp, 0, 0.f, P->sp(13), lp, P->st));
-    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(13), lp, 0, P->sp(10), lp, 0, 0.f, P->sp(12), lp, P->st));
-    TRY(launch_sylvester_scale(P->sp(12), k, lp, P->sig2 + lp, P->sig2, P->sp(13), P->st));
-    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), lp, 0, P->sp(13), lp, 0, 0.f, P->sp(12), lp, P->st));
-    TRY(cudaMemsetAsync(P->sq(), 0, sizeof(float) * l2, P->st));
-    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(12), lp, 0, P->sp(10), lp, 1, 0.f, P->sq(), lp, P->st));
-    // B = Ub Sb Vb^T (k x k), then the lifts' small factors U_R_k Ub and U_Rt_k Vb
-    TRY(launch_jacobi_svd(P->sq(), lp, 0, k, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+    // F = C1 X1_k^T + X2_k C2^T; G = U2^T F U1; H = G ./ (L2_i + L1_j); B = U2 H U1^T (k x k)
+    TRY(launch_small_gemm(k, k, l, 1.f, P->sp(8), lp, 0, P->sp(3), lp, 1, 0.f, P->sp(12), kp, P->st));
+    TRY(launch_small_gemm(k, k, lt, 1.f, P->sp(4), lpp, 0, P->sp(9), lpp, 1, 1.f, P->sp(12), kp, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), kp, 1, P->sp(12), kp, 0, 0.f, P->sp(13), kp, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(13), kp, 0, P->sp(10), kp, 0, 0.f, P->sp(12), kp, P->st));
+    TRY(launch_sylvester_scale(P->sp(12), k, kp, P->sig2 + lq, P->sig2, 1, P->sp(13), P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(11), kp, 0, P->sp(13), kp, 0, 0.f, P->sp(12), kp, P->st));
+    TRY(cudaMemsetAsync(P->sq(), 0, sizeof(float) * lq * lq, P->st));
+    TRY(launch_small_gemm(k, k, k, 1.f, P->sp(12), kp, 0, P->sp(10), kp, 1, 0.f, P->sq(), kp, P->st));
+    // B = Ub Sb Vb^T (k x k), then the lifts' small factors U_R_k Ub (l x k) and U_Rt_k Vb
+    // (l' x k), rows beyond l and l' zero (sp(14), sp(15), ld kp)
+    TRY(launch_jacobi_svd(P->sq(), kp, 0, k, kp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
                           P->status + 1, P->st, P->opt.small_svd));
-    TRY(launch_small_gemm(l, k, k, 1.f, P->sp(5), lp, 0, P->ut(), lp, 0, 0.f, P->sp(14), lp, P->st));
-    TRY(launch_small_gemm(l, k, k, 1.f, P->sp(6), lp, 0, P->w(), lp, 0, 0.f, P->sp(15), lp, P->st));
+    for (int i : {14, 15}) TRY(cudaMemsetAsync(P->sp(i), 0, sizeof(float) * lq * lq, P->st));
+    TRY(launch_small_gemm(l, k, k, 1.f, P->sp(5), lp, 0, P->ut(), kp, 0, 0.f, P->sp(14), kp, P->st));
+    TRY(launch_small_gemm(lt, k, k, 1.f, P->sp(6), lpp, 0, P->w(), kp, 0, 0.f, P->sp(15), kp, P->st));
   }
   if (!U) return RSVD_OK;
   Step sp(P, RSVD_STEP_LIFT);
   sp.launched(2);
-  TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->sp(14), lp, U, P->k, 1, 0, P->st));
-  TRY(launch_gemm_f32(0, P->n, P->k, lp, P->qtbuf, lp, P->sp(15), lp, V, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->sp(14), kp, U, P->k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->n, P->k, lpp, P->qtbuf, lpp, P->sp(15), kp, V, P->k, 1, 0, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+// ---- backward (reverse mode through Algorithm 4.4 + Algorithm 5.1, Omega fixed) ----------
+//
+// Forward map: Y_0 = A Omega = Q_0 R_0; Yt_j = A^T Q_{j-1} = Qt_j Rt_j, Y_j = A Qt_j = Q_j R_j
+// (j = 1 .. q); B = Q_q^T A = Ut S V_B^T (the thin SVD, computed as B^T = Q_B R_B and
+// R_B^T = Ut S W^T, V_B = Q_B W); U = Q_q Ut_k, S = S_k, V = V_B_k.
+// Given the cotangents gU, gS, gV (and the loss ||A - U S V^T||_F^2 + sum S when add_recon):
+//   SVD of B:   J = Ut^T (Q^T gU), K = V_B^T gV, M = F o (J - J^T) S + S F o (K - K^T) + diag gS,
+//               gB^T = Z Ut^T with Z = V_B (M^T - K S^-1) + gV S^-1   (F_ij = 1 / (s_j^2 - s_i^2))
+//   B = Q^T A:  gA += (Q Ut) Z^T,  gQ = (gU | 0) Ut^T + (A Z) Ut^T
+//   Y = Q R:    gY = (gQ + Q copyltu(-gQ^T Q)) R^-T          (R itself unused downstream)
+//   Y = A X:    gA += gY X^T,  gX = A^T gY;   Y = A^T X likewise
+// and with add_recon the reconstruction term adds 2 A - 2 U S V^T to gA and
+// 2 S^2 U - 2 (A V) S to gU, 1 to gS (U^T A V = S and A^T U = V S for the exact SVD of B).
+// gA = alpha A + L R^T is formed by one tiled product over the stacked factors (store
+// mode), or pair by pair (recompute mode, which keeps no stack and recomputes the
+// intermediate bases of Stage A from A).
+struct Bw {
+  // m side (rows m x lp), n side (rows n x lp), small (lp x lp)
+  float *gq, *tm, *ufull, *pm;
+  float *vb, *z, *tn, *gqt;
+  float *J, *K, *M2, *C, *N, *rinv, *utc, *wc, *t1, *gst;
+  float *wq0, *wq1, *wqt;      // recompute mode: Q_{j-1} / Q_j (ping-pong) and Qt_j
+  float *lf, *rf;              // store mode: the stacked factors (m x kr, n x kr)
+  int kr;
+};
+
+size_t bw_layout(rsvd_plan_t P, Bw* b, float* base) {
+  const size_t m = P->m, n = P->n, lp = P->lp, l2 = lp * lp;
+  const bool store = P->opt.recompute == 0;
+  const int blocks = 2 * P->q + 3;   // (recon) + (U_full, Z) + 2 per power step + (gY_0, Omega)
+  b->kr = blocks * (int)lp;
+  size_t off = 0;
+  auto take = [&](float** p, size_t elems) {
+    *p = base ? base + off : nullptr;
+    off += (elems + 63) & ~size_t(63);
+  };
+  take(&b->gq, m * lp); take(&b->tm, m * lp); take(&b->ufull, m * lp); take(&b->pm, m * lp);
+  take(&b->vb, n * lp); take(&b->z, n * lp); take(&b->tn, n * lp); take(&b->gqt, n * lp);
+  for (float** p : {&b->J, &b->K, &b->M2, &b->C, &b->N, &b->rinv, &b->utc, &b->wc, &b->t1})
+    take(p, l2);
+  take(&b->gst, lp);
+  b->wq0 = b->wq1 = b->wqt = b->lf = b->rf = nullptr;
+  if (store) {
+    take(&b->lf, m * (size_t)b->kr);
+    take(&b->rf, n * (size_t)b->kr);
+  } else {
+    take(&b->wq0, m * lp); take(&b->wq1, m * lp); take(&b->wqt, n * lp);
+  }
+  return off;
+}
+
+// out (rows_out x lp) = A X or A^T X for a float32 X (rows_in x lp): one pass with the plan's
+// precision; on the tensor cores X goes in as a bfloat16 hi + lo pair (and A as hi + lo
+// when stored so), so the product carries about 16 bits of the operand.
+rsvd_status_t bw_pass(rsvd_plan_t P, const void* A, int trans, const float* X, float* out) {
+  const int64_t rows_in = trans ? P->m : P->n, rows_out = trans ? P->n : P->m;
+  const int lp = P->lp;
+  int s = 1;
+  int64_t stride = rows_out * lp;
+  Step sp(P, RSVD_STEP_PASS);
+  sp.launched(P->opt.precision == RSVD_BF16_TC ? 3 : 2);
+  if (P->opt.precision == RSVD_PLAIN_FP32) {
+    s = trans ? P->splits_t : P->splits_n;
+    TRY(launch_gemm_f32(trans, rows_out, lp, rows_in, static_cast<const float*>(A), P->lda, X, lp,
+                        P->partial, lp, s, stride, P->st));
+  } else {
+    TRY(launch_to_bf16_t(X, rows_in, lp, P->xbf, tc_ld(rows_in), 1, tc_lo_offset(lp), P->st));
+    const int hilo = P->opt.dtype_A == RSVD_BF16X2 ? 1 : 0;
+    if (tc_pass(&P->tc, trans, 1, hilo, P->partial, &s, P->st) != 0) return RSVD_ERR_CUDA;
+  }
+  TRY(launch_gather(P->partial, s, stride, lp, out, lp, rows_out, lp, lp, P->st));
+  return RSVD_OK;
+}
+
+// out (lp x ncols, ld lp, zero-padded to lp columns) = X^T Y for X (rows x lp), Y (rows x
+// ncols, ld ldy): row blocks as split-K partials, summed in a fixed order.
+rsvd_status_t bw_tn(rsvd_plan_t P, int64_t rows, const float* X, const float* Y, int ldy, int ncols,
+                    float* out) {
+  const int lp = P->lp;
+  const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
+  const int s = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(rows, 512)));
+  const int64_t l2 = (int64_t)lp * lp;
+  TRY(launch_gemm_f32(1, lp, ncols, rows, X, lp, Y, ldy, P->gpart, lp, s, l2, P->st));
+  TRY(launch_gather(P->gpart, s, l2, lp, out, lp, lp, ncols, lp, P->st));
+  return RSVD_OK;
+}
+
+// gY = (gQ + Q copyltu(-gQ^T Q)) R^-T for Y = Q R (rows x lp)
+rsvd_status_t bw_qr(rsvd_plan_t P, Bw& b, int64_t rows, const float* Q, const float* gQ,
+                    const float* R, float* T, float* gY) {
+  const int lp = P->lp;
+  TRYS(bw_tn(P, rows, gQ, Q, lp, lp, b.C));
+  TRY(launch_copyltu_neg(b.C, lp, b.N, P->st));
+  TRY(launch_gather(gQ, 1, 0, lp, T, lp, rows, lp, lp, P->st));
+  TRY(launch_small_gemm((int)rows, lp, lp, 1.0f, Q, lp, 0, b.N, lp, 0, 1.0f, T, lp, P->st));
+  TRY(launch_trinv_upper(R, P->l, lp, b.rinv, P->st));
+  TRY(launch_small_gemm((int)rows, lp, lp, 1.0f, T, lp, 0, b.rinv, lp, 1, 0.0f, gY, lp, P->st));
+  return RSVD_OK;
+}
+
+// Stage A again (recompute mode): with Q_{j-1} in *qprev, Qt_j in b.wqt and, for j < q, Q_j
+// in *qcur -- the forward's kernels and rounds, so the bases are the forward's bit for bit.
+rsvd_status_t bw_recompute(rsvd_plan_t P, const void* A, Bw& b, int j, float** qprev, float** qcur) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  float* buf[2] = {b.wq0, b.wq1};
+  int s;
+  int64_t stride;
+  TRYS(step_draw(P, tc));
+  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, buf[0], nullptr, P->q == 0));
+  const int last = (j < P->q) ? j : j - 1;   // the last Q_i needed
+  for (int i = 1; i <= j; ++i) {
+    if (tc) TRYS(step_convert(P, buf[(i - 1) & 1], P->m, 0));
+    TRYS(step_pass(P, A, 1, buf[(i - 1) & 1], false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->n, b.wqt, nullptr, false));
+    if (i > last) break;
+    if (tc) TRYS(step_convert(P, b.wqt, P->n, 0));
+    TRYS(step_pass(P, A, 0, b.wqt, false, &s, &stride));
+    TRYS(step_orth(P, P->partial, s, stride, P->m, buf[i & 1], nullptr, i == P->q));
+  }
+  *qprev = buf[(j - 1) & 1];
+  *qcur = (j < P->q) ? buf[j & 1] : P->qbuf;
+  return RSVD_OK;
+}
+
+rsvd_status_t run_backward(rsvd_plan_t P, const void* A, const float* gU, const float* gS,
+                           const float* gV, int add_recon, float* gA) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  const bool store = P->opt.recompute == 0;
+  const int lp = P->lp, l = P->l, k = P->k, q = P->q;
+  const int64_t m = P->m, n = P->n;
+  Bw b;
+  if (!P->bw) {
+    const size_t elems = bw_layout(P, &b, nullptr);
+    TRYS(dalloc(P, &P->bw, elems));
+  }
+  bw_layout(P, &b, P->bw);
+  if (tc)
+    TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
+  const int adt = P->opt.dtype_A == RSVD_F32 ? 0 : (P->opt.dtype_A == RSVD_BF16 ? 1 : 2);
+  const float alpha = add_recon ? 2.0f : 0.0f;
+  int block = 0;
+  // one factor pair (L: m x lp, R: n x lp) of gA = alpha A + sum L R^T
+  auto emit = [&](const float* L, const float* R) -> rsvd_status_t {
+    if (store) {
+      TRY(launch_gather(L, 1, 0, lp, b.lf + (size_t)block * lp, b.kr, m, lp, lp, P->st));
+      TRY(launch_gather(R, 1, 0, lp, b.rf + (size_t)block * lp, b.kr, n, lp, lp, P->st));
+    } else {
+      TRY(launch_lowrank_update(m, n, lp, L, lp, R, lp, A, P->lda, adt, block == 0 ? alpha : 0.0f,
+                                block == 0 ? 0.0f : 1.0f, gA, n, P->st));
+    }
+    ++block;
+    return RSVD_OK;
+  };
+  const size_t l2 = (size_t)lp * lp;
+  // clean l x l copies of Ut and W (zero beyond l)
+  TRY(cudaMemsetAsync(b.utc, 0, sizeof(float) * l2, P->st));
+  TRY(cudaMemsetAsync(b.wc, 0, sizeof(float) * l2, P->st));
+  TRY(launch_gather(P->ut(), 1, 0, lp, b.utc, lp, l, l, l, P->st));
+  TRY(launch_gather(P->w(), 1, 0, lp, b.wc, lp, l, l, l, P->st));
+  // V_B = Q_B W, U_full = Q Ut
+  TRY(launch_small_gemm((int)n, lp, lp, 1.0f, P->qtbuf, lp, 0, b.wc, lp, 0, 0.0f, b.vb, lp, P->st));
+  TRY(launch_small_gemm((int)m, lp, lp, 1.0f, P->qbuf, lp, 0, b.utc, lp, 0, 0.0f, b.ufull, lp, P->st));
+  // the reconstruction loss: P = A V_B, gU_t = gU + 2 S^2 U - 2 S P, gS_t = gS + 1, and the
+  // factor (-2 U S, V) of -2 U S V^T
+  if (add_recon) {
+    TRYS(bw_pass(P, A, 0, b.vb, b.pm));
+    TRY(launch_colscale(m, k, lp, b.ufull, lp, P->sig, 0, -2.0f, 0, b.tm, P->st));
+    TRY(launch_colscale(n, k, lp, b.vb, lp, nullptr, 0, 1.0f, 0, b.tn, P->st));
+    TRYS(emit(b.tm, b.tn));
+  }
+  TRY(launch_recon_cotangent(m, k, lp, gU, b.ufull, b.pm, P->sig, add_recon, b.gq, P->st));
+  TRY(launch_gs_total(gS, k, add_recon, b.gst, P->st));
+  // J = Ut^T (Q^T gU_t), K = V_B^T gV (lp x lp, zero beyond column k)
+  TRYS(bw_tn(P, m, P->qbuf, b.gq, lp, lp, b.t1));
+  TRY(launch_small_gemm(lp, lp, lp, 1.0f, b.utc, lp, 1, b.t1, lp, 0, 0.0f, b.J, lp, P->st));
+  if (gV) {
+    TRY(launch_colscale(n, k, lp, gV, k, nullptr, 0, 1.0f, 0, b.tn, P->st));   // gV padded to lp columns
+    TRYS(bw_tn(P, n, b.vb, b.tn, lp, lp, b.K));
+  } else {
+    TRY(cudaMemsetAsync(b.K, 0, sizeof(float) * l2, P->st));
+  }
+  TRY(launch_svd_adjoint(b.J, b.K, P->sig, b.gst, k, l, lp, b.M2, P->st));
+  // Z = V_B M2 + gV S^-1
+  TRY(launch_small_gemm((int)n, lp, lp, 1.0f, b.vb, lp, 0, b.M2, lp, 0, 0.0f, b.z, lp, P->st));
+  if (gV) TRY(launch_colscale(n, k, lp, gV, k, P->sig, 1, 1.0f, 1, b.z, P->st));
+  TRYS(emit(b.ufull, b.z));                                    // gA += (Q Ut) Z^T
+  // gQ = ((gU_t | 0) + A Z) Ut^T
+  TRYS(bw_pass(P, A, 0, b.z, b.tm));
+  TRY(launch_colscale(m, lp, lp, b.gq, lp, nullptr, 0, 1.0f, 1, b.tm, P->st));
+  TRY(launch_small_gemm((int)m, lp, lp, 1.0f, b.tm, lp, 0, b.utc, lp, 1, 0.0f, b.gq, lp, P->st));
+  // Stage A in reverse
+  float* q0 = P->basis_q(0);
+  for (int j = q; j >= 1; --j) {
+    float *qprev, *qcur, *qt;
+    if (store) {
+      qprev = P->basis_q(j - 1);
+      qcur = P->basis_q(j);
+      qt = P->basis_qt(j);
+    } else {
+      TRYS(bw_recompute(P, A, b, j, &qprev, &qcur));
+      qt = b.wqt;
+    }
+    TRYS(bw_qr(P, b, m, qcur, b.gq, P->r_q(j), b.tm, b.pm));     // gY_j
+    TRYS(emit(b.pm, qt));                                       // gA += gY_j Qt_j^T
+    TRYS(bw_pass(P, A, 1, b.pm, b.gqt));                        // gQt_j = A^T gY_j
+    TRYS(bw_qr(P, b, n, qt, b.gqt, P->r_qt(j), b.tn, b.z));     // gYt_j
+    TRYS(emit(qprev, b.z));                                     // gA += Q_{j-1} gYt_j^T
+    TRYS(bw_pass(P, A, 0, b.z, b.gq));                          // gQ_{j-1} = A gYt_j
+    if (j == 1) q0 = qprev;                                     // (recompute mode: still held)
+  }
+  TRYS(bw_qr(P, b, m, q0, b.gq, P->r_q(0), b.tm, b.pm));       // gY_0
+  // Omega as the forward multiplied with it (the draw, or the caller's matrix)
+  TRYS(step_draw(P, false));
+  TRYS(emit(b.pm, P->omega));                                   // gA += gY_0 Omega^T
+  if (store)
+    TRY(launch_lowrank_update(m, n, block * lp, b.lf, b.kr, b.rf, b.kr, A, P->lda, adt, alpha, 0.0f,
+                              gA, n, P->st));
   return RSVD_OK;
 }
 
@@ -506,12 +786,25 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
   if (o.host_f32 != 0 && (o.host_f32 != 1 || o.precision != RSVD_BF16_TC)) return RSVD_ERR_INVALID_ARG;
-  if (o.recompute != 0) return RSVD_ERR_UNSUPPORTED;  // the single-matrix backward keeps no samples
+  if (o.recompute != 0 && o.recompute != 1) return RSVD_ERR_INVALID_ARG;
 
   rsvd_plan_t P = new (std::nothrow) rsvd_plan_s();
   if (!P) return RSVD_ERR_ALLOC;
   P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l;
   P->lp = (int)round_up(l, 16);
+  P->lt = P->lpp = 0;
+  if (o.single_pass) {
+    // Psi: l' columns (Section 5.5 leaves its width open; the default 3 l keeps the system
+    // for B^T overdetermined enough on noisy tails)
+    int64_t lt = o.psi_cols ? o.psi_cols : std::min<int64_t>(std::min<int64_t>(3 * l, kMaxL), n);
+    if (lt < k || lt > kMaxL || lt > n || lt > m) {
+      delete P;
+      return RSVD_ERR_INVALID_ARG;
+    }
+    P->lt = (int)lt;
+    P->lpp = (int)round_up(lt, 16);
+  }
+  P->lq = std::max(P->lp, P->lpp);
   P->seed = seed; P->opt = o; P->lda = o.lda;
   P->maxmn = std::max(m, n);
   P->st = static_cast<cudaStream_t>(stream);
@@ -533,47 +826,61 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     const char* e = getenv("RSVD_NO_GRAPH");
     P->use_graph = !(e && e[0] && e[0] != '0');
   }
-  const int lp = P->lp;
+  const int lp = P->lp, lq = P->lq;
   P->splits_n = choose_splits(m, lp, n, P->num_sms);
   P->splits_t = choose_splits(n, lp, m, P->num_sms);
   int64_t part = std::max((int64_t)P->splits_n * m, (int64_t)P->splits_t * n) * lp;
-  if (o.precision == RSVD_BF16_TC) part = std::max(part, tc_partial_elems(m, n, lp, P->num_sms));
+  if (o.single_pass) {
+    P->splits_psi = choose_splits(n, P->lpp, m, P->num_sms);
+    part = std::max(part, (int64_t)P->splits_psi * n * P->lpp);
+  }
+  if (o.precision == RSVD_BF16_TC) part = std::max(part, tc_partial_elems(m, n, lq, P->num_sms));
   P->partial_elems = part;
   rsvd_status_t s = RSVD_OK;
   const int nblk = std::max(gram_blocks(m), gram_blocks(n));
   if ((s = dalloc(P, &P->omega, (size_t)n * lp)) != RSVD_OK ||
       (s = dalloc(P, &P->qbuf, (size_t)m * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->qtbuf, (size_t)n * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->tmp1, (size_t)P->maxmn * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->tmp2, (size_t)P->maxmn * lp)) != RSVD_OK ||
+      (s = dalloc(P, &P->qtbuf, (size_t)n * lq)) != RSVD_OK ||
+      (s = dalloc(P, &P->tmp1, (size_t)P->maxmn * lq)) != RSVD_OK ||
+      (s = dalloc(P, &P->tmp2, (size_t)P->maxmn * lq)) != RSVD_OK ||
       (s = dalloc(P, &P->partial, (size_t)part)) != RSVD_OK ||
-      (s = dalloc(P, &P->gpart, (size_t)nblk * lp * lp)) != RSVD_OK ||
-      (s = dalloc(P, &P->small, (size_t)24 * lp * lp)) != RSVD_OK ||
-      (o.single_pass && (s = dalloc(P, &P->psi, (size_t)m * lp)) != RSVD_OK) ||
-      (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lp)) != RSVD_OK) ||
+      (s = dalloc(P, &P->gpart, (size_t)nblk * lq * lq)) != RSVD_OK ||
+      (s = dalloc(P, &P->small, (size_t)24 * lq * lq)) != RSVD_OK ||
+      (o.single_pass && (s = dalloc(P, &P->psi, (size_t)m * P->lpp)) != RSVD_OK) ||
+      (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lq)) != RSVD_OK) ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
       (o.test_matrix == RSVD_SRFT && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
     free_plan(P);
     return s;
   }
-  if (o.precision == RSVD_BF16_TC && lp > 128 &&
-      (s = dalloc(P, &P->rimg, apply_tc_image_bytes(lp))) != RSVD_OK) {
+  // the backward's tape (not for the single pass, which has no backward)
+  if (!o.single_pass &&
+      ((s = dalloc(P, &P->tape_r, (size_t)(2 * q + 1) * lp * lp)) != RSVD_OK ||
+       (q > 0 && !o.recompute && (s = dalloc(P, &P->tape_q, (size_t)q * m * lp)) != RSVD_OK) ||
+       (q > 0 && !o.recompute && (s = dalloc(P, &P->tape_qt, (size_t)q * n * lp)) != RSVD_OK))) {
+    free_plan(P);
+    return s;
+  }
+  if (o.precision == RSVD_BF16_TC && lq > 128 &&
+      (s = dalloc(P, &P->rimg, apply_tc_image_bytes(lq))) != RSVD_OK) {
     free_plan(P);
     return s;
   }
   if (o.precision == RSVD_BF16_TC) {
-    const size_t xrows = (size_t)tc_lo_offset(lp) + lp;
+    const size_t xrows = (size_t)tc_lo_offset(lq) + lq;
     if ((s = dalloc(P, &P->xbf, xrows * (size_t)tc_ld(P->maxmn))) != RSVD_OK ||
         cudaMemsetAsync(P->xbf, 0, xrows * (size_t)tc_ld(P->maxmn) * 2, P->st) != cudaSuccess) {
       free_plan(P);
       return s;
     }
-    if (tc_plan_init(&P->tc, m, n, o.lda, lp, P->xbf, P->num_sms) != 0) {
+    if (tc_plan_init(&P->tc, m, n, o.lda, lp, P->xbf, P->num_sms) != 0 ||
+        (o.single_pass && tc_plan_init(&P->tc2, m, n, o.lda, P->lpp, P->xbf, P->num_sms) != 0)) {
       free_plan(P);
       return RSVD_ERR_CUDA;
     }
     P->tc.status = P->status;
+    P->tc2.status = P->status;
   }
   if (o.test_matrix == RSVD_SRFT &&
       launch_srft_select(seed, n, (int)(l / 2), P->srft_freq, P->st) != cudaSuccess) {
@@ -582,7 +889,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_CUDA;
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
-      cudaMemsetAsync(P->small, 0, sizeof(float) * 24 * lp * lp, P->st) != cudaSuccess) {
+      cudaMemsetAsync(P->small, 0, sizeof(float) * 24 * lq * lq, P->st) != cudaSuccess) {
     free_plan(P);
     return RSVD_ERR_CUDA;
   }
@@ -605,6 +912,7 @@ rsvd_status_t rsvd_workspace_bytes(rsvd_plan_t P, size_t* bytes) {
 
 rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t ldq) {
   TRYS(check_plan(P));
+  P->fwd_ok = false;   // the buffers of the last rsvd_svd are reused
   if (!A || !Q || ldq < P->l) return RSVD_ERR_INVALID_ARG;
   if (P->opt.single_pass) return stage_single_pass(P, A, nullptr, nullptr, nullptr, Q, ldq);
   TRYS(stage_a(P, A));
@@ -618,9 +926,11 @@ rsvd_status_t rsvd_range_finder(rsvd_plan_t P, const void* A, float* Q, int64_t 
 // on the legacy default stream (which cannot be captured), if capture fails, or
 // when the environment sets RSVD_NO_GRAPH=1.
 rsvd_status_t run_svd_direct(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  P->fwd_ok = false;
   if (P->opt.single_pass) return stage_single_pass(P, A, U, S, V, nullptr, 0);
   TRYS(stage_a(P, A));
   TRYS(stage_b(P, A, U, S, V));
+  P->fwd_ok = true;
   return RSVD_OK;
 }
 
@@ -670,6 +980,7 @@ rsvd_status_t rsvd_svd(rsvd_plan_t P, const void* A, float* U, float* S, float* 
   }
   TRY(cudaGraphLaunch(P->gexec, P->st));
   for (int k = 0; k < RSVD_NUM_STEPS; ++k) P->launches[k] += P->g_launches[k];
+  P->fwd_ok = true;
   return RSVD_OK;
 }
 
@@ -708,9 +1019,11 @@ rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, fl
 
 rsvd_status_t rsvd_svd_backward(rsvd_plan_t P, const void* A, const float* gU, const float* gS,
                                 const float* gV, int32_t add_recon, float* gA) {
-  (void)A; (void)gU; (void)gS; (void)gV; (void)add_recon; (void)gA;
   TRYS(check_plan(P));
-  return RSVD_ERR_UNSUPPORTED;
+  if (!A || !gA || (add_recon != 0 && add_recon != 1)) return RSVD_ERR_INVALID_ARG;
+  if (P->opt.single_pass) return RSVD_ERR_UNSUPPORTED;
+  if (!P->fwd_ok) return RSVD_ERR_INVALID_ARG;   // needs the state of an rsvd_svd call on A
+  return run_backward(P, A, gU, gS, gV, add_recon, gA);
 }
 
 rsvd_status_t rsvd_get_omega(rsvd_plan_t P, float* Omega) {
@@ -723,6 +1036,7 @@ rsvd_status_t rsvd_get_omega(rsvd_plan_t P, float* Omega) {
 
 rsvd_status_t rsvd_set_omega(rsvd_plan_t P, const float* Omega) {
   TRYS(check_plan(P));
+  P->fwd_ok = false;   // the buffers of the last rsvd_svd are reused
   if (P->gexec) {  // the captured draw no longer matches
     cudaGraphExecDestroy(P->gexec);
     P->gexec = nullptr;
@@ -740,6 +1054,16 @@ rsvd_status_t rsvd_sync(rsvd_plan_t P) {
   TRYS(check_plan(P));
   return take_status(P);
 }
+
+rsvd_status_t rsvd_wait_selftest(rsvd_plan_t P, uint32_t spins) {
+  TRYS(check_plan(P));
+  if (spins == 0) return RSVD_ERR_INVALID_ARG;
+  // status word 3 is never written by any kernel: the wait can only run out
+  TRY(launch_wait_selftest(P->status + 3, spins, P->status, P->st));
+  return RSVD_OK;
+}
+
+void rsvd_debug_fail_alloc(int32_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
 
 rsvd_status_t rsvd_diagnostics(rsvd_plan_t P, uint32_t* out, int32_t n) {
   TRYS(check_plan(P));
@@ -806,6 +1130,7 @@ rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows
 rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const float* X,
                           float* Y) {
   TRYS(check_plan(P));
+  P->fwd_ok = false;   // the buffers of the last rsvd_svd are reused
   if (!A || !X || !Y) return RSVD_ERR_INVALID_ARG;
   const int64_t kx = transpose ? P->m : P->n;
   const int64_t my = transpose ? P->n : P->m;
@@ -824,6 +1149,7 @@ rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const
 
 rsvd_status_t rsvd_orthonormalize(rsvd_plan_t P, int64_t rows, float* Y, float* R) {
   TRYS(check_plan(P));
+  P->fwd_ok = false;   // the buffers of the last rsvd_svd are reused
   if (!Y || rows < P->l || rows > P->maxmn) return RSVD_ERR_INVALID_ARG;
   // the rounds ping-pong through tmp1/tmp2, so the result goes to a basis buffer of `rows` rows
   float* dst = rows <= P->m ? P->qbuf : P->qtbuf;
@@ -836,6 +1162,7 @@ rsvd_status_t rsvd_orthonormalize(rsvd_plan_t P, int64_t rows, float* Y, float* 
 
 rsvd_status_t rsvd_small_svd(rsvd_plan_t P, const float* X, float* Ut, float* S, float* W) {
   TRYS(check_plan(P));
+  P->fwd_ok = false;   // the buffers of the last rsvd_svd are reused
   if (!X || !Ut || !S || !W) return RSVD_ERR_INVALID_ARG;
   TRY(launch_gather(X, 1, 0, P->l, P->sq(), P->lp, P->l, P->l, P->lp, P->st));
   TRY(launch_jacobi_svd(P->sq(), P->lp, 0, P->l, P->lp, P->ut(), P->sig, P->w(), P->lbuf(),

@@ -472,6 +472,10 @@ cudaError_t launch_vpl(int C, int njobs, JacobiJob j0, JacobiJob j1, int64_t ldx
 
 cudaError_t prepare_jacobi_cluster() {
   cudaError_t e;
+  for (const void* fn : {(const void*)jacobi_block_kernel<1>, (const void*)jacobi_block_kernel<2>,
+                         (const void*)jacobi_block_kernel<3>, (const void*)jacobi_block_kernel<4>})
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+      return e;
   if ((e = cudaFuncSetAttribute(jacobi_block_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)block_smem<1>(16))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(jacobi_block_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -492,7 +496,10 @@ cudaError_t launch_jacobi_cluster(const float* x, int64_t ldx, int transposed, i
   if (l < 1 || l > kMaxLC || !scratch) return cudaErrorInvalidValue;
   const int njobs = x_b ? 2 : 1;
   if (x_b && !(ut_b && s_b && w_b && scratch_b)) return cudaErrorInvalidValue;
-  const int C = l <= 128 ? 4 : kMaxCluster;
+#ifndef RSVD_JACOBI_CSMALL
+#define RSVD_JACOBI_CSMALL 4
+#endif
+  const int C = l <= 128 ? RSVD_JACOBI_CSMALL : kMaxCluster;
   const int bw = (l + 2 * C - 1) / (2 * C);   // <= 16
   const float tol = 8.0f * sqrtf((float)l) * kEpsF32;
   const float tol2 = tol * tol;

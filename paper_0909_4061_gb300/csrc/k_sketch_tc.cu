@@ -31,10 +31,9 @@
 // Accumulation: the tensor cores add each k16 product into the float32 accumulator
 // with truncation, so a long chain of MMAs into one accumulator drifts towards zero
 // (about -2e-5 relative over K = 16384, i.e. a thousand k16 steps).  The MMAs of a row
-// tile are therefore cut into chunks of kChunk k tiles, each into a fresh accumulator
-// (double-buffered), and the epilogue adds the chunks in registers with IEEE float32
-// additions: the drift then stays that of one chunk (32 or, with the residual of A, 64
-// k16 steps).
+// tile are therefore cut into chunks of kChunkSteps k16 steps, each into a fresh
+// accumulator (double-buffered), and the epilogue adds the chunks in registers with IEEE
+// float32 additions: the drift then stays that of one chunk.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -49,7 +48,10 @@ using namespace tcx;
 constexpr int kThreads = 192;   // TM = 1, CH = 1
 template <int TM, int CH = 1>
 constexpr int threads_for() { return 64 + 128 * TM * CH; }
-constexpr int kChunk = 8;       // k tiles (of BK = 64) accumulated in tensor memory per chunk
+// k16 accumulation steps per tensor-memory chunk: 128 steps drift by about -2e-6 relative
+// (16 k tiles of BK = 64 when every k16 step also adds the residual of A, else 32); halving
+// the chunk halves the drift and costs about 4 % more time per pass (drains every 8 k tiles).
+constexpr int kChunkSteps = 128;
 constexpr int kAccRegs = 128;   // accumulator columns an epilogue thread holds in registers
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
                                              ~uintptr_t(1023));
   static_assert(TM == 1 || !HILO, "the residual of A is read with single tiles");
   static_assert(TM * CH <= 2, "at most eight epilogue warps");
+  constexpr int kChunk = kChunkSteps / ((BK / 16) * (HILO ? 2 : 1));   // k tiles per chunk
   constexpr int kEpi = 128 * TM * CH;   // epilogue threads
   constexpr uint32_t a_bytes = TM * BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
   const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
@@ -487,6 +490,7 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
   if (tc_encode_2d(tc->map_x_t, xbf, m, lp, ldm, BK, lp)) return -1;
   const int nf = fold_ntotal(lp);
   if (tc_encode_2d(tc->map_x_t2, xbf, m, tc_lo_offset(lp) + lp, ldm, BK, nf > 256 ? 256 : nf)) return -1;
+  if (tc_encode_2d(tc->map_x_n2, xbf, n, tc_lo_offset(lp) + lp, ldn, BK, nf > 256 ? 256 : nf)) return -1;
   TcBuffers* b = new TcBuffers();
   b->grid = num_sms;
   if (cudaMalloc(&b->slots, sizeof(float) * (size_t)num_sms * 2 * BM * lp) != cudaSuccess ||
@@ -554,8 +558,7 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
   const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(
       hilo ? (trans ? tc->map_a_lo : tc->map_a_lo_n) : (trans ? tc->map_a_t : tc->map_a_n));
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(
-      trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : tc->map_x_n);
-  if (split_x && !trans) return -1;
+      trans ? (split_x ? tc->map_x_t2 : tc->map_x_t) : (split_x ? tc->map_x_n2 : tc->map_x_n));
   // launched as a programmatic dependent: the A tiles of the first stages are loaded
   // while the launch that converts the operand finishes.  Bases wider than kAccRegs
   // columns take two epilogue warps per TMEM lane quarter (CH = 2), each holding half of

@@ -1,7 +1,8 @@
 // Small dense products on l x l matrices (l <= 256) for the single-pass Stage B
 // (Section 5.5): C = alpha op(A) op(B) + beta C, op = identity or transpose, one
 // CTA per 32 x 32 block of C, K in chunks of 32 through shared memory; and the
-// elementwise step of the Sylvester solve, H = G ./ (s2_i^2 + s1_j^2).
+// elementwise step of the Sylvester solve, H = G ./ (s2_i^2 + s1_j^2) (or G ./ (s2_i + s1_j)
+// when the eigenvalues of the normal-equation matrices are given directly).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -51,13 +52,13 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(int M, int N, int K, fl
 
 __global__ void sylvester_scale_kernel(const float* __restrict__ G, int l, int lp,
                                        const float* __restrict__ s2, const float* __restrict__ s1,
-                                       float* __restrict__ H) {
+                                       int squared, float* __restrict__ H) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= lp * lp) return;
   const int i = e / lp, j = e % lp;
   float h = 0.0f;
   if (i < l && j < l) {
-    const float d = fmaf(s2[i], s2[i], s1[j] * s1[j]);
+    const float d = squared ? s2[i] + s1[j] : fmaf(s2[i], s2[i], s1[j] * s1[j]);
     h = d > 0.0f ? G[e] / d : 0.0f;
   }
   H[e] = h;
@@ -76,7 +77,27 @@ __global__ void round_bf16_kernel(float* __restrict__ x, int64_t rows, int cols,
   }
 }
 
+// A bounded wait on a device word that nothing sets, in the form of the library's flag
+// waits (poll, back off, give up after `spins` polls and record the timeout in the status
+// word): the kernel always returns, so the context stays usable.
+__global__ void wait_selftest_kernel(const uint32_t* __restrict__ flag, uint32_t spins,
+                                     uint32_t* __restrict__ status) {
+  if (threadIdx.x != 0) return;
+  const volatile uint32_t* f = flag;
+  for (uint32_t i = 0; i < spins; ++i) {
+    if (*f != 0u) return;
+    __nanosleep(64);
+  }
+  set_status(status, ST_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(const uint32_t* flag, uint32_t spins, uint32_t* status,
+                                 cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(flag, spins, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_round_bf16(float* x, int64_t rows, int cols, int64_t ld, cudaStream_t st) {
   const int64_t n = rows * cols;
@@ -96,8 +117,9 @@ cudaError_t launch_small_gemm(int M, int N, int K, float alpha, const float* A, 
 }
 
 cudaError_t launch_sylvester_scale(const float* G, int l, int lp, const float* s2, const float* s1,
-                                   float* H, cudaStream_t st) {
-  sylvester_scale_kernel<<<(unsigned)cdiv((int64_t)lp * lp, 256), 256, 0, st>>>(G, l, lp, s2, s1, H);
+                                   int squared, float* H, cudaStream_t st) {
+  sylvester_scale_kernel<<<(unsigned)cdiv((int64_t)lp * lp, 256), 256, 0, st>>>(G, l, lp, s2, s1,
+                                                                                  squared, H);
   return cudaGetLastError();
 }
 

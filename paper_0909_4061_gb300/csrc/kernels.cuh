@@ -80,14 +80,14 @@ cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64
 // Outputs: ut (l x l, ld lp), s (l), w (l x l, ld lp), descending.
 // info (may be null): atomicMax of the number of sweeps taken.
 // variant: 0 = one CTA up to l = 160, else the cluster; 1 = one CTA; 2 = cluster.
-// C = alpha op(A) op(B) + beta C for small matrices (op: 0 identity, 1 transpose; M, N, K <= a
-// few hundred), and H = G ./ (s2_i^2 + s1_j^2) on the leading l x l (zero elsewhere).
+// C = alpha op(A) op(B) + beta C (op: 0 identity, 1 transpose; 32 x 32 tiles of C), and
+// H = G ./ (s2_i^2 + s1_j^2) (or ./ (s2_i + s1_j) with squared) on the leading l x l.
 cudaError_t launch_small_gemm(int M, int N, int K, float alpha, const float* A, int lda, int ta,
                               const float* B, int ldb, int tb, float beta, float* C, int ldc,
                               cudaStream_t st);
 cudaError_t launch_round_bf16(float* x, int64_t rows, int cols, int64_t ld, cudaStream_t st);
 cudaError_t launch_sylvester_scale(const float* G, int l, int lp, const float* s2, const float* s1,
-                                   float* H, cudaStream_t st);
+                                   int squared, float* H, cudaStream_t st);
 
 // SRFT test matrix (Section 4.6): the lc sampled frequencies (one CTA, at plan creation),
 // then Omega n x cols_pad (2 lc real columns [Re, Im] per frequency, zero padding).
@@ -123,6 +123,33 @@ cudaError_t launch_jacobi_svd_pair(const float* x, const float* x_b, int64_t ldx
                                    float* w_b, float* scratch, float* scratch_b, uint32_t* status,
                                    uint32_t* info, cudaStream_t st, int variant);
 cudaError_t prepare_jacobi_cluster();
+
+// ---- backward (k_backward.cu) ----
+// G = alpha A + beta G + L R^T (L: m x kr, ldl; R: n x kr, ldr; A float32 (adt 0),
+// bfloat16 (1) or bfloat16 hi + lo (2, lo m * lda elements further); alpha = 0 skips A).
+cudaError_t launch_lowrank_update(int64_t m, int64_t n, int kr, const float* L, int64_t ldl,
+                                  const float* R, int64_t ldr, const void* A, int64_t lda, int adt,
+                                  float alpha, float beta, float* G, int64_t ldg, cudaStream_t st);
+// X = R^-1 (R upper triangular l x l within lp x lp, identity beyond l).
+cudaError_t launch_trinv_upper(const float* R, int l, int lp, float* X, cudaStream_t st);
+// N = -copyltu(C) (lp x lp).
+cudaError_t launch_copyltu_neg(const float* C, int lp, float* N, cudaStream_t st);
+// M2 = M^T - K S^-1 of the SVD adjoint (see k_backward.cu).
+cudaError_t launch_svd_adjoint(const float* J, const float* K, const float* s, const float* gS, int k,
+                               int l, int lp, float* M2, cudaStream_t st);
+// gUt = gU + rec (2 S^2 U - 2 S P) on the first k columns (rows x lp, zero beyond k).
+cudaError_t launch_recon_cotangent(int64_t m, int k, int lp, const float* gU, const float* U,
+                                   const float* P, const float* s, int rec, float* gUt, cudaStream_t st);
+// Y (rows x lp) (+)= alpha X[:, :ncols] diag(c or 1/c), zero beyond ncols.
+cudaError_t launch_colscale(int64_t rows, int ncols, int lp, const float* X, int lds, const float* c,
+                            int inv, float alpha, int accumulate, float* Y, cudaStream_t st);
+// out[j] = gS[j] + rec, j < k.
+cudaError_t launch_gs_total(const float* gS, int k, int rec, float* out, cudaStream_t st);
+
+// A bounded wait on `flag` (never set by the library) that records ST_TIMEOUT after `spins`
+// polls and returns (rsvd_wait_selftest).
+cudaError_t launch_wait_selftest(const uint32_t* flag, uint32_t spins, uint32_t* status,
+                                 cudaStream_t st);
 
 // One-time (per device) shared-memory attributes of the one-CTA kernels and of the
 // tensor-core Gram and apply.

@@ -19,6 +19,7 @@ struct TcPlan {
   alignas(64) unsigned char map_x_n[128];  // X^T tiles, K = n
   alignas(64) unsigned char map_x_t[128];  // X^T tiles, K = m (lp rows)
   alignas(64) unsigned char map_x_t2[128]; // X^T tiles, K = m (hi rows, then lo rows at tc_lo_offset)
+  alignas(64) unsigned char map_x_n2[128]; // X^T tiles, K = n (hi rows, then lo rows at tc_lo_offset)
   alignas(64) unsigned char map_a_lo[128]; // residual lo = A - hi, stacked m rows below A (Y = A^T X)
   alignas(64) unsigned char map_a_lo_n[128]; // the same residual as K-major tiles (Y = A X)
   bool ready = false;
@@ -39,9 +40,9 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
                  int num_sms);
 // with_lo: A is followed (m rows of lda further) by its bfloat16 residual lo = A - hi.
 int tc_bind_a(TcPlan* tc, const void* A, int with_lo);
-// One pass.  trans = 0: Y = A X (X^T is lp x n in xbf); trans = 1: Y = A^T X (X^T is lp x m,
-// or 2 lp x m with split_x = 1, the hi and lo halves summed; hilo = 1 also reads the
-// residual of A).  Writes *splits slabs of (rows x lp) float32 into `partial`.
+// One pass.  trans = 0: Y = A X (X^T is lp x n in xbf); trans = 1: Y = A^T X (X^T is lp x m);
+// with split_x = 1 the operand has a hi and a lo half (rows 0 and tc_lo_offset(lp)) whose
+// products are summed; hilo = 1 also reads the residual of A.  Writes *splits slabs of (rows x lp) float32 into `partial`.
 int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* partial, int* splits,
             cudaStream_t st);
 // 2-D bfloat16 tensor map, 128-byte swizzle: inner dimension `inner` (contiguous), `outer`

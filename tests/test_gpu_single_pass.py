@@ -1,7 +1,8 @@
 """GPU parity of the single-pass randomized SVD (Section 5.5) against the oracle.
 
-Both sides take the same Omega (Gaussian, stream 0) and Psi (Gaussian, stream 1):
-the library's own draws, read back through the C ABI, feed the oracle.  B is the
+Both sides take the same Omega (Gaussian, stream 0, n x l) and Psi (Gaussian, stream 1,
+m x l' with the library's default l' = min(3 l, 256, n)): the library's own draws, read
+back through the C ABI, feed the oracle.  B is the
 minimum-residual solution of B X1 = C1, B^T X2 = C2 through the Sylvester normal
 equations; its float32 error grows with the conditioning of that system.  A
 first-order bound: a relative perturbation u of the inputs moves B by about
@@ -30,11 +31,17 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 
 
+def psi_cols(m, n, l):
+    """The library's default width l' of Psi: min(3 l, 256, n)."""
+    return min(3 * l, 256, n)
+
+
 def _draws(pkg, pl, m, n, l, seed, bf16):
     om = torch.zeros(n, l, device="cuda")
     pkg.rsvd_get_omega(pl.handle, om)
-    psi = torch.zeros(m, l, device="cuda")
-    pkg.rsvd_draw_gaussian(seed, 1, m, l, psi, l)
+    lt = psi_cols(m, n, l)
+    psi = torch.zeros(m, lt, device="cuda")
+    pkg.rsvd_draw_gaussian(seed, 1, m, lt, psi, lt)
     torch.cuda.synchronize()
     if bf16:
         om, psi = om.to(torch.bfloat16).float(), psi.to(torch.bfloat16).float()
@@ -117,3 +124,30 @@ def test_single_pass_exact_rank(rsvd_lib):
     print("single pass exact rank: max dsigma/sigma1", np.max(np.abs(s[:r] - st[:r])) / st[0], "tol/sigma1", tol / st[0])
     assert np.max(np.abs(s[:r] - st[:r])) <= tol
     assert np.max(np.abs(s[r:])) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_single_pass_noisy_tall_workload(rsvd_lib, precision):
+    """The tall-skinny workload's recipe at 16384 x 1024 (sigma_j = max(e^-(j-1)/20, 1e-6),
+    k = 64, p = 16, iid Gaussian noise scaled so that its Frobenius norm equals that of the
+    signal, as the 262144 x 4096 workload's does): the relative reconstruction error
+    ||A - U S V^T||_F / ||A||_F of the GPU stays within 2 % of the oracle's on the same
+    Omega and Psi, and below 1 (the error of the zero approximation)."""
+    pkg = rsvd_lib
+    m, n, k, p, seed = 16384, 1024, 64, 16, 47
+    sig = synth.spectrum_exp_floor(n, 20.0, 1e-6)
+    a, *_ = synth.lowrank(m, n, sig, 1003)
+    a += synth.noise(m, n, float(np.sqrt(np.sum(sig ** 2) / (m * n))), 77)
+    a32 = a.astype(np.float32)
+    if precision == pkg.RSVD_BF16_TC:
+        a32 = torch.tensor(a32).to(torch.bfloat16).float().numpy()
+    a64 = a32.astype(np.float64)
+    u, s, v, om, psi, bits = _run(pkg, a32, k, p, seed, precision)
+    ur, sr, vr, _, kap = _oracle(a64, k, om, psi)
+    nrm = np.linalg.norm(a64)
+    e_gpu = np.linalg.norm(a64 - (u * s) @ v.T) / nrm
+    e_ref = np.linalg.norm(a64 - (ur * sr) @ vr.T) / nrm
+    print(f"noisy tall single pass (precision {precision}): GPU {e_gpu:.5f} oracle {e_ref:.5f} "
+          f"max dsigma/sigma1 {np.max(np.abs(s - sr)) / sr[0]:.2e}")
+    assert e_gpu <= 1.02 * e_ref and e_gpu < 1.0
+    assert np.max(np.abs(s - sr)) <= 2 * U32 * kap * sr[0]

@@ -411,3 +411,25 @@ def test_cotangent_gradient_autograd_vs_finite_differences():
     g_s, *_ = grad.cotangent_autograd(a, k, p, q, om, 0 * gu, np.eye(k)[0], 0 * gv)
     fd1 = grad.cotangent_fd(a, k, p, q, om, 0 * gu, np.eye(k)[0], 0 * gv, dirs[:2], h=1e-5, ref=(u, v))
     assert np.allclose([np.sum(g_s * e) for e in dirs[:2]], fd1, rtol=1e-5, atol=1e-8)
+
+
+def test_single_pass_wide_psi_on_the_noisy_tall_workload():
+    """Reading of Section 5.5 for the tall-skinny workload: the width l' of Psi is open.  At
+    the workload's noise level (noise Frobenius norm equal to the signal's), with l' = l
+    the minimum-residual B is worse than the zero matrix (relative error above 1), with
+    l' = 3 l the system for B^T is overdetermined enough to bring it below 1, while two
+    passes with q = 2 stay the reference (the section's remark: one pass costs accuracy)."""
+    m, n, k, p = 16384, 1024, 64, 16
+    sig = synth.spectrum_exp_floor(n, 20.0, 1e-6)
+    a, *_ = synth.lowrank(m, n, sig, 1003)
+    a += synth.noise(m, n, float(np.sqrt(np.sum(sig ** 2) / (m * n))), 77)
+    nrm = np.linalg.norm(a)
+    om = philox.gaussian(2003, 0, n, k + p)
+
+    def rel(u, s, v):
+        return np.linalg.norm(a - (u * s) @ v.T) / nrm
+
+    e_q2 = rel(*rsvd64.rsvd(a, k, p, 2, om)[:3])
+    e_l = rel(*single_pass.rsvd_single_pass(a, k, om, philox.gaussian(2003, 1, m, k + p))[:3])
+    e_3l = rel(*single_pass.rsvd_single_pass(a, k, om, philox.gaussian(2003, 1, m, 3 * (k + p)))[:3])
+    assert e_l > 1.0 and e_3l < 1.0 and e_q2 < e_3l
