@@ -53,9 +53,10 @@ struct rsvd_plan_s {
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
   uint32_t* status = nullptr;
-  // backward tape: the R factors of every orthonormalisation of Stage A (always), and in
-  // store mode (recompute = 0) the intermediate bases Q_0 .. Q_{q-1}, Qt_1 .. Qt_q
-  float* tape_r = nullptr;   // (2q + 1) x lp x lp: R_0 .. R_q, then Rt_1 .. Rt_q
+  // backward tape: R^-1 of every Cholesky-QR round of Stage A (always: the factorisation
+  // writes it there in place of its scratch block), and in store mode (recompute = 0) the
+  // intermediate bases Q_0 .. Q_{q-1}, Qt_1 .. Qt_q
+  float* tape_r = nullptr;   // (2q + 1) x 3 x lp x lp: for Y_0 .. Y_q, then Yt_1 .. Yt_q
   float* tape_q = nullptr;   // q x m x lp
   float* tape_qt = nullptr;  // q x n x lp
   bool fwd_ok = false;       // the last call on the plan was rsvd_svd (its state is intact)
@@ -95,8 +96,11 @@ struct rsvd_plan_s {
   // and Qt_j (j = 1 .. q), and their R factors
   float* basis_q(int j) { return (j < q && tape_q) ? tape_q + (size_t)j * m * lp : qbuf; }
   float* basis_qt(int j) { return tape_qt ? tape_qt + (size_t)(j - 1) * n * lp : qtbuf; }
-  float* r_q(int j) { return tape_r ? tape_r + (size_t)j * lp * lp : nullptr; }
-  float* r_qt(int j) { return tape_r ? tape_r + (size_t)(q + j) * lp * lp : nullptr; }
+  float* r_q(int j) { return tape_r ? tape_r + (size_t)j * 3 * lp * lp : nullptr; }
+  float* r_qt(int j) { return tape_r ? tape_r + (size_t)(q + j) * 3 * lp * lp : nullptr; }
+  int rounds(bool final_basis) const {
+    return final_basis ? opt.orth_rounds : std::min(opt.orth_rounds, 2);
+  }
 };
 
 namespace {
@@ -277,16 +281,20 @@ rsvd_status_t step_pass_psi(rsvd_plan_t P, const void* A, int* splits, int64_t* 
 // Cholesky-QR rounds on the (summed) partial slabs; the basis ends in `dst`
 // (rows x lp).  With `racc`, the triangular factors are multiplied into it.
 rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t stride, int64_t rows,
-                        float* dst, float* racc, bool final_basis = true, int width = 0) {
+                        float* dst, float* racc, bool final_basis = true, int width = 0,
+                        float* rinv_tape = nullptr) {
   // A basis that only feeds the next power-iteration pass needs to span the sample, not
   // to be orthonormal to working precision: the shifted round and one plain round leave
   // ||Q^T Q - I|| ~ u kappa(Q_1)^2 with kappa(Q_1) modest after the shift, and the next
   // orthonormalisation starts from the product anyway.  Final bases get every round.
   // width: the columns of the sample (0: l; the single pass also orthonormalises the l'
   // columns of A^T Psi).
-  const int rounds = final_basis ? P->opt.orth_rounds : std::min(P->opt.orth_rounds, 2);
+  // rinv_tape: R^-1 of round r goes to rinv_tape + r lp^2 (the backward's tape) instead of
+  // the scratch block
+  const int rounds = P->rounds(final_basis);
   const int wl = width ? width : P->l;
   const int lp = (int)round_up(wl, 16);
+  auto ri = [&](int r) { return rinv_tape ? rinv_tape + (size_t)r * lp * lp : P->rinv(); };
   const int nblk = gram_blocks(rows);
   Step sp(P, RSVD_STEP_ORTH);
   sp.launched(lp <= 128 ? 3 * rounds + 1 : 4 * rounds);
@@ -300,11 +308,11 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
     for (int r = 0; r < rounds; ++r) {
       const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
-      TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+      TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), ri(r), racc,
                           r == 0 ? 1 : 0, P->status, P->st));
       const bool last = (r == rounds - 1);
       float* next = last ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
-      TRY(launch_apply_gram(cur, next, rows, lp, P->rinv(), P->gpart, nblk, last ? 0 : 1, P->st));
+      TRY(launch_apply_gram(cur, next, rows, lp, ri(r), P->gpart, nblk, last ? 0 : 1, P->st));
       if (!last) TRY(launch_gram_reduce(P->gpart, nblk, lp, P->g(), P->st));
       cur = next;
     }
@@ -329,13 +337,13 @@ rsvd_status_t step_orth(rsvd_plan_t P, const float* src, int splits, int64_t str
     if (cur_splits > 1) cur = P->tmp1;
     TRY(launch_gram_reduce(P->gpart, gblk, lp, P->g(), P->st));
     const int shifted = (P->opt.orth_rounds >= 3 && r == 0) ? 1 : 0;
-    TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), P->rinv(), racc,
+    TRY(launch_cholesky(P->g(), wl, lp, shifted, P->lbuf(), P->rtmp(), ri(r), racc,
                         r == 0 ? 1 : 0, P->status, P->st));
     float* next = (r == rounds - 1) ? dst : (cur == P->tmp1 ? P->tmp2 : P->tmp1);
     if (tc_gram)
-      TRY(launch_apply_tc(cur, next, rows, lp, P->rinv(), P->rimg, P->status, P->st));
+      TRY(launch_apply_tc(cur, next, rows, lp, ri(r), P->rimg, P->status, P->st));
     else
-      TRY(launch_gemm_f32(0, rows, lp, lp, cur, lp, P->rinv(), lp, next, lp, 1, 0, P->st));
+      TRY(launch_gemm_f32(0, rows, lp, lp, cur, lp, ri(r), lp, next, lp, 1, 0, P->st));
     cur = next;
     cur_splits = 1;
   }
@@ -361,14 +369,14 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   int64_t stride;
   // the bases go where the backward finds them (the tape in store mode), with their R factors
   TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
-  TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(0), P->r_q(0), P->q == 0));
+  TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(0), nullptr, P->q == 0, 0, P->r_q(0)));
   for (int j = 1; j <= P->q; ++j) {
     if (tc) TRYS(step_convert(P, P->basis_q(j - 1), P->m, 0));
     TRYS(step_pass(P, A, 1, P->basis_q(j - 1), false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->n, P->basis_qt(j), P->r_qt(j), false));
+    TRYS(step_orth(P, P->partial, s, stride, P->n, P->basis_qt(j), nullptr, false, 0, P->r_qt(j)));
     if (tc) TRYS(step_convert(P, P->basis_qt(j), P->n, 0));
     TRYS(step_pass(P, A, 0, P->basis_qt(j), false, &s, &stride));
-    TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(j), P->r_q(j), j == P->q));
+    TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(j), nullptr, j == P->q, 0, P->r_q(j)));
   }
   return RSVD_OK;
 }
@@ -591,16 +599,28 @@ rsvd_status_t bw_tn(rsvd_plan_t P, int64_t rows, const float* X, const float* Y,
   return RSVD_OK;
 }
 
-// gY = (gQ + Q copyltu(-gQ^T Q)) R^-T for Y = Q R (rows x lp)
+// gY = (gQ + Q copyltu(-gQ^T Q)) R^-T for Y = Q R (rows x lp), R = R_r ... R_1 the product
+// of the Cholesky-QR rounds, so R^-1 = R_1^-1 ... R_r^-1 from the rounds' inverses on the tape
 rsvd_status_t bw_qr(rsvd_plan_t P, Bw& b, int64_t rows, const float* Q, const float* gQ,
-                    const float* R, float* T, float* gY) {
+                    const float* rinv_rounds, int rounds, float* T, float* gY) {
   const int lp = P->lp;
+  const size_t l2 = (size_t)lp * lp;
   TRYS(bw_tn(P, rows, gQ, Q, lp, lp, b.C));
   TRY(launch_copyltu_neg(b.C, lp, b.N, P->st));
   TRY(launch_gather(gQ, 1, 0, lp, T, lp, rows, lp, lp, P->st));
   TRY(launch_small_gemm((int)rows, lp, lp, 1.0f, Q, lp, 0, b.N, lp, 0, 1.0f, T, lp, P->st));
-  TRY(launch_trinv_upper(R, P->l, lp, b.rinv, P->st));
-  TRY(launch_small_gemm((int)rows, lp, lp, 1.0f, T, lp, 0, b.rinv, lp, 1, 0.0f, gY, lp, P->st));
+  const float* rinv = rinv_rounds;
+  if (rounds > 1) {
+    float* acc[2] = {b.rinv, b.t1};
+    TRY(launch_small_gemm(lp, lp, lp, 1.0f, rinv_rounds, lp, 0, rinv_rounds + l2, lp, 0, 0.0f, acc[0],
+                          lp, P->st));
+    int cur = 0;
+    for (int r = 2; r < rounds; ++r, cur ^= 1)
+      TRY(launch_small_gemm(lp, lp, lp, 1.0f, acc[cur], lp, 0, rinv_rounds + r * l2, lp, 0, 0.0f,
+                            acc[cur ^ 1], lp, P->st));
+    rinv = acc[cur];
+  }
+  TRY(launch_small_gemm((int)rows, lp, lp, 1.0f, T, lp, 0, rinv, lp, 1, 0.0f, gY, lp, P->st));
   return RSVD_OK;
 }
 
@@ -707,15 +727,15 @@ rsvd_status_t run_backward(rsvd_plan_t P, const void* A, const float* gU, const 
       TRYS(bw_recompute(P, A, b, j, &qprev, &qcur));
       qt = b.wqt;
     }
-    TRYS(bw_qr(P, b, m, qcur, b.gq, P->r_q(j), b.tm, b.pm));     // gY_j
+    TRYS(bw_qr(P, b, m, qcur, b.gq, P->r_q(j), P->rounds(j == q), b.tm, b.pm));   // gY_j
     TRYS(emit(b.pm, qt));                                       // gA += gY_j Qt_j^T
     TRYS(bw_pass(P, A, 1, b.pm, b.gqt));                        // gQt_j = A^T gY_j
-    TRYS(bw_qr(P, b, n, qt, b.gqt, P->r_qt(j), b.tn, b.z));     // gYt_j
+    TRYS(bw_qr(P, b, n, qt, b.gqt, P->r_qt(j), P->rounds(false), b.tn, b.z));     // gYt_j
     TRYS(emit(qprev, b.z));                                     // gA += Q_{j-1} gYt_j^T
     TRYS(bw_pass(P, A, 0, b.z, b.gq));                          // gQ_{j-1} = A gYt_j
     if (j == 1) q0 = qprev;                                     // (recompute mode: still held)
   }
-  TRYS(bw_qr(P, b, m, q0, b.gq, P->r_q(0), b.tm, b.pm));       // gY_0
+  TRYS(bw_qr(P, b, m, q0, b.gq, P->r_q(0), P->rounds(q == 0), b.tm, b.pm));   // gY_0
   // Omega as the forward multiplied with it (the draw, or the caller's matrix)
   TRYS(step_draw(P, false));
   TRYS(emit(b.pm, P->omega));                                   // gA += gY_0 Omega^T
@@ -856,7 +876,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   }
   // the backward's tape (not for the single pass, which has no backward)
   if (!o.single_pass &&
-      ((s = dalloc(P, &P->tape_r, (size_t)(2 * q + 1) * lp * lp)) != RSVD_OK ||
+      ((s = dalloc(P, &P->tape_r, (size_t)(2 * q + 1) * 3 * lp * lp)) != RSVD_OK ||
        (q > 0 && !o.recompute && (s = dalloc(P, &P->tape_q, (size_t)q * m * lp)) != RSVD_OK) ||
        (q > 0 && !o.recompute && (s = dalloc(P, &P->tape_qt, (size_t)q * n * lp)) != RSVD_OK))) {
     free_plan(P);

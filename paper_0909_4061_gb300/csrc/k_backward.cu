@@ -4,7 +4,7 @@
 // backward is here:
 //   * small l x l steps: the SVD adjoint of B (F o (J - J^T) S + S F o (K - K^T) +
 //     diag(gS), F_ij = 1 / (s_j^2 - s_i^2)), the antisymmetric part of a QR adjoint
-//     (copyltu), the inverse of an upper triangular factor;
+//     (copyltu);
 //   * row-wise steps on tall matrices: the cotangents of the reconstruction loss, column
 //     scalings;
 //   * the gradient itself, gA = alpha A + beta gA + L R^T, a tiled float32 GEMM whose
@@ -87,25 +87,6 @@ __global__ void __launch_bounds__(256) lowrank_update_kernel(
 }
 
 // ---- l x l steps (one CTA) -----------------------------------------------------------
-
-// X = R^-1 for an upper triangular R (l x l within lp x lp, ld lp; identity beyond l):
-// thread j solves column j by back substitution, X(i, j) = (delta_ij - sum_{t > i}
-// R(i, t) X(t, j)) / R(i, i), i = j .. 0 (R is read through L1/L2; l x l is at most 256 KB).
-__global__ void __launch_bounds__(256) trinv_upper_kernel(const float* __restrict__ R, int l, int lp,
-                                                          float* __restrict__ X) {
-  for (int j = threadIdx.x; j < lp; j += blockDim.x) {
-    for (int i = lp - 1; i > j; --i) X[(int64_t)i * lp + j] = 0.0f;   // zero below row j
-    if (j >= l) {
-      for (int i = j; i >= 0; --i) X[(int64_t)i * lp + j] = (i == j) ? 1.0f : 0.0f;
-      continue;
-    }
-    for (int i = j; i >= 0; --i) {
-      float s = (i == j) ? 1.0f : 0.0f;
-      for (int t = i + 1; t <= j; ++t) s = fmaf(-__ldg(R + (int64_t)i * lp + t), X[(int64_t)t * lp + j], s);
-      X[(int64_t)i * lp + j] = s / __ldg(R + (int64_t)i * lp + i);
-    }
-  }
-}
 
 // N = -copyltu(C): N_ij = -C_ij for i >= j, -C_ji above the diagonal (the QR adjoint's
 // symmetric part, M = -gQ^T Q with its lower triangle mirrored).
@@ -202,11 +183,6 @@ cudaError_t launch_lowrank_update(int64_t m, int64_t n, int kr, const float* L, 
     lowrank_update_kernel<1><<<grid, 256, 0, st>>>(m, n, kr, L, ldl, R, ldr, A, lda, alpha, beta, G, ldg);
   else
     lowrank_update_kernel<2><<<grid, 256, 0, st>>>(m, n, kr, L, ldl, R, ldr, A, lda, alpha, beta, G, ldg);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_trinv_upper(const float* R, int l, int lp, float* X, cudaStream_t st) {
-  trinv_upper_kernel<<<1, 256, 0, st>>>(R, l, lp, X);
   return cudaGetLastError();
 }
 

@@ -130,8 +130,6 @@ cudaError_t prepare_jacobi_cluster();
 cudaError_t launch_lowrank_update(int64_t m, int64_t n, int kr, const float* L, int64_t ldl,
                                   const float* R, int64_t ldr, const void* A, int64_t lda, int adt,
                                   float alpha, float beta, float* G, int64_t ldg, cudaStream_t st);
-// X = R^-1 (R upper triangular l x l within lp x lp, identity beyond l).
-cudaError_t launch_trinv_upper(const float* R, int l, int lp, float* X, cudaStream_t st);
 // N = -copyltu(C) (lp x lp).
 cudaError_t launch_copyltu_neg(const float* C, int lp, float* N, cudaStream_t st);
 // M2 = M^T - K S^-1 of the SVD adjoint (see k_backward.cu).
