@@ -600,7 +600,9 @@ def run_workload(args):
         torch.cuda.synchronize()
         variants = ([("single_pass", dict(single_pass=1, q=0)), ("multi_pass_q2", dict(q=2))]
                     if args.workload == "c3" else
-                    [("srft", dict(test_matrix=pkg.RSVD_SRFT, q=w.q)), ("gaussian", dict(q=w.q))])
+                    [("srft", dict(test_matrix=pkg.RSVD_SRFT, q=w.q)),
+                     ("srft_row_transform", dict(test_matrix=pkg.RSVD_SRFT, srft_fft=1, q=w.q)),
+                     ("gaussian", dict(q=w.q))])
         res = {}
         for name, kw in variants:
             q = kw.pop("q")
@@ -643,13 +645,16 @@ def run_workload(args):
             fwd = _events_ms(lambda: pl.svd(mats, U, S, V), steps, warmup)
             bwd = _events_ms(lambda: pl.backward(mats, grads), steps, warmup)
             sweeps = pl.sync()
+            tuning = pl.tuning()
         elems = sum(m * n for m, n in shapes)
         out.update({"metric": "batched rank-16 rSVD forward / backward ms for the whole batch",
                     "config": {"batch": len(shapes), "k": synth.C5_K, "p": synth.C5_P, "q": synth.C5_Q,
                                "elements": elems},
                     "results": {"forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4),
                                 "forward_A_bytes_per_ms": round(elems * 2 * 4 / fwd / 1e6, 1),
-                                "jacobi_sweeps_max": sweeps}})
+                                "jacobi_sweeps_max": sweeps,
+                                "pass_config": tuning,
+                                "launch": "one CUDA graph per call (forward, backward)"}})
     print(json.dumps(out), flush=True)
 
 

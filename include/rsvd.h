@@ -96,6 +96,15 @@ typedef struct {
                            k <= l' <= min(n, 256); 0 (default) takes min(3 l, 256, n).  A Psi
                            wider than l makes the system for B^T overdetermined (Section 5.5,
                            the remark on single-pass error) */
+  int32_t srft_fft;     /* SRFT plans: 1 forms the first pass Y = A Omega by the transform
+                           along the rows of A (rsvd_sketch_srft; no n x l matrix), 0
+                           (default) by a tensor-core (or float32) pass with the drawn
+                           n x l matrix, which is faster on this GPU at l <= 256 */
+  int32_t autotune;     /* batched plans: 1 (default) times the grouped pass's configurations
+                           (pipeline stages x CTAs per SM) on the first rsvd_batched_svd call
+                           and keeps the fastest per pass kind, cached per shape class in
+                           the JSON file named by the environment variable RSVD_TUNE_CACHE
+                           when it is set; 0 keeps the built-in configuration */
   int32_t host_f32;     /* 1: rsvd_svd_host takes A as float32 (m x n, leading dimension
                            lda) and converts it on the device to the plan's bfloat16 storage
                            (hi, and lo for RSVD_BF16X2) before the SVD, so a caller holding a
@@ -134,6 +143,37 @@ RSVD_API rsvd_status_t rsvd_range_finder(rsvd_plan_t plan, const void* A, float*
  * truncation).  A: device, m x n.  U: device m x k, S: device k, V: device
  * n x k, all float32 row-major with leading dimension k.  A ~= U diag(S) V^T. */
 RSVD_API rsvd_status_t rsvd_svd(rsvd_plan_t plan, const void* A, float* U, float* S, float* V);
+
+/* Stage B for a symmetric A (m = n; Section 5.3, 5.4), after Stage A as in rsvd_svd:
+ *   RSVD_EIG_DIRECT  -- Algorithm 5.3: B = Q^T A Q, B = V Lambda V^T, U = Q V
+ *                       (||A - U Lambda U^T|| <= 2 ||A - Q Q^T A||);
+ *   RSVD_EIG_NYSTROM -- Algorithm 5.5 for a positive semidefinite A: B1 = A Q,
+ *                       Q^T B1 = C^T C (Cholesky), F = B1 C^-1, F = U S W^T, Lambda = S^2
+ *                       (A ~ F F^T, never worse than ||A - Q Q^T A|| in the spectral norm).
+ * A is read once more than by the range finder (B1 = A Q).  Outputs: U (device, m x k
+ * float32, leading dimension k) and Lambda (device, k), the k eigenvalues of largest
+ * magnitude in decreasing order of |lambda|; the sign of each eigenvector is not
+ * specified.  The symmetry of A is assumed, not checked. */
+enum { RSVD_EIG_DIRECT = 0, RSVD_EIG_NYSTROM = 1 };
+RSVD_API rsvd_status_t rsvd_eig(rsvd_plan_t plan, const void* A, int32_t method, float* U,
+                                float* Lambda);
+
+/* The fixed-precision problem (Section 4.4): Algorithm 4.2, the adaptive randomized range
+ * finder, in the blocked form of the remark that follows it.  Samples A w_i (the Gaussian
+ * columns of Philox stream 3 for the plan's seed) are taken `block` at a time; each block's
+ * posterior estimate max_i ||(I - Q Q^T) A w_i|| (Lemma 4.1, estimate (4.3)) is compared
+ * with eps / (10 sqrt(2/pi)); while it is larger the block is reprojected, orthonormalised,
+ * reprojected once normalised, orthonormalised again and appended to Q, and the next block
+ * is sampled.  On return ||(I - Q Q^T) A|| <= eps except with probability
+ * min(m, n) 10^-block, unless the basis reached its cap first.
+ *   The plan sets the cap: at most l = k + p columns (q is not used).  block: a multiple of
+ *   16, 16 <= block <= l.  Q: device, m x l float32, leading dimension ldq >= l; its first
+ *   *rank columns (a multiple of block) are the basis.  *estimate (may be NULL) receives
+ *   the last block's estimate.  The call waits for the device once per block (the host
+ *   takes the stopping decision). */
+RSVD_API rsvd_status_t rsvd_range_finder_adaptive(rsvd_plan_t plan, const void* A, float eps,
+                                                  int32_t block, float* Q, int64_t ldq,
+                                                  int32_t* rank, float* estimate);
 
 /* rsvd_svd for host-resident data: copies A (host, m x n with the plan's lda,
  * in the plan's dtype, or float32 with the host_f32 option) to a device buffer
@@ -244,6 +284,16 @@ RSVD_API rsvd_status_t rsvd_draw_gaussian(uint64_t seed, uint32_t stream_id, int
 RSVD_API rsvd_status_t rsvd_sketch(rsvd_plan_t plan, const void* A, int32_t transpose,
                           const float* X, float* Y);
 
+/* The first pass of an SRFT plan, Y = A Omega (m x l, device float32, leading dimension l),
+ * computed as the paper's transform along the rows of A (Algorithm 4.5 step 2; Section
+ * 4.6): for every row, the random signs, a length-n FFT in shared memory (n / 2 complex
+ * points, four-step), and the l / 2 sampled frequencies as [Re, Im] columns scaled by
+ * (l / 2)^-1/2 -- no n x l matrix is formed.  It applies for n a power of two in
+ * [2048, 32768] and an even lda (else RSVD_ERR_UNSUPPORTED); rsvd_svd and
+ * rsvd_range_finder take this route for their first pass when the plan has srft_fft = 1
+ * and its own draw (after rsvd_set_omega the given matrix is multiplied instead). */
+RSVD_API rsvd_status_t rsvd_sketch_srft(rsvd_plan_t plan, const void* A, float* Y);
+
 /* Orthonormalise the columns of Y (device float32, rows x l, leading
  * dimension l, rows <= max(m, n)) in place with the plan's Cholesky-QR
  * rounds; R (device float32, l x l, may be NULL) receives the upper
@@ -330,6 +380,13 @@ RSVD_API rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t plan, const void* co
  * more and writes every gA_b once; asynchronous on the plan's stream. */
 RSVD_API rsvd_status_t rsvd_batched_svd_backward(rsvd_batched_plan_t plan, const void* const* A,
                                                  float* const* gA);
+
+/* The grouped pass's configuration in use, per pass kind c = 2 mode + fold (mode 0: Y = A X,
+ * 1: Y = A^T X; fold: the operand carries a lo half): stages[c] pipeline stages and ctas[c]
+ * CTAs per SM (4 entries each; either may be NULL).  *tuned = 1 once the autotuner has
+ * chosen them (may be NULL). */
+RSVD_API rsvd_status_t rsvd_batched_tuning(rsvd_batched_plan_t plan, int32_t* stages, int32_t* ctas,
+                                           int32_t* tuned);
 
 /* Waits for the plan's stream and returns the device status as rsvd_sync does;
  * *sweeps (may be NULL) receives the largest Jacobi sweep count since the last call. */

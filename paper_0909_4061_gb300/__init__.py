@@ -30,6 +30,7 @@ RSVD_F32, RSVD_BF16, RSVD_BF16X2 = 0, 1, 2
 RSVD_GAUSSIAN, RSVD_SRFT = 0, 1
 RSVD_PLAIN_FP32, RSVD_BF16_TC = 0, 1
 RSVD_SMALL_AUTO, RSVD_SMALL_ONE_CTA, RSVD_SMALL_CLUSTER = 0, 1, 2
+RSVD_EIG_DIRECT, RSVD_EIG_NYSTROM = 0, 1
 
 # every symbol include/rsvd.h declares (checked by the CPU tests)
 EXPORTS = (
@@ -40,6 +41,7 @@ EXPORTS = (
     "rsvd_diagnostics", "rsvd_sketch_bf16_noalloc", "rsvd_convert_a",
     "rsvd_batched_plan_create", "rsvd_batched_plan_destroy", "rsvd_batched_svd", "rsvd_batched_sync",
     "rsvd_batched_svd_backward", "rsvd_wait_selftest", "rsvd_debug_fail_alloc",
+    "rsvd_batched_tuning", "rsvd_sketch_srft", "rsvd_range_finder_adaptive", "rsvd_eig",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
@@ -69,6 +71,8 @@ class Options(ctypes.Structure):
         ("small_svd", ctypes.c_int32),
         ("residual_passes", ctypes.c_int32),
         ("psi_cols", ctypes.c_int32),
+        ("srft_fft", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
         ("host_f32", ctypes.c_int32),
     ]
 
@@ -110,6 +114,10 @@ _SIGS = {
     "rsvd_batched_sync": (_c.c_int, [_P, _P]),
     "rsvd_batched_svd_backward": (_c.c_int, [_P, _P, _P]),
     "rsvd_wait_selftest": (_c.c_int, [_P, _c.c_uint32]),
+    "rsvd_batched_tuning": (_c.c_int, [_P, _P, _P, _P]),
+    "rsvd_sketch_srft": (_c.c_int, [_P, _P, _P]),
+    "rsvd_eig": (_c.c_int, [_P, _P, _c.c_int32, _P, _P]),
+    "rsvd_range_finder_adaptive": (_c.c_int, [_P, _P, _c.c_float, _c.c_int32, _P, _c.c_int64, _P, _P]),
     "rsvd_debug_fail_alloc": (None, [_c.c_int32]),
 }
 
@@ -246,6 +254,24 @@ def rsvd_sketch(plan, A, transpose, X, Y):
     _check(lib().rsvd_sketch(plan, _ptr(A), int(transpose), _ptr(X), _ptr(Y)), "rsvd_sketch")
 
 
+def rsvd_range_finder_adaptive(plan, A, eps, block, Q, ldq):
+    """Returns (rank, estimate); Q's first `rank` columns are the basis."""
+    rank = ctypes.c_int32(0)
+    est = ctypes.c_float(0.0)
+    _check(lib().rsvd_range_finder_adaptive(plan, _ptr(A), float(eps), int(block), _ptr(Q), int(ldq),
+                                            ctypes.byref(rank), ctypes.byref(est)),
+           "rsvd_range_finder_adaptive")
+    return int(rank.value), float(est.value)
+
+
+def rsvd_eig(plan, A, method, U, Lambda):
+    _check(lib().rsvd_eig(plan, _ptr(A), int(method), _ptr(U), _ptr(Lambda)), "rsvd_eig")
+
+
+def rsvd_sketch_srft(plan, A, Y):
+    _check(lib().rsvd_sketch_srft(plan, _ptr(A), _ptr(Y)), "rsvd_sketch_srft")
+
+
 def rsvd_orthonormalize(plan, rows, Y, R=None):
     _check(lib().rsvd_orthonormalize(plan, int(rows), _ptr(Y), _ptr(R)), "rsvd_orthonormalize")
 
@@ -294,8 +320,10 @@ class Plan:
 
     def __init__(self, m, n, k, p=10, q=1, seed=0, precision=RSVD_PLAIN_FP32, orth_rounds=3,
                  lda=0, stream=None, test_matrix=RSVD_GAUSSIAN, single_pass=0, dtype=None,
-                 small_svd=RSVD_SMALL_AUTO, residual_passes=0, host_f32=0, recompute=0, psi_cols=0):
+                 small_svd=RSVD_SMALL_AUTO, residual_passes=0, host_f32=0, recompute=0, psi_cols=0,
+                 srft_fft=0):
         o = rsvd_options_default()
+        o.srft_fft = srft_fft
         o.psi_cols = psi_cols
         o.host_f32 = host_f32
         o.recompute = recompute
@@ -449,7 +477,8 @@ class BatchedPlan:
     shapes: list of (m_b, n_b); lda_b defaults to n_b rounded up to 8.  Outputs are
     concatenated: U (sum m_b, k), S (batch, k), V (sum n_b, k)."""
 
-    def __init__(self, shapes, k, p=8, q=1, seed=0, lda=None, stream=None, orth_rounds=3):
+    def __init__(self, shapes, k, p=8, q=1, seed=0, lda=None, stream=None, orth_rounds=3,
+                 autotune=1):
         self.shapes = [(int(a), int(b)) for a, b in shapes]
         self.batch = len(self.shapes)
         self.k, self.p, self.q = int(k), int(p), int(q)
@@ -460,6 +489,7 @@ class BatchedPlan:
         o.precision = RSVD_BF16_TC
         o.dtype_A = RSVD_BF16
         o.orth_rounds = orth_rounds
+        o.autotune = autotune
         h = ctypes.c_void_p()
         _check(lib().rsvd_batched_plan_create(ctypes.byref(h), self.batch, ms, ns, ld, self.k, self.p,
                                               self.q, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
@@ -512,6 +542,15 @@ class BatchedPlan:
         _check(lib().rsvd_batched_svd_backward(self.handle, ptrs, gptrs), "rsvd_batched_svd_backward")
         self._keep_b = (ptrs, gptrs)
         return grads
+
+    def tuning(self):
+        """{'stages': [4], 'ctas_per_sm': [4], 'tuned': bool} of the grouped pass (per
+        pass kind 2 mode + fold)."""
+        st = (ctypes.c_int32 * 4)()
+        ct = (ctypes.c_int32 * 4)()
+        tu = ctypes.c_int32(0)
+        _check(lib().rsvd_batched_tuning(self.handle, st, ct, ctypes.byref(tu)), "rsvd_batched_tuning")
+        return {"stages": list(st), "ctas_per_sm": list(ct), "tuned": bool(tu.value)}
 
     def sync(self):
         sw = ctypes.c_uint32(0)

@@ -52,6 +52,7 @@ struct rsvd_plan_s {
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
+  uint32_t* srft_signs = nullptr;  // n bits: the signs d_j of the SRFT (row-transform sketch)
   uint32_t* status = nullptr;
   // backward tape: R^-1 of every Cholesky-QR round of Stage A (always: the factorisation
   // writes it there in place of its scratch block), and in store mode (recompute = 0) the
@@ -61,6 +62,9 @@ struct rsvd_plan_s {
   float* tape_qt = nullptr;  // q x n x lp
   bool fwd_ok = false;       // the last call on the plan was rsvd_svd (its state is intact)
   float* bw = nullptr;       // backward workspace (allocated by the first backward call)
+  float* ad = nullptr;       // adaptive range finder workspace (its first call)
+  int ad_block = 0;
+  TcPlan tcb{};              // the tensor-core pass at the adaptive block width
   __nv_bfloat16* xbf = nullptr;  // 2 lp x maxmn: transposed bfloat16 operand of the tensor-core passes
   TcPlan tc{};
   TcPlan tc2{};   // the tensor-core pass at the width of Psi (single pass)
@@ -154,11 +158,12 @@ void free_plan(rsvd_plan_t P) {
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
                   P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32,
-                  P->tape_r, P->tape_q, P->tape_qt, P->bw};
+                  P->tape_r, P->tape_q, P->tape_qt, P->bw, P->srft_signs, P->ad};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
   tc_plan_destroy(&P->tc2);
+  tc_plan_destroy(&P->tcb);
   delete P;
 }
 
@@ -229,6 +234,25 @@ rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
   } else if (want_bf16) {
     TRY(launch_to_bf16_t(P->omega, P->n, P->lp, P->xbf, tc_ld(P->n), 0, 0, P->st));
   }
+  return RSVD_OK;
+}
+
+// The first pass Y = A Omega of an SRFT plan runs as the transform along the rows of A
+// (Algorithm 4.5 step 2) when n is a power of two the row-transform kernel takes and the
+// test matrix is the plan's own draw.
+bool srft_by_fft(rsvd_plan_t P) {
+  return P->opt.srft_fft && P->opt.test_matrix == RSVD_SRFT && P->srft_signs != nullptr &&
+         !P->omega_user;
+}
+
+rsvd_status_t step_srft_fft(rsvd_plan_t P, const void* A, float* out) {
+  Step sp(P, RSVD_STEP_PASS);
+  sp.launched();
+  const int adt = P->opt.dtype_A == RSVD_F32
+                      ? 0
+                      : ((P->opt.dtype_A == RSVD_BF16X2 && P->opt.residual_passes) ? 2 : 1);
+  TRY(launch_srft_fft(adt, A, P->lda, P->m, P->n, P->srft_signs, P->srft_freq, P->l / 2, out, P->lp,
+                      P->num_sms, P->st));
   return RSVD_OK;
 }
 
@@ -364,11 +388,19 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
   const bool tc = P->opt.precision == RSVD_BF16_TC;
   if (tc)
     TRYS(tc_bind_a(&P->tc, A, P->opt.dtype_A == RSVD_BF16X2) == 0 ? RSVD_OK : RSVD_ERR_CUDA);
-  TRYS(step_draw(P, tc));
   int s;
   int64_t stride;
+  // Y_0 = A Omega: the SRFT by its transform along the rows (no n x l matrix), else a pass
+  // with the drawn test matrix
+  if (srft_by_fft(P)) {
+    TRYS(step_srft_fft(P, A, P->partial));
+    s = 1;
+    stride = P->m * P->lp;
+  } else {
+    TRYS(step_draw(P, tc));
+    TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  }
   // the bases go where the backward finds them (the tape in store mode), with their R factors
-  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(0), nullptr, P->q == 0, 0, P->r_q(0)));
   for (int j = 1; j <= P->q; ++j) {
     if (tc) TRYS(step_convert(P, P->basis_q(j - 1), P->m, 0));
@@ -509,6 +541,144 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
   TRY(launch_gemm_f32(0, P->m, P->k, lp, P->qbuf, lp, P->sp(14), kp, U, P->k, 1, 0, P->st));
   TRY(launch_gemm_f32(0, P->n, P->k, lpp, P->qtbuf, lpp, P->sp(15), kp, V, P->k, 1, 0, P->st));
   TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * P->k, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+// ---- adaptive range finder (Algorithm 4.2, blocked; the fixed-precision problem) ----------
+//
+// The sample stream is the n x (l_p + b) Gaussian matrix of Philox stream 3 (block t is its
+// columns (t - 1) b .. t b - 1).  Per block: the posterior estimate max_i ||(I - Q Q^T) A w_i||
+// over the block's samples (read by the host); if it is above eps / (10 sqrt(2/pi)) (4.3),
+// the block is reprojected, orthonormalised (Cholesky QR), reprojected once normalised and
+// orthonormalised again, and appended to Q; then the next block is sampled and projected.
+constexpr uint32_t kStreamAdaptive = 3u;
+
+struct Ad {
+  float *om, *y, *qb, *c, *g;
+};
+
+void ad_layout(rsvd_plan_t P, int b, Ad* w, float* base) {
+  const size_t n = P->n, m = P->m, lp = P->lp;
+  size_t off = 0;
+  auto take = [&](float** p, size_t elems) {
+    *p = base ? base + off : nullptr;
+    off += (elems + 63) & ~size_t(63);
+  };
+  take(&w->om, n * (lp + b));
+  take(&w->y, m * b);
+  take(&w->qb, m * b);
+  take(&w->c, lp * (size_t)b);
+  take(&w->g, (size_t)b * b);
+  (void)off;
+}
+
+size_t ad_elems(rsvd_plan_t P, int b) {
+  const size_t n = P->n, m = P->m, lp = P->lp;
+  auto r = [](size_t e) { return (e + 63) & ~size_t(63); };
+  return r(n * (lp + b)) + 2 * r(m * b) + r(lp * (size_t)b) + r((size_t)b * b);
+}
+
+// out (m x b) = A X for a float32 X (n x b, leading dimension b) at the block width
+rsvd_status_t ad_pass(rsvd_plan_t P, const void* A, const float* X, int b, float* out) {
+  Step sp(P, RSVD_STEP_PASS);
+  int s = 1;
+  const int64_t stride = P->m * b;
+  if (P->opt.precision == RSVD_PLAIN_FP32) {
+    sp.launched(2);
+    s = choose_splits(P->m, b, P->n, P->num_sms);
+    TRY(launch_gemm_f32(0, P->m, b, P->n, static_cast<const float*>(A), P->lda, X, b, P->partial, b, s,
+                        stride, P->st));
+  } else {
+    sp.launched(3);
+    TRY(launch_to_bf16_t(X, P->n, b, P->xbf, tc_ld(P->n), 0, 0, P->st));
+    const int hilo = (P->opt.residual_passes && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
+    if (tc_pass(&P->tcb, 0, 0, hilo, P->partial, &s, P->st) != 0) return RSVD_ERR_CUDA;
+  }
+  TRY(launch_gather(P->partial, s, stride, b, out, b, P->m, b, b, P->st));
+  return RSVD_OK;
+}
+
+// y <- (I - Q Q^T) y for the first j columns of Q (ld lp) and y (m x b)
+rsvd_status_t ad_project(rsvd_plan_t P, const Ad& w, int j, int b, float* y) {
+  if (j == 0) return RSVD_OK;
+  const int lp = P->lp;
+  const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
+  const int s = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->m, 512)));
+  const int64_t stride = (int64_t)j * b;
+  TRY(launch_gemm_f32(1, j, b, P->m, P->qbuf, lp, y, b, P->gpart, b, s, stride, P->st));
+  TRY(launch_gather(P->gpart, s, stride, b, w.c, b, j, b, b, P->st));
+  TRY(launch_small_gemm((int)P->m, b, j, -1.0f, P->qbuf, lp, 0, w.c, b, 0, 1.0f, y, b, P->st));
+  return RSVD_OK;
+}
+
+// the largest column norm of y (m x b): the diagonal of y^T y, summed in row blocks
+rsvd_status_t ad_estimate(rsvd_plan_t P, const Ad& w, int b, const float* y, float* est) {
+  const int nblk = std::max(gram_blocks(P->m), gram_blocks(P->n));
+  const int s = (int)std::min<int64_t>(nblk, std::max<int64_t>(1, cdiv(P->m, 512)));
+  const int64_t stride = (int64_t)b * b;
+  TRY(launch_gemm_f32(1, b, b, P->m, y, b, y, b, P->gpart, b, s, stride, P->st));
+  TRY(launch_gather(P->gpart, s, stride, b, w.g, b, b, b, b, P->st));
+  std::vector<float> g((size_t)b * b);
+  TRY(cudaMemcpyAsync(g.data(), w.g, sizeof(float) * b * b, cudaMemcpyDeviceToHost, P->st));
+  TRY(cudaStreamSynchronize(P->st));
+  float mx = 0.0f;
+  for (int i = 0; i < b; ++i) mx = std::max(mx, g[(size_t)i * b + i]);
+  *est = sqrtf(std::max(mx, 0.0f));
+  return RSVD_OK;
+}
+
+rsvd_status_t run_adaptive(rsvd_plan_t P, const void* A, float eps, int b, float* Q, int64_t ldq,
+                           int32_t* rank, float* estimate) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  const int lp = P->lp, cap = P->l;
+  if (!P->ad || P->ad_block != b) {
+    if (P->ad) {
+      cudaFree(P->ad);
+      P->ad = nullptr;
+    }
+    tc_plan_destroy(&P->tcb);
+    TRYS(dalloc(P, &P->ad, ad_elems(P, b)));
+    P->ad_block = b;
+    if (tc) {
+      if (tc_plan_init(&P->tcb, P->m, P->n, P->lda, b, P->xbf, P->num_sms) != 0) return RSVD_ERR_CUDA;
+      P->tcb.status = P->status;
+    }
+  }
+  Ad w;
+  ad_layout(P, b, &w, P->ad);
+  if (tc && tc_bind_a(&P->tcb, A, P->opt.dtype_A == RSVD_BF16X2) != 0) return RSVD_ERR_CUDA;
+  {
+    Step sp(P, RSVD_STEP_DRAW);
+    sp.launched();
+    TRY(launch_draw_gaussian(P->seed, kStreamAdaptive, P->n, lp + b, lp + b, w.om, lp + b, nullptr, 0,
+                             P->st));
+  }
+  // block t of the sample stream as an n x b matrix (leading dimension b)
+  auto sample = [&](int t, float* out) -> rsvd_status_t {
+    TRY(launch_gather(w.om + (size_t)t * b, 1, 0, lp + b, P->qtbuf, b, P->n, b, b, P->st));
+    return ad_pass(P, A, P->qtbuf, b, out);
+  };
+  const float thresh = eps / (10.0f * sqrtf(2.0f / 3.14159265358979f));
+  int j = 0, t = 0;
+  TRYS(sample(t++, w.y));
+  float est = 0.0f;
+  for (;;) {
+    TRYS(ad_estimate(P, w, b, w.y, &est));
+    if (!(est > thresh) || j + b > cap) break;
+    // steps 7-8 for the block: reproject, orthonormalise, reproject, orthonormalise
+    TRYS(ad_project(P, w, j, b, w.y));
+    TRYS(step_orth(P, w.y, 1, P->m * b, P->m, w.qb, nullptr, true, b));
+    TRYS(ad_project(P, w, j, b, w.qb));
+    TRYS(step_orth(P, w.qb, 1, P->m * b, P->m, w.y, nullptr, true, b));
+    TRY(launch_gather(w.y, 1, 0, b, P->qbuf + j, lp, P->m, b, b, P->st));
+    j += b;
+    // steps 10-11: the next block of samples, projected
+    TRYS(sample(t++, w.y));
+    TRYS(ad_project(P, w, j, b, w.y));
+  }
+  if (j > 0) TRY(launch_gather(P->qbuf, 1, 0, lp, Q, ldq, P->m, j, j, P->st));
+  *rank = j;
+  if (estimate) *estimate = est;
   return RSVD_OK;
 }
 
@@ -761,6 +931,7 @@ void rsvd_options_default(rsvd_options_t* opt) {
   opt->lda = 0;
   opt->residual_passes = 0;
   opt->host_f32 = 0;
+  opt->autotune = 1;
 }
 
 const char* rsvd_status_string(rsvd_status_t s) {
@@ -806,6 +977,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.small_svd == 1 && l > 160) return RSVD_ERR_INVALID_ARG;  // one-CTA Jacobi limit
   if (o.precision == RSVD_BF16_TC && (o.lda % 8) != 0) return RSVD_ERR_INVALID_ARG;  // 16-byte rows
   if (o.host_f32 != 0 && (o.host_f32 != 1 || o.precision != RSVD_BF16_TC)) return RSVD_ERR_INVALID_ARG;
+  if (o.srft_fft != 0 && (o.srft_fft != 1 || o.test_matrix != RSVD_SRFT)) return RSVD_ERR_INVALID_ARG;
   if (o.recompute != 0 && o.recompute != 1) return RSVD_ERR_INVALID_ARG;
 
   rsvd_plan_t P = new (std::nothrow) rsvd_plan_s();
@@ -907,6 +1079,18 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     cudaGetLastError();
     free_plan(P);
     return RSVD_ERR_CUDA;
+  }
+  // the signs for the row-transform sketch (the lda must be even for its paired loads)
+  if (o.test_matrix == RSVD_SRFT && srft_fft_supported(n) && (o.lda % 2) == 0) {
+    if ((s = dalloc(P, &P->srft_signs, (size_t)cdiv(n, 32))) != RSVD_OK) {
+      free_plan(P);
+      return s;
+    }
+    if (launch_srft_signs(seed, n, P->srft_signs, P->st) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(P);
+      return RSVD_ERR_CUDA;
+    }
   }
   if (cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess ||
       cudaMemsetAsync(P->small, 0, sizeof(float) * 24 * lq * lq, P->st) != cudaSuccess) {
@@ -1164,6 +1348,91 @@ rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const
   int64_t stride;
   TRYS(step_pass(P, A, transpose, xin, false, &s, &stride));
   TRY(launch_gather(P->partial, s, stride, P->lp, Y, P->l, my, P->l, P->l, P->st));
+  return RSVD_OK;
+}
+
+// Hermitian Stage B (Section 5.3, 5.4) after Stage A: B1 = A Q (one pass, the basis as a
+// hi + lo pair on the tensor cores), B = Q^T B1 symmetrised; Algorithm 5.3 takes the
+// eigenpairs of B from its SVD (the sign of each eigenvalue from its pair of singular
+// vectors) and lifts U = Q V; Algorithm 5.5 factors B = C^T C (Cholesky, with the pivot
+// floor), F = B1 C^-1, and takes F = U S W^T through Cholesky QR and Jacobi (U = Q_F Ut),
+// Lambda = S^2.
+rsvd_status_t run_eig(rsvd_plan_t P, const void* A, int method, float* U, float* Lambda) {
+  const bool tc = P->opt.precision == RSVD_BF16_TC;
+  const int lp = P->lp, l = P->l, k = P->k;
+  TRYS(stage_a(P, A));
+  int s;
+  int64_t stride;
+  if (tc) TRYS(step_convert(P, P->qbuf, P->m, 1));
+  TRYS(step_pass(P, A, 0, P->qbuf, true, &s, &stride));             // B1 = A Q
+  TRY(launch_gather(P->partial, s, stride, lp, P->tmp1, lp, P->m, lp, lp, P->st));
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched(4);
+    TRYS(bw_tn(P, P->m, P->qbuf, P->tmp1, lp, lp, P->sq()));           // B = Q^T B1
+    TRY(launch_symmetrize(P->sq(), l, lp, P->st));
+    if (method == RSVD_EIG_DIRECT) {
+      TRY(launch_jacobi_svd(P->sq(), lp, 0, l, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+                            P->status + 1, P->st, P->opt.small_svd));
+      TRY(launch_eig_values(P->ut(), P->w(), P->sig, l, lp, k, 0, Lambda, P->st));
+    }
+  }
+  if (method == RSVD_EIG_DIRECT) {
+    Step sp(P, RSVD_STEP_LIFT);
+    sp.launched();
+    TRY(launch_gemm_f32(0, P->m, k, lp, P->qbuf, lp, P->ut(), lp, U, k, 1, 0, P->st));
+    return RSVD_OK;
+  }
+  // Nystrom: B = C^T C, F = B1 C^-1, F = Q_F R_F, R_F = Ut S W^T, U = Q_F Ut, Lambda = S^2
+  {
+    Step sp(P, RSVD_STEP_ORTH);
+    sp.launched(2);
+    TRY(launch_cholesky(P->sq(), l, lp, 0, P->lbuf(), P->rtmp(), P->rinv(), nullptr, 0, P->status,
+                        P->st));
+    TRY(launch_gemm_f32(0, P->m, lp, lp, P->tmp1, lp, P->rinv(), lp, P->tmp2, lp, 1, 0, P->st));
+  }
+  TRYS(step_orth(P, P->tmp2, 1, P->m * lp, P->m, P->qtbuf, P->racc()));
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched(2);
+    TRY(launch_jacobi_svd(P->racc(), lp, 0, l, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd));
+    TRY(launch_eig_values(P->ut(), P->w(), P->sig, l, lp, k, 1, Lambda, P->st));
+  }
+  Step sp(P, RSVD_STEP_LIFT);
+  sp.launched();
+  TRY(launch_gemm_f32(0, P->m, k, lp, P->qtbuf, lp, P->ut(), lp, U, k, 1, 0, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_eig(rsvd_plan_t P, const void* A, int32_t method, float* U, float* Lambda) {
+  TRYS(check_plan(P));
+  if (!A || !U || !Lambda || P->m != P->n ||
+      (method != RSVD_EIG_DIRECT && method != RSVD_EIG_NYSTROM))
+    return RSVD_ERR_INVALID_ARG;
+  if (P->opt.single_pass) return RSVD_ERR_UNSUPPORTED;
+  P->fwd_ok = false;
+  return run_eig(P, A, method, U, Lambda);
+}
+
+rsvd_status_t rsvd_range_finder_adaptive(rsvd_plan_t P, const void* A, float eps, int32_t block,
+                                         float* Q, int64_t ldq, int32_t* rank, float* estimate) {
+  TRYS(check_plan(P));
+  if (!A || !Q || !rank || !(eps > 0.0f) || block < 16 || block % 16 || block > P->l ||
+      ldq < P->l)
+    return RSVD_ERR_INVALID_ARG;
+  if (P->opt.single_pass) return RSVD_ERR_UNSUPPORTED;
+  P->fwd_ok = false;
+  return run_adaptive(P, A, eps, block, Q, ldq, rank, estimate);
+}
+
+rsvd_status_t rsvd_sketch_srft(rsvd_plan_t P, const void* A, float* Y) {
+  TRYS(check_plan(P));
+  if (!A || !Y) return RSVD_ERR_INVALID_ARG;
+  if (P->opt.test_matrix != RSVD_SRFT || !P->srft_signs) return RSVD_ERR_UNSUPPORTED;
+  P->fwd_ok = false;
+  TRYS(step_srft_fft(P, A, P->partial));
+  TRY(launch_gather(P->partial, 1, 0, P->lp, Y, P->l, P->m, P->l, P->l, P->st));
   return RSVD_OK;
 }
 

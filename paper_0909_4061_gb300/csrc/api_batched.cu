@@ -5,8 +5,12 @@
 // passes are bound by reading A, so the doubled MMA width costs nothing measurable), and
 // Omega is drawn as bfloat16 values: the map differentiated by the backward pass is the
 // float32 map on the bfloat16 A with a bfloat16 Omega.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -23,6 +27,7 @@ struct rsvd_batched_plan_s {
   int num_sms = 0;
   std::vector<int64_t> m, n, lda;
   int64_t sum_m = 0, sum_n = 0, xm_total = 0, xn_total = 0;
+  int64_t max_m = 0, max_n = 0;
   // device index arrays
   int64_t* d_roff_m = nullptr;   // nb + 1
   int64_t* d_roff_n = nullptr;   // nb + 1
@@ -71,6 +76,19 @@ struct rsvd_batched_plan_s {
   float** d_gptr = nullptr;
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
+  // CUDA graphs of the forward and of the backward for one binding of the pointers (the
+  // A_b, and U, S, V or the gA_b): every launch of a call replayed as one graph launch
+  cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
+  // pass configuration per (mode, fold): pipeline stages and CTAs per SM, picked by the
+  // autotuner on the first call (tuned = true) or read from its JSON cache
+  int cfg_stages[4] = {rsvd::kBatchedStages, rsvd::kBatchedStages, rsvd::kBatchedStages,
+                       rsvd::kBatchedStages};
+  int cfg_ctas[4] = {1, 1, 1, 1};
+  bool tuned = false;
+  std::vector<const void*> g_fwd_a, g_bwd_a;
+  std::vector<float*> g_bwd_g;
+  const float *g_u = nullptr, *g_s = nullptr, *g_v = nullptr;
+  bool use_graph = true;
 };
 
 namespace rsvd {
@@ -104,6 +122,8 @@ rsvd_status_t balloc(rsvd_batched_plan_t P, T** ptr, size_t elems) {
 
 void bfree(rsvd_batched_plan_t P) {
   if (!P) return;
+  if (P->g_fwd) cudaGraphExecDestroy(P->g_fwd);
+  if (P->g_bwd) cudaGraphExecDestroy(P->g_bwd);
   for (void* a : P->allocs) cudaFree(a);
   delete P;
 }
@@ -145,14 +165,144 @@ rsvd_status_t bind_maps(rsvd_batched_plan_t P, const void* const* A) {
 
 // Y = A X (mode 0: X on the n side, Y on the m side) or Y = A^T X (mode 1); fold: the
 // operand holds hi and lo halves
-rsvd_status_t bpass(rsvd_batched_plan_t P, int mode, int fold, float* y) {
+rsvd_status_t bpass_cfg(rsvd_batched_plan_t P, int mode, int fold, float* y, int stages, int ctas) {
   const void* maps = P->d_maps + (mode ? (size_t)P->nb * 128 : 0);
+  const int grid = P->num_sms * ctas;
   if (mode == 0)
     BTRY(launch_batched_tc(0, fold, maps, fold ? P->map_x_n2 : P->map_x_n, P->d_units0, P->nunits0,
-                           P->d_n, P->d_m, P->d_xoff_n, P->d_roff_m, y, P->num_sms, P->status, P->st));
+                           P->d_n, P->d_m, P->d_xoff_n, P->d_roff_m, y, grid, P->status, P->st, stages));
   else
     BTRY(launch_batched_tc(1, fold, maps, fold ? P->map_x_m2 : P->map_x_m, P->d_units1, P->nunits1,
-                           P->d_m, P->d_n, P->d_xoff_m, P->d_roff_n, y, P->num_sms, P->status, P->st));
+                           P->d_m, P->d_n, P->d_xoff_m, P->d_roff_n, y, grid, P->status, P->st, stages));
+  return RSVD_OK;
+}
+
+rsvd_status_t bpass(rsvd_batched_plan_t P, int mode, int fold, float* y) {
+  const int c = 2 * mode + fold;
+  return bpass_cfg(P, mode, fold, y, P->cfg_stages[c], P->cfg_ctas[c]);
+}
+
+// ---- autotuner of the grouped pass ------------------------------------------------------
+// Candidates (pipeline stages, CTAs per SM): deep pipelines with one CTA per SM, or shallower
+// ones with two CTAs sharing an SM (more units in flight: the batch's units are short, at
+// most 32 k tiles).  Each (mode, fold) pass is timed with CUDA events on the plan's stream
+// on the caller's matrices (two launches per candidate, the second timed) and the fastest
+// kept.  Choices are cached per shape class in the JSON file named by RSVD_TUNE_CACHE (an
+// object of "key": [stages, ctas, ...] entries), so a later plan of the same class skips
+// the timing.
+constexpr int kTuneCand[][2] = {{8, 1}, {6, 1}, {4, 2}, {3, 2}};
+
+std::string tune_key(rsvd_batched_plan_t P) {
+  char buf[160];
+  snprintf(buf, sizeof buf, "batched_pass b%d m%lld n%lld l%d sms%d", P->nb, (long long)P->sum_m,
+           (long long)P->sum_n, P->l, P->num_sms);
+  return buf;
+}
+
+bool tune_cache_read(const std::string& key, int* stages, int* ctas) {
+  const char* path = getenv("RSVD_TUNE_CACHE");
+  if (!path || !path[0]) return false;
+  FILE* f = fopen(path, "rb");
+  if (!f) return false;
+  std::string text;
+  char chunk[4096];
+  size_t got;
+  while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) text.append(chunk, got);
+  fclose(f);
+  const std::string pat = "\"" + key + "\"";
+  const size_t at = text.find(pat);
+  if (at == std::string::npos) return false;
+  const size_t lb = text.find('[', at + pat.size());
+  if (lb == std::string::npos) return false;
+  int v[8];
+  if (sscanf(text.c_str() + lb, "[%d,%d,%d,%d,%d,%d,%d,%d]", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+             &v[6], &v[7]) != 8)
+    return false;
+  for (int c = 0; c < 4; ++c) {
+    if (v[2 * c] < 2 || v[2 * c] > kBatchedStages || v[2 * c + 1] < 1 || v[2 * c + 1] > 2) return false;
+    stages[c] = v[2 * c];
+    ctas[c] = v[2 * c + 1];
+  }
+  return true;
+}
+
+void tune_cache_write(const std::string& key, const int* stages, const int* ctas) {
+  const char* path = getenv("RSVD_TUNE_CACHE");
+  if (!path || !path[0]) return;
+  std::string text;
+  if (FILE* f = fopen(path, "rb")) {
+    char chunk[4096];
+    size_t got;
+    while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) text.append(chunk, got);
+    fclose(f);
+  }
+  // keep the other keys' entries (one per line), replace this key's
+  std::string out = "{\n";
+  size_t pos = 0;
+  bool first = true;
+  while ((pos = text.find('"', pos)) != std::string::npos) {
+    const size_t end = text.find('"', pos + 1);
+    const size_t eol = text.find(']', end);
+    if (end == std::string::npos || eol == std::string::npos) break;
+    const std::string k = text.substr(pos + 1, end - pos - 1);
+    if (k != key) {
+      out += first ? "  " : ",\n  ";
+      out += text.substr(pos, eol + 1 - pos);
+      first = false;
+    }
+    pos = eol + 1;
+  }
+  char entry[256];
+  snprintf(entry, sizeof entry, "%s\"%s\": [%d,%d,%d,%d,%d,%d,%d,%d]\n}\n", first ? "  " : ",\n  ",
+           key.c_str(), stages[0], ctas[0], stages[1], ctas[1], stages[2], ctas[2], stages[3], ctas[3]);
+  out += entry;
+  const std::string tmp = std::string(path) + ".tmp";
+  if (FILE* f = fopen(tmp.c_str(), "wb")) {
+    fwrite(out.data(), 1, out.size(), f);
+    fclose(f);
+    rename(tmp.c_str(), path);
+  }
+}
+
+rsvd_status_t autotune(rsvd_batched_plan_t P) {
+  const std::string key = tune_key(P);
+  if (tune_cache_read(key, P->cfg_stages, P->cfg_ctas)) {
+    P->tuned = true;
+    return RSVD_OK;
+  }
+  cudaEvent_t e0, e1;
+  BTRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RSVD_ERR_CUDA;
+  }
+  rsvd_status_t st = RSVD_OK;
+  for (int c = 0; c < 4 && st == RSVD_OK; ++c) {
+    const int mode = c >> 1, fold = c & 1;
+    float* y = mode ? P->yn : P->ym;
+    float best = 1e30f;
+    for (const auto& cand : kTuneCand) {
+      float ms = 0.0f;
+      if ((st = bpass_cfg(P, mode, fold, y, cand[0], cand[1])) != RSVD_OK) break;
+      if (cudaEventRecord(e0, P->st) != cudaSuccess ||
+          (st = bpass_cfg(P, mode, fold, y, cand[0], cand[1])) != RSVD_OK ||
+          cudaEventRecord(e1, P->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (st == RSVD_OK) st = RSVD_ERR_CUDA;
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        P->cfg_stages[c] = cand[0];
+        P->cfg_ctas[c] = cand[1];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RSVD_OK) return st;
+  P->tuned = true;
+  tune_cache_write(key, P->cfg_stages, P->cfg_ctas);
   return RSVD_OK;
 }
 
@@ -163,8 +313,9 @@ rsvd_status_t to_operand(rsvd_batched_plan_t P, const float* q, bool m_side, int
   return RSVD_OK;
 }
 
+// The caller (rsvd_batched_svd) has bound the maps of the A_b.
 rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
-  BTRYS(bind_maps(P, A));
+  (void)A;
   const int64_t ldx = std::max(P->xm_total, P->xn_total);
   const int rounds = P->opt.orth_rounds;
   BTRY(launch_batched_draw(P->seed, P->d_roff_n, P->nb, P->sum_n, P->l, P->omega, P->xbf, ldx,
@@ -186,8 +337,8 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
   BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->status, P->st));
   BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
-  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->sum_m, P->ub, P->k, P->k, U, P->k, P->st));
-  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, P->k, P->k, V, P->k, P->st));
+  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->max_m, P->ub, P->k, P->k, U, P->k, P->st));
+  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, P->k, P->k, V, P->k, P->st));
   if (S)
     BTRY(cudaMemcpy2DAsync(S, sizeof(float) * P->k, P->sig, sizeof(float) * LP, sizeof(float) * P->k,
                            P->nb, cudaMemcpyDeviceToDevice, P->st));
@@ -203,15 +354,13 @@ rsvd_status_t qr_back(rsvd_batched_plan_t P, const float* Q, const float* gQ, co
   return RSVD_OK;
 }
 
+// The caller (rsvd_batched_svd_backward) has bound the maps and copied the pointer arrays.
 rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* const* gA) {
-  BTRYS(bind_maps(P, A));
-  for (int b = 0; b < P->nb; ++b)
-    if (!gA[b]) return RSVD_ERR_INVALID_ARG;
-  BTRY(cudaMemcpyAsync(P->d_aptr, A, sizeof(void*) * P->nb, cudaMemcpyHostToDevice, P->st));
-  BTRY(cudaMemcpyAsync(P->d_gptr, gA, sizeof(float*) * P->nb, cudaMemcpyHostToDevice, P->st));
+  (void)A;
+  (void)gA;
   const int kr = P->kr;
   // V = Q_B W_k (n side) is the first right factor and the operand of A V
-  BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->sum_n, P->wb, LP, P->k, P->gn, LP, P->st));
+  BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, LP, P->k, P->gn, LP, P->st));
   BTRY(launch_copy_block(P->gn, P->sum_n, P->rbuf, kr, 0, P->st));
   BTRYS(to_operand(P, P->gn, false, 1));
   BTRYS(bpass(P, 0, 1, P->pm));                                                  // A V
@@ -236,6 +385,42 @@ rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* cons
   BTRY(launch_copy_block(P->omega, P->sum_n, P->rbuf, kr, blk * LP, P->st));
   BTRY(launch_bwd_final(P->d_units_f, P->nunits_f, P->d_aptr, P->d_lda, P->d_gptr, P->d_m, P->d_n,
                         P->d_roff_m, P->d_roff_n, P->lbuf, P->rbuf, kr, P->st));
+  return RSVD_OK;
+}
+
+// Runs `body` once under stream capture and keeps the instantiated graph in *exec (one graph
+// launch per call afterwards).  Falls back to direct launches where capture is not possible
+// (the legacy default stream, or capture or instantiation refused).
+template <class F>
+rsvd_status_t run_captured(rsvd_batched_plan_t P, cudaGraphExec_t* exec, F body) {
+  const bool can = P->use_graph && P->st != nullptr && P->st != cudaStreamLegacy &&
+                   P->st != cudaStreamPerThread;
+  if (!can) return body();
+  if (!*exec) {
+    if (cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return body();
+    }
+    const rsvd_status_t st = body();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(P->st, &graph);
+    if (st != RSVD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess || !graph) {
+      cudaGetLastError();
+      return body();
+    }
+    const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      *exec = nullptr;
+      return body();
+    }
+  }
+  BTRY(cudaGraphLaunch(*exec, P->st));
   return RSVD_OK;
 }
 
@@ -269,6 +454,10 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   rsvd_batched_plan_t P = new (std::nothrow) rsvd_batched_plan_s();
   if (!P) return RSVD_ERR_ALLOC;
   P->nb = batch; P->k = k; P->p = p; P->q = q; P->l = l; P->seed = seed; P->opt = o;
+  {
+    const char* e = getenv("RSVD_NO_GRAPH");
+    P->use_graph = !(e && e[0] && e[0] != '0');
+  }
   P->st = static_cast<cudaStream_t>(stream);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -280,6 +469,8 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   }
   P->m.assign(m, m + batch);
   P->n.assign(n, n + batch);
+  P->max_m = *std::max_element(P->m.begin(), P->m.end());
+  P->max_n = *std::max_element(P->n.begin(), P->n.end());
   P->lda.resize(batch);
   std::vector<int64_t> roff_m(batch + 1, 0), roff_n(batch + 1, 0), xoff_m(batch), xoff_n(batch);
   for (int b = 0; b < batch; ++b) {
@@ -378,12 +569,48 @@ rsvd_status_t rsvd_batched_plan_destroy(rsvd_batched_plan_t P) {
 
 rsvd_status_t rsvd_batched_svd(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
   if (!P || !A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
-  return bforward(P, A, U, S, V);
+  // the tensor maps of the A_b are encoded and copied to the device outside the graph; the
+  // graph (all kernels of the forward) is kept while the plan sees the same pointers
+  BTRYS(bind_maps(P, A));
+  if (P->opt.autotune && !P->tuned) BTRYS(autotune(P));   // before the graph is captured
+  const std::vector<const void*> a(A, A + P->nb);
+  if (P->g_fwd && !(a == P->g_fwd_a && U == P->g_u && S == P->g_s && V == P->g_v)) {
+    cudaGraphExecDestroy(P->g_fwd);
+    P->g_fwd = nullptr;
+  }
+  P->g_fwd_a = a;
+  P->g_u = U; P->g_s = S; P->g_v = V;
+  return run_captured(P, &P->g_fwd, [&] { return bforward(P, A, U, S, V); });
 }
 
 rsvd_status_t rsvd_batched_svd_backward(rsvd_batched_plan_t P, const void* const* A, float* const* gA) {
   if (!P || !A || !gA) return RSVD_ERR_INVALID_ARG;
-  return bbackward(P, A, gA);
+  for (int b = 0; b < P->nb; ++b)
+    if (!gA[b]) return RSVD_ERR_INVALID_ARG;
+  BTRYS(bind_maps(P, A));
+  // the pointer arrays the final kernel reads go to the device outside the graph too
+  BTRY(cudaMemcpyAsync(P->d_aptr, A, sizeof(void*) * P->nb, cudaMemcpyHostToDevice, P->st));
+  BTRY(cudaMemcpyAsync(P->d_gptr, gA, sizeof(float*) * P->nb, cudaMemcpyHostToDevice, P->st));
+  const std::vector<const void*> a(A, A + P->nb);
+  const std::vector<float*> g(gA, gA + P->nb);
+  if (P->g_bwd && !(a == P->g_bwd_a && g == P->g_bwd_g)) {
+    cudaGraphExecDestroy(P->g_bwd);
+    P->g_bwd = nullptr;
+  }
+  P->g_bwd_a = a;
+  P->g_bwd_g = g;
+  return run_captured(P, &P->g_bwd, [&] { return bbackward(P, A, gA); });
+}
+
+rsvd_status_t rsvd_batched_tuning(rsvd_batched_plan_t P, int32_t* stages, int32_t* ctas,
+                                  int32_t* tuned) {
+  if (!P) return RSVD_ERR_INVALID_ARG;
+  for (int c = 0; c < 4; ++c) {
+    if (stages) stages[c] = P->cfg_stages[c];
+    if (ctas) ctas[c] = P->cfg_ctas[c];
+  }
+  if (tuned) *tuned = P->tuned ? 1 : 0;
+  return RSVD_OK;
 }
 
 rsvd_status_t rsvd_batched_sync(rsvd_batched_plan_t P, uint32_t* sweeps) {

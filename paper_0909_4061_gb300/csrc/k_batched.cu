@@ -574,27 +574,44 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
 // out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
 // per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
 // for c < valid, 0 for valid <= c < cols; one CTA per matrix, a warp per row
+// One CTA per (matrix, block of kLiftRows rows): the rows of a matrix are spread over
+// several CTAs, and each warp keeps four rows' loads in flight.
+constexpr int kLiftRows = 128;
+
 __global__ void __launch_bounds__(256) batched_lift_kernel(const float* __restrict__ q,
                                                            const int64_t* __restrict__ roff,
                                                            const float* __restrict__ small, int cols,
                                                            int valid, float* __restrict__ out, int ldo) {
   __shared__ float Ss[LPB][LPB + 1];
   const int b = blockIdx.x;
+  const int64_t r_begin = roff[b] + (int64_t)blockIdx.y * kLiftRows;
+  const int64_t r_end = min(roff[b + 1], r_begin + kLiftRows);
+  if (r_begin >= r_end) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
     const int j = e / LPB, c = e % LPB;
     Ss[j][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
   }
   __syncthreads();
-  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
-    const float qv = q[r * LPB + lane];
-    float v0 = 0.0f, v1 = 0.0f;
+  // warp w takes rows r_begin + w, + 8, + 16, ...: four at a time
+  for (int64_t r = r_begin + warp; r < r_end; r += 4 * (blockDim.x >> 5)) {
+    float qv[4];
 #pragma unroll
-    for (int j = 0; j < LPB; j += 2) {
-      v0 = fmaf(__shfl_sync(0xffffffffu, qv, j), Ss[j][lane], v0);
-      v1 = fmaf(__shfl_sync(0xffffffffu, qv, j + 1), Ss[j + 1][lane], v1);
+    for (int u = 0; u < 4; ++u) {
+      const int64_t ru = r + u * (blockDim.x >> 5);
+      qv[u] = ru < r_end ? q[ru * LPB + lane] : 0.0f;
     }
-    if (lane < cols) out[r * ldo + lane] = v0 + v1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t ru = r + u * (blockDim.x >> 5);
+      float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < LPB; j += 2) {
+        v0 = fmaf(__shfl_sync(0xffffffffu, qv[u], j), Ss[j][lane], v0);
+        v1 = fmaf(__shfl_sync(0xffffffffu, qv[u], j + 1), Ss[j + 1][lane], v1);
+      }
+      if (ru < r_end && lane < cols) out[ru * ldo + lane] = v0 + v1;
+    }
   }
 }
 
@@ -622,15 +639,16 @@ cudaError_t prepare_batched() {
 cudaError_t launch_batched_tc(int mode, int fold, const void* maps, const void* map_x,
                               const int2* units, int nunits, const int64_t* kext, const int64_t* mext,
                               const int64_t* xoff, const int64_t* yoff, float* y, int grid,
-                              uint32_t* status, cudaStream_t st) {
+                              uint32_t* status, cudaStream_t st, int stages) {
   if (nunits <= 0) return cudaSuccess;
+  if (stages < 2 || stages > kBatchedStages) return cudaErrorInvalidValue;
   const CUtensorMap* mp = static_cast<const CUtensorMap*>(maps);
   const CUtensorMap& mx = *static_cast<const CUtensorMap*>(map_x);
-  const size_t sm = batched_tc_smem(kBatchedStages, fold);
+  const size_t sm = batched_tc_smem(stages, fold);
   if (grid > nunits) grid = nunits;
 #define RSVD_BTC(MO, FO)                                                                        \
   batched_tc_kernel<MO, FO><<<grid, kBThreads, sm, st>>>(mp, mx, units, nunits, kext, mext, xoff, \
-                                                         yoff, y, kBatchedStages, status)
+                                                         yoff, y, stages, status)
   if (mode == 0 && !fold) RSVD_BTC(0, 0);
   else if (mode == 0) RSVD_BTC(0, 1);
   else if (!fold) RSVD_BTC(1, 0);
@@ -668,12 +686,13 @@ cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb,
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
+cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows,
                                 const float* small, int cols, int valid, float* out, int ldo,
                                 cudaStream_t st) {
-  (void)total_rows;
-  if (cols > LPB) return cudaErrorInvalidValue;
-  batched_lift_kernel<<<nb, 256, 0, st>>>(q, roff, small, cols, valid, out, ldo);
+  if (cols > LPB || max_rows < 1 || cdiv(max_rows, kLiftRows) > 65535) return cudaErrorInvalidValue;
+  // blocks of kLiftRows rows per matrix, as many as the tallest matrix needs
+  const dim3 grid((unsigned)nb, (unsigned)cdiv(max_rows, kLiftRows));
+  batched_lift_kernel<<<grid, 256, 0, st>>>(q, roff, small, cols, valid, out, ldo);
   return cudaGetLastError();
 }
 

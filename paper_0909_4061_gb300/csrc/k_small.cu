@@ -91,7 +91,45 @@ __global__ void wait_selftest_kernel(const uint32_t* __restrict__ flag, uint32_t
   set_status(status, ST_TIMEOUT);
 }
 
+// B <- (B + B^T) / 2 on the leading l x l of an lp x lp block (one thread per pair).
+__global__ void symmetrize_kernel(float* __restrict__ B, int l, int lp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l * l) return;
+  const int i = e / l, j = e % l;
+  if (j <= i) return;
+  const float v = 0.5f * (B[i * lp + j] + B[j * lp + i]);
+  B[i * lp + j] = v;
+  B[j * lp + i] = v;
+}
+
+// Eigenvalues from the SVD of a symmetric l x l matrix, X = Ut S W^T (one warp per value):
+// mode 0, lambda_i = s_i sign(u_i . w_i) (the left and right singular vectors of a
+// symmetric matrix agree up to the sign of its eigenvalue); mode 1, lambda_i = s_i^2.
+__global__ void eig_values_kernel(const float* __restrict__ ut, const float* __restrict__ w,
+                                  const float* __restrict__ s, int l, int lp, int k, int mode,
+                                  float* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < k; i += blockDim.x >> 5) {
+    float d = 0.0f;
+    if (mode == 0)
+      for (int r = lane; r < l; r += 32) d = fmaf(ut[r * lp + i], w[r * lp + i], d);
+    d = warp_sum(d);
+    if (lane == 0) out[i] = mode == 0 ? (d < 0.0f ? -s[i] : s[i]) : s[i] * s[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_symmetrize(float* B, int l, int lp, cudaStream_t st) {
+  symmetrize_kernel<<<(unsigned)cdiv((int64_t)l * l, 256), 256, 0, st>>>(B, l, lp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_values(const float* ut, const float* w, const float* s, int l, int lp, int k,
+                              int mode, float* out, cudaStream_t st) {
+  eig_values_kernel<<<1, 256, 0, st>>>(ut, w, s, l, lp, k, mode, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wait_selftest(const uint32_t* flag, uint32_t spins, uint32_t* status,
                                  cudaStream_t st) {

@@ -96,6 +96,17 @@ cudaError_t launch_draw_srft(uint64_t seed, int64_t n, int lc, int cols_pad, con
                              float* out, int64_t ld, __nv_bfloat16* out_t, int64_t ld_t,
                              cudaStream_t st);
 
+// The SRFT sketch as a transform along the rows of A (k_srft_fft.cu): y (m x ldy) gets
+// [Re, Im] of l_c^-1/2 sum_j a_j d_j exp(-2 pi i j b_c / n) in columns 2c, 2c + 1 and zeros
+// up to ldy.  adt: A float32 (0), bfloat16 (1), bfloat16 hi + lo (2, lo m rows further);
+// n a power of two in [2048, 32768] (srft_fft_supported), lda even.  signs: n bits, bit j
+// set where d_j = -1 (launch_srft_signs, from the SRFT draws of the seed).
+bool srft_fft_supported(int64_t n);
+cudaError_t launch_srft_signs(uint64_t seed, int64_t n, uint32_t* mask, cudaStream_t st);
+cudaError_t launch_srft_fft(int adt, const void* A, int64_t lda, int64_t m, int64_t n,
+                            const uint32_t* signs, const int* freq, int lc, float* y, int ldy,
+                            int num_sms, cudaStream_t st);
+
 // scratch: lp x lp floats of workspace (used by the cluster variant).
 cudaError_t launch_jacobi_svd(const float* x, int64_t ldx, int transposed, int l, int lp,
                               float* ut, float* s, float* w, float* scratch, uint32_t* status,
@@ -143,6 +154,13 @@ cudaError_t launch_colscale(int64_t rows, int ncols, int lp, const float* X, int
                             int inv, float alpha, int accumulate, float* Y, cudaStream_t st);
 // out[j] = gS[j] + rec, j < k.
 cudaError_t launch_gs_total(const float* gS, int k, int rec, float* out, cudaStream_t st);
+
+// Hermitian Stage B helpers: B <- (B + B^T) / 2 on the leading l x l (ld lp); eigenvalues
+// from the SVD Ut S W^T of a symmetric matrix (mode 0: s_i sign(u_i . w_i)) or the squares
+// s_i^2 (mode 1, the Nystrom factor's), k of them.
+cudaError_t launch_symmetrize(float* B, int l, int lp, cudaStream_t st);
+cudaError_t launch_eig_values(const float* ut, const float* w, const float* s, int l, int lp, int k,
+                              int mode, float* out, cudaStream_t st);
 
 // A bounded wait on `flag` (never set by the library) that records ST_TIMEOUT after `spins`
 // polls and returns (rsvd_wait_selftest).

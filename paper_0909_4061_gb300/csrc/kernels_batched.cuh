@@ -19,13 +19,16 @@ cudaError_t prepare_batched();
 // address of the operand's tensor map (passed by value; 64 rows hi + lo when fold = 1);
 // kext/mext/xoff/yoff: per-matrix K extent, output rows, operand column offset, output
 // row offset (device).
+// grid: CTAs (units are dealt round-robin); stages: pipeline depth, 2 .. kBatchedStages
+// (smem batched_tc_smem(stages, fold) per CTA; fewer stages let two CTAs share an SM).
 cudaError_t launch_batched_tc(int mode, int fold, const void* maps, const void* map_x, const int2* units,
                               int nunits, const int64_t* kext, const int64_t* mext,
                               const int64_t* xoff, const int64_t* yoff, float* y, int grid,
-                              uint32_t* status, cudaStream_t st);
+                              uint32_t* status, cudaStream_t st, int stages = kBatchedStages);
 cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int64_t total_rows, int l,
                                 float* omega, __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff,
                                 cudaStream_t st);
+// Cholesky-QR rounds per matrix (rows of matrix b from roff[b]), one CTA per matrix.
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
                                   int rounds, float* rout, uint32_t* status, cudaStream_t st);
 cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb, int64_t total_rows,
@@ -33,7 +36,9 @@ cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb,
                                     cudaStream_t st);
 cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb, float* ut, float* sig,
                                   float* w, uint32_t* status, uint32_t* info, cudaStream_t st);
-cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t total_rows,
+// out rows of matrix b = its rows of q times the leading `valid` columns of its LP x LP small
+// matrix (cols outputs per row); max_rows: the most rows any matrix has.
+cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows,
                                 const float* small, int cols, int valid, float* out, int ldo,
                                 cudaStream_t st);
 

@@ -104,3 +104,32 @@ def test_batched_backward_matches_autograd(rsvd_lib, q):
         tol = 1e-4 + 20 * 2.0 ** -24 * kap * chain
         print(f"backward b={b} q={q}: rel err {rel:.3e}  chain share {chain:.3e}  kappa(Y0) {kap:.3e}  tol {tol:.3e}")
         assert rel <= tol, (rel, tol)
+
+
+def test_batched_graph_replay_and_autotuner(rsvd_lib, tmp_path, monkeypatch):
+    """The first call times the grouped pass's configurations (autotuner, cached in the JSON
+    file named by RSVD_TUNE_CACHE) and captures the forward in a CUDA graph; later calls
+    replay it.  Replays give the same bits; a second plan of the same shape class reads
+    the cache instead of timing."""
+    import json
+
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("RSVD_TUNE_CACHE", str(cache))
+    shapes = SHAPES[:5]
+    mats, _ = _make_batch(shapes, 1205)
+    with rsvd_lib.BatchedPlan(shapes, 16, 8, 1, seed=5) as pl:
+        U1, S1, V1 = pl.svd(mats)
+        U2, S2, V2 = pl.svd(mats, *[torch.empty_like(t) for t in (U1, S1, V1)])
+        t = pl.tuning()
+        g1 = pl.backward(mats)
+        g2 = pl.backward(mats)
+        pl.sync()
+    assert t["tuned"] and all(2 <= s <= 8 for s in t["stages"]) and all(c in (1, 2) for c in t["ctas_per_sm"])
+    assert torch.equal(U1, U2) and torch.equal(S1, S2) and torch.equal(V1, V2)
+    assert all(torch.equal(a, b) for a, b in zip(g1, g2))
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1 and len(next(iter(entries.values()))) == 8
+    with rsvd_lib.BatchedPlan(shapes, 16, 8, 1, seed=5) as pl2:
+        pl2.svd(mats)
+        assert pl2.tuning() == t
+        pl2.sync()

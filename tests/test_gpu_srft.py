@@ -78,3 +78,54 @@ def test_srft_sketch_is_the_fft_sketch(rsvd_lib):
     ref = srft.sketch_fft(a32.astype(np.float64), signs, freqs)
     scale = np.abs(a32).astype(np.float64) @ np.abs(srft.omega_real(signs, freqs))
     assert np.all(np.abs(_np(Y) - ref) <= 1e-5 * scale + 1e-6)
+
+
+@pytest.mark.parametrize("m,n,l,kind", [(300, 2048, 64, "f32"), (257, 4096, 128, "f32"), (130, 8192, 32, "bf16"),
+                                        (96, 16384, 40, "f32"), (300, 32768, 256, "f32"), (260, 32768, 256, "hilo")])
+def test_srft_row_transform_matches_oracle(rsvd_lib, m, n, l, kind):
+    """The row-transform sketch (signs, a length-n FFT per row in shared memory, the sampled
+    frequencies) against the oracle's full-FFT form of Algorithm 4.5 on the stored A.  An
+    FFT's rounding error per output is about log2(n) u32 ||row||_2 (times the output scale
+    l_c^-1/2): the bound allows 8 log2(n) u32 ||row||_2 / sqrt(l_c)."""
+    pkg = rsvd_lib
+    rng = np.random.default_rng(n + l)
+    a32 = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)))).astype(np.float32)
+    seed = 2004
+    kw = {}
+    if kind == "bf16":
+        kw = dict(precision=pkg.RSVD_BF16_TC, dtype=pkg.RSVD_BF16)
+    elif kind == "hilo":
+        kw = dict(precision=pkg.RSVD_BF16_TC, dtype=pkg.RSVD_BF16X2, residual_passes=1)
+    with pkg.Plan(m, n, l - 4, 4, 0, seed, test_matrix=pkg.RSVD_SRFT, **kw) as pl:
+        A = pl.stored(_dev(a32))
+        Y = torch.full((m, l), float("nan"), device="cuda")
+        pkg.rsvd_sketch_srft(pl.handle, A, Y)
+        assert pkg.rsvd_sync(pl.handle) == pkg.RSVD_OK
+        a_st = _np(A)
+    if kind == "hilo":
+        a_st = a_st[:m] + a_st[m:]
+    signs, freqs = srft.draw(seed, n, l // 2)
+    ref = srft.sketch_fft(a_st, signs, freqs)
+    tol = 8 * np.log2(n) * 2.0 ** -24 * np.linalg.norm(a_st, axis=1, keepdims=True) / np.sqrt(l // 2)
+    err = np.abs(_np(Y) - ref)
+    print(f"srft row transform n={n} l={l} {kind}: max err / tol {np.max(err / tol):.3f}")
+    assert np.all(err <= tol)
+
+
+def test_srft_row_transform_is_the_plans_first_pass(rsvd_lib):
+    """rsvd_range_finder on an SRFT plan with n = 4096 and srft_fft = 1 takes the row
+    transform; setting the same Omega explicitly takes the dense pass: the two bases agree
+    to float32 rounding."""
+    import synth
+
+    pkg = rsvd_lib
+    m, n, k, p, q = 900, 4096, 40, 24, 1
+    a, *_ = synth.lowrank(m, n, synth.spectrum_power(min(m, n), 0.5), 5)
+    A = _dev(a.astype(np.float32))
+    with pkg.Plan(m, n, k, p, q, 7, test_matrix=pkg.RSVD_SRFT, srft_fft=1) as pl:
+        Q1 = pl.range_finder(A)
+        om = torch.zeros(n, k + p, device="cuda")
+        pkg.rsvd_get_omega(pl.handle, om)
+        pkg.rsvd_set_omega(pl.handle, om)
+        Q2 = pl.range_finder(A)
+    assert torch.max(torch.abs(Q1 - Q2)).item() <= 1e-4

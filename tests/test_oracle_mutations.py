@@ -123,3 +123,20 @@ def test_dropped_power_step_in_the_gradient_is_caught(monkeypatch):
     orig = grad._rsvd_torch
     monkeypatch.setattr(grad, "_rsvd_torch", lambda at, om, k, q: orig(at, om, k, 0))
     _fails(pins.test_cotangent_gradient_autograd_vs_finite_differences)
+
+
+def test_adaptive_without_the_second_reprojection_is_caught(monkeypatch):
+    import tests.test_oracle_adaptive as apins
+    from oracle import adaptive
+
+    monkeypatch.setattr(adaptive, "orth_block",
+                        lambda q, y: adaptive.qr_pos(adaptive.project_out(q, y))[0])
+    _fails(apins.test_exact_rank_recovery)
+
+
+def test_adaptive_threshold_without_the_estimate_constant_is_caught(monkeypatch):
+    import tests.test_oracle_adaptive as apins
+    from oracle import adaptive
+
+    monkeypatch.setattr(adaptive, "THRESHOLD_FACTOR", 1.0 / 100.0)   # stops far too early
+    _fails(apins.test_tolerance_is_met_and_the_basis_is_economical, 1e-4, 8)
