@@ -140,3 +140,37 @@ def test_adaptive_threshold_without_the_estimate_constant_is_caught(monkeypatch)
 
     monkeypatch.setattr(adaptive, "THRESHOLD_FACTOR", 1.0 / 100.0)   # stops far too early
     _fails(apins.test_tolerance_is_met_and_the_basis_is_economical, 1e-4, 8)
+
+
+def test_row_pivoting_on_the_shortest_row_is_caught(monkeypatch):
+    import tests.test_oracle_row_extraction as rpins
+    from oracle import row_extraction
+
+    def bad(y, count):
+        r = np.array(y, dtype=np.float64, copy=True)
+        chosen = []
+        for _ in range(count):
+            norms = np.einsum("ij,ij->i", r, r)
+            norms[chosen] = np.inf
+            j = int(np.argmin(norms))
+            chosen.append(j)
+            v = r[j] / np.linalg.norm(r[j])
+            r -= np.outer(r @ v, v)
+        return np.array(chosen)
+
+    monkeypatch.setattr(row_extraction, "pivot_rows", bad)
+    _fails(rpins.test_pivots_match_lapack_column_pivoted_qr)
+
+
+def test_untransposed_r_in_row_extraction_is_caught(monkeypatch):
+    import tests.test_oracle_row_extraction as rpins
+    from oracle import row_extraction
+
+    def bad(a, qmat):
+        jset, x = row_extraction.interpolative_rows(qmat)
+        w, r = row_extraction.qr_pos(a[jset].T)
+        u, s, vt_t = np.linalg.svd(x @ r, full_matrices=False)     # R where R^T belongs
+        return u, s, w @ vt_t.T, jset, x
+
+    monkeypatch.setattr(row_extraction, "svd_row_extraction", bad)
+    _fails(rpins.test_lemma_5_1_identity_and_bound)
