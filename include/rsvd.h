@@ -144,6 +144,29 @@ RSVD_API rsvd_status_t rsvd_range_finder(rsvd_plan_t plan, const void* A, float*
  * n x k, all float32 row-major with leading dimension k.  A ~= U diag(S) V^T. */
 RSVD_API rsvd_status_t rsvd_svd(rsvd_plan_t plan, const void* A, float* U, float* S, float* V);
 
+/* The interpolative decomposition of the rows of Y (Section 3.2.3): an index set J of l
+ * rows and X (m x l) with X[J, :] = I and Y = X Y[J, :], for Y of rank l.  The rows are
+ * chosen by successive orthogonalization with pivoting (Businger--Golub, Section 3.3.2,
+ * applied to the rows: at each step the row with the longest residual; ties to the lowest
+ * index), one cooperative launch of one CTA per SM with a grid barrier per step; X =
+ * C L^-1 from the coefficients C of every row on the pivot directions and their
+ * triangular block L = C[J, :].
+ *   Y: device, m x l float32 (the plan's m and l), leading dimension ldy >= l; read only.
+ *   J: device, l int32, the pivots in the order chosen; X: device, m x l float32, ldx >= l.
+ * Y of rank < l: the pivots from the step where no row is left are -1 and rsvd_sync
+ * returns RSVD_ERR_NUMERICAL.  The entries of X are not bounded by 2 in general (that
+ * bound belongs to the strong rank-revealing ID); they are small for bases from Stage A. */
+RSVD_API rsvd_status_t rsvd_row_id(rsvd_plan_t plan, const float* Y, int64_t ldy, int32_t* J,
+                                   float* X, int64_t ldx);
+
+/* Stage B by row extraction (Algorithm 5.2) after Stage A as in rsvd_svd: the ID of the
+ * basis, Q = X Q[J, :] (rsvd_row_id); A[J, :]^T = W R (Cholesky-QR); Z = X R^T; Z = U S Vt^T
+ * (Cholesky-QR and Jacobi); V = W Vt.  A is read by Stage A and in l rows only: no pass
+ * B = Q^T A.  ||A - U S V^T|| <= (1 + ||X||) ||A - Q Q^T A|| (Lemma 5.1), usually larger
+ * than the error of rsvd_svd.  Outputs as rsvd_svd (device U m x k, S k, V n x k). */
+RSVD_API rsvd_status_t rsvd_svd_row_extraction(rsvd_plan_t plan, const void* A, float* U, float* S,
+                                               float* V);
+
 /* Stage B for a symmetric A (m = n; Section 5.3, 5.4), after Stage A as in rsvd_svd:
  *   RSVD_EIG_DIRECT  -- Algorithm 5.3: B = Q^T A Q, B = V Lambda V^T, U = Q V
  *                       (||A - U Lambda U^T|| <= 2 ||A - Q Q^T A||);
@@ -242,7 +265,8 @@ enum {
   RSVD_STEP_SMALL_SVD = 3,  /* Jacobi SVD of the l x l factor */
   RSVD_STEP_LIFT = 4,       /* U = Q Ut_k, V = Q_B W_k */
   RSVD_STEP_CONVERT = 5,    /* float32 -> transposed bfloat16 operands */
-  RSVD_NUM_STEPS = 6
+  RSVD_STEP_ID = 6,         /* pivoted row selection of the interpolative decomposition */
+  RSVD_NUM_STEPS = 7
 };
 
 /* Start per-step timing: for every step kind whose bit is set in `mask`,

@@ -32,19 +32,28 @@ import numpy as np
 from .rsvd64 import qr_pos
 
 
-def pivot_rows(y: np.ndarray, count: int) -> np.ndarray:
-    """Businger--Golub pivoting on the rows of y: ``count`` row indices, in the order chosen."""
+def pivot_rows(y: np.ndarray, count: int, with_margins: bool = False):
+    """Businger--Golub pivoting on the rows of y: ``count`` row indices, in the order chosen.
+
+    with_margins: also return, per step, how far the chosen row's squared residual norm
+    stands above the next longest, relative to it (a decision that another rounding could
+    take differently has a small margin)."""
     r = np.array(y, dtype=np.float64, copy=True)
     chosen: list[int] = []
+    margins = []
     for _ in range(count):
         norms = np.einsum("ij,ij->i", r, r)
         norms[chosen] = -1.0
         j = int(np.argmax(norms))                # the first of equal maxima
+        if with_margins:
+            second = np.max(np.delete(norms, j)) if len(norms) > 1 else -1.0
+            margins.append((norms[j] - max(second, 0.0)) / norms[j])
         chosen.append(j)
         v = r[j] / np.sqrt(norms[j])
         r -= np.outer(r @ v, v)
         r[j] = 0.0
-    return np.array(chosen, dtype=np.int64)
+    jset = np.array(chosen, dtype=np.int64)
+    return (jset, np.array(margins)) if with_margins else jset
 
 
 def interpolative_rows(y: np.ndarray):

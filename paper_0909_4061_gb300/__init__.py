@@ -42,11 +42,12 @@ EXPORTS = (
     "rsvd_batched_plan_create", "rsvd_batched_plan_destroy", "rsvd_batched_svd", "rsvd_batched_sync",
     "rsvd_batched_svd_backward", "rsvd_wait_selftest", "rsvd_debug_fail_alloc",
     "rsvd_batched_tuning", "rsvd_sketch_srft", "rsvd_range_finder_adaptive", "rsvd_eig",
+    "rsvd_row_id", "rsvd_svd_row_extraction",
 )
 
 RSVD_STEP_DRAW, RSVD_STEP_PASS, RSVD_STEP_ORTH = 0, 1, 2
-RSVD_STEP_SMALL_SVD, RSVD_STEP_LIFT, RSVD_STEP_CONVERT, RSVD_NUM_STEPS = 3, 4, 5, 6
-STEP_NAMES = ("draw", "pass", "orth", "small_svd", "lift", "convert")
+RSVD_STEP_SMALL_SVD, RSVD_STEP_LIFT, RSVD_STEP_CONVERT, RSVD_STEP_ID, RSVD_NUM_STEPS = 3, 4, 5, 6, 7
+STEP_NAMES = ("draw", "pass", "orth", "small_svd", "lift", "convert", "id")
 
 
 class RsvdUnavailable(ImportError):
@@ -117,6 +118,8 @@ _SIGS = {
     "rsvd_batched_tuning": (_c.c_int, [_P, _P, _P, _P]),
     "rsvd_sketch_srft": (_c.c_int, [_P, _P, _P]),
     "rsvd_eig": (_c.c_int, [_P, _P, _c.c_int32, _P, _P]),
+    "rsvd_row_id": (_c.c_int, [_P, _P, _c.c_int64, _P, _P, _c.c_int64]),
+    "rsvd_svd_row_extraction": (_c.c_int, [_P, _P, _P, _P, _P]),
     "rsvd_range_finder_adaptive": (_c.c_int, [_P, _P, _c.c_float, _c.c_int32, _P, _c.c_int64, _P, _P]),
     "rsvd_debug_fail_alloc": (None, [_c.c_int32]),
 }
@@ -262,6 +265,15 @@ def rsvd_range_finder_adaptive(plan, A, eps, block, Q, ldq):
                                             ctypes.byref(rank), ctypes.byref(est)),
            "rsvd_range_finder_adaptive")
     return int(rank.value), float(est.value)
+
+
+def rsvd_row_id(plan, Y, ldy, J, X, ldx):
+    _check(lib().rsvd_row_id(plan, _ptr(Y), int(ldy), _ptr(J), _ptr(X), int(ldx)), "rsvd_row_id")
+
+
+def rsvd_svd_row_extraction(plan, A, U, S, V):
+    _check(lib().rsvd_svd_row_extraction(plan, _ptr(A), _ptr(U), _ptr(S), _ptr(V)),
+           "rsvd_svd_row_extraction")
 
 
 def rsvd_eig(plan, A, method, U, Lambda):

@@ -63,6 +63,8 @@ struct rsvd_plan_s {
   bool fwd_ok = false;       // the last call on the plan was rsvd_svd (its state is intact)
   float* bw = nullptr;       // backward workspace (allocated by the first backward call)
   float* ad = nullptr;       // adaptive range finder workspace (its first call)
+  float* re = nullptr;       // row ID workspace (its first call): C, candidates, pivots, barrier
+  int re_grid = 0;
   int ad_block = 0;
   TcPlan tcb{};              // the tensor-core pass at the adaptive block width
   __nv_bfloat16* xbf = nullptr;  // 2 lp x maxmn: transposed bfloat16 operand of the tensor-core passes
@@ -158,7 +160,7 @@ void free_plan(rsvd_plan_t P) {
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
                   P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32,
-                  P->tape_r, P->tape_q, P->tape_qt, P->bw, P->srft_signs, P->ad};
+                  P->tape_r, P->tape_q, P->tape_qt, P->bw, P->srft_signs, P->ad, P->re};
   for (void* b : bufs)
     if (b) cudaFree(b);
   tc_plan_destroy(&P->tc);
@@ -1403,6 +1405,112 @@ rsvd_status_t run_eig(rsvd_plan_t P, const void* A, int method, float* U, float*
   sp.launched();
   TRY(launch_gemm_f32(0, P->m, k, lp, P->qtbuf, lp, P->ut(), lp, U, k, 1, 0, P->st));
   return RSVD_OK;
+}
+
+// The row ID of res (m x lp, ld lp, overwritten): pivots and coefficients in the row ID
+// workspace, then Linv = L^-1 (lower, ld lp) in sp(1) from Lt = C[J]^T (sp(0)).
+struct Re {
+  float* coef;
+  float* cand;
+  int* piv;
+  unsigned* bar;
+};
+
+rsvd_status_t re_workspace(rsvd_plan_t P, Re* w) {
+  const int lp = P->lp;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(P->num_sms, cdiv(P->m, 64)));
+  const size_t cm = (size_t)P->m * lp, cc = id_cand_floats(grid, lp);
+  const size_t coff = (cm + 63) & ~size_t(63), poff = coff + ((cc + 63) & ~size_t(63));
+  if (!P->re) {
+    TRYS(dalloc(P, &P->re, poff + (size_t)lp + 64));
+    P->re_grid = grid;
+  }
+  w->coef = P->re;
+  w->cand = P->re + coff;
+  w->piv = reinterpret_cast<int*>(P->re + poff);
+  w->bar = reinterpret_cast<unsigned*>(P->re + poff + lp);
+  return RSVD_OK;
+}
+
+rsvd_status_t step_row_id(rsvd_plan_t P, float* res, Re* w) {
+  const int lp = P->lp, l = P->l;
+  TRYS(re_workspace(P, w));
+  {
+    Step sp(P, RSVD_STEP_ID);
+    sp.launched();
+    TRY(cudaMemsetAsync(w->coef, 0, sizeof(float) * (size_t)P->m * lp, P->st));
+    TRY(cudaMemsetAsync(w->bar, 0, sizeof(unsigned), P->st));
+    TRY(launch_id_pivot(res, P->m, l, lp, w->coef, w->piv, w->cand, w->bar, P->status, P->re_grid,
+                        P->st));
+  }
+  Step sp(P, RSVD_STEP_SMALL_SVD);
+  sp.launched(3);
+  TRY(launch_id_lt(w->coef, w->piv, l, lp, P->sp(0), P->st));
+  TRY(launch_trinv_upper(P->sp(0), l, lp, P->sp(2), P->st));      // L^-T
+  TRY(launch_transpose_square(P->sp(2), lp, P->sp(1), P->st));    // L^-1
+  return RSVD_OK;
+}
+
+// Algorithm 5.2 after Stage A: the ID of Q (in place in qbuf), A[J]^T = W R, Z = C L^-1 R^T,
+// Z = Q_Z R_Z, R_Z = Ut S Vt^T, U = Q_Z Ut, V = W Vt.
+rsvd_status_t run_row_extraction(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  const int lp = P->lp, l = P->l, k = P->k;
+  TRYS(stage_a(P, A));
+  Re w;
+  TRYS(step_row_id(P, P->qbuf, &w));
+  {
+    Step sp(P, RSVD_STEP_CONVERT);
+    sp.launched();
+    const int adt = P->opt.dtype_A == RSVD_F32 ? 0 : (P->opt.dtype_A == RSVD_BF16 ? 1 : 2);
+    TRY(launch_gather_rows_t(adt, A, P->lda, P->m, P->n, w.piv, l, lp, P->partial, P->st));
+  }
+  TRYS(step_orth(P, P->partial, 1, P->n * lp, P->n, P->qtbuf, P->racc()));   // A[J]^T = W R
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched(2);
+    TRY(cudaMemsetAsync(P->sp(3), 0, sizeof(float) * (size_t)lp * lp, P->st));
+    TRY(launch_small_gemm(l, l, l, 1.f, P->sp(1), lp, 0, P->racc(), lp, 1, 0.f, P->sp(3), lp, P->st));
+  }
+  {
+    Step sp(P, RSVD_STEP_LIFT);
+    sp.launched();
+    TRY(launch_gemm_f32(0, P->m, lp, lp, w.coef, lp, P->sp(3), lp, P->tmp2, lp, 1, 0, P->st));  // Z
+  }
+  TRYS(step_orth(P, P->tmp2, 1, P->m * lp, P->m, P->qbuf, P->racc()));
+  {
+    Step sp(P, RSVD_STEP_SMALL_SVD);
+    sp.launched();
+    TRY(launch_jacobi_svd(P->racc(), lp, 0, l, lp, P->ut(), P->sig, P->w(), P->lbuf(), P->status,
+                          P->status + 1, P->st, P->opt.small_svd));
+  }
+  Step sp(P, RSVD_STEP_LIFT);
+  sp.launched(2);
+  TRY(launch_gemm_f32(0, P->m, k, lp, P->qbuf, lp, P->ut(), lp, U, k, 1, 0, P->st));
+  TRY(launch_gemm_f32(0, P->n, k, lp, P->qtbuf, lp, P->w(), lp, V, k, 1, 0, P->st));
+  TRY(cudaMemcpyAsync(S, P->sig, sizeof(float) * k, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_row_id(rsvd_plan_t P, const float* Y, int64_t ldy, int32_t* J, float* X, int64_t ldx) {
+  TRYS(check_plan(P));
+  if (!Y || !J || !X || ldy < P->l || ldx < P->l) return RSVD_ERR_INVALID_ARG;
+  P->fwd_ok = false;
+  TRY(launch_gather(Y, 1, 0, ldy, P->tmp1, P->lp, P->m, P->l, P->lp, P->st));
+  Re w;
+  TRYS(step_row_id(P, P->tmp1, &w));
+  Step sp(P, RSVD_STEP_LIFT);
+  sp.launched();
+  TRY(launch_gemm_f32(0, P->m, P->l, P->lp, w.coef, P->lp, P->sp(1), P->lp, X, ldx, 1, 0, P->st));
+  TRY(cudaMemcpyAsync(J, w.piv, sizeof(int32_t) * P->l, cudaMemcpyDeviceToDevice, P->st));
+  return RSVD_OK;
+}
+
+rsvd_status_t rsvd_svd_row_extraction(rsvd_plan_t P, const void* A, float* U, float* S, float* V) {
+  TRYS(check_plan(P));
+  if (!A || !U || !S || !V) return RSVD_ERR_INVALID_ARG;
+  if (P->opt.single_pass) return RSVD_ERR_UNSUPPORTED;
+  P->fwd_ok = false;
+  return run_row_extraction(P, A, U, S, V);
 }
 
 rsvd_status_t rsvd_eig(rsvd_plan_t P, const void* A, int32_t method, float* U, float* Lambda) {

@@ -1293,7 +1293,7 @@ template <int NB>
 cudaError_t prep_chol() {
   cudaError_t e = cudaFuncSetAttribute(cholesky_blocked_kernel<NB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem<NB>());
-  if (e != cudaSuccess || NB <= 10) return e;
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(trinv_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)trinv_smem<NB>());
 }
@@ -1377,6 +1377,20 @@ cudaError_t launch_gram_reduce(const float* gpart, int nblk, int lp, float* g, c
   const int64_t n = (int64_t)lp * lp;
   return launch_pdl(gram_reduce_kernel, dim3((unsigned)cdiv(n, 32)), dim3(512), 0, st, gpart, nblk,
                     lp, g);
+}
+
+cudaError_t launch_trinv_upper(const float* r, int l, int lp, float* rinv, cudaStream_t st) {
+#define RSVD_TRINV_CASE(NB) \
+  case NB:                  \
+    return launch_pdl(trinv_kernel<NB>, dim3(NB), dim3(256), trinv_smem<NB>(), st, r, l, rinv);
+  switch (lp % CB == 0 ? lp / CB : 0) {
+    RSVD_TRINV_CASE(1) RSVD_TRINV_CASE(2) RSVD_TRINV_CASE(3) RSVD_TRINV_CASE(4) RSVD_TRINV_CASE(5)
+    RSVD_TRINV_CASE(6) RSVD_TRINV_CASE(7) RSVD_TRINV_CASE(8) RSVD_TRINV_CASE(9) RSVD_TRINV_CASE(10)
+    RSVD_TRINV_CASE(11) RSVD_TRINV_CASE(12) RSVD_TRINV_CASE(13) RSVD_TRINV_CASE(14)
+    RSVD_TRINV_CASE(15) RSVD_TRINV_CASE(16)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RSVD_TRINV_CASE
 }
 
 cudaError_t launch_cholesky(const float* g, int l, int lp, int shifted, float* lbuf, float* r_out,

@@ -155,6 +155,25 @@ cudaError_t launch_colscale(int64_t rows, int ncols, int lp, const float* X, int
 // out[j] = gS[j] + rec, j < k.
 cudaError_t launch_gs_total(const float* gS, int k, int rec, float* out, cudaStream_t st);
 
+// R^-1 of an upper triangular R (lp x lp, lp a multiple of 16 up to 256, the identity
+// beyond l); block substitution, lp / 16 CTAs.
+cudaError_t launch_trinv_upper(const float* r, int l, int lp, float* rinv, cudaStream_t st);
+
+// Row ID (k_id.cu).  launch_id_pivot: Businger--Golub pivoting on the rows of res (m x lp,
+// ld lp, overwritten by the residuals), l steps, one cooperative launch of `grid` CTAs
+// (at most one per SM); coef (m x lp, zeroed by the caller) gets the coefficients of each
+// row on the pivot directions, piv the l pivots in order (-1 from the step at which no
+// row is left: ST_NUMERICAL); cand: id_cand_floats(grid, lp) floats; bar: one counter,
+// zeroed by the caller.  launch_id_lt: Lt = C[J]^T (upper).  launch_gather_rows_t: out
+// (n x lp) = A[J, :]^T for A float32 (0), bfloat16 (1), bfloat16 hi + lo (2).
+cudaError_t launch_id_pivot(float* res, int64_t m, int l, int lp, float* coef, int* piv, float* cand,
+                            unsigned* bar, uint32_t* status, int grid, cudaStream_t st);
+size_t id_cand_floats(int grid, int lp);
+cudaError_t launch_id_lt(const float* coef, const int* piv, int l, int lp, float* lt, cudaStream_t st);
+cudaError_t launch_transpose_square(const float* src, int lp, float* dst, cudaStream_t st);
+cudaError_t launch_gather_rows_t(int adt, const void* A, int64_t lda, int64_t m, int64_t n, const int* piv,
+                                 int l, int lp, float* out, cudaStream_t st);
+
 // Hermitian Stage B helpers: B <- (B + B^T) / 2 on the leading l x l (ld lp); eigenvalues
 // from the SVD Ut S W^T of a symmetric matrix (mode 0: s_i sign(u_i . w_i)) or the squares
 // s_i^2 (mode 1, the Nystrom factor's), k of them.
