@@ -89,3 +89,58 @@ def sketch_fft(a: np.ndarray, signs: np.ndarray, freqs: np.ndarray) -> np.ndarra
     out[:, 0::2] = yc.real
     out[:, 1::2] = yc.imag
     return out
+
+
+# ---- the modified SRFT with chains of random Givens rotations (Section 4.6, eq. random_Givens)
+#
+# Omega = D'' Theta' D' Theta (sqrt(n / l_c) D F R): the SRFT above with an orthogonal
+# factor on the left, Theta = Pi G(1, 2; t_1) G(2, 3; t_2) ... G(n-1, n; t_{n-1}).
+# Readings: the rotations are real (A is real; D, D', D'' are +-1 like D) with the
+# convention of the cited Golub--Van Loan section, G(i, j; t) = I except
+# [[c, s], [-s, c]] in rows and columns (i, j), c = cos t, s = sin t; Pi is the
+# permutation (Pi x)_t = x_perm[t]; the scale sqrt(n / l_c) of the SRFT is kept (the
+# remark leaves it out; a scale does not change the range).
+# Draws (Philox4x32-10, stream 2, word i mod 4 of counter (i div 4, row, 2, 0)):
+#   row 2: d'_i (top bit set: -1)     row 3: d''_i
+#   row 4: keys of Pi: perm lists 0..n-1 by ascending (key, index)
+#   row 5: t_i = 2 pi u_i, u_i = (word >> 8) 2^-24, for the rotation in plane (i, i+1)
+#   rows 6, 7: the same for Pi', t'.
+
+def gsrft_draw(seed: int, n: int):
+    """Return (d1, d2 (n,) +-1, perm1, perm2 (n,) int64, theta1, theta2 (n - 1,) angles)."""
+    def signs(row):
+        return np.where(_words(seed, row, n) >> np.uint32(31), -1.0, 1.0)
+
+    def perm(row):
+        keys = _words(seed, row, n).astype(np.int64)
+        return np.lexsort((np.arange(n), keys))
+
+    def angles(row):
+        u = (_words(seed, row, n - 1) >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
+        return 2.0 * np.pi * u
+
+    return signs(2), signs(3), perm(4), perm(6), angles(5), angles(7)
+
+
+def givens_chain(theta: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """G(1, 2; t_1) ... G(n-1, n; t_{n-1}) x for x (n,) or (n, cols): the rightmost
+    rotation acts first."""
+    y = np.array(x, dtype=np.float64, copy=True)
+    for i in range(len(theta) - 1, -1, -1):
+        c, s = np.cos(theta[i]), np.sin(theta[i])
+        yi, yj = y[i].copy(), y[i + 1].copy()
+        y[i] = c * yi + s * yj
+        y[i + 1] = -s * yi + c * yj
+    return y
+
+
+def gsrft_omega_real(seed: int, n: int, lc: int) -> np.ndarray:
+    """n x 2 l_c real modified SRFT: D'' Theta' D' Theta applied to the columns of the
+    real SRFT of the same seed."""
+    d, f = draw(seed, n, lc)
+    d1, d2, p1, p2, t1, t2 = gsrft_draw(seed, n)
+    w = omega_real(d, f)
+    w = givens_chain(t1, w)[p1]          # Theta = Pi G(1, 2) ... G(n-1, n)
+    w = d1[:, None] * w                  # D'
+    w = givens_chain(t2, w)[p2]          # Theta'
+    return d2[:, None] * w               # D''

@@ -174,3 +174,17 @@ def test_untransposed_r_in_row_extraction_is_caught(monkeypatch):
 
     monkeypatch.setattr(row_extraction, "svd_row_extraction", bad)
     _fails(rpins.test_lemma_5_1_identity_and_bound)
+
+
+def test_givens_chain_in_the_wrong_order_is_caught(monkeypatch):
+    def bad(theta, x):
+        y = np.array(x, dtype=np.float64, copy=True)
+        for i in range(len(theta)):                      # leftmost rotation first
+            c, s = np.cos(theta[i]), np.sin(theta[i])
+            yi, yj = y[i].copy(), y[i + 1].copy()
+            y[i] = c * yi + s * yj
+            y[i + 1] = -s * yi + c * yj
+        return y
+
+    monkeypatch.setattr(srft, "givens_chain", bad)
+    _fails(pins.test_gsrft_against_the_dense_product)

@@ -433,3 +433,50 @@ def test_single_pass_wide_psi_on_the_noisy_tall_workload():
     e_l = rel(*single_pass.rsvd_single_pass(a, k, om, philox.gaussian(2003, 1, m, k + p))[:3])
     e_3l = rel(*single_pass.rsvd_single_pass(a, k, om, philox.gaussian(2003, 1, m, 3 * (k + p)))[:3])
     assert e_l > 1.0 and e_3l < 1.0 and e_q2 < e_3l
+
+
+def _dense_givens(n, i, t):
+    g = np.eye(n)
+    c, s = np.cos(t), np.sin(t)
+    g[i, i], g[i, i + 1], g[i + 1, i], g[i + 1, i + 1] = c, s, -s, c
+    return g
+
+
+def test_gsrft_against_the_dense_product():
+    """eq. random_Givens written out as dense matrices for n = 16: Omega = D'' Pi' G'..
+    D' Pi G.. D F R, every factor built on its own."""
+    n, lc = 16, 3
+    seed = 5
+    d, f = srft.draw(seed, n, lc)
+    d1, d2, p1, p2, t1, t2 = srft.gsrft_draw(seed, n)
+
+    def theta(p, t):
+        m = np.eye(n)[p]                  # (Pi x)_k = x_p[k]
+        for i in range(n - 1):
+            m = m @ _dense_givens(n, i, t[i])
+        return m
+
+    dense = np.diag(d2) @ theta(p2, t2) @ np.diag(d1) @ theta(p1, t1) @ srft.omega_real(d, f)
+    assert np.max(np.abs(srft.gsrft_omega_real(seed, n, lc) - dense)) <= 1e-14
+    # the draws: +-1 signs, permutations, angles in [0, 2 pi)
+    for x in (d1, d2):
+        assert set(np.unique(x)) <= {-1.0, 1.0}
+    for p in (p1, p2):
+        assert sorted(p.tolist()) == list(range(n))
+    assert np.all((t1 >= 0) & (t1 < 2 * np.pi)) and np.all((t2 >= 0) & (t2 < 2 * np.pi))
+
+
+def test_gsrft_columns_orthogonal_and_random():
+    """The left factor is orthogonal: Omega^T Omega = (n / (2 l_c)) I as for the real SRFT;
+    the factors differ between seeds and are not the identity."""
+    n, lc = 512, 20
+    om = srft.gsrft_omega_real(11, n, lc)
+    assert np.max(np.abs(om.T @ om - n / (2 * lc) * np.eye(2 * lc))) <= 1e-11
+    d, f = srft.draw(11, n, lc)
+    assert np.max(np.abs(om - srft.omega_real(d, f))) > 0.1
+    _, _, p1, _, t1, _ = srft.gsrft_draw(11, n)
+    _, _, q1, _, u1, _ = srft.gsrft_draw(12, n)
+    assert not np.array_equal(p1, q1) and not np.allclose(t1, u1)
+    # angles spread over the circle (a Kolmogorov-Smirnov distance far below 1)
+    u = np.sort(t1 / (2 * np.pi))
+    assert np.max(np.abs(u - (np.arange(1, n) - 0.5) / (n - 1))) < 0.1
