@@ -569,11 +569,66 @@ def _rel_err(A, U, S, V):
     return (num / den) ** 0.5
 
 
+# Table 7.1 of the paper (seconds on its 2009 desktop, double precision, one execution):
+# the gauss (Algorithm 4.1, Gaussian Omega, then Algorithm 5.1) and srft (Algorithm 4.1
+# with the modified SRFT, then Algorithm 5.2) columns, by n and l.  Context only.
+PAPER_TABLE_7_1_S = {
+    1024: {10: (5.63e-2, 9.06e-2), 20: (9.69e-2, 1.03e-1), 40: (1.84e-1, 1.27e-1),
+           80: (4.00e-1, 2.19e-1), 160: (9.92e-1, 6.92e-1)},
+    2048: {10: (2.16e-1, 3.56e-1), 20: (3.69e-1, 3.89e-1), 40: (6.69e-1, 4.33e-1),
+           80: (1.43e0, 6.64e-1), 160: (3.36e0, 1.61e0)},
+    4096: {10: (8.94e-1, 1.45e0), 20: (1.44e0, 1.53e0), 40: (2.64e0, 1.63e0),
+           80: (5.43e0, 2.08e0), 160: (1.16e1, 3.94e0)},
+}
+
+
+def run_table_7_1(pkg, steps, warmup):
+    """The timing experiment of Section 7.4 on this GPU: the l leading singular triplets
+    of an n x n Gaussian matrix (k = l, p = 0, q = 0), gauss = Gaussian Omega + Algorithm
+    5.1 (rsvd_svd), srft = the modified SRFT + Algorithm 5.2 (rsvd_svd_row_extraction),
+    each on the float32 path and the bfloat16 tensor-core path.  The library takes
+    l <= 256: the table's l = 320, 640, 1280 rows are outside it; l = 256 is added."""
+    import torch
+
+    rows = []
+    g = torch.Generator(device="cuda")
+    for n in (1024, 2048, 4096):
+        g.manual_seed(7100 + n)
+        A32 = torch.randn(n, n, device="cuda", generator=g)
+        Ab = A32.to(torch.bfloat16)
+        nrm = float(torch.linalg.matrix_norm(A32.double()))
+        for l in (10, 20, 40, 80, 160, 256):
+            row = {"n": n, "l": l}
+            for prec, A in ((pkg.RSVD_PLAIN_FP32, A32), (pkg.RSVD_BF16_TC, Ab)):
+                tag = "fp32" if prec == pkg.RSVD_PLAIN_FP32 else "bf16_tc"
+                for method, tm in (("gauss", pkg.RSVD_GAUSSIAN), ("srft", pkg.RSVD_GSRFT)):
+                    with pkg.Plan(n, n, l, 0, 0, 7200 + l, prec, test_matrix=tm) as pl:
+                        U = torch.empty(n, l, device="cuda")
+                        S = torch.empty(l, device="cuda")
+                        V = torch.empty(n, l, device="cuda")
+                        fn = ((lambda: pkg.rsvd_svd(pl.handle, A, U, S, V)) if method == "gauss" else
+                              (lambda: pkg.rsvd_svd_row_extraction(pl.handle, A, U, S, V)))
+                        ms = _events_ms(fn, steps, warmup)
+                        pkg._check(pkg.rsvd_sync(pl.handle), "table 7.1 run")
+                        err = float(torch.linalg.matrix_norm(A32.double() - (U.double() * S.double()) @ V.double().T))
+                    row[f"{method}_{tag}_ms"] = round(ms, 4)
+                    row[f"{method}_{tag}_rel_err_F"] = round(err / nrm, 5)
+            paper = PAPER_TABLE_7_1_S.get(n, {}).get(l)
+            if paper:
+                row["paper_gauss_s"], row["paper_srft_s"] = paper
+            rows.append(row)
+        del A32, Ab
+    return {"metric": "l leading singular triplets of an n x n Gaussian matrix, ms per execution",
+            "config": {"k": "l", "p": 0, "q": 0, "matrix": "iid N(0, 1), seeded on the device"},
+            "results": rows}
+
+
 def run_workload(args):
     """Secondary workloads (one JSON line each; not the headline metric):
     c3 -- 262144 x 4096, single-pass (Section 5.5) vs q = 2 multi-pass, k = 64, p = 16;
     c4 -- 32768 x 32768, SRFT (Section 4.6) vs Gaussian test matrix, k = 236, p = 20, q = 1;
-    c5 -- 512 matrices m ~ U[128, 2048], n ~ U[64, 1024], batched forward and backward."""
+    c5 -- 512 matrices m ~ U[128, 2048], n ~ U[64, 1024], batched forward and backward;
+    t71 -- the Section 7.4 timing sweep (Table 7.1) with gauss and the modified SRFT."""
     import torch
 
     import __graft_entry__
@@ -623,6 +678,8 @@ def run_workload(args):
                              "stages_ms": {k2: round(v, 4) for k2, v in stage_ms.items()}}
         out.update({"metric": "rank-k rSVD ms per matrix (bf16 tensor cores)",
                     "config": {"m": w.m, "n": w.n, "k": w.k, "p": w.p}, "results": res})
+    elif args.workload == "t71":
+        out.update(run_table_7_1(pkg, steps, warmup))
     elif args.workload == "c5":
         shapes = synth.c5_shapes()
         if args.profile_run and os.path.exists(cache):
@@ -715,8 +772,9 @@ def main():
                     help="three launches of the tensor-core pass kernel (each mode) on an 8192 x 16384 "
                          "A stored as bf16 hi + lo (537 MB, larger than L2): the small case for "
                          "full ncu captures")
-    ap.add_argument("--workload", choices=("c2", "c3", "c4", "c5"), default="c2",
-                    help="c2 (default) is the headline line; c3/c4/c5 print one secondary line each")
+    ap.add_argument("--workload", choices=("c2", "c3", "c4", "c5", "t71"), default="c2",
+                    help="c2 (default) is the headline line; c3/c4/c5 print one secondary line "
+                         "each; t71 is the timing experiment of Section 7.4 (Table 7.1)")
     args = ap.parse_args()
     if args.workload != "c2" and args.impl == "ours":
         run_workload(args)

@@ -62,7 +62,7 @@ typedef enum {
  * residual lo = bf16(A - hi), as rsvd_convert_a writes them; the final pass B^T = A^T Q
  * reads both (about 16 significant bits), and with residual_passes = 1 every pass does. */
 enum { RSVD_F32 = 0, RSVD_BF16 = 1, RSVD_BF16X2 = 2 };
-enum { RSVD_GAUSSIAN = 0, RSVD_SRFT = 1 };            /* test matrix (Section 4.1 / 4.6) */
+enum { RSVD_GAUSSIAN = 0, RSVD_SRFT = 1, RSVD_GSRFT = 2 };  /* test matrix (Section 4.1 / 4.6) */
 enum { RSVD_PLAIN_FP32 = 0, RSVD_BF16_TC = 1 };       /* how the passes over A are computed */
 
 typedef struct {
@@ -71,7 +71,11 @@ typedef struct {
                            random +-1 signs D, the unitary DFT F and l_c = l / 2 frequencies
                            from {1 .. n/2 - 1} without replacement; for a real A the l real
                            columns are [Re, Im] of each sampled frequency.  Needs l and n
-                           even and n < 2^24 */
+                           even and n < 2^24.  RSVD_GSRFT: the modified SRFT of Section 4.6
+                           (eq. random_Givens), D'' Theta' D' Theta times that SRFT, Theta =
+                           Pi G(1,2; t_1) ... G(n-1,n; t_{n-1}) a random permutation after a
+                           chain of random real Givens rotations, D', D'' random signs; the
+                           same size rules */
   int32_t precision;    /* RSVD_PLAIN_FP32: float32 A, float32 FMA on CUDA cores.
                            RSVD_BF16_TC: bfloat16 A (RSVD_BF16 or RSVD_BF16X2), tcgen05
                            tensor-core products with float32 accumulation, float32

@@ -27,7 +27,7 @@ RSVD_ERR_TIMEOUT = 6
 RSVD_ERR_UNSUPPORTED = 7
 
 RSVD_F32, RSVD_BF16, RSVD_BF16X2 = 0, 1, 2
-RSVD_GAUSSIAN, RSVD_SRFT = 0, 1
+RSVD_GAUSSIAN, RSVD_SRFT, RSVD_GSRFT = 0, 1, 2
 RSVD_PLAIN_FP32, RSVD_BF16_TC = 0, 1
 RSVD_SMALL_AUTO, RSVD_SMALL_ONE_CTA, RSVD_SMALL_CLUSTER = 0, 1, 2
 RSVD_EIG_DIRECT, RSVD_EIG_NYSTROM = 0, 1

@@ -52,6 +52,7 @@ struct rsvd_plan_s {
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
+  int* gsrft_perm = nullptr; // the two permutations of the modified SRFT (2 n)
   uint32_t* srft_signs = nullptr;  // n bits: the signs d_j of the SRFT (row-transform sketch)
   uint32_t* status = nullptr;
   // backward tape: R^-1 of every Cholesky-QR round of Stage A (always: the factorisation
@@ -159,7 +160,7 @@ void free_plan(rsvd_plan_t P) {
     }
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
-                  P->v_dev, P->srft_freq, P->psi, P->sig2, P->rimg, P->a_f32,
+                  P->v_dev, P->srft_freq, P->gsrft_perm, P->psi, P->sig2, P->rimg, P->a_f32,
                   P->tape_r, P->tape_q, P->tape_qt, P->bw, P->srft_signs, P->ad, P->re};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -230,6 +231,14 @@ rsvd_status_t step_draw(rsvd_plan_t P, bool want_bf16) {
   if (!P->omega_user && P->opt.test_matrix == RSVD_SRFT) {
     TRY(launch_draw_srft(P->seed, P->n, P->l / 2, P->lp, P->srft_freq, P->omega, P->lp,
                          want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
+  } else if (!P->omega_user && P->opt.test_matrix == RSVD_GSRFT) {
+    // the SRFT, then its orthogonal left factor D'' Theta' D' Theta (qtbuf as scratch)
+    sp.launched(want_bf16 ? 5 : 4);
+    TRY(launch_draw_srft(P->seed, P->n, P->l / 2, P->lp, P->srft_freq, P->omega, P->lp, nullptr, 0,
+                         P->st));
+    TRY(launch_gsrft_apply(P->seed, P->n, 2 * (P->l / 2), P->lp, P->gsrft_perm, P->omega, P->qtbuf,
+                           P->lp, P->st));
+    if (want_bf16) TRY(launch_to_bf16_t(P->omega, P->n, P->lp, P->xbf, tc_ld(P->n), 0, 0, P->st));
   } else if (!P->omega_user) {
     TRY(launch_draw_gaussian(P->seed, 0u, P->n, P->l, P->lp, P->omega, P->lp,
                              want_bf16 ? P->xbf : nullptr, tc_ld(P->n), P->st));
@@ -970,9 +979,11 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
-  if (o.test_matrix != RSVD_GAUSSIAN && o.test_matrix != RSVD_SRFT) return RSVD_ERR_INVALID_ARG;
+  if (o.test_matrix != RSVD_GAUSSIAN && o.test_matrix != RSVD_SRFT && o.test_matrix != RSVD_GSRFT)
+    return RSVD_ERR_INVALID_ARG;
+  const bool srft = o.test_matrix == RSVD_SRFT || o.test_matrix == RSVD_GSRFT;
   // SRFT: l real columns are l / 2 frequencies from {1 .. n/2 - 1} (Section 4.6 for real A)
-  if (o.test_matrix == RSVD_SRFT &&
+  if (srft &&
       ((l & 1) || (n & 1) || l / 2 > n / 2 - 1 || n >= ((int64_t)1 << 24)))
     return RSVD_ERR_INVALID_ARG;
   if (o.small_svd < 0 || o.small_svd > 2) return RSVD_ERR_INVALID_ARG;
@@ -1043,7 +1054,8 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (o.single_pass && (s = dalloc(P, &P->psi, (size_t)m * P->lpp)) != RSVD_OK) ||
       (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lq)) != RSVD_OK) ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
-      (o.test_matrix == RSVD_SRFT && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
+      (srft && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
+      (o.test_matrix == RSVD_GSRFT && (s = dalloc(P, &P->gsrft_perm, (size_t)(2 * n))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
     free_plan(P);
     return s;
@@ -1076,8 +1088,9 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     P->tc.status = P->status;
     P->tc2.status = P->status;
   }
-  if (o.test_matrix == RSVD_SRFT &&
-      launch_srft_select(seed, n, (int)(l / 2), P->srft_freq, P->st) != cudaSuccess) {
+  if (srft && (launch_srft_select(seed, n, (int)(l / 2), P->srft_freq, P->st) != cudaSuccess ||
+               (o.test_matrix == RSVD_GSRFT &&
+                launch_gsrft_perms(seed, n, P->gsrft_perm, P->st) != cudaSuccess))) {
     cudaGetLastError();
     free_plan(P);
     return RSVD_ERR_CUDA;

@@ -16,6 +16,8 @@
 // Draws (Philox4x32-10, stream 2): d_i is the top bit of word i mod 4 of counter
 // (i / 4, 0, 2, 0); candidate b has key word b mod 4 of counter (b / 4, 1, 2, 0);
 // the l_c candidates with the smallest (key, b) are taken in ascending order.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "philox.cuh"
@@ -93,7 +95,101 @@ __global__ void srft_omega_kernel(uint2 key, int64_t n, int lc, int cols_pad,
   }
 }
 
+// ---- the modified SRFT (Section 4.6, eq. random_Givens): Omega_G = D'' Theta' D' Theta
+// Omega with Omega the SRFT above and Theta = Pi G(1, 2; t_1) ... G(n-1, n; t_{n-1}),
+// G(i, i+1; t) = [[c, s], [-s, c]] in rows/columns (i, i+1), (Pi x)_k = x_perm[k].
+// Draws on stream 2: rows 2, 3 signs d', d''; rows 4, 6 the keys of Pi, Pi' (perm lists
+// the indices by ascending (key, index)); rows 5, 7 the angles, t_i = 2 pi u_i with
+// u_i = (word >> 8) 2^-24.
+
+// rank of (key_j, j) among all n pairs = the position of j in the permutation.  Each
+// thread ranks one index against the keys, staged 2048 at a time in shared memory.
+constexpr int kRankTile = 2048;
+
+__global__ void __launch_bounds__(256) gsrft_perm_kernel(uint2 key, int64_t n, uint32_t row,
+                                                         int* __restrict__ perm) {
+  __shared__ uint32_t ks[kRankTile];
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t kj = j < n ? srft_word(key, row, (uint64_t)j) : 0u;
+  int64_t rank = 0;
+  for (int64_t t0 = 0; t0 < n; t0 += kRankTile) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kRankTile; e += blockDim.x)
+      if (t0 + e < n) ks[e] = srft_word(key, row, (uint64_t)(t0 + e));
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kRankTile, n - t0);
+    if (j < n) {
+      for (int e = 0; e < cnt; ++e) {
+        const uint32_t k = ks[e];
+        rank += (k < kj) || (k == kj && t0 + e < j);
+      }
+    }
+  }
+  if (j < n) perm[rank] = (int)j;
+}
+
+// The Givens chain G(1, 2; t_1) ... G(n-1, n; t_{n-1}) on the columns c < ncols of buf
+// (n x ld), in place, one thread per column: the rightmost rotation first, so the running
+// value of row i + 1 is carried down the chain in a register.
+__global__ void __launch_bounds__(32) gsrft_chain_kernel(uint2 key, int64_t n, uint32_t row,
+                                                         float* __restrict__ buf, int64_t ld,
+                                                         int ncols) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  if (c >= ncols) return;
+  float carry = buf[(n - 1) * ld + c];
+  for (int64_t i = n - 2; i >= 0; --i) {
+    const float u = (float)(srft_word(key, row, (uint64_t)i) >> 8) * 5.9604644775390625e-08f;
+    float sn, cs;
+    sincospif(2.0f * u, &sn, &cs);
+    const float vi = buf[i * ld + c];
+    buf[(i + 1) * ld + c] = fmaf(-sn, vi, cs * carry);
+    carry = fmaf(cs, vi, sn * carry);
+  }
+  buf[c] = carry;
+}
+
+// dst[k][c] = d_k src[perm[k]][c] for c < ncols (d from the sign row), zero for
+// ncols <= c < cols_pad.
+__global__ void gsrft_permute_kernel(uint2 key, int64_t n, uint32_t sign_row, const int* __restrict__ perm,
+                                     const float* __restrict__ src, float* __restrict__ dst, int64_t ld,
+                                     int ncols, int cols_pad) {
+  const int64_t total = n * cols_pad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / cols_pad;
+    const int c = (int)(e % cols_pad);
+    float v = 0.0f;
+    if (c < ncols) {
+      v = src[(int64_t)perm[k] * ld + c];
+      if (srft_word(key, sign_row, (uint64_t)k) >> 31) v = -v;
+    }
+    dst[k * ld + c] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gsrft_perms(uint64_t seed, int64_t n, int* perm, cudaStream_t st) {
+  if (n < 2 || n >= (int64_t)1 << 24) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)cdiv(n, 256);
+  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 4u, perm);
+  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 6u, perm + n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* perm,
+                               float* omega, float* scratch, int64_t ld, cudaStream_t st) {
+  if (n < 2 || ncols < 1 || ncols > cols_pad || cols_pad > ld) return cudaErrorInvalidValue;
+  const uint2 key = seed_key(seed);
+  const unsigned gc = (unsigned)cdiv(ncols, 32);
+  const int64_t total = n * cols_pad;
+  const unsigned gp = (unsigned)std::min<int64_t>(cdiv(total, 256), 16 * kNumSMs);
+  gsrft_chain_kernel<<<gc, 32, 0, st>>>(key, n, 5u, omega, ld, ncols);                 // G chain
+  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 2u, perm, omega, scratch, ld, ncols, cols_pad);  // D' Pi
+  gsrft_chain_kernel<<<gc, 32, 0, st>>>(key, n, 7u, scratch, ld, ncols);               // G' chain
+  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 3u, perm + n, scratch, omega, ld, ncols, cols_pad);  // D'' Pi'
+  return cudaGetLastError();
+}
 
 cudaError_t launch_srft_select(uint64_t seed, int64_t n, int lc, int* freq, cudaStream_t st) {
   if (n < 4 || (n & 1) || lc < 1 || lc > n / 2 - 1 || lc > kSelThreads) return cudaErrorInvalidValue;

@@ -96,6 +96,14 @@ cudaError_t launch_draw_srft(uint64_t seed, int64_t n, int lc, int cols_pad, con
                              float* out, int64_t ld, __nv_bfloat16* out_t, int64_t ld_t,
                              cudaStream_t st);
 
+// The modified SRFT (Section 4.6, eq. random_Givens): launch_gsrft_perms writes the
+// permutations Pi, Pi' (2 n ints) once per plan; launch_gsrft_apply turns the SRFT in
+// omega (n x cols_pad, ld, columns >= ncols zero) into D'' Theta' D' Theta omega in place
+// (scratch: n x ld floats).
+cudaError_t launch_gsrft_perms(uint64_t seed, int64_t n, int* perm, cudaStream_t st);
+cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* perm,
+                               float* omega, float* scratch, int64_t ld, cudaStream_t st);
+
 // The SRFT sketch as a transform along the rows of A (k_srft_fft.cu): y (m x ldy) gets
 // [Re, Im] of l_c^-1/2 sum_j a_j d_j exp(-2 pi i j b_c / n) in columns 2c, 2c + 1 and zeros
 // up to ldy.  adt: A float32 (0), bfloat16 (1), bfloat16 hi + lo (2, lo m rows further);

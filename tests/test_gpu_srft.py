@@ -129,3 +129,62 @@ def test_srft_row_transform_is_the_plans_first_pass(rsvd_lib):
         pkg.rsvd_set_omega(pl.handle, om)
         Q2 = pl.range_finder(A)
     assert torch.max(torch.abs(Q1 - Q2)).item() <= 1e-4
+
+
+# ---- the modified SRFT (Section 4.6, eq. random_Givens)
+#
+# The two Givens chains carry one running value down n - 1 rotations each, so float32
+# rounding accumulates like a random walk: |Omega_gpu - Omega_ref| <= 16 u sqrt(2 n) of
+# the largest entry (u = 2^-24; the angles are float32 sincospi of exactly representable
+# arguments).  The permutations and signs are integer decisions: a wrong one is an O(1)
+# error.
+
+@pytest.mark.parametrize("n,l,seed", [(64, 8, 5), (1024, 80, 3), (4096, 160, 9), (2050, 256, 1)])
+def test_gsrft_omega_matches_oracle(rsvd_lib, n, l, seed):
+    pkg = rsvd_lib
+    with pkg.Plan(l + 8, n, l - 2, 2, 0, seed, test_matrix=pkg.RSVD_GSRFT) as pl:
+        om = torch.zeros(n, l, device="cuda")
+        pkg.rsvd_get_omega(pl.handle, om)
+        assert pkg.rsvd_sync(pl.handle) == pkg.RSVD_OK
+    got = _np(om)
+    ref = srft.gsrft_omega_real(seed, n, l // 2)
+    tol = 16 * 2.0 ** -24 * np.sqrt(2 * n) * np.abs(ref).max()
+    err = np.max(np.abs(got - ref))
+    print(f"GSRFT n={n} l={l}: max error {err:.2e} (tolerance {tol:.2e})")
+    assert err <= tol
+    assert np.allclose(got.T @ got, np.eye(l) * n / l, atol=2e-4 * n / l)
+
+
+@pytest.mark.parametrize("m,n,k,p,q,prec", [(700, 512, 20, 12, 1, 0), (1024, 1024, 80, 0, 0, 0),
+                                            (1500, 2048, 100, 28, 1, 1)])
+def test_gsrft_rsvd_matches_oracle(rsvd_lib, m, n, k, p, q, prec):
+    """The whole randomized SVD with the modified SRFT (plain path: the float32 targets
+    against the oracle run with the oracle's Omega; tensor-core path: the reconstruction
+    error within 1e-3 of the oracle's, as the bfloat16 operands move it by design)."""
+    import synth
+
+    pkg = rsvd_lib
+    a, *_ = synth.lowrank(m, n, synth.spectrum_power(min(m, n), 0.5), m + 5 * n)
+    a32 = a.astype(np.float32)
+    seed = 41
+    l = k + p
+    omega = srft.gsrft_omega_real(seed, n, l // 2)
+    tc = prec == pkg.RSVD_BF16_TC
+    with pkg.Plan(m, n, k, p, q, seed, prec, test_matrix=pkg.RSVD_GSRFT) as pl:
+        A = _dev(a32)
+        if tc:
+            A = A.to(torch.bfloat16)
+        U, S, V = pl.svd(A)
+        torch.cuda.synchronize()
+    u, s, v = _np(U), _np(S), _np(V)
+    a64 = (A.float().cpu().numpy() if tc else a32).astype(np.float64)
+    if not tc:
+        _check_svd(a64, u, s, v, k, p, q, omega)
+    else:
+        from oracle import rsvd64
+
+        ur, sr, vr, _ = rsvd64.rsvd(a64, k, p, q, omega)
+        e_ref = metrics.fro_error_onepass(a64, ur, sr, vr)
+        e_gpu = metrics.fro_error_onepass(a64, u, s, v)
+        assert abs(e_gpu - e_ref) <= 1e-3 * e_ref
+    assert metrics.orthonormality(u) <= 2e-5 and metrics.orthonormality(v) <= 2e-5
