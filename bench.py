@@ -610,6 +610,13 @@ def run_table_7_1(pkg, steps, warmup):
                               (lambda: pkg.rsvd_svd_row_extraction(pl.handle, A, U, S, V)))
                         ms = _events_ms(fn, steps, warmup)
                         pkg._check(pkg.rsvd_sync(pl.handle), "table 7.1 run")
+                        if tag == "bf16_tc":
+                            pkg.rsvd_profile(pl.handle, (1 << pkg.RSVD_NUM_STEPS) - 1)
+                            fn()
+                            torch.cuda.synchronize()
+                            stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
+                            pkg.rsvd_profile(pl.handle, 0)
+                            row[f"{method}_{tag}_stages_ms"] = {k2: round(v, 3) for k2, v in stage_ms.items() if v > 0}
                         err = float(torch.linalg.matrix_norm(A32.double() - (U.double() * S.double()) @ V.double().T))
                     row[f"{method}_{tag}_ms"] = round(ms, 4)
                     row[f"{method}_{tag}_rel_err_F"] = round(err / nrm, 5)

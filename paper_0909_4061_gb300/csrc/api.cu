@@ -52,7 +52,7 @@ struct rsvd_plan_s {
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
-  int* gsrft_perm = nullptr; // the two permutations of the modified SRFT (2 n)
+  int* gsrft_perm = nullptr; // the modified SRFT's permutations and rotations (6 n)
   uint32_t* srft_signs = nullptr;  // n bits: the signs d_j of the SRFT (row-transform sketch)
   uint32_t* status = nullptr;
   // backward tape: R^-1 of every Cholesky-QR round of Stage A (always: the factorisation
@@ -1055,7 +1055,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
       (o.single_pass && (s = dalloc(P, &P->sig2, (size_t)2 * lq)) != RSVD_OK) ||
       (s = dalloc(P, &P->sig, (size_t)lp)) != RSVD_OK ||
       (srft && (s = dalloc(P, &P->srft_freq, (size_t)(l / 2))) != RSVD_OK) ||
-      (o.test_matrix == RSVD_GSRFT && (s = dalloc(P, &P->gsrft_perm, (size_t)(2 * n))) != RSVD_OK) ||
+      (o.test_matrix == RSVD_GSRFT && (s = dalloc(P, &P->gsrft_perm, gsrft_table_ints(n))) != RSVD_OK) ||
       (s = dalloc(P, &P->status, 4))) {
     free_plan(P);
     return s;
@@ -1090,7 +1090,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   }
   if (srft && (launch_srft_select(seed, n, (int)(l / 2), P->srft_freq, P->st) != cudaSuccess ||
                (o.test_matrix == RSVD_GSRFT &&
-                launch_gsrft_perms(seed, n, P->gsrft_perm, P->st) != cudaSuccess))) {
+                launch_gsrft_prepare(seed, n, P->gsrft_perm, P->st) != cudaSuccess))) {
     cudaGetLastError();
     free_plan(P);
     return RSVD_ERR_CUDA;

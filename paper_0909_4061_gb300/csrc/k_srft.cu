@@ -128,24 +128,68 @@ __global__ void __launch_bounds__(256) gsrft_perm_kernel(uint2 key, int64_t n, u
   if (j < n) perm[rank] = (int)j;
 }
 
-// The Givens chain G(1, 2; t_1) ... G(n-1, n; t_{n-1}) on the columns c < ncols of buf
-// (n x ld), in place, one thread per column: the rightmost rotation first, so the running
-// value of row i + 1 is carried down the chain in a register.
-__global__ void __launch_bounds__(32) gsrft_chain_kernel(uint2 key, int64_t n, uint32_t row,
-                                                         float* __restrict__ buf, int64_t ld,
-                                                         int ncols) {
-  const int c = blockIdx.x * 32 + threadIdx.x;
-  if (c >= ncols) return;
-  float carry = buf[(n - 1) * ld + c];
-  for (int64_t i = n - 2; i >= 0; --i) {
-    const float u = (float)(srft_word(key, row, (uint64_t)i) >> 8) * 5.9604644775390625e-08f;
-    float sn, cs;
-    sincospif(2.0f * u, &sn, &cs);
-    const float vi = buf[i * ld + c];
-    buf[(i + 1) * ld + c] = fmaf(-sn, vi, cs * carry);
-    carry = fmaf(cs, vi, sn * carry);
+// cos / sin of the rotation angles of both chains, once per plan: cs[chain][i] for the
+// rotation in plane (i, i + 1), i < n - 1 (float32 sincospi of the exactly representable
+// 2 u_i).
+__global__ void gsrft_angles_kernel(uint2 key, int64_t n, float2* __restrict__ cs) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * (n - 1);
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int chain = (int)(e / (n - 1));
+    const int64_t i = e % (n - 1);
+    const float u = (float)(srft_word(key, chain ? 7u : 5u, (uint64_t)i) >> 8) * 5.9604644775390625e-08f;
+    float sn, cn;
+    sincospif(2.0f * u, &sn, &cn);
+    cs[chain * n + i] = make_float2(cn, sn);
   }
-  buf[c] = carry;
+}
+
+// dst = G(1, 2; t_1) ... G(n-1, n; t_{n-1}) src on the columns c < ncols (n x ld), the
+// rightmost rotation first.  Rotation i maps the running value r of row i + 1 and v_i to
+//   dst_{i+1} = -s_i v_i + c_i r,   r <- c_i v_i + s_i r,
+// a first-order linear recurrence, so the chain is split into 32 segments of rotations,
+// one warp each (lane = column: coalesced rows).  Pass 1: every segment's map of its
+// incoming running value, r_out = alpha r_in + beta.  Then warp 0 carries the true value
+// from the top (r = src_{n-1}) down the segments, and pass 2 recomputes each segment with
+// its incoming value and writes its rows.
+constexpr int kChainSeg = 32;
+
+__global__ void __launch_bounds__(32 * kChainSeg) gsrft_chain_kernel(
+    int64_t n, const float2* __restrict__ cs, const float* __restrict__ src, float* __restrict__ dst,
+    int64_t ld, int ncols) {
+  __shared__ float s_alpha[kChainSeg][32], s_beta[kChainSeg][32], s_in[kChainSeg][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const bool live = c < ncols;
+  const int64_t nrot = n - 1, seg = cdiv(nrot, kChainSeg);
+  const int64_t a = min(nrot, (int64_t)w * seg), b = min(nrot, a + seg);
+  float alpha = 1.0f, beta = 0.0f;
+#pragma unroll 4
+  for (int64_t i = b - 1; i >= a; --i) {
+    const float2 t = cs[i];
+    const float v = live ? src[i * ld + c] : 0.0f;
+    alpha *= t.y;
+    beta = fmaf(t.x, v, t.y * beta);
+  }
+  s_alpha[w][lane] = alpha;
+  s_beta[w][lane] = beta;
+  __syncthreads();
+  if (w == 0) {
+    float r = live ? src[(n - 1) * ld + c] : 0.0f;
+    for (int j = kChainSeg - 1; j >= 0; --j) {
+      s_in[j][lane] = r;
+      r = fmaf(s_alpha[j][lane], r, s_beta[j][lane]);
+    }
+  }
+  __syncthreads();
+  float r = s_in[w][lane];
+#pragma unroll 4
+  for (int64_t i = b - 1; i >= a; --i) {
+    const float2 t = cs[i];
+    const float v = live ? src[i * ld + c] : 0.0f;
+    if (live) dst[(i + 1) * ld + c] = fmaf(-t.y, v, t.x * r);
+    r = fmaf(t.x, v, t.y * r);
+  }
+  if (w == 0 && live) dst[c] = r;
 }
 
 // dst[k][c] = d_k src[perm[k]][c] for c < ncols (d from the sign row), zero for
@@ -169,25 +213,30 @@ __global__ void gsrft_permute_kernel(uint2 key, int64_t n, uint32_t sign_row, co
 
 }  // namespace
 
-cudaError_t launch_gsrft_perms(uint64_t seed, int64_t n, int* perm, cudaStream_t st) {
+cudaError_t launch_gsrft_prepare(uint64_t seed, int64_t n, int* tables, cudaStream_t st) {
   if (n < 2 || n >= (int64_t)1 << 24) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)cdiv(n, 256);
-  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 4u, perm);
-  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 6u, perm + n);
+  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 4u, tables);
+  gsrft_perm_kernel<<<grid, 256, 0, st>>>(seed_key(seed), n, 6u, tables + n);
+  gsrft_angles_kernel<<<(unsigned)std::min<int64_t>(cdiv(2 * n, 256), 16 * kNumSMs), 256, 0, st>>>(
+      seed_key(seed), n, reinterpret_cast<float2*>(tables + 2 * n));
   return cudaGetLastError();
 }
 
-cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* perm,
+size_t gsrft_table_ints(int64_t n) { return (size_t)6 * n; }
+
+cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* tables,
                                float* omega, float* scratch, int64_t ld, cudaStream_t st) {
   if (n < 2 || ncols < 1 || ncols > cols_pad || cols_pad > ld) return cudaErrorInvalidValue;
   const uint2 key = seed_key(seed);
   const unsigned gc = (unsigned)cdiv(ncols, 32);
   const int64_t total = n * cols_pad;
   const unsigned gp = (unsigned)std::min<int64_t>(cdiv(total, 256), 16 * kNumSMs);
-  gsrft_chain_kernel<<<gc, 32, 0, st>>>(key, n, 5u, omega, ld, ncols);                 // G chain
-  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 2u, perm, omega, scratch, ld, ncols, cols_pad);  // D' Pi
-  gsrft_chain_kernel<<<gc, 32, 0, st>>>(key, n, 7u, scratch, ld, ncols);               // G' chain
-  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 3u, perm + n, scratch, omega, ld, ncols, cols_pad);  // D'' Pi'
+  const float2* cs = reinterpret_cast<const float2*>(tables + 2 * n);
+  gsrft_chain_kernel<<<gc, 32 * kChainSeg, 0, st>>>(n, cs, omega, scratch, ld, ncols);       // G chain
+  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 2u, tables, scratch, omega, ld, ncols, cols_pad);  // D' Pi
+  gsrft_chain_kernel<<<gc, 32 * kChainSeg, 0, st>>>(n, cs + n, omega, scratch, ld, ncols);  // G' chain
+  gsrft_permute_kernel<<<gp, 256, 0, st>>>(key, n, 3u, tables + n, scratch, omega, ld, ncols, cols_pad);  // D'' Pi'
   return cudaGetLastError();
 }
 

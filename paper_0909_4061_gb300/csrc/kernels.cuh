@@ -96,12 +96,14 @@ cudaError_t launch_draw_srft(uint64_t seed, int64_t n, int lc, int cols_pad, con
                              float* out, int64_t ld, __nv_bfloat16* out_t, int64_t ld_t,
                              cudaStream_t st);
 
-// The modified SRFT (Section 4.6, eq. random_Givens): launch_gsrft_perms writes the
-// permutations Pi, Pi' (2 n ints) once per plan; launch_gsrft_apply turns the SRFT in
-// omega (n x cols_pad, ld, columns >= ncols zero) into D'' Theta' D' Theta omega in place
-// (scratch: n x ld floats).
-cudaError_t launch_gsrft_perms(uint64_t seed, int64_t n, int* perm, cudaStream_t st);
-cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* perm,
+// The modified SRFT (Section 4.6, eq. random_Givens): launch_gsrft_prepare writes, once
+// per plan, the tables (gsrft_table_ints(n) ints): the permutations Pi, Pi' and the
+// cos / sin of both rotation chains; launch_gsrft_apply turns the SRFT in omega (n x
+// cols_pad, ld, columns >= ncols zero) into D'' Theta' D' Theta omega in place (scratch:
+// n x ld floats).
+cudaError_t launch_gsrft_prepare(uint64_t seed, int64_t n, int* tables, cudaStream_t st);
+size_t gsrft_table_ints(int64_t n);
+cudaError_t launch_gsrft_apply(uint64_t seed, int64_t n, int ncols, int cols_pad, const int* tables,
                                float* omega, float* scratch, int64_t ld, cudaStream_t st);
 
 // The SRFT sketch as a transform along the rows of A (k_srft_fft.cu): y (m x ldy) gets
