@@ -64,12 +64,16 @@ struct rsvd_batched_plan_s {
   int kr = 0;                     // 32 (2q + 2) columns of the low-rank factors of dL/dA
   float* lbuf = nullptr;          // sum_m x kr
   float* rbuf = nullptr;          // sum_n x kr
+  __nv_bfloat16* lplanes = nullptr;  // 3 x sum_m x kr: the bfloat16 split of lbuf (h, m, t)
+  __nv_bfloat16* rplanes = nullptr;  // 3 x sum_n x kr
+  alignas(64) unsigned char map_lp[128];  // tensor maps of the planes (box 64 x 128)
+  alignas(64) unsigned char map_rp[128];
   float* gm = nullptr;            // sum_m x LP
   float* pm = nullptr;            // sum_m x LP
   float* gn = nullptr;            // sum_n x LP
   float* nmat = nullptr;          // nb x LP x LP
   float* rinv = nullptr;          // nb x LP x LP
-  int4* d_units_f = nullptr;      // (b, 64-row tile, 64-column tile) of dL/dA
+  int4* d_units_f = nullptr;      // (b, row tile, column tile) of dL/dA, bwd_final_tile() square
   int nunits_f = 0;
   int64_t* d_lda = nullptr;
   const void** d_aptr = nullptr;
@@ -383,8 +387,10 @@ rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* cons
   BTRYS(qr_back(P, P->qm[0], P->gm, P->rm[0], true, P->pm));                     // dY_0
   BTRY(launch_copy_block(P->pm, P->sum_m, P->lbuf, kr, blk * LP, P->st));
   BTRY(launch_copy_block(P->omega, P->sum_n, P->rbuf, kr, blk * LP, P->st));
-  BTRY(launch_bwd_final(P->d_units_f, P->nunits_f, P->d_aptr, P->d_lda, P->d_gptr, P->d_m, P->d_n,
-                        P->d_roff_m, P->d_roff_n, P->lbuf, P->rbuf, kr, P->st));
+  BTRY(launch_bwd_split(P->lbuf, P->sum_m * kr, P->lplanes, P->st));
+  BTRY(launch_bwd_split(P->rbuf, P->sum_n * kr, P->rplanes, P->st));
+  BTRY(launch_bwd_final(P->map_lp, P->map_rp, P->d_maps, P->d_units_f, P->nunits_f, P->sum_m, P->sum_n, kr,
+                        P->d_gptr, P->d_m, P->d_n, P->d_roff_m, P->d_roff_n, P->num_sms, P->status, P->st));
   return RSVD_OK;
 }
 
@@ -462,7 +468,7 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      prepare_batched() != cudaSuccess) {
+      prepare_batched() != cudaSuccess || prepare_batched_bwd() != cudaSuccess) {
     cudaGetLastError();
     delete P;
     return RSVD_ERR_CUDA;
@@ -512,13 +518,16 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   P->kr = kBatchedLP * (2 * q + 2);
   {
     std::vector<int4> uf;
+    const int ft = bwd_final_tile();
     for (int b = 0; b < batch; ++b)
-      for (int64_t rt = 0; rt < cdiv(m[b], 64); ++rt)
-        for (int64_t ct = 0; ct < cdiv(n[b], 64); ++ct) uf.push_back(make_int4(b, (int)rt, (int)ct, 0));
+      for (int64_t rt = 0; rt < cdiv(m[b], ft); ++rt)
+        for (int64_t ct = 0; ct < cdiv(n[b], ft); ++ct) uf.push_back(make_int4(b, (int)rt, (int)ct, 0));
     P->nunits_f = (int)uf.size();
     if ((s = upload(P, &P->d_units_f, uf)) != RSVD_OK || (s = upload(P, &P->d_lda, P->lda)) != RSVD_OK ||
         (s = balloc(P, &P->lbuf, (size_t)P->sum_m * P->kr)) != RSVD_OK ||
         (s = balloc(P, &P->rbuf, (size_t)P->sum_n * P->kr)) != RSVD_OK ||
+        (s = balloc(P, &P->lplanes, (size_t)3 * P->sum_m * P->kr)) != RSVD_OK ||
+        (s = balloc(P, &P->rplanes, (size_t)3 * P->sum_n * P->kr)) != RSVD_OK ||
         (s = balloc(P, &P->gm, (size_t)P->sum_m * LP)) != RSVD_OK ||
         (s = balloc(P, &P->pm, (size_t)P->sum_m * LP)) != RSVD_OK ||
         (s = balloc(P, &P->gn, (size_t)P->sum_n * LP)) != RSVD_OK ||
@@ -550,6 +559,8 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
       tc_encode_2d(P->map_x_n, P->xbf, P->xn_total, LP, ldx, 64, LP) ||
       tc_encode_2d(P->map_x_m2, P->xbf, P->xm_total, 2 * LP, ldx, 64, 2 * LP) ||
       tc_encode_2d(P->map_x_n2, P->xbf, P->xn_total, 2 * LP, ldx, 64, 2 * LP) ||
+      tc_encode_2d(P->map_lp, P->lplanes, P->kr, 3 * P->sum_m, P->kr, 64, bwd_final_tile()) ||
+      tc_encode_2d(P->map_rp, P->rplanes, P->kr, 3 * P->sum_n, P->kr, 64, bwd_final_tile()) ||
       cudaMemsetAsync(P->xbf, 0, sizeof(__nv_bfloat16) * 2 * LP * ldx, P->st) != cudaSuccess ||
       cudaMemsetAsync(P->status, 0, 4 * sizeof(uint32_t), P->st) != cudaSuccess) {
     cudaGetLastError();

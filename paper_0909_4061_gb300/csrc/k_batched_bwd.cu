@@ -18,11 +18,16 @@
 // So dL/dA = 2 A + L R^T with L = [U (I - 2S) | dY_q | Q_{q-1} | ... | dY_0] and
 // R = [V | Qt_q | dZ_q | ... | Omega]: q + 1 ... passes over A for A V and the chain,
 // then one kernel that reads A and writes dL/dA.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "kernels_batched.cuh"
+#include "tc_ptx.cuh"
 
 namespace rsvd {
 namespace {
+
+using namespace tcx;
 
 constexpr int LPB = 32;
 
@@ -182,57 +187,214 @@ __global__ void copy_block_kernel(const float* __restrict__ src, int64_t rows, f
   }
 }
 
-// gA_b[r][c] = 2 A_b[r][c] + sum_t L[rm_b + r][t] R[rn_b + c][t] on a 64 x 64 tile per CTA;
-// 256 threads, 4 x 4 outputs each, K in chunks of 32 through shared memory
-constexpr int FT = 64;
+// x -> three bfloat16 planes h = bf16(x), m = bf16(x - h), t = bf16(x - h - m) (x to 24
+// significant bits), planes [3][rows][kr], for the tensor-core form of dL/dA.
+__global__ void bwd_split_kernel(const float* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ planes) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[e];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 mm = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 t = __float2bfloat16_rn(r1 - __bfloat162float(mm));
+    planes[e] = h;
+    planes[n + e] = mm;
+    planes[2 * n + e] = t;
+  }
+}
 
-__global__ void __launch_bounds__(256) bwd_final_kernel(
-    const int4* __restrict__ units, const void* const* __restrict__ A, const int64_t* __restrict__ lda,
-    float* const* __restrict__ gA, const int64_t* __restrict__ m, const int64_t* __restrict__ n,
-    const int64_t* __restrict__ roff_m, const int64_t* __restrict__ roff_n, const float* __restrict__ L,
-    const float* __restrict__ R, int kr) {
-  __shared__ float Ls[32][FT + 4];   // Ls[t][row]
-  __shared__ float Rs[32][FT + 4];   // Rs[t][col]
-  const int4 u = units[blockIdx.x];
-  const int b = u.x;
-  const int64_t mb = m[b], nbc = n[b];
-  const int64_t rt0 = (int64_t)u.y * FT, ct0 = (int64_t)u.z * FT;
-  const float* Lb = L + roff_m[b] * kr;
-  const float* Rb = R + roff_n[b] * kr;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4] = {};
-  for (int t0 = 0; t0 < kr; t0 += 32) {
-    __syncthreads();
-    for (int e = tid; e < FT * 32; e += 256) {
-      const int rr = e >> 5, t = e & 31;
-      const int64_t gr = rt0 + rr, gc = ct0 + rr;
-      Ls[t][rr] = gr < mb ? Lb[gr * kr + t0 + t] : 0.0f;
-      Rs[t][rr] = gc < nbc ? Rb[gc * kr + t0 + t] : 0.0f;
+// dL/dA on the tensor cores: gA_b = 2 A_b + L_b R_b^T for 128 x 128 tiles (units: matrix,
+// row tile, column tile; dealt round-robin to persistent CTAs).  The MMA forms the tile
+// transposed, D = R L^T (tensor-memory lane = column of dL/dA, tensor-memory column = row),
+// so that a warp holds 32 adjacent columns of one row in its 32 lanes: A is read and dL/dA
+// written in coalesced rows straight from the accumulator.  L and R come as three bfloat16
+// planes each; per k16 step six products (t h, h t, m m, m h, h m, h h, the small ones
+// first) accumulate in float32, which carries L R^T to about 2^-22 of |L| |R|.  Warp 0
+// loads the six 128 x 64 plane tiles of a k chunk by TMA (two stages of 96 KB) and the
+// unit's tile of A (32 KB, after the previous unit's epilogue has read it), warp 1 issues
+// the MMAs into a double-buffered accumulator, warps 2-5 write 2 A + D^T.
+constexpr int kFT = 128;                                     // tile rows and columns
+constexpr int kFinalThreads = 192;
+constexpr uint32_t kPlaneTile = (uint32_t)kFT * 64 * 2;      // 128 rows x 64 k, bf16
+constexpr uint32_t kFinalStage = 6 * kPlaneTile;             // 96 KB
+constexpr int kFinalStages = 2;
+constexpr uint32_t kATile = (uint32_t)kFT * kFT * 2;         // 32 KB: two 64-column boxes
+constexpr size_t kFinalSmem = (size_t)kFinalStages * kFinalStage + kATile + 1024;
+
+__global__ void __launch_bounds__(kFinalThreads, 1) bwd_final_tc_kernel(
+    const __grid_constant__ CUtensorMap map_l, const __grid_constant__ CUtensorMap map_r,
+    const CUtensorMap* __restrict__ maps_a, const int4* __restrict__ units, int nunits, int64_t sum_m,
+    int64_t sum_n, int kr, float* const* __restrict__ gA, const int64_t* __restrict__ m,
+    const int64_t* __restrict__ n, const int64_t* __restrict__ roff_m, const int64_t* __restrict__ roff_n,
+    uint32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_full[kFinalStages], bar_empty[kFinalStages], bar_acc_full[2], bar_acc_empty[2];
+  __shared__ uint64_t bar_a_full, bar_a_empty;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = smem + kFinalStages * kFinalStage;
+  constexpr uint32_t acc_cols = kFT, tmem_cols = 2 * kFT;
+  const int kc = kr / 64;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFinalStages; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-      const float4 lv = *reinterpret_cast<const float4*>(&Ls[t][ty * 4]);
-      const float4 rv = *reinterpret_cast<const float4*>(&Rs[t][tx * 4]);
-      const float la[4] = {lv.x, lv.y, lv.z, lv.w}, ra[4] = {rv.x, rv.y, rv.z, rv.w};
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&bar_acc_full[a], 1);
+      mbar_init(&bar_acc_empty[a], 4);
+    }
+    mbar_init(&bar_a_full, 1);
+    mbar_init(&bar_a_empty, 4);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t i = 0;
+      int j = 0;
+      int a_loads = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++j) {
+        const int4 un = units[u];
+        const int yl = (int)(roff_m[un.x] + (int64_t)un.y * kFT);
+        const int yr = (int)(roff_n[un.x] + (int64_t)un.z * kFT);
+        for (int kk = 0; kk < kc; ++kk, ++i) {
+          const int s = (int)(i % kFinalStages);
+          const uint32_t ph = (uint32_t)((i / kFinalStages) & 1);
+          if (!mbar_wait(&bar_empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
+          uint8_t* sa = smem + (size_t)s * kFinalStage;
+          mbar_expect_tx(&bar_full[s], kFinalStage);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+          for (int p = 0; p < 3; ++p) {   // MMA A operand: R (columns of dL/dA); B operand: L
+            tma_load_2d(sa + p * kPlaneTile, &map_r, &bar_full[s], kk * 64, (int)(p * sum_n) + yr);
+            tma_load_2d(sa + (3 + p) * kPlaneTile, &map_l, &bar_full[s], kk * 64, (int)(p * sum_m) + yl);
+          }
+        }
+        if (!ok) break;
+        // the tile of A once the previous unit's epilogue is done with the buffer
+        if (!mbar_wait(&bar_a_empty, ((uint32_t)j & 1u) ^ 1u, abort_flag, status)) break;
+        const CUtensorMap* ma = maps_a + un.x;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(ma))
+                     : "memory");
+        mbar_expect_tx(&bar_a_full, kATile);
+        tma_load_2d(sA, ma, &bar_a_full, un.z * kFT, un.y * kFT);
+        tma_load_2d(sA + kATile / 2, ma, &bar_a_full, un.z * kFT + 64, un.y * kFT);
+        ++a_loads;
+      }
+      // let the copies in flight land before the CTA can exit
+      const int64_t issued = i;
+      for (int64_t t = (issued > kFinalStages ? issued - kFinalStages : 0); t < issued; ++t) {
+        const int s = (int)(t % kFinalStages);
+        const uint32_t ph = (uint32_t)((t / kFinalStages) & 1);
+        for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(&bar_full[s], ph); ++w) __nanosleep(64);
+      }
+      if (a_loads > 0) {
+        const uint32_t ph = (uint32_t)((a_loads - 1) & 1);
+        for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(&bar_a_full, ph); ++w) __nanosleep(64);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(kFT, 0);
+      // (R plane, L plane): the smallest products first
+      constexpr int pa[6] = {2, 0, 1, 1, 0, 0};
+      constexpr int pb[6] = {0, 2, 1, 0, 1, 0};
+      int64_t i = 0;
+      int j = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++j) {
+        const int ab = j & 1;
+        if (!mbar_wait(&bar_acc_empty[ab], ((uint32_t)(j >> 1) & 1u) ^ 1u, abort_flag, status)) break;
+        tc_fence_after();
+        const uint32_t dst = tmem + ab * acc_cols;
+        for (int kk = 0; kk < kc; ++kk, ++i) {
+          const int s = (int)(i % kFinalStages);
+          const uint32_t ph = (uint32_t)((i / kFinalStages) & 1);
+          if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * kFinalStage);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(la[i], ra[j], acc[i][j]);
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+              const uint64_t adesc = smem_desc(sa + pa[t] * kPlaneTile + q * 32, 16, 1024);
+              const uint64_t bdesc = smem_desc(sa + (3 + pb[t]) * kPlaneTile + q * 32, 16, 1024);
+              mma_bf16(dst, adesc, bdesc, idesc, (kk == 0 && q == 0 && t == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(&bar_empty[s]);
+        }
+        if (ok) mma_commit(&bar_acc_full[ab]);
+      }
+    }
+  } else {
+    const int quad = warp & 3;            // the tensor-memory lane quarter this warp may read
+    const int cl = quad * 32 + lane;      // column of the tile
+    // the swizzled position of column cl in a 128-byte row of the A tile (two 64-column boxes)
+    const uint32_t box_off = (uint32_t)(cl >> 6) * (kATile / 2);
+    const int chunk16 = (cl & 63) >> 3, within = (cl & 7) * 2;
+    int j = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++j) {
+      const int4 un = units[u];
+      const int ab = j & 1;
+      bool ok = mbar_wait(&bar_acc_full[ab], (uint32_t)(j >> 1) & 1u, abort_flag, status);
+      ok = ok && mbar_wait(&bar_a_full, (uint32_t)j & 1u, abort_flag, status);
+      ok = __all_sync(0xffffffffu, ok);
+      tc_fence_after();
+      if (ok) {
+        const int b = un.x;
+        const int64_t mb = m[b], nb = n[b];
+        const int64_t rbase = (int64_t)un.y * kFT, c = (int64_t)un.z * kFT + cl;
+        float* __restrict__ G = gA[b];
+        for (int c0 = 0; c0 < kFT && rbase + c0 < mb; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ab * acc_cols + c0 + ((uint32_t)(quad * 32) << 16), v);
+          if (c < nb) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const int rl = c0 + t;
+              const int64_t r = rbase + rl;
+              const uint32_t off = box_off + (uint32_t)rl * 128 + (uint32_t)((chunk16 ^ (rl & 7)) << 4) + within;
+              const float a = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + off));
+              if (r < mb) G[r * nb + c] = fmaf(2.0f, a, v[t]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bar_a_empty);
+        mbar_arrive(&bar_acc_empty[ab]);
+      }
+      if (!ok) break;
     }
   }
-  const __nv_bfloat16* Ab = static_cast<const __nv_bfloat16*>(A[b]);
-  float* G = gA[b];
-  const int64_t ld = lda[b];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t r = rt0 + ty * 4 + i;
-    if (r >= mb) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t c = ct0 + tx * 4 + j;
-      if (c < nbc) G[r * nbc + c] = fmaf(2.0f, __bfloat162float(Ab[r * ld + c]), acc[i][j]);
-    }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
   }
 }
 
@@ -270,12 +432,31 @@ cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ld
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_final(const int4* units, int nunits, const void* const* A, const int64_t* lda,
-                             float* const* gA, const int64_t* m, const int64_t* n,
-                             const int64_t* roff_m, const int64_t* roff_n, const float* L,
-                             const float* R, int kr, cudaStream_t st) {
+cudaError_t launch_bwd_split(const float* x, int64_t n, __nv_bfloat16* planes, cudaStream_t st) {
+  const int64_t blocks = cdiv(n, 256);
+  bwd_split_kernel<<<(unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs), 256, 0, st>>>(x, n, planes);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_batched_bwd() {
+  return cudaFuncSetAttribute(bwd_final_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kFinalSmem);
+}
+
+int bwd_final_tile() { return kFT; }
+
+cudaError_t launch_bwd_final(const void* map_l, const void* map_r, const void* maps_a, const int4* units,
+                             int nunits, int64_t sum_m, int64_t sum_n, int kr, float* const* gA,
+                             const int64_t* m, const int64_t* n, const int64_t* roff_m, const int64_t* roff_n,
+                             int grid, uint32_t* status, cudaStream_t st) {
   if (nunits <= 0) return cudaSuccess;
-  bwd_final_kernel<<<nunits, 256, 0, st>>>(units, A, lda, gA, m, n, roff_m, roff_n, L, R, kr);
+  if (kr % 64 || kr <= 0 || 3 * (sum_m > sum_n ? sum_m : sum_n) >= ((int64_t)1 << 31))
+    return cudaErrorInvalidValue;
+  if (grid > nunits) grid = nunits;
+  bwd_final_tc_kernel<<<grid, kFinalThreads, kFinalSmem, st>>>(
+      *static_cast<const CUtensorMap*>(map_l), *static_cast<const CUtensorMap*>(map_r),
+      static_cast<const CUtensorMap*>(maps_a), units, nunits, sum_m, sum_n, kr, gA, m, n, roff_m, roff_n,
+      status);
   return cudaGetLastError();
 }
 

@@ -58,10 +58,19 @@ cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* 
 // dst[r][col0 + c] = src[r][c] (rows x 32 -> ld ldd)
 cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
                               cudaStream_t st);
-// gA_b = 2 A_b + L_b R_b^T over tiles (b, 64-row tile, 64-column tile)
-cudaError_t launch_bwd_final(const int4* units, int nunits, const void* const* A, const int64_t* lda,
-                             float* const* gA, const int64_t* m, const int64_t* n,
-                             const int64_t* roff_m, const int64_t* roff_n, const float* L,
-                             const float* R, int kr, cudaStream_t st);
+// planes [3][n] = the three-way bfloat16 split of x (n floats): h, m, t with
+// x = h + m + t to 24 significant bits.
+cudaError_t launch_bwd_split(const float* x, int64_t n, __nv_bfloat16* planes, cudaStream_t st);
+cudaError_t prepare_batched_bwd();
+int bwd_final_tile();   // rows and columns of a unit of launch_bwd_final
+// gA_b = 2 A_b + L_b R_b^T on the tensor cores over units (b, row tile, column tile) of
+// bwd_final_tile() x bwd_final_tile(); map_l / map_r: host addresses of the tensor maps of
+// the split planes of L (3 sum_m rows of kr bf16) and R (3 sum_n rows), box 64 x 128;
+// maps_a: device array of the per-matrix tensor maps of A_b (box 64 columns x 128 rows);
+// kr a multiple of 64; grid: persistent CTAs (one per SM).
+cudaError_t launch_bwd_final(const void* map_l, const void* map_r, const void* maps_a, const int4* units,
+                             int nunits, int64_t sum_m, int64_t sum_n, int kr, float* const* gA,
+                             const int64_t* m, const int64_t* n, const int64_t* roff_m, const int64_t* roff_n,
+                             int grid, uint32_t* status, cudaStream_t st);
 
 }  // namespace rsvd
