@@ -31,43 +31,95 @@ using namespace tcx;
 
 constexpr int LPB = 32;
 
-// one CTA per matrix (Ut, sigma in shared memory), one warp per row: lane c forms
-// t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u_c = (Q Ut)[r][c]; lane i then
-// gQ[r][i] = sum_{c<k} t_c Ut[i][c]
-__global__ void __launch_bounds__(256) bwd_gq_kernel(const float* __restrict__ P,
-                                                     const float* __restrict__ Q,
-                                                     const int64_t* __restrict__ roff,
-                                                     const float* __restrict__ ut,
-                                                     const float* __restrict__ sig, int k,
-                                                     float* __restrict__ gq, float* __restrict__ ublk,
-                                                     int ldu) {
-  __shared__ float Us[LPB][LPB + 1];
+// Row kernels of the backward: a block of kRowBlock consecutive rows of the concatenated
+// row arrays (they may span several matrices), one thread per row.  The block stages its
+// rows in shared memory (coalesced loads, rows padded to 33 floats), then for each matrix
+// it meets loads that matrix's small factors into shared memory (read by all threads at
+// the same address: broadcasts) and the threads whose rows belong to it do 2 x 32 x 32
+// FMAs in registers; results leave through the same staging buffer, coalesced.
+constexpr int kRowBlock = 128;
+
+__device__ __forceinline__ int row_matrix(const int64_t* __restrict__ off, int nb, int64_t r) {
+  int lo = 0, hi = nb - 1;   // the largest b with off[b] <= r
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// rows (total x 32, ld 32) -> smem [kRowBlock][33] for the block's rows (zero past the end)
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t r0, int64_t total,
+                                           float (*dst)[LPB + 1]) {
+  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
+    const int rr = e >> 5, c = e & 31;
+    dst[rr][c] = r0 + rr < total ? src[(r0 + rr) * LPB + c] : 0.0f;
+  }
+}
+
+// t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u = Q[r] Ut; gQ[r][i] = sum_{c<k} t_c Ut[i][c];
+// ublk[r][c] = u_c (1 - 2 s_c) for c < k, zero beyond (the first left factor U (I - 2S)).
+__global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restrict__ P,
+                                                           const float* __restrict__ Q,
+                                                           const int64_t* __restrict__ roff, int nb,
+                                                           int64_t total, const float* __restrict__ ut,
+                                                           const float* __restrict__ sig, int k,
+                                                           float* __restrict__ gq, float* __restrict__ ublk,
+                                                           int ldu) {
+  __shared__ float qs[kRowBlock][LPB + 1];
+  __shared__ float ps[kRowBlock][LPB + 1];
+  __shared__ float Us[LPB][LPB];
   __shared__ float ss[LPB];
-  const int b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) Us[e / LPB][e % LPB] = ut[(size_t)b * LPB * LPB + e];
-  if (threadIdx.x < LPB) ss[threadIdx.x] = threadIdx.x < k ? sig[(size_t)b * LPB + threadIdx.x] : 0.0f;
+  const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
+  const int rr = threadIdx.x;
+  const int64_t r = r0 + rr;
+  stage_rows(Q, r0, total, qs);
+  stage_rows(P, r0, total, ps);
+  const int b0 = row_matrix(roff, nb, r0);
+  const int b1 = row_matrix(roff, nb, min(r0 + kRowBlock, total) - 1);
+  float g[LPB], uo[LPB];
+  for (int b = b0; b <= b1; ++b) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) Us[e >> 5][e & 31] = ut[(size_t)b * LPB * LPB + e];
+    if (threadIdx.x < LPB) ss[threadIdx.x] = threadIdx.x < k ? sig[(size_t)b * LPB + threadIdx.x] : 0.0f;
+    __syncthreads();
+    if (r < total && r >= roff[b] && r < roff[b + 1]) {
+      float t[LPB];
+#pragma unroll
+      for (int c = 0; c < LPB; ++c) t[c] = 0.0f;
+#pragma unroll 4
+      for (int j = 0; j < LPB; ++j) {
+        const float qj = qs[rr][j];
+#pragma unroll
+        for (int c = 0; c < LPB; ++c) t[c] = fmaf(qj, Us[j][c], t[c]);   // u_c
+      }
+#pragma unroll
+      for (int c = 0; c < LPB; ++c) {
+        const float s = ss[c], c1 = 1.0f - 2.0f * s;
+        uo[c] = c < k ? t[c] * c1 : 0.0f;
+        t[c] = c < k ? fmaf(ps[rr][c], c1, 2.0f * s * s * t[c]) : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < LPB; ++i) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < LPB; ++c) acc = fmaf(t[c], Us[i][c], acc);
+        g[i] = acc;
+      }
+    }
+  }
   __syncthreads();
-  const float s = ss[lane];
-  const float c1 = 1.0f - 2.0f * s, c2 = 2.0f * s * s;
-  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
-    const float qv = Q[r * LPB + lane];
-    float u0 = 0.0f, u1 = 0.0f;
+  if (r < total) {
 #pragma unroll
-    for (int j = 0; j < LPB; j += 2) {
-      u0 = fmaf(__shfl_sync(0xffffffffu, qv, j), Us[j][lane], u0);
-      u1 = fmaf(__shfl_sync(0xffffffffu, qv, j + 1), Us[j + 1][lane], u1);
+    for (int i = 0; i < LPB; ++i) { qs[rr][i] = g[i]; ps[rr][i] = uo[i]; }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
+    const int q = e >> 5, c = e & 31;
+    if (r0 + q < total) {
+      gq[(r0 + q) * LPB + c] = qs[q][c];
+      ublk[(r0 + q) * ldu + c] = ps[q][c];
     }
-    const float u = u0 + u1;
-    const float t = lane < k ? fmaf(P[r * LPB + lane], c1, c2 * u) : 0.0f;
-    ublk[r * ldu + lane] = lane < k ? u * c1 : 0.0f;
-    float g0 = 0.0f, g1 = 0.0f;
-#pragma unroll
-    for (int c = 0; c < LPB; c += 2) {   // t_c = 0 for c >= k
-      g0 = fmaf(__shfl_sync(0xffffffffu, t, c), Us[lane][c], g0);
-      g1 = fmaf(__shfl_sync(0xffffffffu, t, c + 1), Us[lane][c + 1], g1);
-    }
-    gq[r * LPB + lane] = g0 + g1;
   }
 }
 
@@ -140,39 +192,61 @@ __global__ void __launch_bounds__(kSmallThreads) bwd_qr_small_kernel(
   }
 }
 
-// one CTA per matrix (N, R^-1 in shared memory), one warp per row: lane j:
-// w_j = gQ[r][j] + sum_t Q[r][t] N[t][j]; lane i: gY[r][i] = sum_j w_j Rinv[i][j] (gY = w R^-T)
-__global__ void __launch_bounds__(256) bwd_qr_apply_kernel(const float* __restrict__ Q,
-                                                           const float* __restrict__ gQ,
-                                                           const int64_t* __restrict__ roff,
-                                                           const float* __restrict__ N,
-                                                           const float* __restrict__ Rinv,
-                                                           float* __restrict__ gY) {
-  __shared__ float Ns[LPB][LPB + 1];
-  __shared__ float Rs[LPB][LPB + 1];
-  const int b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
-    Ns[e / LPB][e % LPB] = N[(size_t)b * LPB * LPB + e];
-    Rs[e / LPB][e % LPB] = Rinv[(size_t)b * LPB * LPB + e];
+// gY = (gQ + Q N) R^-T per row: w_j = gQ[r][j] + sum_t Q[r][t] N[t][j];
+// gY[r][i] = sum_j w_j Rinv[i][j]; one thread per row (see bwd_gq_kernel).
+__global__ void __launch_bounds__(kRowBlock) bwd_qr_apply_kernel(const float* __restrict__ Q,
+                                                                 const float* __restrict__ gQ,
+                                                                 const int64_t* __restrict__ roff, int nb,
+                                                                 int64_t total, const float* __restrict__ N,
+                                                                 const float* __restrict__ Rinv,
+                                                                 float* __restrict__ gY) {
+  __shared__ float qs[kRowBlock][LPB + 1];
+  __shared__ float gs[kRowBlock][LPB + 1];
+  __shared__ float Ns[LPB][LPB];
+  __shared__ float Rs[LPB][LPB];
+  const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
+  const int rr = threadIdx.x;
+  const int64_t r = r0 + rr;
+  stage_rows(Q, r0, total, qs);
+  stage_rows(gQ, r0, total, gs);
+  const int b0 = row_matrix(roff, nb, r0);
+  const int b1 = row_matrix(roff, nb, min(r0 + kRowBlock, total) - 1);
+  float g[LPB];
+  for (int b = b0; b <= b1; ++b) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
+      Ns[e >> 5][e & 31] = N[(size_t)b * LPB * LPB + e];
+      Rs[e >> 5][e & 31] = Rinv[(size_t)b * LPB * LPB + e];
+    }
+    __syncthreads();
+    if (r < total && r >= roff[b] && r < roff[b + 1]) {
+      float w[LPB];
+#pragma unroll
+      for (int j = 0; j < LPB; ++j) w[j] = gs[rr][j];
+#pragma unroll 4
+      for (int t = 0; t < LPB; ++t) {
+        const float qt = qs[rr][t];
+#pragma unroll
+        for (int j = 0; j < LPB; ++j) w[j] = fmaf(qt, Ns[t][j], w[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < LPB; ++i) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < LPB; ++j) acc = fmaf(w[j], Rs[i][j], acc);
+        g[i] = acc;
+      }
+    }
   }
   __syncthreads();
-  for (int64_t r = roff[b] + warp; r < roff[b + 1]; r += blockDim.x >> 5) {
-    const float qv = Q[r * LPB + lane];
-    float w0 = gQ[r * LPB + lane], w1 = 0.0f;
+  if (r < total) {
 #pragma unroll
-    for (int t = 0; t < LPB; t += 2) {
-      w0 = fmaf(__shfl_sync(0xffffffffu, qv, t), Ns[t][lane], w0);
-      w1 = fmaf(__shfl_sync(0xffffffffu, qv, t + 1), Ns[t + 1][lane], w1);
-    }
-    const float w = w0 + w1;
-    float g0 = 0.0f, g1 = 0.0f;
-#pragma unroll
-    for (int j = 0; j < LPB; j += 2) {
-      g0 = fmaf(__shfl_sync(0xffffffffu, w, j), Rs[lane][j], g0);
-      g1 = fmaf(__shfl_sync(0xffffffffu, w, j + 1), Rs[lane][j + 1], g1);
-    }
-    gY[r * LPB + lane] = g0 + g1;
+    for (int i = 0; i < LPB; ++i) qs[rr][i] = g[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
+    const int q = e >> 5, c = e & 31;
+    if (r0 + q < total) gY[(r0 + q) * LPB + c] = qs[q][c];
   }
 }
 
@@ -403,8 +477,9 @@ __global__ void __launch_bounds__(kFinalThreads, 1) bwd_final_tc_kernel(
 cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
                           const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st) {
-  (void)total_rows;
-  bwd_gq_kernel<<<nb, 256, 0, st>>>(P, Q, roff, ut, sig, k, gq, ublk, ldu);
+  if (total_rows <= 0) return cudaSuccess;
+  bwd_gq_kernel<<<(unsigned)cdiv(total_rows, kRowBlock), kRowBlock, 0, st>>>(P, Q, roff, nb, total_rows, ut,
+                                                                            sig, k, gq, ublk, ldu);
   return cudaGetLastError();
 }
 
@@ -417,9 +492,9 @@ cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* 
 cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
                                 int64_t total_rows, const float* N, const float* Rinv, float* gY,
                                 cudaStream_t st) {
-  (void)nb;
-  (void)total_rows;
-  bwd_qr_apply_kernel<<<nb, 256, 0, st>>>(Q, gQ, roff, N, Rinv, gY);
+  if (total_rows <= 0) return cudaSuccess;
+  bwd_qr_apply_kernel<<<(unsigned)cdiv(total_rows, kRowBlock), kRowBlock, 0, st>>>(Q, gQ, roff, nb, total_rows,
+                                                                                  N, Rinv, gY);
   return cudaGetLastError();
 }
 
