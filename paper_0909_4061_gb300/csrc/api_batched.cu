@@ -38,6 +38,12 @@ struct rsvd_batched_plan_s {
   int2* d_units0 = nullptr;      // (b, row tile of m_b)
   int2* d_units1 = nullptr;      // (b, row tile of n_b)
   int nunits0 = 0, nunits1 = 0;
+  int2* d_qunits_m = nullptr;     // Cholesky-QR units (b, 128-row tile) in matrix order, m side
+  int2* d_qunits_n = nullptr;     // the same on the n side
+  int* d_ustart_m = nullptr;      // nb + 1: the first unit of each matrix
+  int* d_ustart_n = nullptr;
+  int nq_m = 0, nq_n = 0;
+  float* qpart = nullptr;         // max(nq_m, nq_n) x 32 x 32 Gram partials
   // tensor maps of A_b (mode 0 boxes, then mode 1 boxes), device copy + the bound pointers
   unsigned char* d_maps = nullptr;
   std::vector<unsigned char> h_maps;
@@ -140,6 +146,18 @@ rsvd_status_t upload(rsvd_batched_plan_t P, T** dst, const std::vector<T>& src) 
 }
 
 // units of a pass, heaviest first (largest K), so that the round-robin deal to CTAs balances
+// 128-row units of every matrix in matrix order and the first unit of each matrix
+std::vector<int2> make_qr_units(const std::vector<int64_t>& rows, std::vector<int>* ustart) {
+  std::vector<int2> u;
+  ustart->assign(rows.size() + 1, 0);
+  for (size_t b = 0; b < rows.size(); ++b) {
+    (*ustart)[b] = (int)u.size();
+    for (int64_t t = 0; t < cdiv(rows[b], 128); ++t) u.push_back(make_int2((int)b, (int)t));
+  }
+  (*ustart)[rows.size()] = (int)u.size();
+  return u;
+}
+
 std::vector<int2> make_units(const std::vector<int64_t>& rows, const std::vector<int64_t>& kext) {
   std::vector<int> order(rows.size());
   for (size_t b = 0; b < rows.size(); ++b) order[b] = (int)b;
@@ -325,21 +343,23 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRY(launch_batched_draw(P->seed, P->d_roff_n, P->nb, P->sum_n, P->l, P->omega, P->xbf, ldx,
                            P->d_xoff_n, P->st));
   BTRYS(bpass(P, 0, 0, P->ym));                                                  // Y_0 = A Omega
-  BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, rounds, P->rm[0], P->status, P->st));
+  BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, rounds, P->rm[0], P->rinv,
+                               P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status, P->st));
   for (int j = 1; j <= P->q; ++j) {
     BTRYS(to_operand(P, P->qm[j - 1], true, 1));
     BTRYS(bpass(P, 1, 1, P->yn));                                                // A^T Q_{j-1}
-    BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds, P->rn[j - 1],
-                               P->status, P->st));
+    BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds, P->rn[j - 1], P->rinv,
+                               P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
     BTRYS(to_operand(P, P->qn[j - 1], false, 1));
     BTRYS(bpass(P, 0, 1, P->ym));                                                // A Qt_j
-    BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, rounds, P->rm[j], P->status,
-                               P->st));
+    BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, rounds, P->rm[j], P->rinv,
+                               P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status, P->st));
   }
   float* Q = P->qm[P->q];
   BTRYS(to_operand(P, Q, true, 1));
   BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
-  BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->status, P->st));
+  BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->rinv,
+                               P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
   BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
   if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->max_m, P->ub, P->k, P->k, U, P->k, P->st));
   if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, P->k, P->k, V, P->k, P->st));
@@ -493,6 +513,10 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
   const std::vector<int2> u0 = make_units(P->m, P->n), u1 = make_units(P->n, P->m);
   P->nunits0 = (int)u0.size();
   P->nunits1 = (int)u1.size();
+  std::vector<int> us_m, us_n;
+  const std::vector<int2> qu_m = make_qr_units(P->m, &us_m), qu_n = make_qr_units(P->n, &us_n);
+  P->nq_m = (int)qu_m.size();
+  P->nq_n = (int)qu_n.size();
   P->h_maps.assign((size_t)2 * batch * 128, 0);
   P->a_bound.assign(batch, nullptr);
   const int64_t ldx = std::max(P->xm_total, P->xn_total);
@@ -501,6 +525,9 @@ rsvd_status_t rsvd_batched_plan_create(rsvd_batched_plan_t* plan, int32_t batch,
       (s = upload(P, &P->d_xoff_m, xoff_m)) != RSVD_OK || (s = upload(P, &P->d_xoff_n, xoff_n)) != RSVD_OK ||
       (s = upload(P, &P->d_m, P->m)) != RSVD_OK || (s = upload(P, &P->d_n, P->n)) != RSVD_OK ||
       (s = upload(P, &P->d_units0, u0)) != RSVD_OK || (s = upload(P, &P->d_units1, u1)) != RSVD_OK ||
+      (s = upload(P, &P->d_qunits_m, qu_m)) != RSVD_OK || (s = upload(P, &P->d_qunits_n, qu_n)) != RSVD_OK ||
+      (s = upload(P, &P->d_ustart_m, us_m)) != RSVD_OK || (s = upload(P, &P->d_ustart_n, us_n)) != RSVD_OK ||
+      (s = balloc(P, &P->qpart, (size_t)std::max(P->nq_m, P->nq_n) * LP * LP)) != RSVD_OK ||
       (s = balloc(P, &P->d_maps, P->h_maps.size())) != RSVD_OK ||
       (s = balloc(P, &P->xbf, (size_t)2 * LP * ldx)) != RSVD_OK ||
       (s = balloc(P, &P->omega, (size_t)P->sum_n * LP)) != RSVD_OK ||

@@ -16,9 +16,10 @@
 //                             accumulator in tensor memory.
 //   batched_draw_kernel     : Omega_b from seed + b (Philox, stream 0), rounded to
 //                             bfloat16: the transposed operand and its float32 copy.
-//   batched_cholqr_kernel   : one CTA per matrix: Cholesky-QR rounds (shifted first
-//                             round), the 32 x 32 factor and its inverse by one warp in
-//                             registers, the product of the R factors accumulated.
+//   bqr_*_kernel            : Cholesky-QR rounds over 128-row units of all matrices
+//                             (Gram partials, one CTA per matrix for the 32 x 32 factor,
+//                             its inverse and the product of the R factors, a thread per
+//                             row for the apply).
 //   batched_to_bf16t_kernel : basis -> transposed bfloat16 operand.
 //   batched_jacobi_kernel   : one CTA per matrix: one-sided Jacobi of an l x l matrix,
 //                             one warp per column pair, sorted outputs.
@@ -240,8 +241,6 @@ __global__ void batched_draw_kernel(uint64_t seed, const int64_t* __restrict__ r
 // ---------------------------------------------------------------------------
 // Cholesky QR, one CTA per matrix
 // ---------------------------------------------------------------------------
-constexpr int kQRThreads = 256;
-constexpr int kChunk = 64;   // rows staged per step
 
 // 32 x 32 Cholesky of S (+ shift, pivot floor) and inverse, by warp 0: lane r holds
 // row r of L (a) and column r of X = L^-1 (x); entries above the diagonal of a are
@@ -291,159 +290,164 @@ __device__ __forceinline__ void chol32_warp(const float (*S)[LPB + 1], int l, fl
   for (int i = 0; i < LPB; ++i) Xs[i][r] = x[i];
 }
 
-// Rows are streamed in chunks of 64 (two float4 per thread, the next chunk prefetched into
-// registers while the current one is used).  Gram: the 256 threads form 4 row groups of 64,
-// each thread a 4 x 4 block of G over its group's 16 rows of a chunk (float4 loads), the
-// four groups summed at the end in a fixed order.  Apply: a warp per row, column = lane,
-// the row of Y read as float4 and the column of R^-1 held in registers.
-__device__ __forceinline__ void load_chunk(const float* __restrict__ src, int64_t rows, int64_t c0,
-                                           int tid, float4 (&v)[2]) {
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int e = tid + u * kQRThreads;   // float4 index in the 64 x 32 chunk
+// Cholesky-QR over 128-row units (matrix b, tile t; units of one matrix are consecutive,
+// from ustart[b]): every step is one launch over all units of the batch, so the rows of
+// all matrices are worked on in parallel instead of one CTA streaming each matrix.
+//   bqr_gram_kernel  : the Gram of a unit's rows (staged in shared memory), a 32 x 32
+//                      partial per unit;
+//   bqr_chol_kernel  : one CTA per matrix: the sum of its units' partials in unit order
+//                      (deterministic), the factor and its inverse by one warp in
+//                      registers (shift on the first of three rounds, pivot floor), the
+//                      running product of the R factors, and R^-1 for the apply;
+//   bqr_apply_kernel : Q = Y R^-1 a thread per row, and the Gram partial of the new rows
+//                      for the next round.
+constexpr int kUnitRows = 128;
+constexpr int kUnitThreads = 256;
+
+__device__ __forceinline__ void bqr_stage(const float* __restrict__ src, int64_t row0, int nr,
+                                          float (*ys)[LPB]) {
+  for (int e = threadIdx.x; e < kUnitRows * (LPB / 4); e += blockDim.x) {
     const int rr = e >> 3;
-    v[u] = (c0 + rr < rows) ? reinterpret_cast<const float4*>(src + (c0 + rr) * LPB)[e & 7]
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(&ys[0][0])[e] =
+        rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
-__global__ void __launch_bounds__(kQRThreads) batched_cholqr_kernel(
-    const float* __restrict__ yin, float* __restrict__ qout, const int64_t* __restrict__ roff, int l,
-    int rounds, float* __restrict__ rout, uint32_t* status) {
-  __shared__ __align__(16) float buf[2 * kChunk * LPB];   // two row chunks, or the Gram partials
-  float (*chunk)[LPB] = reinterpret_cast<float (*)[LPB]>(buf);
-  float (*qch)[LPB] = reinterpret_cast<float (*)[LPB]>(buf + kChunk * LPB);
-  float (*Gp)[LPB * LPB] = reinterpret_cast<float (*)[LPB * LPB]>(buf);   // 4 row groups
+// Gram partial of the staged rows (256 threads): four row groups of 64 threads, each thread
+// a 4 x 4 block of G over its group's rows (two float4 reads per 16 FMAs), the groups
+// summed in a fixed order through gp (4 x 32 x 32 floats of shared memory).
+__device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, float (*gp)[LPB * LPB],
+                                              float* __restrict__ part) {
+  const int grp = threadIdx.x >> 6, gt = threadIdx.x & 63;
+  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int rr = grp; rr < nr; rr += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(&ys[rr][bi]);
+    const float4 c = *reinterpret_cast<const float4*>(&ys[rr][bj]);
+    const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gp[grp][(bi + i) * LPB + bj + j] = acc[i][j];
+  __syncthreads();
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x)
+    part[e] = (gp[0][e] + gp[1][e]) + (gp[2][e] + gp[3][e]);
+}
+
+__global__ void __launch_bounds__(kUnitThreads) bqr_gram_kernel(const float* __restrict__ src,
+                                                                const int64_t* __restrict__ roff,
+                                                                const int2* __restrict__ units,
+                                                                float* __restrict__ part) {
+  __shared__ __align__(16) float ys[kUnitRows][LPB];
+  __shared__ __align__(16) float gp[4][LPB * LPB];
+  const int2 u = units[blockIdx.x];
+  const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
+  const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
+  bqr_stage(src, row0, nr, ys);
+  __syncthreads();
+  bqr_gram_tile(ys, nr, gp, part + (size_t)blockIdx.x * LPB * LPB);
+}
+
+__global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__ part,
+                                                       const int* __restrict__ ustart, int l, float shift_on,
+                                                       int racc_init, float* __restrict__ racc,
+                                                       float* __restrict__ rinv, uint32_t* status) {
   __shared__ float S[LPB][LPB + 1];
   __shared__ float Ls[LPB][LPB + 1];
   __shared__ float Xs[LPB][LPB + 1];
-  __shared__ float Racc[LPB][LPB + 1];
-  __shared__ float Rtmp[LPB][LPB + 1];
+  __shared__ float Ro[LPB][LPB + 1];
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t r0 = roff[b], rows = roff[b + 1] - r0;
-  const float* Y = yin + r0 * LPB;
-  float* Q = qout + r0 * LPB;
-  const int grp = tid >> 6, gt = tid & 63;           // row group, thread in group
-  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;   // 4 x 4 block of G
-  float acc[4][4];
-  for (int e = tid; e < LPB * LPB; e += kQRThreads) Racc[e / LPB][e % LPB] = (e / LPB == e % LPB) ? 1.0f : 0.0f;
-
-  auto gram_chunk = [&](const float (*C)[LPB], int nr) {
-    for (int rr = grp; rr < nr; rr += 4) {
-      const float4 a = *reinterpret_cast<const float4*>(&C[rr][bi]);
-      const float4 c = *reinterpret_cast<const float4*>(&C[rr][bj]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+  // every thread sums its 8 entries over the matrix's units (the 8 loads of a unit in flight
+  // together, the units in order)
+  constexpr int kPer = LPB * LPB / 128;
+  float v[kPer];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+  for (int q = 0; q < kPer; ++q) v[q] = 0.0f;
+  for (int u = ustart[b]; u < ustart[b + 1]; ++u) {
+    const float* pu = part + (size_t)u * LPB * LPB;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
-    }
-  };
-  auto gram_finish = [&]() {   // callers have synchronised: the chunks are no longer read
+    for (int q = 0; q < kPer; ++q) v[q] += pu[tid + q * 128];
+  }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) Gp[grp][(bi + i) * LPB + bj + j] = acc[i][j];
-    __syncthreads();
-    for (int e = tid; e < LPB * LPB; e += kQRThreads)
-      S[e / LPB][e % LPB] = (Gp[0][e] + Gp[1][e]) + (Gp[2][e] + Gp[3][e]);
-  };
-  auto zero_acc = [&]() {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  };
-
-  // Gram of the input
-  zero_acc();
-  {
-    float4 nxt[2];
-    load_chunk(Y, rows, 0, tid, nxt);
-    for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
-      const int nr = (int)min((int64_t)kChunk, rows - c0);
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 2; ++u) reinterpret_cast<float4*>(&chunk[0][0])[tid + u * kQRThreads] = nxt[u];
-      if (c0 + kChunk < rows) load_chunk(Y, rows, c0 + kChunk, tid, nxt);
-      __syncthreads();
-      gram_chunk(chunk, nr);
-    }
+  for (int q = 0; q < kPer; ++q) {
+    const int e = tid + q * 128;
+    S[e >> 5][e & 31] = v[q];
+    Ro[e >> 5][e & 31] = racc[(size_t)b * LPB * LPB + e];
   }
   __syncthreads();
-  gram_finish();
-  const float* src = Y;
-  for (int round = 0; round < rounds; ++round) {
-    __syncthreads();
-    // shift (first of three rounds) and pivot floor from the trace and largest diagonal
-    if (warp == 0) {
-      const float d = lane < l ? S[lane][lane] : 0.0f;
-      float tr = warp_sum(d), mx = d;
+  if (warp == 0) {
+    const float d = lane < l ? S[lane][lane] : 0.0f;
+    float tr = warp_sum(d), mx = d;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (!isfinite(tr)) {
-        if (lane == 0) set_status(status, ST_NONFINITE);
-      }
-      const float shift = (rounds >= 3 && round == 0) ? (float)l * kEpsF32 * tr : 0.0f;
-      const float pfloor = fmaxf((float)l * kEpsF32 * mx, 1e-30f);
-      chol32_warp(S, l, shift, pfloor, Ls, Xs, status);
-    }
-    __syncthreads();
-    // Racc <- R Racc with R = L^T (upper): Rtmp(i, j) = sum_{i<=c<=j} L(c, i) Racc(c, j)
-    for (int e = tid; e < LPB * LPB; e += kQRThreads) {
-      const int i = e / LPB, jj = e % LPB;
-      float v = 0.0f;
-      for (int c = i; c <= jj; ++c) v = fmaf(Ls[c][i], Racc[c][jj], v);
-      Rtmp[i][jj] = (jj >= i) ? v : 0.0f;
-    }
-    __syncthreads();
-    for (int e = tid; e < LPB * LPB; e += kQRThreads) Racc[e / LPB][e % LPB] = Rtmp[e / LPB][e % LPB];
-    // apply Q = src R^-1 (R^-1(i, j) = X(j, i)), and the Gram of Q for the next round
-    float xr[LPB];
-#pragma unroll
-    for (int i = 0; i < LPB; ++i) xr[i] = Xs[lane][i];   // thread column j = lane
-    zero_acc();
-    const bool more = round + 1 < rounds;
-    float4 nxt[2];
-    load_chunk(src, rows, 0, tid, nxt);
-    for (int64_t c0 = 0; c0 < rows; c0 += kChunk) {
-      const int nr = (int)min((int64_t)kChunk, rows - c0);
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 2; ++u) reinterpret_cast<float4*>(&chunk[0][0])[tid + u * kQRThreads] = nxt[u];
-      if (c0 + kChunk < rows) load_chunk(src, rows, c0 + kChunk, tid, nxt);
-      __syncthreads();
-      for (int rr = warp; rr < nr; rr += kQRThreads / 32) {
-        const float4* yr = reinterpret_cast<const float4*>(&chunk[rr][0]);
-        float v0 = 0.0f, v1 = 0.0f;
-#pragma unroll
-        for (int i4 = 0; i4 < LPB / 4; ++i4) {
-          const float4 y4 = yr[i4];
-          v0 = fmaf(y4.x, xr[4 * i4], v0);
-          v1 = fmaf(y4.y, xr[4 * i4 + 1], v1);
-          v0 = fmaf(y4.z, xr[4 * i4 + 2], v0);
-          v1 = fmaf(y4.w, xr[4 * i4 + 3], v1);
-        }
-        const float qv = v0 + v1;
-        qch[rr][lane] = qv;
-        Q[(c0 + rr) * LPB + lane] = qv;
-      }
-      if (more) {
-        __syncthreads();
-        gram_chunk(qch, nr);
-      }
-    }
-    __syncthreads();
-    if (more) gram_finish();
-    src = Q;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (!isfinite(tr) && lane == 0) set_status(status, ST_NONFINITE);
+    const float shift = shift_on * (float)l * kEpsF32 * tr;
+    const float pfloor = fmaxf((float)l * kEpsF32 * mx, 1e-30f);
+    chol32_warp(S, l, shift, pfloor, Ls, Xs, status);
   }
   __syncthreads();
-  float* R = rout + (size_t)b * LPB * LPB;
-  for (int e = tid; e < LPB * LPB; e += kQRThreads) {
-    const int i = e / LPB, jj = e % LPB;
-    R[e] = (i < l && jj < l) ? Racc[i][jj] : 0.0f;
+  // R = L^T; the running product R Racc (or R itself on the first round), and R^-1 = X^T
+  for (int e = tid; e < LPB * LPB; e += blockDim.x) {
+    const int i = e >> 5, j = e & 31;
+    float v = 0.0f;
+    if (racc_init) {
+      v = (j >= i) ? Ls[j][i] : 0.0f;
+    } else {
+      for (int c = i; c <= j; ++c) v = fmaf(Ls[c][i], Ro[c][j], v);
+      if (j < i) v = 0.0f;
+    }
+    racc[(size_t)b * LPB * LPB + e] = (i < l && j < l) ? v : 0.0f;
+    rinv[(size_t)b * LPB * LPB + e] = Xs[j][i];
   }
+}
+
+// Q = Y R^-1 over a unit: a warp per row, lane = column, the column of R^-1 in registers
+// and the row of Y read as float4 broadcasts; then the Gram partial of the new rows.
+__global__ void __launch_bounds__(kUnitThreads) bqr_apply_kernel(const float* __restrict__ src,
+                                                                 float* __restrict__ dst,
+                                                                 const int64_t* __restrict__ roff,
+                                                                 const int2* __restrict__ units,
+                                                                 const float* __restrict__ rinv,
+                                                                 float* __restrict__ part) {
+  __shared__ __align__(16) float ys[kUnitRows][LPB];
+  __shared__ __align__(16) float gp[4][LPB * LPB];
+  const int2 u = units[blockIdx.x];
+  const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
+  const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bqr_stage(src, row0, nr, ys);
+  float xr[LPB];
+#pragma unroll
+  for (int i = 0; i < LPB; ++i) xr[i] = rinv[(size_t)u.x * LPB * LPB + i * LPB + lane];   // R^-1(i, lane)
+  __syncthreads();
+  for (int rr = warp; rr < nr; rr += kUnitThreads / 32) {
+    const float4* yr = reinterpret_cast<const float4*>(&ys[rr][0]);
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int i4 = 0; i4 < LPB / 4; ++i4) {
+      const float4 y4 = yr[i4];
+      v0 = fmaf(y4.x, xr[4 * i4], v0);
+      v1 = fmaf(y4.y, xr[4 * i4 + 1], v1);
+      v0 = fmaf(y4.z, xr[4 * i4 + 2], v0);
+      v1 = fmaf(y4.w, xr[4 * i4 + 3], v1);
+    }
+    __syncwarp();   // every lane has read the row before it is overwritten
+    ys[rr][lane] = v0 + v1;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * (LPB / 4); e += blockDim.x)
+    reinterpret_cast<float4*>(dst + row0 * LPB)[e] = reinterpret_cast<const float4*>(&ys[0][0])[e];
+  if (part) bqr_gram_tile(ys, nr, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 // basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
@@ -666,8 +670,16 @@ cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int6
 }
 
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
-                                  int rounds, float* rout, uint32_t* status, cudaStream_t st) {
-  batched_cholqr_kernel<<<nb, kQRThreads, 0, st>>>(yin, qout, roff, l, rounds, rout, status);
+                                  int rounds, float* rout, float* rinv, const int2* units, int nunits,
+                                  const int* ustart, float* part, uint32_t* status, cudaStream_t st) {
+  if (nunits <= 0 || rounds < 1) return cudaErrorInvalidValue;
+  bqr_gram_kernel<<<nunits, kUnitThreads, 0, st>>>(yin, roff, units, part);
+  for (int r = 0; r < rounds; ++r) {
+    bqr_chol_kernel<<<nb, 128, 0, st>>>(part, ustart, l, (rounds >= 3 && r == 0) ? 1.0f : 0.0f, r == 0 ? 1 : 0,
+                                        rout, rinv, status);
+    bqr_apply_kernel<<<nunits, kUnitThreads, 0, st>>>(r == 0 ? yin : qout, qout, roff, units, rinv,
+                                                   r + 1 < rounds ? part : nullptr);
+  }
   return cudaGetLastError();
 }
 
