@@ -373,7 +373,9 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
 rsvd_status_t qr_back(rsvd_batched_plan_t P, const float* Q, const float* gQ, const float* R, bool m_side,
                       float* gY) {
   const int64_t* roff = m_side ? P->d_roff_m : P->d_roff_n;
-  BTRY(launch_bwd_qr_small(Q, gQ, roff, P->nb, P->l, R, P->nmat, P->rinv, P->st));
+  BTRY(launch_bwd_qr_small(Q, gQ, roff, m_side ? P->d_qunits_m : P->d_qunits_n, m_side ? P->nq_m : P->nq_n,
+                           m_side ? P->d_ustart_m : P->d_ustart_n, P->nb, P->l, R, P->qpart, P->nmat, P->rinv,
+                           P->st));
   BTRY(launch_bwd_qr_apply(Q, gQ, roff, P->nb, m_side ? P->sum_m : P->sum_n, P->nmat, P->rinv, gY, P->st));
   return RSVD_OK;
 }

@@ -57,6 +57,35 @@ __device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_
   }
 }
 
+// acc[c] += a M[t][c] for all c, and sum_c x[c] M[i][c]: the row of the 32 x 32 matrix in
+// shared memory read as eight float4 broadcasts (every thread of the block reads the same
+// row), four FMAs per load
+__device__ __forceinline__ void axpy_row(float a, const float* __restrict__ mrow, float (&acc)[LPB]) {
+  const float4* m4 = reinterpret_cast<const float4*>(mrow);
+#pragma unroll
+  for (int c4 = 0; c4 < LPB / 4; ++c4) {
+    const float4 v = m4[c4];
+    acc[4 * c4] = fmaf(a, v.x, acc[4 * c4]);
+    acc[4 * c4 + 1] = fmaf(a, v.y, acc[4 * c4 + 1]);
+    acc[4 * c4 + 2] = fmaf(a, v.z, acc[4 * c4 + 2]);
+    acc[4 * c4 + 3] = fmaf(a, v.w, acc[4 * c4 + 3]);
+  }
+}
+
+__device__ __forceinline__ float dot_row(const float* __restrict__ mrow, const float (&x)[LPB]) {
+  const float4* m4 = reinterpret_cast<const float4*>(mrow);
+  float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+  for (int c4 = 0; c4 < LPB / 4; ++c4) {
+    const float4 v = m4[c4];
+    s0 = fmaf(x[4 * c4], v.x, s0);
+    s1 = fmaf(x[4 * c4 + 1], v.y, s1);
+    s0 = fmaf(x[4 * c4 + 2], v.z, s0);
+    s1 = fmaf(x[4 * c4 + 3], v.w, s1);
+  }
+  return s0 + s1;
+}
+
 // t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u = Q[r] Ut; gQ[r][i] = sum_{c<k} t_c Ut[i][c];
 // ublk[r][c] = u_c (1 - 2 s_c) for c < k, zero beyond (the first left factor U (I - 2S)).
 __global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restrict__ P,
@@ -68,7 +97,7 @@ __global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restri
                                                            int ldu) {
   __shared__ float qs[kRowBlock][LPB + 1];
   __shared__ float ps[kRowBlock][LPB + 1];
-  __shared__ float Us[LPB][LPB];
+  __shared__ __align__(16) float Us[LPB][LPB];
   __shared__ float ss[LPB];
   const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
   const int rr = threadIdx.x;
@@ -88,11 +117,7 @@ __global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restri
 #pragma unroll
       for (int c = 0; c < LPB; ++c) t[c] = 0.0f;
 #pragma unroll 4
-      for (int j = 0; j < LPB; ++j) {
-        const float qj = qs[rr][j];
-#pragma unroll
-        for (int c = 0; c < LPB; ++c) t[c] = fmaf(qj, Us[j][c], t[c]);   // u_c
-      }
+      for (int j = 0; j < LPB; ++j) axpy_row(qs[rr][j], Us[j], t);   // u_c
 #pragma unroll
       for (int c = 0; c < LPB; ++c) {
         const float s = ss[c], c1 = 1.0f - 2.0f * s;
@@ -100,12 +125,7 @@ __global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restri
         t[c] = c < k ? fmaf(ps[rr][c], c1, 2.0f * s * s * t[c]) : 0.0f;
       }
 #pragma unroll
-      for (int i = 0; i < LPB; ++i) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int c = 0; c < LPB; ++c) acc = fmaf(t[c], Us[i][c], acc);
-        g[i] = acc;
-      }
+      for (int i = 0; i < LPB; ++i) g[i] = dot_row(Us[i], t);
     }
   }
   __syncthreads();
@@ -123,42 +143,85 @@ __global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restri
   }
 }
 
-// one CTA per matrix: C = gQ^T Q (rows staged in shared memory), N = copyltu(-C);
-// Rinv = R^-1 from R^T = L lower: warp 0, lane r holds row r of L, X = L^-1 by columns.
-constexpr int kSmallThreads = 256;
-constexpr int kRows = 64;
+// C_u = sum over the rows of a Cholesky-QR unit (matrix b, 128-row tile) of gQ[r][i] Q[r][j]:
+// the partial of gQ^T Q, 256 threads in four row groups with 4 x 4 register blocks (two
+// float4 reads per 16 FMAs), the groups summed in a fixed order.
+constexpr int kCrossRows = 128;
 
-__global__ void __launch_bounds__(kSmallThreads) bwd_qr_small_kernel(
-    const float* __restrict__ Q, const float* __restrict__ gQ, const int64_t* __restrict__ roff, int l,
-    const float* __restrict__ R, float* __restrict__ N, float* __restrict__ Rinv) {
-  __shared__ float qs[kRows][LPB];
-  __shared__ float gs[kRows][LPB];
+__global__ void __launch_bounds__(256) bwd_cross_kernel(const float* __restrict__ gQ, const float* __restrict__ Q,
+                                                        const int64_t* __restrict__ roff,
+                                                        const int2* __restrict__ units, float* __restrict__ part) {
+  __shared__ __align__(16) float gs[kCrossRows][LPB];
+  __shared__ __align__(16) float qs[kCrossRows][LPB];
+  __shared__ float gp[4][LPB * LPB / 4];   // one quarter of G per row group at a time
+  const int2 u = units[blockIdx.x];
+  const int64_t row0 = roff[u.x] + (int64_t)u.y * kCrossRows;
+  const int nr = (int)min((int64_t)kCrossRows, roff[u.x + 1] - row0);
+  for (int e = threadIdx.x; e < kCrossRows * (LPB / 4); e += blockDim.x) {
+    const int rr = e >> 3;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(&gs[0][0])[e] = rr < nr ? reinterpret_cast<const float4*>(gQ + (row0 + rr) * LPB)[e & 7] : z;
+    reinterpret_cast<float4*>(&qs[0][0])[e] = rr < nr ? reinterpret_cast<const float4*>(Q + (row0 + rr) * LPB)[e & 7] : z;
+  }
+  __syncthreads();
+  const int grp = threadIdx.x >> 6, gt = threadIdx.x & 63;
+  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int rr = grp; rr < nr; rr += 4) {
+    const float4 x = *reinterpret_cast<const float4*>(&gs[rr][bi]);
+    const float4 y = *reinterpret_cast<const float4*>(&qs[rr][bj]);
+    const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
+  }
+  // the four groups' blocks summed through shared memory, one row quarter of C at a time
+  float* pu = part + (size_t)blockIdx.x * LPB * LPB;
+  for (int qtr = 0; qtr < 4; ++qtr) {
+    __syncthreads();
+    if ((bi >> 3) == qtr) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gp[grp][(bi - 8 * qtr + i) * LPB + bj + j] = acc[i][j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < LPB * LPB / 4; e += blockDim.x)
+      pu[qtr * (LPB * LPB / 4) + e] = (gp[0][e] + gp[1][e]) + (gp[2][e] + gp[3][e]);
+  }
+}
+
+// per matrix: C = the sum of its units' partials (in unit order), N = copyltu(-C); Rinv =
+// R^-1 from R^T = L lower: warp 0, lane r holds row r of L, X = L^-1 by columns.
+__global__ void __launch_bounds__(128) bwd_qr_small_kernel(const float* __restrict__ part,
+                                                           const int* __restrict__ ustart, int l,
+                                                           const float* __restrict__ R, float* __restrict__ N,
+                                                           float* __restrict__ Rinv) {
   __shared__ float C[LPB][LPB + 1];
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t r0 = roff[b], rows = roff[b + 1] - r0;
-  const int gi = 4 * warp, gj = lane;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int64_t c0 = 0; c0 < rows; c0 += kRows) {
-    const int nr = (int)min((int64_t)kRows, rows - c0);
-    __syncthreads();
-    for (int e = tid; e < kRows * LPB; e += kSmallThreads) {
-      const int rr = e / LPB, cc = e % LPB;
-      qs[rr][cc] = rr < nr ? Q[(r0 + c0 + rr) * LPB + cc] : 0.0f;
-      gs[rr][cc] = rr < nr ? gQ[(r0 + c0 + rr) * LPB + cc] : 0.0f;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
-      const float qj = qs[rr][gj];
+  constexpr int kPer = LPB * LPB / 128;
+  float v[kPer];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a] = fmaf(gs[rr][gi + a], qj, acc[a]);
-    }
+  for (int q = 0; q < kPer; ++q) v[q] = 0.0f;
+  for (int u = ustart[b]; u < ustart[b + 1]; ++u) {
+    const float* pu = part + (size_t)u * LPB * LPB;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) v[q] += pu[tid + q * 128];
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) C[gi + a][gj] = acc[a];   // C(i, j) = sum_r gQ[r][i] Q[r][j]
+  for (int q = 0; q < kPer; ++q) {
+    const int e = tid + q * 128;
+    C[e >> 5][e & 31] = v[q];   // C(i, j) = sum_r gQ[r][i] Q[r][j]
+  }
   __syncthreads();
   float* Nb = N + (size_t)b * LPB * LPB;
-  for (int e = tid; e < LPB * LPB; e += kSmallThreads) {
+  for (int e = tid; e < LPB * LPB; e += blockDim.x) {
     const int i = e / LPB, j = e % LPB;
     Nb[e] = -(i >= j ? C[i][j] : C[j][i]);
   }
@@ -202,8 +265,8 @@ __global__ void __launch_bounds__(kRowBlock) bwd_qr_apply_kernel(const float* __
                                                                  float* __restrict__ gY) {
   __shared__ float qs[kRowBlock][LPB + 1];
   __shared__ float gs[kRowBlock][LPB + 1];
-  __shared__ float Ns[LPB][LPB];
-  __shared__ float Rs[LPB][LPB];
+  __shared__ __align__(16) float Ns[LPB][LPB];
+  __shared__ __align__(16) float Rs[LPB][LPB];
   const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
   const int rr = threadIdx.x;
   const int64_t r = r0 + rr;
@@ -224,18 +287,9 @@ __global__ void __launch_bounds__(kRowBlock) bwd_qr_apply_kernel(const float* __
 #pragma unroll
       for (int j = 0; j < LPB; ++j) w[j] = gs[rr][j];
 #pragma unroll 4
-      for (int t = 0; t < LPB; ++t) {
-        const float qt = qs[rr][t];
+      for (int t = 0; t < LPB; ++t) axpy_row(qs[rr][t], Ns[t], w);
 #pragma unroll
-        for (int j = 0; j < LPB; ++j) w[j] = fmaf(qt, Ns[t][j], w[j]);
-      }
-#pragma unroll
-      for (int i = 0; i < LPB; ++i) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int j = 0; j < LPB; ++j) acc = fmaf(w[j], Rs[i][j], acc);
-        g[i] = acc;
-      }
+      for (int i = 0; i < LPB; ++i) g[i] = dot_row(Rs[i], w);
     }
   }
   __syncthreads();
@@ -483,9 +537,12 @@ cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, int nb, int l,
-                                const float* R, float* N, float* Rinv, cudaStream_t st) {
-  bwd_qr_small_kernel<<<nb, kSmallThreads, 0, st>>>(Q, gQ, roff, l, R, N, Rinv);
+cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
+                                int nunits, const int* ustart, int nb, int l, const float* R, float* part,
+                                float* N, float* Rinv, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  bwd_cross_kernel<<<nunits, 256, 0, st>>>(gQ, Q, roff, units, part);
+  bwd_qr_small_kernel<<<nb, 128, 0, st>>>(part, ustart, l, R, N, Rinv);
   return cudaGetLastError();
 }
 

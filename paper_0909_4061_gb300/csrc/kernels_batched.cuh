@@ -52,9 +52,11 @@ cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int
 cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
                           const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st);
-// per matrix: N = copyltu(-gQ^T Q) and Rinv = R^-1 (R upper, l x l, identity beyond l)
-cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, int nb, int l,
-                                const float* R, float* N, float* Rinv, cudaStream_t st);
+// per matrix: N = copyltu(-gQ^T Q) (from partials over the Cholesky-QR units: units /
+// nunits / ustart, part: nunits x 32 x 32) and Rinv = R^-1 (R upper, l x l, identity beyond l)
+cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
+                                int nunits, const int* ustart, int nb, int l, const float* R, float* part,
+                                float* N, float* Rinv, cudaStream_t st);
 // gY = (gQ + Q N) R^-T, per row
 cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
                                 int64_t total_rows, const float* N, const float* Rinv, float* gY,
