@@ -376,7 +376,8 @@ rsvd_status_t qr_back(rsvd_batched_plan_t P, const float* Q, const float* gQ, co
   BTRY(launch_bwd_qr_small(Q, gQ, roff, m_side ? P->d_qunits_m : P->d_qunits_n, m_side ? P->nq_m : P->nq_n,
                            m_side ? P->d_ustart_m : P->d_ustart_n, P->nb, P->l, R, P->qpart, P->nmat, P->rinv,
                            P->st));
-  BTRY(launch_bwd_qr_apply(Q, gQ, roff, P->nb, m_side ? P->sum_m : P->sum_n, P->nmat, P->rinv, gY, P->st));
+  BTRY(launch_bwd_qr_apply(Q, gQ, roff, m_side ? P->d_qunits_m : P->d_qunits_n, m_side ? P->nq_m : P->nq_n,
+                           P->nmat, P->rinv, gY, P->st));
   return RSVD_OK;
 }
 
@@ -391,7 +392,7 @@ rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* cons
   BTRYS(to_operand(P, P->gn, false, 1));
   BTRYS(bpass(P, 0, 1, P->pm));                                                  // A V
   // dL/dQ_q and the first left factor U (I - 2 S)
-  BTRY(launch_bwd_gq(P->pm, P->qm[P->q], P->d_roff_m, P->nb, P->sum_m, P->ub, P->sig, P->k, P->gm,
+  BTRY(launch_bwd_gq(P->pm, P->qm[P->q], P->d_roff_m, P->d_qunits_m, P->nq_m, P->ub, P->sig, P->k, P->gm,
                      P->lbuf, kr, P->st));
   int blk = 1;
   for (int j = P->q; j >= 1; --j, blk += 2) {

@@ -31,116 +31,137 @@ using namespace tcx;
 
 constexpr int LPB = 32;
 
-// Row kernels of the backward: a block of kRowBlock consecutive rows of the concatenated
-// row arrays (they may span several matrices), one thread per row.  The block stages its
-// rows in shared memory (coalesced loads, rows padded to 33 floats), then for each matrix
-// it meets loads that matrix's small factors into shared memory (read by all threads at
-// the same address: broadcasts) and the threads whose rows belong to it do 2 x 32 x 32
-// FMAs in registers; results leave through the same staging buffer, coalesced.
-constexpr int kRowBlock = 128;
+// Row kernels of the backward over the 128-row units of the Cholesky-QR (one matrix per
+// unit): the unit's rows and the matrix's 32 x 32 factors are staged in shared memory
+// (coalesced), a warp takes a row at a time with lane = column, holding the column / row
+// of each factor it needs in registers and reading the row as float4 broadcasts; results
+// leave through the staging buffer, coalesced.
+constexpr int kUR = 128;   // rows per unit
+constexpr int kUT = 256;   // threads per unit block
 
-__device__ __forceinline__ int row_matrix(const int64_t* __restrict__ off, int nb, int64_t r) {
-  int lo = 0, hi = nb - 1;   // the largest b with off[b] <= r
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= r) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+__device__ __forceinline__ void unit_rows(const int64_t* __restrict__ roff, int2 u, int64_t* row0, int* nr) {
+  *row0 = roff[u.x] + (int64_t)u.y * kUR;
+  *nr = (int)min((int64_t)kUR, roff[u.x + 1] - *row0);
 }
 
-// rows (total x 32, ld 32) -> smem [kRowBlock][33] for the block's rows (zero past the end)
-__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t r0, int64_t total,
-                                           float (*dst)[LPB + 1]) {
-  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
-    const int rr = e >> 5, c = e & 31;
-    dst[rr][c] = r0 + rr < total ? src[(r0 + rr) * LPB + c] : 0.0f;
+__device__ __forceinline__ void unit_stage(const float* __restrict__ src, int64_t row0, int nr,
+                                           float (*ys)[LPB]) {
+  for (int e = threadIdx.x; e < kUR * (LPB / 4); e += blockDim.x) {
+    const int rr = e >> 3;
+    reinterpret_cast<float4*>(&ys[0][0])[e] =
+        rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
-// acc[c] += a M[t][c] for all c, and sum_c x[c] M[i][c]: the row of the 32 x 32 matrix in
-// shared memory read as eight float4 broadcasts (every thread of the block reads the same
-// row), four FMAs per load
-__device__ __forceinline__ void axpy_row(float a, const float* __restrict__ mrow, float (&acc)[LPB]) {
-  const float4* m4 = reinterpret_cast<const float4*>(mrow);
+// a 32 x 32 factor into shared memory (rows padded to 33 floats: column and row reads
+// by lane are both conflict-free)
+__device__ __forceinline__ void unit_small(const float* __restrict__ src, float (*ms)[LPB + 1]) {
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) ms[e >> 5][e & 31] = src[e];
+}
+
+// sum_j y_j w[j] for the row y in shared memory (float4 broadcasts), w in registers
+__device__ __forceinline__ float row_dot(const float* __restrict__ y, const float (&w)[LPB]) {
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  float v0 = 0.0f, v1 = 0.0f;
 #pragma unroll
-  for (int c4 = 0; c4 < LPB / 4; ++c4) {
-    const float4 v = m4[c4];
-    acc[4 * c4] = fmaf(a, v.x, acc[4 * c4]);
-    acc[4 * c4 + 1] = fmaf(a, v.y, acc[4 * c4 + 1]);
-    acc[4 * c4 + 2] = fmaf(a, v.z, acc[4 * c4 + 2]);
-    acc[4 * c4 + 3] = fmaf(a, v.w, acc[4 * c4 + 3]);
+  for (int i4 = 0; i4 < LPB / 4; ++i4) {
+    const float4 a = y4[i4];
+    v0 = fmaf(a.x, w[4 * i4], v0);
+    v1 = fmaf(a.y, w[4 * i4 + 1], v1);
+    v0 = fmaf(a.z, w[4 * i4 + 2], v0);
+    v1 = fmaf(a.w, w[4 * i4 + 3], v1);
   }
-}
-
-__device__ __forceinline__ float dot_row(const float* __restrict__ mrow, const float (&x)[LPB]) {
-  const float4* m4 = reinterpret_cast<const float4*>(mrow);
-  float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-  for (int c4 = 0; c4 < LPB / 4; ++c4) {
-    const float4 v = m4[c4];
-    s0 = fmaf(x[4 * c4], v.x, s0);
-    s1 = fmaf(x[4 * c4 + 1], v.y, s1);
-    s0 = fmaf(x[4 * c4 + 2], v.z, s0);
-    s1 = fmaf(x[4 * c4 + 3], v.w, s1);
-  }
-  return s0 + s1;
+  return v0 + v1;
 }
 
 // t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u = Q[r] Ut; gQ[r][i] = sum_{c<k} t_c Ut[i][c];
 // ublk[r][c] = u_c (1 - 2 s_c) for c < k, zero beyond (the first left factor U (I - 2S)).
-__global__ void __launch_bounds__(kRowBlock) bwd_gq_kernel(const float* __restrict__ P,
-                                                           const float* __restrict__ Q,
-                                                           const int64_t* __restrict__ roff, int nb,
-                                                           int64_t total, const float* __restrict__ ut,
-                                                           const float* __restrict__ sig, int k,
-                                                           float* __restrict__ gq, float* __restrict__ ublk,
-                                                           int ldu) {
-  __shared__ float qs[kRowBlock][LPB + 1];
-  __shared__ float ps[kRowBlock][LPB + 1];
-  __shared__ __align__(16) float Us[LPB][LPB];
-  __shared__ float ss[LPB];
-  const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
-  const int rr = threadIdx.x;
-  const int64_t r = r0 + rr;
-  stage_rows(Q, r0, total, qs);
-  stage_rows(P, r0, total, ps);
-  const int b0 = row_matrix(roff, nb, r0);
-  const int b1 = row_matrix(roff, nb, min(r0 + kRowBlock, total) - 1);
-  float g[LPB], uo[LPB];
-  for (int b = b0; b <= b1; ++b) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) Us[e >> 5][e & 31] = ut[(size_t)b * LPB * LPB + e];
-    if (threadIdx.x < LPB) ss[threadIdx.x] = threadIdx.x < k ? sig[(size_t)b * LPB + threadIdx.x] : 0.0f;
-    __syncthreads();
-    if (r < total && r >= roff[b] && r < roff[b + 1]) {
-      float t[LPB];
+__global__ void __launch_bounds__(kUT) bwd_gq_kernel(const float* __restrict__ P, const float* __restrict__ Q,
+                                                     const int64_t* __restrict__ roff,
+                                                     const int2* __restrict__ units,
+                                                     const float* __restrict__ ut, const float* __restrict__ sig,
+                                                     int k, float* __restrict__ gq, float* __restrict__ ublk,
+                                                     int ldu) {
+  __shared__ __align__(16) float qs[kUR][LPB];
+  __shared__ __align__(16) float ps[kUR][LPB];
+  __shared__ __align__(16) float tb[kUT / 32][LPB];
+  __shared__ float Us[LPB][LPB + 1];
+  const int2 u = units[blockIdx.x];
+  int64_t row0;
+  int nr;
+  unit_rows(roff, u, &row0, &nr);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unit_stage(Q, row0, nr, qs);
+  unit_stage(P, row0, nr, ps);
+  unit_small(ut + (size_t)u.x * LPB * LPB, Us);
+  const float s = lane < k ? sig[(size_t)u.x * LPB + lane] : 0.0f;
+  const float c1 = 1.0f - 2.0f * s, c2 = 2.0f * s * s;
+  __syncthreads();
+  float ucol[LPB], urow[LPB];
 #pragma unroll
-      for (int c = 0; c < LPB; ++c) t[c] = 0.0f;
-#pragma unroll 4
-      for (int j = 0; j < LPB; ++j) axpy_row(qs[rr][j], Us[j], t);   // u_c
-#pragma unroll
-      for (int c = 0; c < LPB; ++c) {
-        const float s = ss[c], c1 = 1.0f - 2.0f * s;
-        uo[c] = c < k ? t[c] * c1 : 0.0f;
-        t[c] = c < k ? fmaf(ps[rr][c], c1, 2.0f * s * s * t[c]) : 0.0f;
-      }
-#pragma unroll
-      for (int i = 0; i < LPB; ++i) g[i] = dot_row(Us[i], t);
-    }
+  for (int j = 0; j < LPB; ++j) {
+    ucol[j] = Us[j][lane];   // Ut[j][lane]
+    urow[j] = Us[lane][j];   // Ut[lane][j]
+  }
+  for (int rr = warp; rr < nr; rr += kUT / 32) {
+    const float uc = row_dot(qs[rr], ucol);
+    const float t = lane < k ? fmaf(ps[rr][lane], c1, c2 * uc) : 0.0f;
+    tb[warp][lane] = t;
+    __syncwarp();
+    const float g = row_dot(tb[warp], urow);
+    __syncwarp();   // the warp's rows and its tb row are read before they are overwritten
+    qs[rr][lane] = g;
+    ps[rr][lane] = lane < k ? uc * c1 : 0.0f;
   }
   __syncthreads();
-  if (r < total) {
+  for (int e = threadIdx.x; e < nr * LPB; e += blockDim.x) {
+    const int rr = e >> 5, c = e & 31;
+    gq[(row0 + rr) * LPB + c] = qs[rr][c];
+    ublk[(row0 + rr) * ldu + c] = ps[rr][c];
+  }
+}
+
+// gY = (gQ + Q N) R^-T per row: lane j forms w_j = gQ[r][j] + sum_t Q[r][t] N[t][j] (column
+// j of N in registers); lane i then gY[r][i] = sum_j w_j Rinv[i][j] (row i of R^-1).
+__global__ void __launch_bounds__(kUT) bwd_qr_apply_kernel(const float* __restrict__ Q,
+                                                           const float* __restrict__ gQ,
+                                                           const int64_t* __restrict__ roff,
+                                                           const int2* __restrict__ units,
+                                                           const float* __restrict__ N,
+                                                           const float* __restrict__ Rinv,
+                                                           float* __restrict__ gY) {
+  __shared__ __align__(16) float qs[kUR][LPB];
+  __shared__ __align__(16) float gs[kUR][LPB];
+  __shared__ __align__(16) float wb[kUT / 32][LPB];
+  __shared__ float Ns[LPB][LPB + 1];
+  __shared__ float Rs[LPB][LPB + 1];
+  const int2 u = units[blockIdx.x];
+  int64_t row0;
+  int nr;
+  unit_rows(roff, u, &row0, &nr);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unit_stage(Q, row0, nr, qs);
+  unit_stage(gQ, row0, nr, gs);
+  unit_small(N + (size_t)u.x * LPB * LPB, Ns);
+  unit_small(Rinv + (size_t)u.x * LPB * LPB, Rs);
+  __syncthreads();
+  float ncol[LPB], rrow[LPB];
 #pragma unroll
-    for (int i = 0; i < LPB; ++i) { qs[rr][i] = g[i]; ps[rr][i] = uo[i]; }
+  for (int j = 0; j < LPB; ++j) {
+    ncol[j] = Ns[j][lane];   // N[j][lane]
+    rrow[j] = Rs[lane][j];   // Rinv[lane][j]
+  }
+  for (int rr = warp; rr < nr; rr += kUT / 32) {
+    const float w = gs[rr][lane] + row_dot(qs[rr], ncol);
+    wb[warp][lane] = w;
+    __syncwarp();
+    const float g = row_dot(wb[warp], rrow);
+    __syncwarp();
+    qs[rr][lane] = g;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
-    const int q = e >> 5, c = e & 31;
-    if (r0 + q < total) {
-      gq[(r0 + q) * LPB + c] = qs[q][c];
-      ublk[(r0 + q) * ldu + c] = ps[q][c];
-    }
-  }
+  for (int e = threadIdx.x; e < nr * (LPB / 4); e += blockDim.x)
+    reinterpret_cast<float4*>(gY + row0 * LPB)[e] = reinterpret_cast<const float4*>(&qs[0][0])[e];
 }
 
 // C_u = sum over the rows of a Cholesky-QR unit (matrix b, 128-row tile) of gQ[r][i] Q[r][j]:
@@ -252,55 +273,6 @@ __global__ void __launch_bounds__(128) bwd_qr_small_kernel(const float* __restri
     float* Rib = Rinv + (size_t)b * LPB * LPB;
 #pragma unroll
     for (int i = 0; i < LPB; ++i) Rib[r * LPB + i] = x[i];   // R^-1(r, i) = X(i, r)
-  }
-}
-
-// gY = (gQ + Q N) R^-T per row: w_j = gQ[r][j] + sum_t Q[r][t] N[t][j];
-// gY[r][i] = sum_j w_j Rinv[i][j]; one thread per row (see bwd_gq_kernel).
-__global__ void __launch_bounds__(kRowBlock) bwd_qr_apply_kernel(const float* __restrict__ Q,
-                                                                 const float* __restrict__ gQ,
-                                                                 const int64_t* __restrict__ roff, int nb,
-                                                                 int64_t total, const float* __restrict__ N,
-                                                                 const float* __restrict__ Rinv,
-                                                                 float* __restrict__ gY) {
-  __shared__ float qs[kRowBlock][LPB + 1];
-  __shared__ float gs[kRowBlock][LPB + 1];
-  __shared__ __align__(16) float Ns[LPB][LPB];
-  __shared__ __align__(16) float Rs[LPB][LPB];
-  const int64_t r0 = (int64_t)blockIdx.x * kRowBlock;
-  const int rr = threadIdx.x;
-  const int64_t r = r0 + rr;
-  stage_rows(Q, r0, total, qs);
-  stage_rows(gQ, r0, total, gs);
-  const int b0 = row_matrix(roff, nb, r0);
-  const int b1 = row_matrix(roff, nb, min(r0 + kRowBlock, total) - 1);
-  float g[LPB];
-  for (int b = b0; b <= b1; ++b) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
-      Ns[e >> 5][e & 31] = N[(size_t)b * LPB * LPB + e];
-      Rs[e >> 5][e & 31] = Rinv[(size_t)b * LPB * LPB + e];
-    }
-    __syncthreads();
-    if (r < total && r >= roff[b] && r < roff[b + 1]) {
-      float w[LPB];
-#pragma unroll
-      for (int j = 0; j < LPB; ++j) w[j] = gs[rr][j];
-#pragma unroll 4
-      for (int t = 0; t < LPB; ++t) axpy_row(qs[rr][t], Ns[t], w);
-#pragma unroll
-      for (int i = 0; i < LPB; ++i) g[i] = dot_row(Rs[i], w);
-    }
-  }
-  __syncthreads();
-  if (r < total) {
-#pragma unroll
-    for (int i = 0; i < LPB; ++i) qs[rr][i] = g[i];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kRowBlock * LPB; e += blockDim.x) {
-    const int q = e >> 5, c = e & 31;
-    if (r0 + q < total) gY[(r0 + q) * LPB + c] = qs[q][c];
   }
 }
 
@@ -528,12 +500,11 @@ __global__ void __launch_bounds__(kFinalThreads, 1) bwd_final_tc_kernel(
 
 }  // namespace
 
-cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
+cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, const int2* units, int nunits,
                           const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st) {
-  if (total_rows <= 0) return cudaSuccess;
-  bwd_gq_kernel<<<(unsigned)cdiv(total_rows, kRowBlock), kRowBlock, 0, st>>>(P, Q, roff, nb, total_rows, ut,
-                                                                            sig, k, gq, ublk, ldu);
+  if (nunits <= 0) return cudaSuccess;
+  bwd_gq_kernel<<<nunits, kUT, 0, st>>>(P, Q, roff, units, ut, sig, k, gq, ublk, ldu);
   return cudaGetLastError();
 }
 
@@ -546,12 +517,10 @@ cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
-                                int64_t total_rows, const float* N, const float* Rinv, float* gY,
-                                cudaStream_t st) {
-  if (total_rows <= 0) return cudaSuccess;
-  bwd_qr_apply_kernel<<<(unsigned)cdiv(total_rows, kRowBlock), kRowBlock, 0, st>>>(Q, gQ, roff, nb, total_rows,
-                                                                                  N, Rinv, gY);
+cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
+                                int nunits, const float* N, const float* Rinv, float* gY, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  bwd_qr_apply_kernel<<<nunits, kUT, 0, st>>>(Q, gQ, roff, units, N, Rinv, gY);
   return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int
 // ---- backward (k_batched_bwd.cu) ----
 // gQ = (P (I - 2 S) + 2 U S^2) Ut_k^T with U = Q Ut_k (per row; P = A V, m side), and
 // ublk = U (I - 2 S) (first k columns, zero beyond), ld ldu.
-cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, int nb, int64_t total_rows,
+cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, const int2* units, int nunits,
                           const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st);
 // per matrix: N = copyltu(-gQ^T Q) (from partials over the Cholesky-QR units: units /
@@ -57,10 +57,9 @@ cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, i
 cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
                                 int nunits, const int* ustart, int nb, int l, const float* R, float* part,
                                 float* N, float* Rinv, cudaStream_t st);
-// gY = (gQ + Q N) R^-T, per row
-cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, int nb,
-                                int64_t total_rows, const float* N, const float* Rinv, float* gY,
-                                cudaStream_t st);
+// gY = (gQ + Q N) R^-T, per row (over the Cholesky-QR units of the side)
+cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
+                                int nunits, const float* N, const float* Rinv, float* gY, cudaStream_t st);
 // dst[r][col0 + c] = src[r][c] (rows x 32 -> ld ldd)
 cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
                               cudaStream_t st);
