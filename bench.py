@@ -668,7 +668,12 @@ def run_workload(args):
         res = {}
         for name, kw in variants:
             q = kw.pop("q")
-            with pkg.Plan(w.m, w.n, w.k, w.p, q, w.omega_seed, pkg.RSVD_BF16_TC, **kw) as pl:
+            torch.cuda.synchronize()
+            t_plan = time.perf_counter()
+            pl = pkg.Plan(w.m, w.n, w.k, w.p, q, w.omega_seed, pkg.RSVD_BF16_TC, **kw)
+            pkg.rsvd_sync(pl.handle)
+            plan_ms = (time.perf_counter() - t_plan) * 1e3
+            with pl:
                 U = torch.empty(w.m, w.k, device="cuda")
                 S = torch.empty(w.k, device="cuda")
                 V = torch.empty(w.n, w.k, device="cuda")
@@ -680,6 +685,7 @@ def run_workload(args):
                 stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
                 pkg.rsvd_profile(pl.handle, 0)
                 res[name] = {"ms": round(ms, 4), "rel_err_vs_fp32_A": round(_rel_err(A, U, S, V), 6),
+                             "plan_create_ms": round(plan_ms, 3),
                              "jacobi_sweeps_max": pkg.rsvd_diagnostics(pl.handle)[1],
                              "passes_over_A": (2 if kw.get("single_pass") else 2 * q + 2),
                              "stages_ms": {k2: round(v, 4) for k2, v in stage_ms.items()}}

@@ -48,7 +48,8 @@ struct rsvd_plan_s {
   float* gpart = nullptr;    // nblk x lp x lp
   uint8_t* rimg = nullptr;   // bfloat16 planes of R^-1 for the tensor-core apply (l_p > 128)
   float* small = nullptr;    // 24 x lp x lp: g, lbuf, rtmp, rinv, racc, ut, w, scratch, single pass
-  float* psi = nullptr;      // m x lp   second test matrix of the single-pass sketch
+  float* psi = nullptr;      // m x lpp  second test matrix of the single-pass sketch (drawn
+                             //          once, at plan creation: it depends on the seed alone)
   float* sig2 = nullptr;     // 2 lp     singular values of X1, X2 (single pass)
   float* sig = nullptr;      // lp
   int* srft_freq = nullptr;  // l / 2 sampled frequencies of the SRFT test matrix
@@ -488,12 +489,12 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, P->sp(2)));
   if (Qout) TRY(launch_gather(P->qbuf, 1, 0, lp, Qout, ldq, P->m, l, l, P->st));
   // Yt = A^T Psi (Psi: Gaussian, stream 1, l' columns), Yt = Qt Rt (Rt in racc, ld lpp)
-  {
-    Step sp(P, RSVD_STEP_DRAW);
+  // Psi (drawn at plan creation, float32 holding the bfloat16 values the tensor-core pass
+  // multiplies with): its transposed bfloat16 operand, which other passes overwrite
+  if (tc) {
+    Step sp(P, RSVD_STEP_CONVERT);
     sp.launched();
-    TRY(launch_draw_gaussian(P->seed, 1u, P->m, lt, lpp, P->psi, lpp, tc ? P->xbf : nullptr,
-                             tc_ld(P->m), P->st));
-    if (tc) TRY(launch_round_bf16(P->psi, P->m, lpp, lpp, P->st));
+    TRY(launch_to_bf16_t(P->psi, P->m, lpp, P->xbf, tc_ld(P->m), 0, 0, P->st));
   }
   TRYS(step_pass_psi(P, A, &s, &stride));
   TRYS(step_orth(P, P->partial, s, stride, P->n, P->qtbuf, P->racc(), true, lt));
@@ -1096,6 +1097,16 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
     return RSVD_ERR_CUDA;
   }
   // the signs for the row-transform sketch (the lda must be even for its paired loads)
+  // Psi of the single pass (Gaussian, Philox stream 1, l' columns), rounded to bfloat16 for
+  // the tensor-core path
+  if (o.single_pass &&
+      (launch_draw_gaussian(seed, 1u, m, P->lt, P->lpp, P->psi, P->lpp, nullptr, 0, P->st) != cudaSuccess ||
+       (o.precision == RSVD_BF16_TC &&
+        launch_round_bf16(P->psi, m, P->lpp, P->lpp, P->st) != cudaSuccess))) {
+    cudaGetLastError();
+    free_plan(P);
+    return RSVD_ERR_CUDA;
+  }
   if (o.test_matrix == RSVD_SRFT && srft_fft_supported(n) && (o.lda % 2) == 0) {
     if ((s = dalloc(P, &P->srft_signs, (size_t)cdiv(n, 32))) != RSVD_OK) {
       free_plan(P);

@@ -151,3 +151,24 @@ def test_single_pass_noisy_tall_workload(rsvd_lib, precision):
           f"max dsigma/sigma1 {np.max(np.abs(s - sr)) / sr[0]:.2e}")
     assert e_gpu <= 1.02 * e_ref and e_gpu < 1.0
     assert np.max(np.abs(s - sr)) <= 2 * U32 * kap * sr[0]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_single_pass_repeated_calls_agree(rsvd_lib, precision):
+    """Psi is drawn by a plan's first single pass and kept: a second and third call on the
+    same plan (with other passes' operands written in between) give the same factors bit
+    for bit."""
+    pkg = rsvd_lib
+    m, n, k, p = 3000, 1024, 40, 8
+    rng = np.random.default_rng(4)
+    a = (rng.standard_normal((m, 60)) @ rng.standard_normal((60, n))).astype(np.float32)
+    bf16 = precision == pkg.RSVD_BF16_TC
+    A = torch.tensor(a, device="cuda", dtype=torch.bfloat16 if bf16 else torch.float32)
+    with pkg.Plan(m, n, k, p, 0, 9, precision, single_pass=1) as pl:
+        outs = []
+        for _ in range(3):
+            U, S, V = pl.svd(A)
+            torch.cuda.synchronize()
+            outs.append((U.clone(), S.clone(), V.clone()))
+    for U, S, V in outs[1:]:
+        assert torch.equal(U, outs[0][0]) and torch.equal(S, outs[0][1]) and torch.equal(V, outs[0][2])
