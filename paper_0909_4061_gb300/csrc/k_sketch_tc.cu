@@ -97,7 +97,7 @@ struct Range {
 // residual lo = A - hi (map_alo, the same tile shape and major-ness); each stage carries
 // both tiles and the MMAs of the lo tile accumulate into the same tensor-memory
 // accumulator, so the pass sees A to about 16 significant bits.
-template <int MODE, int HILO = 0, int TM = 1, int CH = 1>
+template <int MODE, int HILO = 0, int TM = 1, int CH = 1, int KB = 1>
 __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a,
                      const __grid_constant__ CUtensorMap map_alo,
@@ -118,10 +118,13 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
                                              ~uintptr_t(1023));
   static_assert(TM == 1 || !HILO, "the residual of A is read with single tiles");
   static_assert(TM * CH <= 2, "at most eight epilogue warps");
-  constexpr int kChunk = kChunkSteps / ((BK / 16) * (HILO ? 2 : 1));   // k tiles per chunk
+  // a k step of a stage is KB adjacent boxes of BK columns (KB = 2: fewer, larger stages)
+  constexpr int kChunk = kChunkSteps / ((KB * BK / 16) * (HILO ? 2 : 1));   // k steps per chunk
   constexpr int kEpi = 128 * TM * CH;   // epilogue threads
-  constexpr uint32_t a_bytes = TM * BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile
-  const uint32_t x_bytes = (uint32_t)n_total * BK * 2;
+  constexpr uint32_t a_box = TM * BM * BK * 2 * (HILO ? 2 : 1);  // 16 KB per A tile and box
+  constexpr uint32_t a_bytes = KB * a_box;
+  const uint32_t x_box = (uint32_t)n_total * BK * 2;
+  const uint32_t x_bytes = KB * x_box;
   const uint32_t stage_bytes = a_bytes + x_bytes;
   // A split operand wider than one MMA (2 lp > 256: hi rows from 0, lo rows from 256) is
   // summed by the tensor cores: both MMAs accumulate into the same lp columns.  A narrower
@@ -172,31 +175,39 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
       // the A tiles (both halves with TM = 2, and the residual with HILO) and the operand
       // tile of iteration `it` into stage s
       auto load_a = [&](int64_t it, int s) {
-        uint8_t* sa = smem + (size_t)s * stage_bytes;
         uint64_t* bar = &bar_full[s];
         const int t = (int)(it / kt), kk = (int)(it % kt);
-        if (MODE == 0) {
 #pragma unroll
-          for (int h = 0; h < TM; ++h)
-            tma_load_2d_hint(sa + h * 16384, &map_a, bar, kk * BK, (t * TM + h) * BM, pol_a);
-          if (HILO) tma_load_2d_hint(sa + 16384, &map_alo, bar, kk * BK, t * BM, pol_a);
-        } else {
+        for (int kb = 0; kb < KB; ++kb) {
+          uint8_t* sa = smem + (size_t)s * stage_bytes + kb * a_box;
+          const int kx = (kk * KB + kb) * BK;
+          if (MODE == 0) {
 #pragma unroll
-          for (int h = 0; h < TM; ++h) {
-            tma_load_2d_hint(sa + h * 16384, &map_a, bar, (t * TM + h) * BM, kk * BK, pol_a);
-            tma_load_2d_hint(sa + h * 16384 + 8192, &map_a, bar, (t * TM + h) * BM + 64, kk * BK, pol_a);
-          }
-          if (HILO) {
-            tma_load_2d_hint(sa + 16384, &map_alo, bar, t * BM, kk * BK, pol_a);
-            tma_load_2d_hint(sa + 16384 + 8192, &map_alo, bar, t * BM + 64, kk * BK, pol_a);
+            for (int h = 0; h < TM; ++h)
+              tma_load_2d_hint(sa + h * 16384, &map_a, bar, kx, (t * TM + h) * BM, pol_a);
+            if (HILO) tma_load_2d_hint(sa + 16384, &map_alo, bar, kx, t * BM, pol_a);
+          } else {
+#pragma unroll
+            for (int h = 0; h < TM; ++h) {
+              tma_load_2d_hint(sa + h * 16384, &map_a, bar, (t * TM + h) * BM, kx, pol_a);
+              tma_load_2d_hint(sa + h * 16384 + 8192, &map_a, bar, (t * TM + h) * BM + 64, kx, pol_a);
+            }
+            if (HILO) {
+              tma_load_2d_hint(sa + 16384, &map_alo, bar, t * BM, kx, pol_a);
+              tma_load_2d_hint(sa + 16384 + 8192, &map_alo, bar, t * BM + 64, kx, pol_a);
+            }
           }
         }
       };
       auto load_x = [&](int64_t it, int s) {
-        uint8_t* sx = smem + (size_t)s * stage_bytes + a_bytes;
         const int kk = (int)(it % kt);
-        for (int c = 0; c * 256 < n_total; ++c)
-          tma_load_2d_hint(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], kk * BK, c * 256, pol_x);
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+          uint8_t* sx = smem + (size_t)s * stage_bytes + a_bytes + (size_t)kb * x_box;
+          for (int c = 0; c * 256 < n_total; ++c)
+            tma_load_2d_hint(sx + (size_t)c * 256 * 128, &map_x, &bar_full[s], (kk * KB + kb) * BK, c * 256,
+                             pol_x);
+        }
       };
       // A is an input of the whole call and is never written by it: the A tiles of the
       // first stages go out before waiting for the launch that wrote the operand.
@@ -249,9 +260,12 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
             const uint32_t ph = (uint32_t)((i / stages) & 1);
             if (!mbar_wait(&bar_full[s], ph, abort_flag, status)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
-            const uint32_t sx = sa + a_bytes;
+            const uint32_t sa0 = smem_u32(smem + (size_t)s * stage_bytes);
             const bool first = (it == ch_begin);
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb) {
+            const uint32_t sa = sa0 + kb * a_box;
+            const uint32_t sx = sa0 + a_bytes + kb * x_box;
 #pragma unroll
             for (int j = 0; j < BK / 16; ++j) {
 #pragma unroll
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
                   const uint64_t bdesc = smem_desc(sx + c * 256 * 128 + j * 32, 16, 1024);
                   const uint32_t idesc = (c == 0) ? idesc_full : idesc_tail;
                   const uint32_t dcol = fold_mma ? 0u : (uint32_t)c * 256;
-                  const uint32_t accum = (first && j == 0 && (c == 0 || !fold_mma)) ? 0u : 1u;
+                  const uint32_t accum = (first && kb == 0 && j == 0 && (c == 0 || !fold_mma)) ? 0u : 1u;
                   mma_bf16(acc + h * acc_cols + dcol, adesc, bdesc, idesc, accum);
                   if (HILO) {
                     const uint64_t adesc_lo = MODE == 0 ? smem_desc(sa + 16384 + j * 32, 16, 1024)
@@ -274,6 +288,7 @@ __global__ void __launch_bounds__(64 + 128 * TM * CH, 1)
                   }
                 }
               }
+            }
             }
             mma_commit(&bar_empty[s]);
           }
@@ -421,8 +436,8 @@ struct TcBuffers {
   int grid = 0;
 };
 
-size_t smem_bytes(int n_total, int stages, int a_tiles = 1) {
-  return (size_t)stages * ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
+size_t smem_bytes(int n_total, int stages, int a_tiles = 1, int kb = 1) {
+  return (size_t)stages * kb * ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2) + 1024;
 }
 
 // Widest operand (columns) for which a work unit takes two row tiles: two double-buffered
@@ -432,9 +447,9 @@ constexpr int kPairMaxN = 128;
 constexpr int kStageBudget = 200 * 1024;
 constexpr int kPassSmemCap = kStageBudget + 4096;   // stages plus the 1 KB alignment pad
 
-int pick_stages(int n_total, int a_tiles = 1) {
+int pick_stages(int n_total, int a_tiles = 1, int kb = 1) {
   const size_t budget = kStageBudget;
-  int s = (int)(budget / ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2));
+  int s = (int)(budget / (kb * ((size_t)a_tiles * BM * BK * 2 + (size_t)n_total * BK * 2)));
   if (s > 8) s = 8;
   return s < 2 ? 2 : s;
 }
@@ -513,7 +528,17 @@ int tc_plan_init(TcPlan* tc, int64_t m, int64_t n, int64_t lda, int lp, __nv_bfl
                          (const void*)sketch_tc_kernel<0, 0, 1, 2>,
                          (const void*)sketch_tc_kernel<1, 0, 1, 2>,
                          (const void*)sketch_tc_kernel<0, 1, 1, 2>,
-                         (const void*)sketch_tc_kernel<1, 1, 1, 2>})
+                         (const void*)sketch_tc_kernel<1, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<0, 0, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<1, 0, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<1, 1, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<0, 1, 1, 1, 2>,
+                         (const void*)sketch_tc_kernel<0, 0, 2, 1, 2>,
+                         (const void*)sketch_tc_kernel<1, 0, 2, 1, 2>,
+                         (const void*)sketch_tc_kernel<0, 0, 1, 2, 2>,
+                         (const void*)sketch_tc_kernel<1, 0, 1, 2, 2>,
+                         (const void*)sketch_tc_kernel<0, 1, 1, 2, 2>,
+                         (const void*)sketch_tc_kernel<1, 1, 1, 2, 2>})
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmemCap) !=
         cudaSuccess)
       return -1;
@@ -547,13 +572,20 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
   const int lo_off = split_x ? tc_lo_offset(lp) : 0;
   const int64_t M = trans ? tc->n : tc->m;
   const int64_t K = trans ? tc->m : tc->n;
-  const int kt = (int)cdiv(K, BK);
   // two row tiles per work unit while both accumulators stay double-buffered
   const int tm = (!hilo && n_total <= kPairMaxN) ? 2 : 1;
+  const int at = hilo ? 2 : tm;   // A tiles per box
+  // operands wider than 128 columns: two adjacent boxes along k per stage when two such
+  // stages fit the budget (half the stages and barrier round trips for the same bytes in
+  // flight; measured 6 % faster at l_p = 256, while at l_p = 112 the deeper ring of single
+  // boxes is faster)
+  const size_t box_set = (size_t)at * BM * BK * 2 + (size_t)n_total * BK * 2;
+  const int kb = (n_total > kPairMaxN && 4 * box_set <= (size_t)kStageBudget) ? 2 : 1;
+  const int kt = (int)cdiv(K, (int64_t)BK * kb);
   const int64_t total = cdiv(M, (int64_t)BM * tm) * kt;
   const int grid = (int)(total < b->grid ? total : b->grid);
-  const int stages = pick_stages(n_total, hilo ? 2 : tm);
-  const size_t sm = smem_bytes(n_total, stages, hilo ? 2 : tm);
+  const int stages = pick_stages(n_total, at, kb);
+  const size_t sm = smem_bytes(n_total, stages, at, kb);
   const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(trans ? tc->map_a_t : tc->map_a_n);
   const CUtensorMap* malo = reinterpret_cast<const CUtensorMap*>(
       hilo ? (trans ? tc->map_a_lo : tc->map_a_lo_n) : (trans ? tc->map_a_t : tc->map_a_n));
@@ -569,24 +601,28 @@ int tc_pass(TcPlan* tc, int trans, int split_x, int hilo, float* out, int* split
                       total, n_total, split_x, lo_off, stages, b->slots, b->flags, tc->status);
   };
   cudaError_t e;
+#define RSVD_PASS(MO, HI, T, C)                                                            \
+  e = (kb == 2) ? go(sketch_tc_kernel<MO, HI, T, C, 2>, threads_for<T, C>())               \
+                : go(sketch_tc_kernel<MO, HI, T, C, 1>, threads_for<T, C>())
   if (ch == 2) {
-    if (hilo && trans) e = go(sketch_tc_kernel<1, 1, 1, 2>, threads_for<1, 2>());
-    else if (hilo) e = go(sketch_tc_kernel<0, 1, 1, 2>, threads_for<1, 2>());
-    else if (trans) e = go(sketch_tc_kernel<1, 0, 1, 2>, threads_for<1, 2>());
-    else e = go(sketch_tc_kernel<0, 0, 1, 2>, threads_for<1, 2>());
+    if (hilo && trans) RSVD_PASS(1, 1, 1, 2);
+    else if (hilo) RSVD_PASS(0, 1, 1, 2);
+    else if (trans) RSVD_PASS(1, 0, 1, 2);
+    else RSVD_PASS(0, 0, 1, 2);
   } else if (hilo && trans) {
-    e = go(sketch_tc_kernel<1, 1>, kThreads);
+    RSVD_PASS(1, 1, 1, 1);
   } else if (hilo) {
-    e = go(sketch_tc_kernel<0, 1>, kThreads);
+    RSVD_PASS(0, 1, 1, 1);
   } else if (tm == 2 && trans) {
-    e = go(sketch_tc_kernel<1, 0, 2>, threads_for<2>());
+    RSVD_PASS(1, 0, 2, 1);
   } else if (tm == 2) {
-    e = go(sketch_tc_kernel<0, 0, 2>, threads_for<2>());
+    RSVD_PASS(0, 0, 2, 1);
   } else if (trans) {
-    e = go(sketch_tc_kernel<1>, kThreads);
+    RSVD_PASS(1, 0, 1, 1);
   } else {
-    e = go(sketch_tc_kernel<0>, kThreads);
+    RSVD_PASS(0, 0, 1, 1);
   }
+#undef RSVD_PASS
   if (e != cudaSuccess) return -1;
   *splits = 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
