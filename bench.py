@@ -630,12 +630,105 @@ def run_table_7_1(pkg, steps, warmup):
             "results": rows}
 
 
+def _spec_norm(apply, n, iters=30, seed=5):
+    """Largest eigenvalue of the symmetric positive semidefinite operator x -> apply(x) (n
+    columns in), by power iteration on the device in float32."""
+    import torch
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    x = torch.randn(n, 1, generator=g, device="cuda")
+    s = 0.0
+    for _ in range(iters):
+        y = apply(x)
+        s = float(torch.linalg.vector_norm(y))
+        x = y / max(s, 1e-30)
+    return s
+
+
+def run_algorithms(pkg, steps, warmup):
+    """The paper's other algorithms at the C2 size (16384 x 16384, bfloat16 A, sigma_j = j^-1.5):
+    the adaptive range finder (Algorithm 4.2 blocked, eps = 0.1 ||A||, blocks of 16), the
+    Hermitian Stage B (Algorithms 5.3 and 5.5 on the psd A = V diag(j^-1.5) V^T), and Stage B
+    by row extraction (Algorithm 5.2) beside Algorithm 5.1 on the same basis; per call the
+    passes over A and the bytes of A they read (2mn each) over the time."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    w = synth.C2
+    n = w.m
+    out = {}
+    A32 = synth.device_lowrank(n, n, w.sigma(), w.matrix_seed)
+    Ab = A32.to(torch.bfloat16)
+    a_bytes = 2.0 * n * n
+    # adaptive range finder
+    eps, block, cap = 0.2 * float(w.sigma()[0]), 16, 128
+    with pkg.Plan(n, n, 112, 16, 0, w.omega_seed, pkg.RSVD_BF16_TC) as pl:
+        Q = torch.zeros(n, cap, device="cuda")
+        res = {}
+        ms = _events_ms(lambda: res.update(r=pkg.rsvd_range_finder_adaptive(pl.handle, Ab, eps, block, Q, cap)),
+                        steps, warmup)
+        rank, est = res["r"]
+        passes = rank // block + 1
+        qk = Q[:, :rank]
+        # ||(I - Q Q^T) A||_2 = sqrt(lambda_max(A^T (I - Q Q^T) A))
+        err = _spec_norm(lambda x: A32.T @ (lambda y: y - qk @ (qk.T @ y))(A32 @ x), n) ** 0.5
+    out["adaptive_range_finder"] = {
+        "ms": round(ms, 4), "eps": eps, "block": block, "rank": rank, "estimate": est,
+        "error_spectral": round(err, 6), "guarantee_met": err <= eps, "passes_over_A": passes,
+        "A_bytes_per_ms": round(passes * a_bytes / ms / 1e6, 1),
+        "note": "the stopping test reads one float per block on the host (it steers the loop)"}
+    # Hermitian Stage B
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.matrix_seed + 7)
+    V = synth.device_haar(n, 1024, g, "cuda")
+    lam = torch.as_tensor(w.sigma()[:1024].astype(np.float32), device="cuda")
+    S32 = (V * lam) @ V.T
+    S32 = 0.5 * (S32 + S32.T)
+    Sb = S32.to(torch.bfloat16)
+    del V
+    for name, method in (("eig_direct", pkg.RSVD_EIG_DIRECT), ("eig_nystrom", pkg.RSVD_EIG_NYSTROM)):
+        with pkg.Plan(n, n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_BF16_TC) as pl:
+            U = torch.zeros(n, w.k, device="cuda")
+            L = torch.zeros(w.k, device="cuda")
+            ms = _events_ms(lambda: pkg.rsvd_eig(pl.handle, Sb, method, U, L), steps, warmup)
+            pkg._check(pkg.rsvd_sync(pl.handle), name)
+        e = float(torch.linalg.matrix_norm(S32.double() - (U.double() * L.double()) @ U.double().T))
+        passes = 2 * w.q + 2
+        out[name] = {"ms": round(ms, 4), "rel_err_F": round(e / float(torch.linalg.matrix_norm(S32.double())), 6),
+                     "lambda_1": round(float(L[0]), 6), "passes_over_A": passes,
+                     "A_bytes_per_ms": round(passes * a_bytes / ms / 1e6, 1)}
+    del S32, Sb
+    # row extraction beside Algorithm 5.1
+    for name, fn, passes in (("svd_alg_5_1", pkg.rsvd_svd, 2 * w.q + 2),
+                             ("svd_row_extraction_alg_5_2", pkg.rsvd_svd_row_extraction, 2 * w.q + 1)):
+        with pkg.Plan(n, n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_BF16_TC) as pl:
+            U = torch.zeros(n, w.k, device="cuda")
+            S = torch.zeros(w.k, device="cuda")
+            Vv = torch.zeros(n, w.k, device="cuda")
+            ms = _events_ms(lambda: fn(pl.handle, Ab, U, S, Vv), steps, warmup)
+            pkg._check(pkg.rsvd_sync(pl.handle), name)
+            pkg.rsvd_profile(pl.handle, (1 << pkg.RSVD_NUM_STEPS) - 1)
+            fn(pl.handle, Ab, U, S, Vv)
+            torch.cuda.synchronize()
+            stage_ms, _ = pkg.rsvd_profile_read(pl.handle)
+            pkg.rsvd_profile(pl.handle, 0)
+        out[name] = {"ms": round(ms, 4), "rel_err_vs_fp32_A": round(_rel_err(A32, U, S, Vv), 6),
+                     "passes_over_A": passes, "stages_ms": {k2: round(v, 4) for k2, v in stage_ms.items() if v > 0}}
+    return {"metric": "the paper's other algorithms at 16384 x 16384 (bf16 tensor cores), ms per call",
+            "config": {"m": n, "n": n, "k": w.k, "p": w.p, "q": w.q, "spectrum": "j^-1.5"},
+            "results": out}
+
+
 def run_workload(args):
     """Secondary workloads (one JSON line each; not the headline metric):
     c3 -- 262144 x 4096, single-pass (Section 5.5) vs q = 2 multi-pass, k = 64, p = 16;
     c4 -- 32768 x 32768, SRFT (Section 4.6) vs Gaussian test matrix, k = 236, p = 20, q = 1;
     c5 -- 512 matrices m ~ U[128, 2048], n ~ U[64, 1024], batched forward and backward;
-    t71 -- the Section 7.4 timing sweep (Table 7.1) with gauss and the modified SRFT."""
+    t71 -- the Section 7.4 timing sweep (Table 7.1) with gauss and the modified SRFT;
+    algos -- the adaptive range finder, Hermitian Stage B and row extraction at 16384^2."""
     import torch
 
     import __graft_entry__
@@ -693,6 +786,8 @@ def run_workload(args):
                     "config": {"m": w.m, "n": w.n, "k": w.k, "p": w.p}, "results": res})
     elif args.workload == "t71":
         out.update(run_table_7_1(pkg, steps, warmup))
+    elif args.workload == "algos":
+        out.update(run_algorithms(pkg, steps, warmup))
     elif args.workload == "c5":
         shapes = synth.c5_shapes()
         if args.profile_run and os.path.exists(cache):
@@ -785,9 +880,10 @@ def main():
                     help="three launches of the tensor-core pass kernel (each mode) on an 8192 x 16384 "
                          "A stored as bf16 hi + lo (537 MB, larger than L2): the small case for "
                          "full ncu captures")
-    ap.add_argument("--workload", choices=("c2", "c3", "c4", "c5", "t71"), default="c2",
+    ap.add_argument("--workload", choices=("c2", "c3", "c4", "c5", "t71", "algos"), default="c2",
                     help="c2 (default) is the headline line; c3/c4/c5 print one secondary line "
-                         "each; t71 is the timing experiment of Section 7.4 (Table 7.1)")
+                         "each; t71 is the timing experiment of Section 7.4 (Table 7.1); algos "
+                         "times the adaptive range finder, the Hermitian Stage B and row extraction")
     args = ap.parse_args()
     if args.workload != "c2" and args.impl == "ours":
         run_workload(args)

@@ -3,8 +3,9 @@
 // 3.3.2, applied to the rows), and the gathers of Algorithm 5.2.
 //
 // id_pivot_kernel: one cooperative launch, one CTA per SM, each CTA owning a contiguous
-// slice of rows of the residual R (initially Y, updated in place in global memory: it is
-// read and written once per step, from L2 at the sizes of the path).  Step i:
+// slice of rows of the residual R (initially Y).  The slice lives in shared memory while it
+// fits (192 KB: m up to about 250 000 rows at l_p = 112 over 152 CTAs), a thread per row;
+// beyond that it is updated in place in global memory, a warp per row.  Step i:
 //   1. every CTA publishes its longest residual row (squared norm, index, the row) in a
 //      double-buffered candidate slot and arrives at a grid barrier (a monotonic counter,
 //      bounded spin);
@@ -24,6 +25,7 @@ namespace {
 constexpr int kIdThreads = 512;
 constexpr int kIdWarps = kIdThreads / 32;
 constexpr uint32_t kIdSpinLimit = 1u << 22;   // grid-barrier polls (about 0.4 s with the sleeps)
+constexpr size_t kIdSliceMax = 192 * 1024;      // largest slice of rows kept in shared memory
 
 __device__ __forceinline__ bool id_better(float n1, int r1, float n2, int r2) {
   return n1 > n2 || (n1 == n2 && r1 >= 0 && (r2 < 0 || r1 < r2));
@@ -36,6 +38,9 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned* p) {
 }
 
 // cand: 2 x grid slots of (4 + lp) floats: [squared norm, row index (int bits), 0, 0, row].
+// SM: the CTA's slice of the residual lives in shared memory for the whole kernel (loaded
+// from res at the start; res is then left as it was), else in res itself.
+template <bool SM>
 __global__ void __launch_bounds__(kIdThreads, 1) id_pivot_kernel(
     float* __restrict__ res, int64_t m, int l, int lp, float* __restrict__ coef,
     int* __restrict__ piv, float* __restrict__ cand, unsigned* __restrict__ bar,
@@ -51,12 +56,21 @@ __global__ void __launch_bounds__(kIdThreads, 1) id_pivot_kernel(
   const int64_t r0 = min(m, (int64_t)b * chunk), r1 = min(m, r0 + chunk);
   const int nper = (lp + 31) / 32;   // elements of a row per lane (lp <= 256: at most 8)
   const int64_t slot_sz = 4 + lp;
+  extern __shared__ __align__(16) float rows_sm[];
+  // row r of the slice (r0 <= r < r1); in shared memory rows are padded to lp + 1 floats so
+  // that a thread per row reads them without bank conflicts
+  const int lds = lp + 1;
+  auto rowp = [&](int64_t r) -> float* { return SM ? rows_sm + (r - r0) * lds : res + r * lp; };
+  if (SM) {
+    for (int64_t e = tid; e < (r1 - r0) * lp; e += kIdThreads) rows_sm[(e / lp) * lds + e % lp] = res[r0 * lp + e];
+    __syncthreads();
+  }
 
   // squared norms of the slice and its longest row
   float bn = -1.0f;
   int br = -1;
   for (int64_t r = r0 + warp; r < r1; r += kIdWarps) {
-    const float* row = res + r * lp;
+    const float* row = rowp(r);
     float s = 0.0f;
     for (int e = 0; e < nper; ++e) {
       const int c = lane + 32 * e;
@@ -82,7 +96,7 @@ __global__ void __launch_bounds__(kIdThreads, 1) id_pivot_kernel(
     // 1. publish this slice's candidate
     float* slot = cand + ((int64_t)(i & 1) * G + b) * slot_sz;
     const int myr = s_best_r;
-    for (int c = tid; c < lp; c += kIdThreads) slot[4 + c] = myr >= 0 ? res[(int64_t)myr * lp + c] : 0.0f;
+    for (int c = tid; c < lp; c += kIdThreads) slot[4 + c] = myr >= 0 ? rowp(myr)[c] : 0.0f;
     if (tid == 0) {
       slot[0] = s_best_n;
       slot[1] = __int_as_float(myr);
@@ -107,13 +121,22 @@ __global__ void __launch_bounds__(kIdThreads, 1) id_pivot_kernel(
     // 2. the winner, the same in every CTA
     const float* slots = cand + (int64_t)(i & 1) * G * slot_sz;
     if (warp == 0) {
+      // every lane's headers (grid <= 256: at most 8) loaded together, then compared
+      float hn[8];
+      int hr[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = lane + 32 * q;
+        const float2 h = c < G ? __ldcg(reinterpret_cast<const float2*>(slots + (int64_t)c * slot_sz))
+                               : make_float2(-1.0f, __int_as_float(-1));
+        hn[q] = h.x;
+        hr[q] = __float_as_int(h.y);
+      }
       float n = -1.0f;
       int r = -1, sl = -1;
-      for (int c = lane; c < G; c += 32) {
-        const float cn = __ldcg(slots + (int64_t)c * slot_sz);
-        const int cr = __float_as_int(__ldcg(slots + (int64_t)c * slot_sz + 1));
-        if (cr >= 0 && id_better(cn, cr, n, r)) { n = cn; r = cr; sl = c; }
-      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (hr[q] >= 0 && id_better(hn[q], hr[q], n, r)) { n = hn[q]; r = hr[q]; sl = lane + 32 * q; }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float on = __shfl_xor_sync(0xffffffffu, n, o);
@@ -145,8 +168,40 @@ __global__ void __launch_bounds__(kIdThreads, 1) id_pivot_kernel(
     // 3. project v out of the slice, record the coefficients, find the next candidate
     bn = -1.0f;
     br = -1;
-    for (int64_t r = r0 + warp; r < r1; r += kIdWarps) {
-      float* row = res + r * lp;
+    if (SM) {   // a thread per row
+      for (int64_t r = r0 + tid; r < r1; r += kIdThreads) {
+        float* row = rowp(r);
+        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+        for (int c = 0; c < lp; c += 4) {   // lp is a multiple of 16
+          d0 = fmaf(row[c], v[c], d0);
+          d1 = fmaf(row[c + 1], v[c + 1], d1);
+          d2 = fmaf(row[c + 2], v[c + 2], d2);
+          d3 = fmaf(row[c + 3], v[c + 3], d3);
+        }
+        const float d = (d0 + d1) + (d2 + d3);
+        coef[r * lp + i] = d;
+        const bool win = (r == wrow);
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int c = 0; c < lp; c += 2) {
+          const float y0 = win ? 0.0f : fmaf(-d, v[c], row[c]);
+          const float y1 = win ? 0.0f : fmaf(-d, v[c + 1], row[c + 1]);
+          row[c] = y0;
+          row[c + 1] = y1;
+          s0 = fmaf(y0, y0, s0);
+          s1 = fmaf(y1, y1, s1);
+        }
+        const float sq = s0 + s1;
+        if (sq > 0.0f && id_better(sq, (int)r, bn, br)) { bn = sq; br = (int)r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {   // the warp's best row
+        const float on = __shfl_xor_sync(0xffffffffu, bn, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (orr >= 0 && id_better(on, orr, bn, br)) { bn = on; br = orr; }
+      }
+    }
+    for (int64_t r = SM ? r1 : r0 + warp; r < r1; r += kIdWarps) {
+      float* row = rowp(r);
       float x[8];
       float d = 0.0f;
 #pragma unroll
@@ -246,9 +301,18 @@ __global__ void gather_rows_t_kernel(const void* __restrict__ A, int64_t lda, in
 
 cudaError_t launch_id_pivot(float* res, int64_t m, int l, int lp, float* coef, int* piv, float* cand,
                             unsigned* bar, uint32_t* status, int grid, cudaStream_t st) {
-  if (grid < 1 || l > kMaxL || lp > kMaxL) return cudaErrorInvalidValue;
+  if (grid < 1 || grid > 256 || l > kMaxL || lp > kMaxL) return cudaErrorInvalidValue;
   void* args[] = {&res, &m, &l, &lp, &coef, &piv, &cand, &bar, &status};
-  return cudaLaunchCooperativeKernel((void*)id_pivot_kernel, dim3(grid), dim3(kIdThreads), args, 0, st);
+  // the slice in shared memory when it fits beside the kernel's own arrays
+  const size_t slice = (size_t)cdiv(m, grid) * (lp + 1) * sizeof(float);
+  if (slice <= kIdSliceMax) {
+    cudaError_t e = cudaFuncSetAttribute(id_pivot_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kIdSliceMax);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((void*)id_pivot_kernel<true>, dim3(grid), dim3(kIdThreads), args, slice,
+                                       st);
+  }
+  return cudaLaunchCooperativeKernel((void*)id_pivot_kernel<false>, dim3(grid), dim3(kIdThreads), args, 0, st);
 }
 
 size_t id_cand_floats(int grid, int lp) { return (size_t)2 * grid * (4 + lp); }
