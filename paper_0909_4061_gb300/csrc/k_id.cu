@@ -4,7 +4,7 @@
 //
 // id_pivot_kernel: one cooperative launch, one CTA per SM, each CTA owning a contiguous
 // slice of rows of the residual R (initially Y).  The slice lives in shared memory while it
-// fits (192 KB: m up to about 250 000 rows at l_p = 112 over 152 CTAs), a thread per row;
+// fits (192 KB: m up to about 66 000 rows at l_p = 112 over 152 CTAs), a thread per row;
 // beyond that it is updated in place in global memory, a warp per row.  Step i:
 //   1. every CTA publishes its longest residual row (squared norm, index, the row) in a
 //      double-buffered candidate slot and arrives at a grid barrier (a monotonic counter,
