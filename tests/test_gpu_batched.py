@@ -133,3 +133,42 @@ def test_batched_graph_replay_and_autotuner(rsvd_lib, tmp_path, monkeypatch):
         pl2.svd(mats)
         assert pl2.tuning() == t
         pl2.sync()
+
+
+def test_batched_full_c5_batch(rsvd_lib):
+    """The timed batched configuration itself: 512 matrices of the C5 shapes (m ~ U[128, 2048],
+    n ~ U[64, 1024]), k = 16, p = 8, q = 1, built on the device as the bench builds them.
+    Sixteen matrices (the first eight and eight spread over the batch) are checked against
+    the oracle: the forward with the acceptance of the tests above, the backward against
+    autograd through the oracle's float64 steps with the same tolerance rule."""
+    from oracle import grad
+
+    pkg = rsvd_lib
+    shapes = synth.c5_shapes()
+    k, p, q, seed = synth.C5_K, synth.C5_P, synth.C5_Q, synth.C5_OMEGA_SEED
+    mats = []
+    for b, (m, n) in enumerate(shapes):
+        a = synth.device_lowrank(m, n, synth.spectrum_exp(min(m, n), 4.0), synth.C5_MATRIX_SEED * 100003 + b)
+        t = torch.zeros(m, -(-n // 8) * 8, dtype=torch.bfloat16, device="cuda")
+        t[:, :n] = a.to(torch.bfloat16)
+        mats.append(t)
+    with pkg.BatchedPlan(shapes, k, p, q, seed=seed) as pl:
+        U, S, V = pl.svd(mats)
+        grads = pl.backward(mats)
+        sweeps = pl.sync()
+        u_all, s_all, v_all = U.cpu().double().numpy(), S.cpu().double().numpy(), V.cpu().double().numpy()
+        rm, rn = pl.row_m, pl.row_n
+    assert 0 < sweeps < 40
+    picks = list(range(8)) + list(range(40, len(shapes), (len(shapes) - 40) // 8))[:8]
+    for b in picks:
+        m, n = shapes[b]
+        a64 = mats[b][:, :n].double().cpu().numpy()
+        om = philox.gaussian(seed + b, 0, n, k + p)
+        _check_ritz(a64, u_all[rm[b]:rm[b + 1]], s_all[b], v_all[rn[b]:rn[b + 1]], k, p, q, om)
+        omb = _omega_bf16(pkg, seed + b, n, k + p)
+        g_ref = grad.grad_autograd(a64, k, p, q, omb)
+        g = grads[b].double().cpu().numpy()
+        rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+        chain = np.linalg.norm(g_ref - grad.grad_exact_svd(a64, k)) / np.linalg.norm(g_ref)
+        tol = 1e-4 + 20 * 2.0 ** -24 * np.linalg.cond(a64 @ omb) * chain
+        assert rel <= tol, (b, rel, tol)
