@@ -5,7 +5,7 @@ design, run on the stored bfloat16 A with the same test matrix).
   * C4: 32768 x 32768, sigma_j = j^-0.5, k = 236, p = 20, q = 1; Gaussian and SRFT test
     matrices (the SRFT's Omega is the oracle's explicit real SRFT of the same draws).
   * C3: 262144 x 4096, sigma_j = max(e^-(j-1)/20, 1e-6) + N(0, 1e-8) noise, k = 64, p = 16,
-    the q = 2 multi-pass form.
+    the q = 2 multi-pass form, and the single pass against oracle.single_pass.
 
 What remains between the GPU and the oracle is float32 arithmetic, held to the library's
 float32 targets: |sigma_j - sigma_j^ref| <= 1e-5 sigma_1, and after sign alignment
@@ -85,3 +85,45 @@ def test_c3_multi_pass_full_size(rsvd_lib):
     um, sm, vm, _ = mixed.rsvd(a64, w.l, 0, q, om)
     del a64
     _check(u, s, v, um, sm, vm, w.k)
+
+
+def test_c3_single_pass_full_size(rsvd_lib):
+    """The single pass (Section 5.5) at the full C3 size against oracle.single_pass on the
+    library's own Omega and Psi (read back through the C ABI, bfloat16 as the passes use
+    them): singular values within 2 u32 (kappa(X1)^2 + kappa(X2)^2) sigma_1 (the first-order
+    bound of tests/test_gpu_single_pass.py), and the relative reconstruction error within
+    2 % of the oracle's."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_gpu_single_pass import U32, _oracle, psi_cols
+
+    pkg = rsvd_lib
+    w = synth.C3
+    A = synth.device_lowrank(w.m, w.n, w.sigma(), w.matrix_seed, noise_std=w.noise_std()).to(torch.bfloat16)
+    with pkg.Plan(w.m, w.n, w.k, w.p, 0, w.omega_seed, pkg.RSVD_BF16_TC, single_pass=1) as pl:
+        U, S, V = pl.svd(A)
+        om = torch.zeros(w.n, w.l, device="cuda")
+        pkg.rsvd_get_omega(pl.handle, om)
+        assert pkg.rsvd_sync(pl.handle) == pkg.RSVD_OK
+    lt = psi_cols(w.m, w.n, w.l)
+    psi = torch.zeros(w.m, lt, device="cuda")
+    pkg.rsvd_draw_gaussian(w.omega_seed, 1, w.m, lt, psi, lt)
+    torch.cuda.synchronize()
+    u, s, v = _np(U), _np(S), _np(V)
+    om64 = _np(om.to(torch.bfloat16))
+    psi64 = _np(psi.to(torch.bfloat16))
+    a64 = _np(A)
+    del A, psi
+    torch.cuda.empty_cache()
+    ur, sr, vr, sb, kap = _oracle(a64, w.k, om64, psi64)
+    tol = 2 * U32 * kap * sr[0]
+    err = np.max(np.abs(s - sr))
+    e_gpu = metrics.fro_error_onepass(a64, u, s, v)
+    e_ref = metrics.fro_error_onepass(a64, ur, sr, vr)
+    na = float(np.sqrt(np.sum(a64 * a64)))
+    print(f"C3 single pass: max dsigma / sigma_1 {err / sr[0]:.2e} (tol {tol / sr[0]:.2e}), "
+          f"relative error {e_gpu / na:.4f} (oracle {e_ref / na:.4f})")
+    assert err <= tol
+    assert abs(e_gpu - e_ref) <= 0.02 * e_ref
