@@ -339,27 +339,34 @@ rsvd_status_t to_operand(rsvd_batched_plan_t P, const float* q, bool m_side, int
 rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, float* S, float* V) {
   (void)A;
   const int64_t ldx = std::max(P->xm_total, P->xn_total);
+  // A basis that only feeds the next pass needs to span its sample, not to be orthonormal to
+  // working precision: it gets the shifted round and one plain one, final bases every round
+  // (the rule of the single-matrix path).
   const int rounds = P->opt.orth_rounds;
+  const int rounds_mid = std::min(rounds, 2);
+  const int shift = rounds >= 3 ? 1 : 0;
   BTRY(launch_batched_draw(P->seed, P->d_roff_n, P->nb, P->sum_n, P->l, P->omega, P->xbf, ldx,
                            P->d_xoff_n, P->st));
   BTRYS(bpass(P, 0, 0, P->ym));                                                  // Y_0 = A Omega
-  BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, rounds, P->rm[0], P->rinv,
-                               P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status, P->st));
+  BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, P->q == 0 ? rounds : rounds_mid, shift,
+                             P->rm[0], P->rinv, P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status,
+                             P->st));
   for (int j = 1; j <= P->q; ++j) {
     BTRYS(to_operand(P, P->qm[j - 1], true, 1));
     BTRYS(bpass(P, 1, 1, P->yn));                                                // A^T Q_{j-1}
-    BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds, P->rn[j - 1], P->rinv,
-                               P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
+    BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds_mid, shift, P->rn[j - 1],
+                               P->rinv, P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
     BTRYS(to_operand(P, P->qn[j - 1], false, 1));
     BTRYS(bpass(P, 0, 1, P->ym));                                                // A Qt_j
-    BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, rounds, P->rm[j], P->rinv,
-                               P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status, P->st));
+    BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, j == P->q ? rounds : rounds_mid, shift,
+                               P->rm[j], P->rinv, P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status,
+                               P->st));
   }
   float* Q = P->qm[P->q];
   BTRYS(to_operand(P, Q, true, 1));
   BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
-  BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, P->rb, P->rinv,
-                               P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
+  BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, shift, P->rb, P->rinv,
+                             P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
   BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
   if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->max_m, P->ub, P->k, P->k, U, P->k, P->st));
   if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, P->k, P->k, V, P->k, P->st));

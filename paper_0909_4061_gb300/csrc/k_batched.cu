@@ -304,57 +304,80 @@ __device__ __forceinline__ void chol32_warp(const float (*S)[LPB + 1], int l, fl
 constexpr int kUnitRows = 128;
 constexpr int kUnitThreads = 256;
 
+// A unit's rows into shared memory (kUnitThreads threads): every thread's four 16-byte
+// loads are issued before the first store, so they are in flight together.
 __device__ __forceinline__ void bqr_stage(const float* __restrict__ src, int64_t row0, int nr,
                                           float (*ys)[LPB]) {
-  for (int e = threadIdx.x; e < kUnitRows * (LPB / 4); e += blockDim.x) {
-    const int rr = e >> 3;
-    reinterpret_cast<float4*>(&ys[0][0])[e] =
-        rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr int N = kUnitRows * (LPB / 4) / kUnitThreads;
+  float4 v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int e = threadIdx.x + k * kUnitThreads, rr = e >> 3;
+    v[k] = rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+#pragma unroll
+  for (int k = 0; k < N; ++k) reinterpret_cast<float4*>(&ys[0][0])[threadIdx.x + k * kUnitThreads] = v[k];
 }
 
-// Gram partial of the staged rows (256 threads): four row groups of 64 threads, each thread
-// a 4 x 4 block of G over its group's rows (two float4 reads per 16 FMAs), the groups
-// summed in a fixed order through gp (4 x 32 x 32 floats of shared memory).
-__device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, float (*gp)[LPB * LPB],
+// Gram partial of the staged rows (256 threads): only the lower triangle of the l x l
+// block is formed (the factorisation reads no more), as 4 x 4 tiles, L4 = ceil(l / 4) tile
+// rows and L4 (L4 + 1) / 2 tiles; the threads form NG = 256 / tiles row groups (12 at
+// l = 24), each thread one tile over its group's rows (two float4 reads per 16 FMAs).  The
+// groups are summed in a fixed order through gp (NG x tiles x 16 floats, at most 16 KB),
+// and the partial is written whole: zero above the diagonal tiles and beyond l.
+__device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, int l, float* gp,
                                               float* __restrict__ part) {
-  const int grp = threadIdx.x >> 6, gt = threadIdx.x & 63;
-  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  for (int rr = grp; rr < nr; rr += 4) {
-    const float4 a = *reinterpret_cast<const float4*>(&ys[rr][bi]);
-    const float4 c = *reinterpret_cast<const float4*>(&ys[rr][bj]);
-    const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+  const int l4 = (l + 3) >> 2;
+  const int ntile = l4 * (l4 + 1) / 2;
+  const int ng = kUnitThreads / ntile;
+  const int grp = threadIdx.x / ntile, t = threadIdx.x - grp * ntile;
+  if (grp < ng) {
+    int ti = 0, tt = t;
+    while (tt > ti) { tt -= ti + 1; ++ti; }
+    const int bi = 4 * ti, bj = 4 * tt;   // tt <= ti
+    float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int rr = grp; rr < nr; rr += ng) {
+      const float4 a = *reinterpret_cast<const float4*>(&ys[rr][bi]);
+      const float4 c = *reinterpret_cast<const float4*>(&ys[rr][bj]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
+    }
+    float* d = gp + (grp * ntile + t) * 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float4*>(d + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gp[grp][(bi + i) * LPB + bj + j] = acc[i][j];
   __syncthreads();
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x)
-    part[e] = (gp[0][e] + gp[1][e]) + (gp[2][e] + gp[3][e]);
+  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
+    const int i = e >> 5, j = e & 31, ti = i >> 2, tj = j >> 2;
+    float v = 0.0f;
+    if (ti < l4 && tj <= ti) {
+      const int off = (ti * (ti + 1) / 2 + tj) * 16 + (i & 3) * 4 + (j & 3);
+      for (int g = 0; g < ng; ++g) v += gp[g * ntile * 16 + off];
+    }
+    part[e] = v;
+  }
 }
 
 __global__ void __launch_bounds__(kUnitThreads) bqr_gram_kernel(const float* __restrict__ src,
                                                                 const int64_t* __restrict__ roff,
-                                                                const int2* __restrict__ units,
+                                                                const int2* __restrict__ units, int l,
                                                                 float* __restrict__ part) {
   __shared__ __align__(16) float ys[kUnitRows][LPB];
-  __shared__ __align__(16) float gp[4][LPB * LPB];
+  __shared__ __align__(16) float gp[kUnitThreads * 16];
   const int2 u = units[blockIdx.x];
   const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
   bqr_stage(src, row0, nr, ys);
   __syncthreads();
-  bqr_gram_tile(ys, nr, gp, part + (size_t)blockIdx.x * LPB * LPB);
+  bqr_gram_tile(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__ part,
@@ -412,42 +435,56 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
 }
 
 // Q = Y R^-1 over a unit: a warp per row, lane = column, the column of R^-1 in registers
-// and the row of Y read as float4 broadcasts; then the Gram partial of the new rows.
+// and the row of Y read as float4 broadcasts, two rows at a time (four independent FMA
+// chains), the sums running over the l4 = ceil(l / 4) float4 of a row that can be nonzero;
+// then the Gram partial of the new rows.
 __global__ void __launch_bounds__(kUnitThreads) bqr_apply_kernel(const float* __restrict__ src,
                                                                  float* __restrict__ dst,
                                                                  const int64_t* __restrict__ roff,
-                                                                 const int2* __restrict__ units,
+                                                                 const int2* __restrict__ units, int l,
                                                                  const float* __restrict__ rinv,
                                                                  float* __restrict__ part) {
   __shared__ __align__(16) float ys[kUnitRows][LPB];
-  __shared__ __align__(16) float gp[4][LPB * LPB];
+  __shared__ __align__(16) float gp[kUnitThreads * 16];
+  constexpr int NW = kUnitThreads / 32;
   const int2 u = units[blockIdx.x];
   const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l4 = (l + 3) >> 2;
   bqr_stage(src, row0, nr, ys);
   float xr[LPB];
 #pragma unroll
-  for (int i = 0; i < LPB; ++i) xr[i] = rinv[(size_t)u.x * LPB * LPB + i * LPB + lane];   // R^-1(i, lane)
+  for (int i = 0; i < LPB; ++i)
+    xr[i] = i < l ? rinv[(size_t)u.x * LPB * LPB + i * LPB + lane] : 0.0f;   // R^-1(i, lane)
   __syncthreads();
-  for (int rr = warp; rr < nr; rr += kUnitThreads / 32) {
-    const float4* yr = reinterpret_cast<const float4*>(&ys[rr][0]);
-    float v0 = 0.0f, v1 = 0.0f;
+  for (int rr = warp; rr < nr; rr += 2 * NW) {
+    const int rb = rr + NW < nr ? rr + NW : rr;   // the warp's second row (the first again at the end)
+    const float4* ya = reinterpret_cast<const float4*>(&ys[rr][0]);
+    const float4* yb = reinterpret_cast<const float4*>(&ys[rb][0]);
+    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
     for (int i4 = 0; i4 < LPB / 4; ++i4) {
-      const float4 y4 = yr[i4];
-      v0 = fmaf(y4.x, xr[4 * i4], v0);
-      v1 = fmaf(y4.y, xr[4 * i4 + 1], v1);
-      v0 = fmaf(y4.z, xr[4 * i4 + 2], v0);
-      v1 = fmaf(y4.w, xr[4 * i4 + 3], v1);
+      if (i4 < l4) {
+        const float4 p = ya[i4], q = yb[i4];
+        a0 = fmaf(p.x, xr[4 * i4], a0);
+        a1 = fmaf(p.y, xr[4 * i4 + 1], a1);
+        b0 = fmaf(q.x, xr[4 * i4], b0);
+        b1 = fmaf(q.y, xr[4 * i4 + 1], b1);
+        a0 = fmaf(p.z, xr[4 * i4 + 2], a0);
+        a1 = fmaf(p.w, xr[4 * i4 + 3], a1);
+        b0 = fmaf(q.z, xr[4 * i4 + 2], b0);
+        b1 = fmaf(q.w, xr[4 * i4 + 3], b1);
+      }
     }
-    __syncwarp();   // every lane has read the row before it is overwritten
-    ys[rr][lane] = v0 + v1;
+    __syncwarp();   // every lane has read both rows before they are overwritten
+    ys[rr][lane] = a0 + a1;
+    if (rb != rr) ys[rb][lane] = b0 + b1;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * (LPB / 4); e += blockDim.x)
     reinterpret_cast<float4*>(dst + row0 * LPB)[e] = reinterpret_cast<const float4*>(&ys[0][0])[e];
-  if (part) bqr_gram_tile(ys, nr, gp, part + (size_t)blockIdx.x * LPB * LPB);
+  if (part) bqr_gram_tile(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 // basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
@@ -587,35 +624,43 @@ __global__ void __launch_bounds__(256) batched_lift_kernel(const float* __restri
                                                            const float* __restrict__ small, int cols,
                                                            int valid, float* __restrict__ out, int ldo) {
   __shared__ float Ss[LPB][LPB + 1];
+  constexpr int NW = 8;                    // warps (256 threads)
+  constexpr int RPW = kLiftRows / NW;      // rows per warp
   const int b = blockIdx.x;
   const int64_t r_begin = roff[b] + (int64_t)blockIdx.y * kLiftRows;
   const int64_t r_end = min(roff[b + 1], r_begin + kLiftRows);
   if (r_begin >= r_end) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
-    const int j = e / LPB, c = e % LPB;
-    Ss[j][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
+  // the small matrix and all of the warp's rows (row r_begin + warp + NW u) are loaded
+  // before any is used, so the loads are in flight together
+  float sv[LPB * LPB / 256];
+#pragma unroll
+  for (int k = 0; k < LPB * LPB / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    sv[k] = (e % LPB) < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
+  }
+  float qv[RPW];
+#pragma unroll
+  for (int u = 0; u < RPW; ++u) {
+    const int64_t ru = r_begin + warp + NW * u;
+    qv[u] = ru < r_end ? q[ru * LPB + lane] : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < LPB * LPB / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    Ss[e / LPB][e % LPB] = sv[k];
   }
   __syncthreads();
-  // warp w takes rows r_begin + w, + 8, + 16, ...: four at a time
-  for (int64_t r = r_begin + warp; r < r_end; r += 4 * (blockDim.x >> 5)) {
-    float qv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t ru = r + u * (blockDim.x >> 5);
-      qv[u] = ru < r_end ? q[ru * LPB + lane] : 0.0f;
+  for (int u = 0; u < RPW; ++u) {
+    const int64_t ru = r_begin + warp + NW * u;
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < LPB; j += 2) {
+      v0 = fmaf(__shfl_sync(0xffffffffu, qv[u], j), Ss[j][lane], v0);
+      v1 = fmaf(__shfl_sync(0xffffffffu, qv[u], j + 1), Ss[j + 1][lane], v1);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t ru = r + u * (blockDim.x >> 5);
-      float v0 = 0.0f, v1 = 0.0f;
-#pragma unroll
-      for (int j = 0; j < LPB; j += 2) {
-        v0 = fmaf(__shfl_sync(0xffffffffu, qv[u], j), Ss[j][lane], v0);
-        v1 = fmaf(__shfl_sync(0xffffffffu, qv[u], j + 1), Ss[j + 1][lane], v1);
-      }
-      if (ru < r_end && lane < cols) out[ru * ldo + lane] = v0 + v1;
-    }
+    if (ru < r_end && lane < cols) out[ru * ldo + lane] = v0 + v1;
   }
 }
 
@@ -670,14 +715,14 @@ cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int6
 }
 
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
-                                  int rounds, float* rout, float* rinv, const int2* units, int nunits,
-                                  const int* ustart, float* part, uint32_t* status, cudaStream_t st) {
+                                  int rounds, int shift_first, float* rout, float* rinv, const int2* units,
+                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st) {
   if (nunits <= 0 || rounds < 1) return cudaErrorInvalidValue;
-  bqr_gram_kernel<<<nunits, kUnitThreads, 0, st>>>(yin, roff, units, part);
+  bqr_gram_kernel<<<nunits, kUnitThreads, 0, st>>>(yin, roff, units, l, part);
   for (int r = 0; r < rounds; ++r) {
-    bqr_chol_kernel<<<nb, 128, 0, st>>>(part, ustart, l, (rounds >= 3 && r == 0) ? 1.0f : 0.0f, r == 0 ? 1 : 0,
+    bqr_chol_kernel<<<nb, 128, 0, st>>>(part, ustart, l, (shift_first && r == 0) ? 1.0f : 0.0f, r == 0 ? 1 : 0,
                                         rout, rinv, status);
-    bqr_apply_kernel<<<nunits, kUnitThreads, 0, st>>>(r == 0 ? yin : qout, qout, roff, units, rinv,
+    bqr_apply_kernel<<<nunits, kUnitThreads, 0, st>>>(r == 0 ? yin : qout, qout, roff, units, l, rinv,
                                                    r + 1 < rounds ? part : nullptr);
   }
   return cudaGetLastError();

@@ -44,19 +44,33 @@ __device__ __forceinline__ void unit_rows(const int64_t* __restrict__ roff, int2
   *nr = (int)min((int64_t)kUR, roff[u.x + 1] - *row0);
 }
 
+// (kUT threads; every thread's loads are issued before its first store, so they are in
+// flight together)
 __device__ __forceinline__ void unit_stage(const float* __restrict__ src, int64_t row0, int nr,
                                            float (*ys)[LPB]) {
-  for (int e = threadIdx.x; e < kUR * (LPB / 4); e += blockDim.x) {
-    const int rr = e >> 3;
-    reinterpret_cast<float4*>(&ys[0][0])[e] =
-        rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr int N = kUR * (LPB / 4) / kUT;
+  float4 v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int e = threadIdx.x + k * kUT, rr = e >> 3;
+    v[k] = rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+#pragma unroll
+  for (int k = 0; k < N; ++k) reinterpret_cast<float4*>(&ys[0][0])[threadIdx.x + k * kUT] = v[k];
 }
 
 // a 32 x 32 factor into shared memory (rows padded to 33 floats: column and row reads
 // by lane are both conflict-free)
 __device__ __forceinline__ void unit_small(const float* __restrict__ src, float (*ms)[LPB + 1]) {
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) ms[e >> 5][e & 31] = src[e];
+  constexpr int N = LPB * LPB / kUT;
+  float v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = src[threadIdx.x + k * kUT];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int e = threadIdx.x + k * kUT;
+    ms[e >> 5][e & 31] = v[k];
+  }
 }
 
 // sum_j y_j w[j] for the row y in shared memory (float4 broadcasts), w in registers
@@ -276,31 +290,65 @@ __global__ void __launch_bounds__(128) bwd_qr_small_kernel(const float* __restri
   }
 }
 
+// rows x 32 floats into columns col0 .. col0 + 31 of dst (ldd and col0 multiples of 4):
+// 16-byte elements, four loads in flight per thread
 __global__ void copy_block_kernel(const float* __restrict__ src, int64_t rows, float* __restrict__ dst,
                                   int ldd, int col0) {
-  const int64_t n = rows * LPB;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / LPB;
-    const int c = (int)(e - r * LPB);
-    dst[r * ldd + col0 + c] = src[e];
+  const int64_t n4 = rows * (LPB / 4);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  auto put = [&](int64_t e, float4 v) {
+    const int64_t r = e >> 3;
+    *reinterpret_cast<float4*>(dst + r * ldd + col0 + 4 * (int)(e & 7)) = v;
+  };
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n4; e += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = s4[e + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) put(e + u * stride, v[u]);
   }
+  for (; e < n4; e += stride) put(e, s4[e]);
 }
 
 // x -> three bfloat16 planes h = bf16(x), m = bf16(x - h), t = bf16(x - h - m) (x to 24
 // significant bits), planes [3][rows][kr], for the tensor-core form of dL/dA.
+// (n a multiple of 4: four elements per step, 16-byte loads and 8-byte stores, two steps'
+// loads in flight per thread)
 __global__ void bwd_split_kernel(const float* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ planes) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const float v = x[e];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 mm = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 t = __float2bfloat16_rn(r1 - __bfloat162float(mm));
-    planes[e] = h;
-    planes[n + e] = mm;
-    planes[2 * n + e] = t;
+  const int64_t n4 = n / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  auto put = [&](int64_t e, float4 v4) {
+    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+    __nv_bfloat16 h[4], mm[4], t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = __float2bfloat16_rn(v[i]);
+      const float r1 = v[i] - __bfloat162float(h[i]);
+      mm[i] = __float2bfloat16_rn(r1);
+      t[i] = __float2bfloat16_rn(r1 - __bfloat162float(mm[i]));
+    }
+    auto st4 = [&](__nv_bfloat16* d, const __nv_bfloat16 (&q)[4]) {
+      __nv_bfloat162 lo, hi;
+      lo.x = q[0]; lo.y = q[1]; hi.x = q[2]; hi.y = q[3];
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&lo);
+      w.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(d + 4 * e) = w;
+    };
+    st4(planes, h);
+    st4(planes + n, mm);
+    st4(planes + 2 * n, t);
+  };
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + stride < n4; e += 2 * stride) {
+    const float4 a = x4[e], b = x4[e + stride];
+    put(e, a);
+    put(e + stride, b);
   }
+  for (; e < n4; e += stride) put(e, x4[e]);
 }
 
 // dL/dA on the tensor cores: gA_b = 2 A_b + L_b R_b^T for 128 x 128 tiles (units: matrix,
@@ -526,7 +574,9 @@ cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* 
 
 cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
                               cudaStream_t st) {
-  const int64_t n = rows * LPB;
+  if (ldd % 4 || col0 % 4 || ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15))
+    return cudaErrorInvalidValue;
+  const int64_t n = rows * (LPB / 4);
   const int64_t blocks = cdiv(n, 256);
   copy_block_kernel<<<(unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs), 256, 0, st>>>(
       src, rows, dst, ldd, col0);
@@ -534,7 +584,9 @@ cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ld
 }
 
 cudaError_t launch_bwd_split(const float* x, int64_t n, __nv_bfloat16* planes, cudaStream_t st) {
-  const int64_t blocks = cdiv(n, 256);
+  if (n % 4 || ((reinterpret_cast<uintptr_t>(x) & 15) | (reinterpret_cast<uintptr_t>(planes) & 7)))
+    return cudaErrorInvalidValue;
+  const int64_t blocks = cdiv(n / 4, 256);
   bwd_split_kernel<<<(unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs), 256, 0, st>>>(x, n, planes);
   return cudaGetLastError();
 }

@@ -31,10 +31,11 @@ cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int6
 // Cholesky-QR rounds of every matrix's rows (matrix b from roff[b]) over 128-row units:
 // units (b, tile) in matrix order, those of matrix b from ustart[b] (nb + 1 entries);
 // part: nunits x 32 x 32 floats of Gram partials; rinv: nb x 32 x 32 scratch; rout gets
-// the product of the rounds' R factors.  1 + 2 rounds launches.
+// the product of the rounds' R factors; shift_first: the first round factors G + s I,
+// s = l u tr(G) (shifted Cholesky QR).  1 + 2 rounds launches.
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
-                                  int rounds, float* rout, float* rinv, const int2* units, int nunits,
-                                  const int* ustart, float* part, uint32_t* status, cudaStream_t st);
+                                  int rounds, int shift_first, float* rout, float* rinv, const int2* units,
+                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st);
 cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb, int64_t total_rows,
                                     __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff, int split,
                                     cudaStream_t st);
