@@ -368,8 +368,8 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, shift, P->rb, P->rinv,
                              P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
   BTRY(launch_batched_jacobi(P->rb, 1, P->l, P->nb, P->ub, P->sig, P->wb, P->status, P->status + 1, P->st));
-  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->max_m, P->ub, P->k, P->k, U, P->k, P->st));
-  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, P->k, P->k, V, P->k, P->st));
+  if (U) BTRY(launch_batched_lift(Q, P->d_roff_m, P->nb, P->max_m, P->l, P->ub, P->k, P->k, U, P->k, P->st));
+  if (V) BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->l, P->wb, P->k, P->k, V, P->k, P->st));
   if (S)
     BTRY(cudaMemcpy2DAsync(S, sizeof(float) * P->k, P->sig, sizeof(float) * LP, sizeof(float) * P->k,
                            P->nb, cudaMemcpyDeviceToDevice, P->st));
@@ -394,7 +394,7 @@ rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* cons
   (void)gA;
   const int kr = P->kr;
   // V = Q_B W_k (n side) is the first right factor and the operand of A V
-  BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->wb, LP, P->k, P->gn, LP, P->st));
+  BTRY(launch_batched_lift(P->qb, P->d_roff_n, P->nb, P->max_n, P->l, P->wb, LP, P->k, P->gn, LP, P->st));
   BTRY(launch_copy_block(P->gn, P->sum_n, P->rbuf, kr, 0, P->st));
   BTRYS(to_operand(P, P->gn, false, 1));
   BTRYS(bpass(P, 0, 1, P->pm));                                                  // A V

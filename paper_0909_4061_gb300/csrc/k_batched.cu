@@ -319,17 +319,19 @@ __device__ __forceinline__ void bqr_stage(const float* __restrict__ src, int64_t
   for (int k = 0; k < N; ++k) reinterpret_cast<float4*>(&ys[0][0])[threadIdx.x + k * kUnitThreads] = v[k];
 }
 
-// Gram partial of the staged rows (256 threads): only the lower triangle of the l x l
-// block is formed (the factorisation reads no more), as 4 x 4 tiles, L4 = ceil(l / 4) tile
-// rows and L4 (L4 + 1) / 2 tiles; the threads form NG = 256 / tiles row groups (12 at
-// l = 24), each thread one tile over its group's rows (two float4 reads per 16 FMAs).  The
-// groups are summed in a fixed order through gp (NG x tiles x 16 floats, at most 16 KB),
-// and the partial is written whole: zero above the diagonal tiles and beyond l.
-__device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, int l, float* gp,
+// Gram partial of the staged rows (NT threads, row r at ys + r YS): only the lower
+// triangle of the l x l block is formed (the factorisation reads no more), as 4 x 4 tiles,
+// L4 = ceil(l / 4) tile rows and L4 (L4 + 1) / 2 tiles; the threads form NG = NT / tiles
+// row groups (12 at l = 24 and NT = 256), each thread one tile over its group's rows (two
+// float4 reads per 16 FMAs).  The groups are summed in a fixed order through gp (NG x
+// tiles x 16 floats, at most NT x 16), and the partial is written whole: zero above the
+// diagonal tiles and beyond l.
+template <int NT, int YS>
+__device__ __forceinline__ void bqr_gram_tile(const float* ys, int nr, int l, float* gp,
                                               float* __restrict__ part) {
   const int l4 = (l + 3) >> 2;
   const int ntile = l4 * (l4 + 1) / 2;
-  const int ng = kUnitThreads / ntile;
+  const int ng = NT / ntile;
   const int grp = threadIdx.x / ntile, t = threadIdx.x - grp * ntile;
   if (grp < ng) {
     int ti = 0, tt = t;
@@ -341,8 +343,8 @@ __device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, in
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
     for (int rr = grp; rr < nr; rr += ng) {
-      const float4 a = *reinterpret_cast<const float4*>(&ys[rr][bi]);
-      const float4 c = *reinterpret_cast<const float4*>(&ys[rr][bj]);
+      const float4 a = *reinterpret_cast<const float4*>(ys + rr * YS + bi);
+      const float4 c = *reinterpret_cast<const float4*>(ys + rr * YS + bj);
       const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -355,7 +357,7 @@ __device__ __forceinline__ void bqr_gram_tile(const float (*ys)[LPB], int nr, in
       *reinterpret_cast<float4*>(d + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < LPB * LPB; e += blockDim.x) {
+  for (int e = threadIdx.x; e < LPB * LPB; e += NT) {
     const int i = e >> 5, j = e & 31, ti = i >> 2, tj = j >> 2;
     float v = 0.0f;
     if (ti < l4 && tj <= ti) {
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kUnitThreads) bqr_gram_kernel(const float* __r
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
   bqr_stage(src, row0, nr, ys);
   __syncthreads();
-  bqr_gram_tile(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
+  bqr_gram_tile<kUnitThreads, LPB>(&ys[0][0], nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__ part,
@@ -434,57 +436,68 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
   }
 }
 
-// Q = Y R^-1 over a unit: a warp per row, lane = column, the column of R^-1 in registers
-// and the row of Y read as float4 broadcasts, two rows at a time (four independent FMA
-// chains), the sums running over the l4 = ceil(l / 4) float4 of a row that can be nonzero;
-// then the Gram partial of the new rows.
-__global__ void __launch_bounds__(kUnitThreads) bqr_apply_kernel(const float* __restrict__ src,
-                                                                 float* __restrict__ dst,
-                                                                 const int64_t* __restrict__ roff,
-                                                                 const int2* __restrict__ units, int l,
-                                                                 const float* __restrict__ rinv,
-                                                                 float* __restrict__ part) {
-  __shared__ __align__(16) float ys[kUnitRows][LPB];
-  __shared__ __align__(16) float gp[kUnitThreads * 16];
-  constexpr int NW = kUnitThreads / 32;
+// Q = Y R^-1 over a unit, a thread per row (kApplyThreads = kUnitRows threads): the row of Y
+// in registers, R^-1 in shared memory read as float4 broadcasts, and only the triangle
+// R^-1 has: column block c4 (4 columns) of Q sums rows 0 .. 4 c4 + 3 of R^-1, over the
+// L4 = ceil(l / 4) blocks that can be nonzero (the sums in row order, as the definition
+// writes them).  The new rows go to global memory and, with a row stride of 36 floats
+// (16-byte rows whose float4 stores by consecutive threads fall in distinct banks), to
+// shared memory for the Gram partial of the next round.
+constexpr int kApplyThreads = kUnitRows;
+
+template <int L4>
+__global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* __restrict__ src,
+                                                                  float* __restrict__ dst,
+                                                                  const int64_t* __restrict__ roff,
+                                                                  const int2* __restrict__ units, int l,
+                                                                  const float* __restrict__ rinv,
+                                                                  float* __restrict__ part) {
+  constexpr int LC = 4 * L4;
+  constexpr int YS = LPB + 4;
+  __shared__ __align__(16) float ys[kUnitRows * YS];
+  __shared__ __align__(16) float rs[LC][LC];
+  __shared__ __align__(16) float gp[kApplyThreads * 16];
   const int2 u = units[blockIdx.x];
   const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int l4 = (l + 3) >> 2;
-  bqr_stage(src, row0, nr, ys);
-  float xr[LPB];
+  const int t = threadIdx.x;
+  float4 yv[L4];
 #pragma unroll
-  for (int i = 0; i < LPB; ++i)
-    xr[i] = i < l ? rinv[(size_t)u.x * LPB * LPB + i * LPB + lane] : 0.0f;   // R^-1(i, lane)
+  for (int c4 = 0; c4 < L4; ++c4)
+    yv[c4] = t < nr ? reinterpret_cast<const float4*>(src + (row0 + t) * LPB)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = t; e < LC * LC; e += kApplyThreads)
+    rs[e / LC][e % LC] = rinv[(size_t)u.x * LPB * LPB + (e / LC) * LPB + e % LC];
   __syncthreads();
-  for (int rr = warp; rr < nr; rr += 2 * NW) {
-    const int rb = rr + NW < nr ? rr + NW : rr;   // the warp's second row (the first again at the end)
-    const float4* ya = reinterpret_cast<const float4*>(&ys[rr][0]);
-    const float4* yb = reinterpret_cast<const float4*>(&ys[rb][0]);
-    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+  float y[LC];
 #pragma unroll
-    for (int i4 = 0; i4 < LPB / 4; ++i4) {
-      if (i4 < l4) {
-        const float4 p = ya[i4], q = yb[i4];
-        a0 = fmaf(p.x, xr[4 * i4], a0);
-        a1 = fmaf(p.y, xr[4 * i4 + 1], a1);
-        b0 = fmaf(q.x, xr[4 * i4], b0);
-        b1 = fmaf(q.y, xr[4 * i4 + 1], b1);
-        a0 = fmaf(p.z, xr[4 * i4 + 2], a0);
-        a1 = fmaf(p.w, xr[4 * i4 + 3], a1);
-        b0 = fmaf(q.z, xr[4 * i4 + 2], b0);
-        b1 = fmaf(q.w, xr[4 * i4 + 3], b1);
-      }
+  for (int c4 = 0; c4 < L4; ++c4) {
+    y[4 * c4] = yv[c4].x; y[4 * c4 + 1] = yv[c4].y; y[4 * c4 + 2] = yv[c4].z; y[4 * c4 + 3] = yv[c4].w;
+  }
+  float4 q[L4];
+#pragma unroll
+  for (int c4 = 0; c4 < L4; ++c4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 4 * c4 + 4; ++i) {
+      const float4 r = *reinterpret_cast<const float4*>(&rs[i][4 * c4]);
+      acc.x = fmaf(y[i], r.x, acc.x);
+      acc.y = fmaf(y[i], r.y, acc.y);
+      acc.z = fmaf(y[i], r.z, acc.z);
+      acc.w = fmaf(y[i], r.w, acc.w);
     }
-    __syncwarp();   // every lane has read both rows before they are overwritten
-    ys[rr][lane] = a0 + a1;
-    if (rb != rr) ys[rb][lane] = b0 + b1;
+    q[c4] = acc;
+  }
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4* yrow = reinterpret_cast<float4*>(ys + t * YS);
+#pragma unroll
+  for (int c4 = 0; c4 < LPB / 4; ++c4) yrow[c4] = c4 < L4 ? q[c4] : z;
+  if (t < nr) {
+    float4* grow = reinterpret_cast<float4*>(dst + (row0 + t) * LPB);
+#pragma unroll
+    for (int c4 = 0; c4 < LPB / 4; ++c4) grow[c4] = c4 < L4 ? q[c4] : z;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nr * (LPB / 4); e += blockDim.x)
-    reinterpret_cast<float4*>(dst + row0 * LPB)[e] = reinterpret_cast<const float4*>(&ys[0][0])[e];
-  if (part) bqr_gram_tile(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
+  if (part) bqr_gram_tile<kApplyThreads, YS>(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 // basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
@@ -615,52 +628,61 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
 // out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
 // per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
 // for c < valid, 0 for valid <= c < cols; one CTA per matrix, a warp per row
-// One CTA per (matrix, block of kLiftRows rows): the rows of a matrix are spread over
-// several CTAs, and each warp keeps four rows' loads in flight.
+// One CTA per (matrix, block of kLiftRows rows), a thread per row: the row of Q_b (its first
+// l columns, the others are zero) in registers, the small matrix's first 4 ceil(l / 4) rows in
+// shared memory read as float4 broadcasts (columns >= valid read as zero), the sums in row
+// order; vec: 16-byte stores (cols and ldo multiples of 4, out 16-byte aligned).
 constexpr int kLiftRows = 128;
 
-__global__ void __launch_bounds__(256) batched_lift_kernel(const float* __restrict__ q,
-                                                           const int64_t* __restrict__ roff,
-                                                           const float* __restrict__ small, int cols,
-                                                           int valid, float* __restrict__ out, int ldo) {
-  __shared__ float Ss[LPB][LPB + 1];
-  constexpr int NW = 8;                    // warps (256 threads)
-  constexpr int RPW = kLiftRows / NW;      // rows per warp
+template <int L4>
+__global__ void __launch_bounds__(kLiftRows) batched_lift_kernel(const float* __restrict__ q,
+                                                                 const int64_t* __restrict__ roff,
+                                                                 const float* __restrict__ small, int cols,
+                                                                 int valid, float* __restrict__ out, int ldo,
+                                                                 int vec) {
+  constexpr int LC = 4 * L4;
+  __shared__ __align__(16) float Ss[LC][LPB];
   const int b = blockIdx.x;
   const int64_t r_begin = roff[b] + (int64_t)blockIdx.y * kLiftRows;
   const int64_t r_end = min(roff[b + 1], r_begin + kLiftRows);
   if (r_begin >= r_end) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the small matrix and all of the warp's rows (row r_begin + warp + NW u) are loaded
-  // before any is used, so the loads are in flight together
-  float sv[LPB * LPB / 256];
+  const int t = threadIdx.x;
+  const int64_t r = r_begin + t;
+  float4 yv[L4];
 #pragma unroll
-  for (int k = 0; k < LPB * LPB / 256; ++k) {
-    const int e = threadIdx.x + 256 * k;
-    sv[k] = (e % LPB) < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
-  }
-  float qv[RPW];
-#pragma unroll
-  for (int u = 0; u < RPW; ++u) {
-    const int64_t ru = r_begin + warp + NW * u;
-    qv[u] = ru < r_end ? q[ru * LPB + lane] : 0.0f;
-  }
-#pragma unroll
-  for (int k = 0; k < LPB * LPB / 256; ++k) {
-    const int e = threadIdx.x + 256 * k;
-    Ss[e / LPB][e % LPB] = sv[k];
+  for (int c4 = 0; c4 < L4; ++c4)
+    yv[c4] = r < r_end ? reinterpret_cast<const float4*>(q + r * LPB)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = t; e < LC * LPB; e += kLiftRows) {
+    const int c = e % LPB;
+    Ss[e / LPB][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
   }
   __syncthreads();
+  float y[LC];
 #pragma unroll
-  for (int u = 0; u < RPW; ++u) {
-    const int64_t ru = r_begin + warp + NW * u;
-    float v0 = 0.0f, v1 = 0.0f;
+  for (int c4 = 0; c4 < L4; ++c4) {
+    y[4 * c4] = yv[c4].x; y[4 * c4 + 1] = yv[c4].y; y[4 * c4 + 2] = yv[c4].z; y[4 * c4 + 3] = yv[c4].w;
+  }
+  const int n4 = (cols + 3) / 4;
+  for (int c4 = 0; c4 < n4; ++c4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < LPB; j += 2) {
-      v0 = fmaf(__shfl_sync(0xffffffffu, qv[u], j), Ss[j][lane], v0);
-      v1 = fmaf(__shfl_sync(0xffffffffu, qv[u], j + 1), Ss[j + 1][lane], v1);
+    for (int j = 0; j < LC; ++j) {
+      const float4 sv = *reinterpret_cast<const float4*>(&Ss[j][4 * c4]);
+      acc.x = fmaf(y[j], sv.x, acc.x);
+      acc.y = fmaf(y[j], sv.y, acc.y);
+      acc.z = fmaf(y[j], sv.z, acc.z);
+      acc.w = fmaf(y[j], sv.w, acc.w);
     }
-    if (ru < r_end && lane < cols) out[ru * ldo + lane] = v0 + v1;
+    if (r < r_end) {
+      if (vec) {
+        *reinterpret_cast<float4*>(out + r * ldo + 4 * c4) = acc;
+      } else {
+        const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * c4 + i < cols) out[r * ldo + 4 * c4 + i] = a4[i];
+      }
+    }
   }
 }
 
@@ -722,8 +744,18 @@ cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* 
   for (int r = 0; r < rounds; ++r) {
     bqr_chol_kernel<<<nb, 128, 0, st>>>(part, ustart, l, (shift_first && r == 0) ? 1.0f : 0.0f, r == 0 ? 1 : 0,
                                         rout, rinv, status);
-    bqr_apply_kernel<<<nunits, kUnitThreads, 0, st>>>(r == 0 ? yin : qout, qout, roff, units, l, rinv,
-                                                   r + 1 < rounds ? part : nullptr);
+    const float* yr = r == 0 ? yin : qout;
+    float* pr = r + 1 < rounds ? part : nullptr;
+    switch ((l + 3) / 4) {
+#define RSVD_BQR_APPLY(L4)                                                                       \
+  case L4:                                                                                      \
+    bqr_apply_kernel<L4><<<nunits, kApplyThreads, 0, st>>>(yr, qout, roff, units, l, rinv, pr); \
+    break;
+      RSVD_BQR_APPLY(1) RSVD_BQR_APPLY(2) RSVD_BQR_APPLY(3) RSVD_BQR_APPLY(4)
+      RSVD_BQR_APPLY(5) RSVD_BQR_APPLY(6) RSVD_BQR_APPLY(7) RSVD_BQR_APPLY(8)
+#undef RSVD_BQR_APPLY
+      default: return cudaErrorInvalidValue;
+    }
   }
   return cudaGetLastError();
 }
@@ -743,13 +775,24 @@ cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb,
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows,
+cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows, int l,
                                 const float* small, int cols, int valid, float* out, int ldo,
                                 cudaStream_t st) {
-  if (cols > LPB || max_rows < 1 || cdiv(max_rows, kLiftRows) > 65535) return cudaErrorInvalidValue;
+  if (cols > LPB || l < 1 || l > LPB || max_rows < 1 || cdiv(max_rows, kLiftRows) > 65535)
+    return cudaErrorInvalidValue;
+  const int vec = (cols % 4 == 0 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) ? 1 : 0;
   // blocks of kLiftRows rows per matrix, as many as the tallest matrix needs
   const dim3 grid((unsigned)nb, (unsigned)cdiv(max_rows, kLiftRows));
-  batched_lift_kernel<<<grid, 256, 0, st>>>(q, roff, small, cols, valid, out, ldo);
+  switch ((l + 3) / 4) {
+#define RSVD_LIFT_CASE(L4)                                                                               \
+  case L4:                                                                                              \
+    batched_lift_kernel<L4><<<grid, kLiftRows, 0, st>>>(q, roff, small, cols, valid, out, ldo, vec); \
+    break;
+    RSVD_LIFT_CASE(1) RSVD_LIFT_CASE(2) RSVD_LIFT_CASE(3) RSVD_LIFT_CASE(4)
+    RSVD_LIFT_CASE(5) RSVD_LIFT_CASE(6) RSVD_LIFT_CASE(7) RSVD_LIFT_CASE(8)
+#undef RSVD_LIFT_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

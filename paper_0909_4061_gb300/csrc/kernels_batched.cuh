@@ -41,9 +41,10 @@ cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb,
                                     cudaStream_t st);
 cudaError_t launch_batched_jacobi(const float* x, int transposed, int l, int nb, float* ut, float* sig,
                                   float* w, uint32_t* status, uint32_t* info, cudaStream_t st);
-// out rows of matrix b = its rows of q times the leading `valid` columns of its LP x LP small
-// matrix (cols outputs per row); max_rows: the most rows any matrix has.
-cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows,
+// out rows of matrix b = its rows of q (nonzero in the first l columns) times the leading
+// `valid` columns of its LP x LP small matrix (cols outputs per row); max_rows: the most
+// rows any matrix has.
+cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int64_t max_rows, int l,
                                 const float* small, int cols, int valid, float* out, int ldo,
                                 cudaStream_t st);
 
