@@ -396,13 +396,17 @@ def run_ours(args):
                           "split into bf16 hi + lo on the device, U/S/V back to pinned host memory"}
 
     # variants: bf16 storage only (every pass reads bf16(A)); hi + lo storage with only the
-    # final pass B^T = A^T Q reading the residual
+    # final pass B^T = A^T Q reading the residual; hi + lo with the residual in the passes
+    # that make the final bases
     variants = {}
     if A is not None and not args.profile_run:
         for name, kw, Ain, desc in (
                 ("bf16_only", {}, Ab, "A as bf16; every pass reads bf16(A)"),
                 ("residual_final_pass_only", {"dtype": pkg.RSVD_BF16X2}, Ahl,
-                 "A as bf16 hi + bf16 lo (A - hi); Stage A reads hi, the final pass both")):
+                 "A as bf16 hi + bf16 lo (A - hi); Stage A reads hi, the final pass both"),
+                ("residual_final_bases", {"dtype": pkg.RSVD_BF16X2, "residual_passes": 2}, Ahl,
+                 "A as bf16 hi + bf16 lo (A - hi); the passes whose samples become final bases "
+                 "(the last of Stage A and the final pass) read both, the earlier ones hi")):
             with pkg.Plan(w.m, w.n, w.k, w.p, w.q, w.omega_seed, pkg.RSVD_BF16_TC, **kw) as plx:
                 for _ in range(max(args.warmup, 3)):
                     pkg.rsvd_svd(plx.handle, Ain, U, S, V)

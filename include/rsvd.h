@@ -84,8 +84,10 @@ typedef struct {
                            every pass with residual_passes = 1). */
   int32_t single_pass;  /* 1: two-sided one-pass sketch of Section 5.5 (q ignored) */
   int32_t recompute;    /* backward: recompute the sample matrices instead of storing them */
-  int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation: 2 or 3 (default 3:
-                           one shifted round for ill-conditioned samples, then two plain) */
+  int32_t orth_rounds;  /* Cholesky-QR rounds per orthonormalisation of a final basis: 2 or
+                           3 (default 3: one shifted round for ill-conditioned samples, then
+                           two plain); the intermediate bases of the power iteration get at
+                           most 2 (the shifted round and one plain one) */
   int64_t lda;          /* leading dimension of A in elements; 0 means n */
   int32_t small_svd;    /* kernel of the l x l SVD (Algorithm 5.1 step 2): RSVD_SMALL_AUTO
                            (default), RSVD_SMALL_ONE_CTA (l <= 160) or RSVD_SMALL_CLUSTER
@@ -94,8 +96,13 @@ typedef struct {
   int32_t residual_passes; /* with dtype_A RSVD_BF16X2: 0 (default) only the final pass
                            reads hi + lo; 1 every pass over A does (twice the bytes of A per
                            pass; the reconstruction error then matches the float32 path's to
-                           about 1e-5 relative where a hi-only Stage A leaves 2e-4 to 1e-3).
-                           Must be 0 for other dtypes */
+                           about 1e-5 relative where a hi-only Stage A leaves 2e-4 to 1e-3);
+                           2 the passes whose samples become final bases do (the last pass
+                           of Stage A, Y = A Qt_q or Y = A Omega for q = 0, the single pass's
+                           sketches, rsvd_sketch) besides the final one, the earlier power-
+                           iteration passes read hi only (between the two: the float64 model
+                           puts its excess at up to 6e-4 at 2048 x 2048, q = 1, against
+                           4e-5 for every pass).  Must be 0 for other dtypes */
   int32_t psi_cols;     /* single pass: columns l' of the second test matrix Psi (m x l'),
                            k <= l' <= min(n, 256); 0 (default) takes min(3 l, 256, n).  A Psi
                            wider than l makes the system for B^T overdetermined (Section 5.5,

@@ -260,9 +260,8 @@ bool srft_by_fft(rsvd_plan_t P) {
 rsvd_status_t step_srft_fft(rsvd_plan_t P, const void* A, float* out) {
   Step sp(P, RSVD_STEP_PASS);
   sp.launched();
-  const int adt = P->opt.dtype_A == RSVD_F32
-                      ? 0
-                      : ((P->opt.dtype_A == RSVD_BF16X2 && P->opt.residual_passes) ? 2 : 1);
+  const bool res = P->opt.residual_passes == 1 || (P->opt.residual_passes == 2 && P->q == 0);
+  const int adt = P->opt.dtype_A == RSVD_F32 ? 0 : ((P->opt.dtype_A == RSVD_BF16X2 && res) ? 2 : 1);
   TRY(launch_srft_fft(adt, A, P->lda, P->m, P->n, P->srft_signs, P->srft_freq, P->l / 2, out, P->lp,
                       P->num_sms, P->st));
   return RSVD_OK;
@@ -271,8 +270,10 @@ rsvd_status_t step_srft_fft(rsvd_plan_t P, const void* A, float* out) {
 // One pass over A (Algorithm 4.4 steps 2, 4, 5; Algorithm 5.1 step 1).
 // FP32 path: X is float32 (K x lp); tensor-core path: the operand is P->xbf.
 // The result is left as `*splits` partial slabs in P->partial (stride rows x lp).
+// final_sample: the pass's output becomes a final basis (the last pass of Stage A), which
+// reads the residual of A too when residual_passes = 2.
 rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X, bool split_x,
-                        int* splits, int64_t* stride) {
+                        int* splits, int64_t* stride, bool final_sample = false) {
   const int64_t M = trans ? P->n : P->m;
   const int64_t K = trans ? P->m : P->n;
   *stride = M * P->lp;
@@ -285,9 +286,10 @@ rsvd_status_t step_pass(rsvd_plan_t P, const void* A, int trans, const float* X,
     *splits = s;
   } else {
     int s = 1;
-    // the residual of A: in the final pass, or in every pass when asked
-    const int hilo =
-        ((split_x || P->opt.residual_passes) && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
+    // the residual of A: in the final pass, in every pass (residual_passes = 1) or in the
+    // passes whose samples become final bases (residual_passes = 2)
+    const bool res = split_x || P->opt.residual_passes == 1 || (P->opt.residual_passes == 2 && final_sample);
+    const int hilo = (res && P->opt.dtype_A == RSVD_BF16X2) ? 1 : 0;
     if (tc_pass(&P->tc, trans, split_x ? 1 : 0, hilo, P->partial, &s, P->st) != 0)
       return RSVD_ERR_CUDA;
     *splits = s;
@@ -410,7 +412,7 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
     stride = P->m * P->lp;
   } else {
     TRYS(step_draw(P, tc));
-    TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+    TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride, P->q == 0));
   }
   // the bases go where the backward finds them (the tape in store mode), with their R factors
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(0), nullptr, P->q == 0, 0, P->r_q(0)));
@@ -419,7 +421,7 @@ rsvd_status_t stage_a(rsvd_plan_t P, const void* A) {
     TRYS(step_pass(P, A, 1, P->basis_q(j - 1), false, &s, &stride));
     TRYS(step_orth(P, P->partial, s, stride, P->n, P->basis_qt(j), nullptr, false, 0, P->r_qt(j)));
     if (tc) TRYS(step_convert(P, P->basis_qt(j), P->n, 0));
-    TRYS(step_pass(P, A, 0, P->basis_qt(j), false, &s, &stride));
+    TRYS(step_pass(P, A, 0, P->basis_qt(j), false, &s, &stride, j == P->q));
     TRYS(step_orth(P, P->partial, s, stride, P->m, P->basis_q(j), nullptr, j == P->q, 0, P->r_q(j)));
   }
   return RSVD_OK;
@@ -485,7 +487,7 @@ rsvd_status_t stage_single_pass(rsvd_plan_t P, const void* A, float* U, float* S
   TRYS(step_draw(P, tc));
   // the cross products below must see the test matrices the bf16 passes multiplied with
   if (tc) TRY(launch_round_bf16(P->omega, P->n, lp, lp, P->st));
-  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride, true));
   TRYS(step_orth(P, P->partial, s, stride, P->m, P->qbuf, P->sp(2)));
   if (Qout) TRY(launch_gather(P->qbuf, 1, 0, lp, Qout, ldq, P->m, l, l, P->st));
   // Yt = A^T Psi (Psi: Gaussian, stream 1, l' columns), Yt = Qt Rt (Rt in racc, ld lpp)
@@ -814,7 +816,7 @@ rsvd_status_t bw_recompute(rsvd_plan_t P, const void* A, Bw& b, int j, float** q
   int s;
   int64_t stride;
   TRYS(step_draw(P, tc));
-  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride));
+  TRYS(step_pass(P, A, 0, P->omega, false, &s, &stride, P->q == 0));
   TRYS(step_orth(P, P->partial, s, stride, P->m, buf[0], nullptr, P->q == 0));
   const int last = (j < P->q) ? j : j - 1;   // the last Q_i needed
   for (int i = 1; i <= j; ++i) {
@@ -823,7 +825,7 @@ rsvd_status_t bw_recompute(rsvd_plan_t P, const void* A, Bw& b, int j, float** q
     TRYS(step_orth(P, P->partial, s, stride, P->n, b.wqt, nullptr, false));
     if (i > last) break;
     if (tc) TRYS(step_convert(P, b.wqt, P->n, 0));
-    TRYS(step_pass(P, A, 0, b.wqt, false, &s, &stride));
+    TRYS(step_pass(P, A, 0, b.wqt, false, &s, &stride, i == P->q));
     TRYS(step_orth(P, P->partial, s, stride, P->m, buf[i & 1], nullptr, i == P->q));
   }
   *qprev = buf[(j - 1) & 1];
@@ -976,7 +978,7 @@ rsvd_status_t rsvd_plan_create(rsvd_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (o.dtype_A != RSVD_F32 && o.dtype_A != RSVD_BF16 && o.dtype_A != RSVD_BF16X2)
     return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_PLAIN_FP32 && o.dtype_A != RSVD_F32) return RSVD_ERR_INVALID_ARG;
-  if (o.residual_passes != 0 && (o.residual_passes != 1 || o.dtype_A != RSVD_BF16X2))
+  if (o.residual_passes != 0 && ((o.residual_passes != 1 && o.residual_passes != 2) || o.dtype_A != RSVD_BF16X2))
     return RSVD_ERR_INVALID_ARG;
   if (o.precision == RSVD_BF16_TC && o.dtype_A == RSVD_F32) return RSVD_ERR_INVALID_ARG;
   if (o.precision != RSVD_PLAIN_FP32 && o.precision != RSVD_BF16_TC) return RSVD_ERR_INVALID_ARG;
@@ -1372,7 +1374,7 @@ rsvd_status_t rsvd_sketch(rsvd_plan_t P, const void* A, int32_t transpose, const
     TRY(launch_to_bf16_t(xin, kx, P->lp, P->xbf, tc_ld(kx), 0, 0, P->st));
   int s;
   int64_t stride;
-  TRYS(step_pass(P, A, transpose, xin, false, &s, &stride));
+  TRYS(step_pass(P, A, transpose, xin, false, &s, &stride, true));
   TRY(launch_gather(P->partial, s, stride, P->lp, Y, P->l, my, P->l, P->l, P->st));
   return RSVD_OK;
 }

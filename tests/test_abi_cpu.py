@@ -91,7 +91,7 @@ def test_plan_create_rejects_bad_options_on_host(pkg):
     assert e.value.status == pkg.RSVD_ERR_INVALID_ARG
     # the residual of A in every pass needs A stored as hi + lo
     assert pkg.rsvd_options_default().residual_passes == 0
-    for dtype, rp in [(pkg.RSVD_BF16, 1), (pkg.RSVD_BF16X2, 2), (pkg.RSVD_F32, 1)]:
+    for dtype, rp in [(pkg.RSVD_BF16, 1), (pkg.RSVD_BF16, 2), (pkg.RSVD_BF16X2, 3), (pkg.RSVD_F32, 1)]:
         o = pkg.rsvd_options_default()
         o.precision = pkg.RSVD_PLAIN_FP32 if dtype == pkg.RSVD_F32 else pkg.RSVD_BF16_TC
         o.dtype_A = dtype

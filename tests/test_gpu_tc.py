@@ -20,7 +20,7 @@ import pytest
 import torch
 
 import synth
-from oracle import metrics, philox, rsvd64
+from oracle import metrics, mixed, philox, rsvd64
 
 pytestmark = pytest.mark.gpu
 
@@ -217,3 +217,33 @@ def test_tc_residual_every_pass_matched_error(rsvd_lib):
         U, S, V = pl.svd(rsvd_lib.split_bf16(_dev(a32)))
     etc = metrics.fro_error(a32.astype(np.float64), _np(U), _np(S), _np(V))
     assert abs(etc - e32) / e32 <= 1e-4, (etc - e32) / e32
+
+
+def test_tc_residual_final_bases_matches_oracle(rsvd_lib):
+    """residual_passes = 2 (the residual lo read by the last pass of Stage A and by the final
+    pass, hi alone by the earlier one) on a 2048 x 2048 slow-decay matrix (sigma_j = j^-1.5,
+    k = 100, p = 10, q = 1), against oracle.mixed with the same pattern and the same Omega:
+    sigma within 1e-5 sigma_1 and the singular vectors within Wedin's bound for a 1e-5
+    sigma_1 perturbation (the float32 targets)."""
+    m = n = 2048
+    k, p, q, seed = 100, 10, 1, 5
+    l = k + p
+    a, *_ = synth.lowrank(m, n, np.arange(1, n + 1, dtype=np.float64) ** -1.5, 4343)
+    a32 = a.astype(np.float32)
+    with rsvd_lib.Plan(m, n, k, p, q, seed, rsvd_lib.RSVD_BF16_TC, dtype=rsvd_lib.RSVD_BF16X2,
+                       residual_passes=2) as pl:
+        U, S, V = pl.svd(rsvd_lib.split_bf16(_dev(a32)))
+        assert rsvd_lib.rsvd_sync(pl.handle) == rsvd_lib.RSVD_OK
+    u, s, v = _np(U), _np(S), _np(V)
+    hi = _bf16(a32)
+    hl = hi + _bf16(a32.astype(np.float64) - hi)
+    om = philox.gaussian(seed, philox.STREAM_OMEGA, n, l)
+    um, sm, vm, _ = mixed.rsvd(hi, l, 0, q, om, a_final=hl, a_last=hl)
+    sr = sm[:k]
+    assert np.max(np.abs(s - sr)) <= 1e-5 * sr[0], np.max(np.abs(s - sr)) / sr[0]
+    bound = metrics.gap_bound(sr, 1e-5, c=1.0, s_next=sm[k]) + 1e-5
+    for x, xr in ((u, um[:, :k]), (v, vm[:, :k])):
+        d = np.sign(np.sum(x * xr, axis=0))
+        d[d == 0] = 1.0
+        dist = np.linalg.norm(x * d - xr, axis=0)
+        assert np.all(dist <= bound), (dist / bound).max()

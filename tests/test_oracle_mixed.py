@@ -115,3 +115,44 @@ def test_first_sample_uses_the_rounded_test_matrix():
     assert np.linalg.norm(y - q0 @ (q0.T @ y)) <= 1e-12 * np.linalg.norm(y)
     y_unrounded = a @ omega
     assert np.linalg.norm(y_unrounded - q0 @ (q0.T @ y_unrounded)) > 1e-6 * np.linalg.norm(y_unrounded)
+
+
+def test_last_product_sees_a_last():
+    """a_last enters the last product of Stage A only: with q = 0 it is the only product;
+    with q = 1 and a_last zero outside a set of rows, the final basis is zero outside those
+    rows too, while the intermediate basis still comes from a_stored (so Q differs from the
+    basis with that restricted matrix in every product)."""
+    rng = np.random.default_rng(21)
+    a = rng.standard_normal((80, 50))
+    x = rng.standard_normal((80, 50))
+    omega = rng.standard_normal((50, 6))
+    assert np.array_equal(mixed.range_finder(x, omega, 0, a_last=a), mixed.range_finder(a, omega, 0))
+    rows = np.arange(80) % 3 == 0
+    a_r = np.where(rows[:, None], a, 0.0)
+    qm = mixed.range_finder(a, omega, 1, a_last=a_r)
+    assert np.max(np.abs(qm[~rows])) <= 1e-15
+    assert metrics.orthonormality(qm) <= 1e-13
+    q_all = mixed.range_finder(a_r, omega, 1)
+    assert np.linalg.norm(qm @ qm.T - q_all @ q_all.T) > 1e-3
+
+
+@pytest.mark.parametrize("seed", [77, 78])
+def test_residual_in_the_final_bases_sits_between(seed):
+    """The residual lo in the products that make the final bases (the last of Stage A and
+    B^T = A^T Q) and hi alone in the earlier power-iteration product: the error of the
+    hi-only product is only partly washed out by the one product after it (q = 1), so the
+    excess lands between the two patterns above -- at most half that of hi alone in all of
+    Stage A, but above the 1e-4 of the residual in every product on some draws (6e-4 for
+    seed 78)."""
+    m = n = 2048
+    k, p, q = 100, 10, 1
+    a, *_ = synth.lowrank(m, n, synth.spectrum_power(n, 1.5), seed)
+    a = a.astype(np.float32).astype(np.float64)
+    omega = np.random.default_rng(seed).standard_normal((n, k + p))
+    e_ref = metrics.fro_error(a, *rsvd64.rsvd(a, k, p, q, omega)[:3])
+    hi = mixed.bf16(a)
+    hl = mixed.split(a)
+    final_bases = metrics.fro_error(a, *mixed.rsvd(hi, k, p, q, omega, a_final=hl, a_last=hl)[:3])
+    stage_a_hi = metrics.fro_error(a, *mixed.rsvd(hi, k, p, q, omega, a_final=hl)[:3])
+    assert (final_bases - e_ref) / e_ref <= 0.5 * (stage_a_hi - e_ref) / e_ref
+    assert (final_bases - e_ref) / e_ref <= 1e-3
