@@ -507,11 +507,20 @@ def run_pass_probe(args):
     m, n, k, p = 8192, 16384, 100, 10
     gen = torch.Generator(device="cuda")
     gen.manual_seed(5)
-    # A as bf16 hi + bf16 lo, every pass reading both: the passes of the bench's headline
-    A = pkg.split_bf16(torch.randn(m, n, generator=gen, device="cuda"))
     X = torch.randn(n, k + p, device="cuda")
     Y = torch.empty(m, k + p, device="cuda")
-    with pkg.Plan(m, n, k, p, 1, 1, pkg.RSVD_BF16_TC, dtype=pkg.RSVD_BF16X2, residual_passes=1) as pl:
+    if args.pass_probe_bf16:
+        # A as bf16 alone (the kernel of the bf16-only storage and of the C3/C4/C5 passes;
+        # 16384 x 16384, 537 MB)
+        m = 16384
+        A = torch.randn(m, n, generator=gen, device="cuda").to(torch.bfloat16)
+        Y = torch.empty(m, k + p, device="cuda")
+        kw = {}
+    else:
+        # A as bf16 hi + bf16 lo, every pass reading both: the passes of the bench's headline
+        A = pkg.split_bf16(torch.randn(m, n, generator=gen, device="cuda"))
+        kw = {"dtype": pkg.RSVD_BF16X2, "residual_passes": 1}
+    with pkg.Plan(m, n, k, p, 1, 1, pkg.RSVD_BF16_TC, **kw) as pl:
         for trans in (0, 1):
             for _ in range(3):
                 if trans:
@@ -520,7 +529,8 @@ def run_pass_probe(args):
                     pkg.rsvd_sketch(pl.handle, A, 0, X, Y)
         if pkg.rsvd_sync(pl.handle) != pkg.RSVD_OK:
             raise RuntimeError("device error in the pass probe")
-    print(json.dumps({"pass_probe": "ok", "m": m, "n": n, "l": k + p}))
+    print(json.dumps({"pass_probe": "ok", "m": m, "n": n, "l": k + p,
+                      "storage": "bf16" if args.pass_probe_bf16 else "bf16 hi + lo"}))
 
 
 def run_small_probe(args):
@@ -880,6 +890,8 @@ def main():
     ap.add_argument("--small-probe", action="store_true",
                     help="two rank-100 SVDs (l = 110) of an 8192 x 8192 bf16 matrix: the small case "
                          "for full ncu captures of the orthonormalisation and small-SVD kernels")
+    ap.add_argument("--pass-probe-bf16", action="store_true",
+                    help="with --pass-probe: A stored as bf16 alone, 16384 x 16384 (537 MB)")
     ap.add_argument("--pass-probe", action="store_true",
                     help="three launches of the tensor-core pass kernel (each mode) on an 8192 x 16384 "
                          "A stored as bf16 hi + lo (537 MB, larger than L2): the small case for "

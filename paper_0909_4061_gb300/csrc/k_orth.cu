@@ -687,130 +687,56 @@ __global__ void __launch_bounds__(512, 1) cholesky_blocked_kernel(
   if (tid < l) arow(tid)[tid] += s_shift;
   __syncthreads();
 
-  // Diagonal block J (16 x 16) by warp 0 as 2 x 2 blocks of 8 x 8: L11 = chol(A11) in
-  // every lane's registers (broadcast loads, no exchange between lanes on the chain of
-  // pivots), L21 = A21 L11^-T by substitution (lane i: row i), A22 - L21 L21^T (one entry
-  // per lane), L22 = chol of that, again in every lane.  L_JJ goes to A, transposed to
-  // s_lt, its reciprocal pivots to s_rpv; a floored pivot is reported once.
+  // Diagonal block J (16 x 16) by warp 0, lane r (and r + 16, which repeats it) holding row
+  // r: per pivot j the pivot comes by a shuffle from lane j, every lane forms 1/sqrt of it
+  // (hardware estimate and one Newton step y <- y (3 - d y^2) / 2), scales its entry of
+  // column j and updates its row with the column's entries fetched by shuffles.  Entries
+  // above the diagonal collect scratch until their own pivot zeroes them.  A pivot at or
+  // below the floor is replaced by it and the column below it set to zero (a rank-deficient
+  // sample); the first such pivot is reported.  Row r of L_JJ goes to A, its transpose to
+  // s_lt, the reciprocal pivots to s_rpv and the column scales to s_csv.
   bool any_low = false;
   float dlow = 0.0f;
-  // Cholesky of the 8 x 8 lower triangle a (in place), pivots base .. base + 7
-  // (rp8: reciprocal pivots; cs8: the scale of the column below each pivot, zero below a
-  // floored one, whose column is rounding noise)
-  auto chol8 = [&](float (&a)[8][8], float (&rp8)[8], float (&cs8)[8], int base) {
+  auto diag_factor = [&](int J) {
+    const int r = lane & 15;
+    float a[CB];
+    {
+      const float4* src = reinterpret_cast<const float4*>(arow(J + r) + J);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float d = a[j][j];
-      const bool low = base + j < l && !(d > pfloor);   // the same in every lane
+      for (int q = 0; q < CB / 4; ++q) {
+        const float4 t = src[q];
+        a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+      }
+    }
+    float myrp = 0.0f, mycs = 0.0f;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      float d = __shfl_sync(0xffffffffu, a[j], j, 16);
+      const bool low = J + j < l && !(d > pfloor);   // the same in every lane
       if (low && !any_low) dlow = d;
       any_low |= low;
       d = low ? pfloor : d;
-      // 1/sqrt(d) by the hardware estimate and one Newton step y <- y (3 - d y^2) / 2
       float rp = rsqrtf(d);
       rp = rp * fmaf(-0.5f * d * rp, rp, 1.5f);
       const float cs = low ? 0.0f : rp;
-      rp8[j] = rp;
-      cs8[j] = cs;
-      a[j][j] = d * rp;
-#pragma unroll
-      for (int i = j + 1; i < 8; ++i) a[i][j] *= cs;
-#pragma unroll
-      for (int i = j + 1; i < 8; ++i)
-#pragma unroll
-        for (int k = j + 1; k <= i; ++k) a[i][k] = fmaf(-a[i][j], a[k][j], a[i][k]);
-    }
-  };
-  // rows r0 .. r0 + 7, columns c0 .. c0 + 7 of A (lower part) into a, in every lane
-  auto load8 = [&](float (&a)[8][8], int r0, int c0) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4* src = reinterpret_cast<const float4*>(arow(r0 + i) + c0);
-      const float4 u = src[0], v = src[1];
-      a[i][0] = u.x; a[i][1] = u.y; a[i][2] = u.z; a[i][3] = u.w;
-      a[i][4] = v.x; a[i][5] = v.y; a[i][6] = v.z; a[i][7] = v.w;
-    }
-  };
-  auto diag_factor = [&](int J) {
-    float l11[8][8], l22[8][8], rp1[8], rp2[8], cs1[8], cs2[8];
-    load8(l11, J, J);
-    chol8(l11, rp1, cs1, J);
-    // L21: lane i & 7 forms row 8 + (i & 7) by forward substitution with L11
-    const int ri = lane & 7;
-    float l21[8];
-    {
-      const float4* src = reinterpret_cast<const float4*>(arow(J + 8 + ri) + J);
-      const float4 u = src[0], v = src[1];
-      l21[0] = u.x; l21[1] = u.y; l21[2] = u.z; l21[3] = u.w;
-      l21[4] = v.x; l21[5] = v.y; l21[6] = v.z; l21[7] = v.w;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        l21[c] *= cs1[c];
-#pragma unroll
-        for (int c2 = c + 1; c2 < 8; ++c2) l21[c2] = fmaf(-l21[c], l11[c2][c], l21[c2]);
+      if (r == j) {
+        myrp = rp;
+        mycs = cs;
       }
+      const float lij = (r == j) ? d * rp : (r > j ? a[j] * cs : 0.0f);
+      a[j] = lij;
+#pragma unroll
+      for (int k = j + 1; k < CB; ++k) a[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k, 16), a[k]);
     }
-    if (lane < 8) {
-      float4* dst = reinterpret_cast<float4*>(arow(J + 8 + ri) + J);
-      dst[0] = make_float4(l21[0], l21[1], l21[2], l21[3]);
-      dst[1] = make_float4(l21[4], l21[5], l21[6], l21[7]);
-    }
-    __syncwarp();
-    // A22 <- A22 - L21 L21^T, lower triangle: 36 entries over the 32 lanes
-    for (int t = lane; t < 36; t += 32) {
-      int i = 0;
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      const int k = t - i * (i + 1) / 2;
-      const float4* pi = reinterpret_cast<const float4*>(arow(J + 8 + i) + J);
-      const float4* pk = reinterpret_cast<const float4*>(arow(J + 8 + k) + J);
-      const float v = dot4(pi[0], pk[0], dot4(pi[1], pk[1], 0.0f));
-      arow(J + 8 + i)[J + 8 + k] -= v;
-    }
-    __syncwarp();
-    load8(l22, J + 8, J + 8);
-    chol8(l22, rp2, cs2, J + 8);
     if (any_low && lane == 0) set_status(status, isnan(dlow) ? ST_NONFINITE : ST_RANK_DEFICIENT);
-    __syncwarp();
-    // L_JJ rows: lane i < 8 writes row i (L11) and row 8 + i (L22 part); s_lt and s_rpv
-    if (lane < 8) {
-      float row1[8], row2[8];
+    if (lane < CB) {
+      float4* dst = reinterpret_cast<float4*>(arow(J + r) + J);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        row1[c] = 0.0f;
-        row2[c] = 0.0f;
-      }
+      for (int q = 0; q < CB / 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i == lane) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            row1[c] = (c <= i) ? l11[i][c] : 0.0f;
-            row2[c] = (c <= i) ? l22[i][c] : 0.0f;
-          }
-        }
-      float4* d1 = reinterpret_cast<float4*>(arow(J + lane) + J);
-      d1[0] = make_float4(row1[0], row1[1], row1[2], row1[3]);
-      d1[1] = make_float4(row1[4], row1[5], row1[6], row1[7]);
-      float4* d2 = reinterpret_cast<float4*>(arow(J + 8 + lane) + J + 8);
-      d2[0] = make_float4(row2[0], row2[1], row2[2], row2[3]);
-      d2[1] = make_float4(row2[4], row2[5], row2[6], row2[7]);
-      // s_lt[c][r] = L(r, c): rows 0..7 from L11, rows 8..15 from L21 and L22
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        s_lt[c][lane] = row1[c];
-        s_lt[c][8 + lane] = l21[c];
-        s_lt[8 + c][8 + lane] = row2[c];
-        s_lt[8 + c][lane] = 0.0f;
-      }
-    }
-    if (lane == 0) {
-      *reinterpret_cast<float4*>(s_rpv + J) = make_float4(rp1[0], rp1[1], rp1[2], rp1[3]);
-      *reinterpret_cast<float4*>(s_rpv + J + 4) = make_float4(rp1[4], rp1[5], rp1[6], rp1[7]);
-      *reinterpret_cast<float4*>(s_rpv + J + 8) = make_float4(rp2[0], rp2[1], rp2[2], rp2[3]);
-      *reinterpret_cast<float4*>(s_rpv + J + 12) = make_float4(rp2[4], rp2[5], rp2[6], rp2[7]);
-      *reinterpret_cast<float4*>(s_csv + J) = make_float4(cs1[0], cs1[1], cs1[2], cs1[3]);
-      *reinterpret_cast<float4*>(s_csv + J + 4) = make_float4(cs1[4], cs1[5], cs1[6], cs1[7]);
-      *reinterpret_cast<float4*>(s_csv + J + 8) = make_float4(cs2[0], cs2[1], cs2[2], cs2[3]);
-      *reinterpret_cast<float4*>(s_csv + J + 12) = make_float4(cs2[4], cs2[5], cs2[6], cs2[7]);
+      for (int c = 0; c < CB; ++c) s_lt[c][r] = a[c];   // s_lt[c][r] = L(r, c)
+      s_rpv[J + r] = myrp;
+      s_csv[J + r] = mycs;
     }
   };
   // X_JJ = L_JJ^-1 by one warp, by columns: lane r holds column r, x[i] = X(i, r), zero for
