@@ -436,14 +436,35 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
   }
 }
 
-// Q = Y R^-1 over a unit, a thread per row (kApplyThreads = kUnitRows threads): the row of Y
-// in registers, R^-1 in shared memory read as float4 broadcasts, and only the triangle
-// R^-1 has: column block c4 (4 columns) of Q sums rows 0 .. 4 c4 + 3 of R^-1, over the
-// L4 = ceil(l / 4) blocks that can be nonzero (the sums in row order, as the definition
-// writes them).  The new rows go to global memory and, with a row stride of 36 floats
-// (16-byte rows whose float4 stores by consecutive threads fall in distinct banks), to
-// shared memory for the Gram partial of the next round.
+// Q = Y R^-1 over a unit, a thread per row (kApplyThreads = kUnitRows threads): the unit's
+// rows are staged in shared memory by coalesced 16-byte loads (row stride 36 floats, so
+// both these stores and a thread's reads of its own row are free of bank conflicts), a
+// thread takes its row into registers and forms its row of Q with R^-1 read as float4
+// broadcasts, summing only the triangle R^-1 has: column block c4 (4 columns) of Q sums
+// rows 0 .. 4 c4 + 3 of R^-1, over the L4 = ceil(l / 4) blocks that can be nonzero (in row
+// order, as the definition writes the sums).  The new rows replace the old in shared
+// memory, leave by coalesced stores, and give the Gram partial of the next round.
 constexpr int kApplyThreads = kUnitRows;
+constexpr int kRowStride = LPB + 4;
+
+// the unit's rows (columns 4 L4 and beyond are zero) into ys, row stride kRowStride
+template <int L4>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t row0, int nr, float* ys) {
+  constexpr int N = kUnitRows * (LPB / 4) / kApplyThreads;   // 8 float4 per thread
+  const int c4 = threadIdx.x & 7;                             // the same column block on every step
+  float4 v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int rr = (threadIdx.x + k * kApplyThreads) >> 3;
+    v[k] = (rr < nr && c4 < L4) ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[c4]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int rr = (threadIdx.x + k * kApplyThreads) >> 3;
+    *reinterpret_cast<float4*>(ys + rr * kRowStride + 4 * c4) = v[k];
+  }
+}
 
 template <int L4>
 __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* __restrict__ src,
@@ -453,27 +474,23 @@ __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* _
                                                                   const float* __restrict__ rinv,
                                                                   float* __restrict__ part) {
   constexpr int LC = 4 * L4;
-  constexpr int YS = LPB + 4;
-  __shared__ __align__(16) float ys[kUnitRows * YS];
+  __shared__ __align__(16) float ys[kUnitRows * kRowStride];
   __shared__ __align__(16) float rs[LC][LC];
   __shared__ __align__(16) float gp[kApplyThreads * 16];
   const int2 u = units[blockIdx.x];
   const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
   const int t = threadIdx.x;
-  float4 yv[L4];
-#pragma unroll
-  for (int c4 = 0; c4 < L4; ++c4)
-    yv[c4] = t < nr ? reinterpret_cast<const float4*>(src + (row0 + t) * LPB)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  stage_rows<L4>(src, row0, nr, ys);
   for (int e = t; e < LC * LC; e += kApplyThreads)
     rs[e / LC][e % LC] = rinv[(size_t)u.x * LPB * LPB + (e / LC) * LPB + e % LC];
   __syncthreads();
   float y[LC];
 #pragma unroll
   for (int c4 = 0; c4 < L4; ++c4) {
-    y[4 * c4] = yv[c4].x; y[4 * c4 + 1] = yv[c4].y; y[4 * c4 + 2] = yv[c4].z; y[4 * c4 + 3] = yv[c4].w;
+    const float4 v = *reinterpret_cast<const float4*>(ys + t * kRowStride + 4 * c4);
+    y[4 * c4] = v.x; y[4 * c4 + 1] = v.y; y[4 * c4 + 2] = v.z; y[4 * c4 + 3] = v.w;
   }
-  float4 q[L4];
 #pragma unroll
   for (int c4 = 0; c4 < L4; ++c4) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -485,19 +502,22 @@ __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* _
       acc.z = fmaf(y[i], r.z, acc.z);
       acc.w = fmaf(y[i], r.w, acc.w);
     }
-    q[c4] = acc;
-  }
-  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4* yrow = reinterpret_cast<float4*>(ys + t * YS);
-#pragma unroll
-  for (int c4 = 0; c4 < LPB / 4; ++c4) yrow[c4] = c4 < L4 ? q[c4] : z;
-  if (t < nr) {
-    float4* grow = reinterpret_cast<float4*>(dst + (row0 + t) * LPB);
-#pragma unroll
-    for (int c4 = 0; c4 < LPB / 4; ++c4) grow[c4] = c4 < L4 ? q[c4] : z;
+    // row t of the staged tile is read by this thread alone (its y is in registers)
+    *reinterpret_cast<float4*>(ys + t * kRowStride + 4 * c4) = acc;
   }
   __syncthreads();
-  if (part) bqr_gram_tile<kApplyThreads, YS>(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
+  // the new rows out, 16 bytes per thread and step, zeros beyond column 4 L4
+  {
+    const int c4 = t & 7;
+#pragma unroll
+    for (int k = 0; k < kUnitRows * (LPB / 4) / kApplyThreads; ++k) {
+      const int rr = (t + k * kApplyThreads) >> 3;
+      if (rr < nr)
+        reinterpret_cast<float4*>(dst + (row0 + rr) * LPB)[c4] =
+            c4 < L4 ? *reinterpret_cast<const float4*>(ys + rr * kRowStride + 4 * c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (part) bqr_gram_tile<kApplyThreads, kRowStride>(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 // basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
@@ -628,10 +648,12 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
 // out rows (concatenated, ldo wide) = Q_b rows times the first `cols` columns of the
 // per-matrix LPB x LPB block small_b (ld LPB): out[r][c] = sum_j Q[r][j] small_b[j][c]
 // for c < valid, 0 for valid <= c < cols; one CTA per matrix, a warp per row
-// One CTA per (matrix, block of kLiftRows rows), a thread per row: the row of Q_b (its first
-// l columns, the others are zero) in registers, the small matrix's first 4 ceil(l / 4) rows in
-// shared memory read as float4 broadcasts (columns >= valid read as zero), the sums in row
-// order; vec: 16-byte stores (cols and ldo multiples of 4, out 16-byte aligned).
+// One CTA per (matrix, block of kLiftRows rows), a thread per row: the rows of Q_b (their
+// first l columns, the others are zero) staged in shared memory by coalesced loads, a
+// thread's row into registers, the small matrix's first 4 ceil(l / 4) rows in shared memory
+// read as float4 broadcasts (columns >= valid read as zero), the sums in row order; the
+// output rows go back through shared memory and leave by coalesced stores when vec (cols
+// and ldo multiples of 4, out 16-byte aligned), else a thread writes its own row.
 constexpr int kLiftRows = 128;
 
 template <int L4>
@@ -640,18 +662,17 @@ __global__ void __launch_bounds__(kLiftRows) batched_lift_kernel(const float* __
                                                                  const float* __restrict__ small, int cols,
                                                                  int valid, float* __restrict__ out, int ldo,
                                                                  int vec) {
+  static_assert(kLiftRows == kUnitRows, "the lift stages rows like a Cholesky-QR unit");
   constexpr int LC = 4 * L4;
+  __shared__ __align__(16) float ys[kLiftRows * kRowStride];
   __shared__ __align__(16) float Ss[LC][LPB];
   const int b = blockIdx.x;
   const int64_t r_begin = roff[b] + (int64_t)blockIdx.y * kLiftRows;
   const int64_t r_end = min(roff[b + 1], r_begin + kLiftRows);
   if (r_begin >= r_end) return;
+  const int nr = (int)(r_end - r_begin);
   const int t = threadIdx.x;
-  const int64_t r = r_begin + t;
-  float4 yv[L4];
-#pragma unroll
-  for (int c4 = 0; c4 < L4; ++c4)
-    yv[c4] = r < r_end ? reinterpret_cast<const float4*>(q + r * LPB)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  stage_rows<L4>(q, r_begin, nr, ys);
   for (int e = t; e < LC * LPB; e += kLiftRows) {
     const int c = e % LPB;
     Ss[e / LPB][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
@@ -660,7 +681,8 @@ __global__ void __launch_bounds__(kLiftRows) batched_lift_kernel(const float* __
   float y[LC];
 #pragma unroll
   for (int c4 = 0; c4 < L4; ++c4) {
-    y[4 * c4] = yv[c4].x; y[4 * c4 + 1] = yv[c4].y; y[4 * c4 + 2] = yv[c4].z; y[4 * c4 + 3] = yv[c4].w;
+    const float4 v = *reinterpret_cast<const float4*>(ys + t * kRowStride + 4 * c4);
+    y[4 * c4] = v.x; y[4 * c4 + 1] = v.y; y[4 * c4 + 2] = v.z; y[4 * c4 + 3] = v.w;
   }
   const int n4 = (cols + 3) / 4;
   for (int c4 = 0; c4 < n4; ++c4) {
@@ -673,16 +695,21 @@ __global__ void __launch_bounds__(kLiftRows) batched_lift_kernel(const float* __
       acc.z = fmaf(y[j], sv.z, acc.z);
       acc.w = fmaf(y[j], sv.w, acc.w);
     }
-    if (r < r_end) {
-      if (vec) {
-        *reinterpret_cast<float4*>(out + r * ldo + 4 * c4) = acc;
-      } else {
-        const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+    if (vec) {
+      *reinterpret_cast<float4*>(ys + t * kRowStride + 4 * c4) = acc;   // this thread's row only
+    } else if (t < nr) {
+      const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (4 * c4 + i < cols) out[r * ldo + 4 * c4 + i] = a4[i];
-      }
+      for (int i = 0; i < 4; ++i)
+        if (4 * c4 + i < cols) out[(r_begin + t) * ldo + 4 * c4 + i] = a4[i];
     }
+  }
+  if (!vec) return;
+  __syncthreads();
+  for (int e = t; e < nr * n4; e += kLiftRows) {
+    const int rr = e / n4, c4 = e - rr * n4;
+    *reinterpret_cast<float4*>(out + (r_begin + rr) * ldo + 4 * c4) =
+        *reinterpret_cast<const float4*>(ys + rr * kRowStride + 4 * c4);
   }
 }
 
