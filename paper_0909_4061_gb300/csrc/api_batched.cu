@@ -348,22 +348,22 @@ rsvd_status_t bforward(rsvd_batched_plan_t P, const void* const* A, float* U, fl
   BTRY(launch_batched_draw(P->seed, P->d_roff_n, P->nb, P->sum_n, P->l, P->omega, P->xbf, ldx,
                            P->d_xoff_n, P->st));
   BTRYS(bpass(P, 0, 0, P->ym));                                                  // Y_0 = A Omega
+  // every basis of Stage A is also written by its last Cholesky-QR round as the next pass's
+  // operand (transposed bfloat16 hi + lo)
   BTRY(launch_batched_cholqr(P->ym, P->qm[0], P->d_roff_m, P->nb, P->l, P->q == 0 ? rounds : rounds_mid, shift,
                              P->rm[0], P->rinv, P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status,
-                             P->st));
+                             P->st, P->xbf, ldx, P->d_xoff_m, 1));
   for (int j = 1; j <= P->q; ++j) {
-    BTRYS(to_operand(P, P->qm[j - 1], true, 1));
     BTRYS(bpass(P, 1, 1, P->yn));                                                // A^T Q_{j-1}
     BTRY(launch_batched_cholqr(P->yn, P->qn[j - 1], P->d_roff_n, P->nb, P->l, rounds_mid, shift, P->rn[j - 1],
-                               P->rinv, P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
-    BTRYS(to_operand(P, P->qn[j - 1], false, 1));
+                               P->rinv, P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st,
+                               P->xbf, ldx, P->d_xoff_n, 1));
     BTRYS(bpass(P, 0, 1, P->ym));                                                // A Qt_j
     BTRY(launch_batched_cholqr(P->ym, P->qm[j], P->d_roff_m, P->nb, P->l, j == P->q ? rounds : rounds_mid, shift,
                                P->rm[j], P->rinv, P->d_qunits_m, P->nq_m, P->d_ustart_m, P->qpart, P->status,
-                               P->st));
+                               P->st, P->xbf, ldx, P->d_xoff_m, 1));
   }
   float* Q = P->qm[P->q];
-  BTRYS(to_operand(P, Q, true, 1));
   BTRYS(bpass(P, 1, 1, P->yn));                                                  // B^T = A^T Q (split Q)
   BTRY(launch_batched_cholqr(P->yn, P->qb, P->d_roff_n, P->nb, P->l, rounds, shift, P->rb, P->rinv,
                              P->d_qunits_n, P->nq_n, P->d_ustart_n, P->qpart, P->status, P->st));
@@ -384,7 +384,7 @@ rsvd_status_t qr_back(rsvd_batched_plan_t P, const float* Q, const float* gQ, co
                            m_side ? P->d_ustart_m : P->d_ustart_n, P->nb, P->l, R, P->qpart, P->nmat, P->rinv,
                            P->st));
   BTRY(launch_bwd_qr_apply(Q, gQ, roff, m_side ? P->d_qunits_m : P->d_qunits_n, m_side ? P->nq_m : P->nq_n,
-                           P->nmat, P->rinv, gY, P->st));
+                           P->l, P->nmat, P->rinv, gY, P->st));
   return RSVD_OK;
 }
 
@@ -399,7 +399,7 @@ rsvd_status_t bbackward(rsvd_batched_plan_t P, const void* const* A, float* cons
   BTRYS(to_operand(P, P->gn, false, 1));
   BTRYS(bpass(P, 0, 1, P->pm));                                                  // A V
   // dL/dQ_q and the first left factor U (I - 2 S)
-  BTRY(launch_bwd_gq(P->pm, P->qm[P->q], P->d_roff_m, P->d_qunits_m, P->nq_m, P->ub, P->sig, P->k, P->gm,
+  BTRY(launch_bwd_gq(P->pm, P->qm[P->q], P->d_roff_m, P->d_qunits_m, P->nq_m, P->l, P->ub, P->sig, P->k, P->gm,
                      P->lbuf, kr, P->st));
   int blk = 1;
   for (int j = P->q; j >= 1; --j, blk += 2) {

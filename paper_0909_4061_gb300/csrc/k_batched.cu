@@ -27,6 +27,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "batched_rows.cuh"
 #include "kernels_batched.cuh"
 #include "philox.cuh"
 #include "tc_ptx.cuh"
@@ -342,6 +343,7 @@ __device__ __forceinline__ void bqr_gram_tile(const float* ys, int nr, int l, fl
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
     for (int rr = grp; rr < nr; rr += ng) {
       const float4 a = *reinterpret_cast<const float4*>(ys + rr * YS + bi);
       const float4 c = *reinterpret_cast<const float4*>(ys + rr * YS + bj);
@@ -392,13 +394,26 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
   __shared__ float Ro[LPB][LPB + 1];
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // every thread sums its 8 entries over the matrix's units (the 8 loads of a unit in flight
-  // together, the units in order)
+  // every thread sums its 8 entries over the matrix's units in unit order, the loads of
+  // four units (32) in flight together
   constexpr int kPer = LPB * LPB / 128;
   float v[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) v[q] = 0.0f;
-  for (int u = ustart[b]; u < ustart[b + 1]; ++u) {
+  const int u0 = ustart[b], u1 = ustart[b + 1];
+  int u = u0;
+  for (; u + 4 <= u1; u += 4) {
+    float w[4][kPer];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) w[d][q] = part[(size_t)(u + d) * LPB * LPB + tid + q * 128];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) v[q] += w[d][q];
+  }
+  for (; u < u1; ++u) {
     const float* pu = part + (size_t)u * LPB * LPB;
 #pragma unroll
     for (int q = 0; q < kPer; ++q) v[q] += pu[tid + q * 128];
@@ -445,26 +460,7 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
 // order, as the definition writes the sums).  The new rows replace the old in shared
 // memory, leave by coalesced stores, and give the Gram partial of the next round.
 constexpr int kApplyThreads = kUnitRows;
-constexpr int kRowStride = LPB + 4;
-
-// the unit's rows (columns 4 L4 and beyond are zero) into ys, row stride kRowStride
-template <int L4>
-__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t row0, int nr, float* ys) {
-  constexpr int N = kUnitRows * (LPB / 4) / kApplyThreads;   // 8 float4 per thread
-  const int c4 = threadIdx.x & 7;                             // the same column block on every step
-  float4 v[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int rr = (threadIdx.x + k * kApplyThreads) >> 3;
-    v[k] = (rr < nr && c4 < L4) ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[c4]
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int rr = (threadIdx.x + k * kApplyThreads) >> 3;
-    *reinterpret_cast<float4*>(ys + rr * kRowStride + 4 * c4) = v[k];
-  }
-}
+static_assert(kUnitRows == kTileRows && LPB == kTileWidth, "units are the row tiles of batched_rows.cuh");
 
 template <int L4>
 __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* __restrict__ src,
@@ -472,7 +468,9 @@ __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* _
                                                                   const int64_t* __restrict__ roff,
                                                                   const int2* __restrict__ units, int l,
                                                                   const float* __restrict__ rinv,
-                                                                  float* __restrict__ part) {
+                                                                  float* __restrict__ part,
+                                                                  __nv_bfloat16* __restrict__ xbf, int64_t ldx,
+                                                                  const int64_t* __restrict__ xoff, int split) {
   constexpr int LC = 4 * L4;
   __shared__ __align__(16) float ys[kUnitRows * kRowStride];
   __shared__ __align__(16) float rs[LC][LC];
@@ -481,16 +479,12 @@ __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* _
   const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
   const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
   const int t = threadIdx.x;
-  stage_rows<L4>(src, row0, nr, ys);
+  stage_tile<L4>(src, row0, nr, ys);
   for (int e = t; e < LC * LC; e += kApplyThreads)
     rs[e / LC][e % LC] = rinv[(size_t)u.x * LPB * LPB + (e / LC) * LPB + e % LC];
   __syncthreads();
   float y[LC];
-#pragma unroll
-  for (int c4 = 0; c4 < L4; ++c4) {
-    const float4 v = *reinterpret_cast<const float4*>(ys + t * kRowStride + 4 * c4);
-    y[4 * c4] = v.x; y[4 * c4 + 1] = v.y; y[4 * c4 + 2] = v.z; y[4 * c4 + 3] = v.w;
-  }
+  load_row<L4>(ys, t, y);
 #pragma unroll
   for (int c4 = 0; c4 < L4; ++c4) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -504,19 +498,27 @@ __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* _
     }
     // row t of the staged tile is read by this thread alone (its y is in registers)
     *reinterpret_cast<float4*>(ys + t * kRowStride + 4 * c4) = acc;
-  }
-  __syncthreads();
-  // the new rows out, 16 bytes per thread and step, zeros beyond column 4 L4
-  {
-    const int c4 = t & 7;
+    if (xbf && t < nr) {
+      __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
+      const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-    for (int k = 0; k < kUnitRows * (LPB / 4) / kApplyThreads; ++k) {
-      const int rr = (t + k * kApplyThreads) >> 3;
-      if (rr < nr)
-        reinterpret_cast<float4*>(dst + (row0 + rr) * LPB)[c4] =
-            c4 < L4 ? *reinterpret_cast<const float4*>(ys + rr * kRowStride + 4 * c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(a4[i]);
+        xb[(int64_t)(4 * c4 + i) * ldx] = hi;
+        if (split) xb[(int64_t)(LPB + 4 * c4 + i) * ldx] = __float2bfloat16_rn(a4[i] - __bfloat162float(hi));
+      }
     }
   }
+  if (xbf && t < nr) {   // the zero columns beyond 4 L4
+    __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+    for (int c = LC; c < LPB; ++c) {
+      xb[(int64_t)c * ldx] = z;
+      if (split) xb[(int64_t)(LPB + c) * ldx] = z;
+    }
+  }
+  __syncthreads();
+  store_tile<L4>(ys, nr, dst, row0, LPB);   // the new rows out, zeros beyond column 4 L4
   if (part) bqr_gram_tile<kApplyThreads, kRowStride>(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
@@ -672,18 +674,14 @@ __global__ void __launch_bounds__(kLiftRows) batched_lift_kernel(const float* __
   if (r_begin >= r_end) return;
   const int nr = (int)(r_end - r_begin);
   const int t = threadIdx.x;
-  stage_rows<L4>(q, r_begin, nr, ys);
+  stage_tile<L4>(q, r_begin, nr, ys);
   for (int e = t; e < LC * LPB; e += kLiftRows) {
     const int c = e % LPB;
     Ss[e / LPB][c] = c < valid ? small[(size_t)b * LPB * LPB + e] : 0.0f;
   }
   __syncthreads();
   float y[LC];
-#pragma unroll
-  for (int c4 = 0; c4 < L4; ++c4) {
-    const float4 v = *reinterpret_cast<const float4*>(ys + t * kRowStride + 4 * c4);
-    y[4 * c4] = v.x; y[4 * c4 + 1] = v.y; y[4 * c4 + 2] = v.z; y[4 * c4 + 3] = v.w;
-  }
+  load_row<L4>(ys, t, y);
   const int n4 = (cols + 3) / 4;
   for (int c4 = 0; c4 < n4; ++c4) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -765,18 +763,22 @@ cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int6
 
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
                                   int rounds, int shift_first, float* rout, float* rinv, const int2* units,
-                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st) {
+                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st,
+                                  __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff, int split) {
   if (nunits <= 0 || rounds < 1) return cudaErrorInvalidValue;
   bqr_gram_kernel<<<nunits, kUnitThreads, 0, st>>>(yin, roff, units, l, part);
   for (int r = 0; r < rounds; ++r) {
     bqr_chol_kernel<<<nb, 128, 0, st>>>(part, ustart, l, (shift_first && r == 0) ? 1.0f : 0.0f, r == 0 ? 1 : 0,
                                         rout, rinv, status);
     const float* yr = r == 0 ? yin : qout;
-    float* pr = r + 1 < rounds ? part : nullptr;
+    const bool last = r + 1 == rounds;
+    float* pr = last ? nullptr : part;
+    __nv_bfloat16* xo = last ? xbf : nullptr;
     switch ((l + 3) / 4) {
-#define RSVD_BQR_APPLY(L4)                                                                       \
-  case L4:                                                                                      \
-    bqr_apply_kernel<L4><<<nunits, kApplyThreads, 0, st>>>(yr, qout, roff, units, l, rinv, pr); \
+#define RSVD_BQR_APPLY(L4)                                                                        \
+  case L4:                                                                                       \
+    bqr_apply_kernel<L4><<<nunits, kApplyThreads, 0, st>>>(yr, qout, roff, units, l, rinv, pr, xo, \
+                                                           ldx, xoff, split);                    \
     break;
       RSVD_BQR_APPLY(1) RSVD_BQR_APPLY(2) RSVD_BQR_APPLY(3) RSVD_BQR_APPLY(4)
       RSVD_BQR_APPLY(5) RSVD_BQR_APPLY(6) RSVD_BQR_APPLY(7) RSVD_BQR_APPLY(8)

@@ -21,6 +21,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "batched_rows.cuh"
 #include "kernels_batched.cuh"
 #include "tc_ptx.cuh"
 
@@ -31,203 +32,224 @@ using namespace tcx;
 
 constexpr int LPB = 32;
 
-// Row kernels of the backward over the 128-row units of the Cholesky-QR (one matrix per
-// unit): the unit's rows and the matrix's 32 x 32 factors are staged in shared memory
-// (coalesced), a warp takes a row at a time with lane = column, holding the column / row
-// of each factor it needs in registers and reading the row as float4 broadcasts; results
-// leave through the staging buffer, coalesced.
-constexpr int kUR = 128;   // rows per unit
-constexpr int kUT = 256;   // threads per unit block
+static_assert(LPB == kTileWidth, "the basis rows are the row tiles of batched_rows.cuh");
 
+// rows of the Cholesky-QR unit u = (matrix, 128-row tile)
 __device__ __forceinline__ void unit_rows(const int64_t* __restrict__ roff, int2 u, int64_t* row0, int* nr) {
-  *row0 = roff[u.x] + (int64_t)u.y * kUR;
-  *nr = (int)min((int64_t)kUR, roff[u.x + 1] - *row0);
+  *row0 = roff[u.x] + (int64_t)u.y * kTileRows;
+  *nr = (int)min((int64_t)kTileRows, roff[u.x + 1] - *row0);
 }
 
-// (kUT threads; every thread's loads are issued before its first store, so they are in
-// flight together)
-__device__ __forceinline__ void unit_stage(const float* __restrict__ src, int64_t row0, int nr,
-                                           float (*ys)[LPB]) {
-  constexpr int N = kUR * (LPB / 4) / kUT;
-  float4 v[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int e = threadIdx.x + k * kUT, rr = e >> 3;
-    v[k] = rr < nr ? reinterpret_cast<const float4*>(src + (row0 + rr) * LPB)[e & 7] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int k = 0; k < N; ++k) reinterpret_cast<float4*>(&ys[0][0])[threadIdx.x + k * kUT] = v[k];
-}
-
-// a 32 x 32 factor into shared memory (rows padded to 33 floats: column and row reads
-// by lane are both conflict-free)
-__device__ __forceinline__ void unit_small(const float* __restrict__ src, float (*ms)[LPB + 1]) {
-  constexpr int N = LPB * LPB / kUT;
-  float v[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = src[threadIdx.x + k * kUT];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int e = threadIdx.x + k * kUT;
-    ms[e >> 5][e & 31] = v[k];
-  }
-}
-
-// sum_j y_j w[j] for the row y in shared memory (float4 broadcasts), w in registers
-__device__ __forceinline__ float row_dot(const float* __restrict__ y, const float (&w)[LPB]) {
-  const float4* y4 = reinterpret_cast<const float4*>(y);
-  float v0 = 0.0f, v1 = 0.0f;
-#pragma unroll
-  for (int i4 = 0; i4 < LPB / 4; ++i4) {
-    const float4 a = y4[i4];
-    v0 = fmaf(a.x, w[4 * i4], v0);
-    v1 = fmaf(a.y, w[4 * i4 + 1], v1);
-    v0 = fmaf(a.z, w[4 * i4 + 2], v0);
-    v1 = fmaf(a.w, w[4 * i4 + 3], v1);
-  }
-  return v0 + v1;
-}
+// The row kernels below take a thread per row of a Cholesky-QR unit (kTileRows threads):
+// the unit's rows are staged by coalesced loads (batched_rows.cuh), a thread holds its row's
+// first 4 L4 entries in registers (L4 = ceil(l / 4): the basis columns beyond l are zero),
+// the per-matrix factors sit in shared memory and are read as float4 broadcasts, the sums
+// run in index order, and the results leave through the staged tile by coalesced stores.
 
 // t_c = P[r][c] (1 - 2 s_c) + 2 s_c^2 u_c with u = Q[r] Ut; gQ[r][i] = sum_{c<k} t_c Ut[i][c];
 // ublk[r][c] = u_c (1 - 2 s_c) for c < k, zero beyond (the first left factor U (I - 2S)).
-__global__ void __launch_bounds__(kUT) bwd_gq_kernel(const float* __restrict__ P, const float* __restrict__ Q,
-                                                     const int64_t* __restrict__ roff,
-                                                     const int2* __restrict__ units,
-                                                     const float* __restrict__ ut, const float* __restrict__ sig,
-                                                     int k, float* __restrict__ gq, float* __restrict__ ublk,
-                                                     int ldu) {
-  __shared__ __align__(16) float qs[kUR][LPB];
-  __shared__ __align__(16) float ps[kUR][LPB];
-  __shared__ __align__(16) float tb[kUT / 32][LPB];
-  __shared__ float Us[LPB][LPB + 1];
-  const int2 u = units[blockIdx.x];
-  int64_t row0;
-  int nr;
-  unit_rows(roff, u, &row0, &nr);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unit_stage(Q, row0, nr, qs);
-  unit_stage(P, row0, nr, ps);
-  unit_small(ut + (size_t)u.x * LPB * LPB, Us);
-  const float s = lane < k ? sig[(size_t)u.x * LPB + lane] : 0.0f;
-  const float c1 = 1.0f - 2.0f * s, c2 = 2.0f * s * s;
-  __syncthreads();
-  float ucol[LPB], urow[LPB];
-#pragma unroll
-  for (int j = 0; j < LPB; ++j) {
-    ucol[j] = Us[j][lane];   // Ut[j][lane]
-    urow[j] = Us[lane][j];   // Ut[lane][j]
-  }
-  for (int rr = warp; rr < nr; rr += kUT / 32) {
-    const float uc = row_dot(qs[rr], ucol);
-    const float t = lane < k ? fmaf(ps[rr][lane], c1, c2 * uc) : 0.0f;
-    tb[warp][lane] = t;
-    __syncwarp();
-    const float g = row_dot(tb[warp], urow);
-    __syncwarp();   // the warp's rows and its tb row are read before they are overwritten
-    qs[rr][lane] = g;
-    ps[rr][lane] = lane < k ? uc * c1 : 0.0f;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nr * LPB; e += blockDim.x) {
-    const int rr = e >> 5, c = e & 31;
-    gq[(row0 + rr) * LPB + c] = qs[rr][c];
-    ublk[(row0 + rr) * ldu + c] = ps[rr][c];
-  }
-}
-
-// gY = (gQ + Q N) R^-T per row: lane j forms w_j = gQ[r][j] + sum_t Q[r][t] N[t][j] (column
-// j of N in registers); lane i then gY[r][i] = sum_j w_j Rinv[i][j] (row i of R^-1).
-__global__ void __launch_bounds__(kUT) bwd_qr_apply_kernel(const float* __restrict__ Q,
-                                                           const float* __restrict__ gQ,
+template <int L4>
+__global__ void __launch_bounds__(kTileRows) bwd_gq_kernel(const float* __restrict__ P, const float* __restrict__ Q,
                                                            const int64_t* __restrict__ roff,
                                                            const int2* __restrict__ units,
-                                                           const float* __restrict__ N,
-                                                           const float* __restrict__ Rinv,
-                                                           float* __restrict__ gY) {
-  __shared__ __align__(16) float qs[kUR][LPB];
-  __shared__ __align__(16) float gs[kUR][LPB];
-  __shared__ __align__(16) float wb[kUT / 32][LPB];
-  __shared__ float Ns[LPB][LPB + 1];
-  __shared__ float Rs[LPB][LPB + 1];
+                                                           const float* __restrict__ ut, const float* __restrict__ sig,
+                                                           int k, float* __restrict__ gq, float* __restrict__ ublk,
+                                                           int ldu) {
+  constexpr int LC = 4 * L4;
+  __shared__ __align__(16) float qs[kTileRows * kRowStride];
+  __shared__ __align__(16) float ps[kTileRows * kRowStride];
+  __shared__ __align__(16) float Us[LC][LPB];     // rows 0 .. LC - 1 of Ut
+  __shared__ __align__(16) float cf[2][LPB];      // 1 - 2 s_c and 2 s_c^2, zero for c >= k
   const int2 u = units[blockIdx.x];
   int64_t row0;
   int nr;
   unit_rows(roff, u, &row0, &nr);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unit_stage(Q, row0, nr, qs);
-  unit_stage(gQ, row0, nr, gs);
-  unit_small(N + (size_t)u.x * LPB * LPB, Ns);
-  unit_small(Rinv + (size_t)u.x * LPB * LPB, Rs);
+  const int t = threadIdx.x;
+  stage_tile<L4>(Q, row0, nr, qs);
+  stage_tile<L4>(P, row0, nr, ps);
+  for (int e = t; e < LC * LPB; e += kTileRows) Us[e / LPB][e % LPB] = ut[(size_t)u.x * LPB * LPB + e];
+  if (t < LPB) {
+    const float s = t < k ? sig[(size_t)u.x * LPB + t] : 0.0f;
+    cf[0][t] = t < k ? 1.0f - 2.0f * s : 0.0f;
+    cf[1][t] = t < k ? 2.0f * s * s : 0.0f;
+  }
   __syncthreads();
-  float ncol[LPB], rrow[LPB];
+  float y[LC], pr[LC];
+  load_row<L4>(qs, t, y);
+  load_row<L4>(ps, t, pr);
+  const int k4 = (k + 3) >> 2;
+  float tv[LC];
+  float4 ub[L4];
 #pragma unroll
-  for (int j = 0; j < LPB; ++j) {
-    ncol[j] = Ns[j][lane];   // N[j][lane]
-    rrow[j] = Rs[lane][j];   // Rinv[lane][j]
+  for (int c4 = 0; c4 < L4; ++c4) {
+    float4 uc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c4 < k4) {
+#pragma unroll
+      for (int j = 0; j < LC; ++j) {
+        const float4 w = *reinterpret_cast<const float4*>(&Us[j][4 * c4]);
+        uc.x = fmaf(y[j], w.x, uc.x);
+        uc.y = fmaf(y[j], w.y, uc.y);
+        uc.z = fmaf(y[j], w.z, uc.z);
+        uc.w = fmaf(y[j], w.w, uc.w);
+      }
+    }
+    const float4 c1 = *reinterpret_cast<const float4*>(&cf[0][4 * c4]);
+    const float4 c2 = *reinterpret_cast<const float4*>(&cf[1][4 * c4]);
+    tv[4 * c4] = fmaf(pr[4 * c4], c1.x, c2.x * uc.x);
+    tv[4 * c4 + 1] = fmaf(pr[4 * c4 + 1], c1.y, c2.y * uc.y);
+    tv[4 * c4 + 2] = fmaf(pr[4 * c4 + 2], c1.z, c2.z * uc.z);
+    tv[4 * c4 + 3] = fmaf(pr[4 * c4 + 3], c1.w, c2.w * uc.w);
+    ub[c4] = make_float4(uc.x * c1.x, uc.y * c1.y, uc.z * c1.z, uc.w * c1.w);
   }
-  for (int rr = warp; rr < nr; rr += kUT / 32) {
-    const float w = gs[rr][lane] + row_dot(qs[rr], ncol);
-    wb[warp][lane] = w;
-    __syncwarp();
-    const float g = row_dot(wb[warp], rrow);
-    __syncwarp();
-    qs[rr][lane] = g;
+  // row t of both tiles is read by this thread alone (its rows are in registers)
+#pragma unroll
+  for (int i4 = 0; i4 < L4; ++i4) {
+    float g[4];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      const int i = 4 * i4 + ii;
+      float a = 0.0f;
+#pragma unroll
+      for (int c4 = 0; c4 < L4; ++c4) {
+        if (c4 < k4) {
+          const float4 w = *reinterpret_cast<const float4*>(&Us[i][4 * c4]);
+          a = fmaf(tv[4 * c4], w.x, a);
+          a = fmaf(tv[4 * c4 + 1], w.y, a);
+          a = fmaf(tv[4 * c4 + 2], w.z, a);
+          a = fmaf(tv[4 * c4 + 3], w.w, a);
+        }
+      }
+      g[ii] = a;
+    }
+    *reinterpret_cast<float4*>(qs + t * kRowStride + 4 * i4) = make_float4(g[0], g[1], g[2], g[3]);
+    *reinterpret_cast<float4*>(ps + t * kRowStride + 4 * i4) = ub[i4];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nr * (LPB / 4); e += blockDim.x)
-    reinterpret_cast<float4*>(gY + row0 * LPB)[e] = reinterpret_cast<const float4*>(&qs[0][0])[e];
+  store_tile<L4>(qs, nr, gq, row0, LPB);
+  store_tile<L4>(ps, nr, ublk, row0, ldu);
 }
 
-// C_u = sum over the rows of a Cholesky-QR unit (matrix b, 128-row tile) of gQ[r][i] Q[r][j]:
-// the partial of gQ^T Q, 256 threads in four row groups with 4 x 4 register blocks (two
-// float4 reads per 16 FMAs), the groups summed in a fixed order.
-constexpr int kCrossRows = 128;
-
-__global__ void __launch_bounds__(256) bwd_cross_kernel(const float* __restrict__ gQ, const float* __restrict__ Q,
-                                                        const int64_t* __restrict__ roff,
-                                                        const int2* __restrict__ units, float* __restrict__ part) {
-  __shared__ __align__(16) float gs[kCrossRows][LPB];
-  __shared__ __align__(16) float qs[kCrossRows][LPB];
-  __shared__ float gp[4][LPB * LPB / 4];   // one quarter of G per row group at a time
+// gY = (gQ + Q N) R^-T per row: w_j = gQ[r][j] + sum_t Q[r][t] N[t][j], then
+// gY[r][i] = sum_{j >= i} w_j Rinv[i][j] (R^-1 is upper triangular).
+template <int L4>
+__global__ void __launch_bounds__(kTileRows) bwd_qr_apply_kernel(const float* __restrict__ Q,
+                                                                 const float* __restrict__ gQ,
+                                                                 const int64_t* __restrict__ roff,
+                                                                 const int2* __restrict__ units,
+                                                                 const float* __restrict__ N,
+                                                                 const float* __restrict__ Rinv,
+                                                                 float* __restrict__ gY) {
+  constexpr int LC = 4 * L4;
+  __shared__ __align__(16) float qs[kTileRows * kRowStride];
+  __shared__ __align__(16) float gs[kTileRows * kRowStride];
+  __shared__ __align__(16) float Ns[LC][LPB];
+  __shared__ __align__(16) float Rs[LC][LPB];
   const int2 u = units[blockIdx.x];
-  const int64_t row0 = roff[u.x] + (int64_t)u.y * kCrossRows;
-  const int nr = (int)min((int64_t)kCrossRows, roff[u.x + 1] - row0);
-  for (int e = threadIdx.x; e < kCrossRows * (LPB / 4); e += blockDim.x) {
-    const int rr = e >> 3;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    reinterpret_cast<float4*>(&gs[0][0])[e] = rr < nr ? reinterpret_cast<const float4*>(gQ + (row0 + rr) * LPB)[e & 7] : z;
-    reinterpret_cast<float4*>(&qs[0][0])[e] = rr < nr ? reinterpret_cast<const float4*>(Q + (row0 + rr) * LPB)[e & 7] : z;
+  int64_t row0;
+  int nr;
+  unit_rows(roff, u, &row0, &nr);
+  const int t = threadIdx.x;
+  stage_tile<L4>(Q, row0, nr, qs);
+  stage_tile<L4>(gQ, row0, nr, gs);
+  for (int e = t; e < LC * LPB; e += kTileRows) {
+    Ns[e / LPB][e % LPB] = N[(size_t)u.x * LPB * LPB + e];
+    Rs[e / LPB][e % LPB] = Rinv[(size_t)u.x * LPB * LPB + e];
   }
   __syncthreads();
-  const int grp = threadIdx.x >> 6, gt = threadIdx.x & 63;
-  const int bi = (gt >> 3) * 4, bj = (gt & 7) * 4;
-  float acc[4][4];
+  float y[LC], g[LC];
+  load_row<L4>(qs, t, y);
+  load_row<L4>(gs, t, g);
+  float w[LC];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j4 = 0; j4 < L4; ++j4) {
+    float4 acc = make_float4(g[4 * j4], g[4 * j4 + 1], g[4 * j4 + 2], g[4 * j4 + 3]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  for (int rr = grp; rr < nr; rr += 4) {
-    const float4 x = *reinterpret_cast<const float4*>(&gs[rr][bi]);
-    const float4 y = *reinterpret_cast<const float4*>(&qs[rr][bj]);
-    const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+    for (int s = 0; s < LC; ++s) {
+      const float4 n4 = *reinterpret_cast<const float4*>(&Ns[s][4 * j4]);
+      acc.x = fmaf(y[s], n4.x, acc.x);
+      acc.y = fmaf(y[s], n4.y, acc.y);
+      acc.z = fmaf(y[s], n4.z, acc.z);
+      acc.w = fmaf(y[s], n4.w, acc.w);
+    }
+    w[4 * j4] = acc.x; w[4 * j4 + 1] = acc.y; w[4 * j4 + 2] = acc.z; w[4 * j4 + 3] = acc.w;
+  }
+#pragma unroll
+  for (int i4 = 0; i4 < L4; ++i4) {
+    float o[4];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      const int i = 4 * i4 + ii;
+      float a = 0.0f;
+#pragma unroll
+      for (int j4 = i4; j4 < L4; ++j4) {
+        const float4 r4 = *reinterpret_cast<const float4*>(&Rs[i][4 * j4]);
+        a = fmaf(w[4 * j4], r4.x, a);
+        a = fmaf(w[4 * j4 + 1], r4.y, a);
+        a = fmaf(w[4 * j4 + 2], r4.z, a);
+        a = fmaf(w[4 * j4 + 3], r4.w, a);
+      }
+      o[ii] = a;
+    }
+    *reinterpret_cast<float4*>(qs + t * kRowStride + 4 * i4) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+  __syncthreads();
+  store_tile<L4>(qs, nr, gY, row0, LPB);
+}
+
+// C_u = sum over the rows of a Cholesky-QR unit (matrix b, 128-row tile) of gQ[r][i] Q[r][j]
+// for i, j < 4 L4 (zero beyond): the partial of gQ^T Q.  The L4 x L4 tiles of 4 x 4 each
+// have one thread in each of NG = 128 / L4^2 row groups (two float4 reads per 16 FMAs);
+// the groups are summed in a fixed order through shared memory.
+template <int L4>
+__global__ void __launch_bounds__(kTileRows) bwd_cross_kernel(const float* __restrict__ gQ, const float* __restrict__ Q,
+                                                              const int64_t* __restrict__ roff,
+                                                              const int2* __restrict__ units, float* __restrict__ part) {
+  constexpr int NTILE = L4 * L4;
+  constexpr int NG = kTileRows / NTILE;
+  __shared__ __align__(16) float gs[kTileRows * kRowStride];
+  __shared__ __align__(16) float qs[kTileRows * kRowStride];
+  __shared__ __align__(16) float gp[NG * NTILE * 16];
+  const int2 u = units[blockIdx.x];
+  int64_t row0;
+  int nr;
+  unit_rows(roff, u, &row0, &nr);
+  stage_tile<L4>(gQ, row0, nr, gs);
+  stage_tile<L4>(Q, row0, nr, qs);
+  __syncthreads();
+  const int grp = threadIdx.x / NTILE, tt = threadIdx.x - grp * NTILE;
+  if (grp < NG) {
+    const int bi = 4 * (tt / L4), bj = 4 * (tt % L4);
+    float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
-  }
-  // the four groups' blocks summed through shared memory, one row quarter of C at a time
-  float* pu = part + (size_t)blockIdx.x * LPB * LPB;
-  for (int qtr = 0; qtr < 4; ++qtr) {
-    __syncthreads();
-    if ((bi >> 3) == qtr) {
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+    for (int rr = grp; rr < nr; rr += NG) {
+      const float4 x = *reinterpret_cast<const float4*>(gs + rr * kRowStride + bi);
+      const float4 y = *reinterpret_cast<const float4*>(qs + rr * kRowStride + bj);
+      const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) gp[grp][(bi - 8 * qtr + i) * LPB + bj + j] = acc[i][j];
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < LPB * LPB / 4; e += blockDim.x)
-      pu[qtr * (LPB * LPB / 4) + e] = (gp[0][e] + gp[1][e]) + (gp[2][e] + gp[3][e]);
+    float* d = gp + (grp * NTILE + tt) * 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float4*>(d + 4 * i) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+  __syncthreads();
+  float* pu = part + (size_t)blockIdx.x * LPB * LPB;
+  for (int e = threadIdx.x; e < LPB * LPB; e += kTileRows) {
+    const int i = e >> 5, j = e & 31, ti = i >> 2, tj = j >> 2;
+    float v = 0.0f;
+    if (ti < L4 && tj < L4) {
+      const int off = (ti * L4 + tj) * 16 + (i & 3) * 4 + (j & 3);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) v += gp[g * NTILE * 16 + off];
+    }
+    pu[e] = v;
   }
 }
 
@@ -548,11 +570,23 @@ __global__ void __launch_bounds__(kFinalThreads, 1) bwd_final_tc_kernel(
 
 }  // namespace
 
+#define RSVD_L4_SWITCH(l, CASE)                                                          \
+  switch (((l) + 3) / 4) {                                                               \
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)                      \
+    default: return cudaErrorInvalidValue;                                               \
+  }
+
 cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, const int2* units, int nunits,
-                          const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
+                          int l, const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st) {
   if (nunits <= 0) return cudaSuccess;
-  bwd_gq_kernel<<<nunits, kUT, 0, st>>>(P, Q, roff, units, ut, sig, k, gq, ublk, ldu);
+  if (k > l || ldu % 4 || (reinterpret_cast<uintptr_t>(ublk) & 15)) return cudaErrorInvalidValue;
+#define RSVD_GQ(L4)                                                                                   \
+  case L4:                                                                                           \
+    bwd_gq_kernel<L4><<<nunits, kTileRows, 0, st>>>(P, Q, roff, units, ut, sig, k, gq, ublk, ldu);   \
+    break;
+  RSVD_L4_SWITCH(l, RSVD_GQ)
+#undef RSVD_GQ
   return cudaGetLastError();
 }
 
@@ -560,17 +594,28 @@ cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* 
                                 int nunits, const int* ustart, int nb, int l, const float* R, float* part,
                                 float* N, float* Rinv, cudaStream_t st) {
   if (nunits <= 0) return cudaSuccess;
-  bwd_cross_kernel<<<nunits, 256, 0, st>>>(gQ, Q, roff, units, part);
+#define RSVD_CROSS(L4)                                                                 \
+  case L4:                                                                            \
+    bwd_cross_kernel<L4><<<nunits, kTileRows, 0, st>>>(gQ, Q, roff, units, part);     \
+    break;
+  RSVD_L4_SWITCH(l, RSVD_CROSS)
+#undef RSVD_CROSS
   bwd_qr_small_kernel<<<nb, 128, 0, st>>>(part, ustart, l, R, N, Rinv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
-                                int nunits, const float* N, const float* Rinv, float* gY, cudaStream_t st) {
+                                int nunits, int l, const float* N, const float* Rinv, float* gY, cudaStream_t st) {
   if (nunits <= 0) return cudaSuccess;
-  bwd_qr_apply_kernel<<<nunits, kUT, 0, st>>>(Q, gQ, roff, units, N, Rinv, gY);
+#define RSVD_QRA(L4)                                                                        \
+  case L4:                                                                                 \
+    bwd_qr_apply_kernel<L4><<<nunits, kTileRows, 0, st>>>(Q, gQ, roff, units, N, Rinv, gY); \
+    break;
+  RSVD_L4_SWITCH(l, RSVD_QRA)
+#undef RSVD_QRA
   return cudaGetLastError();
 }
+#undef RSVD_L4_SWITCH
 
 cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
                               cudaStream_t st) {

@@ -566,11 +566,12 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const float* __restrict_
 // LP + 4 keeps rows 16-byte aligned (float4 loads along a row) with an odd number of
 // float4 per row (a column of float4 loads hits distinct banks).  The factor works
 // on the padded size LP with identity rows and columns beyond l, so every block is
-// a full 16 x 16.  Per block column J: warp 0 factors and inverts the diagonal block
-// in registers (lane = row, shuffles, pivots by a Newton-refined reciprocal square
-// root; branch-free: entries above the diagonal are left as scratch and never read);
-// the panel below is L_iJ = A_iJ X_JJ^T; the trailing lower triangle is updated by
-// all warps, two rows per warp and one column per lane.  The off-diagonal blocks of
+// a full 16 x 16.  Per block column J: warp 0 factors the diagonal block in registers
+// (lane = row, the pivot column by shuffles, pivots by a Newton-refined reciprocal square
+// root; entries above the diagonal collect scratch until their pivot zeroes them) and
+// another warp inverts it; the panel below is L_iJ = A_iJ L_JJ^-T by forward
+// substitution; the trailing lower triangle is updated by all warps, two rows per warp
+// and one column per lane.  The off-diagonal blocks of
 // X follow block row by block row: S = L_I,<I X_<I,<I in 2 x 4 register tiles, then
 // X_I,<I = -X_II S.  Every inner product reads shared memory as float4, so the
 // shared-memory pipe, not the FMA units, sets the pace only where unavoidable.

@@ -32,10 +32,14 @@ cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int6
 // units (b, tile) in matrix order, those of matrix b from ustart[b] (nb + 1 entries);
 // part: nunits x 32 x 32 floats of Gram partials; rinv: nb x 32 x 32 scratch; rout gets
 // the product of the rounds' R factors; shift_first: the first round factors G + s I,
-// s = l u tr(G) (shifted Cholesky QR).  1 + 2 rounds launches.
+// s = l u tr(G) (shifted Cholesky QR).  With xbf, the last round also writes Q as the next
+// pass's operand (as launch_batched_to_bf16t does: matrix b at xbf + xoff[b], leading
+// dimension ldx, with the lo half when split).  1 + 2 rounds launches.
 cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* roff, int nb, int l,
                                   int rounds, int shift_first, float* rout, float* rinv, const int2* units,
-                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st);
+                                  int nunits, const int* ustart, float* part, uint32_t* status, cudaStream_t st,
+                                  __nv_bfloat16* xbf = nullptr, int64_t ldx = 0, const int64_t* xoff = nullptr,
+                                  int split = 0);
 cudaError_t launch_batched_to_bf16t(const float* q, const int64_t* roff, int nb, int64_t total_rows,
                                     __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff, int split,
                                     cudaStream_t st);
@@ -51,8 +55,10 @@ cudaError_t launch_batched_lift(const float* q, const int64_t* roff, int nb, int
 // ---- backward (k_batched_bwd.cu) ----
 // gQ = (P (I - 2 S) + 2 U S^2) Ut_k^T with U = Q Ut_k (per row; P = A V, m side), and
 // ublk = U (I - 2 S) (first k columns, zero beyond), ld ldu.
+// (l: the basis width, columns of Q beyond it are zero; k <= l; ldu a multiple of 4 and
+// ublk 16-byte aligned)
 cudaError_t launch_bwd_gq(const float* P, const float* Q, const int64_t* roff, const int2* units, int nunits,
-                          const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
+                          int l, const float* ut, const float* sig, int k, float* gq, float* ublk, int ldu,
                           cudaStream_t st);
 // per matrix: N = copyltu(-gQ^T Q) (from partials over the Cholesky-QR units: units /
 // nunits / ustart, part: nunits x 32 x 32) and Rinv = R^-1 (R upper, l x l, identity beyond l)
@@ -61,7 +67,7 @@ cudaError_t launch_bwd_qr_small(const float* Q, const float* gQ, const int64_t* 
                                 float* N, float* Rinv, cudaStream_t st);
 // gY = (gQ + Q N) R^-T, per row (over the Cholesky-QR units of the side)
 cudaError_t launch_bwd_qr_apply(const float* Q, const float* gQ, const int64_t* roff, const int2* units,
-                                int nunits, const float* N, const float* Rinv, float* gY, cudaStream_t st);
+                                int nunits, int l, const float* N, const float* Rinv, float* gY, cudaStream_t st);
 // dst[r][col0 + c] = src[r][c] (rows x 32 -> ld ldd)
 cudaError_t launch_copy_block(const float* src, int64_t rows, float* dst, int ldd, int col0,
                               cudaStream_t st);
