@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(256) batched_to_bf16t_kernel(const float* __re
 // ---------------------------------------------------------------------------
 // one-sided Jacobi of the l x l matrices (x_b or x_b^T), one CTA per matrix
 // ---------------------------------------------------------------------------
-constexpr int kJThreads = 512;   // 16 warps: one per column pair of a round
+constexpr int kJThreads = 256;   // 8 warps: a half-warp per column pair of a round (16 pairs)
 
 __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
     const float* __restrict__ x, int transposed, int l, float* __restrict__ ut,
@@ -575,16 +575,26 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
   if (tid == 0) s_rot = 0;
   __syncthreads();
   const int le = l + (l & 1);
+  // a half-warp per pair (two per warp): lane h of it holds rows h and h + 16 of both
+  // columns, so the three sums take four shuffle levels
+  const int half = lane >> 4, hl = lane & 15;
+  const int pr = 2 * warp + half;   // the pair of the round this half-warp takes
   int sweep = 0;
   for (; sweep < 40; ++sweep) {
     for (int round = 0; round < le - 1; ++round) {
-      if (warp < le / 2) {
-        const int p = warp == 0 ? 0 : ((warp - 1 + round) % (le - 1)) + 1;
-        const int kq = le - 1 - warp;
+      if (pr < le / 2) {
+        const int p = pr == 0 ? 0 : ((pr - 1 + round) % (le - 1)) + 1;
+        const int kq = le - 1 - pr;
         const int q = kq == 0 ? 0 : ((kq - 1 + round) % (le - 1)) + 1;
         if (p < l && q < l) {
-          float u = Xc[p][lane], v = Xc[q][lane];
-          const float a = warp_sum(u * u), bb = warp_sum(v * v), g = warp_sum(u * v);
+          const float u0 = Xc[p][hl], u1 = Xc[p][hl + 16], v0 = Xc[q][hl], v1 = Xc[q][hl + 16];
+          float a = fmaf(u0, u0, u1 * u1), bb = fmaf(v0, v0, v1 * v1), g = fmaf(u0, v0, u1 * v1);
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+          }
           if (g != 0.0f && fabsf(g) > tol * sqrtf(a * bb)) {
             const float zeta = __fdividef(bb - a, 2.0f * g);
             const float az = fabsf(zeta);
@@ -594,14 +604,17 @@ __global__ void __launch_bounds__(kJThreads) batched_jacobi_kernel(
             const float w2 = fmaf(t, t, 1.0f);
             float c = rsqrtf(w2);
             c = c * fmaf(-0.5f * w2, c * c, 1.5f);
-            const float sn = c * t, tau = sn / (1.0f + c);
-            Xc[p][lane] = u - sn * fmaf(tau, u, v);
-            Xc[q][lane] = v + sn * fmaf(-tau, v, u);
-            u = Jc[p][lane];
-            v = Jc[q][lane];
-            Jc[p][lane] = u - sn * fmaf(tau, u, v);
-            Jc[q][lane] = v + sn * fmaf(-tau, v, u);
-            if (lane == 0) s_rot = 1;
+            const float sn = c * t, tau = __fdividef(sn, 1.0f + c);
+            Xc[p][hl] = u0 - sn * fmaf(tau, u0, v0);
+            Xc[q][hl] = v0 + sn * fmaf(-tau, v0, u0);
+            Xc[p][hl + 16] = u1 - sn * fmaf(tau, u1, v1);
+            Xc[q][hl + 16] = v1 + sn * fmaf(-tau, v1, u1);
+            const float j0 = Jc[p][hl], j1 = Jc[p][hl + 16], k0 = Jc[q][hl], k1 = Jc[q][hl + 16];
+            Jc[p][hl] = j0 - sn * fmaf(tau, j0, k0);
+            Jc[q][hl] = k0 + sn * fmaf(-tau, k0, j0);
+            Jc[p][hl + 16] = j1 - sn * fmaf(tau, j1, k1);
+            Jc[q][hl + 16] = k1 + sn * fmaf(-tau, k1, j1);
+            if (hl == 0) s_rot = 1;
           }
         }
       }
