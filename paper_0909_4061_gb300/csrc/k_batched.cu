@@ -213,14 +213,15 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_tc_kernel(
 // ---------------------------------------------------------------------------
 // test matrices
 // ---------------------------------------------------------------------------
+// blockIdx.y = g, the group of four columns 4g .. 4g + 3; a thread per row r (over all
+// matrices' rows), its matrix found by binary search on roff.
 __global__ void batched_draw_kernel(uint64_t seed, const int64_t* __restrict__ roff, int nb, int l,
                                     float* __restrict__ omega, __nv_bfloat16* __restrict__ xbf,
                                     int64_t ldx, const int64_t* __restrict__ xoff) {
-  const int64_t total = roff[nb] * (LPB / 4);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e % roff[nb];
-    const int g = (int)(e / roff[nb]);
+  const int64_t nrows = roff[nb];
+  const int g = blockIdx.y;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
     const int b = find_matrix(roff, nb, r);
     const int64_t i = r - roff[b];
     float z[4] = {0.f, 0.f, 0.f, 0.f};
@@ -228,13 +229,19 @@ __global__ void batched_draw_kernel(uint64_t seed, const int64_t* __restrict__ r
       const float4 v = gaussian4(seed_key(seed + (uint64_t)b), (uint32_t)g, (uint32_t)i, 0u);
       z[0] = v.x; z[1] = v.y; z[2] = v.z; z[3] = v.w;
     }
+    // the float32 copy holds exactly the bfloat16 values the first pass multiplies with
+    __nv_bfloat16 h[4];
+    float f[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int j = 4 * g + q;
-      // the float32 copy holds exactly the bfloat16 values the first pass multiplies with
-      const __nv_bfloat16 h = __float2bfloat16_rn(j < l ? z[q] : 0.0f);
-      omega[r * LPB + j] = __bfloat162float(h);
-      if (xbf) xbf[(int64_t)j * ldx + xoff[b] + i] = h;
+      h[q] = __float2bfloat16_rn(4 * g + q < l ? z[q] : 0.0f);
+      f[q] = __bfloat162float(h[q]);
+    }
+    *reinterpret_cast<float4*>(omega + r * LPB + 4 * g) = make_float4(f[0], f[1], f[2], f[3]);
+    if (xbf) {
+      __nv_bfloat16* xb = xbf + xoff[b] + i;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xb[(int64_t)(4 * g + q) * ldx] = h[q];
     }
   }
 }
@@ -769,8 +776,8 @@ cudaError_t launch_batched_tc(int mode, int fold, const void* maps, const void* 
 cudaError_t launch_batched_draw(uint64_t seed, const int64_t* roff, int nb, int64_t total_rows, int l,
                                 float* omega, __nv_bfloat16* xbf, int64_t ldx, const int64_t* xoff,
                                 cudaStream_t st) {
-  batched_draw_kernel<<<grid_for(total_rows * (LPB / 4)), 256, 0, st>>>(seed, roff, nb, l, omega, xbf,
-                                                                          ldx, xoff);
+  const dim3 grid(grid_for(total_rows), LPB / 4);
+  batched_draw_kernel<<<grid, 256, 0, st>>>(seed, roff, nb, l, omega, xbf, ldx, xoff);
   return cudaGetLastError();
 }
 
