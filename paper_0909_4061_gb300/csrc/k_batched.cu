@@ -19,11 +19,13 @@
 //   bqr_*_kernel            : Cholesky-QR rounds over 128-row units of all matrices
 //                             (Gram partials, one CTA per matrix for the 32 x 32 factor,
 //                             its inverse and the product of the R factors, a thread per
-//                             row for the apply).
-//   batched_to_bf16t_kernel : basis -> transposed bfloat16 operand.
+//                             row for the apply, whose last round also writes the next
+//                             pass's operand).
+//   batched_to_bf16t_kernel : basis -> transposed bfloat16 operand (the backward's).
 //   batched_jacobi_kernel   : one CTA per matrix: one-sided Jacobi of an l x l matrix,
-//                             one warp per column pair, sorted outputs.
-//   batched_lift_kernel     : rows of Q_b times the leading columns of a small matrix.
+//                             a half-warp per column pair, sorted outputs.
+//   batched_lift_kernel     : rows of Q_b times the leading columns of a small matrix,
+//                             a thread per row.
 #include <cuda.h>
 
 #include "common.cuh"
