@@ -76,6 +76,10 @@ struct rsvd_plan_s {
   void* a_dev = nullptr;
   float* a_f32 = nullptr;  // float32 staging of A for the host_f32 option
   float *u_dev = nullptr, *s_dev = nullptr, *v_dev = nullptr;
+  // the host copy of A in pieces on several streams (several copy engines at once)
+  static constexpr int kCopyStreams = 4;
+  cudaStream_t cst[kCopyStreams] = {};
+  cudaEvent_t cev[kCopyStreams + 1] = {};
   size_t ws_bytes = 0;
   // CUDA graph of rsvd_svd for one (A, U, S, V) binding
   cudaGraphExec_t gexec = nullptr;
@@ -159,6 +163,10 @@ void free_plan(rsvd_plan_t P) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+  for (cudaStream_t c : P->cst)
+    if (c) cudaStreamDestroy(c);
+  for (cudaEvent_t e : P->cev)
+    if (e) cudaEventDestroy(e);
   void* bufs[] = {P->omega, P->qbuf, P->qtbuf, P->tmp1, P->tmp2, P->partial, P->gpart,
                   P->small, P->sig,  P->status, P->xbf, P->a_dev, P->u_dev, P->s_dev,
                   P->v_dev, P->srft_freq, P->gsrft_perm, P->psi, P->sig2, P->rimg, P->a_f32,
@@ -1216,6 +1224,33 @@ rsvd_status_t rsvd_svd(rsvd_plan_t P, const void* A, float* U, float* S, float* 
   return RSVD_OK;
 }
 
+namespace {
+
+// bytes from host to device in kCopyStreams pieces, each on its own stream after the work
+// already queued on the plan stream; the plan stream then waits for all of them
+rsvd_status_t copy_in_pieces(rsvd_plan_t P, void* dst, const void* src, size_t bytes) {
+  constexpr int NS = rsvd_plan_s::kCopyStreams;
+  if (!P->cst[0]) {
+    for (int c = 0; c < NS; ++c) TRY(cudaStreamCreateWithFlags(&P->cst[c], cudaStreamNonBlocking));
+    for (int c = 0; c <= NS; ++c) TRY(cudaEventCreateWithFlags(&P->cev[c], cudaEventDisableTiming));
+  }
+  TRY(cudaEventRecord(P->cev[0], P->st));
+  const size_t piece = round_up((int64_t)cdiv((int64_t)bytes, NS), 1 << 16);
+  for (int c = 0; c < NS; ++c) {
+    const size_t off = (size_t)c * piece;
+    if (off >= bytes) break;
+    const size_t len = std::min(piece, bytes - off);
+    TRY(cudaStreamWaitEvent(P->cst[c], P->cev[0], 0));
+    TRY(cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len,
+                        cudaMemcpyHostToDevice, P->cst[c]));
+    TRY(cudaEventRecord(P->cev[c + 1], P->cst[c]));
+    TRY(cudaStreamWaitEvent(P->st, P->cev[c + 1], 0));
+  }
+  return RSVD_OK;
+}
+
+}  // namespace
+
 rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, float* S_host,
                             float* V_host) {
   TRYS(check_plan(P));
@@ -1234,13 +1269,13 @@ rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, fl
   }
   if (P->opt.host_f32) {
     // float32 in, the plan's bfloat16 storage (hi, and lo m * lda elements further) out
-    TRY(cudaMemcpyAsync(P->a_f32, A_host, fbytes, cudaMemcpyHostToDevice, P->st));
+    TRYS(copy_in_pieces(P, P->a_f32, A_host, fbytes));
     Step sp(P, RSVD_STEP_CONVERT);
     sp.launched();
     TRY(launch_split_bf16(P->a_f32, P->m, P->n, P->lda, static_cast<__nv_bfloat16*>(P->a_dev),
                           P->lda, hilo ? 1 : 0, P->st));
   } else {
-    TRY(cudaMemcpyAsync(P->a_dev, A_host, abytes, cudaMemcpyHostToDevice, P->st));
+    TRYS(copy_in_pieces(P, P->a_dev, A_host, abytes));
   }
   TRYS(rsvd_svd(P, P->a_dev, P->u_dev, P->s_dev, P->v_dev));
   TRY(cudaMemcpyAsync(U_host, P->u_dev, sizeof(float) * P->m * P->k, cudaMemcpyDeviceToHost, P->st));
