@@ -212,7 +212,7 @@ RSVD_API rsvd_status_t rsvd_range_finder_adaptive(rsvd_plan_t plan, const void* 
 /* rsvd_svd for host-resident data: copies A (host, m x n with the plan's lda,
  * in the plan's dtype, or float32 with the host_f32 option) to a device buffer
  * owned by the plan (allocated on the first call; the copy goes in four pieces on four
- * streams of the plan, so that several copy engines move it at once), runs rsvd_svd,
+ * streams of the plan), runs rsvd_svd,
  * copies U, S, V back to host memory, and waits for completion.  Page-locked host
  * buffers give the full copy bandwidth; pageable buffers work but are staged by the
  * driver. */
