@@ -1230,12 +1230,18 @@ namespace {
 // already queued on the plan stream; the plan stream then waits for all of them.  (Measured
 // with 1 GB from pinned memory: the pieces reach the link's 210 GB/s, where one copy of the
 // whole buffer on the plan stream ran at about 130 GB/s.)
-rsvd_status_t copy_in_pieces(rsvd_plan_t P, void* dst, const void* src, size_t bytes) {
+rsvd_status_t copy_streams(rsvd_plan_t P) {
   constexpr int NS = rsvd_plan_s::kCopyStreams;
   if (!P->cst[0]) {
     for (int c = 0; c < NS; ++c) TRY(cudaStreamCreateWithFlags(&P->cst[c], cudaStreamNonBlocking));
     for (int c = 0; c <= NS; ++c) TRY(cudaEventCreateWithFlags(&P->cev[c], cudaEventDisableTiming));
   }
+  return RSVD_OK;
+}
+
+rsvd_status_t copy_in_pieces(rsvd_plan_t P, void* dst, const void* src, size_t bytes) {
+  constexpr int NS = rsvd_plan_s::kCopyStreams;
+  TRYS(copy_streams(P));
   TRY(cudaEventRecord(P->cev[0], P->st));
   const size_t piece = round_up((int64_t)cdiv((int64_t)bytes, NS), 1 << 16);
   for (int c = 0; c < NS; ++c) {
@@ -1245,6 +1251,29 @@ rsvd_status_t copy_in_pieces(rsvd_plan_t P, void* dst, const void* src, size_t b
     TRY(cudaStreamWaitEvent(P->cst[c], P->cev[0], 0));
     TRY(cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len,
                         cudaMemcpyHostToDevice, P->cst[c]));
+    TRY(cudaEventRecord(P->cev[c + 1], P->cst[c]));
+    TRY(cudaStreamWaitEvent(P->st, P->cev[c + 1], 0));
+  }
+  return RSVD_OK;
+}
+
+// host_f32: the float32 A in pieces of rows on the copy streams, each piece split into the
+// plan's bfloat16 hi (and lo, m * lda elements further) on its stream once its copy lands
+rsvd_status_t copy_split_in_pieces(rsvd_plan_t P, const void* A_host, bool hilo) {
+  constexpr int NS = rsvd_plan_s::kCopyStreams;
+  TRYS(copy_streams(P));
+  TRY(cudaEventRecord(P->cev[0], P->st));
+  const int64_t rp = cdiv(P->m, NS);
+  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(P->a_dev);
+  for (int c = 0; c < NS; ++c) {
+    const int64_t r0 = c * rp, r1 = std::min<int64_t>(P->m, r0 + rp);
+    if (r0 >= r1) break;
+    const size_t len = ((size_t)(r1 - 1 - r0) * P->lda + P->n) * sizeof(float);
+    TRY(cudaStreamWaitEvent(P->cst[c], P->cev[0], 0));
+    TRY(cudaMemcpyAsync(P->a_f32 + r0 * P->lda, static_cast<const float*>(A_host) + r0 * P->lda, len,
+                        cudaMemcpyHostToDevice, P->cst[c]));
+    TRY(launch_split_bf16(P->a_f32 + r0 * P->lda, r1 - r0, P->n, P->lda, out + r0 * P->lda, P->lda,
+                          hilo ? 1 : 0, P->cst[c], P->m * P->lda));
     TRY(cudaEventRecord(P->cev[c + 1], P->cst[c]));
     TRY(cudaStreamWaitEvent(P->st, P->cev[c + 1], 0));
   }
@@ -1270,12 +1299,9 @@ rsvd_status_t rsvd_svd_host(rsvd_plan_t P, const void* A_host, float* U_host, fl
     TRYS(dalloc(P, &P->v_dev, (size_t)P->n * P->k));
   }
   if (P->opt.host_f32) {
-    // float32 in, the plan's bfloat16 storage (hi, and lo m * lda elements further) out
-    TRYS(copy_in_pieces(P, P->a_f32, A_host, fbytes));
-    Step sp(P, RSVD_STEP_CONVERT);
-    sp.launched();
-    TRY(launch_split_bf16(P->a_f32, P->m, P->n, P->lda, static_cast<__nv_bfloat16*>(P->a_dev),
-                          P->lda, hilo ? 1 : 0, P->st));
+    // float32 in, the plan's bfloat16 storage (hi, and lo m * lda elements further) out,
+    // piece by piece, each split while the next ones are still being copied
+    TRYS(copy_split_in_pieces(P, A_host, hilo));
   } else {
     TRYS(copy_in_pieces(P, P->a_dev, A_host, abytes));
   }

@@ -1158,8 +1158,7 @@ __device__ __forceinline__ void split_one(float v, __nv_bfloat16* hi_out, __nv_b
 // on a 16-byte boundary on both sides.
 __global__ void split_bf16_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
                                   int64_t ld, __nv_bfloat16* __restrict__ out, int64_t ld_out,
-                                  int with_lo, int vec4) {
-  const int64_t lo_off = rows * ld_out;
+                                  int with_lo, int vec4, int64_t lo_off) {
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const float* xr = x + r * ld;
     __nv_bfloat16* hr = out + r * ld_out;
@@ -1354,13 +1353,15 @@ cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16
 }
 
 cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st) {
+                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st,
+                              int64_t lo_off) {
   if (rows * cols == 0) return cudaSuccess;
-  const int vec4 = (cols % 4 == 0 && ld % 4 == 0 && ld_out % 4 == 0 &&
+  if (lo_off < 0) lo_off = rows * ld_out;
+  const int vec4 = (cols % 4 == 0 && ld % 4 == 0 && ld_out % 4 == 0 && lo_off % 4 == 0 &&
                     (reinterpret_cast<uintptr_t>(x) & 15) == 0 &&
                     (reinterpret_cast<uintptr_t>(out) & 7) == 0) ? 1 : 0;
   const unsigned grid = (unsigned)(rows < 16 * kNumSMs ? rows : 16 * kNumSMs);
-  split_bf16_kernel<<<grid, 256, 0, st>>>(x, rows, cols, ld, out, ld_out, with_lo, vec4);
+  split_bf16_kernel<<<grid, 256, 0, st>>>(x, rows, cols, ld, out, ld_out, with_lo, vec4, lo_off);
   return cudaGetLastError();
 }
 

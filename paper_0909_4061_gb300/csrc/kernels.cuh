@@ -67,10 +67,11 @@ cudaError_t launch_to_bf16_t(const float* x, int64_t rows, int lp, __nv_bfloat16
                              int64_t ld_t, int split, int lo_off, cudaStream_t st);
 
 // A (float32, rows x cols, ld) -> bfloat16 hi (rows x cols, ld_out) and, with_lo, the
-// bfloat16 residual lo = bf16(A - hi) in the rows x cols block that follows (rows * ld_out
-// elements further).
+// bfloat16 residual lo = bf16(A - hi) lo_off elements further (default, lo_off < 0: the
+// rows x cols block that follows, rows * ld_out elements further).
 cudaError_t launch_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st);
+                              __nv_bfloat16* out, int64_t ld_out, int with_lo, cudaStream_t st,
+                              int64_t lo_off = -1);
 
 // float32 <-> bfloat16 conversion of a whole matrix (rows x cols, ld) for A.
 cudaError_t launch_f32_to_bf16(const float* x, int64_t rows, int64_t cols, int64_t ld,

@@ -294,3 +294,25 @@ def test_c2_full_size_fp32(rsvd_lib):
     del A
     om = philox.gaussian(w.omega_seed, 0, w.n, w.l)
     _check_svd(a64, _np(U), _np(S), _np(V), w.k, w.p, w.q, om)
+
+
+@pytest.mark.parametrize("m", [701, 61])
+def test_host_f32_entry_point_splits_like_the_device(rsvd_lib, m):
+    """rsvd_svd_host with host_f32 = 1 and A stored as hi + lo: the float32 A is copied in
+    four pieces of rows (uneven here: 701 = 3 x 176 + 173, 61 = 3 x 16 + 13)
+    and each piece split into hi + lo on its own stream; the result must equal, bit for
+    bit, rsvd_svd on the device split of the same A."""
+    n, k, p, q = 512, 10, 6, 1
+    a, *_ = synth.lowrank(m, n, synth.spectrum_exp(min(m, n), 7.0), 14)
+    a32 = torch.tensor(a.astype(np.float32)).pin_memory()
+    with rsvd_lib.Plan(m, n, k, p, q, 5, rsvd_lib.RSVD_BF16_TC, dtype=rsvd_lib.RSVD_BF16X2,
+                       residual_passes=1, host_f32=1) as pl:
+        Uh = torch.empty(m, k).pin_memory()
+        Sh = torch.empty(k).pin_memory()
+        Vh = torch.empty(n, k).pin_memory()
+        rsvd_lib.rsvd_svd_host(pl.handle, a32, Uh, Sh, Vh)
+        U, S, V = pl.svd(rsvd_lib.split_bf16(a32.cuda()))
+        assert rsvd_lib.rsvd_sync(pl.handle) == rsvd_lib.RSVD_OK
+    assert np.array_equal(Sh.numpy(), S.cpu().numpy())
+    assert np.array_equal(Uh.numpy(), U.cpu().numpy())
+    assert np.array_equal(Vh.numpy(), V.cpu().numpy())
