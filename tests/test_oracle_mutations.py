@@ -188,3 +188,29 @@ def test_givens_chain_in_the_wrong_order_is_caught(monkeypatch):
 
     monkeypatch.setattr(srft, "givens_chain", bad)
     _fails(pins.test_gsrft_against_the_dense_product)
+
+
+def test_a_last_ignored_is_caught(monkeypatch):
+    """range_finder that lets every product see a_stored (a_last dropped) must fail the pin
+    of the residual-in-the-final-bases reading."""
+    import tests.test_oracle_mixed as mpins
+    from oracle import mixed
+
+    orig = mixed.range_finder
+    monkeypatch.setattr(mixed, "range_finder",
+                        lambda a_stored, omega, q, operand=None, a_last=None: orig(a_stored, omega, q, operand))
+    _fails(mpins.test_last_product_sees_a_last)
+
+
+def test_a_last_in_every_product_is_caught(monkeypatch):
+    """range_finder that uses a_last in every product of Stage A (the early ones too)."""
+    import tests.test_oracle_mixed as mpins
+    from oracle import mixed
+
+    orig = mixed.range_finder
+
+    def bad(a_stored, omega, q, operand=None, a_last=None):
+        return orig(a_stored if a_last is None else a_last, omega, q, operand)
+
+    monkeypatch.setattr(mixed, "range_finder", bad)
+    _fails(mpins.test_last_product_sees_a_last)
