@@ -51,6 +51,32 @@ __device__ __forceinline__ void store_tile(const float* ys, int nr, float* __res
   }
 }
 
+// 16-byte global -> shared copy through L2 (cp.async.cg) that lands without passing through
+// registers, zero-filled (no global read) when !valid
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// stage_tile by cp.async: the copies are issued and left in flight (commit and wait are
+// the caller's); column blocks c4 >= L4 are not copied (a caller that reads them must not)
+template <int L4>
+__device__ __forceinline__ void stage_tile_async(const float* __restrict__ src, int64_t row0, int nr, float* ys) {
+  const int c4 = threadIdx.x & 7;
+  if (c4 >= L4) return;
+#pragma unroll
+  for (int k = 0; k < kTileRows * (kTileWidth / 4) / kTileRows; ++k) {
+    const int rr = (threadIdx.x + k * kTileRows) >> 3;
+    const bool valid = rr < nr;
+    cp_async16(ys + rr * kRowStride + 4 * c4, src + (row0 + (valid ? rr : 0)) * kTileWidth + 4 * c4, valid);
+  }
+}
+
 // the first 4 L4 floats of row t of ys into registers
 template <int L4>
 __device__ __forceinline__ void load_row(const float* ys, int t, float (&y)[4 * L4]) {

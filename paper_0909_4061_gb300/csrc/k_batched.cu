@@ -469,66 +469,99 @@ __global__ void __launch_bounds__(128) bqr_chol_kernel(const float* __restrict__
 // order, as the definition writes the sums).  The new rows replace the old in shared
 // memory, leave by coalesced stores, and give the Gram partial of the next round.
 constexpr int kApplyThreads = kUnitRows;
+constexpr int kApplyCtasPerSm = 4;   // persistent apply: at most 53 KB of shared memory per CTA
 static_assert(kUnitRows == kTileRows && LPB == kTileWidth, "units are the row tiles of batched_rows.cuh");
+
+// With xbf, the new rows also go out as the next pass's operand, transposed bfloat16 (the
+// layout of batched_to_bf16t_kernel, written from the registers that hold them).
+// Persistent: a CTA takes units blockIdx.x, + gridDim.x, ...; while it works one unit, the
+// rows and the R^-1 of its next unit are already being copied into the other half of a
+// double buffer (cp.async), so the unit's loads are not waited for between units.
+// Dynamic shared memory: apply_smem<L4>() bytes.
+template <int L4>
+constexpr size_t apply_smem() {
+  return (size_t)(2 * kUnitRows * kRowStride + 2 * (4 * L4) * (4 * L4) + kApplyThreads * 16) * sizeof(float);
+}
 
 template <int L4>
 __global__ void __launch_bounds__(kApplyThreads) bqr_apply_kernel(const float* __restrict__ src,
                                                                   float* __restrict__ dst,
                                                                   const int64_t* __restrict__ roff,
-                                                                  const int2* __restrict__ units, int l,
+                                                                  const int2* __restrict__ units, int nunits, int l,
                                                                   const float* __restrict__ rinv,
                                                                   float* __restrict__ part,
                                                                   __nv_bfloat16* __restrict__ xbf, int64_t ldx,
                                                                   const int64_t* __restrict__ xoff, int split) {
   constexpr int LC = 4 * L4;
-  __shared__ __align__(16) float ys[kUnitRows * kRowStride];
-  __shared__ __align__(16) float rs[LC][LC];
-  __shared__ __align__(16) float gp[kApplyThreads * 16];
-  const int2 u = units[blockIdx.x];
-  const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
-  const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
+  extern __shared__ __align__(16) float dsm[];
+  // staged rows of two units, then R^-1 (LC x LC) of two units, then the Gram scratch
+  auto ysb = [&](int b) { return dsm + b * (kUnitRows * kRowStride); };
+  auto rsb = [&](int b) { return dsm + 2 * kUnitRows * kRowStride + b * (LC * LC); };
+  float* gp = dsm + 2 * kUnitRows * kRowStride + 2 * LC * LC;
   const int t = threadIdx.x;
-  stage_tile<L4>(src, row0, nr, ys);
-  for (int e = t; e < LC * LC; e += kApplyThreads)
-    rs[e / LC][e % LC] = rinv[(size_t)u.x * LPB * LPB + (e / LC) * LPB + e % LC];
-  __syncthreads();
-  float y[LC];
-  load_row<L4>(ys, t, y);
-#pragma unroll
-  for (int c4 = 0; c4 < L4; ++c4) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < 4 * c4 + 4; ++i) {
-      const float4 r = *reinterpret_cast<const float4*>(&rs[i][4 * c4]);
-      acc.x = fmaf(y[i], r.x, acc.x);
-      acc.y = fmaf(y[i], r.y, acc.y);
-      acc.z = fmaf(y[i], r.z, acc.z);
-      acc.w = fmaf(y[i], r.w, acc.w);
+  auto issue = [&](int ui, int b) {
+    const int2 u = units[ui];
+    const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
+    const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
+    stage_tile_async<L4>(src, row0, nr, ysb(b));
+    for (int e = t; e < LC * L4; e += kApplyThreads) {
+      const int i = e / L4, c4 = e - i * L4;
+      cp_async16(rsb(b) + i * LC + 4 * c4, rinv + (size_t)u.x * LPB * LPB + i * LPB + 4 * c4, true);
     }
-    // row t of the staged tile is read by this thread alone (its y is in registers)
-    *reinterpret_cast<float4*>(ys + t * kRowStride + 4 * c4) = acc;
-    if (xbf && t < nr) {
-      __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
-      const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+  };
+  int ui = blockIdx.x;
+  if (ui >= nunits) return;
+  issue(ui, 0);
+  cp_async_commit();
+  for (int b = 0; ui < nunits; ui += gridDim.x, b ^= 1) {
+    if (ui + (int)gridDim.x < nunits) issue(ui + gridDim.x, b ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();   // this unit's copies have landed; the next unit's may still fly
+    __syncthreads();
+    float* ys = ysb(b);
+    const float* rs = rsb(b);
+    const int2 u = units[ui];
+    const int64_t row0 = roff[u.x] + (int64_t)u.y * kUnitRows;
+    const int nr = (int)min((int64_t)kUnitRows, roff[u.x + 1] - row0);
+    float y[LC];
+    load_row<L4>(ys, t, y);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(a4[i]);
-        xb[(int64_t)(4 * c4 + i) * ldx] = hi;
-        if (split) xb[(int64_t)(LPB + 4 * c4 + i) * ldx] = __float2bfloat16_rn(a4[i] - __bfloat162float(hi));
+    for (int c4 = 0; c4 < L4; ++c4) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 4 * c4 + 4; ++i) {
+        const float4 r = *reinterpret_cast<const float4*>(rs + i * LC + 4 * c4);
+        acc.x = fmaf(y[i], r.x, acc.x);
+        acc.y = fmaf(y[i], r.y, acc.y);
+        acc.z = fmaf(y[i], r.z, acc.z);
+        acc.w = fmaf(y[i], r.w, acc.w);
+      }
+      // row t of the staged tile is read by this thread alone (its y is in registers)
+      *reinterpret_cast<float4*>(ys + t * kRowStride + 4 * c4) = acc;
+      if (xbf && t < nr) {
+        __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
+        const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const __nv_bfloat16 hi = __float2bfloat16_rn(a4[i]);
+          xb[(int64_t)(4 * c4 + i) * ldx] = hi;
+          if (split) xb[(int64_t)(LPB + 4 * c4 + i) * ldx] = __float2bfloat16_rn(a4[i] - __bfloat162float(hi));
+        }
       }
     }
-  }
-  if (xbf && t < nr) {   // the zero columns beyond 4 L4
-    __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-    for (int c = LC; c < LPB; ++c) {
-      xb[(int64_t)c * ldx] = z;
-      if (split) xb[(int64_t)(LPB + c) * ldx] = z;
+    if (xbf && t < nr) {   // the zero columns beyond 4 L4
+      __nv_bfloat16* xb = xbf + xoff[u.x] + (int64_t)u.y * kUnitRows + t;
+      const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+      for (int c = LC; c < LPB; ++c) {
+        xb[(int64_t)c * ldx] = z;
+        if (split) xb[(int64_t)(LPB + c) * ldx] = z;
+      }
     }
+    __syncthreads();
+    store_tile<L4>(ys, nr, dst, row0, LPB);   // the new rows out, zeros beyond column 4 L4
+    if (part) bqr_gram_tile<kApplyThreads, kRowStride>(ys, nr, l, gp, part + (size_t)ui * LPB * LPB);
+    __syncthreads();   // this unit's buffers are free for the copies issued next iteration
   }
-  __syncthreads();
-  store_tile<L4>(ys, nr, dst, row0, LPB);   // the new rows out, zeros beyond column 4 L4
-  if (part) bqr_gram_tile<kApplyThreads, kRowStride>(ys, nr, l, gp, part + (size_t)blockIdx.x * LPB * LPB);
 }
 
 // basis rows (concatenated, LPB wide) -> transposed bfloat16 operand (LPB x sum K); one CTA
@@ -744,7 +777,21 @@ size_t batched_tc_smem(int stages, int fold) {
   return (size_t)stages * (BM * BK * 2 + (fold ? 2 : 1) * LPB * BK * 2) + 1024;
 }
 
+template <int L4>
+cudaError_t prep_apply() {
+  return cudaFuncSetAttribute(bqr_apply_kernel<L4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)apply_smem<L4>());
+}
+
 cudaError_t prepare_batched() {
+  {
+    cudaError_t e;
+    if ((e = prep_apply<1>()) != cudaSuccess || (e = prep_apply<2>()) != cudaSuccess ||
+        (e = prep_apply<3>()) != cudaSuccess || (e = prep_apply<4>()) != cudaSuccess ||
+        (e = prep_apply<5>()) != cudaSuccess || (e = prep_apply<6>()) != cudaSuccess ||
+        (e = prep_apply<7>()) != cudaSuccess || (e = prep_apply<8>()) != cudaSuccess)
+      return e;
+  }
   cudaError_t e;
   const int s0 = (int)batched_tc_smem(kBatchedStages, 0), s1 = (int)batched_tc_smem(kBatchedStages, 1);
   if ((e = cudaFuncSetAttribute(batched_tc_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0)) != cudaSuccess ||
@@ -796,11 +843,13 @@ cudaError_t launch_batched_cholqr(const float* yin, float* qout, const int64_t* 
     const bool last = r + 1 == rounds;
     float* pr = last ? nullptr : part;
     __nv_bfloat16* xo = last ? xbf : nullptr;
+    const int grid = nunits < kApplyCtasPerSm * kNumSMs ? nunits : kApplyCtasPerSm * kNumSMs;
     switch ((l + 3) / 4) {
-#define RSVD_BQR_APPLY(L4)                                                                        \
-  case L4:                                                                                       \
-    bqr_apply_kernel<L4><<<nunits, kApplyThreads, 0, st>>>(yr, qout, roff, units, l, rinv, pr, xo, \
-                                                           ldx, xoff, split);                    \
+#define RSVD_BQR_APPLY(L4)                                                                          \
+  case L4:                                                                                         \
+    bqr_apply_kernel<L4><<<grid, kApplyThreads, apply_smem<L4>(), st>>>(yr, qout, roff, units, nunits, \
+                                                                       l, rinv, pr, xo, ldx, xoff,   \
+                                                                       split);                       \
     break;
       RSVD_BQR_APPLY(1) RSVD_BQR_APPLY(2) RSVD_BQR_APPLY(3) RSVD_BQR_APPLY(4)
       RSVD_BQR_APPLY(5) RSVD_BQR_APPLY(6) RSVD_BQR_APPLY(7) RSVD_BQR_APPLY(8)
